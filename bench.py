@@ -1,0 +1,349 @@
+#!/usr/bin/env python
+"""Benchmark of the CEM explicit step on GB300.
+
+Workload: the 0.1 x 0.04 x 0.01 m notched block refined to 200 x 80 x 10
+hexahedral cells split into six tetrahedra each (960,000 elements, 179,091
+nodes), E = 32 GPa, nu = 0.2, rho = 2450 kg/m^3, Gc = 3 J/m^2, 1 MPa traction
+on the top and bottom faces, element splitting on.  A "step" is one explicit
+time step of the whole path: predictor, element strains, smoothed edge
+stresses, element forces, node update, energy release rates of the crack-front
+elements and the splits they trigger.
+
+Metric: tet-steps/s = (input elements) x (timed steps) / (device time), max
+over ranks, summed over ranks (independent replicas; the step is not sharded
+across GPUs).  Prints one JSON line on rank 0.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl cem|reference]
+
+--impl reference times the CPU FP64 oracle (test infrastructure) on the same
+workload on the host cores, single-threaded.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+if "reference" in sys.argv or "--cpu-baseline-worker" in sys.argv:
+    for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "NUMEXPR_NUM_THREADS"):
+        os.environ[_v] = "1"
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "tet-steps/s"
+WORKLOAD = "notched_block_200x80x10"
+
+
+def _workload():
+    from cem_inputs import plate_medium
+    return plate_medium()
+
+
+KERNEL_UNITS = {"predict": "nodes", "strain": "tets", "edge_stress": "edges", "force": "tets", "node_update": "nodes"}
+
+
+def kernel_costs(T, E, N):
+    """Algorithmic FP64 flops (FMA = 2) and bytes per unit of each hot kernel.
+
+    Bytes are the arrays the kernel reads or writes, each once (gathered
+    operands counted once per producer: u per node, h per element, sigma per
+    edge, element forces per element).  f = mean fan size 6T/E, g = mean node
+    incidence 4T/N.
+    """
+    f, g = 6.0 * T / E, 4.0 * T / N
+    flops = {"predict": 12.0, "strain": 57.0, "edge_stress": 6.0 * f + 13.0, "force": 90.0,
+             "node_update": 3.0 * g + 18.0}
+    byts = {"predict": 96.0,
+            "strain": 16 + 72 + 48 + 24.0 * N / T,
+            "edge_stress": 8 + 4.0 * f + 16 + 48 + 48.0 * T / E,
+            "force": 24 + 72 + 96 + 48.0 * E / T,
+            "node_update": 8 + 4.0 * g + 24 + 8 + 96 + 96.0 * T / N}
+    return flops, byts
+
+
+# --------------------------------------------------------------------------- helpers
+def _args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=300)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", choices=["cem", "reference"], default="cem")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-baseline-worker", action="store_true", help=argparse.SUPPRESS)
+    p.add_argument("--cpu-steps", type=int, default=12, help=argparse.SUPPRESS)
+    return p.parse_args()
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples every 200 ms while running."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, bus_id=None):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        cmd = ["nvidia-smi", "--query-gpu=" + self.Q, "--format=csv,noheader,nounits", "-lms", "200"]
+        if bus_id:
+            cmd += ["-i", bus_id]
+        try:
+            self.p = subprocess.Popen(cmd, stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except Exception:
+                self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def _bus_id(dev):
+    try:
+        import torch
+        p = torch.cuda.get_device_properties(dev)
+        return "%08X:%02X:%02X.0" % (p.pci_domain_id, p.pci_bus_id, p.pci_device_id)
+    except Exception:
+        return None
+
+
+def _oracle_rate(steps):
+    """Time the CPU oracle on the benchmark workload: (tet-steps/s, steps, seconds)."""
+    from oracle import CEMOracle
+    w = _workload()
+    o = CEMOracle.from_workload(w)
+    o.step(1)
+    t0 = time.perf_counter()
+    o.step(steps)
+    dt = time.perf_counter() - t0
+    return w.n_tets * steps / dt, steps, dt
+
+
+def _cpu_baseline(steps):
+    """Run the oracle in a single-threaded subprocess; returns the cpu_baseline object."""
+    cmd = [sys.executable, os.path.abspath(__file__), "--cpu-baseline-worker", "--cpu-steps", str(steps)]
+    env = dict(os.environ)
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "NUMEXPR_NUM_THREADS"):
+        env[v] = "1"
+    r = subprocess.run(cmd, capture_output=True, text=True, env=env, timeout=1800)
+    res = json.loads(r.stdout.strip().splitlines()[-1])
+    return {"value": res["value"], "unit": METRIC, "cores": 1, "kind": "oracle",
+            "sample": "%s, steps 2-%d of the run (%.1f s of CPU time; setup untimed), "
+                      "single-threaded numpy/scipy FP64 oracle" % (WORKLOAD, res["steps"] + 1, res["seconds"])}
+
+
+# --------------------------------------------------------------------------- arms
+def run_reference(a):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    w = _workload()
+    from oracle import CEMOracle
+    o = CEMOracle.from_workload(w)
+    o.step(max(1, min(a.warmup, 3)))
+    budget_s = 150.0
+    t0 = time.perf_counter()
+    done = 0
+    while done < a.steps and (time.perf_counter() - t0) < budget_s:
+        o.step(1)
+        done += 1
+    dt = time.perf_counter() - t0
+    value = w.n_tets * done / dt
+    line = {"metric": METRIC, "value": value, "unit": METRIC, "impl": "reference", "n_gpus": a.gpus,
+            "steps": done, "warmup": a.warmup, "ms_per_step": 1e3 * dt / done, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "tets": w.n_tets, "nodes": w.n_nodes, "precision": "fp64",
+                       "split": True},
+            "cpu_baseline": {"value": value, "unit": METRIC, "cores": 1, "kind": "oracle",
+                             "sample": "%s, %d steps after %d warm-up steps (capped at %.0f s), single-threaded"
+                                       % (WORKLOAD, done, max(1, min(a.warmup, 3)), budget_s)},
+            "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_cem(a):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = local
+
+    from paper_2508_04076_gb300 import CEM, probe_fp64_fma
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+
+    w = _workload()
+    sim = CEM.from_workload(w, device=dev)
+    info0 = sim.info()
+    sim.step(a.warmup)
+    barrier()
+    stream = torch.cuda.current_stream(dev)
+    clocks = ClockSampler(_bus_id(dev)) if rank == 0 else None
+    sim.profile(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sim.step(a.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_ms = e0.elapsed_time(e1)
+    clk = clocks.stop() if clocks else None
+    prof, launches = sim.profile_read()
+    sim.profile(False)
+    barrier()
+    tmax = torch.tensor([t_ms], device="cuda", dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    t_ms = float(tmax.item())
+    info = sim.info()
+    energy = sim.energy()
+    units_total = w.n_tets * a.steps * world
+    value = units_total / (t_ms * 1e-3)
+
+    # dominant kernel and its roofline
+    fp64_peak_meas = probe_fp64_fma(dev, stream.cuda_stream)
+    peaks = _peaks()
+    hbm = peaks.get("hbm_gbs")
+    hot = {k: prof[k] for k in KERNEL_UNITS}
+    dom = max(hot, key=lambda k: hot[k][0])
+    Tm = (info0["n_tets"] + info["n_tets"]) / 2.0          # element slots launched (mean over the window)
+    Ta = (info0["n_active_tets"] + info["n_active_tets"]) / 2.0
+    Em = (info0["n_edges"] + info["n_edges"]) / 2.0
+    Nm = (info0["n_nodes"] + info["n_nodes"]) / 2.0
+    fl, by = kernel_costs(Ta, Em, Nm)
+    sm_clock = (clk or {}).get("sm_max_mhz") or peaks.get("sm_max_mhz") or 2070.0
+    fp64_peak = 152 * 4 * sm_clock * 1e6      # 152 SMs x 2 FP64 FMA/clk x 2 FLOP
+    kernels = {}
+    for k, (ms_tot, nl) in prof.items():
+        kernels[k] = {"ms": ms_tot, "launches": nl, "share": ms_tot / max(t_ms, 1e-9)}
+        if k in KERNEL_UNITS and nl:
+            units = {"tets": Tm, "edges": Em, "nodes": Nm}[KERNEL_UNITS[k]]
+            s = ms_tot * 1e-3 / nl
+            kernels[k].update(per_launch_us=s * 1e6, tflops=fl[k] * units / s / 1e12,
+                              gbs=by[k] * units / s / 1e9)
+    ms_tot, nl = hot[dom]
+    per_launch_s = ms_tot * 1e-3 / max(nl, 1)
+    units = {"tets": Tm, "edges": Em, "nodes": Nm}[KERNEL_UNITS[dom]]
+    flops, bytes_ = fl[dom] * units, by[dom] * units
+    alu_bound = flops / fp64_peak > bytes_ / ((hbm or 6651.4) * 1e9)
+    if alu_bound:
+        achieved, peak, unit = flops / per_launch_s / 1e12, fp64_peak / 1e12, "TFLOP/s"
+        src = "derived: 152 SMs x 4 FP64 FLOP/clk x %.0f MHz (nominal 1.25 TFLOP/s at 2070 MHz)" % sm_clock
+    else:
+        achieved, peak, unit = bytes_ / per_launch_s / 1e9, hbm, "GB/s"
+        src = "MEASURED_PEAKS.json hbm_gbs (measured)"
+    roofline = {"bound": "alu" if alu_bound else "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
+                "unit": unit, "frac": achieved / peak, "traffic": None, "peak_source": src,
+                "per_launch_us": per_launch_s * 1e6,
+                "algorithmic_flops_per_launch": flops, "algorithmic_bytes_per_launch": bytes_,
+                "fp64_fma_measured_tflops": fp64_peak_meas / 1e12,
+                "hbm_gbs_achieved": bytes_ / per_launch_s / 1e9, "hbm_peak_gbs": hbm,
+                "fp64_tflops_achieved": flops / per_launch_s / 1e12, "fp64_peak_tflops": fp64_peak / 1e12}
+
+    # end to end through the public API with host buffers: create + material + K steps + read back
+    barrier()
+    t0 = time.perf_counter()
+    sim2 = CEM.from_workload(w, device=dev)
+    sim2.step(a.steps)
+    u = sim2.field("u")
+    e2 = sim2.energy()
+    torch.cuda.synchronize()
+    t_e2e = time.perf_counter() - t0
+    sim2.close()
+    te = torch.tensor([t_e2e], device="cuda", dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    t_e2e = float(te.item())
+    h2d = (w.X.nbytes + w.tets.nbytes + w.tfaces.nbytes + w.tvec.nbytes + w.notch_tet.nbytes
+           + w.notch_side.nbytes + 16)
+    d2h = u.nbytes + 64
+    sim.close()
+
+    if rank != 0:
+        return
+    cpu = None
+    if world == 1 and not a.no_cpu_baseline:
+        try:
+            cpu = _cpu_baseline(a.cpu_steps)
+        except Exception as ex:  # reported, not hidden
+            cpu = {"value": None, "unit": METRIC, "cores": 1, "kind": "oracle", "sample": "failed: %r" % (ex,)}
+    line = {
+        "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
+        "ms_per_step": t_ms / a.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "tets": w.n_tets, "nodes": w.n_nodes, "edges": info0["n_edges"],
+                   "precision": "fp64", "split": True, "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "working set %.2f GB > 129 MB L2 (no flush needed)" % (info["device_bytes"] / 1e9),
+                   "split_elements_at_end": energy["n_split"], "steps_before_timing": a.warmup},
+        "roofline": roofline,
+        "kernels": kernels,
+        "clocks": clk,
+        "e2e": {"value": w.n_tets * a.steps * world / t_e2e, "unit": METRIC,
+                "h2d_bytes_per_step": h2d / a.steps, "d2h_bytes_per_step": d2h / a.steps,
+                "includes": "mesh upload and topology build, material, K steps, u and energy read-back"},
+        "gpu_launches": launches,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    a = _args()
+    if a.cpu_baseline_worker:
+        v, s, t = _oracle_rate(a.cpu_steps)
+        print(json.dumps({"value": v, "steps": s, "seconds": t}))
+        return
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_cem(a)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,208 @@
+/*
+ * cem.h -- C ABI of the GB300 crack element method (CEM) library.
+ *
+ * The library advances the explicit ES-T-FEM time step of the 3D crack
+ * element method (arxiv 2508.04076) on a linear-tetrahedron mesh held in GPU
+ * memory, evaluates the energy release rate of every crack-front element and
+ * splits elements whose rate exceeds Gc.  All arithmetic of the step runs in
+ * the library's own sm_103a CUDA kernels.
+ *
+ * Conventions shared by every entry point
+ *   - Every function returns an int status: CEM_OK (0) or a negative CEM_E*
+ *     code.  cem_last_error() returns a message for the last failure on a
+ *     context (a static string owned by the context, valid until the next
+ *     call on it).
+ *   - Host arrays passed in are read during the call and copied; the caller
+ *     keeps ownership.  Outputs go to caller-owned host buffers.
+ *   - Device memory is obtained through the allocator in cem_mesh_desc (or
+ *     cudaMalloc when none is given) once, in cem_mesh_create; cem_step never
+ *     allocates.  Every allocation is released by cem_destroy.
+ *   - All device work is queued on the stream given at creation.  cem_step
+ *     synchronises that stream once per step while crack-front elements exist
+ *     (to learn whether any element splits); cem_energy, cem_crack_state and
+ *     cem_get_field return after their results are on the host.
+ *   - A context is not thread-safe; use one host thread per context.
+ *   - Node arrays are returned in the library's canonical order: the input
+ *     nodes first, then one node per (cut original edge, endpoint side) in
+ *     ascending (edge id, side) order, where original edge ids enumerate the
+ *     input mesh's edges by ascending (smaller node id, larger node id).
+ *   - Element local numbering: local edge l joins local nodes
+ *     (0,1),(0,2),(0,3),(1,2),(1,3),(2,3); local face f is the face opposite
+ *     local node f.  An element given with negative signed volume has its
+ *     local nodes 2 and 3 swapped on input (side masks are permuted alike).
+ */
+#ifndef CEM_H
+#define CEM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define CEM_OK          0
+#define CEM_EINVAL     -1   /* bad argument or malformed mesh                        */
+#define CEM_ENOMEM     -2   /* the allocator returned NULL                           */
+#define CEM_ECUDA      -3   /* a CUDA runtime call failed                            */
+#define CEM_ECAPACITY  -4   /* split capacity exhausted; state left at step start   */
+#define CEM_ENONFINITE -5   /* a non-finite displacement was produced               */
+#define CEM_ETIMEOUT   -6   /* reserved: a bounded device wait gave up              */
+#define CEM_ESTATE     -7   /* call not valid in the context's current state        */
+
+/* precision of the force evaluation */
+#define CEM_FP64   0        /* every quantity in FP64                                */
+#define CEM_MIXED  1        /* reserved for FP32 stresses/forces with FP64 state     */
+
+/* fields for cem_get_field */
+#define CEM_FIELD_U 0       /* displacement u                                         */
+#define CEM_FIELD_V 1       /* velocity v                                             */
+#define CEM_FIELD_A 2       /* acceleration a                                         */
+#define CEM_FIELD_X 3       /* reference coordinates X                                */
+
+/* crack patterns reported by cem_crack_state (Sec. 3, Fig. 5) */
+#define CEM_PATTERN_I  1    /* quadrilateral G1 G2 G4 G3: two nodes on each side      */
+#define CEM_PATTERN_II 2    /* triangle G1 G2 G6: one node cut off                    */
+
+/* Device allocator hooks.  alloc returns a device pointer of at least `bytes`
+ * bytes (256-byte aligned) or NULL; free releases it.  `stream` is the
+ * context's stream.  Both are called only inside cem_mesh_create and
+ * cem_destroy. */
+typedef void* (*cem_alloc_fn)(size_t bytes, void* stream, void* user);
+typedef void  (*cem_free_fn)(void* ptr, void* stream, void* user);
+
+/* Mesh, load and notch description for cem_mesh_create (host pointers). */
+typedef struct cem_mesh_desc {
+    int64_t        n_nodes;      /* N > 0                                              */
+    int64_t        n_tets;       /* T > 0                                              */
+    const double*  X;            /* N x 3 row-major reference coordinates [m]          */
+    const int32_t* tets;         /* T x 4 node ids of linear tetrahedra                */
+    int64_t        n_tfaces;     /* F >= 0 traction triangles                          */
+    const int32_t* tfaces;       /* F x 3 node ids                                     */
+    const double*  tvec;         /* F x 3 traction vector of each face [Pa]; the load  */
+                                 /* t*A/3 goes to each face node (Sec. 2.2, Eq. 12)    */
+    int64_t        n_notch;      /* K >= 0 pre-split (notch) elements                  */
+    const int32_t* notch_tet;    /* K element ids, distinct                            */
+    const uint8_t* notch_side;   /* K 4-bit masks over local nodes naming the two      */
+                                 /* sides of the notch crack (not 0, not 15)           */
+    int32_t        precision;    /* CEM_FP64                                           */
+    double         dt;           /* > 0: fixed step [s]; <= 0: cfl_factor * h_min /   */
+                                 /* (2 c_d) (see cem_set_material)                     */
+    double         cfl_factor;   /* used when dt <= 0; <= 0 means 0.5                  */
+    int32_t        split_enabled;/* 0: fixed topology after the notch; 1: CEM splitting*/
+    int64_t        split_capacity; /* max original elements that may be split,         */
+                                 /* notch included; <= 0 means n_tets                  */
+    void*          stream;       /* cudaStream_t for all device work (0 = legacy)      */
+    int32_t        device;       /* CUDA device ordinal                                */
+    cem_alloc_fn   alloc;        /* NULL: cudaMalloc                                   */
+    cem_free_fn    free;         /* NULL: cudaFree                                     */
+    void*          alloc_user;   /* passed to alloc/free                               */
+} cem_mesh_desc;
+
+typedef struct cem_ctx cem_ctx;
+
+/* Energies of the current state (Sec. 2.1, Eq. 2 terms). */
+typedef struct cem_energy_t {
+    double  kinetic;     /* 1/2 sum_i m_i |v_i|^2                                       */
+    double  strain;      /* sum_k 1/2 Vs_k eps_k . sigma_k (smoothed edge strains)       */
+    double  ext_work;    /* f_ext . u (load held constant)                               */
+    double  dissipated;  /* U_d = sum over runtime splits of Gc * crack area            */
+    double  modified;    /* kinetic + strain - ext_work - dt^2/8 a.M.a, conserved by    */
+                         /* the central-difference map while the topology is fixed     */
+    int64_t step;        /* completed steps                                             */
+    double  time;        /* step * dt [s]                                               */
+    int64_t n_split;     /* elements split at run time (notch excluded)                 */
+} cem_energy_t;
+
+/* Sizes and the time step of a context. */
+typedef struct cem_info_t {
+    int64_t n_nodes;         /* current nodes (input + split nodes)                     */
+    int64_t n_tets;          /* current element slots (input + sub-elements)            */
+    int64_t n_active_tets;   /* elements taking part in the step                        */
+    int64_t n_edges;         /* current edges (smoothing domains)                       */
+    int64_t n_candidates;    /* current crack-front elements                            */
+    int64_t n_orig_edges;    /* edges of the input mesh                                 */
+    double  dt;              /* time step [s]                                           */
+    double  h_min;           /* min over input elements of 3V / max face area [m]       */
+    int64_t device_bytes;    /* device memory held by the context                       */
+} cem_info_t;
+
+/* Build the device mesh: edges and their element fans (Sec. 2.2, Fig. 4),
+ * node incidence, face adjacency, traction load, and apply the notch splits
+ * with the same rule as run-time splits.  Errors: CEM_EINVAL (counts, ids
+ * out of range, zero-volume element, bad side mask), CEM_ENOMEM, CEM_ECUDA.
+ * On success *out owns all device memory of the context. */
+int cem_mesh_create(const cem_mesh_desc* d, cem_ctx** out);
+
+/* Material (Sec. 2.1): density rho [kg/m^3], Poisson ratio nu, Young's
+ * modulus E [Pa] (nE = 1: uniform, nE = n_tets: per input element) and
+ * critical energy release rate Gc [J/m^2] (nGc = 1 or n_tets).  Computes the
+ * Lame constants, fan-averaged elasticity, lumped mass (Eq. 11), the time
+ * step when automatic, and a_0 = M^-1 (f_ext - f_int(0)).  Required before
+ * the first cem_step; CEM_ESTATE afterwards. */
+int cem_set_material(cem_ctx* ctx, double rho, double nu,
+                     const double* E, int64_t nE, const double* Gc, int64_t nGc);
+
+/* Advance n >= 0 explicit steps (Eqs. 13-15, beta = 0, gamma = 1/2).  After
+ * each step the energy release rates G_I, G_II (Eqs. 16-18) of every
+ * crack-front element are evaluated on the end-of-step state, and every
+ * element with max(G_I, G_II) > Gc is split (Sec. 3).  Errors: CEM_ESTATE
+ * (no material), CEM_ECAPACITY (state left at the last completed step),
+ * CEM_ECUDA. */
+int cem_step(cem_ctx* ctx, int64_t n);
+
+/* Energies of the current state (deterministic reductions). */
+int cem_energy(cem_ctx* ctx, cem_energy_t* out);
+
+/* Split original elements sorted by (step, element id).  The notch elements
+ * appear with step = -1 and G = 0.  Writes min(count, cap) records to the
+ * (optional, may be NULL) arrays and the total count to *n_split. */
+int cem_crack_state(cem_ctx* ctx, int64_t* n_split, int32_t* tet, int8_t* pattern,
+                    uint8_t* side, int64_t* step, double* G, int64_t cap);
+
+/* Copy a node field (CEM_FIELD_*) as n_nodes x 3 row-major doubles into out
+ * (capacity cap doubles; out may be NULL to query the size).  *n_nodes
+ * receives the current node count. */
+int cem_get_field(cem_ctx* ctx, int which, double* out, int64_t cap, int64_t* n_nodes);
+
+/* Sizes and time step. */
+int cem_info(cem_ctx* ctx, cem_info_t* out);
+
+/* Kernel timing.  cem_profile(ctx, 1) clears the counters and starts
+ * recording a pair of CUDA events (on the context's stream) around every
+ * launch of the hot-path kernels below; cem_profile(ctx, 0) stops.
+ * cem_profile_read copies, for the first n kernel classes, the summed device
+ * time in milliseconds and the number of timed launches (either array may be
+ * NULL) and, in *total_launches (may be NULL), the number of kernels of any
+ * kind the context launched since the last cem_profile(ctx, 1).  Timing adds
+ * two event records per launch; it does not change results. */
+#define CEM_KERNEL_PREDICT     0   /* u <- u + dt v + dt^2/2 a                      */
+#define CEM_KERNEL_STRAIN      1   /* per-element V * strain                        */
+#define CEM_KERNEL_EDGE_STRESS 2   /* fan sum, smoothed edge stress                 */
+#define CEM_KERNEL_FORCE       3   /* per-element nodal forces                      */
+#define CEM_KERNEL_NODE_UPDATE 4   /* nodal force gather, acceleration, velocity    */
+#define CEM_KERNEL_FRONT_G     5   /* energy release rates and split decisions      */
+#define CEM_KERNEL_SPLIT       6   /* the whole split sequence of one step          */
+#define CEM_KERNEL_COUNT       7
+int cem_profile(cem_ctx* ctx, int enable);
+int cem_profile_read(cem_ctx* ctx, double* ms, int64_t* launches, int n, int64_t* total_launches);
+
+/* Diagnostics (no counterpart in the paper): measured FP64 FMA throughput of
+ * `device` in FLOP/s (an FMA counts as two), timed with CUDA events on
+ * `stream`.  The FP64 step kernels are bounded by this rate on GB300.
+ * Allocates and frees a small device buffer itself. */
+int cem_probe_fp64_fma(int device, void* stream, double* flops_per_s);
+
+/* Release every device allocation and the context (NULL is accepted). */
+int cem_destroy(cem_ctx* ctx);
+
+/* Message of the last error on ctx ("" when none).  With ctx == NULL: the message
+ * of the last failed cem_mesh_create on this host thread. */
+const char* cem_last_error(const cem_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CEM_H */

@@ -268,6 +268,7 @@ class CEMOracle:
         ukeys, inv = np.unique(keys.ravel(), return_inverse=True)
         self.orig_edges = np.stack([ukeys // self.N0, ukeys % self.N0], axis=1)
         self.orig_t2e = inv.reshape(T0, 6)
+        self.orig_edge_keys = ukeys
         self.E0 = self.orig_edges.shape[0]
 
         # original face adjacency: face_nbr[t, f] = element across local face f or -1
@@ -525,7 +526,7 @@ class CEMOracle:
 
     def _orig_edge(self, x, y):
         i, j = (x, y) if x < y else (y, x)
-        k = int(np.searchsorted(self.orig_edges[:, 0] * self.N0 + self.orig_edges[:, 1], i * self.N0 + j))
+        k = int(np.searchsorted(self.orig_edge_keys, i * self.N0 + j))
         assert self.orig_edges[k, 0] == i and self.orig_edges[k, 1] == j
         return k
 

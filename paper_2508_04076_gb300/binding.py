@@ -1,0 +1,251 @@
+"""Thin ctypes binding of the CEM C ABI (include/cem.h).
+
+Argument marshalling only: every step of the computation runs in the
+library's CUDA kernels.  PyTorch supplies device memory (its caching
+allocator, installed as the library's allocator hook) and the stream.  There
+is no CPU fallback: if the shared library is missing or no GPU is present the
+calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+CEM_OK, CEM_EINVAL, CEM_ENOMEM, CEM_ECUDA = 0, -1, -2, -3
+CEM_ECAPACITY, CEM_ENONFINITE, CEM_ETIMEOUT, CEM_ESTATE = -4, -5, -6, -7
+CEM_FP64, CEM_MIXED = 0, 1
+FIELD = {"u": 0, "v": 1, "a": 2, "X": 3}
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_void_p)
+
+EXPORTED = ["cem_mesh_create", "cem_set_material", "cem_step", "cem_energy", "cem_crack_state",
+            "cem_get_field", "cem_info", "cem_profile", "cem_profile_read", "cem_probe_fp64_fma", "cem_destroy", "cem_last_error"]
+KERNELS = ["predict", "strain", "edge_stress", "force", "node_update", "front_G", "split"]
+
+
+class MeshDesc(C.Structure):
+    _fields_ = [
+        ("n_nodes", C.c_int64), ("n_tets", C.c_int64),
+        ("X", C.POINTER(C.c_double)), ("tets", C.POINTER(C.c_int32)),
+        ("n_tfaces", C.c_int64), ("tfaces", C.POINTER(C.c_int32)), ("tvec", C.POINTER(C.c_double)),
+        ("n_notch", C.c_int64), ("notch_tet", C.POINTER(C.c_int32)), ("notch_side", C.POINTER(C.c_uint8)),
+        ("precision", C.c_int32), ("dt", C.c_double), ("cfl_factor", C.c_double),
+        ("split_enabled", C.c_int32), ("split_capacity", C.c_int64),
+        ("stream", C.c_void_p), ("device", C.c_int32),
+        ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_user", C.c_void_p),
+    ]
+
+
+class Energy(C.Structure):
+    _fields_ = [("kinetic", C.c_double), ("strain", C.c_double), ("ext_work", C.c_double),
+                ("dissipated", C.c_double), ("modified", C.c_double), ("step", C.c_int64),
+                ("time", C.c_double), ("n_split", C.c_int64)]
+
+
+class Info(C.Structure):
+    _fields_ = [("n_nodes", C.c_int64), ("n_tets", C.c_int64), ("n_active_tets", C.c_int64),
+                ("n_edges", C.c_int64), ("n_candidates", C.c_int64), ("n_orig_edges", C.c_int64),
+                ("dt", C.c_double), ("h_min", C.c_double), ("device_bytes", C.c_int64)]
+
+
+_LIB = None
+
+
+def load_library(build: bool = True):
+    """Load libcem.so (building it first when asked and needed)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = _build.LIB
+    if build:
+        path = _build.build_library()
+    if not os.path.exists(path):
+        raise RuntimeError("libcem.so is not built; run paper_2508_04076_gb300.build.build_library()")
+    lib = C.CDLL(path)
+    P = C.c_void_p
+    lib.cem_mesh_create.argtypes = [C.POINTER(MeshDesc), C.POINTER(P)]
+    lib.cem_set_material.argtypes = [P, C.c_double, C.c_double, C.POINTER(C.c_double), C.c_int64,
+                                     C.POINTER(C.c_double), C.c_int64]
+    lib.cem_step.argtypes = [P, C.c_int64]
+    lib.cem_energy.argtypes = [P, C.POINTER(Energy)]
+    lib.cem_crack_state.argtypes = [P, C.POINTER(C.c_int64), C.POINTER(C.c_int32), C.POINTER(C.c_int8),
+                                    C.POINTER(C.c_uint8), C.POINTER(C.c_int64), C.POINTER(C.c_double), C.c_int64]
+    lib.cem_get_field.argtypes = [P, C.c_int, C.POINTER(C.c_double), C.c_int64, C.POINTER(C.c_int64)]
+    lib.cem_info.argtypes = [P, C.POINTER(Info)]
+    lib.cem_profile.argtypes = [P, C.c_int]
+    lib.cem_profile_read.argtypes = [P, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.c_int, C.POINTER(C.c_int64)]
+    lib.cem_probe_fp64_fma.argtypes = [C.c_int, C.c_void_p, C.POINTER(C.c_double)]
+    lib.cem_destroy.argtypes = [P]
+    lib.cem_last_error.argtypes = [P]
+    lib.cem_last_error.restype = C.c_char_p
+    for name in EXPORTED:
+        if name != "cem_last_error":
+            getattr(lib, name).restype = C.c_int
+    _LIB = lib
+    return lib
+
+
+def probe_fp64_fma(device=0, stream=0) -> float:
+    """Measured FP64 FMA throughput of the GPU in FLOP/s (FMA = 2 FLOP)."""
+    lib = load_library()
+    out = C.c_double()
+    rc = lib.cem_probe_fp64_fma(int(device), C.c_void_p(int(stream)), C.byref(out))
+    if rc != CEM_OK:
+        raise CEMError(rc, "FP64 probe failed")
+    return out.value
+
+
+class CEMError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("CEM error %d: %s" % (code, msg))
+        self.code = code
+
+
+def _ptr(a, ctype):
+    return a.ctypes.data_as(C.POINTER(ctype)) if a is not None and a.size else None
+
+
+class CEM:
+    """One simulation context on one GPU (C ABI: cem_mesh_create ... cem_destroy)."""
+
+    def __init__(self, X, tets, tfaces=None, tvec=None, notch_tet=None, notch_side=None, *,
+                 dt=0.0, cfl_factor=0.5, split_enabled=True, split_capacity=0, device=0,
+                 stream=None, torch_allocator=True):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("the CEM library needs a CUDA GPU; no CPU fallback exists")
+        self._lib = load_library()
+        self._torch = torch
+        self.device = int(device)
+        if stream is None:
+            stream = torch.cuda.current_stream(self.device).cuda_stream
+        self.stream = int(stream)
+        X = np.ascontiguousarray(X, dtype=np.float64).reshape(-1, 3)
+        tets = np.ascontiguousarray(tets, dtype=np.int32).reshape(-1, 4)
+        tfaces = np.ascontiguousarray(np.zeros((0, 3)) if tfaces is None else tfaces, dtype=np.int32).reshape(-1, 3)
+        tvec = np.ascontiguousarray(np.zeros((0, 3)) if tvec is None else tvec, dtype=np.float64).reshape(-1, 3)
+        notch_tet = np.ascontiguousarray([] if notch_tet is None else notch_tet, dtype=np.int32).ravel()
+        notch_side = np.ascontiguousarray([] if notch_side is None else notch_side, dtype=np.uint8).ravel()
+        self._keep = (X, tets, tfaces, tvec, notch_tet, notch_side)
+        d = MeshDesc()
+        d.n_nodes, d.n_tets = X.shape[0], tets.shape[0]
+        d.X, d.tets = _ptr(X, C.c_double), _ptr(tets, C.c_int32)
+        d.n_tfaces, d.tfaces, d.tvec = tfaces.shape[0], _ptr(tfaces, C.c_int32), _ptr(tvec, C.c_double)
+        d.n_notch, d.notch_tet, d.notch_side = notch_tet.size, _ptr(notch_tet, C.c_int32), _ptr(notch_side, C.c_uint8)
+        d.precision = CEM_FP64
+        d.dt, d.cfl_factor = float(dt), float(cfl_factor)
+        d.split_enabled, d.split_capacity = int(bool(split_enabled)), int(split_capacity)
+        d.stream, d.device = self.stream, self.device
+        if torch_allocator:
+            dev = self.device
+
+            def _alloc(nbytes, strm, user):
+                try:
+                    return torch.cuda.caching_allocator_alloc(int(nbytes), dev, int(strm or 0))
+                except Exception:
+                    return None
+
+            def _free(ptr, strm, user):
+                torch.cuda.caching_allocator_delete(int(ptr))
+
+            self._alloc_cb, self._free_cb = ALLOC_FN(_alloc), FREE_FN(_free)
+            d.alloc, d.free = self._alloc_cb, self._free_cb
+        else:
+            self._alloc_cb = self._free_cb = None
+            d.alloc, d.free = ALLOC_FN(), FREE_FN()
+        ctx = C.c_void_p()
+        with torch.cuda.device(self.device):
+            rc = self._lib.cem_mesh_create(C.byref(d), C.byref(ctx))
+        if rc != CEM_OK:
+            raise CEMError(rc, self._lib.cem_last_error(None).decode())
+        self._ctx = ctx
+
+    @classmethod
+    def from_workload(cls, w, **kw):
+        """Context for a cem_inputs.Workload with its material set."""
+        sim = cls(w.X, w.tets, w.tfaces, w.tvec, w.notch_tet, w.notch_side, **kw)
+        sim.set_material(w.rho, w.nu, w.E, w.Gc)
+        return sim
+
+    def _check(self, rc):
+        if rc != CEM_OK:
+            raise CEMError(rc, self._lib.cem_last_error(self._ctx).decode())
+
+    def set_material(self, rho, nu, E, Gc):
+        E = np.ascontiguousarray(np.atleast_1d(E), dtype=np.float64)
+        Gc = np.ascontiguousarray(np.atleast_1d(Gc), dtype=np.float64)
+        if E.size > 1 and np.all(E == E[0]):
+            E = E[:1].copy()
+        if Gc.size > 1 and np.all(Gc == Gc[0]):
+            Gc = Gc[:1].copy()
+        self._check(self._lib.cem_set_material(self._ctx, float(rho), float(nu), _ptr(E, C.c_double), E.size,
+                                               _ptr(Gc, C.c_double), Gc.size))
+
+    def step(self, n=1):
+        self._check(self._lib.cem_step(self._ctx, int(n)))
+
+    def energy(self) -> dict:
+        e = Energy()
+        self._check(self._lib.cem_energy(self._ctx, C.byref(e)))
+        return {k: getattr(e, k) for k, _ in Energy._fields_}
+
+    def info(self) -> dict:
+        i = Info()
+        self._check(self._lib.cem_info(self._ctx, C.byref(i)))
+        return {k: getattr(i, k) for k, _ in Info._fields_}
+
+    def field(self, which="u") -> np.ndarray:
+        n = C.c_int64()
+        self._check(self._lib.cem_get_field(self._ctx, FIELD[which], None, 0, C.byref(n)))
+        out = np.empty((n.value, 3), dtype=np.float64)
+        self._check(self._lib.cem_get_field(self._ctx, FIELD[which], _ptr(out, C.c_double), out.size, C.byref(n)))
+        return out
+
+    def crack_state(self):
+        """Split original elements sorted by (step, element): list of (tet, step, pattern, side, G)."""
+        n = C.c_int64()
+        self._check(self._lib.cem_crack_state(self._ctx, C.byref(n), None, None, None, None, None, 0))
+        m = n.value
+        tet = np.empty(m, np.int32)
+        pat = np.empty(m, np.int8)
+        side = np.empty(m, np.uint8)
+        step = np.empty(m, np.int64)
+        G = np.empty(m, np.float64)
+        self._check(self._lib.cem_crack_state(self._ctx, C.byref(n), _ptr(tet, C.c_int32), _ptr(pat, C.c_int8),
+                                              _ptr(side, C.c_uint8), _ptr(step, C.c_int64), _ptr(G, C.c_double), m))
+        return [(int(tet[i]), int(step[i]), int(pat[i]), int(side[i]), float(G[i])) for i in range(m)]
+
+    def profile(self, enable=True):
+        """Start (and clear) or stop per-kernel CUDA-event timing inside the library."""
+        self._check(self._lib.cem_profile(self._ctx, int(bool(enable))))
+
+    def profile_read(self):
+        """{kernel: (total_ms, launches)} and the total kernel launches since profile(True)."""
+        n = len(KERNELS)
+        ms = (C.c_double * n)()
+        cnt = (C.c_int64 * n)()
+        tot = C.c_int64()
+        self._check(self._lib.cem_profile_read(self._ctx, ms, cnt, n, C.byref(tot)))
+        return {k: (ms[i], cnt[i]) for i, k in enumerate(KERNELS)}, tot.value
+
+    def close(self):
+        if getattr(self, "_ctx", None) is not None and self._ctx.value:
+            self._lib.cem_destroy(self._ctx)
+            self._ctx = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

@@ -1,0 +1,696 @@
+// Host runtime of the CEM library: the C ABI declared in include/cem.h.
+//
+// cem_mesh_create builds the integer topology of the input mesh on the host
+// (node incidence, edges in ascending (i, j) order, element -> edge map, edge
+// fans, face adjacency), uploads it with the traction load, computes element
+// geometry on the device and applies the notch splits with the run-time split
+// path.  cem_step queues the five step kernels per step and, while crack-front
+// elements exist, the energy-release-rate kernel plus (on steps with splits)
+// the split sequence.
+#include "cem_common.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+static thread_local std::string g_create_error;
+
+int cem_fail(cem_ctx* c, int code, const std::string& msg) {
+    if (c) c->err = msg;
+    return code;
+}
+
+int cem_cuda_fail(cem_ctx* c, cudaError_t e, const char* what) {
+    return cem_fail(c, CEM_ECUDA, std::string("CUDA error '") + cudaGetErrorString(e) + "' in " + what);
+}
+
+int64_t cem_reduction_doubles();
+
+namespace {
+
+const int LE[6][2] = {{0, 1}, {0, 2}, {0, 3}, {1, 2}, {1, 3}, {2, 3}};
+
+template <class T>
+bool dalloc(cem_ctx* c, T*& p, int64_t n) {
+    size_t bytes = (size_t)std::max<int64_t>(n, 1) * sizeof(T);
+    bytes = (bytes + 255) & ~(size_t)255;
+    void* q = nullptr;
+    if (c->alloc) {
+        q = c->alloc(bytes, (void*)c->stream, c->alloc_user);
+    } else if (cudaMalloc(&q, bytes) != cudaSuccess) {
+        q = nullptr;
+    }
+    if (!q) return false;
+    c->allocs.push_back(q);
+    c->bytes += (int64_t)bytes;
+    p = (T*)q;
+    return true;
+}
+
+int select_device(cem_ctx* c) {
+    CEM_CK(c, cudaSetDevice(c->device));
+    return CEM_OK;
+}
+
+template <class T>
+int upload(cem_ctx* c, T* dst, const T* src, int64_t n) {
+    if (n <= 0) return CEM_OK;
+    CEM_CK(c, cudaMemcpyAsync(dst, src, (size_t)n * sizeof(T), cudaMemcpyHostToDevice, c->stream));
+    return CEM_OK;
+}
+
+int64_t next_pow2(int64_t x) {
+    int64_t p = 1;
+    while (p < x) p <<= 1;
+    return p;
+}
+
+struct HostTopo {
+    std::vector<int> inc_off, inc;          // node -> element*4+local, ascending
+    std::vector<int> e_off, e_nbr;          // node i -> sorted neighbours j > i (edge ids e_off[i] + r)
+    std::vector<int> t2e;                   // [6][T0]
+    std::vector<int> fan_off, fan;          // edge -> elements, ascending
+    std::vector<int> face_nbr;              // [4][T0]
+};
+
+int build_topology(cem_ctx* c, const std::vector<int>& conn, HostTopo& H) {
+    const int64_t N = c->N0, T = c->T0;
+    H.inc_off.assign(N + 1, 0);
+    for (int64_t t = 0; t < T; ++t)
+        for (int l = 0; l < 4; ++l) H.inc_off[conn[t * 4 + l] + 1]++;
+    for (int64_t i = 0; i < N; ++i) H.inc_off[i + 1] += H.inc_off[i];
+    H.inc.assign(4 * T, 0);
+    {
+        std::vector<int> cur(H.inc_off.begin(), H.inc_off.end() - 1);
+        for (int64_t t = 0; t < T; ++t)
+            for (int l = 0; l < 4; ++l) H.inc[cur[conn[t * 4 + l]]++] = (int)(t * 4 + l);
+    }
+    // edges: for each node the sorted distinct neighbours with larger id
+    H.e_off.assign(N + 1, 0);
+    H.e_nbr.clear();
+    H.e_nbr.reserve(T * 2);
+    std::vector<int> buf;
+    for (int64_t i = 0; i < N; ++i) {
+        buf.clear();
+        for (int q = H.inc_off[i]; q < H.inc_off[i + 1]; ++q) {
+            const int t = H.inc[q] >> 2;
+            for (int l = 0; l < 4; ++l) {
+                const int j = conn[(int64_t)t * 4 + l];
+                if (j > i) buf.push_back(j);
+            }
+        }
+        std::sort(buf.begin(), buf.end());
+        buf.erase(std::unique(buf.begin(), buf.end()), buf.end());
+        H.e_nbr.insert(H.e_nbr.end(), buf.begin(), buf.end());
+        H.e_off[i + 1] = (int)H.e_nbr.size();
+    }
+    c->E0 = (int64_t)H.e_nbr.size();
+    H.t2e.assign(6 * T, 0);
+    for (int64_t t = 0; t < T; ++t)
+        for (int l = 0; l < 6; ++l) {
+            int x = conn[t * 4 + LE[l][0]], y = conn[t * 4 + LE[l][1]];
+            if (x > y) std::swap(x, y);
+            auto b = H.e_nbr.begin() + H.e_off[x], e = H.e_nbr.begin() + H.e_off[x + 1];
+            auto it = std::lower_bound(b, e, y);
+            H.t2e[l * T + t] = H.e_off[x] + (int)(it - b);
+        }
+    // fans: elements of each edge in ascending element order
+    H.fan_off.assign(c->E0 + 1, 0);
+    for (int64_t t = 0; t < T; ++t)
+        for (int l = 0; l < 6; ++l) H.fan_off[H.t2e[l * T + t] + 1]++;
+    for (int64_t e = 0; e < c->E0; ++e) H.fan_off[e + 1] += H.fan_off[e];
+    H.fan.assign(6 * T, 0);
+    {
+        std::vector<int> cur(H.fan_off.begin(), H.fan_off.end() - 1);
+        for (int64_t t = 0; t < T; ++t)
+            for (int l = 0; l < 6; ++l) H.fan[cur[H.t2e[l * T + t]]++] = (int)t;
+    }
+    // face adjacency (local face f is opposite local node f)
+    H.face_nbr.assign(4 * T, -1);
+    for (int64_t t = 0; t < T; ++t)
+        for (int f = 0; f < 4; ++f) {
+            int fn[3], k = 0;
+            for (int l = 0; l < 4; ++l)
+                if (l != f) fn[k++] = conn[t * 4 + l];
+            int found = -1, nfound = 0;
+            for (int q = H.inc_off[fn[0]]; q < H.inc_off[fn[0] + 1]; ++q) {
+                const int s = H.inc[q] >> 2;
+                if (s == t) continue;
+                int hits = 0;
+                for (int l = 0; l < 4; ++l) {
+                    const int x = conn[(int64_t)s * 4 + l];
+                    hits += (x == fn[1]) + (x == fn[2]);
+                }
+                if (hits == 2) {
+                    found = s;
+                    ++nfound;
+                }
+            }
+            if (nfound > 1) return cem_fail(c, CEM_EINVAL, "non-manifold mesh: a face is shared by more than two elements");
+            H.face_nbr[f * T + t] = found;
+        }
+    return CEM_OK;
+}
+
+int sync_counts(cem_ctx* c) {
+    CEM_CK(c, cudaMemcpyAsync(c->hcount, c->dcount, CNT_COUNT * sizeof(long long), cudaMemcpyDeviceToHost,
+                              c->stream));
+    CEM_CK(c, cudaStreamSynchronize(c->stream));
+    return CEM_OK;
+}
+
+int create_impl(const cem_mesh_desc* d, cem_ctx* c) {
+    if (!d || d->n_nodes <= 0 || d->n_tets <= 0 || !d->X || !d->tets)
+        return cem_fail(c, CEM_EINVAL, "n_nodes, n_tets, X and tets are required");
+    if (d->n_nodes >= (1ll << 30) || d->n_tets >= (1ll << 28))
+        return cem_fail(c, CEM_EINVAL, "mesh too large for 32-bit ids");
+    if (d->n_tfaces < 0 || (d->n_tfaces > 0 && (!d->tfaces || !d->tvec)))
+        return cem_fail(c, CEM_EINVAL, "traction faces need tfaces and tvec");
+    if (d->n_notch < 0 || (d->n_notch > 0 && (!d->notch_tet || !d->notch_side)))
+        return cem_fail(c, CEM_EINVAL, "notch needs notch_tet and notch_side");
+    if (d->precision != CEM_FP64) return cem_fail(c, CEM_EINVAL, "only CEM_FP64 is available");
+    c->device = d->device;
+    c->stream = (cudaStream_t)d->stream;
+    c->alloc = d->alloc;
+    c->free_fn = d->free;
+    c->alloc_user = d->alloc_user;
+    c->dt_req = d->dt;
+    c->cfl = d->cfl_factor > 0 ? d->cfl_factor : 0.5;
+    c->split_enabled = d->split_enabled ? 1 : 0;
+    c->precision = d->precision;
+
+    const int64_t N0 = d->n_nodes, T0 = d->n_tets;
+    c->N0 = N0;
+    c->T0 = T0;
+    std::vector<int> conn(d->tets, d->tets + 4 * T0);
+    for (int64_t q = 0; q < 4 * T0; ++q)
+        if (conn[q] < 0 || conn[q] >= N0) return cem_fail(c, CEM_EINVAL, "element node id out of range");
+    // orientation: negative signed volume swaps local nodes 2 and 3
+    std::vector<char> swapped(T0, 0);
+    for (int64_t t = 0; t < T0; ++t) {
+        const double* X = d->X;
+        const int* n = &conn[t * 4];
+        for (int a = 0; a < 4; ++a)
+            for (int b = a + 1; b < 4; ++b)
+                if (n[a] == n[b]) return cem_fail(c, CEM_EINVAL, "element with a repeated node");
+        double e[3][3];
+        for (int r = 0; r < 3; ++r)
+            for (int k = 0; k < 3; ++k) e[r][k] = X[3 * n[r + 1] + k] - X[3 * n[0] + k];
+        const double V6 = e[0][0] * (e[1][1] * e[2][2] - e[1][2] * e[2][1]) -
+                          e[0][1] * (e[1][0] * e[2][2] - e[1][2] * e[2][0]) +
+                          e[0][2] * (e[1][0] * e[2][1] - e[1][1] * e[2][0]);
+        if (!(V6 != 0.0) || !std::isfinite(V6)) return cem_fail(c, CEM_EINVAL, "zero-volume element");
+        if (V6 < 0) {
+            std::swap(conn[t * 4 + 2], conn[t * 4 + 3]);
+            swapped[t] = 1;
+        }
+    }
+    HostTopo H;
+    if (int rc = build_topology(c, conn, H)) return rc;
+    const int64_t E0 = c->E0;
+
+    // notch list: validated, oriented, side masks normalised (local node 0 on side 0), ascending
+    std::vector<std::pair<int, int>> notch;
+    for (int64_t q = 0; q < d->n_notch; ++q) {
+        const int t = d->notch_tet[q];
+        int m = d->notch_side[q] & 15;
+        if (t < 0 || t >= T0) return cem_fail(c, CEM_EINVAL, "notch element id out of range");
+        if (m == 0 || m == 15 || d->notch_side[q] > 15) return cem_fail(c, CEM_EINVAL, "notch side mask must cut the element");
+        if (swapped[t]) m = (m & 3) | (((m >> 2) & 1) << 3) | (((m >> 3) & 1) << 2);
+        if (m & 1) m = (~m) & 15;
+        notch.push_back({t, m});
+    }
+    std::sort(notch.begin(), notch.end());
+    for (size_t q = 1; q < notch.size(); ++q)
+        if (notch[q].first == notch[q - 1].first) return cem_fail(c, CEM_EINVAL, "duplicate notch element");
+
+    // capacities
+    int64_t S_cap = d->split_capacity > 0 ? std::min<int64_t>(d->split_capacity, T0) : T0;
+    if ((int64_t)notch.size() > S_cap) return cem_fail(c, CEM_EINVAL, "split_capacity below the notch size");
+    if (!c->split_enabled) S_cap = (int64_t)notch.size();
+    c->S_cap = S_cap;
+    c->Tc = T0 + 6 * S_cap;
+    c->Nc = N0 + std::min<int64_t>(2 * E0, 8 * S_cap);
+    c->Ec = E0 + 22 * S_cap;
+    c->fan_cap = 6 * c->Tc + (6 * T0) / 4 + 65536;
+    c->inc_cap = 4 * c->Tc + T0 + 65536;
+    c->hash_cap = next_pow2(std::max<int64_t>(1024, 2 * 22 * S_cap));
+    const int64_t n_codes_cap = std::max<int64_t>(36 * S_cap, 1);
+    const int64_t lim = (1ll << 31) - 1;
+    if (c->Tc >= lim || c->Ec >= lim || c->Nc >= lim || c->fan_cap >= lim || c->inc_cap >= lim || 4 * c->Tc >= lim ||
+        n_codes_cap >= lim)
+        return cem_fail(c, CEM_EINVAL, "capacities exceed 32-bit indexing; lower split_capacity");
+    const int64_t big = std::max({c->Ec, c->Nc, T0});
+    const int64_t scan_max = std::max({2 * E0, c->Ec, c->Nc, T0, n_codes_cap});
+    c->scan_blocks_cap = cem_scan_blocks_needed(scan_max);
+
+    if (int rc = select_device(c)) return rc;
+    const int64_t Nc = c->Nc, Tc = c->Tc, Ec = c->Ec;
+    bool ok = true;
+    ok = ok && dalloc(c, c->X, 3 * Nc) && dalloc(c, c->u, 3 * Nc) && dalloc(c, c->v, 3 * Nc) && dalloc(c, c->a, 3 * Nc);
+    ok = ok && dalloc(c, c->fext, 3 * Nc) && dalloc(c, c->mass, Nc) && dalloc(c, c->minv, Nc);
+    ok = ok && dalloc(c, c->inc_off, Nc) && dalloc(c, c->inc_cnt, Nc);
+    ok = ok && dalloc(c, c->inc_pool, c->inc_cap) && dalloc(c, c->inc_pool2, c->inc_cap);
+    ok = ok && dalloc(c, c->conn, 4 * Tc) && dalloc(c, c->t2e, 6 * Tc) && dalloc(c, c->anc, Tc);
+    ok = ok && dalloc(c, c->active, Tc) && dalloc(c, c->Vg, 9 * Tc) && dalloc(c, c->vol, Tc);
+    ok = ok && dalloc(c, c->lam, Tc) && dalloc(c, c->mu, Tc) && dalloc(c, c->h, 6 * Tc) && dalloc(c, c->fp, 12 * Tc);
+    ok = ok && dalloc(c, c->fan_off, Ec) && dalloc(c, c->fan_cnt, Ec);
+    ok = ok && dalloc(c, c->fan_pool, c->fan_cap) && dalloc(c, c->fan_pool2, c->fan_cap);
+    ok = ok && dalloc(c, c->cl, Ec) && dalloc(c, c->cm, Ec) && dalloc(c, c->sumV, Ec) && dalloc(c, c->sig, 6 * Ec);
+    ok = ok && dalloc(c, c->face_nbr, 4 * T0) && dalloc(c, c->side, T0) && dalloc(c, c->split_step, T0);
+    ok = ok && dalloc(c, c->split_G, T0) && dalloc(c, c->Gc, T0) && dalloc(c, c->oe_n0, E0) && dalloc(c, c->oe_n1, E0);
+    ok = ok && dalloc(c, c->node_of_key, 2 * E0) && dalloc(c, c->cand_flag, T0) && dalloc(c, c->cand_list, T0);
+    ok = ok && dalloc(c, c->dec_mask, T0) && dalloc(c, c->dec_G, T0) && dalloc(c, c->split_list, T0);
+    ok = ok && dalloc(c, c->split_mask, T0) && dalloc(c, c->split_Gv, T0) && dalloc(c, c->ud_part, T0);
+    ok = ok && dalloc(c, c->Ud, 1);
+    ok = ok && dalloc(c, c->hkeys, c->hash_cap) && dalloc(c, c->hvals, c->hash_cap) && dalloc(c, c->hfirst, c->hash_cap);
+    ok = ok && dalloc(c, c->key_flag, 2 * E0) && dalloc(c, c->edge_flag, Ec) && dalloc(c, c->node_flag, Nc);
+    ok = ok && dalloc(c, c->code_flag, n_codes_cap) && dalloc(c, c->new_keys, 2 * E0) && dalloc(c, c->sub_off, T0);
+    ok = ok && dalloc(c, c->slot_of, n_codes_cap) && dalloc(c, c->code_rank, n_codes_cap);
+    ok = ok && dalloc(c, c->aff, big) && dalloc(c, c->aff_keep, big) && dalloc(c, c->aff_new, big) &&
+         dalloc(c, c->aff_off, big);
+    ok = ok && dalloc(c, c->add_cnt, big) && dalloc(c, c->cursor, big) && dalloc(c, c->scan_tmp, scan_max);
+    ok = ok && dalloc(c, c->scan_blocks, c->scan_blocks_cap);
+    ok = ok && dalloc(c, c->red_part, cem_reduction_doubles()) && dalloc(c, c->red_out, 8);
+    ok = ok && dalloc(c, c->dcount, CNT_COUNT);
+    if (!ok) return cem_fail(c, CEM_ENOMEM, "device allocation failed");
+    CEM_CK(c, cudaMallocHost((void**)&c->hcount, CNT_COUNT * sizeof(long long)));
+    CEM_CK(c, cudaMallocHost((void**)&c->hred, 8 * sizeof(double)));
+
+    cudaStream_t s = c->stream;
+    // zero / sentinel initialisation
+    CEM_CK(c, cudaMemsetAsync(c->u, 0, 3 * Nc * sizeof(double), s));
+    CEM_CK(c, cudaMemsetAsync(c->v, 0, 3 * Nc * sizeof(double), s));
+    CEM_CK(c, cudaMemsetAsync(c->a, 0, 3 * Nc * sizeof(double), s));
+    CEM_CK(c, cudaMemsetAsync(c->fext, 0, 3 * Nc * sizeof(double), s));
+    CEM_CK(c, cudaMemsetAsync(c->mass, 0, Nc * sizeof(double), s));
+    CEM_CK(c, cudaMemsetAsync(c->minv, 0, Nc * sizeof(double), s));
+    CEM_CK(c, cudaMemsetAsync(c->active, 0, Tc, s));
+    CEM_CK(c, cudaMemsetAsync(c->lam, 0, Tc * sizeof(double), s));
+    CEM_CK(c, cudaMemsetAsync(c->mu, 0, Tc * sizeof(double), s));
+    CEM_CK(c, cudaMemsetAsync(c->h, 0, 6 * Tc * sizeof(double), s));
+    CEM_CK(c, cudaMemsetAsync(c->fp, 0, 12 * Tc * sizeof(double), s));
+    CEM_CK(c, cudaMemsetAsync(c->sig, 0, 6 * Ec * sizeof(double), s));
+    CEM_CK(c, cudaMemsetAsync(c->side, 0, T0, s));
+    CEM_CK(c, cudaMemsetAsync(c->split_step, 0, T0 * sizeof(int), s));
+    CEM_CK(c, cudaMemsetAsync(c->split_G, 0, T0 * sizeof(double), s));
+    CEM_CK(c, cudaMemsetAsync(c->Gc, 0, T0 * sizeof(double), s));
+    CEM_CK(c, cudaMemsetAsync(c->node_of_key, 0xFF, 2 * E0 * sizeof(int), s));
+    CEM_CK(c, cudaMemsetAsync(c->cand_flag, 0, T0, s));
+    CEM_CK(c, cudaMemsetAsync(c->dec_mask, 0, T0, s));
+    CEM_CK(c, cudaMemsetAsync(c->Ud, 0, sizeof(double), s));
+    CEM_CK(c, cudaMemsetAsync(c->hkeys, 0xFF, c->hash_cap * sizeof(unsigned long long), s));
+    CEM_CK(c, cudaMemsetAsync(c->hvals, 0xFF, c->hash_cap * sizeof(int), s));
+    CEM_CK(c, cudaMemsetAsync(c->hfirst, 0x7F, c->hash_cap * sizeof(int), s));
+    CEM_CK(c, cudaMemsetAsync(c->key_flag, 0, 2 * E0, s));
+    CEM_CK(c, cudaMemsetAsync(c->edge_flag, 0, Ec, s));
+    CEM_CK(c, cudaMemsetAsync(c->node_flag, 0, Nc, s));
+    CEM_CK(c, cudaMemsetAsync(c->code_flag, 0, n_codes_cap, s));
+    CEM_CK(c, cudaMemsetAsync(c->add_cnt, 0, big * sizeof(int), s));
+    CEM_CK(c, cudaMemsetAsync(c->cursor, 0, big * sizeof(int), s));
+    CEM_CK(c, cudaMemsetAsync(c->fan_cnt, 0, Ec * sizeof(int), s));
+    CEM_CK(c, cudaMemsetAsync(c->fan_off, 0, Ec * sizeof(int), s));
+    CEM_CK(c, cudaMemsetAsync(c->inc_cnt, 0, Nc * sizeof(int), s));
+    CEM_CK(c, cudaMemsetAsync(c->inc_off, 0, Nc * sizeof(int), s));
+    CEM_CK(c, cudaMemsetAsync(c->dcount, 0, CNT_COUNT * sizeof(long long), s));
+
+    // uploads (structure of arrays)
+    {
+        std::vector<double> Xs(3 * N0);
+        for (int64_t i = 0; i < N0; ++i)
+            for (int k = 0; k < 3; ++k) Xs[k * N0 + i] = d->X[3 * i + k];
+        for (int k = 0; k < 3; ++k)
+            if (int rc = upload(c, c->X + k * Nc, Xs.data() + k * N0, N0)) return rc;
+        CEM_CK(c, cudaStreamSynchronize(s));
+    }
+    {
+        std::vector<int> cs(4 * T0);
+        for (int64_t t = 0; t < T0; ++t)
+            for (int l = 0; l < 4; ++l) cs[l * T0 + t] = conn[t * 4 + l];
+        for (int l = 0; l < 4; ++l)
+            if (int rc = upload(c, c->conn + l * Tc, cs.data() + l * T0, T0)) return rc;
+        for (int l = 0; l < 6; ++l)
+            if (int rc = upload(c, c->t2e + l * Tc, H.t2e.data() + l * T0, T0)) return rc;
+        std::vector<int> anc(T0);
+        std::iota(anc.begin(), anc.end(), 0);
+        if (int rc = upload(c, c->anc, anc.data(), T0)) return rc;
+        CEM_CK(c, cudaMemsetAsync(c->active, 1, T0, s));
+        if (int rc = upload(c, c->face_nbr, H.face_nbr.data(), 4 * T0)) return rc;
+        CEM_CK(c, cudaStreamSynchronize(s));
+    }
+    {
+        std::vector<int> fo(E0), fc(E0), n0(E0), n1(E0);
+        for (int64_t e = 0; e < E0; ++e) {
+            fo[e] = H.fan_off[e];
+            fc[e] = H.fan_off[e + 1] - H.fan_off[e];
+        }
+        for (int64_t i = 0; i < N0; ++i)
+            for (int q = H.e_off[i]; q < H.e_off[i + 1]; ++q) {
+                n0[q] = (int)i;
+                n1[q] = H.e_nbr[q];
+            }
+        if (int rc = upload(c, c->fan_off, fo.data(), E0)) return rc;
+        if (int rc = upload(c, c->fan_cnt, fc.data(), E0)) return rc;
+        if (int rc = upload(c, c->fan_pool, H.fan.data(), (int64_t)H.fan.size())) return rc;
+        if (int rc = upload(c, c->oe_n0, n0.data(), E0)) return rc;
+        if (int rc = upload(c, c->oe_n1, n1.data(), E0)) return rc;
+        c->fan_top = (int64_t)H.fan.size();
+        std::vector<int> io(N0), ic(N0);
+        for (int64_t i = 0; i < N0; ++i) {
+            io[i] = H.inc_off[i];
+            ic[i] = H.inc_off[i + 1] - H.inc_off[i];
+        }
+        if (int rc = upload(c, c->inc_off, io.data(), N0)) return rc;
+        if (int rc = upload(c, c->inc_cnt, ic.data(), N0)) return rc;
+        if (int rc = upload(c, c->inc_pool, H.inc.data(), (int64_t)H.inc.size())) return rc;
+        c->inc_top = (int64_t)H.inc.size();
+        CEM_CK(c, cudaStreamSynchronize(s));
+    }
+    {   // traction load, Eq. 12: t * A / 3 to each face node, in face order
+        std::vector<double> f(3 * N0, 0.0);
+        for (int64_t q = 0; q < d->n_tfaces; ++q) {
+            const int* fn = d->tfaces + 3 * q;
+            for (int k = 0; k < 3; ++k)
+                if (fn[k] < 0 || fn[k] >= N0) return cem_fail(c, CEM_EINVAL, "traction face node id out of range");
+            const double* P = d->X + 3 * fn[0];
+            const double* Q = d->X + 3 * fn[1];
+            const double* R = d->X + 3 * fn[2];
+            const double a[3] = {Q[0] - P[0], Q[1] - P[1], Q[2] - P[2]};
+            const double b[3] = {R[0] - P[0], R[1] - P[1], R[2] - P[2]};
+            const double cr[3] = {a[1] * b[2] - a[2] * b[1], a[2] * b[0] - a[0] * b[2], a[0] * b[1] - a[1] * b[0]};
+            const double A = 0.5 * std::sqrt(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]);
+            for (int k = 0; k < 3; ++k)
+                for (int r = 0; r < 3; ++r) f[k * N0 + fn[r]] += d->tvec[3 * q + k] * A / 3.0;
+        }
+        for (int k = 0; k < 3; ++k)
+            if (int rc = upload(c, c->fext + k * Nc, f.data() + k * N0, N0)) return rc;
+        CEM_CK(c, cudaStreamSynchronize(s));
+    }
+    c->N = N0;
+    c->T = T0;
+    c->E = E0;
+    c->n_active = T0;
+
+    // geometry of the input elements; h_min = min 3V / max face area
+    if (int rc = cem_launch_geometry(c, 0, T0, c->h)) return rc;
+    {
+        std::vector<double> hm(T0);
+        CEM_CK(c, cudaMemcpyAsync(hm.data(), c->h, T0 * sizeof(double), cudaMemcpyDeviceToHost, s));
+        CEM_CK(c, cudaStreamSynchronize(s));
+        c->h_min = *std::min_element(hm.begin(), hm.end());
+    }
+
+    // notch: the run-time split path with no energy booked
+    if (!notch.empty()) {
+        const int64_t S = (int64_t)notch.size();
+        std::vector<int> sl(S);
+        std::vector<uint8_t> sm(S);
+        std::vector<double> sg(S, 0.0);
+        for (int64_t q = 0; q < S; ++q) {
+            sl[q] = notch[q].first;
+            sm[q] = (uint8_t)notch[q].second;
+        }
+        if (int rc = upload(c, c->split_list, sl.data(), S)) return rc;
+        if (int rc = upload(c, c->split_mask, sm.data(), S)) return rc;
+        if (int rc = upload(c, c->split_Gv, sg.data(), S)) return rc;
+        if (int rc = cem_apply_splits(c, S, -1, 0)) return rc;
+    }
+    CEM_CK(c, cudaStreamSynchronize(s));
+    return CEM_OK;
+}
+
+// ---- kernel timing: event pairs on the context's stream, resolved after a sync
+cudaEvent_t ev_get(cem_ctx* c) {
+    cudaEvent_t e = nullptr;
+    if (!c->ev_pool.empty()) {
+        e = c->ev_pool.back();
+        c->ev_pool.pop_back();
+    } else if (cudaEventCreate(&e) != cudaSuccess) {
+        e = nullptr;
+    }
+    return e;
+}
+
+cudaEvent_t prof_begin(cem_ctx* c) {
+    if (!c->prof) return nullptr;
+    cudaEvent_t e = ev_get(c);
+    if (e) cudaEventRecord(e, c->stream);
+    return e;
+}
+
+void prof_end(cem_ctx* c, int id, cudaEvent_t a) {
+    if (!a) return;
+    cudaEvent_t b = ev_get(c);
+    if (!b) return;
+    cudaEventRecord(b, c->stream);
+    c->ev_pending.push_back({id, a, b});
+}
+
+int prof_resolve(cem_ctx* c) {
+    for (auto& r : c->ev_pending) {
+        CEM_CK(c, cudaEventSynchronize(r.b));
+        float ms = 0.f;
+        CEM_CK(c, cudaEventElapsedTime(&ms, r.a, r.b));
+        c->prof_ms[r.id] += ms;
+        c->prof_n[r.id] += 1;
+        c->ev_pool.push_back(r.a);
+        c->ev_pool.push_back(r.b);
+    }
+    c->ev_pending.clear();
+    return CEM_OK;
+}
+
+#define TIMED(c, id, expr)                 \
+    do {                                   \
+        cudaEvent_t ev_ = prof_begin(c);   \
+        int rc_ = (expr);                  \
+        prof_end(c, id, ev_);              \
+        if (rc_) return rc_;               \
+    } while (0)
+
+int run_step(cem_ctx* c) {
+    TIMED(c, CEM_KERNEL_PREDICT, cem_launch_predict(c));
+    TIMED(c, CEM_KERNEL_STRAIN, cem_launch_strain(c));
+    TIMED(c, CEM_KERNEL_EDGE_STRESS, cem_launch_edge_stress(c));
+    TIMED(c, CEM_KERNEL_FORCE, cem_launch_force(c));
+    TIMED(c, CEM_KERNEL_NODE_UPDATE, cem_launch_node_update(c, 0));
+    c->step += 1;
+    if (c->split_enabled && c->n_cand > 0) {
+        TIMED(c, CEM_KERNEL_FRONT_G, cem_launch_front_G(c));
+        int rc;
+        if ((rc = sync_counts(c))) return rc;
+        const int64_t S = c->hcount[CNT_SPLIT];
+        if (S > 0) {
+            if (c->n_split_all + S > c->S_cap)
+                return cem_fail(c, CEM_ECAPACITY, "split capacity exhausted; splits of this step not applied");
+            TIMED(c, CEM_KERNEL_SPLIT, cem_apply_splits(c, S, c->step, 1));
+        }
+    }
+    if (c->ev_pending.size() > 4096) return prof_resolve(c);
+    return CEM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int cem_mesh_create(const cem_mesh_desc* d, cem_ctx** out) {
+    if (!out) return CEM_EINVAL;
+    *out = nullptr;
+    cem_ctx* c = new cem_ctx();
+    int rc = create_impl(d, c);
+    if (rc != CEM_OK) {
+        g_create_error = c->err;
+        cem_destroy(c);
+        return rc;
+    }
+    *out = c;
+    return CEM_OK;
+}
+
+int cem_set_material(cem_ctx* c, double rho, double nu, const double* E, int64_t nE, const double* Gc, int64_t nGc) {
+    if (!c) return CEM_EINVAL;
+    if (c->step > 0) return cem_fail(c, CEM_ESTATE, "material can only be set before the first step");
+    if (!(rho > 0) || !(nu > -1.0 && nu < 0.5)) return cem_fail(c, CEM_EINVAL, "need rho > 0 and -1 < nu < 0.5");
+    if (!E || !Gc || (nE != 1 && nE != c->T0) || (nGc != 1 && nGc != c->T0))
+        return cem_fail(c, CEM_EINVAL, "E and Gc must have 1 or n_tets entries");
+    double Emax = 0.0;
+    for (int64_t q = 0; q < nE; ++q) {
+        if (!(E[q] > 0) || !std::isfinite(E[q])) return cem_fail(c, CEM_EINVAL, "E must be positive");
+        Emax = std::max(Emax, E[q]);
+    }
+    for (int64_t q = 0; q < nGc; ++q)
+        if (!(Gc[q] >= 0) || !std::isfinite(Gc[q])) return cem_fail(c, CEM_EINVAL, "Gc must be non-negative");
+    if (int rc = select_device(c)) return rc;
+    c->rho = rho;
+    c->nu = nu;
+    // the T0-sized dec_G and ud_part buffers stage E and Gc
+    if (int rc = upload(c, c->dec_G, E, nE)) return rc;
+    if (int rc = upload(c, c->ud_part, Gc, nGc)) return rc;
+    if (int rc = cem_launch_material(c, c->dec_G, (int)(nE == 1 ? 1 : 2), c->ud_part, (int)(nGc == 1 ? 1 : 2)))
+        return rc;
+    if (int rc = cem_launch_edge_coeffs(c, nullptr, 0)) return rc;
+    if (int rc = cem_launch_node_mass(c, nullptr, 0)) return rc;
+    const double lam = Emax * nu / ((1 + nu) * (1 - 2 * nu)), mu = Emax / (2 * (1 + nu));
+    const double c_d = std::sqrt((lam + 2 * mu) / rho);
+    c->dt = c->dt_req > 0 ? c->dt_req : c->cfl * c->h_min / (2.0 * c_d);
+    // a_0 = M^-1 (f_ext - f_int(u_0))
+    int rc;
+    if ((rc = cem_launch_strain(c)) || (rc = cem_launch_edge_stress(c)) || (rc = cem_launch_force(c)) ||
+        (rc = cem_launch_node_update(c, 1)))
+        return rc;
+    CEM_CK(c, cudaStreamSynchronize(c->stream));
+    c->material = true;
+    return CEM_OK;
+}
+
+int cem_step(cem_ctx* c, int64_t n) {
+    if (!c || n < 0) return CEM_EINVAL;
+    if (!c->material) return cem_fail(c, CEM_ESTATE, "cem_set_material must be called before cem_step");
+    if (int rc = select_device(c)) return rc;
+    for (int64_t q = 0; q < n; ++q)
+        if (int rc = run_step(c)) return rc;
+    if (int rc = cem_launch_check_finite(c)) return rc;
+    if (int rc = sync_counts(c)) return rc;
+    if (c->hcount[CNT_SCRATCH1]) return cem_fail(c, CEM_ENONFINITE, "non-finite displacement");
+    return prof_resolve(c);
+}
+
+int cem_profile(cem_ctx* c, int enable) {
+    if (!c) return CEM_EINVAL;
+    if (int rc = select_device(c)) return rc;
+    if (int rc = prof_resolve(c)) return rc;
+    if (enable) {
+        for (int q = 0; q < CEM_KERNEL_COUNT; ++q) {
+            c->prof_ms[q] = 0.0;
+            c->prof_n[q] = 0;
+        }
+        c->n_launch = 0;
+    }
+    c->prof = enable != 0;
+    return CEM_OK;
+}
+
+int cem_profile_read(cem_ctx* c, double* ms, int64_t* launches, int n, int64_t* total_launches) {
+    if (!c || n < 0) return CEM_EINVAL;
+    if (int rc = select_device(c)) return rc;
+    if (int rc = prof_resolve(c)) return rc;
+    for (int q = 0; q < n && q < CEM_KERNEL_COUNT; ++q) {
+        if (ms) ms[q] = c->prof_ms[q];
+        if (launches) launches[q] = c->prof_n[q];
+    }
+    if (total_launches) *total_launches = c->n_launch;
+    return CEM_OK;
+}
+
+int cem_energy(cem_ctx* c, cem_energy_t* out) {
+    if (!c || !out) return CEM_EINVAL;
+    if (!c->material) return cem_fail(c, CEM_ESTATE, "no material");
+    if (int rc = select_device(c)) return rc;
+    int rc;
+    if ((rc = cem_launch_strain(c)) || (rc = cem_launch_edge_stress(c))) return rc;
+    double r[4];
+    if ((rc = cem_energy_reduce(c, r))) return rc;
+    double Ud = 0.0;
+    CEM_CK(c, cudaMemcpy(&Ud, c->Ud, sizeof(double), cudaMemcpyDeviceToHost));
+    out->kinetic = r[0];
+    out->ext_work = r[1];
+    out->strain = r[3];
+    out->dissipated = Ud;
+    out->modified = r[0] + r[3] - r[1] - c->dt * c->dt / 8.0 * r[2];
+    out->step = c->step;
+    out->time = (double)c->step * c->dt;
+    out->n_split = c->n_split_run;
+    return CEM_OK;
+}
+
+int cem_crack_state(cem_ctx* c, int64_t* n_split, int32_t* tet, int8_t* pattern, uint8_t* side, int64_t* step,
+                    double* G, int64_t cap) {
+    if (!c || !n_split) return CEM_EINVAL;
+    if (int rc = select_device(c)) return rc;
+    const int64_t T0 = c->T0;
+    std::vector<uint8_t> sd(T0);
+    std::vector<int> st(T0);
+    std::vector<double> g(T0);
+    CEM_CK(c, cudaMemcpyAsync(sd.data(), c->side, T0, cudaMemcpyDeviceToHost, c->stream));
+    CEM_CK(c, cudaMemcpyAsync(st.data(), c->split_step, T0 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CEM_CK(c, cudaMemcpyAsync(g.data(), c->split_G, T0 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CEM_CK(c, cudaStreamSynchronize(c->stream));
+    std::vector<std::pair<int, int>> rec;
+    for (int64_t t = 0; t < T0; ++t)
+        if (sd[t]) rec.push_back({st[t], (int)t});
+    std::sort(rec.begin(), rec.end());
+    *n_split = (int64_t)rec.size();
+    const int64_t m = std::min<int64_t>(cap, (int64_t)rec.size());
+    for (int64_t q = 0; q < m; ++q) {
+        const int t = rec[q].second;
+        if (tet) tet[q] = t;
+        if (pattern) pattern[q] = (int8_t)(__builtin_popcount(sd[t]) == 2 ? CEM_PATTERN_I : CEM_PATTERN_II);
+        if (side) side[q] = sd[t];
+        if (step) step[q] = rec[q].first;
+        if (G) G[q] = g[t];
+    }
+    return CEM_OK;
+}
+
+int cem_get_field(cem_ctx* c, int which, double* out, int64_t cap, int64_t* n_nodes) {
+    if (!c) return CEM_EINVAL;
+    if (n_nodes) *n_nodes = c->N;
+    if (!out) return CEM_OK;
+    if (cap < 3 * c->N) return cem_fail(c, CEM_EINVAL, "output buffer too small");
+    const double* src = which == CEM_FIELD_U ? c->u : which == CEM_FIELD_V ? c->v : which == CEM_FIELD_A ? c->a
+                      : which == CEM_FIELD_X ? c->X : nullptr;
+    if (!src) return cem_fail(c, CEM_EINVAL, "unknown field");
+    if (int rc = select_device(c)) return rc;
+    std::vector<double> tmp(3 * c->N);
+    for (int k = 0; k < 3; ++k)
+        CEM_CK(c, cudaMemcpyAsync(tmp.data() + k * c->N, src + k * c->Nc, c->N * sizeof(double),
+                                  cudaMemcpyDeviceToHost, c->stream));
+    CEM_CK(c, cudaStreamSynchronize(c->stream));
+    for (int64_t i = 0; i < c->N; ++i)
+        for (int k = 0; k < 3; ++k) out[3 * i + k] = tmp[k * c->N + i];
+    return CEM_OK;
+}
+
+int cem_info(cem_ctx* c, cem_info_t* out) {
+    if (!c || !out) return CEM_EINVAL;
+    out->n_nodes = c->N;
+    out->n_tets = c->T;
+    out->n_active_tets = c->n_active;
+    out->n_edges = c->E;
+    out->n_candidates = c->n_cand;
+    out->n_orig_edges = c->E0;
+    out->dt = c->dt;
+    out->h_min = c->h_min;
+    out->device_bytes = c->bytes;
+    return CEM_OK;
+}
+
+int cem_destroy(cem_ctx* c) {
+    if (!c) return CEM_OK;
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->stream);
+    for (void* p : c->allocs) {
+        if (c->free_fn) c->free_fn(p, (void*)c->stream, c->alloc_user);
+        else cudaFree(p);
+    }
+    for (auto& r : c->ev_pending) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+    if (c->hcount) cudaFreeHost(c->hcount);
+    if (c->hred) cudaFreeHost(c->hred);
+    delete c;
+    return CEM_OK;
+}
+
+const char* cem_last_error(const cem_ctx* c) {
+    if (!c) return g_create_error.c_str();
+    return c->err.c_str();
+}
+
+}  // extern "C"

@@ -1,0 +1,165 @@
+// Internal declarations shared by the CEM library's translation units.
+//
+// Device data layout (structure of arrays, FP64 unless noted):
+//   nodes    X, u, v, a, f_ext : [3][Nc]      mass, minv : [Nc]
+//            node incidence    : inc_off/inc_cnt [Nc] into inc_pool (entries tet*4+local)
+//   elements conn : [4][Tc] i32   t2e : [6][Tc] i32 (edge id of local edge l)
+//            Vg   : [9][Tc]  V_j * grad N_a for a = 0,1,2 (grad N_3 = -sum)
+//            vol, lam, mu : [Tc]    active : [Tc] u8    anc : [Tc] i32 original ancestor
+//            h    : [6][Tc]  V_j * (Voigt strain of element j)       (step scratch)
+//            fp   : [12][Tc] per-element nodal forces times 6         (step scratch)
+//   edges    fan_off/fan_cnt [Ec] into fan_pool (element ids, ascending)
+//            cl = lambda_bar / sumV, cm = mu_bar / sumV, sumV : [Ec]
+//            sig  : [6][Ec]  smoothed edge stress                    (step output)
+//   cracks   (original elements only, [T0]) side mask, split step, G, Gc, face_nbr [4][T0]
+//            node_of_key [2*E0]: new node on original edge e attached to its
+//            smaller (side 0) or larger (side 1) endpoint, -1 if none.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/cem.h"
+
+#define CEM_LE0(l) (((l) < 3) ? 0 : (((l) < 5) ? 1 : 2))
+#define CEM_LE1(l) (((l) < 3) ? (l) + 1 : (((l) < 5) ? (l) - 1 : 3))
+
+// counters kept on the device (int64 slots of ctx->dcount)
+enum {
+    CNT_SPLIT = 0,     // elements splitting in this step
+    CNT_NEWNODE,       // new nodes in this split step
+    CNT_NEWSUB,        // new sub-elements in this split step
+    CNT_NEWEDGE,       // new edges in this split step
+    CNT_AFFECTED,      // affected edges / nodes (reused)
+    CNT_POOLNEED,      // pool entries needed by this update
+    CNT_CAND,          // crack-front elements
+    CNT_ERR,           // device-side error flags (bit mask)
+    CNT_SCRATCH0,
+    CNT_SCRATCH1,
+    CNT_COUNT
+};
+
+enum { DERR_HASH_FULL = 1, DERR_CAPACITY = 2 };
+
+struct cem_ctx {
+    // sizes: original, capacity, current (host mirrors of the device state)
+    int64_t N0 = 0, T0 = 0, E0 = 0;
+    int64_t Nc = 0, Tc = 0, Ec = 0;
+    int64_t N = 0, T = 0, E = 0;
+    int64_t n_cand = 0;
+    int64_t S_cap = 0;          // original elements that may be split (notch included)
+    int64_t n_split_all = 0;    // split original elements (notch included)
+    int64_t n_split_run = 0;    // split at run time
+    int64_t n_active = 0;
+    int64_t fan_cap = 0, fan_top = 0, inc_cap = 0, inc_top = 0;
+    int64_t hash_cap = 0;
+    int64_t scan_blocks_cap = 0;
+    int64_t bytes = 0;
+    double dt = 0.0, dt_req = 0.0, cfl = 0.5, h_min = 0.0;
+    double rho = 0.0, nu = 0.0;
+    bool material = false;
+    int64_t step = 0;
+    int split_enabled = 1;
+    int precision = CEM_FP64;
+    cudaStream_t stream = 0;
+    int device = 0;
+    cem_alloc_fn alloc = nullptr;
+    cem_free_fn free_fn = nullptr;
+    void* alloc_user = nullptr;
+    std::vector<void*> allocs;
+    std::string err;
+
+    // nodes
+    double *X = nullptr, *u = nullptr, *v = nullptr, *a = nullptr, *fext = nullptr;
+    double *mass = nullptr, *minv = nullptr;
+    int *inc_off = nullptr, *inc_cnt = nullptr, *inc_pool = nullptr, *inc_pool2 = nullptr;
+    // elements
+    int *conn = nullptr, *t2e = nullptr, *anc = nullptr;
+    uint8_t* active = nullptr;
+    double *Vg = nullptr, *vol = nullptr, *lam = nullptr, *mu = nullptr;
+    double *h = nullptr, *fp = nullptr;
+    // edges
+    int *fan_off = nullptr, *fan_cnt = nullptr, *fan_pool = nullptr, *fan_pool2 = nullptr;
+    double *cl = nullptr, *cm = nullptr, *sumV = nullptr, *sig = nullptr;
+    // cracks
+    int* face_nbr = nullptr;
+    uint8_t* side = nullptr;
+    int* split_step = nullptr;
+    double *split_G = nullptr, *Gc = nullptr;
+    int *oe_n0 = nullptr, *oe_n1 = nullptr;
+    int* node_of_key = nullptr;
+    uint8_t* cand_flag = nullptr;
+    int* cand_list = nullptr;
+    uint8_t* dec_mask = nullptr;
+    double* dec_G = nullptr;
+    int* split_list = nullptr;         // [T0] this step's split parents (ascending)
+    uint8_t* split_mask = nullptr;     // [T0]
+    double* split_Gv = nullptr;        // [T0]
+    double* ud_part = nullptr;         // [T0] Gc*area per split of this step
+    double* Ud = nullptr;              // [1]
+    // new-edge hash table
+    unsigned long long* hkeys = nullptr;
+    int *hvals = nullptr, *hfirst = nullptr;
+    // split-step scratch
+    uint8_t *key_flag = nullptr, *edge_flag = nullptr, *node_flag = nullptr, *code_flag = nullptr;
+    int *new_keys = nullptr, *sub_off = nullptr, *slot_of = nullptr, *code_rank = nullptr;
+    int *aff = nullptr, *aff_keep = nullptr, *aff_new = nullptr, *aff_off = nullptr;
+    int *add_cnt = nullptr, *cursor = nullptr;           // [max(Ec, Nc)]
+    int* scan_tmp = nullptr;                            // positions, [max scan length]
+    int* scan_blocks = nullptr;                         // block sums
+    // reductions
+    double* red_part = nullptr;   // block partials
+    double* red_out = nullptr;    // final values
+    long long* dcount = nullptr;  // device counters
+    long long* hcount = nullptr;  // pinned host mirror
+    double* hred = nullptr;       // pinned host mirror of red_out
+    // kernel timing and launch count
+    int64_t n_launch = 0;
+    bool prof = false;
+    double prof_ms[CEM_KERNEL_COUNT] = {};
+    int64_t prof_n[CEM_KERNEL_COUNT] = {};
+    std::vector<cudaEvent_t> ev_pool;
+    struct EvRec { int id; cudaEvent_t a, b; };
+    std::vector<EvRec> ev_pending;
+};
+
+static inline void cem_launched(cem_ctx* c, int k = 1) { c->n_launch += k; }
+
+// ---------------------------------------------------------------- error helpers
+int cem_fail(cem_ctx* c, int code, const std::string& msg);
+int cem_cuda_fail(cem_ctx* c, cudaError_t e, const char* what);
+#define CEM_CK(ctx, call)                                              \
+    do {                                                               \
+        cudaError_t e__ = (call);                                      \
+        if (e__ != cudaSuccess) return cem_cuda_fail((ctx), e__, #call); \
+    } while (0)
+
+static inline unsigned cem_grid(int64_t n, int bs) { return (unsigned)((n + bs - 1) / bs); }
+
+// ---------------------------------------------------------------- scan / compaction (cem_scan.cu)
+// Ordered compaction of a u8 flag array: idx[0..count) = ascending i with flags[i] != 0.
+// The count is written to dcount[slot].  Deterministic.
+int cem_compact_u8(cem_ctx* c, const uint8_t* flags, int64_t n, int* idx, int slot);
+// Exclusive scan of int values: out[i] = sum_{k<i} in[k]; total -> dcount[slot].
+int cem_scan_i32(cem_ctx* c, const int* in, int64_t n, int* out, int slot);
+int64_t cem_scan_blocks_needed(int64_t n);
+
+// ---------------------------------------------------------------- step kernels (cem_step.cu)
+int cem_launch_geometry(cem_ctx* c, int64_t t_begin, int64_t t_end, double* hbuf);
+int cem_launch_predict(cem_ctx* c);
+int cem_launch_strain(cem_ctx* c);
+int cem_launch_edge_stress(cem_ctx* c);
+int cem_launch_force(cem_ctx* c);
+int cem_launch_node_update(cem_ctx* c, int first);
+int cem_launch_edge_coeffs(cem_ctx* c, const int* list, int64_t n);     // list == NULL: all E
+int cem_launch_node_mass(cem_ctx* c, const int* list, int64_t n);       // list == NULL: all N
+int cem_launch_material(cem_ctx* c, const double* E_dev, int nE, const double* Gc_dev, int nGc);
+int cem_energy_reduce(cem_ctx* c, double out[4]);
+int cem_launch_check_finite(cem_ctx* c);
+
+// ---------------------------------------------------------------- crack path (cem_crack.cu)
+int cem_launch_front_G(cem_ctx* c);
+int cem_apply_splits(cem_ctx* c, int64_t S, int64_t step, int book_energy);

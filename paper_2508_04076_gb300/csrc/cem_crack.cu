@@ -1,0 +1,832 @@
+// Crack element method on the device (Sec. 3): energy release rates of the
+// crack-front elements and the element split.
+//
+// Front element: an unsplit original element sharing a face with a split
+// element whose crack cuts two of that face's edges.  On such a face the two
+// cut edges meet at the apex c (N2 of Fig. 5), a and b (N1, N3) are the other
+// face nodes and d (N4) the element's fourth node.  With G1 = mid(ac),
+// G2 = mid(cb), G3 = mid(ad), G4 = mid(bd), G6 = mid(cd):
+//   G_I  = 1/2 [ s(ad) |delta(ac).n_I| + s(bd) |delta(cb).n_I| ]    (Eq. 17)
+//   G_II = 1/2 s(cd) [ |delta(ac).n_II| + |delta(cb).n_II| ]         (Eq. 18)
+// where delta is the edge stretch of Eq. 16, n_I the normal of the planar
+// quadrilateral G1 G2 G4 G3 (Appendix I) and n_II that of the triangle
+// G1 G2 G6, both from reference coordinates, and s(k) = sigma_1 |p_1 . n| is
+// the projection of the principal stress vector of edge k's smoothed stress.
+// The element splits when max(G_I, G_II) over its front faces exceeds Gc.
+//
+// A split element leaves the computation and is replaced by sub-elements:
+// pattern I (two nodes per side) by two triangular prisms, pattern II (one
+// node cut off) by a corner tetrahedron and a prism; each prism is divided
+// into three tetrahedra (the remainder rule of Sec. 3).  Every cut original
+// edge carries one new node per side, shared by all elements cut through that
+// edge on that side.  New nodes, elements and edges are numbered in a
+// canonical order (ascending key / parent / first reference) with ordered
+// scans, so the topology is identical on every run.
+#include "cem_common.cuh"
+
+#include <climits>
+
+namespace {
+
+constexpr int BS = 256;
+constexpr unsigned long long HEMPTY = ~0ull;
+
+__device__ __forceinline__ int local_edge(int x, int y) {   // x != y local nodes
+    if (x > y) { int t = x; x = y; y = t; }
+    return x == 0 ? y - 1 : (x == 1 ? y + 1 : 5);
+}
+
+__device__ __forceinline__ void load3(const double* A, int64_t Nc, int i, double r[3]) {
+    r[0] = A[i];
+    r[1] = A[Nc + i];
+    r[2] = A[2 * Nc + i];
+}
+
+__device__ __forceinline__ void cross3(const double a[3], const double b[3], double r[3]) {
+    r[0] = a[1] * b[2] - a[2] * b[1];
+    r[1] = a[2] * b[0] - a[0] * b[2];
+    r[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+__device__ __forceinline__ double dot3(const double a[3], const double b[3]) {
+    return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
+}
+
+// Eq. 16: (u_i - u_j) if the edge is longer than in the reference, else 0.
+__device__ void stretch(const double* X, const double* u, int64_t Nc, int i, int j, double d[3]) {
+    double Xi[3], Xj[3], ui[3], uj[3];
+    load3(X, Nc, i, Xi);
+    load3(X, Nc, j, Xj);
+    load3(u, Nc, i, ui);
+    load3(u, Nc, j, uj);
+    double L2 = 0, l2 = 0;
+    for (int c = 0; c < 3; ++c) {
+        double dX = Xj[c] - Xi[c];
+        double dx = dX + (uj[c] - ui[c]);
+        L2 += dX * dX;
+        l2 += dx * dx;
+    }
+    const bool on = l2 > L2;
+    for (int c = 0; c < 3; ++c) d[c] = on ? ui[c] - uj[c] : 0.0;
+}
+
+// sigma_1 * sqrt(n^T P_1 n) of a Voigt stress: closed-form eigenvalues of a
+// symmetric 3x3 matrix (trigonometric solution of the characteristic cubic)
+// and the spectral projector P_1 = (A - l2)(A - l3) / ((l1 - l2)(l1 - l3)).
+// A repeated top eigenvalue (within 1e-12 of the largest magnitude) projects
+// onto its whole eigenspace.
+__device__ double principal_projection(const double s[6], const double n[3]) {
+    const double a11 = s[0], a22 = s[1], a33 = s[2], a12 = s[3], a23 = s[4], a13 = s[5];
+    const double q = (a11 + a22 + a33) * (1.0 / 3.0);
+    const double b11 = a11 - q, b22 = a22 - q, b33 = a33 - q;
+    const double p1 = a12 * a12 + a13 * a13 + a23 * a23;
+    const double p2 = b11 * b11 + b22 * b22 + b33 * b33 + 2.0 * p1;
+    const double tol = 1e-12;
+    double l1, l2, l3;
+    if (p2 <= 0.0) {
+        l1 = l2 = l3 = q;
+    } else {
+        const double p = sqrt(p2 * (1.0 / 6.0));
+        const double ip = 1.0 / p;
+        const double c11 = b11 * ip, c22 = b22 * ip, c33 = b33 * ip;
+        const double c12 = a12 * ip, c23 = a23 * ip, c13 = a13 * ip;
+        const double det = c11 * (c22 * c33 - c23 * c23) - c12 * (c12 * c33 - c23 * c13) + c13 * (c12 * c23 - c22 * c13);
+        double r = 0.5 * det;
+        r = fmin(1.0, fmax(-1.0, r));
+        const double phi = acos(r) * (1.0 / 3.0);
+        l1 = q + 2.0 * p * cos(phi);
+        l3 = q + 2.0 * p * cos(phi + 2.0943951023931957);
+        l2 = 3.0 * q - l1 - l3;
+    }
+    const double scale = fmax(fabs(l1), fmax(fabs(l2), fabs(l3)));
+    double proj2;
+    if (l1 - l3 <= tol * scale) {
+        proj2 = 1.0;
+    } else {
+        double w3[3] = {(a11 - l3) * n[0] + a12 * n[1] + a13 * n[2], a12 * n[0] + (a22 - l3) * n[1] + a23 * n[2],
+                        a13 * n[0] + a23 * n[1] + (a33 - l3) * n[2]};
+        if (l1 - l2 <= tol * scale) {
+            proj2 = dot3(n, w3) / (l1 - l3);
+        } else {
+            double w2[3] = {(a11 - l2) * n[0] + a12 * n[1] + a13 * n[2], a12 * n[0] + (a22 - l2) * n[1] + a23 * n[2],
+                            a13 * n[0] + a23 * n[1] + (a33 - l2) * n[2]};
+            proj2 = dot3(w2, w3) / ((l1 - l2) * (l1 - l3));
+        }
+        proj2 = fmin(1.0, fmax(0.0, proj2));
+    }
+    return l1 * sqrt(proj2);
+}
+
+__device__ __forceinline__ void load_sig(const double* sig, int64_t Ec, int k, double s[6]) {
+    for (int q = 0; q < 6; ++q) s[q] = sig[q * Ec + k];
+}
+
+__device__ __forceinline__ int normalize_side(int m) { return (m & 1) ? ((~m) & 15) : m; }
+
+__global__ void __launch_bounds__(BS) k_front_G(const int* __restrict__ cand_list, int n_cand,
+                                                const int* __restrict__ conn, const int* __restrict__ t2e, int64_t Tc,
+                                                const int* __restrict__ face_nbr, const uint8_t* __restrict__ side,
+                                                int64_t T0, const double* __restrict__ X, const double* __restrict__ u,
+                                                int64_t Nc, const double* __restrict__ sig, int64_t Ec,
+                                                const double* __restrict__ Gc, uint8_t* __restrict__ dec_mask,
+                                                double* __restrict__ dec_G) {
+    const int ci = blockIdx.x * BS + threadIdx.x;
+    if (ci >= n_cand) return;
+    const int t = cand_list[ci];
+    int tn[4];
+    for (int l = 0; l < 4; ++l) tn[l] = conn[l * Tc + t];
+    double bestG = -1.0 / 0.0;
+    int bestMask = 0;
+    for (int f = 0; f < 4; ++f) {
+        const int s = face_nbr[f * T0 + t];
+        if (s < 0) continue;
+        const int ms = side[s];
+        if (!ms) continue;
+        int sn[4];
+        for (int l = 0; l < 4; ++l) sn[l] = conn[l * Tc + s];
+        int fl[3], k = 0;
+        for (int l = 0; l < 4; ++l)
+            if (l != f) fl[k++] = l;
+        int bit[3];
+        for (int q = 0; q < 3; ++q) {
+            bit[q] = 0;
+            for (int r = 0; r < 4; ++r)
+                if (sn[r] == tn[fl[q]]) bit[q] = (ms >> r) & 1;
+        }
+        if (bit[0] == bit[1] && bit[1] == bit[2]) continue;   // no cut edge on this face
+        const int apex = (bit[0] == bit[1]) ? 2 : ((bit[0] == bit[2]) ? 1 : 0);
+        const int cl_ = fl[apex];
+        const int al = fl[apex == 0 ? 1 : 0];
+        const int bl = fl[apex == 2 ? 1 : 2];
+        const int dl = f;
+        const int a = tn[al], c = tn[cl_], b = tn[bl], d = tn[dl];
+        double d1[3], d2[3];
+        stretch(X, u, Nc, a, c, d1);
+        stretch(X, u, Nc, c, b, d2);
+        double Xa[3], Xb[3], Xc[3], Xd[3];
+        load3(X, Nc, a, Xa);
+        load3(X, Nc, b, Xb);
+        load3(X, Nc, c, Xc);
+        load3(X, Nc, d, Xd);
+        double ba[3] = {Xb[0] - Xa[0], Xb[1] - Xa[1], Xb[2] - Xa[2]};
+        double dc[3] = {Xd[0] - Xc[0], Xd[1] - Xc[1], Xd[2] - Xc[2]};
+        double da[3] = {Xd[0] - Xa[0], Xd[1] - Xa[1], Xd[2] - Xa[2]};
+        double nI[3], nII[3];
+        cross3(ba, dc, nI);
+        cross3(ba, da, nII);
+        const double iI = 1.0 / sqrt(dot3(nI, nI)), iII = 1.0 / sqrt(dot3(nII, nII));
+        for (int q = 0; q < 3; ++q) {
+            nI[q] *= iI;
+            nII[q] *= iII;
+        }
+        double sg[6];
+        load_sig(sig, Ec, t2e[local_edge(al, dl) * Tc + t], sg);
+        const double s_ad = principal_projection(sg, nI);
+        load_sig(sig, Ec, t2e[local_edge(bl, dl) * Tc + t], sg);
+        const double s_bd = principal_projection(sg, nI);
+        load_sig(sig, Ec, t2e[local_edge(cl_, dl) * Tc + t], sg);
+        const double s_cd = principal_projection(sg, nII);
+        const double GI = 0.5 * (s_ad * fabs(dot3(d1, nI)) + s_bd * fabs(dot3(d2, nI)));
+        const double GII = 0.5 * (s_cd * fabs(dot3(d1, nII)) + s_cd * fabs(dot3(d2, nII)));
+        double G;
+        int mask;
+        if (GI >= GII) {
+            G = GI;
+            mask = (1 << cl_) | (1 << dl);
+        } else {
+            G = GII;
+            mask = 1 << cl_;
+        }
+        if (G > bestG) {
+            bestG = G;
+            bestMask = normalize_side(mask);
+        }
+    }
+    dec_G[ci] = bestG;
+    dec_mask[ci] = (bestMask != 0 && bestG > Gc[t]) ? (uint8_t)bestMask : (uint8_t)0;
+}
+
+// ------------------------------------------------------------------ split list
+__global__ void k_gather_splits(const int* __restrict__ pos, const long long* __restrict__ count,
+                                const int* __restrict__ cand_list, const uint8_t* __restrict__ dec_mask,
+                                const double* __restrict__ dec_G, int* __restrict__ split_list,
+                                uint8_t* __restrict__ split_mask, double* __restrict__ split_G) {
+    const int i = blockIdx.x * BS + threadIdx.x;
+    if (i >= *count) return;
+    const int ci = pos[i];
+    split_list[i] = cand_list[ci];
+    split_mask[i] = dec_mask[ci];
+    split_G[i] = dec_G[ci];
+}
+
+// ------------------------------------------------------------------ new nodes
+__global__ void k_mark_keys(int S, const int* __restrict__ split_list, const uint8_t* __restrict__ split_mask,
+                            const int* __restrict__ t2e, int64_t Tc, const int* __restrict__ node_of_key,
+                            uint8_t* __restrict__ key_flag) {
+    const int i = blockIdx.x * BS + threadIdx.x;
+    if (i >= S) return;
+    const int p = split_list[i], m = split_mask[i];
+    for (int l = 0; l < 6; ++l) {
+        const int x = CEM_LE0(l), y = CEM_LE1(l);
+        if (((m >> x) ^ (m >> y)) & 1) {
+            const int e = t2e[l * Tc + p];
+            for (int s = 0; s < 2; ++s)
+                if (node_of_key[2 * e + s] < 0) key_flag[2 * e + s] = 1;
+        }
+    }
+}
+
+__global__ void k_create_nodes(const long long* __restrict__ count, const int* __restrict__ new_keys, int64_t N,
+                               int* __restrict__ node_of_key, uint8_t* __restrict__ key_flag,
+                               const int* __restrict__ oe_n0, const int* __restrict__ oe_n1, double* __restrict__ X,
+                               double* __restrict__ u, double* __restrict__ v, double* __restrict__ a,
+                               double* __restrict__ fext, double* __restrict__ mass, double* __restrict__ minv,
+                               int* __restrict__ inc_off, int* __restrict__ inc_cnt, int64_t Nc) {
+    const int i = blockIdx.x * BS + threadIdx.x;
+    if (i >= *count) return;
+    const int key = new_keys[i];
+    const int e = key >> 1;
+    const int64_t id = N + i;
+    node_of_key[key] = (int)id;
+    key_flag[key] = 0;
+    const int n0 = oe_n0[e], n1 = oe_n1[e];
+    for (int c = 0; c < 3; ++c) {
+        X[c * Nc + id] = 0.5 * (X[c * Nc + n0] + X[c * Nc + n1]);
+        u[c * Nc + id] = 0.5 * (u[c * Nc + n0] + u[c * Nc + n1]);
+        v[c * Nc + id] = 0.5 * (v[c * Nc + n0] + v[c * Nc + n1]);
+        a[c * Nc + id] = 0.5 * (a[c * Nc + n0] + a[c * Nc + n1]);
+        fext[c * Nc + id] = 0.0;
+    }
+    mass[id] = 0.0;
+    minv[id] = 0.0;
+    inc_off[id] = 0;
+    inc_cnt[id] = 0;
+}
+
+// ------------------------------------------------------------------ sub-elements
+__global__ void k_sub_count(int S, const uint8_t* __restrict__ split_mask, int* __restrict__ cnt) {
+    const int i = blockIdx.x * BS + threadIdx.x;
+    if (i >= S) return;
+    cnt[i] = (__popc((unsigned)split_mask[i]) == 2) ? 6 : 4;
+}
+
+struct SubCtx {
+    const int* pn;        // parent's 4 node ids
+    int p;
+    const int* t2e;
+    int64_t Tc;
+    const int* node_of_key;
+    // new node on the parent's edge between local nodes x and y, attached to x
+    __device__ int M(int x, int y) const {
+        const int e = t2e[local_edge(x, y) * Tc + p];
+        const int s = (pn[x] < pn[y]) ? 0 : 1;
+        return node_of_key[2 * e + s];
+    }
+};
+
+__device__ __forceinline__ void prism(int out[][4], int& k, const int A[3], const int B[3]) {
+    int t0[4] = {A[0], A[1], A[2], B[2]};
+    int t1[4] = {A[0], A[1], B[1], B[2]};
+    int t2[4] = {A[0], B[0], B[1], B[2]};
+    for (int q = 0; q < 4; ++q) {
+        out[k][q] = t0[q];
+        out[k + 1][q] = t1[q];
+        out[k + 2][q] = t2[q];
+    }
+    k += 3;
+}
+
+__global__ void k_create_subs(int S, int64_t T, const int* __restrict__ split_list,
+                              const uint8_t* __restrict__ split_mask, const double* __restrict__ split_Gv,
+                              const int* __restrict__ sub_off, int64_t step, int book, int* __restrict__ conn,
+                              const int* __restrict__ t2e, int* __restrict__ anc, uint8_t* __restrict__ active,
+                              double* __restrict__ Vg, double* __restrict__ vol, double* __restrict__ lam,
+                              double* __restrict__ mu, int64_t Tc, const int* __restrict__ node_of_key,
+                              const double* __restrict__ X, int64_t Nc, uint8_t* __restrict__ side,
+                              int* __restrict__ split_step, double* __restrict__ split_G,
+                              const double* __restrict__ Gc, uint8_t* __restrict__ cand_flag,
+                              double* __restrict__ ud_part) {
+    const int i = blockIdx.x * BS + threadIdx.x;
+    if (i >= S) return;
+    const int p = split_list[i];
+    const int m = split_mask[i];
+    int pn[4];
+    for (int l = 0; l < 4; ++l) pn[l] = conn[l * Tc + p];
+    SubCtx sc{pn, p, t2e, Tc, node_of_key};
+    int subs[6][4];
+    int ns = 0;
+    double area;
+    if (__popc((unsigned)m) == 2) {
+        int P[2], Q[2], kp = 0, kq = 0;
+        for (int l = 0; l < 4; ++l) {
+            if ((m >> l) & 1) Q[kq++] = l;
+            else P[kp++] = l;
+        }
+        for (int side_ = 0; side_ < 2; ++side_) {
+            const int* G = side_ ? Q : P;
+            const int* H = side_ ? P : Q;
+            int A[3] = {pn[G[0]], sc.M(G[0], H[0]), sc.M(G[0], H[1])};
+            int B[3] = {pn[G[1]], sc.M(G[1], H[0]), sc.M(G[1], H[1])};
+            prism(subs, ns, A, B);
+        }
+        double xp0[3], xp1[3], xq0[3], xq1[3];
+        load3(X, Nc, pn[P[0]], xp0);
+        load3(X, Nc, pn[P[1]], xp1);
+        load3(X, Nc, pn[Q[0]], xq0);
+        load3(X, Nc, pn[Q[1]], xq1);
+        double e1[3] = {xp1[0] - xp0[0], xp1[1] - xp0[1], xp1[2] - xp0[2]};
+        double e2[3] = {xq1[0] - xq0[0], xq1[1] - xq0[1], xq1[2] - xq0[2]};
+        double cr[3];
+        cross3(e1, e2, cr);
+        area = 0.25 * sqrt(dot3(cr, cr));
+    } else {
+        int ones = 0, lone1 = -1, lone0 = -1;
+        for (int l = 0; l < 4; ++l) {
+            if ((m >> l) & 1) { ++ones; lone1 = l; }
+            else if (lone0 < 0) lone0 = l;
+        }
+        const int lone = (ones == 1) ? lone1 : lone0;
+        int o[3], k = 0;
+        for (int l = 0; l < 4; ++l)
+            if (l != lone) o[k++] = l;
+        subs[0][0] = pn[lone];
+        subs[0][1] = sc.M(lone, o[0]);
+        subs[0][2] = sc.M(lone, o[1]);
+        subs[0][3] = sc.M(lone, o[2]);
+        ns = 1;
+        int A[3] = {sc.M(o[0], lone), sc.M(o[1], lone), sc.M(o[2], lone)};
+        int B[3] = {pn[o[0]], pn[o[1]], pn[o[2]]};
+        prism(subs, ns, A, B);
+        double x0[3], x1[3], x2[3];
+        load3(X, Nc, pn[o[0]], x0);
+        load3(X, Nc, pn[o[1]], x1);
+        load3(X, Nc, pn[o[2]], x2);
+        double e1[3] = {x1[0] - x0[0], x1[1] - x0[1], x1[2] - x0[2]};
+        double e2[3] = {x2[0] - x0[0], x2[1] - x0[1], x2[2] - x0[2]};
+        double cr[3];
+        cross3(e1, e2, cr);
+        area = 0.125 * sqrt(dot3(cr, cr));
+    }
+    const int64_t base = T + sub_off[i];
+    const double lp = lam[p], mp = mu[p];
+    for (int q = 0; q < ns; ++q) {
+        int* s = subs[q];
+        // orientation and geometry (V * grad N for local nodes 1..3)
+        double x0[3], e[3][3];
+        load3(X, Nc, s[0], x0);
+        for (int r = 1; r < 4; ++r) {
+            double xr[3];
+            load3(X, Nc, s[r], xr);
+            for (int c = 0; c < 3; ++c) e[r - 1][c] = xr[c] - x0[c];
+        }
+        double c23[3];
+        cross3(e[1], e[2], c23);
+        double V6 = dot3(e[0], c23);
+        if (V6 < 0.0) {
+            int tmp = s[2];
+            s[2] = s[3];
+            s[3] = tmp;
+            for (int c = 0; c < 3; ++c) {
+                double w = e[1][c];
+                e[1][c] = e[2][c];
+                e[2][c] = w;
+            }
+            cross3(e[1], e[2], c23);
+            V6 = dot3(e[0], c23);
+        }
+        double c31[3], c12[3];
+        cross3(e[2], e[0], c31);
+        cross3(e[0], e[1], c12);
+        const int64_t j = base + q;
+        const double s6 = 1.0 / 6.0;
+        for (int c = 0; c < 3; ++c) {
+            Vg[c * Tc + j] = c23[c] * s6;
+            Vg[(3 + c) * Tc + j] = c31[c] * s6;
+            Vg[(6 + c) * Tc + j] = c12[c] * s6;
+        }
+        vol[j] = V6 * s6;
+        for (int l = 0; l < 4; ++l) conn[l * Tc + j] = s[l];
+        anc[j] = p;
+        active[j] = 1;
+        lam[j] = lp;
+        mu[j] = mp;
+    }
+    active[p] = 0;
+    side[p] = (uint8_t)m;
+    split_step[p] = (int)step;
+    split_G[p] = split_Gv[i];
+    cand_flag[p] = 0;
+    ud_part[i] = book ? Gc[p] * area : 0.0;
+}
+
+__global__ void k_ud_sum(int S, const double* __restrict__ part, double* __restrict__ Ud) {
+    __shared__ double sh[BS];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < S; i += BS) s += part[i];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = BS / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *Ud += sh[0];
+}
+
+// ------------------------------------------------------------------ new edges
+__device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__global__ void k_sub_edges(int n_codes, int64_t T, int64_t N0, const int* __restrict__ conn,
+                            int* __restrict__ t2e, const int* __restrict__ anc, int64_t Tc,
+                            unsigned long long* __restrict__ hkeys, const int* __restrict__ hvals,
+                            int* __restrict__ hfirst, int64_t hmask, int* __restrict__ slot_of,
+                            long long* __restrict__ err) {
+    const int cidx = blockIdx.x * BS + threadIdx.x;
+    if (cidx >= n_codes) return;
+    const int q = cidx / 6, l = cidx % 6;
+    const int64_t s = T + q;
+    const int x = conn[CEM_LE0(l) * Tc + s], y = conn[CEM_LE1(l) * Tc + s];
+    if (x < N0 && y < N0) {   // both original nodes: an edge of the parent
+        const int p = anc[s];
+        int e = -1;
+        for (int l2 = 0; l2 < 6; ++l2) {
+            const int px = conn[CEM_LE0(l2) * Tc + p], py = conn[CEM_LE1(l2) * Tc + p];
+            if ((px == x && py == y) || (px == y && py == x)) e = t2e[l2 * Tc + p];
+        }
+        t2e[l * Tc + s] = e;
+        slot_of[cidx] = -1;
+        return;
+    }
+    const unsigned long long lo = (unsigned)min(x, y), hi = (unsigned)max(x, y);
+    const unsigned long long key = (lo << 32) | hi;
+    int64_t slot = (int64_t)(mix64(key) & (unsigned long long)hmask);
+    for (int64_t probe = 0;; ++probe) {
+        if (probe > hmask) {
+            atomicOr((unsigned long long*)err, (unsigned long long)DERR_HASH_FULL);
+            slot_of[cidx] = -1;
+            return;
+        }
+        unsigned long long k = hkeys[slot];
+        if (k == key) break;
+        if (k == HEMPTY) {
+            unsigned long long prev = atomicCAS(&hkeys[slot], HEMPTY, key);
+            if (prev == HEMPTY || prev == key) break;
+        }
+        slot = (slot + 1) & hmask;
+    }
+    slot_of[cidx] = (int)slot;
+    if (hvals[slot] < 0) atomicMin(&hfirst[slot], cidx);
+}
+
+__global__ void k_edge_owner(int n_codes, const int* __restrict__ slot_of, const int* __restrict__ hvals,
+                             const int* __restrict__ hfirst, uint8_t* __restrict__ code_flag) {
+    const int c = blockIdx.x * BS + threadIdx.x;
+    if (c >= n_codes) return;
+    const int s = slot_of[c];
+    code_flag[c] = (s >= 0 && hvals[s] < 0 && hfirst[s] == c) ? 1 : 0;
+}
+
+__global__ void k_edge_assign(const long long* __restrict__ count, const int* __restrict__ owners, int64_t E,
+                              const int* __restrict__ slot_of, int* __restrict__ hvals, int* __restrict__ hfirst,
+                              uint8_t* __restrict__ code_flag, int* __restrict__ fan_off, int* __restrict__ fan_cnt,
+                              double* __restrict__ cl, double* __restrict__ cm, double* __restrict__ sumV) {
+    const int r = blockIdx.x * BS + threadIdx.x;
+    if (r >= *count) return;
+    const int c = owners[r];
+    const int s = slot_of[c];
+    const int64_t e = E + r;
+    hvals[s] = (int)e;
+    hfirst[s] = INT_MAX;
+    code_flag[c] = 0;
+    fan_off[e] = 0;
+    fan_cnt[e] = 0;
+    cl[e] = 0.0;
+    cm[e] = 0.0;
+    sumV[e] = 0.0;
+}
+
+__global__ void k_edge_resolve(int n_codes, int64_t T, const int* __restrict__ slot_of,
+                               const int* __restrict__ hvals, int* __restrict__ t2e, int64_t Tc) {
+    const int c = blockIdx.x * BS + threadIdx.x;
+    if (c >= n_codes) return;
+    const int s = slot_of[c];
+    if (s < 0) return;
+    t2e[(c % 6) * Tc + T + c / 6] = hvals[s];
+}
+
+// ------------------------------------------------------------------ fans / incidence
+// kind 0: edge fans (entries: element id; 6 per element via t2e)
+// kind 1: node incidence (entries: element*4 + local; 4 per element via conn)
+__global__ void k_mark_affected(int kind, int S, const int* __restrict__ split_list, int NS, int64_t T,
+                                const int* __restrict__ t2e, const int* __restrict__ conn, int64_t Tc,
+                                uint8_t* __restrict__ flag, int* __restrict__ add_cnt) {
+    const int per = kind == 0 ? 6 : 4;
+    const int i = blockIdx.x * BS + threadIdx.x;
+    if (i < S * per) {
+        const int p = split_list[i / per], l = i % per;
+        const int x = kind == 0 ? t2e[l * Tc + p] : conn[l * Tc + p];
+        flag[x] = 1;
+        return;
+    }
+    const int c = i - S * per;
+    if (c >= NS * per) return;
+    const int64_t s = T + c / per;
+    const int l = c % per;
+    const int x = kind == 0 ? t2e[l * Tc + s] : conn[l * Tc + s];
+    flag[x] = 1;
+    atomicAdd(&add_cnt[x], 1);
+}
+
+__global__ void k_list_count(int kind, const long long* __restrict__ count, const int* __restrict__ aff,
+                             const int* __restrict__ off, const int* __restrict__ cnt, const int* __restrict__ pool,
+                             const uint8_t* __restrict__ active, const int* __restrict__ add_cnt,
+                             int* __restrict__ keep, int* __restrict__ need) {
+    const int i = blockIdx.x * BS + threadIdx.x;
+    if (i >= *count) return;
+    const int x = aff[i];
+    const int o = off[x], n = cnt[x];
+    int k = 0;
+    for (int q = 0; q < n; ++q) {
+        const int e = pool[o + q];
+        k += active[kind == 0 ? e : (e >> 2)] ? 1 : 0;
+    }
+    keep[i] = k;
+    need[i] = k + add_cnt[x];
+}
+
+__global__ void k_list_write(int kind, const long long* __restrict__ count, const int* __restrict__ aff,
+                             int64_t top, const int* __restrict__ aoff, const int* __restrict__ keep,
+                             const int* __restrict__ need, int* __restrict__ off, int* __restrict__ cnt,
+                             int* __restrict__ pool, const uint8_t* __restrict__ active, int* __restrict__ cursor) {
+    const int i = blockIdx.x * BS + threadIdx.x;
+    if (i >= *count) return;
+    const int x = aff[i];
+    const int o = off[x], n = cnt[x];
+    const int64_t no = top + aoff[i];
+    int w = 0;
+    for (int q = 0; q < n; ++q) {
+        const int e = pool[o + q];
+        if (active[kind == 0 ? e : (e >> 2)]) pool[no + w++] = e;
+    }
+    off[x] = (int)no;
+    cnt[x] = need[i];
+    cursor[x] = keep[i];
+}
+
+__global__ void k_list_append(int kind, int NS, int64_t T, const int* __restrict__ t2e,
+                              const int* __restrict__ conn, int64_t Tc, const int* __restrict__ off,
+                              int* __restrict__ pool, int* __restrict__ cursor) {
+    const int per = kind == 0 ? 6 : 4;
+    const int c = blockIdx.x * BS + threadIdx.x;
+    if (c >= NS * per) return;
+    const int64_t s = T + c / per;
+    const int l = c % per;
+    const int x = kind == 0 ? t2e[l * Tc + s] : conn[l * Tc + s];
+    const int pos = atomicAdd(&cursor[x], 1);
+    pool[off[x] + pos] = kind == 0 ? (int)s : (int)(s * 4 + l);
+}
+
+__global__ void k_list_finish(int kind, const long long* __restrict__ count, const int* __restrict__ aff,
+                              const int* __restrict__ keep, const int* __restrict__ off, const int* __restrict__ cnt,
+                              int* __restrict__ pool, uint8_t* __restrict__ flag, int* __restrict__ add_cnt,
+                              const double* __restrict__ vol, const double* __restrict__ lam,
+                              const double* __restrict__ mu, double* __restrict__ cl, double* __restrict__ cm,
+                              double* __restrict__ sumV, double rho, double* __restrict__ mass,
+                              double* __restrict__ minv) {
+    const int i = blockIdx.x * BS + threadIdx.x;
+    if (i >= *count) return;
+    const int x = aff[i];
+    const int o = off[x], n = cnt[x], k0 = keep[i];
+    // appended entries arrive in any order: sort them (ascending) after the kept ones
+    for (int q = k0 + 1; q < n; ++q) {
+        const int e = pool[o + q];
+        int r = q - 1;
+        while (r >= k0 && pool[o + r] > e) {
+            pool[o + r + 1] = pool[o + r];
+            --r;
+        }
+        pool[o + r + 1] = e;
+    }
+    flag[x] = 0;
+    add_cnt[x] = 0;
+    if (kind == 0) {
+        double sv = 0.0, sl = 0.0, sm = 0.0;
+        for (int q = 0; q < n; ++q) {
+            const int j = pool[o + q];
+            const double V = vol[j];
+            sv += V;
+            sl += V * lam[j];
+            sm += V * mu[j];
+        }
+        const double inv2 = sv > 0.0 ? 1.0 / (sv * sv) : 0.0;
+        cl[x] = sl * inv2;
+        cm[x] = sm * inv2;
+        sumV[x] = sv;
+    } else {
+        double m = 0.0;
+        for (int q = 0; q < n; ++q) m += rho * vol[pool[o + q] >> 2] * 0.25;
+        mass[x] = m;
+        minv[x] = m > 0.0 ? 1.0 / m : 0.0;
+    }
+}
+
+// defragmentation: copy every live list into the spare pool
+__global__ void k_defrag(int64_t n, const int* __restrict__ newoff, int* __restrict__ off,
+                         const int* __restrict__ cnt, const int* __restrict__ pool, int* __restrict__ pool2) {
+    const int64_t x = (int64_t)blockIdx.x * BS + threadIdx.x;
+    if (x >= n) return;
+    const int o = off[x], m = cnt[x], no = newoff[x];
+    for (int q = 0; q < m; ++q) pool2[no + q] = pool[o + q];
+    off[x] = no;
+}
+
+// ------------------------------------------------------------------ candidates
+__global__ void k_cand_mark(int S, const int* __restrict__ split_list, const uint8_t* __restrict__ split_mask,
+                            const int* __restrict__ face_nbr, int64_t T0, const uint8_t* __restrict__ side,
+                            uint8_t* __restrict__ cand_flag) {
+    const int i = blockIdx.x * BS + threadIdx.x;
+    if (i >= S) return;
+    const int p = split_list[i], m = split_mask[i];
+    for (int f = 0; f < 4; ++f) {
+        int b[3], k = 0;
+        for (int l = 0; l < 4; ++l)
+            if (l != f) b[k++] = (m >> l) & 1;
+        if (b[0] == b[1] && b[1] == b[2]) continue;
+        const int nb = face_nbr[f * T0 + p];
+        if (nb >= 0 && side[nb] == 0) cand_flag[nb] = 1;
+    }
+}
+
+int sync_counts(cem_ctx* c) {
+    CEM_CK(c, cudaMemcpyAsync(c->hcount, c->dcount, CNT_COUNT * sizeof(long long), cudaMemcpyDeviceToHost,
+                              c->stream));
+    CEM_CK(c, cudaStreamSynchronize(c->stream));
+    return CEM_OK;
+}
+
+// Rebuild every list of `kind` into the spare pool, compactly.
+int defrag(cem_ctx* c, int kind) {
+    const int64_t n = kind == 0 ? c->E : c->N;
+    int* off = kind == 0 ? c->fan_off : c->inc_off;
+    int* cnt = kind == 0 ? c->fan_cnt : c->inc_cnt;
+    int*& pool = kind == 0 ? c->fan_pool : c->inc_pool;
+    int*& pool2 = kind == 0 ? c->fan_pool2 : c->inc_pool2;
+    int rc = cem_scan_i32(c, cnt, n, c->scan_tmp, CNT_SCRATCH0);
+    if (rc) return rc;
+    k_defrag<<<cem_grid(n, BS), BS, 0, c->stream>>>(n, c->scan_tmp, off, cnt, pool, pool2);
+    cem_launched(c, 1);
+    CEM_CK(c, cudaGetLastError());
+    rc = sync_counts(c);
+    if (rc) return rc;
+    int* t = pool;
+    pool = pool2;
+    pool2 = t;
+    (kind == 0 ? c->fan_top : c->inc_top) = c->hcount[CNT_SCRATCH0];
+    return CEM_OK;
+}
+
+// Update the fan (kind 0) or incidence (kind 1) lists of every affected edge / node.
+int update_lists(cem_ctx* c, int kind, int S, int NS, int64_t n_items) {
+    const int per = kind == 0 ? 6 : 4;
+    uint8_t* flag = kind == 0 ? c->edge_flag : c->node_flag;
+    int* off = kind == 0 ? c->fan_off : c->inc_off;
+    int* cnt = kind == 0 ? c->fan_cnt : c->inc_cnt;
+    const int64_t nth = (int64_t)(S + NS) * per;
+    k_mark_affected<<<cem_grid(nth, BS), BS, 0, c->stream>>>(kind, S, c->split_list, NS, c->T, c->t2e, c->conn, c->Tc,
+                                                             flag, c->add_cnt);
+    cem_launched(c, 1);
+    CEM_CK(c, cudaGetLastError());
+    int rc = cem_compact_u8(c, flag, n_items, c->aff, CNT_AFFECTED);
+    if (rc) return rc;
+    const int64_t bound = nth;   // affected items never exceed the marks
+    int* pool = kind == 0 ? c->fan_pool : c->inc_pool;
+    k_list_count<<<cem_grid(bound, BS), BS, 0, c->stream>>>(kind, c->dcount + CNT_AFFECTED, c->aff, off, cnt, pool,
+                                                           c->active, c->add_cnt, c->aff_keep, c->aff_new);
+    cem_launched(c, 1);
+    CEM_CK(c, cudaGetLastError());
+    rc = sync_counts(c);
+    if (rc) return rc;
+    const int64_t n_aff = c->hcount[CNT_AFFECTED];
+    rc = cem_scan_i32(c, c->aff_new, n_aff, c->aff_off, CNT_POOLNEED);
+    if (rc) return rc;
+    rc = sync_counts(c);
+    if (rc) return rc;
+    const int64_t need = c->hcount[CNT_POOLNEED];
+    int64_t& top = kind == 0 ? c->fan_top : c->inc_top;
+    const int64_t cap = kind == 0 ? c->fan_cap : c->inc_cap;
+    if (top + need > cap) {
+        rc = defrag(c, kind);
+        if (rc) return rc;
+        if (top + need > cap) return cem_fail(c, CEM_ECAPACITY, "fan/incidence pool exhausted");
+    }
+    pool = kind == 0 ? c->fan_pool : c->inc_pool;
+    k_list_write<<<cem_grid(n_aff, BS), BS, 0, c->stream>>>(kind, c->dcount + CNT_AFFECTED, c->aff, top, c->aff_off,
+                                                           c->aff_keep, c->aff_new, off, cnt, pool, c->active,
+                                                           c->cursor);
+    k_list_append<<<cem_grid((int64_t)NS * per, BS), BS, 0, c->stream>>>(kind, NS, c->T, c->t2e, c->conn, c->Tc, off,
+                                                                        pool, c->cursor);
+    k_list_finish<<<cem_grid(n_aff, BS), BS, 0, c->stream>>>(kind, c->dcount + CNT_AFFECTED, c->aff, c->aff_keep, off,
+                                                            cnt, pool, flag, c->add_cnt, c->vol, c->lam, c->mu, c->cl,
+                                                            c->cm, c->sumV, c->rho, c->mass, c->minv);
+    cem_launched(c, 3);
+    CEM_CK(c, cudaGetLastError());
+    top += need;
+    return CEM_OK;
+}
+
+}  // namespace
+
+int cem_launch_front_G(cem_ctx* c) {
+    if (c->n_cand > 0) {
+        k_front_G<<<cem_grid(c->n_cand, BS), BS, 0, c->stream>>>(c->cand_list, (int)c->n_cand, c->conn, c->t2e, c->Tc,
+                                                                 c->face_nbr, c->side, c->T0, c->X, c->u, c->Nc, c->sig,
+                                                                 c->Ec, c->Gc, c->dec_mask, c->dec_G);
+        cem_launched(c, 1);
+        CEM_CK(c, cudaGetLastError());
+    }
+    int rc = cem_compact_u8(c, c->dec_mask, c->n_cand, c->scan_tmp, CNT_SPLIT);
+    if (rc) return rc;
+    if (c->n_cand > 0) {
+        k_gather_splits<<<cem_grid(c->n_cand, BS), BS, 0, c->stream>>>(c->scan_tmp, c->dcount + CNT_SPLIT, c->cand_list,
+                                                                       c->dec_mask, c->dec_G, c->split_list,
+                                                                       c->split_mask, c->split_Gv);
+        cem_launched(c, 1);
+        CEM_CK(c, cudaGetLastError());
+    }
+    return CEM_OK;
+}
+
+// Apply the S splits held in split_list / split_mask / split_Gv (ascending
+// element ids).  step is recorded with each split; book_energy adds Gc * area
+// to the dissipated energy.
+int cem_apply_splits(cem_ctx* c, int64_t S64, int64_t step, int book_energy) {
+    if (S64 <= 0) return CEM_OK;
+    const int S = (int)S64;
+    int rc;
+    // 1. new nodes: one per (cut original edge, side) not yet present
+    k_mark_keys<<<cem_grid(S, BS), BS, 0, c->stream>>>(S, c->split_list, c->split_mask, c->t2e, c->Tc, c->node_of_key,
+                                                       c->key_flag);
+    cem_launched(c, 1);
+    CEM_CK(c, cudaGetLastError());
+    if ((rc = cem_compact_u8(c, c->key_flag, 2 * c->E0, c->new_keys, CNT_NEWNODE))) return rc;
+    k_create_nodes<<<cem_grid(8 * (int64_t)S, BS), BS, 0, c->stream>>>(
+        c->dcount + CNT_NEWNODE, c->new_keys, c->N, c->node_of_key, c->key_flag, c->oe_n0, c->oe_n1, c->X, c->u, c->v,
+        c->a, c->fext, c->mass, c->minv, c->inc_off, c->inc_cnt, c->Nc);
+    cem_launched(c, 1);
+    CEM_CK(c, cudaGetLastError());
+    // 2. sub-elements, numbered by (parent, local sub index)
+    k_sub_count<<<cem_grid(S, BS), BS, 0, c->stream>>>(S, c->split_mask, c->aff_new);
+    cem_launched(c, 1);
+    CEM_CK(c, cudaGetLastError());
+    if ((rc = cem_scan_i32(c, c->aff_new, S, c->sub_off, CNT_NEWSUB))) return rc;
+    k_create_subs<<<cem_grid(S, BS), BS, 0, c->stream>>>(
+        S, c->T, c->split_list, c->split_mask, c->split_Gv, c->sub_off, step, book_energy, c->conn, c->t2e, c->anc,
+        c->active, c->Vg, c->vol, c->lam, c->mu, c->Tc, c->node_of_key, c->X, c->Nc, c->side, c->split_step,
+        c->split_G, c->Gc, c->cand_flag, c->ud_part);
+    k_ud_sum<<<1, BS, 0, c->stream>>>(S, c->ud_part, c->Ud);
+    cem_launched(c, 2);
+    CEM_CK(c, cudaGetLastError());
+    if ((rc = sync_counts(c))) return rc;
+    const int64_t NN = c->hcount[CNT_NEWNODE], NS = c->hcount[CNT_NEWSUB];
+    if (c->N + NN > c->Nc || c->T + NS > c->Tc) return cem_fail(c, CEM_ECAPACITY, "node/element capacity exhausted");
+    // 3. edges of the sub-elements: parent edges or (new) hashed node pairs
+    const int n_codes = (int)(6 * NS);
+    k_sub_edges<<<cem_grid(n_codes, BS), BS, 0, c->stream>>>(n_codes, c->T, c->N0, c->conn, c->t2e, c->anc, c->Tc,
+                                                             c->hkeys, c->hvals, c->hfirst, c->hash_cap - 1,
+                                                             c->slot_of, c->dcount + CNT_ERR);
+    k_edge_owner<<<cem_grid(n_codes, BS), BS, 0, c->stream>>>(n_codes, c->slot_of, c->hvals, c->hfirst, c->code_flag);
+    cem_launched(c, 2);
+    CEM_CK(c, cudaGetLastError());
+    if ((rc = cem_compact_u8(c, c->code_flag, n_codes, c->code_rank, CNT_NEWEDGE))) return rc;
+    k_edge_assign<<<cem_grid(n_codes, BS), BS, 0, c->stream>>>(c->dcount + CNT_NEWEDGE, c->code_rank, c->E, c->slot_of,
+                                                               c->hvals, c->hfirst, c->code_flag, c->fan_off,
+                                                               c->fan_cnt, c->cl, c->cm, c->sumV);
+    k_edge_resolve<<<cem_grid(n_codes, BS), BS, 0, c->stream>>>(n_codes, c->T, c->slot_of, c->hvals, c->t2e, c->Tc);
+    cem_launched(c, 2);
+    CEM_CK(c, cudaGetLastError());
+    if ((rc = sync_counts(c))) return rc;
+    if (c->hcount[CNT_ERR]) return cem_fail(c, CEM_ECAPACITY, "edge hash table full");
+    const int64_t NE = c->hcount[CNT_NEWEDGE];
+    if (c->E + NE > c->Ec) return cem_fail(c, CEM_ECAPACITY, "edge capacity exhausted");
+    // 4. fans of affected edges, incidence (and mass) of affected nodes
+    if ((rc = update_lists(c, 0, S, (int)NS, c->E + NE))) return rc;
+    if ((rc = update_lists(c, 1, S, (int)NS, c->N + NN))) return rc;
+    // 5. crack-front candidates
+    k_cand_mark<<<cem_grid(S, BS), BS, 0, c->stream>>>(S, c->split_list, c->split_mask, c->face_nbr, c->T0, c->side,
+                                                       c->cand_flag);
+    cem_launched(c, 1);
+    CEM_CK(c, cudaGetLastError());
+    if ((rc = cem_compact_u8(c, c->cand_flag, c->T0, c->cand_list, CNT_CAND))) return rc;
+    if ((rc = sync_counts(c))) return rc;
+    c->N += NN;
+    c->T += NS;
+    c->E += NE;
+    c->n_cand = c->hcount[CNT_CAND];
+    c->n_active += NS - S;
+    c->n_split_all += S;
+    if (book_energy) c->n_split_run += S;
+    return CEM_OK;
+}

@@ -1,0 +1,86 @@
+"""C-ABI checks that need no GPU: the library builds, loads, exports every
+symbol declared in include/cem.h, and rejects malformed input on the host."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    txt = open(os.path.join(ROOT, "include", "cem.h")).read()
+    return sorted(set(re.findall(r"^\s*(?:int|const char\*)\s+(cem_\w+)\s*\(", txt, re.M)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2508_04076_gb300 import load_library
+    return load_library()
+
+
+def test_exports_every_declared_symbol(lib):
+    names = _declared()
+    assert len(names) >= 11
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def _desc(X, tets, notch_tet=(), notch_side=(), precision=0):
+    from paper_2508_04076_gb300.binding import MeshDesc, ALLOC_FN, FREE_FN
+    X = np.ascontiguousarray(X, np.float64)
+    tets = np.ascontiguousarray(tets, np.int32)
+    nt = np.ascontiguousarray(notch_tet, np.int32)
+    ns = np.ascontiguousarray(notch_side, np.uint8)
+    d = MeshDesc()
+    d.n_nodes, d.n_tets = len(X), len(tets)
+    d.X = X.ctypes.data_as(C.POINTER(C.c_double))
+    d.tets = tets.ctypes.data_as(C.POINTER(C.c_int32))
+    d.n_notch = len(nt)
+    d.notch_tet = nt.ctypes.data_as(C.POINTER(C.c_int32)) if len(nt) else None
+    d.notch_side = ns.ctypes.data_as(C.POINTER(C.c_uint8)) if len(ns) else None
+    d.precision = precision
+    d.split_enabled = 1
+    d.alloc, d.free = ALLOC_FN(), FREE_FN()
+    return d, (X, tets, nt, ns)
+
+
+UNIT = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1.0]])
+
+
+@pytest.mark.parametrize("case,expect", [
+    ("node_out_of_range", "out of range"),
+    ("repeated_node", "repeated node"),
+    ("zero_volume", "zero-volume"),
+    ("bad_notch_mask", "side mask"),
+    ("notch_out_of_range", "out of range"),
+    ("bad_precision", "CEM_FP64"),
+])
+def test_host_validation_rejects(lib, case, expect):
+    X, tets, nt, ns, prec = UNIT, [[0, 1, 2, 3]], [], [], 0
+    if case == "node_out_of_range":
+        tets = [[0, 1, 2, 4]]
+    elif case == "repeated_node":
+        tets = [[0, 1, 1, 3]]
+    elif case == "zero_volume":
+        X = np.array([[0, 0, 0], [1, 0, 0], [2, 0, 0], [0, 0, 1.0]])
+    elif case == "bad_notch_mask":
+        nt, ns = [0], [15]
+    elif case == "notch_out_of_range":
+        nt, ns = [3], [1]
+    elif case == "bad_precision":
+        prec = 7
+    d, keep = _desc(X, tets, nt, ns, prec)
+    ctx = C.c_void_p()
+    rc = lib.cem_mesh_create(C.byref(d), C.byref(ctx))
+    assert rc == -1
+    assert not ctx.value
+    assert expect in lib.cem_last_error(None).decode()
+
+
+def test_null_arguments(lib):
+    assert lib.cem_mesh_create(None, None) == -1
+    assert lib.cem_destroy(None) == 0
+    assert lib.cem_step(None, 1) == -1
