@@ -71,7 +71,7 @@ def kernel_costs(T, E, N):
 def _args():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=300)
+    p.add_argument("--steps", type=int, default=19995)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", choices=["cem", "reference"], default="cem")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -88,7 +88,7 @@ def _peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clock/throttle samples every 200 ms while running."""
+    """nvidia-smi clock/throttle samples every 100 ms while running."""
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -96,7 +96,7 @@ class ClockSampler:
 
     def __init__(self, bus_id=None):
         self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
-        cmd = ["nvidia-smi", "--query-gpu=" + self.Q, "--format=csv,noheader,nounits", "-lms", "200"]
+        cmd = ["nvidia-smi", "--query-gpu=" + self.Q, "--format=csv,noheader,nounits", "-lms", "100"]
         if bus_id:
             cmd += ["-i", bus_id]
         try:
