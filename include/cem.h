@@ -194,6 +194,28 @@ int cem_profile_read(cem_ctx* ctx, double* ms, int64_t* launches, int n, int64_t
  * Allocates and frees a small device buffer itself. */
 int cem_probe_fp64_fma(int device, void* stream, double* flops_per_s);
 
+/* Nodal energy sums of caller-owned device arrays, with no allocation.  The
+ * paper has no counterpart: this is a library facility for callers that
+ * cannot call cudaMalloc, for example code whose device memory is entirely
+ * reserved by another allocator (a caching allocator holding the free memory
+ * makes a raw cudaMalloc fail) or code running under a fixed device-memory
+ * budget.  It computes, into out[0..2] (device memory, written on `stream`):
+ *   out[0] = 1/2 sum_i mass[i] |v_i|^2,  out[1] = sum_i f_ext_i . u_i,
+ *   out[2] = sum_i mass[i] |a_i|^2,
+ * the nodal terms of cem_energy.  u, v, a, fext are [3][ld] structure-of-
+ * arrays device arrays (component c of node i at c*ld + i), mass is [n_nodes].
+ * The block partial sums live in one fixed 96 KiB __device__ array per GPU
+ * (held by every GPU that loads the library until the process exits), which
+ * bounds n_nodes to 16,777,216: larger counts return CEM_ECAPACITY without
+ * touching the GPU.  Bad pointers or ld < n_nodes return CEM_EINVAL.  The
+ * first call on a device looks up that array's address (cudaGetSymbolAddress)
+ * with the device current; make that first call before any stream capture
+ * begins.  All calls on a device share the array: calls that overlap on the
+ * GPU race and give wrong sums.  Calls no cudaMalloc, cudaFree or allocating
+ * library routine. */
+int cem_node_energies_noalloc(const double* u, const double* v, const double* a, const double* mass,
+                              const double* fext, int64_t n_nodes, int64_t ld, double* out, void* stream);
+
 /* Release every device allocation and the context (NULL is accepted). */
 int cem_destroy(cem_ctx* ctx);
 
