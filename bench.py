@@ -75,6 +75,7 @@ def _args():
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", choices=["cem", "reference"], default="cem")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
     p.add_argument("--split-capacity", type=int, default=0,
                    help="max elements that may split (0: all); lower it to shrink device memory for profiling")
     p.add_argument("--cpu-baseline-worker", action="store_true", help=argparse.SUPPRESS)
@@ -220,7 +221,7 @@ def run_cem(a):
             dist.barrier()
 
     w = _workload()
-    sim = CEM.from_workload(w, device=dev, split_capacity=a.split_capacity)
+    sim = CEM.from_workload(w, device=dev, split_capacity=a.split_capacity, precision=a.precision)
     info0 = sim.info()
     sim.step(a.warmup)
     barrier()
@@ -289,7 +290,7 @@ def run_cem(a):
     # end to end through the public API with host buffers: create + material + K steps + read back
     barrier()
     t0 = time.perf_counter()
-    sim2 = CEM.from_workload(w, device=dev, split_capacity=a.split_capacity)
+    sim2 = CEM.from_workload(w, device=dev, split_capacity=a.split_capacity, precision=a.precision)
     sim2.step(a.steps)
     u = sim2.field("u")
     e2 = sim2.energy()

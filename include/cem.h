@@ -53,7 +53,8 @@ extern "C" {
 
 /* precision of the force evaluation */
 #define CEM_FP64   0        /* every quantity in FP64                                */
-#define CEM_MIXED  1        /* reserved for FP32 stresses/forces with FP64 state     */
+#define CEM_MIXED  1        /* FP32 element strains, edge stresses and element forces; */
+                            /* FP64 node state, integration, energies and G test      */
 
 /* fields for cem_get_field */
 #define CEM_FIELD_U 0       /* displacement u                                         */
@@ -86,7 +87,7 @@ typedef struct cem_mesh_desc {
     const int32_t* notch_tet;    /* K element ids, distinct                            */
     const uint8_t* notch_side;   /* K 4-bit masks over local nodes naming the two      */
                                  /* sides of the notch crack (not 0, not 15)           */
-    int32_t        precision;    /* CEM_FP64                                           */
+    int32_t        precision;    /* CEM_FP64 or CEM_MIXED                              */
     double         dt;           /* > 0: fixed step [s]; <= 0: cfl_factor * h_min /   */
                                  /* (2 c_d) (see cem_set_material)                     */
     double         cfl_factor;   /* used when dt <= 0; <= 0 means 0.5                  */

@@ -115,7 +115,7 @@ class CEM:
 
     def __init__(self, X, tets, tfaces=None, tvec=None, notch_tet=None, notch_side=None, *,
                  dt=0.0, cfl_factor=0.5, split_enabled=True, split_capacity=0, device=0,
-                 stream=None, torch_allocator=True):
+                 stream=None, torch_allocator=True, precision="fp64"):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("the CEM library needs a CUDA GPU; no CPU fallback exists")
@@ -137,7 +137,10 @@ class CEM:
         d.X, d.tets = _ptr(X, C.c_double), _ptr(tets, C.c_int32)
         d.n_tfaces, d.tfaces, d.tvec = tfaces.shape[0], _ptr(tfaces, C.c_int32), _ptr(tvec, C.c_double)
         d.n_notch, d.notch_tet, d.notch_side = notch_tet.size, _ptr(notch_tet, C.c_int32), _ptr(notch_side, C.c_uint8)
-        d.precision = CEM_FP64
+        if precision not in ("fp64", "mixed"):
+            raise ValueError("precision must be 'fp64' or 'mixed'")
+        d.precision = CEM_FP64 if precision == "fp64" else CEM_MIXED
+        self.precision = precision
         d.dt, d.cfl_factor = float(dt), float(cfl_factor)
         d.split_enabled, d.split_capacity = int(bool(split_enabled)), int(split_capacity)
         d.stream, d.device = self.stream, self.device

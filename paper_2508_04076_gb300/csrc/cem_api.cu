@@ -171,7 +171,8 @@ int create_impl(const cem_mesh_desc* d, cem_ctx* c) {
         return cem_fail(c, CEM_EINVAL, "traction faces need tfaces and tvec");
     if (d->n_notch < 0 || (d->n_notch > 0 && (!d->notch_tet || !d->notch_side)))
         return cem_fail(c, CEM_EINVAL, "notch needs notch_tet and notch_side");
-    if (d->precision != CEM_FP64) return cem_fail(c, CEM_EINVAL, "only CEM_FP64 is available");
+    if (d->precision != CEM_FP64 && d->precision != CEM_MIXED)
+        return cem_fail(c, CEM_EINVAL, "precision must be CEM_FP64 or CEM_MIXED");
     c->device = d->device;
     c->stream = (cudaStream_t)d->stream;
     c->alloc = d->alloc;
@@ -256,10 +257,17 @@ int create_impl(const cem_mesh_desc* d, cem_ctx* c) {
     ok = ok && dalloc(c, c->inc_pool, c->inc_cap) && dalloc(c, c->inc_pool2, c->inc_cap);
     ok = ok && dalloc(c, c->conn, 4 * Tc) && dalloc(c, c->t2e, 6 * Tc) && dalloc(c, c->anc, Tc);
     ok = ok && dalloc(c, c->active, Tc) && dalloc(c, c->Vg, 9 * Tc) && dalloc(c, c->vol, Tc);
-    ok = ok && dalloc(c, c->lam, Tc) && dalloc(c, c->mu, Tc) && dalloc(c, c->h, 6 * Tc) && dalloc(c, c->fp, 12 * Tc);
+    ok = ok && dalloc(c, c->lam, Tc) && dalloc(c, c->mu, Tc);
+    const bool mixed = c->precision == CEM_MIXED;
+    if (mixed)
+        ok = ok && dalloc(c, c->Vg32, 9 * Tc) && dalloc(c, c->h32, 8 * Tc) && dalloc(c, c->fp32, 16 * Tc) &&
+             dalloc(c, c->uhl, 8 * Nc) && dalloc(c, c->cl32, Ec) && dalloc(c, c->cm32, Ec) &&
+             dalloc(c, c->sig32, 8 * Ec);
+    else
+        ok = ok && dalloc(c, c->h, 6 * Tc) && dalloc(c, c->fp, 12 * Tc) && dalloc(c, c->sig, 6 * Ec);
     ok = ok && dalloc(c, c->fan_off, Ec) && dalloc(c, c->fan_cnt, Ec);
     ok = ok && dalloc(c, c->fan_pool, c->fan_cap) && dalloc(c, c->fan_pool2, c->fan_cap);
-    ok = ok && dalloc(c, c->cl, Ec) && dalloc(c, c->cm, Ec) && dalloc(c, c->sumV, Ec) && dalloc(c, c->sig, 6 * Ec);
+    ok = ok && dalloc(c, c->cl, Ec) && dalloc(c, c->cm, Ec) && dalloc(c, c->sumV, Ec);
     ok = ok && dalloc(c, c->face_nbr, 4 * T0) && dalloc(c, c->side, T0) && dalloc(c, c->split_step, T0);
     ok = ok && dalloc(c, c->split_G, T0) && dalloc(c, c->Gc, T0) && dalloc(c, c->oe_n0, E0) && dalloc(c, c->oe_n1, E0);
     ok = ok && dalloc(c, c->node_of_key, 2 * E0) && dalloc(c, c->cand_flag, T0) && dalloc(c, c->cand_list, T0);
@@ -291,9 +299,18 @@ int create_impl(const cem_mesh_desc* d, cem_ctx* c) {
     CEM_CK(c, cudaMemsetAsync(c->active, 0, Tc, s));
     CEM_CK(c, cudaMemsetAsync(c->lam, 0, Tc * sizeof(double), s));
     CEM_CK(c, cudaMemsetAsync(c->mu, 0, Tc * sizeof(double), s));
-    CEM_CK(c, cudaMemsetAsync(c->h, 0, 6 * Tc * sizeof(double), s));
-    CEM_CK(c, cudaMemsetAsync(c->fp, 0, 12 * Tc * sizeof(double), s));
-    CEM_CK(c, cudaMemsetAsync(c->sig, 0, 6 * Ec * sizeof(double), s));
+    if (mixed) {
+        CEM_CK(c, cudaMemsetAsync(c->h32, 0, 8 * Tc * sizeof(float), s));
+        CEM_CK(c, cudaMemsetAsync(c->fp32, 0, 16 * Tc * sizeof(float), s));
+        CEM_CK(c, cudaMemsetAsync(c->sig32, 0, 8 * Ec * sizeof(float), s));
+        CEM_CK(c, cudaMemsetAsync(c->uhl, 0, 8 * Nc * sizeof(float), s));
+        CEM_CK(c, cudaMemsetAsync(c->cl32, 0, Ec * sizeof(float), s));
+        CEM_CK(c, cudaMemsetAsync(c->cm32, 0, Ec * sizeof(float), s));
+    } else {
+        CEM_CK(c, cudaMemsetAsync(c->h, 0, 6 * Tc * sizeof(double), s));
+        CEM_CK(c, cudaMemsetAsync(c->fp, 0, 12 * Tc * sizeof(double), s));
+        CEM_CK(c, cudaMemsetAsync(c->sig, 0, 6 * Ec * sizeof(double), s));
+    }
     CEM_CK(c, cudaMemsetAsync(c->side, 0, T0, s));
     CEM_CK(c, cudaMemsetAsync(c->split_step, 0, T0 * sizeof(int), s));
     CEM_CK(c, cudaMemsetAsync(c->split_G, 0, T0 * sizeof(double), s));
@@ -395,10 +412,10 @@ int create_impl(const cem_mesh_desc* d, cem_ctx* c) {
     c->n_active = T0;
 
     // geometry of the input elements; h_min = min 3V / max face area
-    if (int rc = cem_launch_geometry(c, 0, T0, c->h)) return rc;
+    if (int rc = cem_launch_geometry(c, 0, T0, c->dec_G)) return rc;
     {
         std::vector<double> hm(T0);
-        CEM_CK(c, cudaMemcpyAsync(hm.data(), c->h, T0 * sizeof(double), cudaMemcpyDeviceToHost, s));
+        CEM_CK(c, cudaMemcpyAsync(hm.data(), c->dec_G, T0 * sizeof(double), cudaMemcpyDeviceToHost, s));
         CEM_CK(c, cudaStreamSynchronize(s));
         c->h_min = *std::min_element(hm.begin(), hm.end());
     }
@@ -591,7 +608,7 @@ int cem_energy(cem_ctx* c, cem_energy_t* out) {
     if (!c->material) return cem_fail(c, CEM_ESTATE, "no material");
     if (int rc = select_device(c)) return rc;
     int rc;
-    if ((rc = cem_launch_strain(c)) || (rc = cem_launch_edge_stress(c))) return rc;
+    if ((rc = cem_launch_split_u(c)) || (rc = cem_launch_strain(c)) || (rc = cem_launch_edge_stress(c))) return rc;
     double r[4];
     if ((rc = cem_energy_reduce(c, r))) return rc;
     double Ud = 0.0;

@@ -6,11 +6,14 @@
 //   elements conn : [4][Tc] i32   t2e : [6][Tc] i32 (edge id of local edge l)
 //            Vg   : [9][Tc]  V_j * grad N_a for a = 0,1,2 (grad N_3 = -sum)
 //            vol, lam, mu : [Tc]    active : [Tc] u8    anc : [Tc] i32 original ancestor
-//            h    : [6][Tc]  V_j * (Voigt strain of element j)       (step scratch)
-//            fp   : [12][Tc] per-element nodal forces times 6         (step scratch)
+//            h    : one 6-value record per element, V_j * (Voigt strain)  (step scratch)
+//            fp   : one record per element, its 4 nodal forces times 6  (step scratch)
 //   edges    fan_off/fan_cnt [Ec] into fan_pool (element ids, ascending)
 //            cl = lambda_bar / sumV, cm = mu_bar / sumV, sumV : [Ec]
-//            sig  : [6][Ec]  smoothed edge stress                    (step output)
+//            sig  : one 6-value record per edge, smoothed edge stress  (step output)
+//   mixed precision (CEM_MIXED) keeps FP32 copies Vg32, cl32, cm32 and FP32
+//   h32 / sig32 / fp32 records in place of the FP64 ones, plus uhl: per node
+//   8 floats (hi.xyz, lo.xyz, pad) with u = hi + lo, written by the predictor.
 //   cracks   (original elements only, [T0]) side mask, split step, G, Gc, face_nbr [4][T0]
 //            node_of_key [2*E0]: new node on original edge e attached to its
 //            smaller (side 0) or larger (side 1) endpoint, -1 if none.
@@ -81,9 +84,11 @@ struct cem_ctx {
     uint8_t* active = nullptr;
     double *Vg = nullptr, *vol = nullptr, *lam = nullptr, *mu = nullptr;
     double *h = nullptr, *fp = nullptr;
+    float *Vg32 = nullptr, *h32 = nullptr, *fp32 = nullptr, *uhl = nullptr;
     // edges
     int *fan_off = nullptr, *fan_cnt = nullptr, *fan_pool = nullptr, *fan_pool2 = nullptr;
     double *cl = nullptr, *cm = nullptr, *sumV = nullptr, *sig = nullptr;
+    float *cl32 = nullptr, *cm32 = nullptr, *sig32 = nullptr;
     // cracks
     int* face_nbr = nullptr;
     uint8_t* side = nullptr;
@@ -150,6 +155,7 @@ int64_t cem_scan_blocks_needed(int64_t n);
 // ---------------------------------------------------------------- step kernels (cem_step.cu)
 int cem_launch_geometry(cem_ctx* c, int64_t t_begin, int64_t t_end, double* hbuf);
 int cem_launch_predict(cem_ctx* c);
+int cem_launch_split_u(cem_ctx* c);   // mixed: refresh the FP32 hi/lo copy of u
 int cem_launch_strain(cem_ctx* c);
 int cem_launch_edge_stress(cem_ctx* c);
 int cem_launch_force(cem_ctx* c);

@@ -117,8 +117,13 @@ __device__ double principal_projection(const double s[6], const double n[3]) {
     return l1 * sqrt(proj2);
 }
 
-__device__ __forceinline__ void load_sig(const double* sig, int64_t Ec, int k, double s[6]) {
-    for (int q = 0; q < 6; ++q) s[q] = sig[q * Ec + k];
+// edge stress record k (FP64: 6 doubles; FP32: 8 floats, first 6 used), promoted to FP64
+__device__ __forceinline__ void load_sig(const double* sig64, const float* sig32, int k, double s[6]) {
+    if (sig32) {
+        for (int q = 0; q < 6; ++q) s[q] = (double)sig32[8 * (int64_t)k + q];
+    } else {
+        for (int q = 0; q < 6; ++q) s[q] = sig64[6 * (int64_t)k + q];
+    }
 }
 
 __device__ __forceinline__ int normalize_side(int m) { return (m & 1) ? ((~m) & 15) : m; }
@@ -127,7 +132,8 @@ __global__ void __launch_bounds__(BS) k_front_G(const int* __restrict__ cand_lis
                                                 const int* __restrict__ conn, const int* __restrict__ t2e, int64_t Tc,
                                                 const int* __restrict__ face_nbr, const uint8_t* __restrict__ side,
                                                 int64_t T0, const double* __restrict__ X, const double* __restrict__ u,
-                                                int64_t Nc, const double* __restrict__ sig, int64_t Ec,
+                                                int64_t Nc, const double* __restrict__ sig,
+                                                const float* __restrict__ sig32,
                                                 const double* __restrict__ Gc, uint8_t* __restrict__ dec_mask,
                                                 double* __restrict__ dec_G) {
     const int ci = blockIdx.x * BS + threadIdx.x;
@@ -180,11 +186,11 @@ __global__ void __launch_bounds__(BS) k_front_G(const int* __restrict__ cand_lis
             nII[q] *= iII;
         }
         double sg[6];
-        load_sig(sig, Ec, t2e[local_edge(al, dl) * Tc + t], sg);
+        load_sig(sig, sig32, t2e[local_edge(al, dl) * Tc + t], sg);
         const double s_ad = principal_projection(sg, nI);
-        load_sig(sig, Ec, t2e[local_edge(bl, dl) * Tc + t], sg);
+        load_sig(sig, sig32, t2e[local_edge(bl, dl) * Tc + t], sg);
         const double s_bd = principal_projection(sg, nI);
-        load_sig(sig, Ec, t2e[local_edge(cl_, dl) * Tc + t], sg);
+        load_sig(sig, sig32, t2e[local_edge(cl_, dl) * Tc + t], sg);
         const double s_cd = principal_projection(sg, nII);
         const double GI = 0.5 * (s_ad * fabs(dot3(d1, nI)) + s_bd * fabs(dot3(d2, nI)));
         const double GII = 0.5 * (s_cd * fabs(dot3(d1, nII)) + s_cd * fabs(dot3(d2, nII)));
@@ -300,7 +306,8 @@ __global__ void k_create_subs(int S, int64_t T, const int* __restrict__ split_li
                               const uint8_t* __restrict__ split_mask, const double* __restrict__ split_Gv,
                               const int* __restrict__ sub_off, int64_t step, int book, int* __restrict__ conn,
                               const int* __restrict__ t2e, int* __restrict__ anc, uint8_t* __restrict__ active,
-                              double* __restrict__ Vg, double* __restrict__ vol, double* __restrict__ lam,
+                              double* __restrict__ Vg, float* __restrict__ Vg32, double* __restrict__ vol,
+                              double* __restrict__ lam,
                               double* __restrict__ mu, int64_t Tc, const int* __restrict__ node_of_key,
                               const double* __restrict__ X, int64_t Nc, uint8_t* __restrict__ side,
                               int* __restrict__ split_step, double* __restrict__ split_G,
@@ -404,6 +411,12 @@ __global__ void k_create_subs(int S, int64_t T, const int* __restrict__ split_li
             Vg[(3 + c) * Tc + j] = c31[c] * s6;
             Vg[(6 + c) * Tc + j] = c12[c] * s6;
         }
+        if (Vg32)
+            for (int c = 0; c < 3; ++c) {
+                Vg32[c * Tc + j] = (float)(c23[c] * s6);
+                Vg32[(3 + c) * Tc + j] = (float)(c31[c] * s6);
+                Vg32[(6 + c) * Tc + j] = (float)(c12[c] * s6);
+            }
         vol[j] = V6 * s6;
         for (int l = 0; l < 4; ++l) conn[l * Tc + j] = s[l];
         anc[j] = p;
@@ -492,7 +505,8 @@ __global__ void k_edge_owner(int n_codes, const int* __restrict__ slot_of, const
 __global__ void k_edge_assign(const long long* __restrict__ count, const int* __restrict__ owners, int64_t E,
                               const int* __restrict__ slot_of, int* __restrict__ hvals, int* __restrict__ hfirst,
                               uint8_t* __restrict__ code_flag, int* __restrict__ fan_off, int* __restrict__ fan_cnt,
-                              double* __restrict__ cl, double* __restrict__ cm, double* __restrict__ sumV) {
+                              double* __restrict__ cl, double* __restrict__ cm, double* __restrict__ sumV,
+                              float* __restrict__ cl32, float* __restrict__ cm32) {
     const int r = blockIdx.x * BS + threadIdx.x;
     if (r >= *count) return;
     const int c = owners[r];
@@ -506,6 +520,10 @@ __global__ void k_edge_assign(const long long* __restrict__ count, const int* __
     cl[e] = 0.0;
     cm[e] = 0.0;
     sumV[e] = 0.0;
+    if (cl32) {
+        cl32[e] = 0.f;
+        cm32[e] = 0.f;
+    }
 }
 
 __global__ void k_edge_resolve(int n_codes, int64_t T, const int* __restrict__ slot_of,
@@ -594,8 +612,8 @@ __global__ void k_list_finish(int kind, const long long* __restrict__ count, con
                               int* __restrict__ pool, uint8_t* __restrict__ flag, int* __restrict__ add_cnt,
                               const double* __restrict__ vol, const double* __restrict__ lam,
                               const double* __restrict__ mu, double* __restrict__ cl, double* __restrict__ cm,
-                              double* __restrict__ sumV, double rho, double* __restrict__ mass,
-                              double* __restrict__ minv) {
+                              double* __restrict__ sumV, float* __restrict__ cl32, float* __restrict__ cm32,
+                              double rho, double* __restrict__ mass, double* __restrict__ minv) {
     const int i = blockIdx.x * BS + threadIdx.x;
     if (i >= *count) return;
     const int x = aff[i];
@@ -625,6 +643,10 @@ __global__ void k_list_finish(int kind, const long long* __restrict__ count, con
         cl[x] = sl * inv2;
         cm[x] = sm * inv2;
         sumV[x] = sv;
+        if (cl32) {
+            cl32[x] = (float)(sl * inv2);
+            cm32[x] = (float)(sm * inv2);
+        }
     } else {
         double m = 0.0;
         for (int q = 0; q < n; ++q) m += rho * vol[pool[o + q] >> 2] * 0.25;
@@ -730,7 +752,8 @@ int update_lists(cem_ctx* c, int kind, int S, int NS, int64_t n_items) {
                                                                         pool, c->cursor);
     k_list_finish<<<cem_grid(n_aff, BS), BS, 0, c->stream>>>(kind, c->dcount + CNT_AFFECTED, c->aff, c->aff_keep, off,
                                                             cnt, pool, flag, c->add_cnt, c->vol, c->lam, c->mu, c->cl,
-                                                            c->cm, c->sumV, c->rho, c->mass, c->minv);
+                                                            c->cm, c->sumV, c->cl32, c->cm32, c->rho, c->mass,
+                                                            c->minv);
     cem_launched(c, 3);
     CEM_CK(c, cudaGetLastError());
     top += need;
@@ -743,7 +766,7 @@ int cem_launch_front_G(cem_ctx* c) {
     if (c->n_cand > 0) {
         k_front_G<<<cem_grid(c->n_cand, BS), BS, 0, c->stream>>>(c->cand_list, (int)c->n_cand, c->conn, c->t2e, c->Tc,
                                                                  c->face_nbr, c->side, c->T0, c->X, c->u, c->Nc, c->sig,
-                                                                 c->Ec, c->Gc, c->dec_mask, c->dec_G);
+                                                                 c->sig32, c->Gc, c->dec_mask, c->dec_G);
         cem_launched(c, 1);
         CEM_CK(c, cudaGetLastError());
     }
@@ -784,7 +807,7 @@ int cem_apply_splits(cem_ctx* c, int64_t S64, int64_t step, int book_energy) {
     if ((rc = cem_scan_i32(c, c->aff_new, S, c->sub_off, CNT_NEWSUB))) return rc;
     k_create_subs<<<cem_grid(S, BS), BS, 0, c->stream>>>(
         S, c->T, c->split_list, c->split_mask, c->split_Gv, c->sub_off, step, book_energy, c->conn, c->t2e, c->anc,
-        c->active, c->Vg, c->vol, c->lam, c->mu, c->Tc, c->node_of_key, c->X, c->Nc, c->side, c->split_step,
+        c->active, c->Vg, c->Vg32, c->vol, c->lam, c->mu, c->Tc, c->node_of_key, c->X, c->Nc, c->side, c->split_step,
         c->split_G, c->Gc, c->cand_flag, c->ud_part);
     k_ud_sum<<<1, BS, 0, c->stream>>>(S, c->ud_part, c->Ud);
     cem_launched(c, 2);
@@ -803,7 +826,7 @@ int cem_apply_splits(cem_ctx* c, int64_t S64, int64_t step, int book_energy) {
     if ((rc = cem_compact_u8(c, c->code_flag, n_codes, c->code_rank, CNT_NEWEDGE))) return rc;
     k_edge_assign<<<cem_grid(n_codes, BS), BS, 0, c->stream>>>(c->dcount + CNT_NEWEDGE, c->code_rank, c->E, c->slot_of,
                                                                c->hvals, c->hfirst, c->code_flag, c->fan_off,
-                                                               c->fan_cnt, c->cl, c->cm, c->sumV);
+                                                               c->fan_cnt, c->cl, c->cm, c->sumV, c->cl32, c->cm32);
     k_edge_resolve<<<cem_grid(n_codes, BS), BS, 0, c->stream>>>(n_codes, c->T, c->slot_of, c->hvals, c->t2e, c->Tc);
     cem_launched(c, 2);
     CEM_CK(c, cudaGetLastError());

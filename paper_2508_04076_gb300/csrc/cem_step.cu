@@ -1,6 +1,6 @@
-// Explicit ES-T-FEM step kernels (Sec. 2.2) in FP64.
+// Explicit ES-T-FEM step kernels (Sec. 2.2).
 //
-// One step is five launches over structure-of-arrays data:
+// One step is five launches over the device mesh:
 //   predict      u <- u + dt v + dt^2/2 a                          (Eq. 15)
 //   strain       h_j = V_j * Voigt(sym grad u) of every element    (Eq. 6 per element)
 //   edge_stress  sigma_k = Dbar_k (sum_{j in fan(k)} h_j) / sumV_k  (Eqs. 4-6, Sec. 2.1)
@@ -12,16 +12,61 @@
 // (Vs_k = sumV_k / 6, Bbar_k = sum_j V_j B_j / sumV_k, each element lies in the
 // fan of exactly its six edges), which turns the edge-to-node scatter into two
 // gathers.  All sums run in a fixed order (ascending fan and incidence lists),
-// so results do not depend on scheduling.  FP64 is the scarce resource on
-// GB300, so the kernels keep the FP64 instruction count low: gradients are
-// stored premultiplied by the volume (V grad N_a is a cofactor / 6, no
-// division), 1/sumV is folded into the edge coefficients, and the 1/6 is
-// applied once per node.
+// so results do not depend on scheduling.
+//
+// Precision.  R = double: every quantity in FP64.  FP64 is the scarce unit on
+// GB300 (2 instructions per clock per SM), so these kernels keep the FP64
+// instruction count low: gradients are stored premultiplied by the volume
+// (V grad N_a is a cofactor / 6), 1/sumV is folded into the edge coefficients
+// and the 1/6 of the element stress average is applied once per node.
+// R = float (mixed): element strains, edge stresses and element forces in
+// FP32; node state u, v, a, masses, loads and the time integration in FP64.
+// The strain kernel differences an FP32 hi/lo split of u written by the
+// predictor, so displacement differences keep FP32 relative accuracy however
+// large u grows; the node gather sums FP32 forces with compensation.
+//
+// Layout of the gathered intermediates: one record per element / edge so a
+// gather touches one or two sectors: h and sigma hold 6 values per record
+// (FP64: 6 doubles = 48 B; FP32: padded to 8 floats = 32 B), element forces
+// hold 3 values per local node (FP64: 12 doubles per element; FP32: padded to
+// 4 floats per local node, 64 B per element).
 #include "cem_common.cuh"
 
 namespace {
 
 constexpr int BS = 256;
+
+template <class R> struct Rec;
+template <> struct Rec<double> {
+    static constexpr int S6 = 6;     // stride of a 6-value record
+    static constexpr int SF = 12;    // stride of an element force record
+    static constexpr int SL = 3;     // stride of one local node inside it
+    __device__ static void load6(const double* p, double v[6]) {
+        const double2 a = reinterpret_cast<const double2*>(p)[0];
+        const double2 b = reinterpret_cast<const double2*>(p)[1];
+        const double2 c = reinterpret_cast<const double2*>(p)[2];
+        v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y; v[4] = c.x; v[5] = c.y;
+    }
+    __device__ static void store6(double* p, const double v[6]) {
+        reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]);
+        reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
+        reinterpret_cast<double2*>(p)[2] = make_double2(v[4], v[5]);
+    }
+};
+template <> struct Rec<float> {
+    static constexpr int S6 = 8;
+    static constexpr int SF = 16;
+    static constexpr int SL = 4;
+    __device__ static void load6(const float* p, float v[6]) {
+        const float4 a = reinterpret_cast<const float4*>(p)[0];
+        const float2 b = reinterpret_cast<const float2*>(p)[2];
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y;
+    }
+    __device__ static void store6(float* p, const float v[6]) {
+        reinterpret_cast<float4*>(p)[0] = make_float4(v[0], v[1], v[2], v[3]);
+        reinterpret_cast<float4*>(p)[1] = make_float4(v[4], v[5], 0.f, 0.f);
+    }
+};
 
 // V * grad N_a for local nodes 1..3 (grad N_0 = -sum) and the signed volume.
 __device__ __forceinline__ void tet_cofactors(const double* X, int64_t Nc, const int n[4],
@@ -55,13 +100,16 @@ __device__ __forceinline__ double tri_area(const double* X, int64_t Nc, int p, i
 __global__ void __launch_bounds__(BS) k_geometry(const double* __restrict__ X, int64_t Nc,
                                                  const int* __restrict__ conn, int64_t Tc,
                                                  int64_t t0, int64_t t1, double* __restrict__ Vg,
-                                                 double* __restrict__ vol, double* __restrict__ hmin) {
+                                                 float* __restrict__ Vg32, double* __restrict__ vol,
+                                                 double* __restrict__ hmin) {
     int64_t j = t0 + (int64_t)blockIdx.x * BS + threadIdx.x;
     if (j >= t1) return;
     int n[4] = {conn[j], conn[Tc + j], conn[2 * Tc + j], conn[3 * Tc + j]};
     double g[9], V;
     tet_cofactors(X, Nc, n, g, &V);
     for (int q = 0; q < 9; ++q) Vg[q * Tc + j] = g[q];
+    if (Vg32)
+        for (int q = 0; q < 9; ++q) Vg32[q * Tc + j] = (float)g[q];
     vol[j] = V;
     if (hmin) {
         double am = tri_area(X, Nc, n[1], n[2], n[3]);
@@ -72,119 +120,206 @@ __global__ void __launch_bounds__(BS) k_geometry(const double* __restrict__ X, i
     }
 }
 
+// uhl (mixed only): per node 8 floats: hi.xyz, lo.xyz, 2 pad; u = hi + lo to ~48 bits.
 __global__ void __launch_bounds__(BS) k_predict(double* __restrict__ u, const double* __restrict__ v,
                                                 const double* __restrict__ a, int64_t Nc, int64_t N,
-                                                double dt, double hdt2) {
+                                                double dt, double hdt2, float* __restrict__ uhl) {
     int64_t i = (int64_t)blockIdx.x * BS + threadIdx.x;
     if (i >= N) return;
+    double un[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         int64_t k = c * Nc + i;
-        u[k] = u[k] + dt * v[k] + hdt2 * a[k];
+        un[c] = u[k] + dt * v[k] + hdt2 * a[k];
+        u[k] = un[c];
+    }
+    if (uhl) {
+        float hi[3], lo[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            hi[c] = (float)un[c];
+            lo[c] = (float)(un[c] - (double)hi[c]);
+        }
+        float4* p = reinterpret_cast<float4*>(uhl + 8 * i);
+        p[0] = make_float4(hi[0], hi[1], hi[2], lo[0]);
+        p[1] = make_float4(lo[1], lo[2], 0.f, 0.f);
     }
 }
 
-__global__ void __launch_bounds__(BS) k_strain(const double* __restrict__ u, int64_t Nc,
-                                               const int* __restrict__ conn, const double* __restrict__ Vg,
-                                               int64_t Tc, int64_t T, double* __restrict__ h) {
-    int64_t j = (int64_t)blockIdx.x * BS + threadIdx.x;
-    if (j >= T) return;
-    const int n0 = conn[j], n1 = conn[Tc + j], n2 = conn[2 * Tc + j], n3 = conn[3 * Tc + j];
-    double d[3][3];   // d[a][c] = u_{a+1,c} - u_{0,c}
+// Split u into FP32 hi/lo records (mixed mode, after set-up or a split).
+__global__ void __launch_bounds__(BS) k_split_u(const double* __restrict__ u, int64_t Nc, int64_t N,
+                                                float* __restrict__ uhl) {
+    int64_t i = (int64_t)blockIdx.x * BS + threadIdx.x;
+    if (i >= N) return;
+    float hi[3], lo[3];
+    for (int c = 0; c < 3; ++c) {
+        const double x = u[c * Nc + i];
+        hi[c] = (float)x;
+        lo[c] = (float)(x - (double)hi[c]);
+    }
+    float4* p = reinterpret_cast<float4*>(uhl + 8 * i);
+    p[0] = make_float4(hi[0], hi[1], hi[2], lo[0]);
+    p[1] = make_float4(lo[1], lo[2], 0.f, 0.f);
+}
+
+template <class R>
+__device__ __forceinline__ void node_disp_diff(const double* u, const float* uhl, int64_t Nc, const int n[4],
+                                               R d[3][3]);
+
+template <>
+__device__ __forceinline__ void node_disp_diff<double>(const double* u, const float*, int64_t Nc, const int n[4],
+                                                       double d[3][3]) {
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         const double* uc = u + c * Nc;
-        double u0 = uc[n0];
-        d[0][c] = uc[n1] - u0;
-        d[1][c] = uc[n2] - u0;
-        d[2][c] = uc[n3] - u0;
+        const double u0 = uc[n[0]];
+        d[0][c] = uc[n[1]] - u0;
+        d[1][c] = uc[n[2]] - u0;
+        d[2][c] = uc[n[3]] - u0;
     }
-    double g[3][3];
+}
+
+template <>
+__device__ __forceinline__ void node_disp_diff<float>(const double*, const float* uhl, int64_t, const int n[4],
+                                                      float d[3][3]) {
+    float hi[4][3], lo[4][3];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const float4* p = reinterpret_cast<const float4*>(uhl + 8 * (int64_t)n[q]);
+        const float4 a = p[0];
+        const float2 b = reinterpret_cast<const float2*>(p + 1)[0];
+        hi[q][0] = a.x; hi[q][1] = a.y; hi[q][2] = a.z;
+        lo[q][0] = a.w; lo[q][1] = b.x; lo[q][2] = b.y;
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) d[a][c] = (hi[a + 1][c] - hi[0][c]) + (lo[a + 1][c] - lo[0][c]);
+}
+
+template <class R>
+__global__ void __launch_bounds__(BS) k_strain(const double* __restrict__ u, const float* __restrict__ uhl,
+                                               int64_t Nc, const int* __restrict__ conn, const R* __restrict__ Vg,
+                                               int64_t Tc, int64_t T, R* __restrict__ h) {
+    int64_t j = (int64_t)blockIdx.x * BS + threadIdx.x;
+    if (j >= T) return;
+    const int n[4] = {conn[j], conn[Tc + j], conn[2 * Tc + j], conn[3 * Tc + j]};
+    R d[3][3];   // d[a][c] = u_{a+1,c} - u_{0,c}
+    node_disp_diff<R>(u, uhl, Nc, n, d);
+    R g[3][3];
 #pragma unroll
     for (int q = 0; q < 9; ++q) g[q / 3][q % 3] = Vg[q * Tc + j];
-    double F[3][3];   // F[c][e] = sum_a d[a][c] * g[a][e]  (V * du_c/dx_e)
+    R F[3][3];   // F[c][e] = sum_a d[a][c] * g[a][e]  (V * du_c/dx_e)
 #pragma unroll
     for (int c = 0; c < 3; ++c)
 #pragma unroll
         for (int e = 0; e < 3; ++e) F[c][e] = d[0][c] * g[0][e] + d[1][c] * g[1][e] + d[2][c] * g[2][e];
-    h[j] = F[0][0];
-    h[Tc + j] = F[1][1];
-    h[2 * Tc + j] = F[2][2];
-    h[3 * Tc + j] = F[0][1] + F[1][0];
-    h[4 * Tc + j] = F[1][2] + F[2][1];
-    h[5 * Tc + j] = F[0][2] + F[2][0];
+    const R out[6] = {F[0][0], F[1][1], F[2][2], F[0][1] + F[1][0], F[1][2] + F[2][1], F[0][2] + F[2][0]};
+    Rec<R>::store6(h + Rec<R>::S6 * j, out);
 }
 
-__global__ void __launch_bounds__(BS) k_edge_stress(const double* __restrict__ h, int64_t Tc,
-                                                    const int* __restrict__ fan_off, const int* __restrict__ fan_cnt,
-                                                    const int* __restrict__ fan_pool, const double* __restrict__ cl,
-                                                    const double* __restrict__ cm, int64_t Ec, int64_t E,
-                                                    double* __restrict__ sig) {
+template <class R>
+__global__ void __launch_bounds__(BS) k_edge_stress(const R* __restrict__ h, const int* __restrict__ fan_off,
+                                                    const int* __restrict__ fan_cnt, const int* __restrict__ fan_pool,
+                                                    const R* __restrict__ cl, const R* __restrict__ cm, int64_t E,
+                                                    R* __restrict__ sig) {
     int64_t k = (int64_t)blockIdx.x * BS + threadIdx.x;
     if (k >= E) return;
     const int off = fan_off[k], cnt = fan_cnt[k];
-    double H[6] = {0, 0, 0, 0, 0, 0};
+    R H[6] = {0, 0, 0, 0, 0, 0};
     for (int i = 0; i < cnt; ++i) {
         const int j = fan_pool[off + i];
+        R x[6];
+        Rec<R>::load6(h + Rec<R>::S6 * (int64_t)j, x);
 #pragma unroll
-        for (int q = 0; q < 6; ++q) H[q] += h[q * Tc + j];
+        for (int q = 0; q < 6; ++q) H[q] += x[q];
     }
-    const double tr = H[0] + H[1] + H[2];
-    const double l = cl[k] * tr, m = cm[k], m2 = m + m;
-    sig[k] = m2 * H[0] + l;
-    sig[Ec + k] = m2 * H[1] + l;
-    sig[2 * Ec + k] = m2 * H[2] + l;
-    sig[3 * Ec + k] = m * H[3];
-    sig[4 * Ec + k] = m * H[4];
-    sig[5 * Ec + k] = m * H[5];
+    const R tr = H[0] + H[1] + H[2];
+    const R l = cl[k] * tr, m = cm[k], m2 = m + m;
+    const R s[6] = {m2 * H[0] + l, m2 * H[1] + l, m2 * H[2] + l, m * H[3], m * H[4], m * H[5]};
+    Rec<R>::store6(sig + Rec<R>::S6 * k, s);
 }
 
-__global__ void __launch_bounds__(BS) k_force(const double* __restrict__ sig, int64_t Ec,
-                                              const int* __restrict__ t2e, const double* __restrict__ Vg,
-                                              int64_t Tc, int64_t T, double* __restrict__ fp) {
+template <class R>
+__global__ void __launch_bounds__(BS) k_force(const R* __restrict__ sig, const int* __restrict__ t2e,
+                                              const R* __restrict__ Vg, int64_t Tc, int64_t T, R* __restrict__ fp) {
     int64_t j = (int64_t)blockIdx.x * BS + threadIdx.x;
     if (j >= T) return;
-    double S[6] = {0, 0, 0, 0, 0, 0};
+    R S[6] = {0, 0, 0, 0, 0, 0};
 #pragma unroll
     for (int l = 0; l < 6; ++l) {
         const int k = t2e[l * Tc + j];
+        R x[6];
+        Rec<R>::load6(sig + Rec<R>::S6 * (int64_t)k, x);
 #pragma unroll
-        for (int q = 0; q < 6; ++q) S[q] += sig[q * Ec + k];
+        for (int q = 0; q < 6; ++q) S[q] += x[q];
     }
-    double f0[3] = {0, 0, 0};
+    R f[4][3];
+    f[0][0] = f[0][1] = f[0][2] = 0;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        const double gx = Vg[(3 * a) * Tc + j], gy = Vg[(3 * a + 1) * Tc + j], gz = Vg[(3 * a + 2) * Tc + j];
-        const double fx = S[0] * gx + S[3] * gy + S[5] * gz;
-        const double fy = S[3] * gx + S[1] * gy + S[4] * gz;
-        const double fz = S[5] * gx + S[4] * gy + S[2] * gz;
-        fp[(3 * (a + 1)) * Tc + j] = fx;
-        fp[(3 * (a + 1) + 1) * Tc + j] = fy;
-        fp[(3 * (a + 1) + 2) * Tc + j] = fz;
-        f0[0] += fx;
-        f0[1] += fy;
-        f0[2] += fz;
+        const R gx = Vg[(3 * a) * Tc + j], gy = Vg[(3 * a + 1) * Tc + j], gz = Vg[(3 * a + 2) * Tc + j];
+        f[a + 1][0] = S[0] * gx + S[3] * gy + S[5] * gz;
+        f[a + 1][1] = S[3] * gx + S[1] * gy + S[4] * gz;
+        f[a + 1][2] = S[5] * gx + S[4] * gy + S[2] * gz;
+        f[0][0] += f[a + 1][0];
+        f[0][1] += f[a + 1][1];
+        f[0][2] += f[a + 1][2];
     }
-    fp[j] = -f0[0];
-    fp[Tc + j] = -f0[1];
-    fp[2 * Tc + j] = -f0[2];
+    f[0][0] = -f[0][0];
+    f[0][1] = -f[0][1];
+    f[0][2] = -f[0][2];
+    R* o = fp + Rec<R>::SF * j;
+    if constexpr (sizeof(R) == 8) {
+        double2* p = reinterpret_cast<double2*>(o);
+        p[0] = make_double2(f[0][0], f[0][1]);
+        p[1] = make_double2(f[0][2], f[1][0]);
+        p[2] = make_double2(f[1][1], f[1][2]);
+        p[3] = make_double2(f[2][0], f[2][1]);
+        p[4] = make_double2(f[2][2], f[3][0]);
+        p[5] = make_double2(f[3][1], f[3][2]);
+    } else {
+        float4* p = reinterpret_cast<float4*>(o);
+#pragma unroll
+        for (int a = 0; a < 4; ++a) p[a] = make_float4(f[a][0], f[a][1], f[a][2], 0.f);
+    }
 }
 
-__global__ void __launch_bounds__(BS) k_node_update(const double* __restrict__ fp, int64_t Tc,
-                                                    const int* __restrict__ inc_off, const int* __restrict__ inc_cnt,
-                                                    const int* __restrict__ inc_pool, const double* __restrict__ fext,
-                                                    const double* __restrict__ minv, double* __restrict__ v,
-                                                    double* __restrict__ a, int64_t Nc, int64_t N, double hdt, int first) {
+template <class R>
+__global__ void __launch_bounds__(BS) k_node_update(const R* __restrict__ fp, const int* __restrict__ inc_off,
+                                                    const int* __restrict__ inc_cnt, const int* __restrict__ inc_pool,
+                                                    const double* __restrict__ fext, const double* __restrict__ minv,
+                                                    double* __restrict__ v, double* __restrict__ a, int64_t Nc,
+                                                    int64_t N, double hdt, int first) {
     int64_t i = (int64_t)blockIdx.x * BS + threadIdx.x;
     if (i >= N) return;
     const int off = inc_off[i], cnt = inc_cnt[i];
-    double f[3] = {0, 0, 0};
-    for (int q = 0; q < cnt; ++q) {
-        const int e = inc_pool[off + q];
-        const int64_t j = e >> 2, l = e & 3;
-        f[0] += fp[(3 * l) * Tc + j];
-        f[1] += fp[(3 * l + 1) * Tc + j];
-        f[2] += fp[(3 * l + 2) * Tc + j];
+    double f[3];
+    if constexpr (sizeof(R) == 8) {
+        f[0] = f[1] = f[2] = 0.0;
+        for (int q = 0; q < cnt; ++q) {
+            const double* p = fp + 12 * (int64_t)(inc_pool[off + q] >> 2) + 3 * (inc_pool[off + q] & 3);
+            f[0] += p[0];
+            f[1] += p[1];
+            f[2] += p[2];
+        }
+    } else {
+        // compensated FP32 sum (Kahan) of the FP32 element forces
+        float s[3] = {0.f, 0.f, 0.f}, cmp[3] = {0.f, 0.f, 0.f};
+        for (int q = 0; q < cnt; ++q) {
+            const int e = inc_pool[off + q];
+            const float4 x = reinterpret_cast<const float4*>(fp)[4 * (int64_t)(e >> 2) + (e & 3)];
+            const float xv[3] = {x.x, x.y, x.z};
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const float y = xv[c] - cmp[c];
+                const float t = s[c] + y;
+                cmp[c] = (t - s[c]) - y;
+                s[c] = t;
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) f[c] = (double)s[c] - (double)cmp[c];
     }
     const double mi = minv[i];
     const double sixth = 1.0 / 6.0;
@@ -202,7 +337,8 @@ __global__ void __launch_bounds__(BS) k_edge_coeffs(const int* __restrict__ list
                                                     const int* __restrict__ fan_pool, const double* __restrict__ vol,
                                                     const double* __restrict__ lam, const double* __restrict__ mu,
                                                     double* __restrict__ cl, double* __restrict__ cm,
-                                                    double* __restrict__ sumV) {
+                                                    double* __restrict__ sumV, float* __restrict__ cl32,
+                                                    float* __restrict__ cm32) {
     int64_t i = (int64_t)blockIdx.x * BS + threadIdx.x;
     if (i >= n) return;
     const int k = list ? list[i] : (int)i;
@@ -219,6 +355,10 @@ __global__ void __launch_bounds__(BS) k_edge_coeffs(const int* __restrict__ list
     cl[k] = sl * inv2;
     cm[k] = sm * inv2;
     sumV[k] = sv;
+    if (cl32) {
+        cl32[k] = (float)(sl * inv2);
+        cm32[k] = (float)(sm * inv2);
+    }
 }
 
 __global__ void __launch_bounds__(BS) k_node_mass(const int* __restrict__ list, int64_t n,
@@ -287,20 +427,23 @@ __global__ void __launch_bounds__(RB) k_energy_nodes(const double* __restrict__ 
     block_sum_store<3>(x, part);
 }
 
-__global__ void __launch_bounds__(RB) k_energy_edges(const double* __restrict__ h, int64_t Tc,
-                                                     const int* __restrict__ fan_off, const int* __restrict__ fan_cnt,
-                                                     const int* __restrict__ fan_pool, const double* __restrict__ sig,
-                                                     int64_t Ec, int64_t E, double* __restrict__ part) {
+template <class R>
+__global__ void __launch_bounds__(RB) k_energy_edges(const R* __restrict__ h, const int* __restrict__ fan_off,
+                                                     const int* __restrict__ fan_cnt, const int* __restrict__ fan_pool,
+                                                     const R* __restrict__ sig, int64_t E, double* __restrict__ part) {
     double x[1] = {0};
     for (int64_t k = (int64_t)blockIdx.x * RB + threadIdx.x; k < E; k += (int64_t)RG * RB) {
         const int off = fan_off[k], cnt = fan_cnt[k];
         double H[6] = {0, 0, 0, 0, 0, 0};
         for (int i = 0; i < cnt; ++i) {
-            const int j = fan_pool[off + i];
-            for (int q = 0; q < 6; ++q) H[q] += h[q * Tc + j];
+            R y[6];
+            Rec<R>::load6(h + Rec<R>::S6 * (int64_t)fan_pool[off + i], y);
+            for (int q = 0; q < 6; ++q) H[q] += (double)y[q];
         }
+        R s[6];
+        Rec<R>::load6(sig + Rec<R>::S6 * k, s);
         double e = 0;
-        for (int q = 0; q < 6; ++q) e += H[q] * sig[q * Ec + k];
+        for (int q = 0; q < 6; ++q) e += H[q] * (double)s[q];
         x[0] += e * (1.0 / 12.0);   // 1/2 Vs eps.sigma = 1/2 (sumV/6) (H/sumV).sigma
     }
     block_sum_store<1>(x, part + 3 * RG);
@@ -332,11 +475,14 @@ __global__ void __launch_bounds__(RB) k_count_nonfinite(const double* __restrict
     if (__syncthreads_or(bad) && threadIdx.x == 0) atomicAdd((unsigned long long*)cnt, 1ull);
 }
 
+inline bool mixed(const cem_ctx* c) { return c->precision == CEM_MIXED; }
+
 }  // namespace
 
 int cem_launch_geometry(cem_ctx* c, int64_t t0, int64_t t1, double* hbuf) {
     if (t1 <= t0) return CEM_OK;
-    k_geometry<<<cem_grid(t1 - t0, BS), BS, 0, c->stream>>>(c->X, c->Nc, c->conn, c->Tc, t0, t1, c->Vg, c->vol, hbuf);
+    k_geometry<<<cem_grid(t1 - t0, BS), BS, 0, c->stream>>>(c->X, c->Nc, c->conn, c->Tc, t0, t1, c->Vg, c->Vg32,
+                                                            c->vol, hbuf);
     cem_launched(c);
     CEM_CK(c, cudaGetLastError());
     return CEM_OK;
@@ -344,37 +490,62 @@ int cem_launch_geometry(cem_ctx* c, int64_t t0, int64_t t1, double* hbuf) {
 
 int cem_launch_predict(cem_ctx* c) {
     if (c->N == 0) return CEM_OK;
-    k_predict<<<cem_grid(c->N, BS), BS, 0, c->stream>>>(c->u, c->v, c->a, c->Nc, c->N, c->dt, 0.5 * c->dt * c->dt);
+    k_predict<<<cem_grid(c->N, BS), BS, 0, c->stream>>>(c->u, c->v, c->a, c->Nc, c->N, c->dt, 0.5 * c->dt * c->dt,
+                                                        mixed(c) ? c->uhl : nullptr);
+    cem_launched(c);
+    CEM_CK(c, cudaGetLastError());
+    return CEM_OK;
+}
+
+int cem_launch_split_u(cem_ctx* c) {
+    if (!mixed(c) || c->N == 0) return CEM_OK;
+    k_split_u<<<cem_grid(c->N, BS), BS, 0, c->stream>>>(c->u, c->Nc, c->N, c->uhl);
     cem_launched(c);
     CEM_CK(c, cudaGetLastError());
     return CEM_OK;
 }
 
 int cem_launch_strain(cem_ctx* c) {
-    k_strain<<<cem_grid(c->T, BS), BS, 0, c->stream>>>(c->u, c->Nc, c->conn, c->Vg, c->Tc, c->T, c->h);
+    if (mixed(c))
+        k_strain<float><<<cem_grid(c->T, BS), BS, 0, c->stream>>>(c->u, c->uhl, c->Nc, c->conn, c->Vg32, c->Tc, c->T,
+                                                                  c->h32);
+    else
+        k_strain<double><<<cem_grid(c->T, BS), BS, 0, c->stream>>>(c->u, nullptr, c->Nc, c->conn, c->Vg, c->Tc, c->T,
+                                                                   c->h);
     cem_launched(c);
     CEM_CK(c, cudaGetLastError());
     return CEM_OK;
 }
 
 int cem_launch_edge_stress(cem_ctx* c) {
-    k_edge_stress<<<cem_grid(c->E, BS), BS, 0, c->stream>>>(c->h, c->Tc, c->fan_off, c->fan_cnt, c->fan_pool, c->cl,
-                                                            c->cm, c->Ec, c->E, c->sig);
+    if (mixed(c))
+        k_edge_stress<float><<<cem_grid(c->E, BS), BS, 0, c->stream>>>(c->h32, c->fan_off, c->fan_cnt, c->fan_pool,
+                                                                       c->cl32, c->cm32, c->E, c->sig32);
+    else
+        k_edge_stress<double><<<cem_grid(c->E, BS), BS, 0, c->stream>>>(c->h, c->fan_off, c->fan_cnt, c->fan_pool,
+                                                                        c->cl, c->cm, c->E, c->sig);
     cem_launched(c);
     CEM_CK(c, cudaGetLastError());
     return CEM_OK;
 }
 
 int cem_launch_force(cem_ctx* c) {
-    k_force<<<cem_grid(c->T, BS), BS, 0, c->stream>>>(c->sig, c->Ec, c->t2e, c->Vg, c->Tc, c->T, c->fp);
+    if (mixed(c))
+        k_force<float><<<cem_grid(c->T, BS), BS, 0, c->stream>>>(c->sig32, c->t2e, c->Vg32, c->Tc, c->T, c->fp32);
+    else
+        k_force<double><<<cem_grid(c->T, BS), BS, 0, c->stream>>>(c->sig, c->t2e, c->Vg, c->Tc, c->T, c->fp);
     cem_launched(c);
     CEM_CK(c, cudaGetLastError());
     return CEM_OK;
 }
 
 int cem_launch_node_update(cem_ctx* c, int first) {
-    k_node_update<<<cem_grid(c->N, BS), BS, 0, c->stream>>>(c->fp, c->Tc, c->inc_off, c->inc_cnt, c->inc_pool, c->fext,
-                                                            c->minv, c->v, c->a, c->Nc, c->N, 0.5 * c->dt, first);
+    if (mixed(c))
+        k_node_update<float><<<cem_grid(c->N, BS), BS, 0, c->stream>>>(
+            c->fp32, c->inc_off, c->inc_cnt, c->inc_pool, c->fext, c->minv, c->v, c->a, c->Nc, c->N, 0.5 * c->dt, first);
+    else
+        k_node_update<double><<<cem_grid(c->N, BS), BS, 0, c->stream>>>(
+            c->fp, c->inc_off, c->inc_cnt, c->inc_pool, c->fext, c->minv, c->v, c->a, c->Nc, c->N, 0.5 * c->dt, first);
     cem_launched(c);
     CEM_CK(c, cudaGetLastError());
     return CEM_OK;
@@ -384,7 +555,7 @@ int cem_launch_edge_coeffs(cem_ctx* c, const int* list, int64_t n) {
     if (!list) n = c->E;
     if (n <= 0) return CEM_OK;
     k_edge_coeffs<<<cem_grid(n, BS), BS, 0, c->stream>>>(list, n, c->fan_off, c->fan_cnt, c->fan_pool, c->vol, c->lam,
-                                                         c->mu, c->cl, c->cm, c->sumV);
+                                                         c->mu, c->cl, c->cm, c->sumV, c->cl32, c->cm32);
     cem_launched(c);
     CEM_CK(c, cudaGetLastError());
     return CEM_OK;
@@ -411,8 +582,12 @@ int cem_launch_material(cem_ctx* c, const double* E, int nE, const double* Gc, i
 // out = {kinetic, ext_work, aMa, strain}; needs h and sig of the current state.
 int cem_energy_reduce(cem_ctx* c, double out[4]) {
     k_energy_nodes<<<RG, RB, 0, c->stream>>>(c->u, c->v, c->a, c->mass, c->fext, c->Nc, c->N, c->red_part);
-    k_energy_edges<<<RG, RB, 0, c->stream>>>(c->h, c->Tc, c->fan_off, c->fan_cnt, c->fan_pool, c->sig, c->Ec, c->E,
-                                              c->red_part);
+    if (mixed(c))
+        k_energy_edges<float><<<RG, RB, 0, c->stream>>>(c->h32, c->fan_off, c->fan_cnt, c->fan_pool, c->sig32, c->E,
+                                                        c->red_part);
+    else
+        k_energy_edges<double><<<RG, RB, 0, c->stream>>>(c->h, c->fan_off, c->fan_cnt, c->fan_pool, c->sig, c->E,
+                                                         c->red_part);
     k_reduce_final<<<1, RB, 0, c->stream>>>(c->red_part, 4, c->red_out);
     cem_launched(c, 3);
     CEM_CK(c, cudaGetLastError());
@@ -431,4 +606,4 @@ int cem_launch_check_finite(cem_ctx* c) {
 }
 
 // Reduction scratch size (doubles) needed by cem_energy_reduce.
-extern "C++" int64_t cem_reduction_doubles() { return 4 * RG; }
+int64_t cem_reduction_doubles() { return 4 * RG; }
