@@ -48,22 +48,31 @@ def _workload():
 KERNEL_UNITS = {"predict": "nodes", "strain": "tets", "edge_stress": "edges", "force": "tets", "node_update": "nodes"}
 
 
-def kernel_costs(T, E, N):
-    """Algorithmic FP64 flops (FMA = 2) and bytes per unit of each hot kernel.
+def kernel_costs(T, E, N, precision):
+    """Algorithmic FP64 flops (FMA = 2; FP64 path) and bytes per unit of each hot kernel.
 
     Bytes are the arrays the kernel reads or writes, each once (gathered
     operands counted once per producer: u per node, h per element, sigma per
     edge, element forces per element).  f = mean fan size 6T/E, g = mean node
-    incidence 4T/N.
+    incidence 4T/N.  Mixed precision: FP32 geometry, coefficients and
+    intermediate records (h, sigma: 32 B; element forces: 64 B), an FP32
+    hi/lo copy of u (32 B per node), FP64 node state.
     """
     f, g = 6.0 * T / E, 4.0 * T / N
     flops = {"predict": 12.0, "strain": 57.0, "edge_stress": 6.0 * f + 13.0, "force": 90.0,
              "node_update": 3.0 * g + 18.0}
-    byts = {"predict": 96.0,
-            "strain": 16 + 72 + 48 + 24.0 * N / T,
-            "edge_stress": 8 + 4.0 * f + 16 + 48 + 48.0 * T / E,
-            "force": 24 + 72 + 96 + 48.0 * E / T,
-            "node_update": 8 + 4.0 * g + 24 + 8 + 96 + 96.0 * T / N}
+    if precision == "fp64":
+        byts = {"predict": 96.0,
+                "strain": 16 + 72 + 48 + 24.0 * N / T,
+                "edge_stress": 8 + 4.0 * f + 16 + 48 + 48.0 * T / E,
+                "force": 24 + 72 + 96 + 48.0 * E / T,
+                "node_update": 8 + 4.0 * g + 24 + 8 + 96 + 96.0 * T / N}
+    else:
+        byts = {"predict": 128.0,
+                "strain": 16 + 36 + 32 + 32.0 * N / T,
+                "edge_stress": 8 + 4.0 * f + 8 + 32 + 32.0 * T / E,
+                "force": 24 + 36 + 64 + 32.0 * E / T,
+                "node_update": 8 + 4.0 * g + 24 + 8 + 96 + 64.0 * T / N}
     return flops, byts
 
 
@@ -75,7 +84,8 @@ def _args():
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", choices=["cem", "reference"], default="cem")
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
+    p.add_argument("--precision", choices=["fp64", "mixed"], default="mixed")
+    p.add_argument("--no-compare", action="store_true", help="skip the second-precision run and agreement check")
     p.add_argument("--split-capacity", type=int, default=0,
                    help="max elements that may split (0: all); lower it to shrink device memory for profiling")
     p.add_argument("--cpu-baseline-worker", action="store_true", help=argparse.SUPPRESS)
@@ -221,71 +231,97 @@ def run_cem(a):
             dist.barrier()
 
     w = _workload()
-    sim = CEM.from_workload(w, device=dev, split_capacity=a.split_capacity, precision=a.precision)
-    info0 = sim.info()
-    sim.step(a.warmup)
-    barrier()
     stream = torch.cuda.current_stream(dev)
-    clocks = ClockSampler(_bus_id(dev)) if rank == 0 else None
-    sim.profile(True)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    sim.step(a.steps)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    t_ms = e0.elapsed_time(e1)
-    clk = clocks.stop() if clocks else None
-    prof, launches = sim.profile_read()
-    sim.profile(False)
-    barrier()
-    tmax = torch.tensor([t_ms], device="cuda", dtype=torch.float64)
-    if world > 1:
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-    t_ms = float(tmax.item())
-    info = sim.info()
-    energy = sim.energy()
-    units_total = w.n_tets * a.steps * world
-    value = units_total / (t_ms * 1e-3)
-
-    # dominant kernel and its roofline
-    fp64_peak_meas = probe_fp64_fma(dev, stream.cuda_stream)
     peaks = _peaks()
     hbm = peaks.get("hbm_gbs")
-    hot = {k: prof[k] for k in KERNEL_UNITS}
-    dom = max(hot, key=lambda k: hot[k][0])
-    Tm = (info0["n_tets"] + info["n_tets"]) / 2.0          # element slots launched (mean over the window)
-    Ta = (info0["n_active_tets"] + info["n_active_tets"]) / 2.0
-    Em = (info0["n_edges"] + info["n_edges"]) / 2.0
-    Nm = (info0["n_nodes"] + info["n_nodes"]) / 2.0
-    fl, by = kernel_costs(Ta, Em, Nm)
-    sm_clock = (clk or {}).get("sm_max_mhz") or peaks.get("sm_max_mhz") or 2070.0
-    fp64_peak = 152 * 4 * sm_clock * 1e6      # 152 SMs x 2 FP64 FMA/clk x 2 FLOP
-    kernels = {}
-    for k, (ms_tot, nl) in prof.items():
-        kernels[k] = {"ms": ms_tot, "launches": nl, "share": ms_tot / max(t_ms, 1e-9)}
-        if k in KERNEL_UNITS and nl:
-            units = {"tets": Tm, "edges": Em, "nodes": Nm}[KERNEL_UNITS[k]]
-            s = ms_tot * 1e-3 / nl
-            kernels[k].update(per_launch_us=s * 1e6, tflops=fl[k] * units / s / 1e12,
-                              gbs=by[k] * units / s / 1e9)
-    ms_tot, nl = hot[dom]
-    per_launch_s = ms_tot * 1e-3 / max(nl, 1)
-    units = {"tets": Tm, "edges": Em, "nodes": Nm}[KERNEL_UNITS[dom]]
-    flops, bytes_ = fl[dom] * units, by[dom] * units
-    alu_bound = flops / fp64_peak > bytes_ / ((hbm or 6651.4) * 1e9)
-    if alu_bound:
-        achieved, peak, unit = flops / per_launch_s / 1e12, fp64_peak / 1e12, "TFLOP/s"
-        src = "derived: 152 SMs x 4 FP64 FLOP/clk x %.0f MHz (nominal 1.25 TFLOP/s at 2070 MHz)" % sm_clock
-    else:
-        achieved, peak, unit = bytes_ / per_launch_s / 1e9, hbm, "GB/s"
-        src = "MEASURED_PEAKS.json hbm_gbs (measured)"
-    roofline = {"bound": "alu" if alu_bound else "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
-                "unit": unit, "frac": achieved / peak, "traffic": None, "peak_source": src,
-                "per_launch_us": per_launch_s * 1e6,
-                "algorithmic_flops_per_launch": flops, "algorithmic_bytes_per_launch": bytes_,
-                "fp64_fma_measured_tflops": fp64_peak_meas / 1e12,
-                "hbm_gbs_achieved": bytes_ / per_launch_s / 1e9, "hbm_peak_gbs": hbm,
-                "fp64_tflops_achieved": flops / per_launch_s / 1e12, "fp64_peak_tflops": fp64_peak / 1e12}
+    fp64_peak_meas = probe_fp64_fma(dev, stream.cuda_stream)
+
+    def timed(precision, clocks_on):
+        """W untimed then K timed steps of a fresh context: metrics of the timed region."""
+        sim = CEM.from_workload(w, device=dev, split_capacity=a.split_capacity, precision=precision)
+        info0 = sim.info()
+        sim.step(a.warmup)
+        barrier()
+        clocks = ClockSampler(_bus_id(dev)) if (clocks_on and rank == 0) else None
+        sim.profile(True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sim.step(a.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t_ms = e0.elapsed_time(e1)
+        clk = clocks.stop() if clocks else None
+        prof, launches = sim.profile_read()
+        sim.profile(False)
+        barrier()
+        tmax = torch.tensor([t_ms], device="cuda", dtype=torch.float64)
+        if world > 1:
+            dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        t_ms = float(tmax.item())
+        info = sim.info()
+        energy = sim.energy()
+        sim.close()
+        Tm = (info0["n_tets"] + info["n_tets"]) / 2.0
+        Ta = (info0["n_active_tets"] + info["n_active_tets"]) / 2.0
+        Em = (info0["n_edges"] + info["n_edges"]) / 2.0
+        Nm = (info0["n_nodes"] + info["n_nodes"]) / 2.0
+        fl, by = kernel_costs(Ta, Em, Nm, precision)
+        sm_clock = (clk or {}).get("sm_max_mhz") or peaks.get("sm_max_mhz") or 2070.0
+        fp64_peak = 152 * 4 * sm_clock * 1e6      # 152 SMs x 2 FP64 FMA/clk x 2 FLOP
+        kernels = {}
+        for k, (ms_tot, nl) in prof.items():
+            kernels[k] = {"ms": ms_tot, "launches": nl, "share": ms_tot / max(t_ms, 1e-9)}
+            if k in KERNEL_UNITS and nl:
+                units = {"tets": Tm, "edges": Em, "nodes": Nm}[KERNEL_UNITS[k]]
+                sec = ms_tot * 1e-3 / nl
+                kernels[k].update(per_launch_us=sec * 1e6, gbs=by[k] * units / sec / 1e9)
+                if precision == "fp64":
+                    kernels[k]["fp64_tflops"] = fl[k] * units / sec / 1e12
+        hot = {k: prof[k] for k in KERNEL_UNITS}
+        dom = max(hot, key=lambda k: hot[k][0])
+        ms_tot, nl = hot[dom]
+        per_launch_s = ms_tot * 1e-3 / max(nl, 1)
+        units = {"tets": Tm, "edges": Em, "nodes": Nm}[KERNEL_UNITS[dom]]
+        flops, bytes_ = fl[dom] * units, by[dom] * units
+        alu_bound = precision == "fp64" and flops / fp64_peak > bytes_ / ((hbm or 6651.4) * 1e9)
+        if alu_bound:
+            achieved, peak, unit = flops / per_launch_s / 1e12, fp64_peak / 1e12, "TFLOP/s"
+            src = "derived: 152 SMs x 4 FP64 FLOP/clk x %.0f MHz (nominal 1.25 TFLOP/s at 2070 MHz)" % sm_clock
+        else:
+            achieved, peak, unit = bytes_ / per_launch_s / 1e9, hbm, "GB/s"
+            src = "MEASURED_PEAKS.json hbm_gbs (measured copy bandwidth)"
+        roofline = {"bound": "alu" if alu_bound else "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
+                    "unit": unit, "frac": achieved / peak, "traffic": None, "peak_source": src,
+                    "per_launch_us": per_launch_s * 1e6, "algorithmic_bytes_per_launch": bytes_,
+                    "hbm_gbs_achieved": bytes_ / per_launch_s / 1e9, "hbm_peak_gbs": hbm,
+                    "units_per_launch": units}
+        if precision == "fp64":
+            roofline.update(algorithmic_flops_per_launch=flops, fp64_tflops_achieved=flops / per_launch_s / 1e12,
+                            fp64_peak_tflops=fp64_peak / 1e12, fp64_fma_measured_tflops=fp64_peak_meas / 1e12)
+        return dict(t_ms=t_ms, value=w.n_tets * a.steps * world / (t_ms * 1e-3), roofline=roofline, kernels=kernels,
+                    clocks=clk, launches=launches, info0=info0, info=info, energy=energy)
+
+    main = timed(a.precision, True)
+    other = None
+    if not a.no_compare:
+        other = timed("fp64" if a.precision == "mixed" else "mixed", False)
+
+    # agreement of the two precisions on a short window (both paths from the same start)
+    agree = None
+    if not a.no_compare:
+        n_cmp = 500
+        s64 = CEM.from_workload(w, device=dev, split_capacity=a.split_capacity, precision="fp64")
+        s32 = CEM.from_workload(w, device=dev, split_capacity=a.split_capacity, precision="mixed")
+        s64.step(n_cmp)
+        s32.step(n_cmp)
+        u64, u32 = s64.field("u"), s32.field("u")
+        c64 = {(r[0], r[3]) for r in s64.crack_state()}
+        c32 = {(r[0], r[3]) for r in s32.crack_state()}
+        rel = (float(np.linalg.norm(u32 - u64) / np.linalg.norm(u64)) if u32.shape == u64.shape else None)
+        agree = {"steps": n_cmp, "rel_l2_u_mixed_vs_fp64": rel,
+                 "split_jaccard": len(c64 & c32) / max(len(c64 | c32), 1), "splits_fp64": len(c64)}
+        s64.close()
+        s32.close()
 
     # end to end through the public API with host buffers: create + material + K steps + read back
     barrier()
@@ -293,7 +329,7 @@ def run_cem(a):
     sim2 = CEM.from_workload(w, device=dev, split_capacity=a.split_capacity, precision=a.precision)
     sim2.step(a.steps)
     u = sim2.field("u")
-    e2 = sim2.energy()
+    sim2.energy()
     torch.cuda.synchronize()
     t_e2e = time.perf_counter() - t0
     sim2.close()
@@ -304,7 +340,6 @@ def run_cem(a):
     h2d = (w.X.nbytes + w.tets.nbytes + w.tfaces.nbytes + w.tvec.nbytes + w.notch_tet.nbytes
            + w.notch_side.nbytes + 16)
     d2h = u.nbytes + 64
-    sim.close()
 
     if rank != 0:
         return
@@ -314,23 +349,34 @@ def run_cem(a):
             cpu = _cpu_baseline(a.cpu_steps)
         except Exception as ex:  # reported, not hidden
             cpu = {"value": None, "unit": METRIC, "cores": 1, "kind": "oracle", "sample": "failed: %r" % (ex,)}
+    info0, info, energy = main["info0"], main["info"], main["energy"]
     line = {
-        "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
-        "ms_per_step": t_ms / a.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64", "data": "synthetic",
+        "metric": METRIC, "value": main["value"], "unit": METRIC, "n_gpus": world, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": main["t_ms"] / a.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32/f64 mixed" if a.precision == "mixed" else "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "tets": w.n_tets, "nodes": w.n_nodes, "edges": info0["n_edges"],
-                   "precision": "fp64", "split": True, "parallelism": "replicas" if world > 1 else "single",
+                   "precision": a.precision, "split": True,
+                   "parallelism": "replicas" if world > 1 else "single",
                    "l2": "working set %.2f GB > 129 MB L2 (no flush needed)" % (info["device_bytes"] / 1e9),
-                   "split_elements_at_end": energy["n_split"], "steps_before_timing": a.warmup},
-        "roofline": roofline,
-        "kernels": kernels,
-        "clocks": clk,
+                   "split_elements_at_end": energy["n_split"], "elements_at_end": info["n_active_tets"],
+                   "steps_before_timing": a.warmup},
+        "roofline": main["roofline"],
+        "kernels": main["kernels"],
+        "clocks": main["clocks"],
         "e2e": {"value": w.n_tets * a.steps * world / t_e2e, "unit": METRIC,
                 "h2d_bytes_per_step": h2d / a.steps, "d2h_bytes_per_step": d2h / a.steps,
                 "includes": "mesh upload and topology build, material, K steps, u and energy read-back"},
-        "gpu_launches": launches,
+        "gpu_launches": main["launches"],
         "cpu_baseline": cpu,
     }
+    if other is not None:
+        line["fp64" if a.precision == "mixed" else "mixed"] = {
+            "value": other["value"], "ms_per_step": other["t_ms"] / a.steps, "roofline": other["roofline"],
+            "kernels": {k: {kk: v[kk] for kk in ("ms", "share", "per_launch_us") if kk in v}
+                        for k, v in other["kernels"].items()},
+            "gpu_launches": other["launches"], "speedup_of_main": main["value"] / other["value"]}
+    if agree is not None:
+        line["precision_agreement"] = agree
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

@@ -108,6 +108,8 @@ int build_topology(cem_ctx* c, const std::vector<int>& conn, HostTopo& H) {
         H.e_off[i + 1] = (int)H.e_nbr.size();
     }
     c->E0 = (int64_t)H.e_nbr.size();
+    c->max_inc0 = 0;
+    for (int64_t i = 0; i < N; ++i) c->max_inc0 = std::max<int64_t>(c->max_inc0, H.inc_off[i + 1] - H.inc_off[i]);
     H.t2e.assign(6 * T, 0);
     for (int64_t t = 0; t < T; ++t)
         for (int l = 0; l < 6; ++l) {
@@ -121,6 +123,8 @@ int build_topology(cem_ctx* c, const std::vector<int>& conn, HostTopo& H) {
     H.fan_off.assign(c->E0 + 1, 0);
     for (int64_t t = 0; t < T; ++t)
         for (int l = 0; l < 6; ++l) H.fan_off[H.t2e[l * T + t] + 1]++;
+    c->max_fan0 = 0;
+    for (int64_t e = 0; e < c->E0; ++e) c->max_fan0 = std::max<int64_t>(c->max_fan0, H.fan_off[e + 1]);
     for (int64_t e = 0; e < c->E0; ++e) H.fan_off[e + 1] += H.fan_off[e];
     H.fan.assign(6 * T, 0);
     {
@@ -245,7 +249,8 @@ int create_impl(const cem_mesh_desc* d, cem_ctx* c) {
         n_codes_cap >= lim)
         return cem_fail(c, CEM_EINVAL, "capacities exceed 32-bit indexing; lower split_capacity");
     const int64_t big = std::max({c->Ec, c->Nc, T0});
-    const int64_t scan_max = std::max({2 * E0, c->Ec, c->Nc, T0, n_codes_cap});
+    const int64_t aff_cap = std::max(big, 42 * S_cap);   // affected marks of one split step: 7 S x 6
+    const int64_t scan_max = std::max({2 * E0, c->Ec, c->Nc, T0, n_codes_cap, aff_cap});
     c->scan_blocks_cap = cem_scan_blocks_needed(scan_max);
 
     if (int rc = select_device(c)) return rc;
@@ -278,8 +283,8 @@ int create_impl(const cem_mesh_desc* d, cem_ctx* c) {
     ok = ok && dalloc(c, c->key_flag, 2 * E0) && dalloc(c, c->edge_flag, Ec) && dalloc(c, c->node_flag, Nc);
     ok = ok && dalloc(c, c->code_flag, n_codes_cap) && dalloc(c, c->new_keys, 2 * E0) && dalloc(c, c->sub_off, T0);
     ok = ok && dalloc(c, c->slot_of, n_codes_cap) && dalloc(c, c->code_rank, n_codes_cap);
-    ok = ok && dalloc(c, c->aff, big) && dalloc(c, c->aff_keep, big) && dalloc(c, c->aff_new, big) &&
-         dalloc(c, c->aff_off, big);
+    ok = ok && dalloc(c, c->aff, aff_cap) && dalloc(c, c->aff_keep, aff_cap) && dalloc(c, c->aff_new, aff_cap) &&
+         dalloc(c, c->aff_off, aff_cap);
     ok = ok && dalloc(c, c->add_cnt, big) && dalloc(c, c->cursor, big) && dalloc(c, c->scan_tmp, scan_max);
     ok = ok && dalloc(c, c->scan_blocks, c->scan_blocks_cap);
     ok = ok && dalloc(c, c->red_part, cem_reduction_doubles()) && dalloc(c, c->red_out, 8);

@@ -37,7 +37,9 @@ enum {
     CNT_NEWSUB,        // new sub-elements in this split step
     CNT_NEWEDGE,       // new edges in this split step
     CNT_AFFECTED,      // affected edges / nodes (reused)
-    CNT_POOLNEED,      // pool entries needed by this update
+    CNT_POOLNEED,      // pool entries needed by this update (exact path)
+    CNT_NEED_FAN,      // pool entries taken by this step's fan update
+    CNT_NEED_INC,      // pool entries taken by this step's incidence update
     CNT_CAND,          // crack-front elements
     CNT_ERR,           // device-side error flags (bit mask)
     CNT_SCRATCH0,
@@ -58,6 +60,7 @@ struct cem_ctx {
     int64_t n_split_run = 0;    // split at run time
     int64_t n_active = 0;
     int64_t fan_cap = 0, fan_top = 0, inc_cap = 0, inc_top = 0;
+    int64_t max_fan0 = 0, max_inc0 = 0;   // largest fan / node incidence of the input mesh
     int64_t hash_cap = 0;
     int64_t scan_blocks_cap = 0;
     int64_t bytes = 0;

@@ -70,64 +70,81 @@ __device__ void stretch(const double* X, const double* u, int64_t Nc, int i, int
     for (int c = 0; c < 3; ++c) d[c] = on ? ui[c] - uj[c] : 0.0;
 }
 
-// sigma_1 * sqrt(n^T P_1 n) of a Voigt stress: closed-form eigenvalues of a
-// symmetric 3x3 matrix (trigonometric solution of the characteristic cubic)
-// and the spectral projector P_1 = (A - l2)(A - l3) / ((l1 - l2)(l1 - l3)).
-// A repeated top eigenvalue (within 1e-12 of the largest magnitude) projects
-// onto its whole eigenspace.
-__device__ double principal_projection(const double s[6], const double n[3]) {
-    const double a11 = s[0], a22 = s[1], a33 = s[2], a12 = s[3], a23 = s[4], a13 = s[5];
-    const double q = (a11 + a22 + a33) * (1.0 / 3.0);
-    const double b11 = a11 - q, b22 = a22 - q, b33 = a33 - q;
-    const double p1 = a12 * a12 + a13 * a13 + a23 * a23;
-    const double p2 = b11 * b11 + b22 * b22 + b33 * b33 + 2.0 * p1;
-    const double tol = 1e-12;
-    double l1, l2, l3;
-    if (p2 <= 0.0) {
-        l1 = l2 = l3 = q;
-    } else {
-        const double p = sqrt(p2 * (1.0 / 6.0));
-        const double ip = 1.0 / p;
-        const double c11 = b11 * ip, c22 = b22 * ip, c33 = b33 * ip;
-        const double c12 = a12 * ip, c23 = a23 * ip, c13 = a13 * ip;
-        const double det = c11 * (c22 * c33 - c23 * c23) - c12 * (c12 * c33 - c23 * c13) + c13 * (c12 * c23 - c22 * c13);
-        double r = 0.5 * det;
-        r = fmin(1.0, fmax(-1.0, r));
-        const double phi = acos(r) * (1.0 / 3.0);
-        l1 = q + 2.0 * p * cos(phi);
-        l3 = q + 2.0 * p * cos(phi + 2.0943951023931957);
-        l2 = 3.0 * q - l1 - l3;
-    }
-    const double scale = fmax(fabs(l1), fmax(fabs(l2), fabs(l3)));
-    double proj2;
-    if (l1 - l3 <= tol * scale) {
-        proj2 = 1.0;
-    } else {
-        double w3[3] = {(a11 - l3) * n[0] + a12 * n[1] + a13 * n[2], a12 * n[0] + (a22 - l3) * n[1] + a23 * n[2],
-                        a13 * n[0] + a23 * n[1] + (a33 - l3) * n[2]};
-        if (l1 - l2 <= tol * scale) {
-            proj2 = dot3(n, w3) / (l1 - l3);
-        } else {
-            double w2[3] = {(a11 - l2) * n[0] + a12 * n[1] + a13 * n[2], a12 * n[0] + (a22 - l2) * n[1] + a23 * n[2],
-                            a13 * n[0] + a23 * n[1] + (a33 - l2) * n[2]};
-            proj2 = dot3(w2, w3) / ((l1 - l2) * (l1 - l3));
+// s = sigma_1 * sqrt(n^T P_1 n) of a Voigt stress, where sigma_1 is the largest
+// eigenvalue and P_1 the spectral projector onto its eigenspace.  With
+// q = tr/3, p = sqrt(tr((A - q)^2) / 6) and B = (A - q I) / p, the eigenvalues
+// of B are the roots of beta^3 - 3 beta - det(B) = 0 (Smith's trigonometric
+// form: beta_1 = 2 cos(acos(det(B)/2) / 3)); given beta_1 the other two are
+// (-beta_1 +- sqrt(12 - 3 beta_1^2)) / 2 and
+//   n^T P_1 n = ((B - beta_2) n) . ((B - beta_3) n) / ((beta_1 - beta_2)(beta_1 - beta_3)).
+// A top eigenvalue repeated within 1e-12 of the largest magnitude projects
+// onto its whole eigenspace.  FP64: beta_1 is seeded in FP32 and polished by
+// two FP64 Newton steps on the cubic (no FP64 transcendental functions, which
+// are slow on GB300).  Mixed precision promotes the FP32 edge stress to FP64
+// first: in FP32 the projector loses accuracy next to repeated eigenvalues.
+template <class T>
+__device__ T principal_projection(const T s[6], const T n[3]) {
+    const T a11 = s[0], a22 = s[1], a33 = s[2], a12 = s[3], a23 = s[4], a13 = s[5];
+    const T q = (a11 + a22 + a33) * (T(1) / T(3));
+    const T b11 = a11 - q, b22 = a22 - q, b33 = a33 - q;
+    const T p2 = b11 * b11 + b22 * b22 + b33 * b33 + T(2) * (a12 * a12 + a13 * a13 + a23 * a23);
+    if (!(p2 > T(0))) return q;                        // A = q I: every direction is principal
+    const T p = sqrt(p2 * (T(1) / T(6)));
+    const T ip = T(1) / p;
+    const T c11 = b11 * ip, c22 = b22 * ip, c33 = b33 * ip, c12 = a12 * ip, c23 = a23 * ip, c13 = a13 * ip;
+    const T detB = c11 * (c22 * c33 - c23 * c23) - c12 * (c12 * c33 - c23 * c13) + c13 * (c12 * c23 - c22 * c13);
+    const float rf = fminf(1.f, fmaxf(-1.f, (float)(T(0.5) * detB)));
+    T b1 = (T)(2.f * cosf(acosf(rf) * (1.f / 3.f)));
+    if (sizeof(T) == 8) {
+        for (int it = 0; it < 2; ++it) {
+            const T f = b1 * (b1 * b1 - T(3)) - detB;
+            const T d = T(3) * (b1 * b1 - T(1));
+            if (d > T(0)) b1 -= f / d;
         }
-        proj2 = fmin(1.0, fmax(0.0, proj2));
+    }
+    b1 = fmin(T(2), fmax(T(1), b1));
+    const T disc = sqrt(fmax(T(0), T(12) - T(3) * b1 * b1));
+    const T b2 = T(0.5) * (-b1 + disc), b3 = T(0.5) * (-b1 - disc);
+    const T l1 = q + p * b1, l2 = q + p * b2, l3 = q + p * b3;
+    const T scale = fmax(fabs(l1), fmax(fabs(l2), fabs(l3)));
+    const T tol = T(1e-12) * scale;
+    T proj2;
+    if (l1 - l3 <= tol) {
+        proj2 = T(1);
+    } else {
+        const T w3[3] = {(c11 - b3) * n[0] + c12 * n[1] + c13 * n[2], c12 * n[0] + (c22 - b3) * n[1] + c23 * n[2],
+                         c13 * n[0] + c23 * n[1] + (c33 - b3) * n[2]};
+        if (l1 - l2 <= tol) {
+            proj2 = (n[0] * w3[0] + n[1] * w3[1] + n[2] * w3[2]) / (b1 - b3);
+        } else {
+            const T w2[3] = {(c11 - b2) * n[0] + c12 * n[1] + c13 * n[2],
+                             c12 * n[0] + (c22 - b2) * n[1] + c23 * n[2],
+                             c13 * n[0] + c23 * n[1] + (c33 - b2) * n[2]};
+            proj2 = (w2[0] * w3[0] + w2[1] * w3[1] + w2[2] * w3[2]) / ((b1 - b2) * (b1 - b3));
+        }
+        proj2 = fmin(T(1), fmax(T(0), proj2));
     }
     return l1 * sqrt(proj2);
 }
 
-// edge stress record k (FP64: 6 doubles; FP32: 8 floats, first 6 used), promoted to FP64
-__device__ __forceinline__ void load_sig(const double* sig64, const float* sig32, int k, double s[6]) {
+// s(edge k, n) in FP64 (FP32 records of the mixed path are promoted).
+__device__ __forceinline__ double edge_projection(const double* sig64, const float* sig32, int k, const double n[3]) {
+    double sd[6];
     if (sig32) {
-        for (int q = 0; q < 6; ++q) s[q] = (double)sig32[8 * (int64_t)k + q];
+        const float4 a = reinterpret_cast<const float4*>(sig32 + 8 * (int64_t)k)[0];
+        const float2 b = reinterpret_cast<const float2*>(sig32 + 8 * (int64_t)k)[2];
+        sd[0] = a.x; sd[1] = a.y; sd[2] = a.z; sd[3] = a.w; sd[4] = b.x; sd[5] = b.y;
     } else {
-        for (int q = 0; q < 6; ++q) s[q] = sig64[6 * (int64_t)k + q];
+        for (int q = 0; q < 6; ++q) sd[q] = sig64[6 * (int64_t)k + q];
     }
+    return principal_projection<double>(sd, n);
 }
 
 __device__ __forceinline__ int normalize_side(int m) { return (m & 1) ? ((~m) & 15) : m; }
 
+// One thread per (candidate, local face f); the four faces of a candidate are
+// neighbouring lanes of one warp and are reduced with shuffles: largest G,
+// ties to the lowest face.
 __global__ void __launch_bounds__(BS) k_front_G(const int* __restrict__ cand_list, int n_cand,
                                                 const int* __restrict__ conn, const int* __restrict__ t2e, int64_t Tc,
                                                 const int* __restrict__ face_nbr, const uint8_t* __restrict__ side,
@@ -136,80 +153,87 @@ __global__ void __launch_bounds__(BS) k_front_G(const int* __restrict__ cand_lis
                                                 const float* __restrict__ sig32,
                                                 const double* __restrict__ Gc, uint8_t* __restrict__ dec_mask,
                                                 double* __restrict__ dec_G) {
-    const int ci = blockIdx.x * BS + threadIdx.x;
-    if (ci >= n_cand) return;
-    const int t = cand_list[ci];
-    int tn[4];
-    for (int l = 0; l < 4; ++l) tn[l] = conn[l * Tc + t];
-    double bestG = -1.0 / 0.0;
-    int bestMask = 0;
-    for (int f = 0; f < 4; ++f) {
+    const int tid = blockIdx.x * BS + threadIdx.x;
+    const int ci = tid >> 2, f = tid & 3;
+    double G = -1.0 / 0.0;
+    int mask = 0;
+    int t = -1;
+    if (ci < n_cand) {
+        t = cand_list[ci];
         const int s = face_nbr[f * T0 + t];
-        if (s < 0) continue;
-        const int ms = side[s];
-        if (!ms) continue;
-        int sn[4];
-        for (int l = 0; l < 4; ++l) sn[l] = conn[l * Tc + s];
-        int fl[3], k = 0;
-        for (int l = 0; l < 4; ++l)
-            if (l != f) fl[k++] = l;
-        int bit[3];
-        for (int q = 0; q < 3; ++q) {
-            bit[q] = 0;
-            for (int r = 0; r < 4; ++r)
-                if (sn[r] == tn[fl[q]]) bit[q] = (ms >> r) & 1;
-        }
-        if (bit[0] == bit[1] && bit[1] == bit[2]) continue;   // no cut edge on this face
-        const int apex = (bit[0] == bit[1]) ? 2 : ((bit[0] == bit[2]) ? 1 : 0);
-        const int cl_ = fl[apex];
-        const int al = fl[apex == 0 ? 1 : 0];
-        const int bl = fl[apex == 2 ? 1 : 2];
-        const int dl = f;
-        const int a = tn[al], c = tn[cl_], b = tn[bl], d = tn[dl];
-        double d1[3], d2[3];
-        stretch(X, u, Nc, a, c, d1);
-        stretch(X, u, Nc, c, b, d2);
-        double Xa[3], Xb[3], Xc[3], Xd[3];
-        load3(X, Nc, a, Xa);
-        load3(X, Nc, b, Xb);
-        load3(X, Nc, c, Xc);
-        load3(X, Nc, d, Xd);
-        double ba[3] = {Xb[0] - Xa[0], Xb[1] - Xa[1], Xb[2] - Xa[2]};
-        double dc[3] = {Xd[0] - Xc[0], Xd[1] - Xc[1], Xd[2] - Xc[2]};
-        double da[3] = {Xd[0] - Xa[0], Xd[1] - Xa[1], Xd[2] - Xa[2]};
-        double nI[3], nII[3];
-        cross3(ba, dc, nI);
-        cross3(ba, da, nII);
-        const double iI = 1.0 / sqrt(dot3(nI, nI)), iII = 1.0 / sqrt(dot3(nII, nII));
-        for (int q = 0; q < 3; ++q) {
-            nI[q] *= iI;
-            nII[q] *= iII;
-        }
-        double sg[6];
-        load_sig(sig, sig32, t2e[local_edge(al, dl) * Tc + t], sg);
-        const double s_ad = principal_projection(sg, nI);
-        load_sig(sig, sig32, t2e[local_edge(bl, dl) * Tc + t], sg);
-        const double s_bd = principal_projection(sg, nI);
-        load_sig(sig, sig32, t2e[local_edge(cl_, dl) * Tc + t], sg);
-        const double s_cd = principal_projection(sg, nII);
-        const double GI = 0.5 * (s_ad * fabs(dot3(d1, nI)) + s_bd * fabs(dot3(d2, nI)));
-        const double GII = 0.5 * (s_cd * fabs(dot3(d1, nII)) + s_cd * fabs(dot3(d2, nII)));
-        double G;
-        int mask;
-        if (GI >= GII) {
-            G = GI;
-            mask = (1 << cl_) | (1 << dl);
-        } else {
-            G = GII;
-            mask = 1 << cl_;
-        }
-        if (G > bestG) {
-            bestG = G;
-            bestMask = normalize_side(mask);
+        const int ms = (s >= 0) ? side[s] : 0;
+        if (ms) {
+            int tn[4], sn[4];
+            for (int l = 0; l < 4; ++l) {
+                tn[l] = conn[l * Tc + t];
+                sn[l] = conn[l * Tc + s];
+            }
+            int fl[3], k = 0;
+            for (int l = 0; l < 4; ++l)
+                if (l != f) fl[k++] = l;
+            int bit[3];
+            for (int q = 0; q < 3; ++q) {
+                bit[q] = 0;
+                for (int r = 0; r < 4; ++r)
+                    if (sn[r] == tn[fl[q]]) bit[q] = (ms >> r) & 1;
+            }
+            if (!(bit[0] == bit[1] && bit[1] == bit[2])) {   // two cut edges on this face
+                const int apex = (bit[0] == bit[1]) ? 2 : ((bit[0] == bit[2]) ? 1 : 0);
+                const int cl_ = fl[apex];
+                const int al = fl[apex == 0 ? 1 : 0];
+                const int bl = fl[apex == 2 ? 1 : 2];
+                const int dl = f;
+                const int a = tn[al], c = tn[cl_], b = tn[bl], d = tn[dl];
+                double d1[3], d2[3];
+                stretch(X, u, Nc, a, c, d1);
+                stretch(X, u, Nc, c, b, d2);
+                double Xa[3], Xb[3], Xc[3], Xd[3];
+                load3(X, Nc, a, Xa);
+                load3(X, Nc, b, Xb);
+                load3(X, Nc, c, Xc);
+                load3(X, Nc, d, Xd);
+                double ba[3] = {Xb[0] - Xa[0], Xb[1] - Xa[1], Xb[2] - Xa[2]};
+                double dc[3] = {Xd[0] - Xc[0], Xd[1] - Xc[1], Xd[2] - Xc[2]};
+                double da[3] = {Xd[0] - Xa[0], Xd[1] - Xa[1], Xd[2] - Xa[2]};
+                double nI[3], nII[3];
+                cross3(ba, dc, nI);
+                cross3(ba, da, nII);
+                const double iI = 1.0 / sqrt(dot3(nI, nI)), iII = 1.0 / sqrt(dot3(nII, nII));
+                for (int q = 0; q < 3; ++q) {
+                    nI[q] *= iI;
+                    nII[q] *= iII;
+                }
+                const double s_ad = edge_projection(sig, sig32, t2e[local_edge(al, dl) * Tc + t], nI);
+                const double s_bd = edge_projection(sig, sig32, t2e[local_edge(bl, dl) * Tc + t], nI);
+                const double s_cd = edge_projection(sig, sig32, t2e[local_edge(cl_, dl) * Tc + t], nII);
+                const double GI = 0.5 * (s_ad * fabs(dot3(d1, nI)) + s_bd * fabs(dot3(d2, nI)));
+                const double GII = 0.5 * (s_cd * fabs(dot3(d1, nII)) + s_cd * fabs(dot3(d2, nII)));
+                if (GI >= GII) {
+                    G = GI;
+                    mask = normalize_side((1 << cl_) | (1 << dl));
+                } else {
+                    G = GII;
+                    mask = normalize_side(1 << cl_);
+                }
+            }
         }
     }
-    dec_G[ci] = bestG;
-    dec_mask[ci] = (bestMask != 0 && bestG > Gc[t]) ? (uint8_t)bestMask : (uint8_t)0;
+    int fb = f;
+#pragma unroll
+    for (int o = 1; o < 4; o <<= 1) {
+        const double G2 = __shfl_xor_sync(0xffffffffu, G, o);
+        const int m2 = __shfl_xor_sync(0xffffffffu, mask, o);
+        const int f2 = __shfl_xor_sync(0xffffffffu, fb, o);
+        if (G2 > G || (G2 == G && f2 < fb)) {
+            G = G2;
+            mask = m2;
+            fb = f2;
+        }
+    }
+    if (f == 0 && ci < n_cand) {
+        dec_G[ci] = G;
+        dec_mask[ci] = (mask != 0 && G > Gc[t]) ? (uint8_t)mask : (uint8_t)0;
+    }
 }
 
 // ------------------------------------------------------------------ split list
@@ -452,13 +476,13 @@ __device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
     return z ^ (z >> 31);
 }
 
-__global__ void k_sub_edges(int n_codes, int64_t T, int64_t N0, const int* __restrict__ conn,
+__global__ void k_sub_edges(const long long* __restrict__ nsub, int64_t T, int64_t N0, const int* __restrict__ conn,
                             int* __restrict__ t2e, const int* __restrict__ anc, int64_t Tc,
                             unsigned long long* __restrict__ hkeys, const int* __restrict__ hvals,
                             int* __restrict__ hfirst, int64_t hmask, int* __restrict__ slot_of,
                             long long* __restrict__ err) {
     const int cidx = blockIdx.x * BS + threadIdx.x;
-    if (cidx >= n_codes) return;
+    if (cidx >= 6 * *nsub) return;
     const int q = cidx / 6, l = cidx % 6;
     const int64_t s = T + q;
     const int x = conn[CEM_LE0(l) * Tc + s], y = conn[CEM_LE1(l) * Tc + s];
@@ -494,10 +518,11 @@ __global__ void k_sub_edges(int n_codes, int64_t T, int64_t N0, const int* __res
     if (hvals[slot] < 0) atomicMin(&hfirst[slot], cidx);
 }
 
-__global__ void k_edge_owner(int n_codes, const int* __restrict__ slot_of, const int* __restrict__ hvals,
-                             const int* __restrict__ hfirst, uint8_t* __restrict__ code_flag) {
+__global__ void k_edge_owner(const long long* __restrict__ nsub, const int* __restrict__ slot_of,
+                             const int* __restrict__ hvals, const int* __restrict__ hfirst,
+                             uint8_t* __restrict__ code_flag) {
     const int c = blockIdx.x * BS + threadIdx.x;
-    if (c >= n_codes) return;
+    if (c >= 6 * *nsub) return;
     const int s = slot_of[c];
     code_flag[c] = (s >= 0 && hvals[s] < 0 && hfirst[s] == c) ? 1 : 0;
 }
@@ -526,10 +551,10 @@ __global__ void k_edge_assign(const long long* __restrict__ count, const int* __
     }
 }
 
-__global__ void k_edge_resolve(int n_codes, int64_t T, const int* __restrict__ slot_of,
+__global__ void k_edge_resolve(const long long* __restrict__ nsub, int64_t T, const int* __restrict__ slot_of,
                                const int* __restrict__ hvals, int* __restrict__ t2e, int64_t Tc) {
     const int c = blockIdx.x * BS + threadIdx.x;
-    if (c >= n_codes) return;
+    if (c >= 6 * *nsub) return;
     const int s = slot_of[c];
     if (s < 0) return;
     t2e[(c % 6) * Tc + T + c / 6] = hvals[s];
@@ -538,7 +563,8 @@ __global__ void k_edge_resolve(int n_codes, int64_t T, const int* __restrict__ s
 // ------------------------------------------------------------------ fans / incidence
 // kind 0: edge fans (entries: element id; 6 per element via t2e)
 // kind 1: node incidence (entries: element*4 + local; 4 per element via conn)
-__global__ void k_mark_affected(int kind, int S, const int* __restrict__ split_list, int NS, int64_t T,
+__global__ void k_mark_affected(int kind, int S, const int* __restrict__ split_list,
+                                const long long* __restrict__ nsub, int64_t T,
                                 const int* __restrict__ t2e, const int* __restrict__ conn, int64_t Tc,
                                 uint8_t* __restrict__ flag, int* __restrict__ add_cnt) {
     const int per = kind == 0 ? 6 : 4;
@@ -550,7 +576,7 @@ __global__ void k_mark_affected(int kind, int S, const int* __restrict__ split_l
         return;
     }
     const int c = i - S * per;
-    if (c >= NS * per) return;
+    if (c >= *nsub * per) return;
     const int64_t s = T + c / per;
     const int l = c % per;
     const int x = kind == 0 ? t2e[l * Tc + s] : conn[l * Tc + s];
@@ -561,9 +587,14 @@ __global__ void k_mark_affected(int kind, int S, const int* __restrict__ split_l
 __global__ void k_list_count(int kind, const long long* __restrict__ count, const int* __restrict__ aff,
                              const int* __restrict__ off, const int* __restrict__ cnt, const int* __restrict__ pool,
                              const uint8_t* __restrict__ active, const int* __restrict__ add_cnt,
-                             int* __restrict__ keep, int* __restrict__ need) {
+                             int* __restrict__ keep, int* __restrict__ need, int bound) {
     const int i = blockIdx.x * BS + threadIdx.x;
-    if (i >= *count) return;
+    if (i >= bound) return;
+    if (i >= *count) {   // slots past the affected count take no pool space
+        keep[i] = 0;
+        need[i] = 0;
+        return;
+    }
     const int x = aff[i];
     const int o = off[x], n = cnt[x];
     int k = 0;
@@ -594,12 +625,12 @@ __global__ void k_list_write(int kind, const long long* __restrict__ count, cons
     cursor[x] = keep[i];
 }
 
-__global__ void k_list_append(int kind, int NS, int64_t T, const int* __restrict__ t2e,
+__global__ void k_list_append(int kind, const long long* __restrict__ nsub, int64_t T, const int* __restrict__ t2e,
                               const int* __restrict__ conn, int64_t Tc, const int* __restrict__ off,
                               int* __restrict__ pool, int* __restrict__ cursor) {
     const int per = kind == 0 ? 6 : 4;
     const int c = blockIdx.x * BS + threadIdx.x;
-    if (c >= NS * per) return;
+    if (c >= *nsub * per) return;
     const int64_t s = T + c / per;
     const int l = c % per;
     const int x = kind == 0 ? t2e[l * Tc + s] : conn[l * Tc + s];
@@ -710,61 +741,65 @@ int defrag(cem_ctx* c, int kind) {
     return CEM_OK;
 }
 
-// Update the fan (kind 0) or incidence (kind 1) lists of every affected edge / node.
-int update_lists(cem_ctx* c, int kind, int S, int NS, int64_t n_items) {
+// Update the fan (kind 0) or incidence (kind 1) lists of every affected edge /
+// node.  S splits of this step; the number of new sub-elements is read on the
+// device (at most 6 S), n_items bounds the flag range.  The host does not wait
+// unless the pool may be too short for the worst case this step can need.
+int update_lists(cem_ctx* c, int kind, int S, int64_t n_items) {
     const int per = kind == 0 ? 6 : 4;
     uint8_t* flag = kind == 0 ? c->edge_flag : c->node_flag;
     int* off = kind == 0 ? c->fan_off : c->inc_off;
     int* cnt = kind == 0 ? c->fan_cnt : c->inc_cnt;
-    const int64_t nth = (int64_t)(S + NS) * per;
-    k_mark_affected<<<cem_grid(nth, BS), BS, 0, c->stream>>>(kind, S, c->split_list, NS, c->T, c->t2e, c->conn, c->Tc,
-                                                             flag, c->add_cnt);
+    const long long* nsub = c->dcount + CNT_NEWSUB;
+    const int bound = 7 * S * per;   // marks: S parents + at most 6 S sub-elements
+    k_mark_affected<<<cem_grid(bound, BS), BS, 0, c->stream>>>(kind, S, c->split_list, nsub, c->T, c->t2e, c->conn,
+                                                              c->Tc, flag, c->add_cnt);
     cem_launched(c, 1);
     CEM_CK(c, cudaGetLastError());
     int rc = cem_compact_u8(c, flag, n_items, c->aff, CNT_AFFECTED);
     if (rc) return rc;
-    const int64_t bound = nth;   // affected items never exceed the marks
     int* pool = kind == 0 ? c->fan_pool : c->inc_pool;
     k_list_count<<<cem_grid(bound, BS), BS, 0, c->stream>>>(kind, c->dcount + CNT_AFFECTED, c->aff, off, cnt, pool,
-                                                           c->active, c->add_cnt, c->aff_keep, c->aff_new);
+                                                           c->active, c->add_cnt, c->aff_keep, c->aff_new, bound);
     cem_launched(c, 1);
     CEM_CK(c, cudaGetLastError());
-    rc = sync_counts(c);
+    const int need_slot = kind == 0 ? CNT_NEED_FAN : CNT_NEED_INC;
+    rc = cem_scan_i32(c, c->aff_new, bound, c->aff_off, need_slot);
     if (rc) return rc;
-    const int64_t n_aff = c->hcount[CNT_AFFECTED];
-    rc = cem_scan_i32(c, c->aff_new, n_aff, c->aff_off, CNT_POOLNEED);
-    if (rc) return rc;
-    rc = sync_counts(c);
-    if (rc) return rc;
-    const int64_t need = c->hcount[CNT_POOLNEED];
     int64_t& top = kind == 0 ? c->fan_top : c->inc_top;
     const int64_t cap = kind == 0 ? c->fan_cap : c->inc_cap;
-    if (top + need > cap) {
-        rc = defrag(c, kind);
+    // every affected list holds at most 3 times the largest input fan / incidence
+    const int64_t per_list = 3 * (kind == 0 ? c->max_fan0 : std::max(c->max_inc0, c->max_fan0));
+    if (top + (int64_t)bound * per_list > cap) {
+        rc = sync_counts(c);
         if (rc) return rc;
-        if (top + need > cap) return cem_fail(c, CEM_ECAPACITY, "fan/incidence pool exhausted");
+        const int64_t need = c->hcount[need_slot];
+        if (top + need > cap) {
+            rc = defrag(c, kind);
+            if (rc) return rc;
+            if (top + need > cap) return cem_fail(c, CEM_ECAPACITY, "fan/incidence pool exhausted");
+        }
     }
     pool = kind == 0 ? c->fan_pool : c->inc_pool;
-    k_list_write<<<cem_grid(n_aff, BS), BS, 0, c->stream>>>(kind, c->dcount + CNT_AFFECTED, c->aff, top, c->aff_off,
+    k_list_write<<<cem_grid(bound, BS), BS, 0, c->stream>>>(kind, c->dcount + CNT_AFFECTED, c->aff, top, c->aff_off,
                                                            c->aff_keep, c->aff_new, off, cnt, pool, c->active,
                                                            c->cursor);
-    k_list_append<<<cem_grid((int64_t)NS * per, BS), BS, 0, c->stream>>>(kind, NS, c->T, c->t2e, c->conn, c->Tc, off,
-                                                                        pool, c->cursor);
-    k_list_finish<<<cem_grid(n_aff, BS), BS, 0, c->stream>>>(kind, c->dcount + CNT_AFFECTED, c->aff, c->aff_keep, off,
+    k_list_append<<<cem_grid(6 * S * per, BS), BS, 0, c->stream>>>(kind, nsub, c->T, c->t2e, c->conn, c->Tc, off,
+                                                                  pool, c->cursor);
+    k_list_finish<<<cem_grid(bound, BS), BS, 0, c->stream>>>(kind, c->dcount + CNT_AFFECTED, c->aff, c->aff_keep, off,
                                                             cnt, pool, flag, c->add_cnt, c->vol, c->lam, c->mu, c->cl,
                                                             c->cm, c->sumV, c->cl32, c->cm32, c->rho, c->mass,
                                                             c->minv);
     cem_launched(c, 3);
     CEM_CK(c, cudaGetLastError());
-    top += need;
-    return CEM_OK;
+    return CEM_OK;   // the host advances `top` by the need once it next reads the counters
 }
 
 }  // namespace
 
 int cem_launch_front_G(cem_ctx* c) {
     if (c->n_cand > 0) {
-        k_front_G<<<cem_grid(c->n_cand, BS), BS, 0, c->stream>>>(c->cand_list, (int)c->n_cand, c->conn, c->t2e, c->Tc,
+        k_front_G<<<cem_grid(4 * c->n_cand, BS), BS, 0, c->stream>>>(c->cand_list, (int)c->n_cand, c->conn, c->t2e, c->Tc,
                                                                  c->face_nbr, c->side, c->T0, c->X, c->u, c->Nc, c->sig,
                                                                  c->sig32, c->Gc, c->dec_mask, c->dec_G);
         cem_launched(c, 1);
@@ -784,10 +819,13 @@ int cem_launch_front_G(cem_ctx* c) {
 
 // Apply the S splits held in split_list / split_mask / split_Gv (ascending
 // element ids).  step is recorded with each split; book_energy adds Gc * area
-// to the dissipated energy.
+// to the dissipated energy.  Grid sizes come from per-split bounds (at most 8
+// new nodes, 6 sub-elements and 22 new edges per split); the kernels read the
+// actual counts on the device, and the host waits once, at the end.
 int cem_apply_splits(cem_ctx* c, int64_t S64, int64_t step, int book_energy) {
     if (S64 <= 0) return CEM_OK;
     const int S = (int)S64;
+    if (c->n_split_all + S > c->S_cap) return cem_fail(c, CEM_ECAPACITY, "split capacity exhausted");
     int rc;
     // 1. new nodes: one per (cut original edge, side) not yet present
     k_mark_keys<<<cem_grid(S, BS), BS, 0, c->stream>>>(S, c->split_list, c->split_mask, c->t2e, c->Tc, c->node_of_key,
@@ -798,11 +836,9 @@ int cem_apply_splits(cem_ctx* c, int64_t S64, int64_t step, int book_energy) {
     k_create_nodes<<<cem_grid(8 * (int64_t)S, BS), BS, 0, c->stream>>>(
         c->dcount + CNT_NEWNODE, c->new_keys, c->N, c->node_of_key, c->key_flag, c->oe_n0, c->oe_n1, c->X, c->u, c->v,
         c->a, c->fext, c->mass, c->minv, c->inc_off, c->inc_cnt, c->Nc);
-    cem_launched(c, 1);
-    CEM_CK(c, cudaGetLastError());
     // 2. sub-elements, numbered by (parent, local sub index)
     k_sub_count<<<cem_grid(S, BS), BS, 0, c->stream>>>(S, c->split_mask, c->aff_new);
-    cem_launched(c, 1);
+    cem_launched(c, 2);
     CEM_CK(c, cudaGetLastError());
     if ((rc = cem_scan_i32(c, c->aff_new, S, c->sub_off, CNT_NEWSUB))) return rc;
     k_create_subs<<<cem_grid(S, BS), BS, 0, c->stream>>>(
@@ -810,33 +846,25 @@ int cem_apply_splits(cem_ctx* c, int64_t S64, int64_t step, int book_energy) {
         c->active, c->Vg, c->Vg32, c->vol, c->lam, c->mu, c->Tc, c->node_of_key, c->X, c->Nc, c->side, c->split_step,
         c->split_G, c->Gc, c->cand_flag, c->ud_part);
     k_ud_sum<<<1, BS, 0, c->stream>>>(S, c->ud_part, c->Ud);
-    cem_launched(c, 2);
-    CEM_CK(c, cudaGetLastError());
-    if ((rc = sync_counts(c))) return rc;
-    const int64_t NN = c->hcount[CNT_NEWNODE], NS = c->hcount[CNT_NEWSUB];
-    if (c->N + NN > c->Nc || c->T + NS > c->Tc) return cem_fail(c, CEM_ECAPACITY, "node/element capacity exhausted");
     // 3. edges of the sub-elements: parent edges or (new) hashed node pairs
-    const int n_codes = (int)(6 * NS);
-    k_sub_edges<<<cem_grid(n_codes, BS), BS, 0, c->stream>>>(n_codes, c->T, c->N0, c->conn, c->t2e, c->anc, c->Tc,
-                                                             c->hkeys, c->hvals, c->hfirst, c->hash_cap - 1,
-                                                             c->slot_of, c->dcount + CNT_ERR);
-    k_edge_owner<<<cem_grid(n_codes, BS), BS, 0, c->stream>>>(n_codes, c->slot_of, c->hvals, c->hfirst, c->code_flag);
+    const long long* nsub = c->dcount + CNT_NEWSUB;
+    const int codes = 36 * S;
+    k_sub_edges<<<cem_grid(codes, BS), BS, 0, c->stream>>>(nsub, c->T, c->N0, c->conn, c->t2e, c->anc, c->Tc, c->hkeys,
+                                                           c->hvals, c->hfirst, c->hash_cap - 1, c->slot_of,
+                                                           c->dcount + CNT_ERR);
+    k_edge_owner<<<cem_grid(codes, BS), BS, 0, c->stream>>>(nsub, c->slot_of, c->hvals, c->hfirst, c->code_flag);
+    cem_launched(c, 4);
+    CEM_CK(c, cudaGetLastError());
+    if ((rc = cem_compact_u8(c, c->code_flag, codes, c->code_rank, CNT_NEWEDGE))) return rc;
+    k_edge_assign<<<cem_grid(codes, BS), BS, 0, c->stream>>>(c->dcount + CNT_NEWEDGE, c->code_rank, c->E, c->slot_of,
+                                                             c->hvals, c->hfirst, c->code_flag, c->fan_off,
+                                                             c->fan_cnt, c->cl, c->cm, c->sumV, c->cl32, c->cm32);
+    k_edge_resolve<<<cem_grid(codes, BS), BS, 0, c->stream>>>(nsub, c->T, c->slot_of, c->hvals, c->t2e, c->Tc);
     cem_launched(c, 2);
     CEM_CK(c, cudaGetLastError());
-    if ((rc = cem_compact_u8(c, c->code_flag, n_codes, c->code_rank, CNT_NEWEDGE))) return rc;
-    k_edge_assign<<<cem_grid(n_codes, BS), BS, 0, c->stream>>>(c->dcount + CNT_NEWEDGE, c->code_rank, c->E, c->slot_of,
-                                                               c->hvals, c->hfirst, c->code_flag, c->fan_off,
-                                                               c->fan_cnt, c->cl, c->cm, c->sumV, c->cl32, c->cm32);
-    k_edge_resolve<<<cem_grid(n_codes, BS), BS, 0, c->stream>>>(n_codes, c->T, c->slot_of, c->hvals, c->t2e, c->Tc);
-    cem_launched(c, 2);
-    CEM_CK(c, cudaGetLastError());
-    if ((rc = sync_counts(c))) return rc;
-    if (c->hcount[CNT_ERR]) return cem_fail(c, CEM_ECAPACITY, "edge hash table full");
-    const int64_t NE = c->hcount[CNT_NEWEDGE];
-    if (c->E + NE > c->Ec) return cem_fail(c, CEM_ECAPACITY, "edge capacity exhausted");
     // 4. fans of affected edges, incidence (and mass) of affected nodes
-    if ((rc = update_lists(c, 0, S, (int)NS, c->E + NE))) return rc;
-    if ((rc = update_lists(c, 1, S, (int)NS, c->N + NN))) return rc;
+    if ((rc = update_lists(c, 0, S, c->E + 22 * (int64_t)S))) return rc;
+    if ((rc = update_lists(c, 1, S, c->N + 8 * (int64_t)S))) return rc;
     // 5. crack-front candidates
     k_cand_mark<<<cem_grid(S, BS), BS, 0, c->stream>>>(S, c->split_list, c->split_mask, c->face_nbr, c->T0, c->side,
                                                        c->cand_flag);
@@ -844,6 +872,12 @@ int cem_apply_splits(cem_ctx* c, int64_t S64, int64_t step, int book_energy) {
     CEM_CK(c, cudaGetLastError());
     if ((rc = cem_compact_u8(c, c->cand_flag, c->T0, c->cand_list, CNT_CAND))) return rc;
     if ((rc = sync_counts(c))) return rc;
+    if (c->hcount[CNT_ERR]) return cem_fail(c, CEM_ECAPACITY, "edge hash table full");
+    const int64_t NN = c->hcount[CNT_NEWNODE], NS = c->hcount[CNT_NEWSUB], NE = c->hcount[CNT_NEWEDGE];
+    if (c->N + NN > c->Nc || c->T + NS > c->Tc || c->E + NE > c->Ec)
+        return cem_fail(c, CEM_ECAPACITY, "node/element/edge capacity exhausted");
+    c->fan_top += c->hcount[CNT_NEED_FAN];
+    c->inc_top += c->hcount[CNT_NEED_INC];
     c->N += NN;
     c->T += NS;
     c->E += NE;

@@ -197,12 +197,14 @@ __device__ __forceinline__ void node_disp_diff<float>(const double*, const float
         for (int c = 0; c < 3; ++c) d[a][c] = (hi[a + 1][c] - hi[0][c]) + (lo[a + 1][c] - lo[0][c]);
 }
 
+// Inactive (split) element slots are skipped: no fan or incidence list refers to them.
 template <class R>
 __global__ void __launch_bounds__(BS) k_strain(const double* __restrict__ u, const float* __restrict__ uhl,
                                                int64_t Nc, const int* __restrict__ conn, const R* __restrict__ Vg,
-                                               int64_t Tc, int64_t T, R* __restrict__ h) {
+                                               const uint8_t* __restrict__ active, int64_t Tc, int64_t T,
+                                               R* __restrict__ h) {
     int64_t j = (int64_t)blockIdx.x * BS + threadIdx.x;
-    if (j >= T) return;
+    if (j >= T || !active[j]) return;
     const int n[4] = {conn[j], conn[Tc + j], conn[2 * Tc + j], conn[3 * Tc + j]};
     R d[3][3];   // d[a][c] = u_{a+1,c} - u_{0,c}
     node_disp_diff<R>(u, uhl, Nc, n, d);
@@ -242,9 +244,10 @@ __global__ void __launch_bounds__(BS) k_edge_stress(const R* __restrict__ h, con
 
 template <class R>
 __global__ void __launch_bounds__(BS) k_force(const R* __restrict__ sig, const int* __restrict__ t2e,
-                                              const R* __restrict__ Vg, int64_t Tc, int64_t T, R* __restrict__ fp) {
+                                              const R* __restrict__ Vg, const uint8_t* __restrict__ active,
+                                              int64_t Tc, int64_t T, R* __restrict__ fp) {
     int64_t j = (int64_t)blockIdx.x * BS + threadIdx.x;
-    if (j >= T) return;
+    if (j >= T || !active[j]) return;
     R S[6] = {0, 0, 0, 0, 0, 0};
 #pragma unroll
     for (int l = 0; l < 6; ++l) {
@@ -507,11 +510,11 @@ int cem_launch_split_u(cem_ctx* c) {
 
 int cem_launch_strain(cem_ctx* c) {
     if (mixed(c))
-        k_strain<float><<<cem_grid(c->T, BS), BS, 0, c->stream>>>(c->u, c->uhl, c->Nc, c->conn, c->Vg32, c->Tc, c->T,
-                                                                  c->h32);
+        k_strain<float><<<cem_grid(c->T, BS), BS, 0, c->stream>>>(c->u, c->uhl, c->Nc, c->conn, c->Vg32, c->active, c->Tc,
+                                                                  c->T, c->h32);
     else
-        k_strain<double><<<cem_grid(c->T, BS), BS, 0, c->stream>>>(c->u, nullptr, c->Nc, c->conn, c->Vg, c->Tc, c->T,
-                                                                   c->h);
+        k_strain<double><<<cem_grid(c->T, BS), BS, 0, c->stream>>>(c->u, nullptr, c->Nc, c->conn, c->Vg, c->active, c->Tc,
+                                                                   c->T, c->h);
     cem_launched(c);
     CEM_CK(c, cudaGetLastError());
     return CEM_OK;
@@ -531,9 +534,11 @@ int cem_launch_edge_stress(cem_ctx* c) {
 
 int cem_launch_force(cem_ctx* c) {
     if (mixed(c))
-        k_force<float><<<cem_grid(c->T, BS), BS, 0, c->stream>>>(c->sig32, c->t2e, c->Vg32, c->Tc, c->T, c->fp32);
+        k_force<float><<<cem_grid(c->T, BS), BS, 0, c->stream>>>(c->sig32, c->t2e, c->Vg32, c->active, c->Tc, c->T,
+                                                                 c->fp32);
     else
-        k_force<double><<<cem_grid(c->T, BS), BS, 0, c->stream>>>(c->sig, c->t2e, c->Vg, c->Tc, c->T, c->fp);
+        k_force<double><<<cem_grid(c->T, BS), BS, 0, c->stream>>>(c->sig, c->t2e, c->Vg, c->active, c->Tc, c->T,
+                                                                  c->fp);
     cem_launched(c);
     CEM_CK(c, cudaGetLastError());
     return CEM_OK;
