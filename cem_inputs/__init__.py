@@ -1,3 +1,3 @@
 """Seeded synthetic specimens shared, as input data only, by the CUDA path and the oracle."""
-from .mesh import (Workload, kuhn_block, plate_small, plate_medium, plate_large,
+from .mesh import (Workload, kuhn_block, plate_small, plate_medium, plate_large, union, ensemble, ensemble_members,
                    scaled_plate, splitmix64, uniform01, normal01, lognormal)

@@ -209,3 +209,63 @@ def scaled_plate(nx: int, ny: int, nz: int, **kw) -> Workload:
     """The 0.1 x 0.04 x 0.01 m notched block at an arbitrary resolution."""
     kw.setdefault("notch_length", 0.05)
     return kuhn_block(nx, ny, nz, 0.1, 0.04, 0.01, **kw)
+
+
+# ---------------------------------------------------------------------------
+# Ensembles: many independent specimens as one disjoint-union mesh.
+# ---------------------------------------------------------------------------
+
+def union(workloads, name="union", spacing=0.05):
+    """Disjoint union of specimens.  Instance i is translated by i * spacing in z
+    (rigid shift, no effect on the mechanics) so that the pieces never overlap.
+    Returns a Workload with an extra ``tet_instance`` array and per-instance
+    node / element offsets in ``params``."""
+    X, tets, tf, tv, E, Gc, nt, ns, inst = [], [], [], [], [], [], [], [], []
+    noff, toff = [0], [0]
+    nu, rho = workloads[0].nu, workloads[0].rho
+    for i, w in enumerate(workloads):
+        if w.nu != nu or w.rho != rho:
+            raise ValueError("instances of one union share nu and rho")
+        n0, t0 = noff[-1], toff[-1]
+        X.append(w.X + np.array([0.0, 0.0, i * spacing]))
+        tets.append(w.tets + n0)
+        tf.append(w.tfaces + n0)
+        tv.append(w.tvec)
+        E.append(w.E)
+        Gc.append(w.Gc)
+        nt.append(w.notch_tet + t0)
+        ns.append(w.notch_side)
+        inst.append(np.full(w.n_tets, i, dtype=np.int32))
+        noff.append(n0 + w.n_nodes)
+        toff.append(t0 + w.n_tets)
+    u = Workload(name=name, X=np.concatenate(X), tets=np.concatenate(tets).astype(np.int32),
+                 tfaces=np.concatenate(tf).astype(np.int32), tvec=np.concatenate(tv),
+                 E=np.concatenate(E), Gc=np.concatenate(Gc), nu=nu, rho=rho,
+                 notch_tet=np.concatenate(nt).astype(np.int32), notch_side=np.concatenate(ns).astype(np.uint8),
+                 params=dict(node_offsets=noff, tet_offsets=toff, n_instances=len(workloads), spacing=spacing))
+    u.tet_instance = np.concatenate(inst)
+    return u
+
+
+def ensemble_members(n=256, seed=4, t_min=5_000, t_max=200_000):
+    """Notched blocks (0.1 x 0.04 x 0.01 m) of seeded random size and material:
+    element count ~ U[t_min, t_max], E ~ U[25, 40] GPa, Gc ~ U[2, 5] J/m^2,
+    traction ~ U[0.5, 1.5] MPa; cells n_z = max(1, round s), n_y = 2 max(1, round 2s),
+    n_x = max(2, round(T / (6 n_y n_z))) with s = (T / 240)^(1/3)."""
+    r = uniform01(seed, 4 * n, stream=7).reshape(n, 4)
+    out = []
+    for i in range(n):
+        T = t_min + r[i, 0] * (t_max - t_min)
+        s = (T / 240.0) ** (1.0 / 3.0)
+        nz = max(1, int(round(s)))
+        ny = 2 * max(1, int(round(2 * s)))
+        nx = max(2, int(round(T / (6 * ny * nz))))
+        out.append(kuhn_block(nx, ny, nz, 0.1, 0.04, 0.01, notch_length=0.05,
+                              E=25e9 + r[i, 1] * 15e9, Gc=2.0 + r[i, 2] * 3.0,
+                              traction=0.5e6 + r[i, 3] * 1.0e6, name="member_%d" % i))
+    return out
+
+
+def ensemble(n=256, seed=4):
+    """The 256-specimen ensemble (about 2.6e7 elements) as one union mesh."""
+    return union(ensemble_members(n, seed), name="ensemble_%d_seed%d" % (n, seed))

@@ -99,6 +99,11 @@ typedef struct cem_mesh_desc {
     cem_alloc_fn   alloc;        /* NULL: cudaMalloc                                   */
     cem_free_fn    free;         /* NULL: cudaFree                                     */
     void*          alloc_user;   /* passed to alloc/free                               */
+    int64_t        n_instances;  /* <= 1: one specimen.  > 1: the mesh is a disjoint   */
+                                 /* union of independent specimens (an ensemble)       */
+    const int32_t* tet_instance; /* T specimen ids in [0, n_instances) (NULL if <= 1); */
+                                 /* the elements of one specimen share no node with    */
+                                 /* another's; each specimen gets its own time step    */
 } cem_mesh_desc;
 
 typedef struct cem_ctx cem_ctx;
@@ -140,7 +145,8 @@ int cem_mesh_create(const cem_mesh_desc* d, cem_ctx** out);
  * modulus E [Pa] (nE = 1: uniform, nE = n_tets: per input element) and
  * critical energy release rate Gc [J/m^2] (nGc = 1 or n_tets).  Computes the
  * Lame constants, fan-averaged elasticity, lumped mass (Eq. 11), the time
- * step when automatic, and a_0 = M^-1 (f_ext - f_int(0)).  Required before
+ * step when automatic (per specimen of an ensemble, from its own elements),
+ * and a_0 = M^-1 (f_ext - f_int(0)).  Required before
  * the first cem_step; CEM_ESTATE afterwards. */
 int cem_set_material(cem_ctx* ctx, double rho, double nu,
                      const double* E, int64_t nE, const double* Gc, int64_t nGc);
@@ -155,6 +161,10 @@ int cem_step(cem_ctx* ctx, int64_t n);
 
 /* Energies of the current state (deterministic reductions). */
 int cem_energy(cem_ctx* ctx, cem_energy_t* out);
+
+/* Energies of one specimen of an ensemble (instance in [0, n_instances); 0
+ * for a single specimen).  `time` is step * that specimen's time step. */
+int cem_energy_instance(cem_ctx* ctx, int64_t instance, cem_energy_t* out);
 
 /* Split original elements sorted by (step, element id).  The notch elements
  * appear with step = -1 and G = 0.  Writes min(count, cap) records to the

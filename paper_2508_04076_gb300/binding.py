@@ -24,7 +24,7 @@ ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_void_p)
 
 EXPORTED = ["cem_mesh_create", "cem_set_material", "cem_step", "cem_energy", "cem_crack_state",
-            "cem_get_field", "cem_info", "cem_profile", "cem_profile_read", "cem_probe_fp64_fma", "cem_destroy", "cem_last_error"]
+            "cem_get_field", "cem_info", "cem_energy_instance", "cem_profile", "cem_profile_read", "cem_probe_fp64_fma", "cem_destroy", "cem_last_error"]
 KERNELS = ["predict", "strain", "edge_stress", "force", "node_update", "front_G", "split"]
 
 
@@ -38,6 +38,7 @@ class MeshDesc(C.Structure):
         ("split_enabled", C.c_int32), ("split_capacity", C.c_int64),
         ("stream", C.c_void_p), ("device", C.c_int32),
         ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_user", C.c_void_p),
+        ("n_instances", C.c_int64), ("tet_instance", C.POINTER(C.c_int32)),
     ]
 
 
@@ -73,6 +74,7 @@ def load_library(build: bool = True):
                                      C.POINTER(C.c_double), C.c_int64]
     lib.cem_step.argtypes = [P, C.c_int64]
     lib.cem_energy.argtypes = [P, C.POINTER(Energy)]
+    lib.cem_energy_instance.argtypes = [P, C.c_int64, C.POINTER(Energy)]
     lib.cem_crack_state.argtypes = [P, C.POINTER(C.c_int64), C.POINTER(C.c_int32), C.POINTER(C.c_int8),
                                     C.POINTER(C.c_uint8), C.POINTER(C.c_int64), C.POINTER(C.c_double), C.c_int64]
     lib.cem_get_field.argtypes = [P, C.c_int, C.POINTER(C.c_double), C.c_int64, C.POINTER(C.c_int64)]
@@ -115,7 +117,7 @@ class CEM:
 
     def __init__(self, X, tets, tfaces=None, tvec=None, notch_tet=None, notch_side=None, *,
                  dt=0.0, cfl_factor=0.5, split_enabled=True, split_capacity=0, device=0,
-                 stream=None, torch_allocator=True, precision="fp64"):
+                 stream=None, torch_allocator=True, precision="fp64", tet_instance=None):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("the CEM library needs a CUDA GPU; no CPU fallback exists")
@@ -131,7 +133,9 @@ class CEM:
         tvec = np.ascontiguousarray(np.zeros((0, 3)) if tvec is None else tvec, dtype=np.float64).reshape(-1, 3)
         notch_tet = np.ascontiguousarray([] if notch_tet is None else notch_tet, dtype=np.int32).ravel()
         notch_side = np.ascontiguousarray([] if notch_side is None else notch_side, dtype=np.uint8).ravel()
-        self._keep = (X, tets, tfaces, tvec, notch_tet, notch_side)
+        inst = None if tet_instance is None else np.ascontiguousarray(tet_instance, dtype=np.int32).ravel()
+        self.n_instances = 1 if inst is None else int(inst.max()) + 1
+        self._keep = (X, tets, tfaces, tvec, notch_tet, notch_side, inst)
         d = MeshDesc()
         d.n_nodes, d.n_tets = X.shape[0], tets.shape[0]
         d.X, d.tets = _ptr(X, C.c_double), _ptr(tets, C.c_int32)
@@ -144,6 +148,8 @@ class CEM:
         d.dt, d.cfl_factor = float(dt), float(cfl_factor)
         d.split_enabled, d.split_capacity = int(bool(split_enabled)), int(split_capacity)
         d.stream, d.device = self.stream, self.device
+        if inst is not None and self.n_instances > 1:
+            d.n_instances, d.tet_instance = self.n_instances, _ptr(inst, C.c_int32)
         if torch_allocator:
             dev = self.device
 
@@ -171,6 +177,7 @@ class CEM:
     @classmethod
     def from_workload(cls, w, **kw):
         """Context for a cem_inputs.Workload with its material set."""
+        kw.setdefault("tet_instance", getattr(w, "tet_instance", None))
         sim = cls(w.X, w.tets, w.tfaces, w.tvec, w.notch_tet, w.notch_side, **kw)
         sim.set_material(w.rho, w.nu, w.E, w.Gc)
         return sim
@@ -195,6 +202,12 @@ class CEM:
     def energy(self) -> dict:
         e = Energy()
         self._check(self._lib.cem_energy(self._ctx, C.byref(e)))
+        return {k: getattr(e, k) for k, _ in Energy._fields_}
+
+    def energy_instance(self, i) -> dict:
+        """Energies of specimen i of an ensemble."""
+        e = Energy()
+        self._check(self._lib.cem_energy_instance(self._ctx, int(i), C.byref(e)))
         return {k: getattr(e, k) for k, _ in Energy._fields_}
 
     def info(self) -> dict:

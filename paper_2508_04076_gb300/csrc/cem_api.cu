@@ -213,6 +213,26 @@ int create_impl(const cem_mesh_desc* d, cem_ctx* c) {
             swapped[t] = 1;
         }
     }
+    // ensembles: element -> specimen map; every node must belong to one specimen
+    std::vector<int> node_inst;
+    c->n_inst = d->n_instances > 1 ? d->n_instances : 1;
+    if (c->n_inst > 1) {
+        if (!d->tet_instance) return cem_fail(c, CEM_EINVAL, "n_instances > 1 needs tet_instance");
+        if (c->n_inst >= (1ll << 30)) return cem_fail(c, CEM_EINVAL, "too many instances");
+        c->h_tet_inst.assign(d->tet_instance, d->tet_instance + T0);
+        node_inst.assign(N0, -1);
+        for (int64_t t = 0; t < T0; ++t) {
+            const int i = c->h_tet_inst[t];
+            if (i < 0 || i >= c->n_inst) return cem_fail(c, CEM_EINVAL, "tet_instance out of range");
+            for (int l = 0; l < 4; ++l) {
+                int& ni = node_inst[conn[t * 4 + l]];
+                if (ni >= 0 && ni != i) return cem_fail(c, CEM_EINVAL, "a node is shared by two instances");
+                ni = i;
+            }
+        }
+        for (int64_t q = 0; q < N0; ++q)
+            if (node_inst[q] < 0) node_inst[q] = 0;   // a node of no element: any specimen
+    }
     HostTopo H;
     if (int rc = build_topology(c, conn, H)) return rc;
     const int64_t E0 = c->E0;
@@ -278,7 +298,10 @@ int create_impl(const cem_mesh_desc* d, cem_ctx* c) {
     ok = ok && dalloc(c, c->node_of_key, 2 * E0) && dalloc(c, c->cand_flag, T0) && dalloc(c, c->cand_list, T0);
     ok = ok && dalloc(c, c->dec_mask, T0) && dalloc(c, c->dec_G, T0) && dalloc(c, c->split_list, T0);
     ok = ok && dalloc(c, c->split_mask, T0) && dalloc(c, c->split_Gv, T0) && dalloc(c, c->ud_part, T0);
-    ok = ok && dalloc(c, c->Ud, 1);
+    ok = ok && dalloc(c, c->Ud, 1) && dalloc(c, c->ud_tet, T0);
+    if (c->n_inst > 1)
+        ok = ok && dalloc(c, c->node_inst, Nc) && dalloc(c, c->dtn, Nc) && dalloc(c, c->tet_inst, T0) &&
+             dalloc(c, c->inst_dt_dev, c->n_inst);
     ok = ok && dalloc(c, c->hkeys, c->hash_cap) && dalloc(c, c->hvals, c->hash_cap) && dalloc(c, c->hfirst, c->hash_cap);
     ok = ok && dalloc(c, c->key_flag, 2 * E0) && dalloc(c, c->edge_flag, Ec) && dalloc(c, c->node_flag, Nc);
     ok = ok && dalloc(c, c->code_flag, n_codes_cap) && dalloc(c, c->new_keys, 2 * E0) && dalloc(c, c->sub_off, T0);
@@ -324,6 +347,13 @@ int create_impl(const cem_mesh_desc* d, cem_ctx* c) {
     CEM_CK(c, cudaMemsetAsync(c->cand_flag, 0, T0, s));
     CEM_CK(c, cudaMemsetAsync(c->dec_mask, 0, T0, s));
     CEM_CK(c, cudaMemsetAsync(c->Ud, 0, sizeof(double), s));
+    CEM_CK(c, cudaMemsetAsync(c->ud_tet, 0, T0 * sizeof(double), s));
+    if (c->n_inst > 1) {
+        CEM_CK(c, cudaMemsetAsync(c->dtn, 0, Nc * sizeof(double), s));
+        if (int rc = upload(c, c->node_inst, node_inst.data(), N0)) return rc;
+        if (int rc = upload(c, c->tet_inst, c->h_tet_inst.data(), T0)) return rc;
+        CEM_CK(c, cudaStreamSynchronize(s));
+    }
     CEM_CK(c, cudaMemsetAsync(c->hkeys, 0xFF, c->hash_cap * sizeof(unsigned long long), s));
     CEM_CK(c, cudaMemsetAsync(c->hvals, 0xFF, c->hash_cap * sizeof(int), s));
     CEM_CK(c, cudaMemsetAsync(c->hfirst, 0x7F, c->hash_cap * sizeof(int), s));
@@ -423,6 +453,11 @@ int create_impl(const cem_mesh_desc* d, cem_ctx* c) {
         CEM_CK(c, cudaMemcpyAsync(hm.data(), c->dec_G, T0 * sizeof(double), cudaMemcpyDeviceToHost, s));
         CEM_CK(c, cudaStreamSynchronize(s));
         c->h_min = *std::min_element(hm.begin(), hm.end());
+        c->inst_hmin.assign(c->n_inst, 1e300);
+        for (int64_t t = 0; t < T0; ++t) {
+            const int i = c->n_inst > 1 ? c->h_tet_inst[t] : 0;
+            c->inst_hmin[i] = std::min(c->inst_hmin[i], hm[t]);
+        }
     }
 
     // notch: the run-time split path with no energy booked
@@ -556,9 +591,24 @@ int cem_set_material(cem_ctx* c, double rho, double nu, const double* E, int64_t
         return rc;
     if (int rc = cem_launch_edge_coeffs(c, nullptr, 0)) return rc;
     if (int rc = cem_launch_node_mass(c, nullptr, 0)) return rc;
-    const double lam = Emax * nu / ((1 + nu) * (1 - 2 * nu)), mu = Emax / (2 * (1 + nu));
-    const double c_d = std::sqrt((lam + 2 * mu) / rho);
-    c->dt = c->dt_req > 0 ? c->dt_req : c->cfl * c->h_min / (2.0 * c_d);
+    // time step of every specimen: cfl * h_min / (2 c_d) at its largest modulus
+    std::vector<double> Ei(c->n_inst, 0.0);
+    for (int64_t t = 0; t < c->T0; ++t) {
+        const int i = c->n_inst > 1 ? c->h_tet_inst[t] : 0;
+        Ei[i] = std::max(Ei[i], nE == 1 ? E[0] : E[t]);
+    }
+    (void)Emax;
+    c->inst_dt.assign(c->n_inst, 0.0);
+    for (int64_t i = 0; i < c->n_inst; ++i) {
+        const double lam = Ei[i] * nu / ((1 + nu) * (1 - 2 * nu)), mu = Ei[i] / (2 * (1 + nu));
+        const double c_d = std::sqrt((lam + 2 * mu) / rho);
+        c->inst_dt[i] = c->dt_req > 0 ? c->dt_req : c->cfl * c->inst_hmin[i] / (2.0 * c_d);
+    }
+    c->dt = *std::min_element(c->inst_dt.begin(), c->inst_dt.end());
+    if (c->n_inst > 1) {
+        if (int rc = upload(c, c->inst_dt_dev, c->inst_dt.data(), c->n_inst)) return rc;
+        if (int rc = cem_launch_node_dt(c)) return rc;
+    }
     // a_0 = M^-1 (f_ext - f_int(u_0))
     int rc;
     if ((rc = cem_launch_strain(c)) || (rc = cem_launch_edge_stress(c)) || (rc = cem_launch_force(c)) ||
@@ -626,6 +676,39 @@ int cem_energy(cem_ctx* c, cem_energy_t* out) {
     out->step = c->step;
     out->time = (double)c->step * c->dt;
     out->n_split = c->n_split_run;
+    return CEM_OK;
+}
+
+int cem_energy_instance(cem_ctx* c, int64_t instance, cem_energy_t* out) {
+    if (!c || !out) return CEM_EINVAL;
+    if (instance < 0 || instance >= c->n_inst) return cem_fail(c, CEM_EINVAL, "instance out of range");
+    if (!c->material) return cem_fail(c, CEM_ESTATE, "no material");
+    if (int rc = select_device(c)) return rc;
+    int rc;
+    if ((rc = cem_launch_split_u(c)) || (rc = cem_launch_strain(c)) || (rc = cem_launch_edge_stress(c))) return rc;
+    double r[5];
+    if ((rc = cem_energy_reduce_instance(c, (int)instance, r))) return rc;
+    const double dt = c->inst_dt[instance];
+    int64_t nsplit = 0;
+    if (c->n_inst > 1) {
+        // run-time splits of this specimen: counted on the host from the crack state
+        std::vector<uint8_t> sd(c->T0);
+        std::vector<int> st(c->T0);
+        CEM_CK(c, cudaMemcpy(sd.data(), c->side, c->T0, cudaMemcpyDeviceToHost));
+        CEM_CK(c, cudaMemcpy(st.data(), c->split_step, c->T0 * sizeof(int), cudaMemcpyDeviceToHost));
+        for (int64_t t = 0; t < c->T0; ++t)
+            if (sd[t] && st[t] >= 0 && c->h_tet_inst[t] == instance) ++nsplit;
+    } else {
+        nsplit = c->n_split_run;
+    }
+    out->kinetic = r[0];
+    out->ext_work = r[1];
+    out->strain = r[3];
+    out->dissipated = r[4];
+    out->modified = r[0] + r[3] - r[1] - dt * dt / 8.0 * r[2];
+    out->step = c->step;
+    out->time = (double)c->step * dt;
+    out->n_split = nsplit;
     return CEM_OK;
 }
 

@@ -61,6 +61,9 @@ struct cem_ctx {
     int64_t n_active = 0;
     int64_t fan_cap = 0, fan_top = 0, inc_cap = 0, inc_top = 0;
     int64_t max_fan0 = 0, max_inc0 = 0;   // largest fan / node incidence of the input mesh
+    int64_t n_inst = 1;                   // specimens in the mesh (ensemble when > 1)
+    std::vector<int> h_tet_inst;          // host copy of the element -> specimen map
+    std::vector<double> inst_hmin, inst_dt;
     int64_t hash_cap = 0;
     int64_t scan_blocks_cap = 0;
     int64_t bytes = 0;
@@ -92,6 +95,11 @@ struct cem_ctx {
     int *fan_off = nullptr, *fan_cnt = nullptr, *fan_pool = nullptr, *fan_pool2 = nullptr;
     double *cl = nullptr, *cm = nullptr, *sumV = nullptr, *sig = nullptr;
     float *cl32 = nullptr, *cm32 = nullptr, *sig32 = nullptr;
+    // ensembles: specimen of every node / input element, per-node time step
+    int *node_inst = nullptr, *tet_inst = nullptr;
+    double* dtn = nullptr;
+    double* inst_dt_dev = nullptr;
+    double* ud_tet = nullptr;          // [T0] dissipated energy booked by each split input element
     // cracks
     int* face_nbr = nullptr;
     uint8_t* side = nullptr;
@@ -167,6 +175,8 @@ int cem_launch_edge_coeffs(cem_ctx* c, const int* list, int64_t n);     // list 
 int cem_launch_node_mass(cem_ctx* c, const int* list, int64_t n);       // list == NULL: all N
 int cem_launch_material(cem_ctx* c, const double* E_dev, int nE, const double* Gc_dev, int nGc);
 int cem_energy_reduce(cem_ctx* c, double out[4]);
+int cem_energy_reduce_instance(cem_ctx* c, int inst, double out[5]);   // + U_d of the specimen
+int cem_launch_node_dt(cem_ctx* c);                                     // dtn[i] = dt of node i's specimen
 int cem_launch_check_finite(cem_ctx* c);
 
 // ---------------------------------------------------------------- crack path (cem_crack.cu)

@@ -271,7 +271,8 @@ __global__ void k_create_nodes(const long long* __restrict__ count, const int* _
                                const int* __restrict__ oe_n0, const int* __restrict__ oe_n1, double* __restrict__ X,
                                double* __restrict__ u, double* __restrict__ v, double* __restrict__ a,
                                double* __restrict__ fext, double* __restrict__ mass, double* __restrict__ minv,
-                               int* __restrict__ inc_off, int* __restrict__ inc_cnt, int64_t Nc) {
+                               int* __restrict__ inc_off, int* __restrict__ inc_cnt, int64_t Nc,
+                               int* __restrict__ node_inst, double* __restrict__ dtn) {
     const int i = blockIdx.x * BS + threadIdx.x;
     if (i >= *count) return;
     const int key = new_keys[i];
@@ -291,6 +292,8 @@ __global__ void k_create_nodes(const long long* __restrict__ count, const int* _
     minv[id] = 0.0;
     inc_off[id] = 0;
     inc_cnt[id] = 0;
+    if (node_inst) node_inst[id] = node_inst[n0];
+    if (dtn) dtn[id] = dtn[n0];
 }
 
 // ------------------------------------------------------------------ sub-elements
@@ -336,7 +339,7 @@ __global__ void k_create_subs(int S, int64_t T, const int* __restrict__ split_li
                               const double* __restrict__ X, int64_t Nc, uint8_t* __restrict__ side,
                               int* __restrict__ split_step, double* __restrict__ split_G,
                               const double* __restrict__ Gc, uint8_t* __restrict__ cand_flag,
-                              double* __restrict__ ud_part) {
+                              double* __restrict__ ud_part, double* __restrict__ ud_tet) {
     const int i = blockIdx.x * BS + threadIdx.x;
     if (i >= S) return;
     const int p = split_list[i];
@@ -454,6 +457,7 @@ __global__ void k_create_subs(int S, int64_t T, const int* __restrict__ split_li
     split_G[p] = split_Gv[i];
     cand_flag[p] = 0;
     ud_part[i] = book ? Gc[p] * area : 0.0;
+    ud_tet[p] = ud_part[i];
 }
 
 __global__ void k_ud_sum(int S, const double* __restrict__ part, double* __restrict__ Ud) {
@@ -835,7 +839,7 @@ int cem_apply_splits(cem_ctx* c, int64_t S64, int64_t step, int book_energy) {
     if ((rc = cem_compact_u8(c, c->key_flag, 2 * c->E0, c->new_keys, CNT_NEWNODE))) return rc;
     k_create_nodes<<<cem_grid(8 * (int64_t)S, BS), BS, 0, c->stream>>>(
         c->dcount + CNT_NEWNODE, c->new_keys, c->N, c->node_of_key, c->key_flag, c->oe_n0, c->oe_n1, c->X, c->u, c->v,
-        c->a, c->fext, c->mass, c->minv, c->inc_off, c->inc_cnt, c->Nc);
+        c->a, c->fext, c->mass, c->minv, c->inc_off, c->inc_cnt, c->Nc, c->node_inst, c->dtn);
     // 2. sub-elements, numbered by (parent, local sub index)
     k_sub_count<<<cem_grid(S, BS), BS, 0, c->stream>>>(S, c->split_mask, c->aff_new);
     cem_launched(c, 2);
@@ -844,7 +848,7 @@ int cem_apply_splits(cem_ctx* c, int64_t S64, int64_t step, int book_energy) {
     k_create_subs<<<cem_grid(S, BS), BS, 0, c->stream>>>(
         S, c->T, c->split_list, c->split_mask, c->split_Gv, c->sub_off, step, book_energy, c->conn, c->t2e, c->anc,
         c->active, c->Vg, c->Vg32, c->vol, c->lam, c->mu, c->Tc, c->node_of_key, c->X, c->Nc, c->side, c->split_step,
-        c->split_G, c->Gc, c->cand_flag, c->ud_part);
+        c->split_G, c->Gc, c->cand_flag, c->ud_part, c->ud_tet);
     k_ud_sum<<<1, BS, 0, c->stream>>>(S, c->ud_part, c->Ud);
     // 3. edges of the sub-elements: parent edges or (new) hashed node pairs
     const long long* nsub = c->dcount + CNT_NEWSUB;

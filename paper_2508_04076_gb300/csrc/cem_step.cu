@@ -121,11 +121,17 @@ __global__ void __launch_bounds__(BS) k_geometry(const double* __restrict__ X, i
 }
 
 // uhl (mixed only): per node 8 floats: hi.xyz, lo.xyz, 2 pad; u = hi + lo to ~48 bits.
+// dtn (ensembles): per-node time step of the node's specimen; NULL: dt for all.
 __global__ void __launch_bounds__(BS) k_predict(double* __restrict__ u, const double* __restrict__ v,
                                                 const double* __restrict__ a, int64_t Nc, int64_t N,
-                                                double dt, double hdt2, float* __restrict__ uhl) {
+                                                double dt, double hdt2, float* __restrict__ uhl,
+                                                const double* __restrict__ dtn) {
     int64_t i = (int64_t)blockIdx.x * BS + threadIdx.x;
     if (i >= N) return;
+    if (dtn) {
+        dt = dtn[i];
+        hdt2 = 0.5 * dt * dt;
+    }
     double un[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
@@ -293,9 +299,10 @@ __global__ void __launch_bounds__(BS) k_node_update(const R* __restrict__ fp, co
                                                     const int* __restrict__ inc_cnt, const int* __restrict__ inc_pool,
                                                     const double* __restrict__ fext, const double* __restrict__ minv,
                                                     double* __restrict__ v, double* __restrict__ a, int64_t Nc,
-                                                    int64_t N, double hdt, int first) {
+                                                    int64_t N, double hdt, int first, const double* __restrict__ dtn) {
     int64_t i = (int64_t)blockIdx.x * BS + threadIdx.x;
     if (i >= N) return;
+    if (dtn) hdt = 0.5 * dtn[i];
     const int off = inc_off[i], cnt = inc_cnt[i];
     double f[3];
     if constexpr (sizeof(R) == 8) {
@@ -452,6 +459,74 @@ __global__ void __launch_bounds__(RB) k_energy_edges(const R* __restrict__ h, co
     block_sum_store<1>(x, part + 3 * RG);
 }
 
+// Energies of one specimen of an ensemble: the same reductions restricted to
+// its nodes, its edges (specimen of the edge's first fan element) and its
+// split input elements.
+__global__ void __launch_bounds__(RB) k_energy_nodes_inst(const double* __restrict__ u, const double* __restrict__ v,
+                                                          const double* __restrict__ a,
+                                                          const double* __restrict__ mass,
+                                                          const double* __restrict__ fext,
+                                                          const int* __restrict__ node_inst, int inst, int64_t Nc,
+                                                          int64_t N, double* __restrict__ part) {
+    double x[3] = {0, 0, 0};
+    for (int64_t i = (int64_t)blockIdx.x * RB + threadIdx.x; i < N; i += (int64_t)RG * RB) {
+        if (node_inst && node_inst[i] != inst) continue;
+        const double m = mass[i];
+        double vv = 0, fu = 0, aa = 0;
+        for (int c = 0; c < 3; ++c) {
+            const int64_t k = c * Nc + i;
+            vv += v[k] * v[k];
+            fu += fext[k] * u[k];
+            aa += a[k] * a[k];
+        }
+        x[0] += 0.5 * m * vv;
+        x[1] += fu;
+        x[2] += m * aa;
+    }
+    block_sum_store<3>(x, part);
+}
+
+template <class R>
+__global__ void __launch_bounds__(RB) k_energy_edges_inst(const R* __restrict__ h, const int* __restrict__ fan_off,
+                                                          const int* __restrict__ fan_cnt,
+                                                          const int* __restrict__ fan_pool, const R* __restrict__ sig,
+                                                          const int* __restrict__ anc,
+                                                          const int* __restrict__ tet_inst, int inst, int64_t E,
+                                                          double* __restrict__ part) {
+    double x[1] = {0};
+    for (int64_t k = (int64_t)blockIdx.x * RB + threadIdx.x; k < E; k += (int64_t)RG * RB) {
+        const int off = fan_off[k], cnt = fan_cnt[k];
+        if (cnt == 0) continue;
+        if (tet_inst && tet_inst[anc[fan_pool[off]]] != inst) continue;
+        double H[6] = {0, 0, 0, 0, 0, 0};
+        for (int i = 0; i < cnt; ++i) {
+            R y[6];
+            Rec<R>::load6(h + Rec<R>::S6 * (int64_t)fan_pool[off + i], y);
+            for (int q = 0; q < 6; ++q) H[q] += (double)y[q];
+        }
+        R s[6];
+        Rec<R>::load6(sig + Rec<R>::S6 * k, s);
+        double e = 0;
+        for (int q = 0; q < 6; ++q) e += H[q] * (double)s[q];
+        x[0] += e * (1.0 / 12.0);
+    }
+    block_sum_store<1>(x, part + 3 * RG);
+}
+
+__global__ void __launch_bounds__(RB) k_ud_inst(const double* __restrict__ ud_tet, const int* __restrict__ tet_inst,
+                                                int inst, int64_t T0, double* __restrict__ part) {
+    double x[1] = {0};
+    for (int64_t t = (int64_t)blockIdx.x * RB + threadIdx.x; t < T0; t += (int64_t)RG * RB)
+        if (!tet_inst || tet_inst[t] == inst) x[0] += ud_tet[t];
+    block_sum_store<1>(x, part + 4 * RG);
+}
+
+__global__ void __launch_bounds__(BS) k_node_dt(const int* __restrict__ node_inst, const double* __restrict__ inst_dt,
+                                                int64_t N, double* __restrict__ dtn) {
+    int64_t i = (int64_t)blockIdx.x * BS + threadIdx.x;
+    if (i < N) dtn[i] = inst_dt[node_inst[i]];
+}
+
 __global__ void __launch_bounds__(RB) k_reduce_final(const double* __restrict__ part, int nv,
                                                      double* __restrict__ out) {
     __shared__ double sh[RB];
@@ -494,7 +569,7 @@ int cem_launch_geometry(cem_ctx* c, int64_t t0, int64_t t1, double* hbuf) {
 int cem_launch_predict(cem_ctx* c) {
     if (c->N == 0) return CEM_OK;
     k_predict<<<cem_grid(c->N, BS), BS, 0, c->stream>>>(c->u, c->v, c->a, c->Nc, c->N, c->dt, 0.5 * c->dt * c->dt,
-                                                        mixed(c) ? c->uhl : nullptr);
+                                                        mixed(c) ? c->uhl : nullptr, c->dtn);
     cem_launched(c);
     CEM_CK(c, cudaGetLastError());
     return CEM_OK;
@@ -547,10 +622,12 @@ int cem_launch_force(cem_ctx* c) {
 int cem_launch_node_update(cem_ctx* c, int first) {
     if (mixed(c))
         k_node_update<float><<<cem_grid(c->N, BS), BS, 0, c->stream>>>(
-            c->fp32, c->inc_off, c->inc_cnt, c->inc_pool, c->fext, c->minv, c->v, c->a, c->Nc, c->N, 0.5 * c->dt, first);
+            c->fp32, c->inc_off, c->inc_cnt, c->inc_pool, c->fext, c->minv, c->v, c->a, c->Nc, c->N, 0.5 * c->dt, first,
+            c->dtn);
     else
         k_node_update<double><<<cem_grid(c->N, BS), BS, 0, c->stream>>>(
-            c->fp, c->inc_off, c->inc_cnt, c->inc_pool, c->fext, c->minv, c->v, c->a, c->Nc, c->N, 0.5 * c->dt, first);
+            c->fp, c->inc_off, c->inc_cnt, c->inc_pool, c->fext, c->minv, c->v, c->a, c->Nc, c->N, 0.5 * c->dt, first,
+            c->dtn);
     cem_launched(c);
     CEM_CK(c, cudaGetLastError());
     return CEM_OK;
@@ -602,6 +679,34 @@ int cem_energy_reduce(cem_ctx* c, double out[4]) {
     return CEM_OK;
 }
 
+// out = {kinetic, ext_work, aMa, strain, U_d} of specimen inst.
+int cem_energy_reduce_instance(cem_ctx* c, int inst, double out[5]) {
+    k_energy_nodes_inst<<<RG, RB, 0, c->stream>>>(c->u, c->v, c->a, c->mass, c->fext, c->node_inst, inst, c->Nc, c->N,
+                                                  c->red_part);
+    if (mixed(c))
+        k_energy_edges_inst<float><<<RG, RB, 0, c->stream>>>(c->h32, c->fan_off, c->fan_cnt, c->fan_pool, c->sig32,
+                                                             c->anc, c->tet_inst, inst, c->E, c->red_part);
+    else
+        k_energy_edges_inst<double><<<RG, RB, 0, c->stream>>>(c->h, c->fan_off, c->fan_cnt, c->fan_pool, c->sig,
+                                                              c->anc, c->tet_inst, inst, c->E, c->red_part);
+    k_ud_inst<<<RG, RB, 0, c->stream>>>(c->ud_tet, c->tet_inst, inst, c->T0, c->red_part);
+    k_reduce_final<<<1, RB, 0, c->stream>>>(c->red_part, 5, c->red_out);
+    cem_launched(c, 4);
+    CEM_CK(c, cudaGetLastError());
+    CEM_CK(c, cudaMemcpyAsync(c->hred, c->red_out, 5 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CEM_CK(c, cudaStreamSynchronize(c->stream));
+    for (int q = 0; q < 5; ++q) out[q] = c->hred[q];
+    return CEM_OK;
+}
+
+int cem_launch_node_dt(cem_ctx* c) {
+    if (!c->dtn || c->N == 0) return CEM_OK;
+    k_node_dt<<<cem_grid(c->N, BS), BS, 0, c->stream>>>(c->node_inst, c->inst_dt_dev, c->N, c->dtn);
+    cem_launched(c);
+    CEM_CK(c, cudaGetLastError());
+    return CEM_OK;
+}
+
 int cem_launch_check_finite(cem_ctx* c) {
     CEM_CK(c, cudaMemsetAsync(c->dcount + CNT_SCRATCH1, 0, sizeof(long long), c->stream));
     k_count_nonfinite<<<RG, RB, 0, c->stream>>>(c->u, c->Nc, c->N, c->dcount + CNT_SCRATCH1);
@@ -611,4 +716,4 @@ int cem_launch_check_finite(cem_ctx* c) {
 }
 
 // Reduction scratch size (doubles) needed by cem_energy_reduce.
-int64_t cem_reduction_doubles() { return 4 * RG; }
+int64_t cem_reduction_doubles() { return 5 * RG; }
