@@ -40,7 +40,10 @@ METRIC = "tet-steps/s"
 WORKLOAD = "notched_block_200x80x10"
 
 
-def _workload():
+def _workload(name="block"):
+    if name == "ensemble":
+        from cem_inputs import ensemble
+        return ensemble()
     from cem_inputs import plate_medium
     return plate_medium()
 
@@ -85,6 +88,11 @@ def _args():
     p.add_argument("--impl", choices=["cem", "reference"], default="cem")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--precision", choices=["fp64", "mixed"], default="mixed")
+    p.add_argument("--workload", choices=["block", "ensemble"], default="block",
+                   help="block: the 960,000-element notched block; ensemble: 256 notched blocks of "
+                        "5k-200k elements (about 2.6e7) advanced as one union mesh")
+    p.add_argument("--ensemble-steps", type=int, default=200,
+                   help="steps of the ensemble sub-run in the default (block) mode; 0 skips it")
     p.add_argument("--no-compare", action="store_true", help="skip the second-precision run and agreement check")
     p.add_argument("--split-capacity", type=int, default=0,
                    help="max elements that may split (0: all); lower it to shrink device memory for profiling")
@@ -230,15 +238,19 @@ def run_cem(a):
         if world > 1:
             dist.barrier()
 
-    w = _workload()
+    w = _workload(a.workload)
+    if a.workload == "ensemble" and a.split_capacity == 0:
+        a.split_capacity = w.n_tets // 4
     stream = torch.cuda.current_stream(dev)
     peaks = _peaks()
     hbm = peaks.get("hbm_gbs")
     fp64_peak_meas = probe_fp64_fma(dev, stream.cuda_stream)
 
-    def timed(precision, clocks_on):
+    def timed(precision, clocks_on, w=w, steps=None, split_capacity=None):
         """W untimed then K timed steps of a fresh context: metrics of the timed region."""
-        sim = CEM.from_workload(w, device=dev, split_capacity=a.split_capacity, precision=precision)
+        steps = a.steps if steps is None else steps
+        cap = a.split_capacity if split_capacity is None else split_capacity
+        sim = CEM.from_workload(w, device=dev, split_capacity=cap, precision=precision)
         info0 = sim.info()
         sim.step(a.warmup)
         barrier()
@@ -246,7 +258,7 @@ def run_cem(a):
         sim.profile(True)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        sim.step(a.steps)
+        sim.step(steps)
         e1.record(stream)
         torch.cuda.synchronize()
         t_ms = e0.elapsed_time(e1)
@@ -298,8 +310,8 @@ def run_cem(a):
         if precision == "fp64":
             roofline.update(algorithmic_flops_per_launch=flops, fp64_tflops_achieved=flops / per_launch_s / 1e12,
                             fp64_peak_tflops=fp64_peak / 1e12, fp64_fma_measured_tflops=fp64_peak_meas / 1e12)
-        return dict(t_ms=t_ms, value=w.n_tets * a.steps * world / (t_ms * 1e-3), roofline=roofline, kernels=kernels,
-                    clocks=clk, launches=launches, info0=info0, info=info, energy=energy)
+        return dict(t_ms=t_ms, value=w.n_tets * steps * world / (t_ms * 1e-3), roofline=roofline, kernels=kernels,
+                    clocks=clk, launches=launches, info0=info0, info=info, energy=energy, steps=steps)
 
     main = timed(a.precision, True)
     other = None
@@ -308,7 +320,7 @@ def run_cem(a):
 
     # agreement of the two precisions on a short window (both paths from the same start)
     agree = None
-    if not a.no_compare:
+    if not a.no_compare and a.workload == "block":
         n_cmp = 500
         s64 = CEM.from_workload(w, device=dev, split_capacity=a.split_capacity, precision="fp64")
         s32 = CEM.from_workload(w, device=dev, split_capacity=a.split_capacity, precision="mixed")
@@ -322,6 +334,22 @@ def run_cem(a):
                  "split_jaccard": len(c64 & c32) / max(len(c64 | c32), 1), "splits_fp64": len(c64)}
         s64.close()
         s32.close()
+
+    # the 256-specimen ensemble as one union mesh, mixed against FP64 (default block mode only)
+    ens = None
+    if a.workload == "block" and a.ensemble_steps > 0:
+        we = _workload("ensemble")
+        em = timed("mixed", False, w=we, steps=a.ensemble_steps, split_capacity=we.n_tets // 4)
+        ef = timed("fp64", False, w=we, steps=a.ensemble_steps, split_capacity=we.n_tets // 4)
+        ens = {"workload": we.name, "instances": we.params["n_instances"], "tets": we.n_tets,
+               "steps": a.ensemble_steps, "warmup": a.warmup,
+               "mixed": {"value": em["value"], "ms_per_step": em["t_ms"] / a.ensemble_steps,
+                         "roofline": {k: em["roofline"][k] for k in ("bound", "kernel", "achieved", "peak", "unit",
+                                                                     "frac")}},
+               "fp64": {"value": ef["value"], "ms_per_step": ef["t_ms"] / a.ensemble_steps},
+               "mixed_speedup_over_fp64": em["value"] / ef["value"],
+               "split_elements_at_end_mixed": em["energy"]["n_split"]}
+        del we
 
     # end to end through the public API with host buffers: create + material + K steps + read back
     barrier()
@@ -344,7 +372,7 @@ def run_cem(a):
     if rank != 0:
         return
     cpu = None
-    if world == 1 and not a.no_cpu_baseline:
+    if world == 1 and not a.no_cpu_baseline and a.workload == "block":
         try:
             cpu = _cpu_baseline(a.cpu_steps)
         except Exception as ex:  # reported, not hidden
@@ -377,6 +405,12 @@ def run_cem(a):
             "gpu_launches": other["launches"], "speedup_of_main": main["value"] / other["value"]}
     if agree is not None:
         line["precision_agreement"] = agree
+    if ens is not None:
+        line["ensemble"] = ens
+    if a.workload == "ensemble":
+        line["config"]["workload"] = w.name
+        line["config"]["instances"] = w.params["n_instances"]
+        line["config"]["split_capacity"] = a.split_capacity
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
