@@ -226,6 +226,12 @@ __global__ void __launch_bounds__(BS) k_strain(const double* __restrict__ u, con
     Rec<R>::store6(h + Rec<R>::S6 * j, out);
 }
 
+// Node gathers are issued in batches (all indices, then all records) so several
+// records are in flight per thread; sums keep the list's ascending order.  (The
+// edge fans are short, about five elements, and a batched fan loop costs more
+// occupancy than it gains.)
+template <class R> struct Batch { static constexpr int B = (sizeof(R) == 4) ? 8 : 4; };
+
 template <class R>
 __global__ void __launch_bounds__(BS) k_edge_stress(const R* __restrict__ h, const int* __restrict__ fan_off,
                                                     const int* __restrict__ fan_cnt, const int* __restrict__ fan_pool,
@@ -255,14 +261,16 @@ __global__ void __launch_bounds__(BS) k_force(const R* __restrict__ sig, const i
     int64_t j = (int64_t)blockIdx.x * BS + threadIdx.x;
     if (j >= T || !active[j]) return;
     R S[6] = {0, 0, 0, 0, 0, 0};
+    int kk[6];
 #pragma unroll
-    for (int l = 0; l < 6; ++l) {
-        const int k = t2e[l * Tc + j];
-        R x[6];
-        Rec<R>::load6(sig + Rec<R>::S6 * (int64_t)k, x);
+    for (int l = 0; l < 6; ++l) kk[l] = t2e[l * Tc + j];
+    R x[6][6];
 #pragma unroll
-        for (int q = 0; q < 6; ++q) S[q] += x[q];
-    }
+    for (int l = 0; l < 6; ++l) Rec<R>::load6(sig + Rec<R>::S6 * (int64_t)kk[l], x[l]);
+#pragma unroll
+    for (int l = 0; l < 6; ++l)
+#pragma unroll
+        for (int q = 0; q < 6; ++q) S[q] += x[l][q];
     R f[4][3];
     f[0][0] = f[0][1] = f[0][2] = 0;
 #pragma unroll
@@ -305,28 +313,53 @@ __global__ void __launch_bounds__(BS) k_node_update(const R* __restrict__ fp, co
     if (dtn) hdt = 0.5 * dtn[i];
     const int off = inc_off[i], cnt = inc_cnt[i];
     double f[3];
+    constexpr int B = Batch<R>::B;
     if constexpr (sizeof(R) == 8) {
         f[0] = f[1] = f[2] = 0.0;
-        for (int q = 0; q < cnt; ++q) {
-            const double* p = fp + 12 * (int64_t)(inc_pool[off + q] >> 2) + 3 * (inc_pool[off + q] & 3);
-            f[0] += p[0];
-            f[1] += p[1];
-            f[2] += p[2];
+        for (int base = 0; base < cnt; base += B) {
+            int ee[B];
+#pragma unroll
+            for (int b = 0; b < B; ++b) ee[b] = (base + b < cnt) ? inc_pool[off + base + b] : -1;
+            double x[B][3];
+#pragma unroll
+            for (int b = 0; b < B; ++b)
+                if (ee[b] >= 0) {
+                    const double* p = fp + 12 * (int64_t)(ee[b] >> 2) + 3 * (ee[b] & 3);
+                    x[b][0] = p[0];
+                    x[b][1] = p[1];
+                    x[b][2] = p[2];
+                }
+#pragma unroll
+            for (int b = 0; b < B; ++b)
+                if (ee[b] >= 0) {
+                    f[0] += x[b][0];
+                    f[1] += x[b][1];
+                    f[2] += x[b][2];
+                }
         }
     } else {
         // compensated FP32 sum (Kahan) of the FP32 element forces
         float s[3] = {0.f, 0.f, 0.f}, cmp[3] = {0.f, 0.f, 0.f};
-        for (int q = 0; q < cnt; ++q) {
-            const int e = inc_pool[off + q];
-            const float4 x = reinterpret_cast<const float4*>(fp)[4 * (int64_t)(e >> 2) + (e & 3)];
-            const float xv[3] = {x.x, x.y, x.z};
+        for (int base = 0; base < cnt; base += B) {
+            int ee[B];
 #pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                const float y = xv[c] - cmp[c];
-                const float t = s[c] + y;
-                cmp[c] = (t - s[c]) - y;
-                s[c] = t;
-            }
+            for (int b = 0; b < B; ++b) ee[b] = (base + b < cnt) ? inc_pool[off + base + b] : -1;
+            float4 x[B];
+#pragma unroll
+            for (int b = 0; b < B; ++b)
+                if (ee[b] >= 0) x[b] = reinterpret_cast<const float4*>(fp)[4 * (int64_t)(ee[b] >> 2) + (ee[b] & 3)];
+#pragma unroll
+            for (int b = 0; b < B; ++b)
+                if (ee[b] >= 0) {
+                    const float xv[3] = {x[b].x, x[b].y, x[b].z};
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        const float y = xv[c] - cmp[c];
+                        const float t = s[c] + y;
+                        cmp[c] = (t - s[c]) - y;
+                        s[c] = t;
+                    }
+                }
         }
 #pragma unroll
         for (int c = 0; c < 3; ++c) f[c] = (double)s[c] - (double)cmp[c];
