@@ -343,6 +343,7 @@ class CEMOracle:
         inv = inv.reshape(-1, 6)
         nE = ukeys.size
         self.edge_keys = ukeys
+        self.t2e_active = inv
         self.key_base = N
         # fan pairs (edge k, element j): every element is in the fan of its 6 edges
         k_of = inv.ravel()
@@ -586,6 +587,67 @@ class CEMOracle:
     def crack_state(self):
         """Split original elements sorted by (step, tet): (tet, step, pattern, side, G)."""
         return sorted(self.crack_log, key=lambda r: (r[1], r[0]))
+
+    # ------------------------------------------------------------------ adjoint
+    def adjoint(self, n_steps, c_strain=1.0, w_u=None):
+        """Discrete adjoint of n_steps explicit steps from the current state.
+
+        Objective J = c_strain * 1/2 u_N^T K u_N + w_u . u_N.  Returns J, dJ/dE
+        per input element (sub-elements add to their parent) and dJ/dalpha, the
+        derivative with respect to the traction amplitude alpha in
+        f_ext = alpha * f_ext (at alpha = 1).  The topology must stay fixed
+        (splitting off).  Not a formula of the paper: the adjoint of its
+        explicit Newmark step (Eqs. 13-15) with K = sum_k Vs_k Bbar_k^T Dbar_k Bbar_k,
+        Dbar_k = sum_j w_j E_j Dhat, so that y^T (dK/dE_j) u =
+        (V_j / 6) sum_{k in edges(j)} eps_k(y)^T Dhat eps_k(u).
+        The state at the call is taken as given, except that a call from step 0
+        also differentiates a_0 = alpha M^-1 f_ext.
+        """
+        if self.split_enabled:
+            raise ValueError("the adjoint needs a fixed topology (splitting off)")
+        dt = self.dt
+        from_start = self.n_step == 0
+        w = np.zeros_like(self.u) if w_u is None else np.asarray(w_u, dtype=np.float64).reshape(self.u.shape)
+        us = [self.u.copy()]
+        for _ in range(int(n_steps)):
+            self.step(1)
+            us.append(self.u.copy())
+        lamh, muh = lame(1.0, self.nu)
+        Dhat = elasticity_matrix(lamh, muh)
+        act = self.active_ids
+        Vact = self.V_active
+        gE_act = np.zeros(act.size)
+
+        def K(y):
+            return self._internal_force(y)[0]
+
+        def edge_strain(y):
+            return (self.Bbar @ y.ravel()).reshape(-1, 6)
+
+        def dK_dE(y, u):   # y^T (dK/dE_j) u for every active element j
+            sk = np.einsum("ki,ij,kj->k", edge_strain(y), Dhat, edge_strain(u))
+            return Vact / 6.0 * sk[self.t2e_active].sum(axis=1)
+
+        uN = us[-1]
+        KuN = K(uN)
+        J = c_strain * 0.5 * float(np.sum(uN * KuN)) + float(np.sum(w * uN))
+        gE_act += c_strain * 0.5 * dK_dE(uN, uN)
+        lu, lv, la = c_strain * KuN + w, np.zeros_like(uN), np.zeros_like(uN)
+        minv = np.where(self.mass > 0, 1.0 / np.where(self.mass > 0, self.mass, 1.0), 0.0)
+        dalpha = 0.0
+        for n in range(int(n_steps) - 1, -1, -1):
+            g = la + 0.5 * dt * lv
+            y = minv[:, None] * g
+            dalpha += float(np.sum(y * self.f_ext))
+            gE_act -= dK_dE(y, us[n + 1])
+            lu_tot = lu - K(y)
+            lu, lv, la = lu_tot, lv + dt * lu_tot, 0.5 * dt * lv + 0.5 * dt * dt * lu_tot
+        if from_start:
+            dalpha += float(np.sum(la * minv[:, None] * self.f_ext))
+        dE = np.zeros(self.T0)
+        anc = np.where(self.parent[act] >= 0, self.parent[act], act)
+        np.add.at(dE, anc, gE_act)          # a sub-element carries its parent's modulus
+        return J, dE, dalpha
 
     @classmethod
     def from_workload(cls, w, **kw):

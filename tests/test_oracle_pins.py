@@ -414,3 +414,39 @@ def test_mass_and_volume_closure_after_runtime_splits():
         assert G > o.Gc_t[t]
         Ud += o.Gc_t[t] * crack_area(w.X[o.conn[t]], mask)
     assert abs(Ud - o.U_d) < 1e-12 * Ud
+
+
+# --------------------------------------------------------------------------- adjoint (central differences)
+def _J(w, E, alpha, n, c, wu_fn):
+    o = CEMOracle(w.X, w.tets, w.tfaces, w.tvec, E, w.Gc, w.nu, w.rho, notch_tet=w.notch_tet,
+                  notch_side=w.notch_side, split_enabled=False)
+    o.f_ext *= alpha
+    o.a = o._accel(o._internal_force(o.u)[0])
+    o.step(n)
+    f, _, _ = o._internal_force(o.u)
+    return c * 0.5 * float(np.sum(o.u * f)) + float(np.sum(wu_fn(o) * o.u))
+
+
+def test_adjoint_matches_central_differences():
+    """dJ/dE_j and dJ/dalpha of the discrete adjoint equal central differences of the forward model."""
+    w = kuhn_block(5, 4, 1, 0.025, 0.02, 0.005, notch_length=0.012, E_cov=0.2, seed=8, traction=2e6)
+    n, c = 40, 1.0
+
+    def wu_fn(o):   # mean top-face y displacement
+        top = np.isclose(o.X[:, 1], 0.02)
+        wu = np.zeros_like(o.X)
+        wu[top, 1] = 1.0 / top.sum()
+        return wu * 1e3
+
+    o = CEMOracle.from_workload(w, split_enabled=False)
+    J, dE, da = o.adjoint(n, c_strain=c, w_u=wu_fn(o))
+    assert abs(J - _J(w, w.E, 1.0, n, c, wu_fn)) < 1e-12 * abs(J)
+    h = 1e-5
+    for j in [0, int(w.notch_tet[0]), 37, w.n_tets - 1]:
+        Ep, Em = w.E.copy(), w.E.copy()
+        Ep[j] *= 1 + h
+        Em[j] *= 1 - h
+        fd = (_J(w, Ep, 1.0, n, c, wu_fn) - _J(w, Em, 1.0, n, c, wu_fn)) / (2 * h * w.E[j])
+        assert abs(fd - dE[j]) <= 1e-6 * np.abs(dE).max(), (j, fd, dE[j])
+    fd = (_J(w, w.E, 1 + h, n, c, wu_fn) - _J(w, w.E, 1 - h, n, c, wu_fn)) / (2 * h)
+    assert abs(fd - da) <= 1e-6 * abs(da), (fd, da)
