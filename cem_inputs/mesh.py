@@ -269,3 +269,17 @@ def ensemble_members(n=256, seed=4, t_min=5_000, t_max=200_000):
 def ensemble(n=256, seed=4):
     """The 256-specimen ensemble (about 2.6e7 elements) as one union mesh."""
     return union(ensemble_members(n, seed), name="ensemble_%d_seed%d" % (n, seed))
+
+
+def adjoint_block() -> Workload:
+    """0.1 x 0.04 x 0.01 m, 50x20x17 cells (102,000 elements), notch 0.05 m: the
+    gradient (adjoint) workload."""
+    return kuhn_block(50, 20, 17, 0.1, 0.04, 0.01, notch_length=0.05, name="notched_block_50x20x17")
+
+
+def top_face_weights(X, Ly=0.04):
+    """Weights w with w . u = mean y displacement of the nodes on y = Ly."""
+    top = np.isclose(X[:, 1], Ly)
+    w = np.zeros_like(X)
+    w[top, 1] = 1.0 / max(int(top.sum()), 1)
+    return w

@@ -15,8 +15,9 @@
  *   - Host arrays passed in are read during the call and copied; the caller
  *     keeps ownership.  Outputs go to caller-owned host buffers.
  *   - Device memory is obtained through the allocator in cem_mesh_desc (or
- *     cudaMalloc when none is given) once, in cem_mesh_create; cem_step never
- *     allocates.  Every allocation is released by cem_destroy.
+ *     cudaMalloc when none is given) in cem_mesh_create, and by cem_adjoint
+ *     for its working memory (released before it returns); cem_step never
+ *     allocates.  Every allocation of the context is released by cem_destroy.
  *   - All device work is queued on the stream given at creation.  cem_step
  *     synchronises that stream once per step while crack-front elements exist
  *     (to learn whether any element splits); cem_energy, cem_crack_state and
@@ -68,8 +69,8 @@ extern "C" {
 
 /* Device allocator hooks.  alloc returns a device pointer of at least `bytes`
  * bytes (256-byte aligned) or NULL; free releases it.  `stream` is the
- * context's stream.  Both are called only inside cem_mesh_create and
- * cem_destroy. */
+ * context's stream.  Both are called only inside cem_mesh_create,
+ * cem_adjoint and cem_destroy. */
 typedef void* (*cem_alloc_fn)(size_t bytes, void* stream, void* user);
 typedef void  (*cem_free_fn)(void* ptr, void* stream, void* user);
 
@@ -158,6 +159,22 @@ int cem_set_material(cem_ctx* ctx, double rho, double nu,
  * (no material), CEM_ECAPACITY (state left at the last completed step),
  * CEM_ECUDA. */
 int cem_step(cem_ctx* ctx, int64_t n);
+
+/* Discrete adjoint of n_steps explicit steps from the current state, with the
+ * topology fixed (requires split_enabled = 0; one specimen).  Objective
+ *   J = c_strain * 1/2 u_N^T K u_N + sum_i w_u[i] . u_N[i]
+ * (w_u: host, n_nodes x 3 row-major, or NULL).  Returns J, dJ_dE (host,
+ * n_tets input elements; a split element's sub-elements add to it) and
+ * dJ_dalpha, the derivative with respect to the traction amplitude alpha in
+ * f_ext = alpha f_ext at alpha = 1 (a call from step 0 includes the
+ * dependence of a_0 on alpha).  The adjoint of Eqs. 13-15 is not in the
+ * paper.  States are kept every checkpoint_every steps (<= 0: ceil(sqrt(n)))
+ * and each segment is recomputed before its reverse sweep.  The context ends
+ * at step + n_steps.  Allocates its working memory through the context's
+ * allocator and frees it before returning.  Errors: CEM_ESTATE (no material,
+ * splitting on, ensemble), CEM_ENOMEM, CEM_ECUDA. */
+int cem_adjoint(cem_ctx* ctx, int64_t n_steps, int64_t checkpoint_every, double c_strain,
+                const double* w_u, double* J, double* dJ_dE, double* dJ_dalpha);
 
 /* Energies of the current state (deterministic reductions). */
 int cem_energy(cem_ctx* ctx, cem_energy_t* out);

@@ -24,7 +24,7 @@ ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_void_p)
 
 EXPORTED = ["cem_mesh_create", "cem_set_material", "cem_step", "cem_energy", "cem_crack_state",
-            "cem_get_field", "cem_info", "cem_energy_instance", "cem_profile", "cem_profile_read", "cem_probe_fp64_fma", "cem_destroy", "cem_last_error"]
+            "cem_get_field", "cem_info", "cem_energy_instance", "cem_adjoint", "cem_profile", "cem_profile_read", "cem_probe_fp64_fma", "cem_destroy", "cem_last_error"]
 KERNELS = ["predict", "strain", "edge_stress", "force", "node_update", "front_G", "split"]
 
 
@@ -75,6 +75,8 @@ def load_library(build: bool = True):
     lib.cem_step.argtypes = [P, C.c_int64]
     lib.cem_energy.argtypes = [P, C.POINTER(Energy)]
     lib.cem_energy_instance.argtypes = [P, C.c_int64, C.POINTER(Energy)]
+    lib.cem_adjoint.argtypes = [P, C.c_int64, C.c_int64, C.c_double, C.POINTER(C.c_double),
+                                C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)]
     lib.cem_crack_state.argtypes = [P, C.POINTER(C.c_int64), C.POINTER(C.c_int32), C.POINTER(C.c_int8),
                                     C.POINTER(C.c_uint8), C.POINTER(C.c_int64), C.POINTER(C.c_double), C.c_int64]
     lib.cem_get_field.argtypes = [P, C.c_int, C.POINTER(C.c_double), C.c_int64, C.POINTER(C.c_int64)]
@@ -209,6 +211,17 @@ class CEM:
         e = Energy()
         self._check(self._lib.cem_energy_instance(self._ctx, int(i), C.byref(e)))
         return {k: getattr(e, k) for k, _ in Energy._fields_}
+
+    def adjoint(self, n_steps, c_strain=1.0, w_u=None, checkpoint_every=0):
+        """(J, dJ/dE per input element, dJ/dalpha) of n_steps steps from the current state."""
+        n_tets = self._keep[1].shape[0]
+        dE = np.zeros(n_tets, dtype=np.float64)
+        J, da = C.c_double(), C.c_double()
+        wu = None if w_u is None else np.ascontiguousarray(w_u, dtype=np.float64).reshape(-1, 3)
+        self._check(self._lib.cem_adjoint(self._ctx, int(n_steps), int(checkpoint_every), float(c_strain),
+                                          _ptr(wu, C.c_double) if wu is not None else None, C.byref(J),
+                                          _ptr(dE, C.c_double), C.byref(da)))
+        return J.value, dE, da.value
 
     def info(self) -> dict:
         i = Info()

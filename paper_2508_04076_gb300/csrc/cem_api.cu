@@ -552,6 +552,8 @@ int run_step(cem_ctx* c) {
 
 }  // namespace
 
+int cem_run_step(cem_ctx* c) { return run_step(c); }
+
 extern "C" {
 
 int cem_mesh_create(const cem_mesh_desc* d, cem_ctx** out) {

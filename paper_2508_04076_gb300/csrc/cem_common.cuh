@@ -177,6 +177,17 @@ int cem_launch_material(cem_ctx* c, const double* E_dev, int nE, const double* G
 int cem_energy_reduce(cem_ctx* c, double out[4]);
 int cem_energy_reduce_instance(cem_ctx* c, int inst, double out[5]);   // + U_d of the specimen
 int cem_launch_node_dt(cem_ctx* c);                                     // dtn[i] = dt of node i's specimen
+
+// ---------------------------------------------------------------- adjoint helpers (cem_step.cu)
+int cem_adj_strain(cem_ctx* c, const double* y, float* yhl, void* hbuf);
+int cem_adj_apply_K(cem_ctx* c, const double* y, float* yhl, double* Ky);
+int cem_adj_grad_E(cem_ctx* c, const void* hy, const void* hu, double* s, double coef, double* gE);
+int cem_adj_y(cem_ctx* c, const double* la, const double* lv, double* y, double* dalpha);
+int cem_adj_update(cem_ctx* c, double* lu, double* lv, double* la, const double* Ky);
+int cem_adj_init(cem_ctx* c, double* lu, double* lv, double* la, const double* Ku, const double* w, double cK);
+int cem_adj_dot(cem_ctx* c, const double* a, const double* b, const double* mscale, double* out);
+// one explicit step without the crack test (cem_api.cu)
+int cem_run_step(cem_ctx* c);
 int cem_launch_check_finite(cem_ctx* c);
 
 // ---------------------------------------------------------------- crack path (cem_crack.cu)

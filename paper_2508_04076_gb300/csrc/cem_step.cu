@@ -39,8 +39,7 @@ constexpr int BS = 256;
 template <class R> struct Rec;
 template <> struct Rec<double> {
     static constexpr int S6 = 6;     // stride of a 6-value record
-    static constexpr int SF = 12;    // stride of an element force record
-    static constexpr int SL = 3;     // stride of one local node inside it
+    static constexpr int SF = 12;    // stride of an element force record (3 values per local node)
     __device__ static void load6(const double* p, double v[6]) {
         const double2 a = reinterpret_cast<const double2*>(p)[0];
         const double2 b = reinterpret_cast<const double2*>(p)[1];
@@ -55,8 +54,7 @@ template <> struct Rec<double> {
 };
 template <> struct Rec<float> {
     static constexpr int S6 = 8;
-    static constexpr int SF = 16;
-    static constexpr int SL = 4;
+    static constexpr int SF = 16;    // 4 values (3 + pad) per local node
     __device__ static void load6(const float* p, float v[6]) {
         const float4 a = reinterpret_cast<const float4*>(p)[0];
         const float2 b = reinterpret_cast<const float2*>(p)[2];
@@ -588,7 +586,232 @@ __global__ void __launch_bounds__(RB) k_count_nonfinite(const double* __restrict
 
 inline bool mixed(const cem_ctx* c) { return c->precision == CEM_MIXED; }
 
+// ---------------------------------------------------------------- adjoint of the step
+// f[i] = (1/6) sum over node incidence of the element forces: K y when the
+// element forces were computed from the strain of y.
+template <class R>
+__global__ void __launch_bounds__(BS) k_node_force(const R* __restrict__ fp, const int* __restrict__ inc_off,
+                                                   const int* __restrict__ inc_cnt, const int* __restrict__ inc_pool,
+                                                   int64_t Nc, int64_t N, double* __restrict__ out) {
+    int64_t i = (int64_t)blockIdx.x * BS + threadIdx.x;
+    if (i >= N) return;
+    const int off = inc_off[i], cnt = inc_cnt[i];
+    double f[3] = {0.0, 0.0, 0.0};
+    for (int q = 0; q < cnt; ++q) {
+        const int e = inc_pool[off + q];
+        const int64_t j = e >> 2, l = e & 3;
+        if constexpr (sizeof(R) == 8) {
+            const double* p = fp + 12 * j + 3 * l;
+            f[0] += p[0];
+            f[1] += p[1];
+            f[2] += p[2];
+        } else {
+            const float4 x = reinterpret_cast<const float4*>(fp)[4 * j + l];
+            f[0] += (double)x.x;
+            f[1] += (double)x.y;
+            f[2] += (double)x.z;
+        }
+    }
+    for (int c = 0; c < 3; ++c) out[c * Nc + i] = f[c] * (1.0 / 6.0);
+}
+
+// s_k = epsbar_k(y)^T Dhat epsbar_k(u) with Dhat the elasticity of a unit modulus.
+template <class R>
+__global__ void __launch_bounds__(BS) k_edge_pair(const R* __restrict__ hy, const R* __restrict__ hu,
+                                                  const int* __restrict__ fan_off, const int* __restrict__ fan_cnt,
+                                                  const int* __restrict__ fan_pool, const double* __restrict__ sumV,
+                                                  double lamh, double muh, int64_t E, double* __restrict__ s) {
+    int64_t k = (int64_t)blockIdx.x * BS + threadIdx.x;
+    if (k >= E) return;
+    const int off = fan_off[k], cnt = fan_cnt[k];
+    double Y[6] = {0, 0, 0, 0, 0, 0}, U[6] = {0, 0, 0, 0, 0, 0};
+    for (int i = 0; i < cnt; ++i) {
+        const int j = fan_pool[off + i];
+        R a[6], b[6];
+        Rec<R>::load6(hy + Rec<R>::S6 * (int64_t)j, a);
+        Rec<R>::load6(hu + Rec<R>::S6 * (int64_t)j, b);
+        for (int q = 0; q < 6; ++q) {
+            Y[q] += (double)a[q];
+            U[q] += (double)b[q];
+        }
+    }
+    const double sv = sumV[k];
+    if (cnt == 0 || !(sv > 0.0)) {
+        s[k] = 0.0;
+        return;
+    }
+    const double e = lamh * (Y[0] + Y[1] + Y[2]) * (U[0] + U[1] + U[2]) +
+                     muh * (2.0 * (Y[0] * U[0] + Y[1] * U[1] + Y[2] * U[2]) + Y[3] * U[3] + Y[4] * U[4] + Y[5] * U[5]);
+    s[k] = e / (sv * sv);
+}
+
+// gE[j] += coef * V_j / 6 * sum over the element's edges of s_k (active elements).
+__global__ void __launch_bounds__(BS) k_elem_acc(const double* __restrict__ s, const int* __restrict__ t2e,
+                                                 const double* __restrict__ vol, const uint8_t* __restrict__ active,
+                                                 int64_t Tc, int64_t T, double coef, double* __restrict__ gE) {
+    int64_t j = (int64_t)blockIdx.x * BS + threadIdx.x;
+    if (j >= T || !active[j]) return;
+    double t = 0.0;
+    for (int l = 0; l < 6; ++l) t += s[t2e[l * Tc + j]];
+    gE[j] += coef * vol[j] * (1.0 / 6.0) * t;
+}
+
+// y = M^-1 (la + dt/2 lv) and the block partials of y . f_ext.
+__global__ void __launch_bounds__(RB) k_adj_y(const double* __restrict__ la, const double* __restrict__ lv,
+                                              const double* __restrict__ minv, const double* __restrict__ fext,
+                                              double hdt, int64_t Nc, int64_t N, double* __restrict__ y,
+                                              double* __restrict__ part) {
+    double x[1] = {0.0};
+    for (int64_t i = (int64_t)blockIdx.x * RB + threadIdx.x; i < N; i += (int64_t)RG * RB) {
+        const double mi = minv[i];
+        for (int c = 0; c < 3; ++c) {
+            const int64_t k = c * Nc + i;
+            const double yy = mi * (la[k] + hdt * lv[k]);
+            y[k] = yy;
+            x[0] += yy * fext[k];
+        }
+    }
+    block_sum_store<1>(x, part);
+}
+
+// One step of the reverse sweep: lu' = lu - K y; (lu, lv, la) <- (lu', lv + dt lu', dt/2 lv + dt^2/2 lu').
+__global__ void __launch_bounds__(BS) k_adj_update(double* __restrict__ lu, double* __restrict__ lv,
+                                                   double* __restrict__ la, const double* __restrict__ Ky, double dt,
+                                                   int64_t Nc, int64_t N) {
+    int64_t i = (int64_t)blockIdx.x * BS + threadIdx.x;
+    if (i >= N) return;
+    for (int c = 0; c < 3; ++c) {
+        const int64_t k = c * Nc + i;
+        const double l = lu[k] - Ky[k];
+        const double v0 = lv[k];
+        lu[k] = l;
+        lv[k] = v0 + dt * l;
+        la[k] = 0.5 * dt * v0 + 0.5 * dt * dt * l;
+    }
+}
+
+// Block partials of sum_i a_i . (m_i b_i) (mscale NULL: sum a . b).
+__global__ void __launch_bounds__(RB) k_adj_dot(const double* __restrict__ a, const double* __restrict__ b,
+                                                const double* __restrict__ mscale, int64_t Nc, int64_t N,
+                                                double* __restrict__ part) {
+    double x[1] = {0.0};
+    for (int64_t i = (int64_t)blockIdx.x * RB + threadIdx.x; i < N; i += (int64_t)RG * RB) {
+        const double m = mscale ? mscale[i] : 1.0;
+        for (int c = 0; c < 3; ++c) x[0] += a[c * Nc + i] * m * b[c * Nc + i];
+    }
+    block_sum_store<1>(x, part);
+}
+
+// lu = cK * Ku + w, lv = la = 0.
+__global__ void __launch_bounds__(BS) k_adj_init(double* __restrict__ lu, double* __restrict__ lv,
+                                                 double* __restrict__ la, const double* __restrict__ Ku,
+                                                 const double* __restrict__ w, double cK, int64_t Nc, int64_t N) {
+    int64_t i = (int64_t)blockIdx.x * BS + threadIdx.x;
+    if (i >= N) return;
+    for (int c = 0; c < 3; ++c) {
+        const int64_t k = c * Nc + i;
+        lu[k] = cK * Ku[k] + w[k];
+        lv[k] = 0.0;
+        la[k] = 0.0;
+    }
+}
+
+__global__ void __launch_bounds__(RB) k_reduce_one(const double* __restrict__ part, double* __restrict__ out) {
+    __shared__ double sh[RB];
+    double s = 0;
+    for (int i = threadIdx.x; i < RG; i += RB) s += part[i];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = RB / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = sh[0];
+}
+
 }  // namespace
+
+// ---- adjoint launchers (vectors are FP64 structure of arrays [3][Nc])
+// Element strain records of y into hbuf (mixed: through the FP32 hi/lo copy yhl).
+int cem_adj_strain(cem_ctx* c, const double* y, float* yhl, void* hbuf) {
+    if (mixed(c)) {
+        k_split_u<<<cem_grid(c->N, BS), BS, 0, c->stream>>>(y, c->Nc, c->N, yhl);
+        k_strain<float><<<cem_grid(c->T, BS), BS, 0, c->stream>>>(y, yhl, c->Nc, c->conn, c->Vg32, c->active, c->Tc,
+                                                                  c->T, (float*)hbuf);
+        cem_launched(c, 2);
+    } else {
+        k_strain<double><<<cem_grid(c->T, BS), BS, 0, c->stream>>>(y, nullptr, c->Nc, c->conn, c->Vg, c->active, c->Tc,
+                                                                   c->T, (double*)hbuf);
+        cem_launched(c, 1);
+    }
+    CEM_CK(c, cudaGetLastError());
+    return CEM_OK;
+}
+
+// Ky = K y (internal force of y); uses the context's h / sig / fp scratch, so h holds y's strain afterwards.
+int cem_adj_apply_K(cem_ctx* c, const double* y, float* yhl, double* Ky) {
+    int rc = cem_adj_strain(c, y, yhl, mixed(c) ? (void*)c->h32 : (void*)c->h);
+    if (rc) return rc;
+    if ((rc = cem_launch_edge_stress(c)) || (rc = cem_launch_force(c))) return rc;
+    if (mixed(c))
+        k_node_force<float><<<cem_grid(c->N, BS), BS, 0, c->stream>>>(c->fp32, c->inc_off, c->inc_cnt, c->inc_pool,
+                                                                      c->Nc, c->N, Ky);
+    else
+        k_node_force<double><<<cem_grid(c->N, BS), BS, 0, c->stream>>>(c->fp, c->inc_off, c->inc_cnt, c->inc_pool,
+                                                                       c->Nc, c->N, Ky);
+    cem_launched(c);
+    CEM_CK(c, cudaGetLastError());
+    return CEM_OK;
+}
+
+// gE += coef * y^T (dK/dE_j) u for every active element, from strain records hy, hu.
+int cem_adj_grad_E(cem_ctx* c, const void* hy, const void* hu, double* s, double coef, double* gE) {
+    const double lamh = c->nu / ((1.0 + c->nu) * (1.0 - 2.0 * c->nu)), muh = 1.0 / (2.0 * (1.0 + c->nu));
+    if (mixed(c))
+        k_edge_pair<float><<<cem_grid(c->E, BS), BS, 0, c->stream>>>((const float*)hy, (const float*)hu, c->fan_off,
+                                                                     c->fan_cnt, c->fan_pool, c->sumV, lamh, muh, c->E,
+                                                                     s);
+    else
+        k_edge_pair<double><<<cem_grid(c->E, BS), BS, 0, c->stream>>>((const double*)hy, (const double*)hu,
+                                                                      c->fan_off, c->fan_cnt, c->fan_pool, c->sumV,
+                                                                      lamh, muh, c->E, s);
+    k_elem_acc<<<cem_grid(c->T, BS), BS, 0, c->stream>>>(s, c->t2e, c->vol, c->active, c->Tc, c->T, coef, gE);
+    cem_launched(c, 2);
+    CEM_CK(c, cudaGetLastError());
+    return CEM_OK;
+}
+
+// y = M^-1 (la + dt/2 lv); *dalpha (device) = y . f_ext.
+int cem_adj_y(cem_ctx* c, const double* la, const double* lv, double* y, double* dalpha) {
+    k_adj_y<<<RG, RB, 0, c->stream>>>(la, lv, c->minv, c->fext, 0.5 * c->dt, c->Nc, c->N, y, c->red_part);
+    k_reduce_one<<<1, RB, 0, c->stream>>>(c->red_part, dalpha);
+    cem_launched(c, 2);
+    CEM_CK(c, cudaGetLastError());
+    return CEM_OK;
+}
+
+int cem_adj_update(cem_ctx* c, double* lu, double* lv, double* la, const double* Ky) {
+    k_adj_update<<<cem_grid(c->N, BS), BS, 0, c->stream>>>(lu, lv, la, Ky, c->dt, c->Nc, c->N);
+    cem_launched(c);
+    CEM_CK(c, cudaGetLastError());
+    return CEM_OK;
+}
+
+int cem_adj_init(cem_ctx* c, double* lu, double* lv, double* la, const double* Ku, const double* w, double cK) {
+    k_adj_init<<<cem_grid(c->N, BS), BS, 0, c->stream>>>(lu, lv, la, Ku, w, cK, c->Nc, c->N);
+    cem_launched(c);
+    CEM_CK(c, cudaGetLastError());
+    return CEM_OK;
+}
+
+// *out (device) = sum a . (m b) over nodes (m = mscale or 1).
+int cem_adj_dot(cem_ctx* c, const double* a, const double* b, const double* mscale, double* out) {
+    k_adj_dot<<<RG, RB, 0, c->stream>>>(a, b, mscale, c->Nc, c->N, c->red_part);
+    k_reduce_one<<<1, RB, 0, c->stream>>>(c->red_part, out);
+    cem_launched(c, 2);
+    CEM_CK(c, cudaGetLastError());
+    return CEM_OK;
+}
 
 int cem_launch_geometry(cem_ctx* c, int64_t t0, int64_t t1, double* hbuf) {
     if (t1 <= t0) return CEM_OK;
