@@ -37,6 +37,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "tet-steps/s"
+PROFILE_EVERY = 16   # kernel timing sampled on every 16th step (events between kernels block launch overlap)
 WORKLOAD = "notched_block_200x80x10"
 
 
@@ -91,6 +92,8 @@ def _args():
     p.add_argument("--workload", choices=["block", "ensemble"], default="block",
                    help="block: the 960,000-element notched block; ensemble: 256 notched blocks of "
                         "5k-200k elements (about 2.6e7) advanced as one union mesh")
+    p.add_argument("--adjoint-steps", type=int, default=5000,
+                   help="steps of the gradient (adjoint) sub-run on the 102,000-element block; 0 skips it")
     p.add_argument("--ensemble-steps", type=int, default=200,
                    help="steps of the ensemble sub-run in the default (block) mode; 0 skips it")
     p.add_argument("--no-compare", action="store_true", help="skip the second-precision run and agreement check")
@@ -255,7 +258,7 @@ def run_cem(a):
         sim.step(a.warmup)
         barrier()
         clocks = ClockSampler(_bus_id(dev)) if (clocks_on and rank == 0) else None
-        sim.profile(True)
+        sim.profile(PROFILE_EVERY)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         sim.step(steps)
@@ -264,7 +267,7 @@ def run_cem(a):
         t_ms = e0.elapsed_time(e1)
         clk = clocks.stop() if clocks else None
         prof, launches = sim.profile_read()
-        sim.profile(False)
+        sim.profile(0)
         barrier()
         tmax = torch.tensor([t_ms], device="cuda", dtype=torch.float64)
         if world > 1:
@@ -280,9 +283,12 @@ def run_cem(a):
         fl, by = kernel_costs(Ta, Em, Nm, precision)
         sm_clock = (clk or {}).get("sm_max_mhz") or peaks.get("sm_max_mhz") or 2070.0
         fp64_peak = 152 * 4 * sm_clock * 1e6      # 152 SMs x 2 FP64 FMA/clk x 2 FLOP
+        # timed launches are a sample (every PROFILE_EVERY-th step): scale sums to the whole region
+        n_sampled = max(prof["predict"][1], 1)
+        scale = steps / n_sampled
         kernels = {}
         for k, (ms_tot, nl) in prof.items():
-            kernels[k] = {"ms": ms_tot, "launches": nl, "share": ms_tot / max(t_ms, 1e-9)}
+            kernels[k] = {"ms": ms_tot * scale, "launches_timed": nl, "share": ms_tot * scale / max(t_ms, 1e-9)}
             if k in KERNEL_UNITS and nl:
                 units = {"tets": Tm, "edges": Em, "nodes": Nm}[KERNEL_UNITS[k]]
                 sec = ms_tot * 1e-3 / nl
@@ -351,6 +357,34 @@ def run_cem(a):
                "split_elements_at_end_mixed": em["energy"]["n_split"]}
         del we
 
+    # gradients: FP32 forward + adjoint with sqrt(N) checkpoints on the 102,000-element block,
+    # J = final strain energy + mean top-face y displacement, topology frozen after the notch
+    adj = None
+    if a.workload == "block" and a.adjoint_steps > 0:
+        from cem_inputs import adjoint_block, top_face_weights
+        wa = adjoint_block()
+        res = {}
+        for prec in ("mixed", "fp64"):
+            sa = CEM.from_workload(wa, device=dev, split_enabled=False, precision=prec)
+            wu = top_face_weights(sa.field("X"))
+            barrier()
+            t0 = time.perf_counter()
+            J, dE, da = sa.adjoint(a.adjoint_steps, c_strain=1.0, w_u=wu)
+            torch.cuda.synchronize()
+            res[prec] = (time.perf_counter() - t0, J, dE, da)
+            sa.close()
+        tm, Jm, dEm, dam = res["mixed"]
+        tf, Jf, dEf, daf = res["fp64"]
+        adj = {"workload": wa.name, "tets": wa.n_tets, "steps": a.adjoint_steps,
+               "checkpoint_every": int(np.ceil(np.sqrt(a.adjoint_steps))),
+               "mixed": {"seconds": tm, "tet_steps_per_s": wa.n_tets * a.adjoint_steps / tm},
+               "fp64": {"seconds": tf, "tet_steps_per_s": wa.n_tets * a.adjoint_steps / tf},
+               "rel_err_J_mixed": abs(Jm - Jf) / abs(Jf),
+               "rel_err_dJdE_mixed": float(np.abs(dEm - dEf).max() / np.abs(dEf).max()),
+               "rel_err_dJdalpha_mixed": abs(dam - daf) / abs(daf),
+               "note": "wall time of one cem_adjoint call: forward, segment recompute and reverse sweep"}
+        del wa
+
     # end to end through the public API with host buffers: create + material + K steps + read back
     barrier()
     t0 = time.perf_counter()
@@ -407,6 +441,8 @@ def run_cem(a):
         line["precision_agreement"] = agree
     if ens is not None:
         line["ensemble"] = ens
+    if adj is not None:
+        line["adjoint"] = adj
     if a.workload == "ensemble":
         line["config"]["workload"] = w.name
         line["config"]["instances"] = w.params["n_instances"]

@@ -197,13 +197,15 @@ int cem_get_field(cem_ctx* ctx, int which, double* out, int64_t cap, int64_t* n_
 /* Sizes and time step. */
 int cem_info(cem_ctx* ctx, cem_info_t* out);
 
-/* Kernel timing.  cem_profile(ctx, 1) clears the counters and starts
- * recording a pair of CUDA events (on the context's stream) around every
- * launch of the hot-path kernels below; cem_profile(ctx, 0) stops.
+/* Kernel timing.  cem_profile(ctx, k) with k >= 1 clears the counters and
+ * starts recording a pair of CUDA events (on the context's stream) around
+ * the hot-path kernels below on every k-th step (events between kernels stop
+ * a kernel's launch from overlapping the previous one, so sampling keeps the
+ * other steps undisturbed); cem_profile(ctx, 0) stops.
  * cem_profile_read copies, for the first n kernel classes, the summed device
  * time in milliseconds and the number of timed launches (either array may be
  * NULL) and, in *total_launches (may be NULL), the number of kernels of any
- * kind the context launched since the last cem_profile(ctx, 1).  Timing adds
+ * kind the context launched since the last cem_profile(ctx, k >= 1).  Timing adds
  * two event records per launch; it does not change results. */
 #define CEM_KERNEL_PREDICT     0   /* u <- u + dt v + dt^2/2 a                      */
 #define CEM_KERNEL_STRAIN      1   /* per-element V * strain                        */

@@ -249,9 +249,9 @@ class CEM:
                                               _ptr(side, C.c_uint8), _ptr(step, C.c_int64), _ptr(G, C.c_double), m))
         return [(int(tet[i]), int(step[i]), int(pat[i]), int(side[i]), float(G[i])) for i in range(m)]
 
-    def profile(self, enable=True):
-        """Start (and clear) or stop per-kernel CUDA-event timing inside the library."""
-        self._check(self._lib.cem_profile(self._ctx, int(bool(enable))))
+    def profile(self, every=1):
+        """Start (and clear) per-kernel CUDA-event timing on every `every`-th step; 0 / False stops."""
+        self._check(self._lib.cem_profile(self._ctx, int(every)))
 
     def profile_read(self):
         """{kernel: (total_ms, launches)} and the total kernel launches since profile(True)."""

@@ -492,7 +492,7 @@ cudaEvent_t ev_get(cem_ctx* c) {
 }
 
 cudaEvent_t prof_begin(cem_ctx* c) {
-    if (!c->prof) return nullptr;
+    if (!c->prof_now) return nullptr;
     cudaEvent_t e = ev_get(c);
     if (e) cudaEventRecord(e, c->stream);
     return e;
@@ -529,6 +529,7 @@ int prof_resolve(cem_ctx* c) {
     } while (0)
 
 int run_step(cem_ctx* c) {
+    c->prof_now = c->prof && (c->step % c->prof_every == 0);
     TIMED(c, CEM_KERNEL_PREDICT, cem_launch_predict(c));
     TIMED(c, CEM_KERNEL_STRAIN, cem_launch_strain(c));
     TIMED(c, CEM_KERNEL_EDGE_STRESS, cem_launch_edge_stress(c));
@@ -644,7 +645,9 @@ int cem_profile(cem_ctx* c, int enable) {
         }
         c->n_launch = 0;
     }
-    c->prof = enable != 0;
+    c->prof = enable > 0;
+    c->prof_every = enable > 0 ? enable : 1;
+    c->prof_now = false;
     return CEM_OK;
 }
 

@@ -135,6 +135,8 @@ struct cem_ctx {
     // kernel timing and launch count
     int64_t n_launch = 0;
     bool prof = false;
+    int prof_every = 1;           // time every k-th step (events between kernels block launch overlap)
+    bool prof_now = false;
     double prof_ms[CEM_KERNEL_COUNT] = {};
     int64_t prof_n[CEM_KERNEL_COUNT] = {};
     std::vector<cudaEvent_t> ev_pool;
@@ -143,6 +145,28 @@ struct cem_ctx {
 };
 
 static inline void cem_launched(cem_ctx* c, int k = 1) { c->n_launch += k; }
+
+// Programmatic dependent launch: kernels of the step and split sequences are
+// launched with programmatic stream serialization, so a kernel's launch
+// overlaps the tail of the previous one.  Every such kernel starts with
+// CEM_PDL_ENTRY: it waits until the previous grid has completed and its
+// writes are visible (griddepcontrol.wait), then lets the next grid launch.
+#define CEM_PDL_ENTRY() asm volatile("griddepcontrol.wait;\n\tgriddepcontrol.launch_dependents;" ::: "memory")
+
+template <typename... KArgs, typename... Args>
+static inline void cem_pdl(cudaStream_t s, void (*k)(KArgs...), dim3 grid, dim3 block, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, k, static_cast<KArgs>(args)...);
+}
 
 // ---------------------------------------------------------------- error helpers
 int cem_fail(cem_ctx* c, int code, const std::string& msg);

@@ -153,6 +153,7 @@ __global__ void __launch_bounds__(BS) k_front_G(const int* __restrict__ cand_lis
                                                 const float* __restrict__ sig32,
                                                 const double* __restrict__ Gc, uint8_t* __restrict__ dec_mask,
                                                 double* __restrict__ dec_G) {
+    CEM_PDL_ENTRY();
     const int tid = blockIdx.x * BS + threadIdx.x;
     const int ci = tid >> 2, f = tid & 3;
     double G = -1.0 / 0.0;
@@ -241,6 +242,7 @@ __global__ void k_gather_splits(const int* __restrict__ pos, const long long* __
                                 const int* __restrict__ cand_list, const uint8_t* __restrict__ dec_mask,
                                 const double* __restrict__ dec_G, int* __restrict__ split_list,
                                 uint8_t* __restrict__ split_mask, double* __restrict__ split_G) {
+    CEM_PDL_ENTRY();
     const int i = blockIdx.x * BS + threadIdx.x;
     if (i >= *count) return;
     const int ci = pos[i];
@@ -253,6 +255,7 @@ __global__ void k_gather_splits(const int* __restrict__ pos, const long long* __
 __global__ void k_mark_keys(int S, const int* __restrict__ split_list, const uint8_t* __restrict__ split_mask,
                             const int* __restrict__ t2e, int64_t Tc, const int* __restrict__ node_of_key,
                             uint8_t* __restrict__ key_flag) {
+    CEM_PDL_ENTRY();
     const int i = blockIdx.x * BS + threadIdx.x;
     if (i >= S) return;
     const int p = split_list[i], m = split_mask[i];
@@ -273,6 +276,7 @@ __global__ void k_create_nodes(const long long* __restrict__ count, const int* _
                                double* __restrict__ fext, double* __restrict__ mass, double* __restrict__ minv,
                                int* __restrict__ inc_off, int* __restrict__ inc_cnt, int64_t Nc,
                                int* __restrict__ node_inst, double* __restrict__ dtn) {
+    CEM_PDL_ENTRY();
     const int i = blockIdx.x * BS + threadIdx.x;
     if (i >= *count) return;
     const int key = new_keys[i];
@@ -298,6 +302,7 @@ __global__ void k_create_nodes(const long long* __restrict__ count, const int* _
 
 // ------------------------------------------------------------------ sub-elements
 __global__ void k_sub_count(int S, const uint8_t* __restrict__ split_mask, int* __restrict__ cnt) {
+    CEM_PDL_ENTRY();
     const int i = blockIdx.x * BS + threadIdx.x;
     if (i >= S) return;
     cnt[i] = (__popc((unsigned)split_mask[i]) == 2) ? 6 : 4;
@@ -340,6 +345,7 @@ __global__ void k_create_subs(int S, int64_t T, const int* __restrict__ split_li
                               int* __restrict__ split_step, double* __restrict__ split_G,
                               const double* __restrict__ Gc, uint8_t* __restrict__ cand_flag,
                               double* __restrict__ ud_part, double* __restrict__ ud_tet) {
+    CEM_PDL_ENTRY();
     const int i = blockIdx.x * BS + threadIdx.x;
     if (i >= S) return;
     const int p = split_list[i];
@@ -461,6 +467,7 @@ __global__ void k_create_subs(int S, int64_t T, const int* __restrict__ split_li
 }
 
 __global__ void k_ud_sum(int S, const double* __restrict__ part, double* __restrict__ Ud) {
+    CEM_PDL_ENTRY();
     __shared__ double sh[BS];
     double s = 0.0;
     for (int i = threadIdx.x; i < S; i += BS) s += part[i];
@@ -485,6 +492,7 @@ __global__ void k_sub_edges(const long long* __restrict__ nsub, int64_t T, int64
                             unsigned long long* __restrict__ hkeys, const int* __restrict__ hvals,
                             int* __restrict__ hfirst, int64_t hmask, int* __restrict__ slot_of,
                             long long* __restrict__ err) {
+    CEM_PDL_ENTRY();
     const int cidx = blockIdx.x * BS + threadIdx.x;
     if (cidx >= 6 * *nsub) return;
     const int q = cidx / 6, l = cidx % 6;
@@ -525,6 +533,7 @@ __global__ void k_sub_edges(const long long* __restrict__ nsub, int64_t T, int64
 __global__ void k_edge_owner(const long long* __restrict__ nsub, const int* __restrict__ slot_of,
                              const int* __restrict__ hvals, const int* __restrict__ hfirst,
                              uint8_t* __restrict__ code_flag) {
+    CEM_PDL_ENTRY();
     const int c = blockIdx.x * BS + threadIdx.x;
     if (c >= 6 * *nsub) return;
     const int s = slot_of[c];
@@ -536,6 +545,7 @@ __global__ void k_edge_assign(const long long* __restrict__ count, const int* __
                               uint8_t* __restrict__ code_flag, int* __restrict__ fan_off, int* __restrict__ fan_cnt,
                               double* __restrict__ cl, double* __restrict__ cm, double* __restrict__ sumV,
                               float* __restrict__ cl32, float* __restrict__ cm32) {
+    CEM_PDL_ENTRY();
     const int r = blockIdx.x * BS + threadIdx.x;
     if (r >= *count) return;
     const int c = owners[r];
@@ -557,6 +567,7 @@ __global__ void k_edge_assign(const long long* __restrict__ count, const int* __
 
 __global__ void k_edge_resolve(const long long* __restrict__ nsub, int64_t T, const int* __restrict__ slot_of,
                                const int* __restrict__ hvals, int* __restrict__ t2e, int64_t Tc) {
+    CEM_PDL_ENTRY();
     const int c = blockIdx.x * BS + threadIdx.x;
     if (c >= 6 * *nsub) return;
     const int s = slot_of[c];
@@ -571,6 +582,7 @@ __global__ void k_mark_affected(int kind, int S, const int* __restrict__ split_l
                                 const long long* __restrict__ nsub, int64_t T,
                                 const int* __restrict__ t2e, const int* __restrict__ conn, int64_t Tc,
                                 uint8_t* __restrict__ flag, int* __restrict__ add_cnt) {
+    CEM_PDL_ENTRY();
     const int per = kind == 0 ? 6 : 4;
     const int i = blockIdx.x * BS + threadIdx.x;
     if (i < S * per) {
@@ -592,6 +604,7 @@ __global__ void k_list_count(int kind, const long long* __restrict__ count, cons
                              const int* __restrict__ off, const int* __restrict__ cnt, const int* __restrict__ pool,
                              const uint8_t* __restrict__ active, const int* __restrict__ add_cnt,
                              int* __restrict__ keep, int* __restrict__ need, int bound) {
+    CEM_PDL_ENTRY();
     const int i = blockIdx.x * BS + threadIdx.x;
     if (i >= bound) return;
     if (i >= *count) {   // slots past the affected count take no pool space
@@ -614,6 +627,7 @@ __global__ void k_list_write(int kind, const long long* __restrict__ count, cons
                              int64_t top, const int* __restrict__ aoff, const int* __restrict__ keep,
                              const int* __restrict__ need, int* __restrict__ off, int* __restrict__ cnt,
                              int* __restrict__ pool, const uint8_t* __restrict__ active, int* __restrict__ cursor) {
+    CEM_PDL_ENTRY();
     const int i = blockIdx.x * BS + threadIdx.x;
     if (i >= *count) return;
     const int x = aff[i];
@@ -632,6 +646,7 @@ __global__ void k_list_write(int kind, const long long* __restrict__ count, cons
 __global__ void k_list_append(int kind, const long long* __restrict__ nsub, int64_t T, const int* __restrict__ t2e,
                               const int* __restrict__ conn, int64_t Tc, const int* __restrict__ off,
                               int* __restrict__ pool, int* __restrict__ cursor) {
+    CEM_PDL_ENTRY();
     const int per = kind == 0 ? 6 : 4;
     const int c = blockIdx.x * BS + threadIdx.x;
     if (c >= *nsub * per) return;
@@ -649,6 +664,7 @@ __global__ void k_list_finish(int kind, const long long* __restrict__ count, con
                               const double* __restrict__ mu, double* __restrict__ cl, double* __restrict__ cm,
                               double* __restrict__ sumV, float* __restrict__ cl32, float* __restrict__ cm32,
                               double rho, double* __restrict__ mass, double* __restrict__ minv) {
+    CEM_PDL_ENTRY();
     const int i = blockIdx.x * BS + threadIdx.x;
     if (i >= *count) return;
     const int x = aff[i];
@@ -693,6 +709,7 @@ __global__ void k_list_finish(int kind, const long long* __restrict__ count, con
 // defragmentation: copy every live list into the spare pool
 __global__ void k_defrag(int64_t n, const int* __restrict__ newoff, int* __restrict__ off,
                          const int* __restrict__ cnt, const int* __restrict__ pool, int* __restrict__ pool2) {
+    CEM_PDL_ENTRY();
     const int64_t x = (int64_t)blockIdx.x * BS + threadIdx.x;
     if (x >= n) return;
     const int o = off[x], m = cnt[x], no = newoff[x];
@@ -704,6 +721,7 @@ __global__ void k_defrag(int64_t n, const int* __restrict__ newoff, int* __restr
 __global__ void k_cand_mark(int S, const int* __restrict__ split_list, const uint8_t* __restrict__ split_mask,
                             const int* __restrict__ face_nbr, int64_t T0, const uint8_t* __restrict__ side,
                             uint8_t* __restrict__ cand_flag) {
+    CEM_PDL_ENTRY();
     const int i = blockIdx.x * BS + threadIdx.x;
     if (i >= S) return;
     const int p = split_list[i], m = split_mask[i];
@@ -733,7 +751,7 @@ int defrag(cem_ctx* c, int kind) {
     int*& pool2 = kind == 0 ? c->fan_pool2 : c->inc_pool2;
     int rc = cem_scan_i32(c, cnt, n, c->scan_tmp, CNT_SCRATCH0);
     if (rc) return rc;
-    k_defrag<<<cem_grid(n, BS), BS, 0, c->stream>>>(n, c->scan_tmp, off, cnt, pool, pool2);
+    cem_pdl(c->stream, k_defrag, cem_grid(n, BS), BS, n, c->scan_tmp, off, cnt, pool, pool2);
     cem_launched(c, 1);
     CEM_CK(c, cudaGetLastError());
     rc = sync_counts(c);
@@ -756,14 +774,14 @@ int update_lists(cem_ctx* c, int kind, int S, int64_t n_items) {
     int* cnt = kind == 0 ? c->fan_cnt : c->inc_cnt;
     const long long* nsub = c->dcount + CNT_NEWSUB;
     const int bound = 7 * S * per;   // marks: S parents + at most 6 S sub-elements
-    k_mark_affected<<<cem_grid(bound, BS), BS, 0, c->stream>>>(kind, S, c->split_list, nsub, c->T, c->t2e, c->conn,
+    cem_pdl(c->stream, k_mark_affected, cem_grid(bound, BS), BS, kind, S, c->split_list, nsub, c->T, c->t2e, c->conn,
                                                               c->Tc, flag, c->add_cnt);
     cem_launched(c, 1);
     CEM_CK(c, cudaGetLastError());
     int rc = cem_compact_u8(c, flag, n_items, c->aff, CNT_AFFECTED);
     if (rc) return rc;
     int* pool = kind == 0 ? c->fan_pool : c->inc_pool;
-    k_list_count<<<cem_grid(bound, BS), BS, 0, c->stream>>>(kind, c->dcount + CNT_AFFECTED, c->aff, off, cnt, pool,
+    cem_pdl(c->stream, k_list_count, cem_grid(bound, BS), BS, kind, c->dcount + CNT_AFFECTED, c->aff, off, cnt, pool,
                                                            c->active, c->add_cnt, c->aff_keep, c->aff_new, bound);
     cem_launched(c, 1);
     CEM_CK(c, cudaGetLastError());
@@ -785,12 +803,12 @@ int update_lists(cem_ctx* c, int kind, int S, int64_t n_items) {
         }
     }
     pool = kind == 0 ? c->fan_pool : c->inc_pool;
-    k_list_write<<<cem_grid(bound, BS), BS, 0, c->stream>>>(kind, c->dcount + CNT_AFFECTED, c->aff, top, c->aff_off,
+    cem_pdl(c->stream, k_list_write, cem_grid(bound, BS), BS, kind, c->dcount + CNT_AFFECTED, c->aff, top, c->aff_off,
                                                            c->aff_keep, c->aff_new, off, cnt, pool, c->active,
                                                            c->cursor);
-    k_list_append<<<cem_grid(6 * S * per, BS), BS, 0, c->stream>>>(kind, nsub, c->T, c->t2e, c->conn, c->Tc, off,
+    cem_pdl(c->stream, k_list_append, cem_grid(6 * S * per, BS), BS, kind, nsub, c->T, c->t2e, c->conn, c->Tc, off,
                                                                   pool, c->cursor);
-    k_list_finish<<<cem_grid(bound, BS), BS, 0, c->stream>>>(kind, c->dcount + CNT_AFFECTED, c->aff, c->aff_keep, off,
+    cem_pdl(c->stream, k_list_finish, cem_grid(bound, BS), BS, kind, c->dcount + CNT_AFFECTED, c->aff, c->aff_keep, off,
                                                             cnt, pool, flag, c->add_cnt, c->vol, c->lam, c->mu, c->cl,
                                                             c->cm, c->sumV, c->cl32, c->cm32, c->rho, c->mass,
                                                             c->minv);
@@ -803,7 +821,7 @@ int update_lists(cem_ctx* c, int kind, int S, int64_t n_items) {
 
 int cem_launch_front_G(cem_ctx* c) {
     if (c->n_cand > 0) {
-        k_front_G<<<cem_grid(4 * c->n_cand, BS), BS, 0, c->stream>>>(c->cand_list, (int)c->n_cand, c->conn, c->t2e, c->Tc,
+        cem_pdl(c->stream, k_front_G, cem_grid(4 * c->n_cand, BS), BS, c->cand_list, (int)c->n_cand, c->conn, c->t2e, c->Tc,
                                                                  c->face_nbr, c->side, c->T0, c->X, c->u, c->Nc, c->sig,
                                                                  c->sig32, c->Gc, c->dec_mask, c->dec_G);
         cem_launched(c, 1);
@@ -812,7 +830,7 @@ int cem_launch_front_G(cem_ctx* c) {
     int rc = cem_compact_u8(c, c->dec_mask, c->n_cand, c->scan_tmp, CNT_SPLIT);
     if (rc) return rc;
     if (c->n_cand > 0) {
-        k_gather_splits<<<cem_grid(c->n_cand, BS), BS, 0, c->stream>>>(c->scan_tmp, c->dcount + CNT_SPLIT, c->cand_list,
+        cem_pdl(c->stream, k_gather_splits, cem_grid(c->n_cand, BS), BS, c->scan_tmp, c->dcount + CNT_SPLIT, c->cand_list,
                                                                        c->dec_mask, c->dec_G, c->split_list,
                                                                        c->split_mask, c->split_Gv);
         cem_launched(c, 1);
@@ -832,45 +850,45 @@ int cem_apply_splits(cem_ctx* c, int64_t S64, int64_t step, int book_energy) {
     if (c->n_split_all + S > c->S_cap) return cem_fail(c, CEM_ECAPACITY, "split capacity exhausted");
     int rc;
     // 1. new nodes: one per (cut original edge, side) not yet present
-    k_mark_keys<<<cem_grid(S, BS), BS, 0, c->stream>>>(S, c->split_list, c->split_mask, c->t2e, c->Tc, c->node_of_key,
+    cem_pdl(c->stream, k_mark_keys, cem_grid(S, BS), BS, S, c->split_list, c->split_mask, c->t2e, c->Tc, c->node_of_key,
                                                        c->key_flag);
     cem_launched(c, 1);
     CEM_CK(c, cudaGetLastError());
     if ((rc = cem_compact_u8(c, c->key_flag, 2 * c->E0, c->new_keys, CNT_NEWNODE))) return rc;
-    k_create_nodes<<<cem_grid(8 * (int64_t)S, BS), BS, 0, c->stream>>>(
+    cem_pdl(c->stream, k_create_nodes, cem_grid(8 * (int64_t)S, BS), BS, 
         c->dcount + CNT_NEWNODE, c->new_keys, c->N, c->node_of_key, c->key_flag, c->oe_n0, c->oe_n1, c->X, c->u, c->v,
         c->a, c->fext, c->mass, c->minv, c->inc_off, c->inc_cnt, c->Nc, c->node_inst, c->dtn);
     // 2. sub-elements, numbered by (parent, local sub index)
-    k_sub_count<<<cem_grid(S, BS), BS, 0, c->stream>>>(S, c->split_mask, c->aff_new);
+    cem_pdl(c->stream, k_sub_count, cem_grid(S, BS), BS, S, c->split_mask, c->aff_new);
     cem_launched(c, 2);
     CEM_CK(c, cudaGetLastError());
     if ((rc = cem_scan_i32(c, c->aff_new, S, c->sub_off, CNT_NEWSUB))) return rc;
-    k_create_subs<<<cem_grid(S, BS), BS, 0, c->stream>>>(
+    cem_pdl(c->stream, k_create_subs, cem_grid(S, BS), BS, 
         S, c->T, c->split_list, c->split_mask, c->split_Gv, c->sub_off, step, book_energy, c->conn, c->t2e, c->anc,
         c->active, c->Vg, c->Vg32, c->vol, c->lam, c->mu, c->Tc, c->node_of_key, c->X, c->Nc, c->side, c->split_step,
         c->split_G, c->Gc, c->cand_flag, c->ud_part, c->ud_tet);
-    k_ud_sum<<<1, BS, 0, c->stream>>>(S, c->ud_part, c->Ud);
+    cem_pdl(c->stream, k_ud_sum, 1, BS, S, c->ud_part, c->Ud);
     // 3. edges of the sub-elements: parent edges or (new) hashed node pairs
     const long long* nsub = c->dcount + CNT_NEWSUB;
     const int codes = 36 * S;
-    k_sub_edges<<<cem_grid(codes, BS), BS, 0, c->stream>>>(nsub, c->T, c->N0, c->conn, c->t2e, c->anc, c->Tc, c->hkeys,
+    cem_pdl(c->stream, k_sub_edges, cem_grid(codes, BS), BS, nsub, c->T, c->N0, c->conn, c->t2e, c->anc, c->Tc, c->hkeys,
                                                            c->hvals, c->hfirst, c->hash_cap - 1, c->slot_of,
                                                            c->dcount + CNT_ERR);
-    k_edge_owner<<<cem_grid(codes, BS), BS, 0, c->stream>>>(nsub, c->slot_of, c->hvals, c->hfirst, c->code_flag);
+    cem_pdl(c->stream, k_edge_owner, cem_grid(codes, BS), BS, nsub, c->slot_of, c->hvals, c->hfirst, c->code_flag);
     cem_launched(c, 4);
     CEM_CK(c, cudaGetLastError());
     if ((rc = cem_compact_u8(c, c->code_flag, codes, c->code_rank, CNT_NEWEDGE))) return rc;
-    k_edge_assign<<<cem_grid(codes, BS), BS, 0, c->stream>>>(c->dcount + CNT_NEWEDGE, c->code_rank, c->E, c->slot_of,
+    cem_pdl(c->stream, k_edge_assign, cem_grid(codes, BS), BS, c->dcount + CNT_NEWEDGE, c->code_rank, c->E, c->slot_of,
                                                              c->hvals, c->hfirst, c->code_flag, c->fan_off,
                                                              c->fan_cnt, c->cl, c->cm, c->sumV, c->cl32, c->cm32);
-    k_edge_resolve<<<cem_grid(codes, BS), BS, 0, c->stream>>>(nsub, c->T, c->slot_of, c->hvals, c->t2e, c->Tc);
+    cem_pdl(c->stream, k_edge_resolve, cem_grid(codes, BS), BS, nsub, c->T, c->slot_of, c->hvals, c->t2e, c->Tc);
     cem_launched(c, 2);
     CEM_CK(c, cudaGetLastError());
     // 4. fans of affected edges, incidence (and mass) of affected nodes
     if ((rc = update_lists(c, 0, S, c->E + 22 * (int64_t)S))) return rc;
     if ((rc = update_lists(c, 1, S, c->N + 8 * (int64_t)S))) return rc;
     // 5. crack-front candidates
-    k_cand_mark<<<cem_grid(S, BS), BS, 0, c->stream>>>(S, c->split_list, c->split_mask, c->face_nbr, c->T0, c->side,
+    cem_pdl(c->stream, k_cand_mark, cem_grid(S, BS), BS, S, c->split_list, c->split_mask, c->face_nbr, c->T0, c->side,
                                                        c->cand_flag);
     cem_launched(c, 1);
     CEM_CK(c, cudaGetLastError());

@@ -64,6 +64,7 @@ struct PosStore {     // scan: index -> position
 
 template <class Load>
 __global__ void __launch_bounds__(SB) k_scan_reduce(Load ld, int64_t n, int* bsum) {
+    CEM_PDL_ENTRY();
     const int64_t base = (int64_t)blockIdx.x * SCHUNK + (int64_t)threadIdx.x * SI;
     int s = 0;
 #pragma unroll
@@ -77,6 +78,7 @@ __global__ void __launch_bounds__(SB) k_scan_reduce(Load ld, int64_t n, int* bsu
 }
 
 __global__ void __launch_bounds__(SB) k_scan_top(int* bsum, int nb, long long* count) {
+    CEM_PDL_ENTRY();
     int carry = 0;
     for (int base = 0; base < nb; base += SB) {
         const int i = base + threadIdx.x;
@@ -91,6 +93,7 @@ __global__ void __launch_bounds__(SB) k_scan_top(int* bsum, int nb, long long* c
 
 template <class Load, class Store>
 __global__ void __launch_bounds__(SB) k_scan_down(Load ld, Store st, int64_t n, const int* bsum) {
+    CEM_PDL_ENTRY();
     const int64_t base = (int64_t)blockIdx.x * SCHUNK + (int64_t)threadIdx.x * SI;
     int vals[SI];
     int s = 0;
@@ -110,12 +113,13 @@ __global__ void __launch_bounds__(SB) k_scan_down(Load ld, Store st, int64_t n, 
     }
 }
 
-__global__ void k_set_count(long long* count, long long v) { *count = v; }
+__global__ void k_set_count(long long* count, long long v) {
+    CEM_PDL_ENTRY(); *count = v; }
 
 template <class Load, class Store>
 int run_scan(cem_ctx* c, Load ld, Store st, int64_t n, int slot) {
     if (n <= 0) {
-        k_set_count<<<1, 1, 0, c->stream>>>(c->dcount + slot, 0);
+        cem_pdl(c->stream, k_set_count, 1, 1, c->dcount + slot, 0);
         cem_launched(c);
         CEM_CK(c, cudaGetLastError());
         return CEM_OK;
@@ -123,9 +127,9 @@ int run_scan(cem_ctx* c, Load ld, Store st, int64_t n, int slot) {
     const int64_t nb = (n + SCHUNK - 1) / SCHUNK;
     if (nb + 1 > c->scan_blocks_cap)
         return cem_fail(c, CEM_EINVAL, "internal: scan longer than its block buffer");
-    k_scan_reduce<<<(unsigned)nb, SB, 0, c->stream>>>(ld, n, c->scan_blocks);
-    k_scan_top<<<1, SB, 0, c->stream>>>(c->scan_blocks, (int)nb, c->dcount + slot);
-    k_scan_down<<<(unsigned)nb, SB, 0, c->stream>>>(ld, st, n, c->scan_blocks);
+    cem_pdl(c->stream, k_scan_reduce<Load>, (unsigned)nb, SB, ld, n, c->scan_blocks);
+    cem_pdl(c->stream, k_scan_top, 1, SB, c->scan_blocks, (int)nb, c->dcount + slot);
+    cem_pdl(c->stream, (k_scan_down<Load, Store>), (unsigned)nb, SB, ld, st, n, c->scan_blocks);
     cem_launched(c, 3);
     CEM_CK(c, cudaGetLastError());
     return CEM_OK;

@@ -100,6 +100,7 @@ __global__ void __launch_bounds__(BS) k_geometry(const double* __restrict__ X, i
                                                  int64_t t0, int64_t t1, double* __restrict__ Vg,
                                                  float* __restrict__ Vg32, double* __restrict__ vol,
                                                  double* __restrict__ hmin) {
+    CEM_PDL_ENTRY();
     int64_t j = t0 + (int64_t)blockIdx.x * BS + threadIdx.x;
     if (j >= t1) return;
     int n[4] = {conn[j], conn[Tc + j], conn[2 * Tc + j], conn[3 * Tc + j]};
@@ -124,6 +125,7 @@ __global__ void __launch_bounds__(BS) k_predict(double* __restrict__ u, const do
                                                 const double* __restrict__ a, int64_t Nc, int64_t N,
                                                 double dt, double hdt2, float* __restrict__ uhl,
                                                 const double* __restrict__ dtn) {
+    CEM_PDL_ENTRY();
     int64_t i = (int64_t)blockIdx.x * BS + threadIdx.x;
     if (i >= N) return;
     if (dtn) {
@@ -153,6 +155,7 @@ __global__ void __launch_bounds__(BS) k_predict(double* __restrict__ u, const do
 // Split u into FP32 hi/lo records (mixed mode, after set-up or a split).
 __global__ void __launch_bounds__(BS) k_split_u(const double* __restrict__ u, int64_t Nc, int64_t N,
                                                 float* __restrict__ uhl) {
+    CEM_PDL_ENTRY();
     int64_t i = (int64_t)blockIdx.x * BS + threadIdx.x;
     if (i >= N) return;
     float hi[3], lo[3];
@@ -207,6 +210,7 @@ __global__ void __launch_bounds__(BS) k_strain(const double* __restrict__ u, con
                                                int64_t Nc, const int* __restrict__ conn, const R* __restrict__ Vg,
                                                const uint8_t* __restrict__ active, int64_t Tc, int64_t T,
                                                R* __restrict__ h) {
+    CEM_PDL_ENTRY();
     int64_t j = (int64_t)blockIdx.x * BS + threadIdx.x;
     if (j >= T || !active[j]) return;
     const int n[4] = {conn[j], conn[Tc + j], conn[2 * Tc + j], conn[3 * Tc + j]};
@@ -235,6 +239,7 @@ __global__ void __launch_bounds__(BS) k_edge_stress(const R* __restrict__ h, con
                                                     const int* __restrict__ fan_cnt, const int* __restrict__ fan_pool,
                                                     const R* __restrict__ cl, const R* __restrict__ cm, int64_t E,
                                                     R* __restrict__ sig) {
+    CEM_PDL_ENTRY();
     int64_t k = (int64_t)blockIdx.x * BS + threadIdx.x;
     if (k >= E) return;
     const int off = fan_off[k], cnt = fan_cnt[k];
@@ -256,6 +261,7 @@ template <class R>
 __global__ void __launch_bounds__(BS) k_force(const R* __restrict__ sig, const int* __restrict__ t2e,
                                               const R* __restrict__ Vg, const uint8_t* __restrict__ active,
                                               int64_t Tc, int64_t T, R* __restrict__ fp) {
+    CEM_PDL_ENTRY();
     int64_t j = (int64_t)blockIdx.x * BS + threadIdx.x;
     if (j >= T || !active[j]) return;
     R S[6] = {0, 0, 0, 0, 0, 0};
@@ -306,6 +312,7 @@ __global__ void __launch_bounds__(BS) k_node_update(const R* __restrict__ fp, co
                                                     const double* __restrict__ fext, const double* __restrict__ minv,
                                                     double* __restrict__ v, double* __restrict__ a, int64_t Nc,
                                                     int64_t N, double hdt, int first, const double* __restrict__ dtn) {
+    CEM_PDL_ENTRY();
     int64_t i = (int64_t)blockIdx.x * BS + threadIdx.x;
     if (i >= N) return;
     if (dtn) hdt = 0.5 * dtn[i];
@@ -380,6 +387,7 @@ __global__ void __launch_bounds__(BS) k_edge_coeffs(const int* __restrict__ list
                                                     double* __restrict__ cl, double* __restrict__ cm,
                                                     double* __restrict__ sumV, float* __restrict__ cl32,
                                                     float* __restrict__ cm32) {
+    CEM_PDL_ENTRY();
     int64_t i = (int64_t)blockIdx.x * BS + threadIdx.x;
     if (i >= n) return;
     const int k = list ? list[i] : (int)i;
@@ -406,6 +414,7 @@ __global__ void __launch_bounds__(BS) k_node_mass(const int* __restrict__ list, 
                                                   const int* __restrict__ inc_off, const int* __restrict__ inc_cnt,
                                                   const int* __restrict__ inc_pool, const double* __restrict__ vol,
                                                   double rho, double* __restrict__ mass, double* __restrict__ minv) {
+    CEM_PDL_ENTRY();
     int64_t i0 = (int64_t)blockIdx.x * BS + threadIdx.x;
     if (i0 >= n) return;
     const int i = list ? list[i0] : (int)i0;
@@ -420,6 +429,7 @@ __global__ void __launch_bounds__(BS) k_material(const int* __restrict__ anc, in
                                                  const double* __restrict__ E, int nE, const double* __restrict__ Gcin,
                                                  int nGc, double nu, double* __restrict__ lam, double* __restrict__ mu,
                                                  double* __restrict__ Gc) {
+    CEM_PDL_ENTRY();
     int64_t j = (int64_t)blockIdx.x * BS + threadIdx.x;
     if (j >= T) return;
     const int o = anc[j];
@@ -451,6 +461,7 @@ __global__ void __launch_bounds__(RB) k_energy_nodes(const double* __restrict__ 
                                                      const double* __restrict__ a, const double* __restrict__ mass,
                                                      const double* __restrict__ fext, int64_t Nc, int64_t N,
                                                      double* __restrict__ part) {
+    CEM_PDL_ENTRY();
     double x[3] = {0, 0, 0};
     for (int64_t i = (int64_t)blockIdx.x * RB + threadIdx.x; i < N; i += (int64_t)RG * RB) {
         const double m = mass[i];
@@ -472,6 +483,7 @@ template <class R>
 __global__ void __launch_bounds__(RB) k_energy_edges(const R* __restrict__ h, const int* __restrict__ fan_off,
                                                      const int* __restrict__ fan_cnt, const int* __restrict__ fan_pool,
                                                      const R* __restrict__ sig, int64_t E, double* __restrict__ part) {
+    CEM_PDL_ENTRY();
     double x[1] = {0};
     for (int64_t k = (int64_t)blockIdx.x * RB + threadIdx.x; k < E; k += (int64_t)RG * RB) {
         const int off = fan_off[k], cnt = fan_cnt[k];
@@ -499,6 +511,7 @@ __global__ void __launch_bounds__(RB) k_energy_nodes_inst(const double* __restri
                                                           const double* __restrict__ fext,
                                                           const int* __restrict__ node_inst, int inst, int64_t Nc,
                                                           int64_t N, double* __restrict__ part) {
+    CEM_PDL_ENTRY();
     double x[3] = {0, 0, 0};
     for (int64_t i = (int64_t)blockIdx.x * RB + threadIdx.x; i < N; i += (int64_t)RG * RB) {
         if (node_inst && node_inst[i] != inst) continue;
@@ -524,6 +537,7 @@ __global__ void __launch_bounds__(RB) k_energy_edges_inst(const R* __restrict__ 
                                                           const int* __restrict__ anc,
                                                           const int* __restrict__ tet_inst, int inst, int64_t E,
                                                           double* __restrict__ part) {
+    CEM_PDL_ENTRY();
     double x[1] = {0};
     for (int64_t k = (int64_t)blockIdx.x * RB + threadIdx.x; k < E; k += (int64_t)RG * RB) {
         const int off = fan_off[k], cnt = fan_cnt[k];
@@ -546,6 +560,7 @@ __global__ void __launch_bounds__(RB) k_energy_edges_inst(const R* __restrict__ 
 
 __global__ void __launch_bounds__(RB) k_ud_inst(const double* __restrict__ ud_tet, const int* __restrict__ tet_inst,
                                                 int inst, int64_t T0, double* __restrict__ part) {
+    CEM_PDL_ENTRY();
     double x[1] = {0};
     for (int64_t t = (int64_t)blockIdx.x * RB + threadIdx.x; t < T0; t += (int64_t)RG * RB)
         if (!tet_inst || tet_inst[t] == inst) x[0] += ud_tet[t];
@@ -554,12 +569,14 @@ __global__ void __launch_bounds__(RB) k_ud_inst(const double* __restrict__ ud_te
 
 __global__ void __launch_bounds__(BS) k_node_dt(const int* __restrict__ node_inst, const double* __restrict__ inst_dt,
                                                 int64_t N, double* __restrict__ dtn) {
+    CEM_PDL_ENTRY();
     int64_t i = (int64_t)blockIdx.x * BS + threadIdx.x;
     if (i < N) dtn[i] = inst_dt[node_inst[i]];
 }
 
 __global__ void __launch_bounds__(RB) k_reduce_final(const double* __restrict__ part, int nv,
                                                      double* __restrict__ out) {
+    CEM_PDL_ENTRY();
     __shared__ double sh[RB];
     for (int q = 0; q < nv; ++q) {
         double s = 0;
@@ -577,6 +594,7 @@ __global__ void __launch_bounds__(RB) k_reduce_final(const double* __restrict__ 
 
 __global__ void __launch_bounds__(RB) k_count_nonfinite(const double* __restrict__ u, int64_t Nc, int64_t N,
                                                         long long* __restrict__ cnt) {
+    CEM_PDL_ENTRY();
     int bad = 0;
     for (int64_t i = (int64_t)blockIdx.x * RB + threadIdx.x; i < N; i += (int64_t)RG * RB)
         for (int c = 0; c < 3; ++c)
@@ -593,6 +611,7 @@ template <class R>
 __global__ void __launch_bounds__(BS) k_node_force(const R* __restrict__ fp, const int* __restrict__ inc_off,
                                                    const int* __restrict__ inc_cnt, const int* __restrict__ inc_pool,
                                                    int64_t Nc, int64_t N, double* __restrict__ out) {
+    CEM_PDL_ENTRY();
     int64_t i = (int64_t)blockIdx.x * BS + threadIdx.x;
     if (i >= N) return;
     const int off = inc_off[i], cnt = inc_cnt[i];
@@ -621,6 +640,7 @@ __global__ void __launch_bounds__(BS) k_edge_pair(const R* __restrict__ hy, cons
                                                   const int* __restrict__ fan_off, const int* __restrict__ fan_cnt,
                                                   const int* __restrict__ fan_pool, const double* __restrict__ sumV,
                                                   double lamh, double muh, int64_t E, double* __restrict__ s) {
+    CEM_PDL_ENTRY();
     int64_t k = (int64_t)blockIdx.x * BS + threadIdx.x;
     if (k >= E) return;
     const int off = fan_off[k], cnt = fan_cnt[k];
@@ -649,6 +669,7 @@ __global__ void __launch_bounds__(BS) k_edge_pair(const R* __restrict__ hy, cons
 __global__ void __launch_bounds__(BS) k_elem_acc(const double* __restrict__ s, const int* __restrict__ t2e,
                                                  const double* __restrict__ vol, const uint8_t* __restrict__ active,
                                                  int64_t Tc, int64_t T, double coef, double* __restrict__ gE) {
+    CEM_PDL_ENTRY();
     int64_t j = (int64_t)blockIdx.x * BS + threadIdx.x;
     if (j >= T || !active[j]) return;
     double t = 0.0;
@@ -661,6 +682,7 @@ __global__ void __launch_bounds__(RB) k_adj_y(const double* __restrict__ la, con
                                               const double* __restrict__ minv, const double* __restrict__ fext,
                                               double hdt, int64_t Nc, int64_t N, double* __restrict__ y,
                                               double* __restrict__ part) {
+    CEM_PDL_ENTRY();
     double x[1] = {0.0};
     for (int64_t i = (int64_t)blockIdx.x * RB + threadIdx.x; i < N; i += (int64_t)RG * RB) {
         const double mi = minv[i];
@@ -678,6 +700,7 @@ __global__ void __launch_bounds__(RB) k_adj_y(const double* __restrict__ la, con
 __global__ void __launch_bounds__(BS) k_adj_update(double* __restrict__ lu, double* __restrict__ lv,
                                                    double* __restrict__ la, const double* __restrict__ Ky, double dt,
                                                    int64_t Nc, int64_t N) {
+    CEM_PDL_ENTRY();
     int64_t i = (int64_t)blockIdx.x * BS + threadIdx.x;
     if (i >= N) return;
     for (int c = 0; c < 3; ++c) {
@@ -694,6 +717,7 @@ __global__ void __launch_bounds__(BS) k_adj_update(double* __restrict__ lu, doub
 __global__ void __launch_bounds__(RB) k_adj_dot(const double* __restrict__ a, const double* __restrict__ b,
                                                 const double* __restrict__ mscale, int64_t Nc, int64_t N,
                                                 double* __restrict__ part) {
+    CEM_PDL_ENTRY();
     double x[1] = {0.0};
     for (int64_t i = (int64_t)blockIdx.x * RB + threadIdx.x; i < N; i += (int64_t)RG * RB) {
         const double m = mscale ? mscale[i] : 1.0;
@@ -706,6 +730,7 @@ __global__ void __launch_bounds__(RB) k_adj_dot(const double* __restrict__ a, co
 __global__ void __launch_bounds__(BS) k_adj_init(double* __restrict__ lu, double* __restrict__ lv,
                                                  double* __restrict__ la, const double* __restrict__ Ku,
                                                  const double* __restrict__ w, double cK, int64_t Nc, int64_t N) {
+    CEM_PDL_ENTRY();
     int64_t i = (int64_t)blockIdx.x * BS + threadIdx.x;
     if (i >= N) return;
     for (int c = 0; c < 3; ++c) {
@@ -717,6 +742,7 @@ __global__ void __launch_bounds__(BS) k_adj_init(double* __restrict__ lu, double
 }
 
 __global__ void __launch_bounds__(RB) k_reduce_one(const double* __restrict__ part, double* __restrict__ out) {
+    CEM_PDL_ENTRY();
     __shared__ double sh[RB];
     double s = 0;
     for (int i = threadIdx.x; i < RG; i += RB) s += part[i];
@@ -735,12 +761,12 @@ __global__ void __launch_bounds__(RB) k_reduce_one(const double* __restrict__ pa
 // Element strain records of y into hbuf (mixed: through the FP32 hi/lo copy yhl).
 int cem_adj_strain(cem_ctx* c, const double* y, float* yhl, void* hbuf) {
     if (mixed(c)) {
-        k_split_u<<<cem_grid(c->N, BS), BS, 0, c->stream>>>(y, c->Nc, c->N, yhl);
-        k_strain<float><<<cem_grid(c->T, BS), BS, 0, c->stream>>>(y, yhl, c->Nc, c->conn, c->Vg32, c->active, c->Tc,
+        cem_pdl(c->stream, k_split_u, cem_grid(c->N, BS), BS, y, c->Nc, c->N, yhl);
+        cem_pdl(c->stream, k_strain<float>, cem_grid(c->T, BS), BS, y, yhl, c->Nc, c->conn, c->Vg32, c->active, c->Tc,
                                                                   c->T, (float*)hbuf);
         cem_launched(c, 2);
     } else {
-        k_strain<double><<<cem_grid(c->T, BS), BS, 0, c->stream>>>(y, nullptr, c->Nc, c->conn, c->Vg, c->active, c->Tc,
+        cem_pdl(c->stream, k_strain<double>, cem_grid(c->T, BS), BS, y, nullptr, c->Nc, c->conn, c->Vg, c->active, c->Tc,
                                                                    c->T, (double*)hbuf);
         cem_launched(c, 1);
     }
@@ -754,10 +780,10 @@ int cem_adj_apply_K(cem_ctx* c, const double* y, float* yhl, double* Ky) {
     if (rc) return rc;
     if ((rc = cem_launch_edge_stress(c)) || (rc = cem_launch_force(c))) return rc;
     if (mixed(c))
-        k_node_force<float><<<cem_grid(c->N, BS), BS, 0, c->stream>>>(c->fp32, c->inc_off, c->inc_cnt, c->inc_pool,
+        cem_pdl(c->stream, k_node_force<float>, cem_grid(c->N, BS), BS, c->fp32, c->inc_off, c->inc_cnt, c->inc_pool,
                                                                       c->Nc, c->N, Ky);
     else
-        k_node_force<double><<<cem_grid(c->N, BS), BS, 0, c->stream>>>(c->fp, c->inc_off, c->inc_cnt, c->inc_pool,
+        cem_pdl(c->stream, k_node_force<double>, cem_grid(c->N, BS), BS, c->fp, c->inc_off, c->inc_cnt, c->inc_pool,
                                                                        c->Nc, c->N, Ky);
     cem_launched(c);
     CEM_CK(c, cudaGetLastError());
@@ -768,14 +794,14 @@ int cem_adj_apply_K(cem_ctx* c, const double* y, float* yhl, double* Ky) {
 int cem_adj_grad_E(cem_ctx* c, const void* hy, const void* hu, double* s, double coef, double* gE) {
     const double lamh = c->nu / ((1.0 + c->nu) * (1.0 - 2.0 * c->nu)), muh = 1.0 / (2.0 * (1.0 + c->nu));
     if (mixed(c))
-        k_edge_pair<float><<<cem_grid(c->E, BS), BS, 0, c->stream>>>((const float*)hy, (const float*)hu, c->fan_off,
+        cem_pdl(c->stream, k_edge_pair<float>, cem_grid(c->E, BS), BS, (const float*)hy, (const float*)hu, c->fan_off,
                                                                      c->fan_cnt, c->fan_pool, c->sumV, lamh, muh, c->E,
                                                                      s);
     else
-        k_edge_pair<double><<<cem_grid(c->E, BS), BS, 0, c->stream>>>((const double*)hy, (const double*)hu,
+        cem_pdl(c->stream, k_edge_pair<double>, cem_grid(c->E, BS), BS, (const double*)hy, (const double*)hu,
                                                                       c->fan_off, c->fan_cnt, c->fan_pool, c->sumV,
                                                                       lamh, muh, c->E, s);
-    k_elem_acc<<<cem_grid(c->T, BS), BS, 0, c->stream>>>(s, c->t2e, c->vol, c->active, c->Tc, c->T, coef, gE);
+    cem_pdl(c->stream, k_elem_acc, cem_grid(c->T, BS), BS, s, c->t2e, c->vol, c->active, c->Tc, c->T, coef, gE);
     cem_launched(c, 2);
     CEM_CK(c, cudaGetLastError());
     return CEM_OK;
@@ -783,22 +809,22 @@ int cem_adj_grad_E(cem_ctx* c, const void* hy, const void* hu, double* s, double
 
 // y = M^-1 (la + dt/2 lv); *dalpha (device) = y . f_ext.
 int cem_adj_y(cem_ctx* c, const double* la, const double* lv, double* y, double* dalpha) {
-    k_adj_y<<<RG, RB, 0, c->stream>>>(la, lv, c->minv, c->fext, 0.5 * c->dt, c->Nc, c->N, y, c->red_part);
-    k_reduce_one<<<1, RB, 0, c->stream>>>(c->red_part, dalpha);
+    cem_pdl(c->stream, k_adj_y, RG, RB, la, lv, c->minv, c->fext, 0.5 * c->dt, c->Nc, c->N, y, c->red_part);
+    cem_pdl(c->stream, k_reduce_one, 1, RB, c->red_part, dalpha);
     cem_launched(c, 2);
     CEM_CK(c, cudaGetLastError());
     return CEM_OK;
 }
 
 int cem_adj_update(cem_ctx* c, double* lu, double* lv, double* la, const double* Ky) {
-    k_adj_update<<<cem_grid(c->N, BS), BS, 0, c->stream>>>(lu, lv, la, Ky, c->dt, c->Nc, c->N);
+    cem_pdl(c->stream, k_adj_update, cem_grid(c->N, BS), BS, lu, lv, la, Ky, c->dt, c->Nc, c->N);
     cem_launched(c);
     CEM_CK(c, cudaGetLastError());
     return CEM_OK;
 }
 
 int cem_adj_init(cem_ctx* c, double* lu, double* lv, double* la, const double* Ku, const double* w, double cK) {
-    k_adj_init<<<cem_grid(c->N, BS), BS, 0, c->stream>>>(lu, lv, la, Ku, w, cK, c->Nc, c->N);
+    cem_pdl(c->stream, k_adj_init, cem_grid(c->N, BS), BS, lu, lv, la, Ku, w, cK, c->Nc, c->N);
     cem_launched(c);
     CEM_CK(c, cudaGetLastError());
     return CEM_OK;
@@ -806,8 +832,8 @@ int cem_adj_init(cem_ctx* c, double* lu, double* lv, double* la, const double* K
 
 // *out (device) = sum a . (m b) over nodes (m = mscale or 1).
 int cem_adj_dot(cem_ctx* c, const double* a, const double* b, const double* mscale, double* out) {
-    k_adj_dot<<<RG, RB, 0, c->stream>>>(a, b, mscale, c->Nc, c->N, c->red_part);
-    k_reduce_one<<<1, RB, 0, c->stream>>>(c->red_part, out);
+    cem_pdl(c->stream, k_adj_dot, RG, RB, a, b, mscale, c->Nc, c->N, c->red_part);
+    cem_pdl(c->stream, k_reduce_one, 1, RB, c->red_part, out);
     cem_launched(c, 2);
     CEM_CK(c, cudaGetLastError());
     return CEM_OK;
@@ -815,7 +841,7 @@ int cem_adj_dot(cem_ctx* c, const double* a, const double* b, const double* msca
 
 int cem_launch_geometry(cem_ctx* c, int64_t t0, int64_t t1, double* hbuf) {
     if (t1 <= t0) return CEM_OK;
-    k_geometry<<<cem_grid(t1 - t0, BS), BS, 0, c->stream>>>(c->X, c->Nc, c->conn, c->Tc, t0, t1, c->Vg, c->Vg32,
+    cem_pdl(c->stream, k_geometry, cem_grid(t1 - t0, BS), BS, c->X, c->Nc, c->conn, c->Tc, t0, t1, c->Vg, c->Vg32,
                                                             c->vol, hbuf);
     cem_launched(c);
     CEM_CK(c, cudaGetLastError());
@@ -824,7 +850,7 @@ int cem_launch_geometry(cem_ctx* c, int64_t t0, int64_t t1, double* hbuf) {
 
 int cem_launch_predict(cem_ctx* c) {
     if (c->N == 0) return CEM_OK;
-    k_predict<<<cem_grid(c->N, BS), BS, 0, c->stream>>>(c->u, c->v, c->a, c->Nc, c->N, c->dt, 0.5 * c->dt * c->dt,
+    cem_pdl(c->stream, k_predict, cem_grid(c->N, BS), BS, c->u, c->v, c->a, c->Nc, c->N, c->dt, 0.5 * c->dt * c->dt,
                                                         mixed(c) ? c->uhl : nullptr, c->dtn);
     cem_launched(c);
     CEM_CK(c, cudaGetLastError());
@@ -833,7 +859,7 @@ int cem_launch_predict(cem_ctx* c) {
 
 int cem_launch_split_u(cem_ctx* c) {
     if (!mixed(c) || c->N == 0) return CEM_OK;
-    k_split_u<<<cem_grid(c->N, BS), BS, 0, c->stream>>>(c->u, c->Nc, c->N, c->uhl);
+    cem_pdl(c->stream, k_split_u, cem_grid(c->N, BS), BS, c->u, c->Nc, c->N, c->uhl);
     cem_launched(c);
     CEM_CK(c, cudaGetLastError());
     return CEM_OK;
@@ -841,10 +867,10 @@ int cem_launch_split_u(cem_ctx* c) {
 
 int cem_launch_strain(cem_ctx* c) {
     if (mixed(c))
-        k_strain<float><<<cem_grid(c->T, BS), BS, 0, c->stream>>>(c->u, c->uhl, c->Nc, c->conn, c->Vg32, c->active, c->Tc,
+        cem_pdl(c->stream, k_strain<float>, cem_grid(c->T, BS), BS, c->u, c->uhl, c->Nc, c->conn, c->Vg32, c->active, c->Tc,
                                                                   c->T, c->h32);
     else
-        k_strain<double><<<cem_grid(c->T, BS), BS, 0, c->stream>>>(c->u, nullptr, c->Nc, c->conn, c->Vg, c->active, c->Tc,
+        cem_pdl(c->stream, k_strain<double>, cem_grid(c->T, BS), BS, c->u, nullptr, c->Nc, c->conn, c->Vg, c->active, c->Tc,
                                                                    c->T, c->h);
     cem_launched(c);
     CEM_CK(c, cudaGetLastError());
@@ -853,10 +879,10 @@ int cem_launch_strain(cem_ctx* c) {
 
 int cem_launch_edge_stress(cem_ctx* c) {
     if (mixed(c))
-        k_edge_stress<float><<<cem_grid(c->E, BS), BS, 0, c->stream>>>(c->h32, c->fan_off, c->fan_cnt, c->fan_pool,
+        cem_pdl(c->stream, k_edge_stress<float>, cem_grid(c->E, BS), BS, c->h32, c->fan_off, c->fan_cnt, c->fan_pool,
                                                                        c->cl32, c->cm32, c->E, c->sig32);
     else
-        k_edge_stress<double><<<cem_grid(c->E, BS), BS, 0, c->stream>>>(c->h, c->fan_off, c->fan_cnt, c->fan_pool,
+        cem_pdl(c->stream, k_edge_stress<double>, cem_grid(c->E, BS), BS, c->h, c->fan_off, c->fan_cnt, c->fan_pool,
                                                                         c->cl, c->cm, c->E, c->sig);
     cem_launched(c);
     CEM_CK(c, cudaGetLastError());
@@ -865,10 +891,10 @@ int cem_launch_edge_stress(cem_ctx* c) {
 
 int cem_launch_force(cem_ctx* c) {
     if (mixed(c))
-        k_force<float><<<cem_grid(c->T, BS), BS, 0, c->stream>>>(c->sig32, c->t2e, c->Vg32, c->active, c->Tc, c->T,
+        cem_pdl(c->stream, k_force<float>, cem_grid(c->T, BS), BS, c->sig32, c->t2e, c->Vg32, c->active, c->Tc, c->T,
                                                                  c->fp32);
     else
-        k_force<double><<<cem_grid(c->T, BS), BS, 0, c->stream>>>(c->sig, c->t2e, c->Vg, c->active, c->Tc, c->T,
+        cem_pdl(c->stream, k_force<double>, cem_grid(c->T, BS), BS, c->sig, c->t2e, c->Vg, c->active, c->Tc, c->T,
                                                                   c->fp);
     cem_launched(c);
     CEM_CK(c, cudaGetLastError());
@@ -877,11 +903,11 @@ int cem_launch_force(cem_ctx* c) {
 
 int cem_launch_node_update(cem_ctx* c, int first) {
     if (mixed(c))
-        k_node_update<float><<<cem_grid(c->N, BS), BS, 0, c->stream>>>(
+        cem_pdl(c->stream, k_node_update<float>, cem_grid(c->N, BS), BS, 
             c->fp32, c->inc_off, c->inc_cnt, c->inc_pool, c->fext, c->minv, c->v, c->a, c->Nc, c->N, 0.5 * c->dt, first,
             c->dtn);
     else
-        k_node_update<double><<<cem_grid(c->N, BS), BS, 0, c->stream>>>(
+        cem_pdl(c->stream, k_node_update<double>, cem_grid(c->N, BS), BS, 
             c->fp, c->inc_off, c->inc_cnt, c->inc_pool, c->fext, c->minv, c->v, c->a, c->Nc, c->N, 0.5 * c->dt, first,
             c->dtn);
     cem_launched(c);
@@ -892,7 +918,7 @@ int cem_launch_node_update(cem_ctx* c, int first) {
 int cem_launch_edge_coeffs(cem_ctx* c, const int* list, int64_t n) {
     if (!list) n = c->E;
     if (n <= 0) return CEM_OK;
-    k_edge_coeffs<<<cem_grid(n, BS), BS, 0, c->stream>>>(list, n, c->fan_off, c->fan_cnt, c->fan_pool, c->vol, c->lam,
+    cem_pdl(c->stream, k_edge_coeffs, cem_grid(n, BS), BS, list, n, c->fan_off, c->fan_cnt, c->fan_pool, c->vol, c->lam,
                                                          c->mu, c->cl, c->cm, c->sumV, c->cl32, c->cm32);
     cem_launched(c);
     CEM_CK(c, cudaGetLastError());
@@ -902,7 +928,7 @@ int cem_launch_edge_coeffs(cem_ctx* c, const int* list, int64_t n) {
 int cem_launch_node_mass(cem_ctx* c, const int* list, int64_t n) {
     if (!list) n = c->N;
     if (n <= 0) return CEM_OK;
-    k_node_mass<<<cem_grid(n, BS), BS, 0, c->stream>>>(list, n, c->inc_off, c->inc_cnt, c->inc_pool, c->vol, c->rho,
+    cem_pdl(c->stream, k_node_mass, cem_grid(n, BS), BS, list, n, c->inc_off, c->inc_cnt, c->inc_pool, c->vol, c->rho,
                                                        c->mass, c->minv);
     cem_launched(c);
     CEM_CK(c, cudaGetLastError());
@@ -910,7 +936,7 @@ int cem_launch_node_mass(cem_ctx* c, const int* list, int64_t n) {
 }
 
 int cem_launch_material(cem_ctx* c, const double* E, int nE, const double* Gc, int nGc) {
-    k_material<<<cem_grid(c->T, BS), BS, 0, c->stream>>>(c->anc, c->T, c->T0, E, nE, Gc, nGc, c->nu, c->lam, c->mu,
+    cem_pdl(c->stream, k_material, cem_grid(c->T, BS), BS, c->anc, c->T, c->T0, E, nE, Gc, nGc, c->nu, c->lam, c->mu,
                                                          c->Gc);
     cem_launched(c);
     CEM_CK(c, cudaGetLastError());
@@ -919,14 +945,14 @@ int cem_launch_material(cem_ctx* c, const double* E, int nE, const double* Gc, i
 
 // out = {kinetic, ext_work, aMa, strain}; needs h and sig of the current state.
 int cem_energy_reduce(cem_ctx* c, double out[4]) {
-    k_energy_nodes<<<RG, RB, 0, c->stream>>>(c->u, c->v, c->a, c->mass, c->fext, c->Nc, c->N, c->red_part);
+    cem_pdl(c->stream, k_energy_nodes, RG, RB, c->u, c->v, c->a, c->mass, c->fext, c->Nc, c->N, c->red_part);
     if (mixed(c))
-        k_energy_edges<float><<<RG, RB, 0, c->stream>>>(c->h32, c->fan_off, c->fan_cnt, c->fan_pool, c->sig32, c->E,
+        cem_pdl(c->stream, k_energy_edges<float>, RG, RB, c->h32, c->fan_off, c->fan_cnt, c->fan_pool, c->sig32, c->E,
                                                         c->red_part);
     else
-        k_energy_edges<double><<<RG, RB, 0, c->stream>>>(c->h, c->fan_off, c->fan_cnt, c->fan_pool, c->sig, c->E,
+        cem_pdl(c->stream, k_energy_edges<double>, RG, RB, c->h, c->fan_off, c->fan_cnt, c->fan_pool, c->sig, c->E,
                                                          c->red_part);
-    k_reduce_final<<<1, RB, 0, c->stream>>>(c->red_part, 4, c->red_out);
+    cem_pdl(c->stream, k_reduce_final, 1, RB, c->red_part, 4, c->red_out);
     cem_launched(c, 3);
     CEM_CK(c, cudaGetLastError());
     CEM_CK(c, cudaMemcpyAsync(c->hred, c->red_out, 4 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
@@ -937,16 +963,16 @@ int cem_energy_reduce(cem_ctx* c, double out[4]) {
 
 // out = {kinetic, ext_work, aMa, strain, U_d} of specimen inst.
 int cem_energy_reduce_instance(cem_ctx* c, int inst, double out[5]) {
-    k_energy_nodes_inst<<<RG, RB, 0, c->stream>>>(c->u, c->v, c->a, c->mass, c->fext, c->node_inst, inst, c->Nc, c->N,
+    cem_pdl(c->stream, k_energy_nodes_inst, RG, RB, c->u, c->v, c->a, c->mass, c->fext, c->node_inst, inst, c->Nc, c->N,
                                                   c->red_part);
     if (mixed(c))
-        k_energy_edges_inst<float><<<RG, RB, 0, c->stream>>>(c->h32, c->fan_off, c->fan_cnt, c->fan_pool, c->sig32,
+        cem_pdl(c->stream, k_energy_edges_inst<float>, RG, RB, c->h32, c->fan_off, c->fan_cnt, c->fan_pool, c->sig32,
                                                              c->anc, c->tet_inst, inst, c->E, c->red_part);
     else
-        k_energy_edges_inst<double><<<RG, RB, 0, c->stream>>>(c->h, c->fan_off, c->fan_cnt, c->fan_pool, c->sig,
+        cem_pdl(c->stream, k_energy_edges_inst<double>, RG, RB, c->h, c->fan_off, c->fan_cnt, c->fan_pool, c->sig,
                                                               c->anc, c->tet_inst, inst, c->E, c->red_part);
-    k_ud_inst<<<RG, RB, 0, c->stream>>>(c->ud_tet, c->tet_inst, inst, c->T0, c->red_part);
-    k_reduce_final<<<1, RB, 0, c->stream>>>(c->red_part, 5, c->red_out);
+    cem_pdl(c->stream, k_ud_inst, RG, RB, c->ud_tet, c->tet_inst, inst, c->T0, c->red_part);
+    cem_pdl(c->stream, k_reduce_final, 1, RB, c->red_part, 5, c->red_out);
     cem_launched(c, 4);
     CEM_CK(c, cudaGetLastError());
     CEM_CK(c, cudaMemcpyAsync(c->hred, c->red_out, 5 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
@@ -957,7 +983,7 @@ int cem_energy_reduce_instance(cem_ctx* c, int inst, double out[5]) {
 
 int cem_launch_node_dt(cem_ctx* c) {
     if (!c->dtn || c->N == 0) return CEM_OK;
-    k_node_dt<<<cem_grid(c->N, BS), BS, 0, c->stream>>>(c->node_inst, c->inst_dt_dev, c->N, c->dtn);
+    cem_pdl(c->stream, k_node_dt, cem_grid(c->N, BS), BS, c->node_inst, c->inst_dt_dev, c->N, c->dtn);
     cem_launched(c);
     CEM_CK(c, cudaGetLastError());
     return CEM_OK;
@@ -965,7 +991,7 @@ int cem_launch_node_dt(cem_ctx* c) {
 
 int cem_launch_check_finite(cem_ctx* c) {
     CEM_CK(c, cudaMemsetAsync(c->dcount + CNT_SCRATCH1, 0, sizeof(long long), c->stream));
-    k_count_nonfinite<<<RG, RB, 0, c->stream>>>(c->u, c->Nc, c->N, c->dcount + CNT_SCRATCH1);
+    cem_pdl(c->stream, k_count_nonfinite, RG, RB, c->u, c->Nc, c->N, c->dcount + CNT_SCRATCH1);
     cem_launched(c);
     CEM_CK(c, cudaGetLastError());
     return CEM_OK;
