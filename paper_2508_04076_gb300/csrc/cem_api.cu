@@ -309,7 +309,7 @@ int create_impl(const cem_mesh_desc* d, cem_ctx* c) {
     ok = ok && dalloc(c, c->aff, aff_cap) && dalloc(c, c->aff_keep, aff_cap) && dalloc(c, c->aff_new, aff_cap) &&
          dalloc(c, c->aff_off, aff_cap);
     ok = ok && dalloc(c, c->add_cnt, big) && dalloc(c, c->cursor, big) && dalloc(c, c->scan_tmp, scan_max);
-    ok = ok && dalloc(c, c->scan_blocks, c->scan_blocks_cap);
+    ok = ok && dalloc(c, c->scan_status, c->scan_blocks_cap) && dalloc(c, c->scan_ticket, 1);
     ok = ok && dalloc(c, c->red_part, cem_reduction_doubles()) && dalloc(c, c->red_out, 8);
     ok = ok && dalloc(c, c->dcount, CNT_COUNT);
     if (!ok) return cem_fail(c, CEM_ENOMEM, "device allocation failed");
@@ -368,6 +368,8 @@ int create_impl(const cem_mesh_desc* d, cem_ctx* c) {
     CEM_CK(c, cudaMemsetAsync(c->inc_cnt, 0, Nc * sizeof(int), s));
     CEM_CK(c, cudaMemsetAsync(c->inc_off, 0, Nc * sizeof(int), s));
     CEM_CK(c, cudaMemsetAsync(c->dcount, 0, CNT_COUNT * sizeof(long long), s));
+    CEM_CK(c, cudaMemsetAsync(c->scan_status, 0, c->scan_blocks_cap * sizeof(unsigned long long), s));
+    CEM_CK(c, cudaMemsetAsync(c->scan_ticket, 0, sizeof(unsigned int), s));
 
     // uploads (structure of arrays)
     {
@@ -540,6 +542,8 @@ int run_step(cem_ctx* c) {
         TIMED(c, CEM_KERNEL_FRONT_G, cem_launch_front_G(c));
         int rc;
         if ((rc = sync_counts(c))) return rc;
+        if (c->hcount[CNT_ERR] & DERR_SCAN_WAIT)
+            return cem_fail(c, CEM_ETIMEOUT, "a scan's bounded look-back wait gave up");
         const int64_t S = c->hcount[CNT_SPLIT];
         if (S > 0) {
             if (c->n_split_all + S > c->S_cap)

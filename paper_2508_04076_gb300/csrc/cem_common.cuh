@@ -47,7 +47,7 @@ enum {
     CNT_COUNT
 };
 
-enum { DERR_HASH_FULL = 1, DERR_CAPACITY = 2 };
+enum { DERR_HASH_FULL = 1, DERR_CAPACITY = 2, DERR_SCAN_WAIT = 4 };
 
 struct cem_ctx {
     // sizes: original, capacity, current (host mirrors of the device state)
@@ -125,7 +125,10 @@ struct cem_ctx {
     int *aff = nullptr, *aff_keep = nullptr, *aff_new = nullptr, *aff_off = nullptr;
     int *add_cnt = nullptr, *cursor = nullptr;           // [max(Ec, Nc)]
     int* scan_tmp = nullptr;                            // positions, [max scan length]
-    int* scan_blocks = nullptr;                         // block sums
+    int* scan_blocks = nullptr;                         // (unused by the single-pass scan)
+    unsigned long long* scan_status = nullptr;          // look-back status words, one per block
+    unsigned int* scan_ticket = nullptr;                // block tickets of the running scan
+    unsigned long long scan_epoch = 0;
     // reductions
     double* red_part = nullptr;   // block partials
     double* red_out = nullptr;    // final values

@@ -22,7 +22,7 @@
 // edge on that side.  New nodes, elements and edges are numbered in a
 // canonical order (ascending key / parent / first reference) with ordered
 // scans, so the topology is identical on every run.
-#include "cem_common.cuh"
+#include "cem_scan.cuh"
 
 #include <climits>
 
@@ -237,24 +237,94 @@ __global__ void __launch_bounds__(BS) k_front_G(const int* __restrict__ cand_lis
     }
 }
 
-// ------------------------------------------------------------------ split list
-__global__ void k_gather_splits(const int* __restrict__ pos, const long long* __restrict__ count,
-                                const int* __restrict__ cand_list, const uint8_t* __restrict__ dec_mask,
-                                const double* __restrict__ dec_G, int* __restrict__ split_list,
-                                uint8_t* __restrict__ split_mask, double* __restrict__ split_G) {
-    CEM_PDL_ENTRY();
-    const int i = blockIdx.x * BS + threadIdx.x;
-    if (i >= *count) return;
-    const int ci = pos[i];
-    split_list[i] = cand_list[ci];
-    split_mask[i] = dec_mask[ci];
-    split_G[i] = dec_G[ci];
-}
+// ------------------------------------------------------------------ scan functors
+struct U8Load {
+    const uint8_t* f;
+    __device__ int operator()(int64_t i) const { return f[i] != 0; }
+};
 
-// ------------------------------------------------------------------ new nodes
-__global__ void k_mark_keys(int S, const int* __restrict__ split_list, const uint8_t* __restrict__ split_mask,
-                            const int* __restrict__ t2e, int64_t Tc, const int* __restrict__ node_of_key,
-                            uint8_t* __restrict__ key_flag) {
+// The decisions of front element i, kept in candidate (ascending element) order.
+struct SplitStore {
+    const int* cand_list;
+    const uint8_t* dec_mask;
+    const double* dec_G;
+    int* split_list;
+    uint8_t* split_mask;
+    double* split_G;
+    __device__ void operator()(int64_t i, int pos, int val) const {
+        if (!val) return;
+        split_list[pos] = cand_list[i];
+        split_mask[pos] = dec_mask[i];
+        split_G[pos] = dec_G[i];
+    }
+};
+
+// New node for flagged key i = 2 e + side: id N + rank, at the midpoint of
+// original edge e with the mean u, v, a of its ends.
+struct NodeStore {
+    int64_t N, Nc;
+    int* node_of_key;
+    uint8_t* key_flag;
+    const int *oe_n0, *oe_n1;
+    double *X, *u, *v, *a, *fext, *mass, *minv, *dtn;
+    int *inc_off, *inc_cnt, *node_inst;
+    __device__ void operator()(int64_t key, int pos, int val) const {
+        if (!val) return;
+        const int e = (int)(key >> 1);
+        const int64_t id = N + pos;
+        node_of_key[key] = (int)id;
+        key_flag[key] = 0;
+        const int n0 = oe_n0[e], n1 = oe_n1[e];
+        for (int c = 0; c < 3; ++c) {
+            X[c * Nc + id] = 0.5 * (X[c * Nc + n0] + X[c * Nc + n1]);
+            u[c * Nc + id] = 0.5 * (u[c * Nc + n0] + u[c * Nc + n1]);
+            v[c * Nc + id] = 0.5 * (v[c * Nc + n0] + v[c * Nc + n1]);
+            a[c * Nc + id] = 0.5 * (a[c * Nc + n0] + a[c * Nc + n1]);
+            fext[c * Nc + id] = 0.0;
+        }
+        mass[id] = 0.0;
+        minv[id] = 0.0;
+        inc_off[id] = 0;
+        inc_cnt[id] = 0;
+        if (node_inst) node_inst[id] = node_inst[n0];
+        if (dtn) dtn[id] = dtn[n0];
+    }
+};
+
+// New edge for owner code i (first reference of a new node pair): id E + rank.
+struct EdgeStore {
+    int64_t E;
+    const int* slot_of;
+    int *hvals, *hfirst;
+    uint8_t* code_flag;
+    int *fan_off, *fan_cnt;
+    double *cl, *cm, *sumV;
+    float *cl32, *cm32;
+    __device__ void operator()(int64_t code, int pos, int val) const {
+        if (!val) return;
+        const int s = slot_of[code];
+        const int64_t e = E + pos;
+        hvals[s] = (int)e;
+        hfirst[s] = INT_MAX;
+        code_flag[code] = 0;
+        fan_off[e] = 0;
+        fan_cnt[e] = 0;
+        cl[e] = 0.0;
+        cm[e] = 0.0;
+        sumV[e] = 0.0;
+        if (cl32) {
+            cl32[e] = 0.f;
+            cm32[e] = 0.f;
+        }
+    }
+};
+
+// ------------------------------------------------------------------ new nodes and sub-elements
+// Per split: flag the (cut edge, side) keys that have no node yet, and count
+// its sub-elements (6 for pattern I, 4 for pattern II).
+__global__ void k_split_prep(int S, const int* __restrict__ split_list, const uint8_t* __restrict__ split_mask,
+                             const int* __restrict__ t2e, int64_t Tc, const int* __restrict__ node_of_key,
+                             uint8_t* __restrict__ key_flag, int* __restrict__ cnt) {
     CEM_PDL_ENTRY();
     const int i = blockIdx.x * BS + threadIdx.x;
     if (i >= S) return;
@@ -267,46 +337,9 @@ __global__ void k_mark_keys(int S, const int* __restrict__ split_list, const uin
                 if (node_of_key[2 * e + s] < 0) key_flag[2 * e + s] = 1;
         }
     }
+    cnt[i] = (__popc((unsigned)m) == 2) ? 6 : 4;
 }
 
-__global__ void k_create_nodes(const long long* __restrict__ count, const int* __restrict__ new_keys, int64_t N,
-                               int* __restrict__ node_of_key, uint8_t* __restrict__ key_flag,
-                               const int* __restrict__ oe_n0, const int* __restrict__ oe_n1, double* __restrict__ X,
-                               double* __restrict__ u, double* __restrict__ v, double* __restrict__ a,
-                               double* __restrict__ fext, double* __restrict__ mass, double* __restrict__ minv,
-                               int* __restrict__ inc_off, int* __restrict__ inc_cnt, int64_t Nc,
-                               int* __restrict__ node_inst, double* __restrict__ dtn) {
-    CEM_PDL_ENTRY();
-    const int i = blockIdx.x * BS + threadIdx.x;
-    if (i >= *count) return;
-    const int key = new_keys[i];
-    const int e = key >> 1;
-    const int64_t id = N + i;
-    node_of_key[key] = (int)id;
-    key_flag[key] = 0;
-    const int n0 = oe_n0[e], n1 = oe_n1[e];
-    for (int c = 0; c < 3; ++c) {
-        X[c * Nc + id] = 0.5 * (X[c * Nc + n0] + X[c * Nc + n1]);
-        u[c * Nc + id] = 0.5 * (u[c * Nc + n0] + u[c * Nc + n1]);
-        v[c * Nc + id] = 0.5 * (v[c * Nc + n0] + v[c * Nc + n1]);
-        a[c * Nc + id] = 0.5 * (a[c * Nc + n0] + a[c * Nc + n1]);
-        fext[c * Nc + id] = 0.0;
-    }
-    mass[id] = 0.0;
-    minv[id] = 0.0;
-    inc_off[id] = 0;
-    inc_cnt[id] = 0;
-    if (node_inst) node_inst[id] = node_inst[n0];
-    if (dtn) dtn[id] = dtn[n0];
-}
-
-// ------------------------------------------------------------------ sub-elements
-__global__ void k_sub_count(int S, const uint8_t* __restrict__ split_mask, int* __restrict__ cnt) {
-    CEM_PDL_ENTRY();
-    const int i = blockIdx.x * BS + threadIdx.x;
-    if (i >= S) return;
-    cnt[i] = (__popc((unsigned)split_mask[i]) == 2) ? 6 : 4;
-}
 
 struct SubCtx {
     const int* pn;        // parent's 4 node ids
@@ -540,30 +573,6 @@ __global__ void k_edge_owner(const long long* __restrict__ nsub, const int* __re
     code_flag[c] = (s >= 0 && hvals[s] < 0 && hfirst[s] == c) ? 1 : 0;
 }
 
-__global__ void k_edge_assign(const long long* __restrict__ count, const int* __restrict__ owners, int64_t E,
-                              const int* __restrict__ slot_of, int* __restrict__ hvals, int* __restrict__ hfirst,
-                              uint8_t* __restrict__ code_flag, int* __restrict__ fan_off, int* __restrict__ fan_cnt,
-                              double* __restrict__ cl, double* __restrict__ cm, double* __restrict__ sumV,
-                              float* __restrict__ cl32, float* __restrict__ cm32) {
-    CEM_PDL_ENTRY();
-    const int r = blockIdx.x * BS + threadIdx.x;
-    if (r >= *count) return;
-    const int c = owners[r];
-    const int s = slot_of[c];
-    const int64_t e = E + r;
-    hvals[s] = (int)e;
-    hfirst[s] = INT_MAX;
-    code_flag[c] = 0;
-    fan_off[e] = 0;
-    fan_cnt[e] = 0;
-    cl[e] = 0.0;
-    cm[e] = 0.0;
-    sumV[e] = 0.0;
-    if (cl32) {
-        cl32[e] = 0.f;
-        cm32[e] = 0.f;
-    }
-}
 
 __global__ void k_edge_resolve(const long long* __restrict__ nsub, int64_t T, const int* __restrict__ slot_of,
                                const int* __restrict__ hvals, int* __restrict__ t2e, int64_t Tc) {
@@ -827,16 +836,9 @@ int cem_launch_front_G(cem_ctx* c) {
         cem_launched(c, 1);
         CEM_CK(c, cudaGetLastError());
     }
-    int rc = cem_compact_u8(c, c->dec_mask, c->n_cand, c->scan_tmp, CNT_SPLIT);
-    if (rc) return rc;
-    if (c->n_cand > 0) {
-        cem_pdl(c->stream, k_gather_splits, cem_grid(c->n_cand, BS), BS, c->scan_tmp, c->dcount + CNT_SPLIT, c->cand_list,
-                                                                       c->dec_mask, c->dec_G, c->split_list,
-                                                                       c->split_mask, c->split_Gv);
-        cem_launched(c, 1);
-        CEM_CK(c, cudaGetLastError());
-    }
-    return CEM_OK;
+    return run_scan(c, U8Load{c->dec_mask},
+                    SplitStore{c->cand_list, c->dec_mask, c->dec_G, c->split_list, c->split_mask, c->split_Gv},
+                    c->n_cand, CNT_SPLIT);
 }
 
 // Apply the S splits held in split_list / split_mask / split_Gv (ascending
@@ -849,40 +851,38 @@ int cem_apply_splits(cem_ctx* c, int64_t S64, int64_t step, int book_energy) {
     const int S = (int)S64;
     if (c->n_split_all + S > c->S_cap) return cem_fail(c, CEM_ECAPACITY, "split capacity exhausted");
     int rc;
-    // 1. new nodes: one per (cut original edge, side) not yet present
-    cem_pdl(c->stream, k_mark_keys, cem_grid(S, BS), BS, S, c->split_list, c->split_mask, c->t2e, c->Tc, c->node_of_key,
-                                                       c->key_flag);
+    // 1. new nodes: one per (cut original edge, side) not yet present; sub-element counts
+    cem_pdl(c->stream, k_split_prep, cem_grid(S, BS), BS, S, c->split_list, c->split_mask, c->t2e, c->Tc,
+            c->node_of_key, c->key_flag, c->aff_new);
     cem_launched(c, 1);
     CEM_CK(c, cudaGetLastError());
-    if ((rc = cem_compact_u8(c, c->key_flag, 2 * c->E0, c->new_keys, CNT_NEWNODE))) return rc;
-    cem_pdl(c->stream, k_create_nodes, cem_grid(8 * (int64_t)S, BS), BS, 
-        c->dcount + CNT_NEWNODE, c->new_keys, c->N, c->node_of_key, c->key_flag, c->oe_n0, c->oe_n1, c->X, c->u, c->v,
-        c->a, c->fext, c->mass, c->minv, c->inc_off, c->inc_cnt, c->Nc, c->node_inst, c->dtn);
+    if ((rc = run_scan(c, U8Load{c->key_flag},
+                       NodeStore{c->N, c->Nc, c->node_of_key, c->key_flag, c->oe_n0, c->oe_n1, c->X, c->u, c->v, c->a,
+                                 c->fext, c->mass, c->minv, c->dtn, c->inc_off, c->inc_cnt, c->node_inst},
+                       2 * c->E0, CNT_NEWNODE)))
+        return rc;
     // 2. sub-elements, numbered by (parent, local sub index)
-    cem_pdl(c->stream, k_sub_count, cem_grid(S, BS), BS, S, c->split_mask, c->aff_new);
-    cem_launched(c, 2);
-    CEM_CK(c, cudaGetLastError());
     if ((rc = cem_scan_i32(c, c->aff_new, S, c->sub_off, CNT_NEWSUB))) return rc;
-    cem_pdl(c->stream, k_create_subs, cem_grid(S, BS), BS, 
-        S, c->T, c->split_list, c->split_mask, c->split_Gv, c->sub_off, step, book_energy, c->conn, c->t2e, c->anc,
-        c->active, c->Vg, c->Vg32, c->vol, c->lam, c->mu, c->Tc, c->node_of_key, c->X, c->Nc, c->side, c->split_step,
-        c->split_G, c->Gc, c->cand_flag, c->ud_part, c->ud_tet);
+    cem_pdl(c->stream, k_create_subs, cem_grid(S, BS), BS,
+            S, c->T, c->split_list, c->split_mask, c->split_Gv, c->sub_off, step, book_energy, c->conn, c->t2e, c->anc,
+            c->active, c->Vg, c->Vg32, c->vol, c->lam, c->mu, c->Tc, c->node_of_key, c->X, c->Nc, c->side,
+            c->split_step, c->split_G, c->Gc, c->cand_flag, c->ud_part, c->ud_tet);
     cem_pdl(c->stream, k_ud_sum, 1, BS, S, c->ud_part, c->Ud);
     // 3. edges of the sub-elements: parent edges or (new) hashed node pairs
     const long long* nsub = c->dcount + CNT_NEWSUB;
     const int codes = 36 * S;
-    cem_pdl(c->stream, k_sub_edges, cem_grid(codes, BS), BS, nsub, c->T, c->N0, c->conn, c->t2e, c->anc, c->Tc, c->hkeys,
-                                                           c->hvals, c->hfirst, c->hash_cap - 1, c->slot_of,
-                                                           c->dcount + CNT_ERR);
+    cem_pdl(c->stream, k_sub_edges, cem_grid(codes, BS), BS, nsub, c->T, c->N0, c->conn, c->t2e, c->anc, c->Tc,
+            c->hkeys, c->hvals, c->hfirst, c->hash_cap - 1, c->slot_of, c->dcount + CNT_ERR);
     cem_pdl(c->stream, k_edge_owner, cem_grid(codes, BS), BS, nsub, c->slot_of, c->hvals, c->hfirst, c->code_flag);
     cem_launched(c, 4);
     CEM_CK(c, cudaGetLastError());
-    if ((rc = cem_compact_u8(c, c->code_flag, codes, c->code_rank, CNT_NEWEDGE))) return rc;
-    cem_pdl(c->stream, k_edge_assign, cem_grid(codes, BS), BS, c->dcount + CNT_NEWEDGE, c->code_rank, c->E, c->slot_of,
-                                                             c->hvals, c->hfirst, c->code_flag, c->fan_off,
-                                                             c->fan_cnt, c->cl, c->cm, c->sumV, c->cl32, c->cm32);
+    if ((rc = run_scan(c, U8Load{c->code_flag},
+                       EdgeStore{c->E, c->slot_of, c->hvals, c->hfirst, c->code_flag, c->fan_off, c->fan_cnt, c->cl,
+                                 c->cm, c->sumV, c->cl32, c->cm32},
+                       codes, CNT_NEWEDGE)))
+        return rc;
     cem_pdl(c->stream, k_edge_resolve, cem_grid(codes, BS), BS, nsub, c->T, c->slot_of, c->hvals, c->t2e, c->Tc);
-    cem_launched(c, 2);
+    cem_launched(c, 1);
     CEM_CK(c, cudaGetLastError());
     // 4. fans of affected edges, incidence (and mass) of affected nodes
     if ((rc = update_lists(c, 0, S, c->E + 22 * (int64_t)S))) return rc;
@@ -894,7 +894,8 @@ int cem_apply_splits(cem_ctx* c, int64_t S64, int64_t step, int book_energy) {
     CEM_CK(c, cudaGetLastError());
     if ((rc = cem_compact_u8(c, c->cand_flag, c->T0, c->cand_list, CNT_CAND))) return rc;
     if ((rc = sync_counts(c))) return rc;
-    if (c->hcount[CNT_ERR]) return cem_fail(c, CEM_ECAPACITY, "edge hash table full");
+    if (c->hcount[CNT_ERR] & DERR_SCAN_WAIT) return cem_fail(c, CEM_ETIMEOUT, "a scan's bounded look-back wait gave up");
+    if (c->hcount[CNT_ERR] & DERR_HASH_FULL) return cem_fail(c, CEM_ECAPACITY, "edge hash table full");
     const int64_t NN = c->hcount[CNT_NEWNODE], NS = c->hcount[CNT_NEWSUB], NE = c->hcount[CNT_NEWEDGE];
     if (c->N + NN > c->Nc || c->T + NS > c->Tc || c->E + NE > c->Ec)
         return cem_fail(c, CEM_ECAPACITY, "node/element/edge capacity exhausted");
