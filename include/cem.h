@@ -67,6 +67,16 @@ extern "C" {
 #define CEM_PATTERN_I  1    /* quadrilateral G1 G2 G4 G3: two nodes on each side      */
 #define CEM_PATTERN_II 2    /* triangle G1 G2 G6: one node cut off                    */
 
+/* split rule (cem_mesh_desc.split_mode) */
+#define CEM_SPLIT_SUBDIVIDE  0  /* the split element is replaced by sub-tetrahedra on    */
+                                /* both sides of its crack (its remainder keeps working) */
+#define CEM_SPLIT_DEACTIVATE 1  /* the split element only leaves the computation         */
+                                /* (literal wording of Sec. 1 and the conclusion)        */
+
+/* traction of the energy release rate (cem_mesh_desc.g_variant), Eqs. 17-18 */
+#define CEM_G_PRINCIPAL 0       /* s = sigma_1 |p_1 . n| (principal-stress vector)        */
+#define CEM_G_NORMAL    1       /* s = n . sigma n (normal traction of the edge stress)   */
+
 /* Device allocator hooks.  alloc returns a device pointer of at least `bytes`
  * bytes (256-byte aligned) or NULL; free releases it.  `stream` is the
  * context's stream.  Both are called only inside cem_mesh_create,
@@ -105,6 +115,20 @@ typedef struct cem_mesh_desc {
     const int32_t* tet_instance; /* T specimen ids in [0, n_instances) (NULL if <= 1); */
                                  /* the elements of one specimen share no node with    */
                                  /* another's; each specimen gets its own time step    */
+    int32_t        split_mode;   /* CEM_SPLIT_SUBDIVIDE (0) or CEM_SPLIT_DEACTIVATE;    */
+                                 /* applies to the notch as well                       */
+    int32_t        g_variant;    /* CEM_G_PRINCIPAL (0) or CEM_G_NORMAL                 */
+    int64_t        n_dirichlet;  /* D >= 0 prescribed velocity components (Sec. 4.1-  */
+                                 /* 4.3, 4.5): component dir_comp[q] of node           */
+                                 /* dir_node[q] follows v(t) = min(t / t0, 1) dir_v0[q]*/
+                                 /* with a = dir_v0[q] / t0 while t < t0, else 0.  The */
+                                 /* values overwrite the corrector's v and a at the end*/
+                                 /* of every step and at t = 0; nodes created by splits*/
+                                 /* are free.  (node, component) pairs are distinct.   */
+    const int32_t* dir_node;     /* D input node ids                                   */
+    const uint8_t* dir_comp;     /* D components in {0, 1, 2}                          */
+    const double*  dir_v0;       /* D final velocities [m/s]                           */
+    double         dir_t0;       /* ramp time t0 [s]; <= 0: v = v0 from t = 0          */
 } cem_mesh_desc;
 
 typedef struct cem_ctx cem_ctx;
@@ -136,9 +160,11 @@ typedef struct cem_info_t {
 } cem_info_t;
 
 /* Build the device mesh: edges and their element fans (Sec. 2.2, Fig. 4),
- * node incidence, face adjacency, traction load, and apply the notch splits
- * with the same rule as run-time splits.  Errors: CEM_EINVAL (counts, ids
- * out of range, zero-volume element, bad side mask), CEM_ENOMEM, CEM_ECUDA.
+ * node incidence, face adjacency, traction load, prescribed velocities, and
+ * apply the notch splits with the same rule as run-time splits.  Errors:
+ * CEM_EINVAL (counts, ids out of range, zero-volume element, bad side mask,
+ * unknown split_mode or g_variant, a repeated or out-of-range prescribed
+ * component), CEM_ENOMEM, CEM_ECUDA.
  * On success *out owns all device memory of the context. */
 int cem_mesh_create(const cem_mesh_desc* d, cem_ctx** out);
 
@@ -172,7 +198,7 @@ int cem_step(cem_ctx* ctx, int64_t n);
  * and each segment is recomputed before its reverse sweep.  The context ends
  * at step + n_steps.  Allocates its working memory through the context's
  * allocator and frees it before returning.  Errors: CEM_ESTATE (no material,
- * splitting on, ensemble), CEM_ENOMEM, CEM_ECUDA. */
+ * splitting on, ensemble, prescribed velocities), CEM_ENOMEM, CEM_ECUDA. */
 int cem_adjoint(cem_ctx* ctx, int64_t n_steps, int64_t checkpoint_every, double c_strain,
                 const double* w_u, double* J, double* dJ_dE, double* dJ_dalpha);
 

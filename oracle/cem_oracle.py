@@ -41,6 +41,16 @@ What it computes, in the paper's order and notation (arxiv 2508.04076):
   three tetrahedra as for the parallelepiped remainder in Sec. 3).
 * Appendix I: the quadrilateral crack surface is planar.
 
+Paper variants (constructor switches):
+* split_mode="deactivate": the literal wording of Sec. 1 and the conclusion,
+  where an element whose rate exceeds Gc is only deactivated (no
+  sub-elements); the notch elements are deactivated likewise.
+* g_variant="normal": the traction of sigma_G replaced by the normal
+  traction n . sigma n of the edge stress.
+* dirichlet: the velocity ramp v(t) = min(t / t0, 1) v0 prescribed on chosen
+  node components (Sec. 4.1-4.3, 4.5).  The prescribed velocity and the ramp
+  acceleration overwrite the corrector's values at the end of every step.
+
 Readings where the paper is silent (each one is stated where it is used):
 front = a face shared with a split element whose crack cuts two of the
 face's edges; sigma_G is the principal-stress vector sigma_1 p_1 of the edge
@@ -232,7 +242,16 @@ class CEMOracle:
 
     def __init__(self, X, tets, tfaces, tvec, E, Gc, nu, rho,
                  notch_tet=(), notch_side=(), dt=None, cfl_factor=0.5,
-                 split_enabled=True):
+                 split_enabled=True, split_mode="subdivide", g_variant="principal",
+                 dirichlet=None):
+        """split_mode: "subdivide" (sub-elements, the default reading) or
+        "deactivate" (the paper's literal wording: the split element only leaves
+        the computation).  g_variant: "principal" (s = sigma_1 |p_1 . n|) or
+        "normal" (s = n . sigma n).  dirichlet: None or (nodes, comps, v0, t0),
+        D prescribed velocity components: node nodes[q], component comps[q]
+        follows v(t) = min(t / t0, 1) v0[q] (the velocity ramp of Sec. 4.1-4.3
+        and 4.5; t0 <= 0 gives v0 from t = 0), with a = v0 / t0 during the ramp
+        and 0 after it."""
         X = np.array(X, dtype=np.float64).reshape(-1, 3)
         tets = np.array(tets, dtype=np.int64).reshape(-1, 4)
         T0 = tets.shape[0]
@@ -240,6 +259,9 @@ class CEMOracle:
         Gc = np.broadcast_to(np.asarray(Gc, dtype=np.float64), (T0,)).copy()
         self.nu, self.rho = float(nu), float(rho)
         self.split_enabled = bool(split_enabled)
+        if split_mode not in ("subdivide", "deactivate") or g_variant not in ("principal", "normal"):
+            raise ValueError("unknown split_mode or g_variant")
+        self.split_mode, self.g_variant = split_mode, g_variant
 
         # orientation: a negative signed volume swaps local nodes 2 and 3
         V0, _ = tet_geometry(X[tets])
@@ -319,6 +341,19 @@ class CEMOracle:
         self.U_d = 0.0
         self.sigma = None
 
+        # prescribed velocity ramp
+        self.dir_mask = np.zeros((n, 3), dtype=bool)
+        self.dir_v0 = np.zeros((n, 3))
+        self.dir_t0 = 0.0
+        if dirichlet is not None:
+            nodes, comps, v0, t0 = dirichlet
+            for i, c, vv in zip(np.asarray(nodes).ravel(), np.asarray(comps).ravel(), np.asarray(v0, float).ravel()):
+                if self.dir_mask[i, c]:
+                    raise ValueError("a node component is prescribed twice")
+                self.dir_mask[i, c] = True
+                self.dir_v0[i, c] = vv
+            self.dir_t0 = float(t0)
+
         # pre-split notch (no dissipated energy is booked for it)
         if notch_tet.size:
             order = np.argsort(notch_tet, kind="stable")
@@ -327,6 +362,21 @@ class CEMOracle:
         self._build()
         f_int, _, _ = self._internal_force(self.u)
         self.a = self._accel(f_int)
+        self._prescribe(0.0, self.v, self.a)
+
+    def _ramp(self, t):
+        """(velocity factor, acceleration factor) of v(t) = min(t / t0, 1) v0."""
+        if self.dir_t0 <= 0.0:
+            return 1.0, 0.0
+        return (t / self.dir_t0, 1.0 / self.dir_t0) if t < self.dir_t0 else (1.0, 0.0)
+
+    def _prescribe(self, t, v, a):
+        if not self.dir_mask.any():
+            return
+        fv, fa = self._ramp(t)
+        m = self.dir_mask[: v.shape[0]]
+        v[m] = fv * self.dir_v0[: v.shape[0]][m]
+        a[m] = fa * self.dir_v0[: v.shape[0]][m]
 
     # ------------------------------------------------------------------ topology
     def _build(self):
@@ -402,6 +452,7 @@ class CEMOracle:
             f_int, eps, sig = self._internal_force(u1)
             a1 = self._accel(f_int)
             v1 = self.v + 0.5 * dt * (self.a + a1)
+            self._prescribe((self.n_step + 1) * dt, v1, a1)
             self.u, self.v, self.a = u1, v1, a1
             self.eps, self.sigma = eps, sig
             self.n_step += 1
@@ -458,8 +509,12 @@ class CEMOracle:
         return (self.u[i] - self.u[j]) if ratio - 1.0 > 0.0 else np.zeros(3)
 
     def _s(self, i, j, n):
-        """sigma_G . n with sigma_G = sigma_1 p_1 of edge {i, j}, projection in absolute value."""
-        s1, pn = principal_stress_projection(self.sigma[self._edge_index(i, j)], n)
+        """sigma_G . n with sigma_G = sigma_1 p_1 of edge {i, j}, projection in absolute value
+        (g_variant "normal": the normal traction n . sigma n of the edge stress)."""
+        sig = self.sigma[self._edge_index(i, j)]
+        if self.g_variant == "normal":
+            return float(n @ voigt_to_tensor(sig) @ n)
+        s1, pn = principal_stress_projection(sig, n)
         return s1 * pn
 
     def energy_release_rates(self, a, c, b, d):
@@ -538,8 +593,9 @@ class CEMOracle:
         new elements in ascending (parent, local sub-element) order.  A new
         node starts at the edge midpoint with the mean u, v and a of the edge.
         """
+        deact = self.split_mode == "deactivate"
         keys = set()
-        for t, mask, _ in splits:
+        for t, mask, _ in ([] if deact else splits):
             bits = _bits(mask)
             for l, (l0, l1) in enumerate(LOCAL_EDGES):
                 if bits[l0] != bits[l1]:
@@ -562,9 +618,11 @@ class CEMOracle:
             self.v = np.vstack([self.v, vn])
             self.a = np.vstack([self.a, an])
             self.f_ext = np.vstack([self.f_ext, np.zeros((len(new_keys), 3))])
+            self.dir_mask = np.vstack([self.dir_mask, np.zeros((len(new_keys), 3), dtype=bool)])
+            self.dir_v0 = np.vstack([self.dir_v0, np.zeros((len(new_keys), 3))])
         new_conn, new_parent = [], []
         for t, mask, G in sorted(splits):
-            for sub in sub_tet_nodes(self.conn[t], mask, self._M):
+            for sub in ([] if deact else sub_tet_nodes(self.conn[t], mask, self._M)):
                 sub = list(sub)
                 Vs, _ = tet_geometry(self.X[np.array(sub)][None])
                 if Vs[0] < 0.0:

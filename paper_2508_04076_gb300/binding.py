@@ -18,6 +18,8 @@ from . import build as _build
 CEM_OK, CEM_EINVAL, CEM_ENOMEM, CEM_ECUDA = 0, -1, -2, -3
 CEM_ECAPACITY, CEM_ENONFINITE, CEM_ETIMEOUT, CEM_ESTATE = -4, -5, -6, -7
 CEM_FP64, CEM_MIXED = 0, 1
+SPLIT_MODES = {"subdivide": 0, "deactivate": 1}
+G_VARIANTS = {"principal": 0, "normal": 1}
 FIELD = {"u": 0, "v": 1, "a": 2, "X": 3}
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
@@ -39,6 +41,9 @@ class MeshDesc(C.Structure):
         ("stream", C.c_void_p), ("device", C.c_int32),
         ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_user", C.c_void_p),
         ("n_instances", C.c_int64), ("tet_instance", C.POINTER(C.c_int32)),
+        ("split_mode", C.c_int32), ("g_variant", C.c_int32),
+        ("n_dirichlet", C.c_int64), ("dir_node", C.POINTER(C.c_int32)), ("dir_comp", C.POINTER(C.c_uint8)),
+        ("dir_v0", C.POINTER(C.c_double)), ("dir_t0", C.c_double),
     ]
 
 
@@ -119,7 +124,10 @@ class CEM:
 
     def __init__(self, X, tets, tfaces=None, tvec=None, notch_tet=None, notch_side=None, *,
                  dt=0.0, cfl_factor=0.5, split_enabled=True, split_capacity=0, device=0,
-                 stream=None, torch_allocator=True, precision="fp64", tet_instance=None):
+                 stream=None, torch_allocator=True, precision="fp64", tet_instance=None,
+                 split_mode="subdivide", g_variant="principal", dirichlet=None):
+        """dirichlet: None or (nodes, comps, v0, t0), prescribed velocity components
+        v(t) = min(t / t0, 1) v0 (see cem_mesh_desc)."""
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("the CEM library needs a CUDA GPU; no CPU fallback exists")
@@ -137,7 +145,17 @@ class CEM:
         notch_side = np.ascontiguousarray([] if notch_side is None else notch_side, dtype=np.uint8).ravel()
         inst = None if tet_instance is None else np.ascontiguousarray(tet_instance, dtype=np.int32).ravel()
         self.n_instances = 1 if inst is None else int(inst.max()) + 1
-        self._keep = (X, tets, tfaces, tvec, notch_tet, notch_side, inst)
+        if dirichlet is not None:
+            dn, dc, dv, dt0 = dirichlet
+            dn = np.ascontiguousarray(dn, dtype=np.int32).ravel()
+            dc = np.ascontiguousarray(dc, dtype=np.uint8).ravel()
+            dv = np.ascontiguousarray(dv, dtype=np.float64).ravel()
+            if not (dn.size == dc.size == dv.size):
+                raise ValueError("dirichlet nodes, components and velocities differ in length")
+        else:
+            dn = dc = dv = None
+            dt0 = 0.0
+        self._keep = (X, tets, tfaces, tvec, notch_tet, notch_side, inst, dn, dc, dv)
         d = MeshDesc()
         d.n_nodes, d.n_tets = X.shape[0], tets.shape[0]
         d.X, d.tets = _ptr(X, C.c_double), _ptr(tets, C.c_int32)
@@ -152,6 +170,12 @@ class CEM:
         d.stream, d.device = self.stream, self.device
         if inst is not None and self.n_instances > 1:
             d.n_instances, d.tet_instance = self.n_instances, _ptr(inst, C.c_int32)
+        if split_mode not in SPLIT_MODES or g_variant not in G_VARIANTS:
+            raise ValueError("split_mode must be one of %s, g_variant one of %s" % (list(SPLIT_MODES), list(G_VARIANTS)))
+        d.split_mode, d.g_variant = SPLIT_MODES[split_mode], G_VARIANTS[g_variant]
+        if dn is not None:
+            d.n_dirichlet, d.dir_node, d.dir_comp, d.dir_v0 = dn.size, _ptr(dn, C.c_int32), _ptr(dc, C.c_uint8), _ptr(dv, C.c_double)
+            d.dir_t0 = float(dt0)
         if torch_allocator:
             dev = self.device
 

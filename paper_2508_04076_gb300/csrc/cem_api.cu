@@ -177,6 +177,13 @@ int create_impl(const cem_mesh_desc* d, cem_ctx* c) {
         return cem_fail(c, CEM_EINVAL, "notch needs notch_tet and notch_side");
     if (d->precision != CEM_FP64 && d->precision != CEM_MIXED)
         return cem_fail(c, CEM_EINVAL, "precision must be CEM_FP64 or CEM_MIXED");
+    if (d->split_mode != CEM_SPLIT_SUBDIVIDE && d->split_mode != CEM_SPLIT_DEACTIVATE)
+        return cem_fail(c, CEM_EINVAL, "split_mode must be CEM_SPLIT_SUBDIVIDE or CEM_SPLIT_DEACTIVATE");
+    if (d->g_variant != CEM_G_PRINCIPAL && d->g_variant != CEM_G_NORMAL)
+        return cem_fail(c, CEM_EINVAL, "g_variant must be CEM_G_PRINCIPAL or CEM_G_NORMAL");
+    if (d->n_dirichlet < 0 || (d->n_dirichlet > 0 && (!d->dir_node || !d->dir_comp || !d->dir_v0)))
+        return cem_fail(c, CEM_EINVAL, "prescribed velocities need dir_node, dir_comp and dir_v0");
+    if (!std::isfinite(d->dir_t0)) return cem_fail(c, CEM_EINVAL, "dir_t0 must be finite");
     c->device = d->device;
     c->stream = (cudaStream_t)d->stream;
     c->alloc = d->alloc;
@@ -185,6 +192,8 @@ int create_impl(const cem_mesh_desc* d, cem_ctx* c) {
     c->dt_req = d->dt;
     c->cfl = d->cfl_factor > 0 ? d->cfl_factor : 0.5;
     c->split_enabled = d->split_enabled ? 1 : 0;
+    c->split_mode = d->split_mode;
+    c->g_variant = d->g_variant;
     c->precision = d->precision;
 
     const int64_t N0 = d->n_nodes, T0 = d->n_tets;
@@ -236,6 +245,25 @@ int create_impl(const cem_mesh_desc* d, cem_ctx* c) {
     HostTopo H;
     if (int rc = build_topology(c, conn, H)) return rc;
     const int64_t E0 = c->E0;
+
+    // prescribed velocity components, keyed 4 * node + component (distinct)
+    std::vector<int> dir_key(d->n_dirichlet);
+    std::vector<double> dir_v0(d->n_dirichlet);
+    for (int64_t q = 0; q < d->n_dirichlet; ++q) {
+        const int i = d->dir_node[q], k = d->dir_comp[q];
+        if (i < 0 || i >= N0 || k > 2) return cem_fail(c, CEM_EINVAL, "prescribed node or component out of range");
+        if (!std::isfinite(d->dir_v0[q])) return cem_fail(c, CEM_EINVAL, "prescribed velocity must be finite");
+        dir_key[q] = 4 * i + k;
+        dir_v0[q] = d->dir_v0[q];
+    }
+    {
+        std::vector<int> sorted_keys(dir_key);
+        std::sort(sorted_keys.begin(), sorted_keys.end());
+        if (std::adjacent_find(sorted_keys.begin(), sorted_keys.end()) != sorted_keys.end())
+            return cem_fail(c, CEM_EINVAL, "a node component is prescribed twice");
+    }
+    c->n_dir = d->n_dirichlet;
+    c->dir_t0 = d->dir_t0;
 
     // notch list: validated, oriented, side masks normalised (local node 0 on side 0), ascending
     std::vector<std::pair<int, int>> notch;
@@ -312,6 +340,7 @@ int create_impl(const cem_mesh_desc* d, cem_ctx* c) {
     ok = ok && dalloc(c, c->scan_status, c->scan_blocks_cap) && dalloc(c, c->scan_ticket, 1);
     ok = ok && dalloc(c, c->red_part, cem_reduction_doubles()) && dalloc(c, c->red_out, 8);
     ok = ok && dalloc(c, c->dcount, CNT_COUNT);
+    if (c->n_dir > 0) ok = ok && dalloc(c, c->dir_key, c->n_dir) && dalloc(c, c->dir_v0, c->n_dir);
     if (!ok) return cem_fail(c, CEM_ENOMEM, "device allocation failed");
     CEM_CK(c, cudaMallocHost((void**)&c->hcount, CNT_COUNT * sizeof(long long)));
     CEM_CK(c, cudaMallocHost((void**)&c->hred, 8 * sizeof(double)));
@@ -443,6 +472,11 @@ int create_impl(const cem_mesh_desc* d, cem_ctx* c) {
             if (int rc = upload(c, c->fext + k * Nc, f.data() + k * N0, N0)) return rc;
         CEM_CK(c, cudaStreamSynchronize(s));
     }
+    if (c->n_dir > 0) {
+        if (int rc = upload(c, c->dir_key, dir_key.data(), c->n_dir)) return rc;
+        if (int rc = upload(c, c->dir_v0, dir_v0.data(), c->n_dir)) return rc;
+        CEM_CK(c, cudaStreamSynchronize(s));
+    }
     c->N = N0;
     c->T = T0;
     c->E = E0;
@@ -537,6 +571,7 @@ int run_step(cem_ctx* c) {
     TIMED(c, CEM_KERNEL_EDGE_STRESS, cem_launch_edge_stress(c));
     TIMED(c, CEM_KERNEL_FORCE, cem_launch_force(c));
     TIMED(c, CEM_KERNEL_NODE_UPDATE, cem_launch_node_update(c, 0));
+    if (int rc = cem_launch_prescribe(c, c->step + 1)) return rc;
     c->step += 1;
     if (c->split_enabled && c->n_cand > 0) {
         TIMED(c, CEM_KERNEL_FRONT_G, cem_launch_front_G(c));
@@ -619,7 +654,7 @@ int cem_set_material(cem_ctx* c, double rho, double nu, const double* E, int64_t
     // a_0 = M^-1 (f_ext - f_int(u_0))
     int rc;
     if ((rc = cem_launch_strain(c)) || (rc = cem_launch_edge_stress(c)) || (rc = cem_launch_force(c)) ||
-        (rc = cem_launch_node_update(c, 1)))
+        (rc = cem_launch_node_update(c, 1)) || (rc = cem_launch_prescribe(c, 0)))
         return rc;
     CEM_CK(c, cudaStreamSynchronize(c->stream));
     c->material = true;

@@ -72,6 +72,8 @@ struct cem_ctx {
     bool material = false;
     int64_t step = 0;
     int split_enabled = 1;
+    int split_mode = CEM_SPLIT_SUBDIVIDE;
+    int g_variant = CEM_G_PRINCIPAL;
     int precision = CEM_FP64;
     cudaStream_t stream = 0;
     int device = 0;
@@ -100,6 +102,11 @@ struct cem_ctx {
     double* dtn = nullptr;
     double* inst_dt_dev = nullptr;
     double* ud_tet = nullptr;          // [T0] dissipated energy booked by each split input element
+    // prescribed velocity components: (node, component) packed as 4 * node + comp, target v0
+    int64_t n_dir = 0;
+    int* dir_key = nullptr;
+    double* dir_v0 = nullptr;
+    double dir_t0 = 0.0;
     // cracks
     int* face_nbr = nullptr;
     uint8_t* side = nullptr;
@@ -194,6 +201,7 @@ int64_t cem_scan_blocks_needed(int64_t n);
 int cem_launch_geometry(cem_ctx* c, int64_t t_begin, int64_t t_end, double* hbuf);
 int cem_launch_predict(cem_ctx* c);
 int cem_launch_split_u(cem_ctx* c);   // mixed: refresh the FP32 hi/lo copy of u
+int cem_launch_prescribe(cem_ctx* c, int64_t step);   // v, a of prescribed components at t = step * dt
 int cem_launch_strain(cem_ctx* c);
 int cem_launch_edge_stress(cem_ctx* c);
 int cem_launch_force(cem_ctx* c);

@@ -14,6 +14,11 @@
 // the projection of the principal stress vector of edge k's smoothed stress.
 // The element splits when max(G_I, G_II) over its front faces exceeds Gc.
 //
+// Variants: s(k) = n . sigma_k n (CEM_G_NORMAL) in place of the principal
+// projection, and a split that only deactivates the element
+// (CEM_SPLIT_DEACTIVATE, the literal wording of Sec. 1) in place of the
+// sub-element rule below.
+//
 // A split element leaves the computation and is replaced by sub-elements:
 // pattern I (two nodes per side) by two triangular prisms, pattern II (one
 // node cut off) by a corner tetrahedron and a prism; each prism is divided
@@ -127,8 +132,10 @@ __device__ T principal_projection(const T s[6], const T n[3]) {
     return l1 * sqrt(proj2);
 }
 
-// s(edge k, n) in FP64 (FP32 records of the mixed path are promoted).
-__device__ __forceinline__ double edge_projection(const double* sig64, const float* sig32, int k, const double n[3]) {
+// s(edge k, n) in FP64 (FP32 records of the mixed path are promoted):
+// sigma_1 |p_1 . n|, or n . sigma n for the normal-traction variant.
+__device__ __forceinline__ double edge_projection(const double* sig64, const float* sig32, int k, const double n[3],
+                                                  int gvar) {
     double sd[6];
     if (sig32) {
         const float4 a = reinterpret_cast<const float4*>(sig32 + 8 * (int64_t)k)[0];
@@ -136,6 +143,12 @@ __device__ __forceinline__ double edge_projection(const double* sig64, const flo
         sd[0] = a.x; sd[1] = a.y; sd[2] = a.z; sd[3] = a.w; sd[4] = b.x; sd[5] = b.y;
     } else {
         for (int q = 0; q < 6; ++q) sd[q] = sig64[6 * (int64_t)k + q];
+    }
+    if (gvar == CEM_G_NORMAL) {
+        const double sn0 = sd[0] * n[0] + sd[3] * n[1] + sd[5] * n[2];
+        const double sn1 = sd[3] * n[0] + sd[1] * n[1] + sd[4] * n[2];
+        const double sn2 = sd[5] * n[0] + sd[4] * n[1] + sd[2] * n[2];
+        return n[0] * sn0 + n[1] * sn1 + n[2] * sn2;
     }
     return principal_projection<double>(sd, n);
 }
@@ -151,8 +164,8 @@ __global__ void __launch_bounds__(BS) k_front_G(const int* __restrict__ cand_lis
                                                 int64_t T0, const double* __restrict__ X, const double* __restrict__ u,
                                                 int64_t Nc, const double* __restrict__ sig,
                                                 const float* __restrict__ sig32,
-                                                const double* __restrict__ Gc, uint8_t* __restrict__ dec_mask,
-                                                double* __restrict__ dec_G) {
+                                                const double* __restrict__ Gc, int gvar,
+                                                uint8_t* __restrict__ dec_mask, double* __restrict__ dec_G) {
     CEM_PDL_ENTRY();
     const int tid = blockIdx.x * BS + threadIdx.x;
     const int ci = tid >> 2, f = tid & 3;
@@ -204,9 +217,9 @@ __global__ void __launch_bounds__(BS) k_front_G(const int* __restrict__ cand_lis
                     nI[q] *= iI;
                     nII[q] *= iII;
                 }
-                const double s_ad = edge_projection(sig, sig32, t2e[local_edge(al, dl) * Tc + t], nI);
-                const double s_bd = edge_projection(sig, sig32, t2e[local_edge(bl, dl) * Tc + t], nI);
-                const double s_cd = edge_projection(sig, sig32, t2e[local_edge(cl_, dl) * Tc + t], nII);
+                const double s_ad = edge_projection(sig, sig32, t2e[local_edge(al, dl) * Tc + t], nI, gvar);
+                const double s_bd = edge_projection(sig, sig32, t2e[local_edge(bl, dl) * Tc + t], nI, gvar);
+                const double s_cd = edge_projection(sig, sig32, t2e[local_edge(cl_, dl) * Tc + t], nII, gvar);
                 const double GI = 0.5 * (s_ad * fabs(dot3(d1, nI)) + s_bd * fabs(dot3(d2, nI)));
                 const double GII = 0.5 * (s_cd * fabs(dot3(d1, nII)) + s_cd * fabs(dot3(d2, nII)));
                 if (GI >= GII) {
@@ -321,13 +334,18 @@ struct EdgeStore {
 
 // ------------------------------------------------------------------ new nodes and sub-elements
 // Per split: flag the (cut edge, side) keys that have no node yet, and count
-// its sub-elements (6 for pattern I, 4 for pattern II).
+// its sub-elements (6 for pattern I, 4 for pattern II; none when splits only
+// deactivate).
 __global__ void k_split_prep(int S, const int* __restrict__ split_list, const uint8_t* __restrict__ split_mask,
                              const int* __restrict__ t2e, int64_t Tc, const int* __restrict__ node_of_key,
-                             uint8_t* __restrict__ key_flag, int* __restrict__ cnt) {
+                             uint8_t* __restrict__ key_flag, int* __restrict__ cnt, int deact) {
     CEM_PDL_ENTRY();
     const int i = blockIdx.x * BS + threadIdx.x;
     if (i >= S) return;
+    if (deact) {
+        cnt[i] = 0;
+        return;
+    }
     const int p = split_list[i], m = split_mask[i];
     for (int l = 0; l < 6; ++l) {
         const int x = CEM_LE0(l), y = CEM_LE1(l);
@@ -377,7 +395,7 @@ __global__ void k_create_subs(int S, int64_t T, const int* __restrict__ split_li
                               const double* __restrict__ X, int64_t Nc, uint8_t* __restrict__ side,
                               int* __restrict__ split_step, double* __restrict__ split_G,
                               const double* __restrict__ Gc, uint8_t* __restrict__ cand_flag,
-                              double* __restrict__ ud_part, double* __restrict__ ud_tet) {
+                              double* __restrict__ ud_part, double* __restrict__ ud_tet, int deact) {
     CEM_PDL_ENTRY();
     const int i = blockIdx.x * BS + threadIdx.x;
     if (i >= S) return;
@@ -440,6 +458,7 @@ __global__ void k_create_subs(int S, int64_t T, const int* __restrict__ split_li
         cross3(e1, e2, cr);
         area = 0.125 * sqrt(dot3(cr, cr));
     }
+    if (deact) ns = 0;   // the element only leaves the computation
     const int64_t base = T + sub_off[i];
     const double lp = lam[p], mp = mu[p];
     for (int q = 0; q < ns; ++q) {
@@ -832,7 +851,8 @@ int cem_launch_front_G(cem_ctx* c) {
     if (c->n_cand > 0) {
         cem_pdl(c->stream, k_front_G, cem_grid(4 * c->n_cand, BS), BS, c->cand_list, (int)c->n_cand, c->conn, c->t2e, c->Tc,
                                                                  c->face_nbr, c->side, c->T0, c->X, c->u, c->Nc, c->sig,
-                                                                 c->sig32, c->Gc, c->dec_mask, c->dec_G);
+                                                                 c->sig32, c->Gc, c->g_variant, c->dec_mask,
+                                                                 c->dec_G);
         cem_launched(c, 1);
         CEM_CK(c, cudaGetLastError());
     }
@@ -853,7 +873,7 @@ int cem_apply_splits(cem_ctx* c, int64_t S64, int64_t step, int book_energy) {
     int rc;
     // 1. new nodes: one per (cut original edge, side) not yet present; sub-element counts
     cem_pdl(c->stream, k_split_prep, cem_grid(S, BS), BS, S, c->split_list, c->split_mask, c->t2e, c->Tc,
-            c->node_of_key, c->key_flag, c->aff_new);
+            c->node_of_key, c->key_flag, c->aff_new, (int)(c->split_mode == CEM_SPLIT_DEACTIVATE));
     cem_launched(c, 1);
     CEM_CK(c, cudaGetLastError());
     if ((rc = run_scan(c, U8Load{c->key_flag},
@@ -866,7 +886,8 @@ int cem_apply_splits(cem_ctx* c, int64_t S64, int64_t step, int book_energy) {
     cem_pdl(c->stream, k_create_subs, cem_grid(S, BS), BS,
             S, c->T, c->split_list, c->split_mask, c->split_Gv, c->sub_off, step, book_energy, c->conn, c->t2e, c->anc,
             c->active, c->Vg, c->Vg32, c->vol, c->lam, c->mu, c->Tc, c->node_of_key, c->X, c->Nc, c->side,
-            c->split_step, c->split_G, c->Gc, c->cand_flag, c->ud_part, c->ud_tet);
+            c->split_step, c->split_G, c->Gc, c->cand_flag, c->ud_part, c->ud_tet,
+            (int)(c->split_mode == CEM_SPLIT_DEACTIVATE));
     cem_pdl(c->stream, k_ud_sum, 1, BS, S, c->ud_part, c->Ud);
     // 3. edges of the sub-elements: parent edges or (new) hashed node pairs
     const long long* nsub = c->dcount + CNT_NEWSUB;

@@ -306,6 +306,26 @@ __global__ void __launch_bounds__(BS) k_force(const R* __restrict__ sig, const i
     }
 }
 
+// Prescribed velocity ramp v(t) = min(t / t0, 1) v0 (Sec. 4.1-4.3, 4.5): the
+// velocity and the ramp's acceleration overwrite the corrector's values.
+__global__ void __launch_bounds__(BS) k_prescribe(int64_t n, const int* __restrict__ key,
+                                                  const double* __restrict__ v0, double t0, int64_t step, double dt,
+                                                  const double* __restrict__ dtn, double* __restrict__ v,
+                                                  double* __restrict__ a, int64_t Nc) {
+    CEM_PDL_ENTRY();
+    const int64_t q = (int64_t)blockIdx.x * BS + threadIdx.x;
+    if (q >= n) return;
+    const int i = key[q] >> 2, comp = key[q] & 3;
+    const double t = (double)step * (dtn ? dtn[i] : dt);
+    double fv = 1.0, fa = 0.0;
+    if (t0 > 0.0 && t < t0) {
+        fv = t / t0;
+        fa = 1.0 / t0;
+    }
+    v[comp * Nc + i] = fv * v0[q];
+    a[comp * Nc + i] = fa * v0[q];
+}
+
 template <class R>
 __global__ void __launch_bounds__(BS) k_node_update(const R* __restrict__ fp, const int* __restrict__ inc_off,
                                                     const int* __restrict__ inc_cnt, const int* __restrict__ inc_pool,
@@ -910,6 +930,15 @@ int cem_launch_node_update(cem_ctx* c, int first) {
         cem_pdl(c->stream, k_node_update<double>, cem_grid(c->N, BS), BS, 
             c->fp, c->inc_off, c->inc_cnt, c->inc_pool, c->fext, c->minv, c->v, c->a, c->Nc, c->N, 0.5 * c->dt, first,
             c->dtn);
+    cem_launched(c);
+    CEM_CK(c, cudaGetLastError());
+    return CEM_OK;
+}
+
+int cem_launch_prescribe(cem_ctx* c, int64_t step) {
+    if (c->n_dir == 0) return CEM_OK;
+    cem_pdl(c->stream, k_prescribe, cem_grid(c->n_dir, BS), BS, c->n_dir, c->dir_key, c->dir_v0, c->dir_t0, step, c->dt,
+            c->dtn, c->v, c->a, c->Nc);
     cem_launched(c);
     CEM_CK(c, cudaGetLastError());
     return CEM_OK;

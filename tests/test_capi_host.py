@@ -57,9 +57,16 @@ UNIT = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1.0]])
     ("bad_notch_mask", "side mask"),
     ("notch_out_of_range", "out of range"),
     ("bad_precision", "CEM_FP64"),
+    ("bad_split_mode", "split_mode"),
+    ("bad_g_variant", "g_variant"),
+    ("dir_twice", "prescribed twice"),
+    ("dir_component", "out of range"),
+    ("dir_node", "out of range"),
+    ("dir_missing", "dir_node"),
 ])
 def test_host_validation_rejects(lib, case, expect):
     X, tets, nt, ns, prec = UNIT, [[0, 1, 2, 3]], [], [], 0
+    dirichlet = None
     if case == "node_out_of_range":
         tets = [[0, 1, 2, 4]]
     elif case == "repeated_node":
@@ -72,7 +79,28 @@ def test_host_validation_rejects(lib, case, expect):
         nt, ns = [3], [1]
     elif case == "bad_precision":
         prec = 7
+    elif case == "dir_twice":
+        dirichlet = ([1, 2, 1], [0, 0, 0], [0.0, 0.0, 1.0])
+    elif case == "dir_component":
+        dirichlet = ([1], [3], [0.0])
+    elif case == "dir_node":
+        dirichlet = ([4], [0], [0.0])
     d, keep = _desc(X, tets, nt, ns, prec)
+    if case == "bad_split_mode":
+        d.split_mode = 2
+    elif case == "bad_g_variant":
+        d.g_variant = -1
+    elif case == "dir_missing":
+        d.n_dirichlet = 1
+    if dirichlet is not None:
+        dn = np.ascontiguousarray(dirichlet[0], np.int32)
+        dc = np.ascontiguousarray(dirichlet[1], np.uint8)
+        dv = np.ascontiguousarray(dirichlet[2], np.float64)
+        keep = keep + (dn, dc, dv)
+        d.n_dirichlet = dn.size
+        d.dir_node = dn.ctypes.data_as(C.POINTER(C.c_int32))
+        d.dir_comp = dc.ctypes.data_as(C.POINTER(C.c_uint8))
+        d.dir_v0 = dv.ctypes.data_as(C.POINTER(C.c_double))
     ctx = C.c_void_p()
     rc = lib.cem_mesh_create(C.byref(d), C.byref(ctx))
     assert rc == -1
