@@ -91,3 +91,50 @@ def test_adjoint_requires_fixed_topology(CEM):
     with pytest.raises(CEMError) as e:
         sim.adjoint(5)
     assert e.value.code == -7
+
+
+def _oracle_at(w, alpha, n, wu):
+    o = CEMOracle.from_workload(w, split_enabled=False)
+    o.f_ext *= alpha
+    o.a = o._accel(o._internal_force(o.u)[0])
+    return o.adjoint(n, c_strain=1.0, w_u=wu)
+
+
+def test_autograd_function_matches_oracle_adjoint(CEM):
+    """torch.autograd through cem_objective: J, dJ/dE (through a chain rule) and dJ/dalpha."""
+    import torch
+    from paper_2508_04076_gb300.autograd import cem_objective
+    w = _small()
+    n = 30
+    o = CEMOracle.from_workload(w, split_enabled=False)
+    wu = top_face_weights(o.X, 0.02) * 1e3
+    alpha0 = 1.3
+    Jo, dEo, dso = _oracle_at(w, alpha0, n, wu)
+    theta = torch.zeros(w.n_tets, dtype=torch.float64, requires_grad=True)
+    alpha = torch.tensor(alpha0, dtype=torch.float64, requires_grad=True)
+    E = torch.as_tensor(w.E, dtype=torch.float64) * torch.exp(theta)   # E = E0 exp(theta)
+    J = cem_objective(E, alpha, w, n, w_u=wu, precision="fp64")
+    J.backward()
+    assert abs(J.item() - Jo) <= 1e-12 * abs(Jo)
+    g_theta = theta.grad.numpy()
+    assert np.abs(g_theta - dEo * w.E).max() <= 1e-9 * np.abs(dEo * w.E).max()
+    assert abs(alpha.grad.item() - dso / alpha0) <= 1e-9 * abs(dso / alpha0)
+
+
+def test_autograd_function_at_zero_load(CEM):
+    """At alpha = 0: J = 0, dJ/dE = 0 and dJ/dalpha = w . u_hat (response to the unscaled load)."""
+    import torch
+    from paper_2508_04076_gb300.autograd import cem_objective
+    w = _small()
+    n = 20
+    o = CEMOracle.from_workload(w, split_enabled=False)
+    wu = top_face_weights(o.X, 0.02) * 1e3
+    o.step(n)
+    want = float(np.sum(wu * o.u))
+    E = torch.as_tensor(w.E, dtype=torch.float64).requires_grad_(True)
+    alpha = torch.tensor(0.0, dtype=torch.float64, requires_grad=True)
+    J = cem_objective(E, alpha, w, n, w_u=wu, precision="fp64")
+    J.backward()
+    assert J.item() == 0.0
+    assert np.all(E.grad.numpy() == 0.0)
+    assert abs(alpha.grad.item() - want) <= 1e-8 * abs(want)
