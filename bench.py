@@ -97,6 +97,7 @@ def _args():
     p.add_argument("--ensemble-steps", type=int, default=200,
                    help="steps of the ensemble sub-run in the default (block) mode; 0 skips it")
     p.add_argument("--no-compare", action="store_true", help="skip the second-precision run and agreement check")
+    p.add_argument("--no-autotune", action="store_true", help="keep the default launch variants")
     p.add_argument("--split-capacity", type=int, default=0,
                    help="max elements that may split (0: all); lower it to shrink device memory for profiling")
     p.add_argument("--cpu-baseline-worker", action="store_true", help=argparse.SUPPRESS)
@@ -255,6 +256,8 @@ def run_cem(a):
         cap = a.split_capacity if split_capacity is None else split_capacity
         sim = CEM.from_workload(w, device=dev, split_capacity=cap, precision=precision)
         info0 = sim.info()
+        if not a.no_autotune:   # launch variants for the current sizes; re-tuned in the run as the mesh grows
+            sim.autotune(reps=10, automatic=True)
         sim.step(a.warmup)
         barrier()
         clocks = ClockSampler(_bus_id(dev)) if (clocks_on and rank == 0) else None
@@ -275,6 +278,7 @@ def run_cem(a):
         t_ms = float(tmax.item())
         info = sim.info()
         energy = sim.energy()
+        tuning = {k: {"block": v[0], "batch": v[1]} for k, v in sim.tuning().items()}
         sim.close()
         Tm = (info0["n_tets"] + info["n_tets"]) / 2.0
         Ta = (info0["n_active_tets"] + info["n_active_tets"]) / 2.0
@@ -317,7 +321,8 @@ def run_cem(a):
             roofline.update(algorithmic_flops_per_launch=flops, fp64_tflops_achieved=flops / per_launch_s / 1e12,
                             fp64_peak_tflops=fp64_peak / 1e12, fp64_fma_measured_tflops=fp64_peak_meas / 1e12)
         return dict(t_ms=t_ms, value=w.n_tets * steps * world / (t_ms * 1e-3), roofline=roofline, kernels=kernels,
-                    clocks=clk, launches=launches, info0=info0, info=info, energy=energy, steps=steps)
+                    clocks=clk, launches=launches, info0=info0, info=info, energy=energy, steps=steps,
+                    tuning=tuning)
 
     main = timed(a.precision, True)
     other = None
@@ -389,6 +394,8 @@ def run_cem(a):
     barrier()
     t0 = time.perf_counter()
     sim2 = CEM.from_workload(w, device=dev, split_capacity=a.split_capacity, precision=a.precision)
+    if not a.no_autotune:
+        sim2.autotune(reps=10, automatic=True)
     sim2.step(a.steps)
     u = sim2.field("u")
     sim2.energy()
@@ -430,6 +437,7 @@ def run_cem(a):
                 "includes": "mesh upload and topology build, material, K steps, u and energy read-back"},
         "gpu_launches": main["launches"],
         "cpu_baseline": cpu,
+        "launch_variants": main["tuning"] if not a.no_autotune else "defaults (autotuner off)",
     }
     if other is not None:
         line["fp64" if a.precision == "mixed" else "mixed"] = {

@@ -80,7 +80,7 @@ extern "C" {
 /* Device allocator hooks.  alloc returns a device pointer of at least `bytes`
  * bytes (256-byte aligned) or NULL; free releases it.  `stream` is the
  * context's stream.  Both are called only inside cem_mesh_create,
- * cem_adjoint and cem_destroy. */
+ * cem_adjoint, cem_autotune (once per context) and cem_destroy. */
 typedef void* (*cem_alloc_fn)(size_t bytes, void* stream, void* user);
 typedef void  (*cem_free_fn)(void* ptr, void* stream, void* user);
 
@@ -243,6 +243,45 @@ int cem_info(cem_ctx* ctx, cem_info_t* out);
 #define CEM_KERNEL_COUNT       7
 int cem_profile(cem_ctx* ctx, int enable);
 int cem_profile_read(cem_ctx* ctx, double* ms, int64_t* launches, int n, int64_t* total_launches);
+
+/* Autotuner of the step kernels' launch variants (no counterpart in the
+ * paper).  Four kernels have variants: CEM_TUNE_STRAIN (per-element strain),
+ * CEM_TUNE_EDGE (edge stress, a gather over each edge's element fan),
+ * CEM_TUNE_FORCE (per-element forces) and CEM_TUNE_NODE (node update, a
+ * gather over each node's element incidence).  A variant is a block size
+ * (128, 256 or 512 threads) and, for the two gathers, how many list entries
+ * have their loads issued together (fan: 1, 2 or 4; incidence: 2, 4 or 8).
+ * All variants of a kernel compute the same values in the same order: the
+ * choice never changes results, only speed.
+ *
+ * cem_autotune times every variant on the context's current mesh and state
+ * (CUDA events, one warm-up launch then `reps` launches; reps <= 0 means 5),
+ * keeps the fastest, and records it under (GPU name, kernel, precision,
+ * floor(log2(item count))).  cache_path (may be NULL) names a text file that
+ * is read first (entries found there are used without timing) and appended
+ * with new results.  automatic != 0 makes cem_step re-tune a kernel (from the
+ * cache when possible) whenever its item count (elements, edges or nodes)
+ * enters a new power-of-two bucket.  The state of the simulation is
+ * unchanged.  The first call allocates one 3 x (node capacity) double buffer
+ * through the context's allocator, held until cem_destroy.  Errors:
+ * CEM_ESTATE (no material), CEM_EINVAL, CEM_ENOMEM, CEM_ECUDA.
+ *
+ * cem_tune_get reports kernel k's current variant and, from its last tuning,
+ * the time per launch of that variant and of the untuned default (us; 0 if
+ * the kernel was never timed, e.g. taken from the cache).  Any output
+ * pointer may be NULL. */
+#define CEM_TUNE_STRAIN 0
+#define CEM_TUNE_EDGE   1
+#define CEM_TUNE_FORCE  2
+#define CEM_TUNE_NODE   3
+#define CEM_TUNE_COUNT  4
+int cem_autotune(cem_ctx* ctx, const char* cache_path, int reps, int automatic);
+int cem_tune_get(cem_ctx* ctx, int kernel, int* block, int* batch, double* us, double* default_us);
+/* Pin kernel k's variant (block in {128, 256, 512}; batch 1 for strain and
+ * force, {1, 2, 4} for the edge stress, {2, 4, 8} for the node update).  An
+ * automatic autotuner may replace it when the kernel's bucket changes.
+ * CEM_EINVAL for an unknown kernel or variant. */
+int cem_tune_set(cem_ctx* ctx, int kernel, int block, int batch);
 
 /* Diagnostics (no counterpart in the paper): measured FP64 FMA throughput of
  * `device` in FLOP/s (an FMA counts as two), timed with CUDA events on

@@ -26,7 +26,9 @@ ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_void_p)
 
 EXPORTED = ["cem_mesh_create", "cem_set_material", "cem_step", "cem_energy", "cem_crack_state",
-            "cem_get_field", "cem_info", "cem_energy_instance", "cem_adjoint", "cem_profile", "cem_profile_read", "cem_probe_fp64_fma", "cem_destroy", "cem_last_error"]
+            "cem_get_field", "cem_info", "cem_energy_instance", "cem_adjoint", "cem_profile", "cem_profile_read",
+            "cem_autotune", "cem_tune_get", "cem_tune_set", "cem_probe_fp64_fma", "cem_destroy", "cem_last_error"]
+TUNED = ["strain", "edge_stress", "force", "node_update"]
 KERNELS = ["predict", "strain", "edge_stress", "force", "node_update", "front_G", "split"]
 
 
@@ -89,6 +91,10 @@ def load_library(build: bool = True):
     lib.cem_profile.argtypes = [P, C.c_int]
     lib.cem_profile_read.argtypes = [P, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.c_int, C.POINTER(C.c_int64)]
     lib.cem_probe_fp64_fma.argtypes = [C.c_int, C.c_void_p, C.POINTER(C.c_double)]
+    lib.cem_autotune.argtypes = [P, C.c_char_p, C.c_int, C.c_int]
+    lib.cem_tune_set.argtypes = [P, C.c_int, C.c_int, C.c_int]
+    lib.cem_tune_get.argtypes = [P, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_double),
+                                 C.POINTER(C.c_double)]
     lib.cem_destroy.argtypes = [P]
     lib.cem_last_error.argtypes = [P]
     lib.cem_last_error.restype = C.c_char_p
@@ -246,6 +252,25 @@ class CEM:
                                           _ptr(wu, C.c_double) if wu is not None else None, C.byref(J),
                                           _ptr(dE, C.c_double), C.byref(da)))
         return J.value, dE, da.value
+
+    def autotune(self, cache_path=None, reps=5, automatic=True):
+        """Pick the fastest launch variant of each step kernel (results unchanged)."""
+        path = None if cache_path is None else os.fsencode(cache_path)
+        self._check(self._lib.cem_autotune(self._ctx, path, int(reps), int(bool(automatic))))
+        return self.tuning()
+
+    def tune_set(self, kernel, block, batch):
+        """Pin one kernel's launch variant (kernel: one of TUNED)."""
+        self._check(self._lib.cem_tune_set(self._ctx, TUNED.index(kernel), int(block), int(batch)))
+
+    def tuning(self) -> dict:
+        """{kernel: (block, batch, us, default_us)} of the current launch variants."""
+        out = {}
+        for k, name in enumerate(TUNED):
+            b, q, us, du = C.c_int(), C.c_int(), C.c_double(), C.c_double()
+            self._check(self._lib.cem_tune_get(self._ctx, k, C.byref(b), C.byref(q), C.byref(us), C.byref(du)))
+            out[name] = (b.value, q.value, us.value, du.value)
+        return out
 
     def info(self) -> dict:
         i = Info()

@@ -195,6 +195,7 @@ int create_impl(const cem_mesh_desc* d, cem_ctx* c) {
     c->split_mode = d->split_mode;
     c->g_variant = d->g_variant;
     c->precision = d->precision;
+    for (int k = 0; k < TUNE_COUNT; ++k) c->tune[k] = cem_tune_default(k, c->precision);
 
     const int64_t N0 = d->n_nodes, T0 = d->n_tets;
     c->N0 = N0;
@@ -565,6 +566,8 @@ int prof_resolve(cem_ctx* c) {
     } while (0)
 
 int run_step(cem_ctx* c) {
+    if (c->tune_auto)
+        if (int rc = cem_tune_maybe(c)) return rc;
     c->prof_now = c->prof && (c->step % c->prof_every == 0);
     TIMED(c, CEM_KERNEL_PREDICT, cem_launch_predict(c));
     TIMED(c, CEM_KERNEL_STRAIN, cem_launch_strain(c));

@@ -49,6 +49,9 @@ enum {
 
 enum { DERR_HASH_FULL = 1, DERR_CAPACITY = 2, DERR_SCAN_WAIT = 4 };
 
+// kernels with tuned launch variants (block size, gather batch)
+enum { TUNE_STRAIN = 0, TUNE_EDGE, TUNE_FORCE, TUNE_NODE, TUNE_COUNT };
+
 struct cem_ctx {
     // sizes: original, capacity, current (host mirrors of the device state)
     int64_t N0 = 0, T0 = 0, E0 = 0;
@@ -142,6 +145,15 @@ struct cem_ctx {
     long long* dcount = nullptr;  // device counters
     long long* hcount = nullptr;  // pinned host mirror
     double* hred = nullptr;       // pinned host mirror of red_out
+    // launch variants of the tuned kernels and the autotuner's state (cem_tune.cu)
+    int tune[TUNE_COUNT] = {1, 1, 1, 1};
+    bool tune_auto = false;
+    int tune_reps = 5;
+    int tune_bucket[TUNE_COUNT] = {-1, -1, -1, -1};
+    double tune_us[TUNE_COUNT] = {};        // time of the chosen variant at its last tuning
+    double tune_default_us[TUNE_COUNT] = {};// time of the untuned default variant then
+    std::string tune_path;                  // cache file ("" = in memory only)
+    double* tune_save = nullptr;            // [3 * Nc] copy of a while the node update is timed
     // kernel timing and launch count
     int64_t n_launch = 0;
     bool prof = false;
@@ -224,6 +236,12 @@ int cem_adj_dot(cem_ctx* c, const double* a, const double* b, const double* msca
 // one explicit step without the crack test (cem_api.cu)
 int cem_run_step(cem_ctx* c);
 int cem_launch_check_finite(cem_ctx* c);
+// tuned variants (cem_step.cu) and the autotuner (cem_tune.cu)
+int cem_tune_variants(int kernel);
+void cem_tune_describe(int kernel, int v, int* block, int* batch);
+int cem_tune_default(int kernel, int precision);
+int cem_launch_tune_variant(cem_ctx* c, int kernel, int v);
+int cem_tune_maybe(cem_ctx* c);   // re-tune kernels whose size bucket changed (automatic mode)
 
 // ---------------------------------------------------------------- crack path (cem_crack.cu)
 int cem_launch_front_G(cem_ctx* c);

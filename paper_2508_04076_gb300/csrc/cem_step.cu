@@ -205,13 +205,14 @@ __device__ __forceinline__ void node_disp_diff<float>(const double*, const float
 }
 
 // Inactive (split) element slots are skipped: no fan or incidence list refers to them.
-template <class R>
-__global__ void __launch_bounds__(BS) k_strain(const double* __restrict__ u, const float* __restrict__ uhl,
+// TB (threads per block) is a tuning parameter (see cem_tune.cu).
+template <class R, int TB>
+__global__ void __launch_bounds__(TB) k_strain(const double* __restrict__ u, const float* __restrict__ uhl,
                                                int64_t Nc, const int* __restrict__ conn, const R* __restrict__ Vg,
                                                const uint8_t* __restrict__ active, int64_t Tc, int64_t T,
                                                R* __restrict__ h) {
     CEM_PDL_ENTRY();
-    int64_t j = (int64_t)blockIdx.x * BS + threadIdx.x;
+    int64_t j = (int64_t)blockIdx.x * TB + threadIdx.x;
     if (j >= T || !active[j]) return;
     const int n[4] = {conn[j], conn[Tc + j], conn[2 * Tc + j], conn[3 * Tc + j]};
     R d[3][3];   // d[a][c] = u_{a+1,c} - u_{0,c}
@@ -228,23 +229,36 @@ __global__ void __launch_bounds__(BS) k_strain(const double* __restrict__ u, con
     Rec<R>::store6(h + Rec<R>::S6 * j, out);
 }
 
-// Node gathers are issued in batches (all indices, then all records) so several
-// records are in flight per thread; sums keep the list's ascending order.  (The
-// edge fans are short, about five elements, and a batched fan loop costs more
-// occupancy than it gains.)
-template <class R> struct Batch { static constexpr int B = (sizeof(R) == 4) ? 8 : 4; };
-
-template <class R>
-__global__ void __launch_bounds__(BS) k_edge_stress(const R* __restrict__ h, const int* __restrict__ fan_off,
+// Gathers may be issued in batches of FB (fan) or NB (node incidence) entries:
+// all indices, then all records, so several records are in flight per thread.
+// Sums keep the list's ascending order whatever the batch, so every variant
+// gives bit-identical results; the autotuner picks the fastest.
+template <class R, int TB, int FB>
+__global__ void __launch_bounds__(TB) k_edge_stress(const R* __restrict__ h, const int* __restrict__ fan_off,
                                                     const int* __restrict__ fan_cnt, const int* __restrict__ fan_pool,
                                                     const R* __restrict__ cl, const R* __restrict__ cm, int64_t E,
                                                     R* __restrict__ sig) {
     CEM_PDL_ENTRY();
-    int64_t k = (int64_t)blockIdx.x * BS + threadIdx.x;
+    int64_t k = (int64_t)blockIdx.x * TB + threadIdx.x;
     if (k >= E) return;
     const int off = fan_off[k], cnt = fan_cnt[k];
     R H[6] = {0, 0, 0, 0, 0, 0};
-    for (int i = 0; i < cnt; ++i) {
+    int i = 0;
+    if constexpr (FB > 1) {
+        for (; i + FB <= cnt; i += FB) {
+            int jj[FB];
+#pragma unroll
+            for (int b = 0; b < FB; ++b) jj[b] = fan_pool[off + i + b];
+            R x[FB][6];
+#pragma unroll
+            for (int b = 0; b < FB; ++b) Rec<R>::load6(h + Rec<R>::S6 * (int64_t)jj[b], x[b]);
+#pragma unroll
+            for (int b = 0; b < FB; ++b)
+#pragma unroll
+                for (int q = 0; q < 6; ++q) H[q] += x[b][q];
+        }
+    }
+    for (; i < cnt; ++i) {
         const int j = fan_pool[off + i];
         R x[6];
         Rec<R>::load6(h + Rec<R>::S6 * (int64_t)j, x);
@@ -257,12 +271,12 @@ __global__ void __launch_bounds__(BS) k_edge_stress(const R* __restrict__ h, con
     Rec<R>::store6(sig + Rec<R>::S6 * k, s);
 }
 
-template <class R>
-__global__ void __launch_bounds__(BS) k_force(const R* __restrict__ sig, const int* __restrict__ t2e,
+template <class R, int TB>
+__global__ void __launch_bounds__(TB) k_force(const R* __restrict__ sig, const int* __restrict__ t2e,
                                               const R* __restrict__ Vg, const uint8_t* __restrict__ active,
                                               int64_t Tc, int64_t T, R* __restrict__ fp) {
     CEM_PDL_ENTRY();
-    int64_t j = (int64_t)blockIdx.x * BS + threadIdx.x;
+    int64_t j = (int64_t)blockIdx.x * TB + threadIdx.x;
     if (j >= T || !active[j]) return;
     R S[6] = {0, 0, 0, 0, 0, 0};
     int kk[6];
@@ -326,19 +340,19 @@ __global__ void __launch_bounds__(BS) k_prescribe(int64_t n, const int* __restri
     a[comp * Nc + i] = fa * v0[q];
 }
 
-template <class R>
-__global__ void __launch_bounds__(BS) k_node_update(const R* __restrict__ fp, const int* __restrict__ inc_off,
+template <class R, int TB, int NB>
+__global__ void __launch_bounds__(TB) k_node_update(const R* __restrict__ fp, const int* __restrict__ inc_off,
                                                     const int* __restrict__ inc_cnt, const int* __restrict__ inc_pool,
                                                     const double* __restrict__ fext, const double* __restrict__ minv,
                                                     double* __restrict__ v, double* __restrict__ a, int64_t Nc,
                                                     int64_t N, double hdt, int first, const double* __restrict__ dtn) {
     CEM_PDL_ENTRY();
-    int64_t i = (int64_t)blockIdx.x * BS + threadIdx.x;
+    int64_t i = (int64_t)blockIdx.x * TB + threadIdx.x;
     if (i >= N) return;
     if (dtn) hdt = 0.5 * dtn[i];
     const int off = inc_off[i], cnt = inc_cnt[i];
     double f[3];
-    constexpr int B = Batch<R>::B;
+    constexpr int B = NB;
     if constexpr (sizeof(R) == 8) {
         f[0] = f[1] = f[2] = 0.0;
         for (int base = 0; base < cnt; base += B) {
@@ -389,13 +403,16 @@ __global__ void __launch_bounds__(BS) k_node_update(const R* __restrict__ fp, co
 #pragma unroll
         for (int c = 0; c < 3; ++c) f[c] = (double)s[c] - (double)cmp[c];
     }
+    // Explicitly rounded operations: whether the compiler would fuse a multiply
+    // and an add here depends on the code around it, which differs between the
+    // launch variants; fixing the roundings keeps every variant bit-identical.
     const double mi = minv[i];
     const double sixth = 1.0 / 6.0;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         const int64_t k = c * Nc + i;
-        const double an = (mi == 0.0) ? 0.0 : (fext[k] - f[c] * sixth) * mi;
-        if (!first) v[k] = v[k] + hdt * (a[k] + an);
+        const double an = (mi == 0.0) ? 0.0 : __dmul_rn(__fma_rn(-f[c], sixth, fext[k]), mi);
+        if (!first) v[k] = __fma_rn(hdt, __dadd_rn(a[k], an), v[k]);
         a[k] = an;
     }
 }
@@ -624,6 +641,78 @@ __global__ void __launch_bounds__(RB) k_count_nonfinite(const double* __restrict
 
 inline bool mixed(const cem_ctx* c) { return c->precision == CEM_MIXED; }
 
+// ---------------------------------------------------------------- variant dispatch
+// Variant v: TB = 128 << (v % 3) threads per block; v / 3 selects the batch.
+template <class R, int TB>
+void go_strain(cem_ctx* c, const double* u, const float* uhl, const R* Vg, R* h) {
+    cem_pdl(c->stream, k_strain<R, TB>, cem_grid(c->T, TB), TB, u, uhl, c->Nc, c->conn, Vg, c->active, c->Tc, c->T, h);
+}
+template <class R>
+void launch_strain(cem_ctx* c, int v, const double* u, const float* uhl, const R* Vg, R* h) {
+    switch (v % 3) {
+        case 0: go_strain<R, 128>(c, u, uhl, Vg, h); break;
+        case 1: go_strain<R, 256>(c, u, uhl, Vg, h); break;
+        default: go_strain<R, 512>(c, u, uhl, Vg, h);
+    }
+}
+
+template <class R, int TB, int FB>
+void go_edge(cem_ctx* c, const R* h, const R* cl, const R* cm, R* sig) {
+    cem_pdl(c->stream, k_edge_stress<R, TB, FB>, cem_grid(c->E, TB), TB, h, c->fan_off, c->fan_cnt, c->fan_pool, cl, cm,
+            c->E, sig);
+}
+template <class R, int FB>
+void go_edge_tb(cem_ctx* c, int v, const R* h, const R* cl, const R* cm, R* sig) {
+    switch (v % 3) {
+        case 0: go_edge<R, 128, FB>(c, h, cl, cm, sig); break;
+        case 1: go_edge<R, 256, FB>(c, h, cl, cm, sig); break;
+        default: go_edge<R, 512, FB>(c, h, cl, cm, sig);
+    }
+}
+template <class R>
+void launch_edge(cem_ctx* c, int v, const R* h, const R* cl, const R* cm, R* sig) {
+    switch (v / 3) {
+        case 0: go_edge_tb<R, 1>(c, v, h, cl, cm, sig); break;
+        case 1: go_edge_tb<R, 2>(c, v, h, cl, cm, sig); break;
+        default: go_edge_tb<R, 4>(c, v, h, cl, cm, sig);
+    }
+}
+
+template <class R, int TB>
+void go_force(cem_ctx* c, const R* sig, const R* Vg, R* fp) {
+    cem_pdl(c->stream, k_force<R, TB>, cem_grid(c->T, TB), TB, sig, c->t2e, Vg, c->active, c->Tc, c->T, fp);
+}
+template <class R>
+void launch_force(cem_ctx* c, int v, const R* sig, const R* Vg, R* fp) {
+    switch (v % 3) {
+        case 0: go_force<R, 128>(c, sig, Vg, fp); break;
+        case 1: go_force<R, 256>(c, sig, Vg, fp); break;
+        default: go_force<R, 512>(c, sig, Vg, fp);
+    }
+}
+
+template <class R, int TB, int NB>
+void go_node(cem_ctx* c, const R* fp, int first) {
+    cem_pdl(c->stream, k_node_update<R, TB, NB>, cem_grid(c->N, TB), TB, fp, c->inc_off, c->inc_cnt, c->inc_pool,
+            c->fext, c->minv, c->v, c->a, c->Nc, c->N, 0.5 * c->dt, first, c->dtn);
+}
+template <class R, int NB>
+void go_node_tb(cem_ctx* c, int v, const R* fp, int first) {
+    switch (v % 3) {
+        case 0: go_node<R, 128, NB>(c, fp, first); break;
+        case 1: go_node<R, 256, NB>(c, fp, first); break;
+        default: go_node<R, 512, NB>(c, fp, first);
+    }
+}
+template <class R>
+void launch_node(cem_ctx* c, int v, const R* fp, int first) {
+    switch (v / 3) {
+        case 0: go_node_tb<R, 2>(c, v, fp, first); break;
+        case 1: go_node_tb<R, 4>(c, v, fp, first); break;
+        default: go_node_tb<R, 8>(c, v, fp, first);
+    }
+}
+
 // ---------------------------------------------------------------- adjoint of the step
 // f[i] = (1/6) sum over node incidence of the element forces: K y when the
 // element forces were computed from the strain of y.
@@ -782,12 +871,10 @@ __global__ void __launch_bounds__(RB) k_reduce_one(const double* __restrict__ pa
 int cem_adj_strain(cem_ctx* c, const double* y, float* yhl, void* hbuf) {
     if (mixed(c)) {
         cem_pdl(c->stream, k_split_u, cem_grid(c->N, BS), BS, y, c->Nc, c->N, yhl);
-        cem_pdl(c->stream, k_strain<float>, cem_grid(c->T, BS), BS, y, yhl, c->Nc, c->conn, c->Vg32, c->active, c->Tc,
-                                                                  c->T, (float*)hbuf);
+        launch_strain<float>(c, c->tune[TUNE_STRAIN], y, yhl, c->Vg32, (float*)hbuf);
         cem_launched(c, 2);
     } else {
-        cem_pdl(c->stream, k_strain<double>, cem_grid(c->T, BS), BS, y, nullptr, c->Nc, c->conn, c->Vg, c->active, c->Tc,
-                                                                   c->T, (double*)hbuf);
+        launch_strain<double>(c, c->tune[TUNE_STRAIN], y, nullptr, c->Vg, (double*)hbuf);
         cem_launched(c, 1);
     }
     CEM_CK(c, cudaGetLastError());
@@ -887,11 +974,9 @@ int cem_launch_split_u(cem_ctx* c) {
 
 int cem_launch_strain(cem_ctx* c) {
     if (mixed(c))
-        cem_pdl(c->stream, k_strain<float>, cem_grid(c->T, BS), BS, c->u, c->uhl, c->Nc, c->conn, c->Vg32, c->active, c->Tc,
-                                                                  c->T, c->h32);
+        launch_strain<float>(c, c->tune[TUNE_STRAIN], c->u, c->uhl, c->Vg32, c->h32);
     else
-        cem_pdl(c->stream, k_strain<double>, cem_grid(c->T, BS), BS, c->u, nullptr, c->Nc, c->conn, c->Vg, c->active, c->Tc,
-                                                                   c->T, c->h);
+        launch_strain<double>(c, c->tune[TUNE_STRAIN], c->u, nullptr, c->Vg, c->h);
     cem_launched(c);
     CEM_CK(c, cudaGetLastError());
     return CEM_OK;
@@ -899,11 +984,9 @@ int cem_launch_strain(cem_ctx* c) {
 
 int cem_launch_edge_stress(cem_ctx* c) {
     if (mixed(c))
-        cem_pdl(c->stream, k_edge_stress<float>, cem_grid(c->E, BS), BS, c->h32, c->fan_off, c->fan_cnt, c->fan_pool,
-                                                                       c->cl32, c->cm32, c->E, c->sig32);
+        launch_edge<float>(c, c->tune[TUNE_EDGE], c->h32, c->cl32, c->cm32, c->sig32);
     else
-        cem_pdl(c->stream, k_edge_stress<double>, cem_grid(c->E, BS), BS, c->h, c->fan_off, c->fan_cnt, c->fan_pool,
-                                                                        c->cl, c->cm, c->E, c->sig);
+        launch_edge<double>(c, c->tune[TUNE_EDGE], c->h, c->cl, c->cm, c->sig);
     cem_launched(c);
     CEM_CK(c, cudaGetLastError());
     return CEM_OK;
@@ -911,11 +994,9 @@ int cem_launch_edge_stress(cem_ctx* c) {
 
 int cem_launch_force(cem_ctx* c) {
     if (mixed(c))
-        cem_pdl(c->stream, k_force<float>, cem_grid(c->T, BS), BS, c->sig32, c->t2e, c->Vg32, c->active, c->Tc, c->T,
-                                                                 c->fp32);
+        launch_force<float>(c, c->tune[TUNE_FORCE], c->sig32, c->Vg32, c->fp32);
     else
-        cem_pdl(c->stream, k_force<double>, cem_grid(c->T, BS), BS, c->sig, c->t2e, c->Vg, c->active, c->Tc, c->T,
-                                                                  c->fp);
+        launch_force<double>(c, c->tune[TUNE_FORCE], c->sig, c->Vg, c->fp);
     cem_launched(c);
     CEM_CK(c, cudaGetLastError());
     return CEM_OK;
@@ -923,13 +1004,54 @@ int cem_launch_force(cem_ctx* c) {
 
 int cem_launch_node_update(cem_ctx* c, int first) {
     if (mixed(c))
-        cem_pdl(c->stream, k_node_update<float>, cem_grid(c->N, BS), BS, 
-            c->fp32, c->inc_off, c->inc_cnt, c->inc_pool, c->fext, c->minv, c->v, c->a, c->Nc, c->N, 0.5 * c->dt, first,
-            c->dtn);
+        launch_node<float>(c, c->tune[TUNE_NODE], c->fp32, first);
     else
-        cem_pdl(c->stream, k_node_update<double>, cem_grid(c->N, BS), BS, 
-            c->fp, c->inc_off, c->inc_cnt, c->inc_pool, c->fext, c->minv, c->v, c->a, c->Nc, c->N, 0.5 * c->dt, first,
-            c->dtn);
+        launch_node<double>(c, c->tune[TUNE_NODE], c->fp, first);
+    cem_launched(c);
+    CEM_CK(c, cudaGetLastError());
+    return CEM_OK;
+}
+
+// ---- tuning variants: variant v of a kernel runs TB = 128 << (v % 3) threads per
+// block and the kernel's batch parameter BATCH[kernel][v / 3]
+namespace {
+constexpr int TUNE_BATCH[TUNE_COUNT][3] = {{1, 1, 1}, {1, 2, 4}, {1, 1, 1}, {2, 4, 8}};
+}  // namespace
+
+int cem_tune_variants(int k) { return (k == TUNE_EDGE || k == TUNE_NODE) ? 9 : 3; }
+
+void cem_tune_describe(int k, int v, int* block, int* batch) {
+    *block = 128 << (v % 3);
+    *batch = TUNE_BATCH[k][v / 3];
+}
+
+// The variants used before any tuning: 256 threads, plain fans, node batches of 8 (FP32) or 4 (FP64).
+int cem_tune_default(int k, int precision) {
+    if (k == TUNE_NODE) return 1 + 3 * (precision == CEM_MIXED ? 2 : 1);
+    return 1;
+}
+
+// One launch of variant v on the context's current buffers (the node update in
+// its first-step form, which writes a only).
+int cem_launch_tune_variant(cem_ctx* c, int k, int v) {
+    const bool m = mixed(c);
+    switch (k) {
+        case TUNE_STRAIN:
+            if (m) launch_strain<float>(c, v, c->u, c->uhl, c->Vg32, c->h32);
+            else launch_strain<double>(c, v, c->u, nullptr, c->Vg, c->h);
+            break;
+        case TUNE_EDGE:
+            if (m) launch_edge<float>(c, v, c->h32, c->cl32, c->cm32, c->sig32);
+            else launch_edge<double>(c, v, c->h, c->cl, c->cm, c->sig);
+            break;
+        case TUNE_FORCE:
+            if (m) launch_force<float>(c, v, c->sig32, c->Vg32, c->fp32);
+            else launch_force<double>(c, v, c->sig, c->Vg, c->fp);
+            break;
+        default:
+            if (m) launch_node<float>(c, v, c->fp32, 1);
+            else launch_node<double>(c, v, c->fp, 1);
+    }
     cem_launched(c);
     CEM_CK(c, cudaGetLastError());
     return CEM_OK;
