@@ -60,7 +60,8 @@ def kernel_costs(T, E, N, precision):
     edge, element forces per element).  f = mean fan size 6T/E, g = mean node
     incidence 4T/N.  Mixed precision: FP32 geometry, coefficients and
     intermediate records (h, sigma: 32 B; element forces: 64 B), an FP32
-    hi/lo copy of u (32 B per node), FP64 node state.
+    hi/lo copy of the predicted u (32 B per node), FP64 node state; the node
+    update also reads and writes u and writes that copy (the fused predictor).
     """
     f, g = 6.0 * T / E, 4.0 * T / N
     flops = {"predict": 12.0, "strain": 57.0, "edge_stress": 6.0 * f + 13.0, "force": 90.0,
@@ -72,11 +73,11 @@ def kernel_costs(T, E, N, precision):
                 "force": 24 + 72 + 96 + 48.0 * E / T,
                 "node_update": 8 + 4.0 * g + 24 + 8 + 96 + 96.0 * T / N}
     else:
-        byts = {"predict": 128.0,
+        byts = {"predict": 0.0,   # carried by the node update
                 "strain": 16 + 36 + 32 + 32.0 * N / T,
                 "edge_stress": 8 + 4.0 * f + 8 + 32 + 32.0 * T / E,
                 "force": 24 + 36 + 64 + 32.0 * E / T,
-                "node_update": 8 + 4.0 * g + 24 + 8 + 96 + 64.0 * T / N}
+                "node_update": 8 + 4.0 * g + 24 + 8 + 96 + 80 + 64.0 * T / N}
     return flops, byts
 
 
@@ -288,7 +289,7 @@ def run_cem(a):
         sm_clock = (clk or {}).get("sm_max_mhz") or peaks.get("sm_max_mhz") or 2070.0
         fp64_peak = 152 * 4 * sm_clock * 1e6      # 152 SMs x 2 FP64 FMA/clk x 2 FLOP
         # timed launches are a sample (every PROFILE_EVERY-th step): scale sums to the whole region
-        n_sampled = max(prof["predict"][1], 1)
+        n_sampled = max(prof["strain"][1], 1)
         scale = steps / n_sampled
         kernels = {}
         for k, (ms_tot, nl) in prof.items():

@@ -233,11 +233,13 @@ int cem_info(cem_ctx* ctx, cem_info_t* out);
  * NULL) and, in *total_launches (may be NULL), the number of kernels of any
  * kind the context launched since the last cem_profile(ctx, k >= 1).  Timing adds
  * two event records per launch; it does not change results. */
-#define CEM_KERNEL_PREDICT     0   /* u <- u + dt v + dt^2/2 a                      */
+#define CEM_KERNEL_PREDICT     0   /* u <- u + dt v + dt^2/2 a (FP64 path; in mixed */
+                                   /* precision the node update carries it)         */
 #define CEM_KERNEL_STRAIN      1   /* per-element V * strain                        */
 #define CEM_KERNEL_EDGE_STRESS 2   /* fan sum, smoothed edge stress                 */
 #define CEM_KERNEL_FORCE       3   /* per-element nodal forces                      */
 #define CEM_KERNEL_NODE_UPDATE 4   /* nodal force gather, acceleration, velocity    */
+                                   /* (mixed: also u and the next predictor)        */
 #define CEM_KERNEL_FRONT_G     5   /* energy release rates and split decisions      */
 #define CEM_KERNEL_SPLIT       6   /* the whole split sequence of one step          */
 #define CEM_KERNEL_COUNT       7

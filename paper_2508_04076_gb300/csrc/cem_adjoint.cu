@@ -108,7 +108,7 @@ extern "C" int cem_adjoint(cem_ctx* c, int64_t n_steps, int64_t checkpoint_every
         int r;
         if ((r = copy3(c, c->u, src)) || (r = copy3(c, c->v, src + 3 * Nc)) || (r = copy3(c, c->a, src + 6 * Nc)))
             return r;
-        return cem_launch_split_u(c);
+        return cem_launch_pred_u(c);
     };
     // forward sweep with checkpoints
     for (int64_t n = 0; n < n_steps; ++n) {

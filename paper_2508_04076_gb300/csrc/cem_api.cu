@@ -569,7 +569,8 @@ int run_step(cem_ctx* c) {
     if (c->tune_auto)
         if (int rc = cem_tune_maybe(c)) return rc;
     c->prof_now = c->prof && (c->step % c->prof_every == 0);
-    TIMED(c, CEM_KERNEL_PREDICT, cem_launch_predict(c));
+    if (c->precision != CEM_MIXED)   // mixed precision: the node update carries the predictor
+        TIMED(c, CEM_KERNEL_PREDICT, cem_launch_predict(c));
     TIMED(c, CEM_KERNEL_STRAIN, cem_launch_strain(c));
     TIMED(c, CEM_KERNEL_EDGE_STRESS, cem_launch_edge_stress(c));
     TIMED(c, CEM_KERNEL_FORCE, cem_launch_force(c));
@@ -712,7 +713,7 @@ int cem_energy(cem_ctx* c, cem_energy_t* out) {
     int rc;
     if ((rc = cem_launch_split_u(c)) || (rc = cem_launch_strain(c)) || (rc = cem_launch_edge_stress(c))) return rc;
     double r[4];
-    if ((rc = cem_energy_reduce(c, r))) return rc;
+    if ((rc = cem_energy_reduce(c, r)) || (rc = cem_launch_pred_u(c))) return rc;
     double Ud = 0.0;
     CEM_CK(c, cudaMemcpy(&Ud, c->Ud, sizeof(double), cudaMemcpyDeviceToHost));
     out->kinetic = r[0];
@@ -734,7 +735,7 @@ int cem_energy_instance(cem_ctx* c, int64_t instance, cem_energy_t* out) {
     int rc;
     if ((rc = cem_launch_split_u(c)) || (rc = cem_launch_strain(c)) || (rc = cem_launch_edge_stress(c))) return rc;
     double r[5];
-    if ((rc = cem_energy_reduce_instance(c, (int)instance, r))) return rc;
+    if ((rc = cem_energy_reduce_instance(c, (int)instance, r)) || (rc = cem_launch_pred_u(c))) return rc;
     const double dt = c->inst_dt[instance];
     int64_t nsplit = 0;
     if (c->n_inst > 1) {

@@ -13,7 +13,9 @@
 //            sig  : one 6-value record per edge, smoothed edge stress  (step output)
 //   mixed precision (CEM_MIXED) keeps FP32 copies Vg32, cl32, cm32 and FP32
 //   h32 / sig32 / fp32 records in place of the FP64 ones, plus uhl: per node
-//   8 floats (hi.xyz, lo.xyz, pad) with u = hi + lo, written by the predictor.
+//   8 floats (hi.xyz, lo.xyz, pad) with hi + lo = the displacement the next
+//   step's strain kernel uses (the predictor of Eq. 15), written by the node
+//   update of the previous step (which also advances u itself).
 //   cracks   (original elements only, [T0]) side mask, split step, G, Gc, face_nbr [4][T0]
 //            node_of_key [2*E0]: new node on original edge e attached to its
 //            smaller (side 0) or larger (side 1) endpoint, -1 if none.
@@ -26,6 +28,27 @@
 #include <vector>
 
 #include "../../include/cem.h"
+
+// Predictor of Eq. 15, u + dt v + dt^2/2 a, with fixed roundings: the fused
+// node update, the split path and the re-prediction after an energy call must
+// produce the same bits for the same node.
+__device__ __forceinline__ double cem_pred(double u, double v, double a, double dt, double hdt2) {
+    return __fma_rn(hdt2, a, __fma_rn(dt, v, u));
+}
+
+// Mixed precision: FP32 hi/lo record of a node's predicted displacement
+// (hi.xyz, lo.x | lo.y, lo.z, pad, pad), read by the strain kernel.
+__device__ __forceinline__ void cem_store_hl(float* uhl, int64_t i, const double x[3]) {
+    float hi[3], lo[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        hi[c] = (float)x[c];
+        lo[c] = (float)(x[c] - (double)hi[c]);
+    }
+    float4* p = reinterpret_cast<float4*>(uhl + 8 * i);
+    p[0] = make_float4(hi[0], hi[1], hi[2], lo[0]);
+    p[1] = make_float4(lo[1], lo[2], 0.f, 0.f);
+}
 
 #define CEM_LE0(l) (((l) < 3) ? 0 : (((l) < 5) ? 1 : 2))
 #define CEM_LE1(l) (((l) < 3) ? (l) + 1 : (((l) < 5) ? (l) - 1 : 3))
@@ -212,7 +235,8 @@ int64_t cem_scan_blocks_needed(int64_t n);
 // ---------------------------------------------------------------- step kernels (cem_step.cu)
 int cem_launch_geometry(cem_ctx* c, int64_t t_begin, int64_t t_end, double* hbuf);
 int cem_launch_predict(cem_ctx* c);
-int cem_launch_split_u(cem_ctx* c);   // mixed: refresh the FP32 hi/lo copy of u
+int cem_launch_split_u(cem_ctx* c);   // mixed: FP32 hi/lo copy of the current u (energy evaluation)
+int cem_launch_pred_u(cem_ctx* c);    // mixed: FP32 hi/lo copy of the next step's predicted u
 int cem_launch_prescribe(cem_ctx* c, int64_t step);   // v, a of prescribed components at t = step * dt
 int cem_launch_strain(cem_ctx* c);
 int cem_launch_edge_stress(cem_ctx* c);

@@ -281,6 +281,8 @@ struct NodeStore {
     const int *oe_n0, *oe_n1;
     double *X, *u, *v, *a, *fext, *mass, *minv, *dtn;
     int *inc_off, *inc_cnt, *node_inst;
+    float* uhl;     // mixed precision: the new node's next-predictor record
+    double dt;
     __device__ void operator()(int64_t key, int pos, int val) const {
         if (!val) return;
         const int e = (int)(key >> 1);
@@ -300,7 +302,14 @@ struct NodeStore {
         inc_off[id] = 0;
         inc_cnt[id] = 0;
         if (node_inst) node_inst[id] = node_inst[n0];
-        if (dtn) dtn[id] = dtn[n0];
+        double d = dt;
+        if (dtn) d = dtn[id] = dtn[n0];
+        if (uhl) {
+            double x[3];
+            for (int c = 0; c < 3; ++c)
+                x[c] = cem_pred(u[c * Nc + id], v[c * Nc + id], a[c * Nc + id], d, 0.5 * d * d);
+            cem_store_hl(uhl, id, x);
+        }
     }
 };
 
@@ -878,7 +887,8 @@ int cem_apply_splits(cem_ctx* c, int64_t S64, int64_t step, int book_energy) {
     CEM_CK(c, cudaGetLastError());
     if ((rc = run_scan(c, U8Load{c->key_flag},
                        NodeStore{c->N, c->Nc, c->node_of_key, c->key_flag, c->oe_n0, c->oe_n1, c->X, c->u, c->v, c->a,
-                                 c->fext, c->mass, c->minv, c->dtn, c->inc_off, c->inc_cnt, c->node_inst},
+                                 c->fext, c->mass, c->minv, c->dtn, c->inc_off, c->inc_cnt, c->node_inst,
+                                 c->precision == CEM_MIXED ? c->uhl : nullptr, c->dt},
                        2 * c->E0, CNT_NEWNODE)))
         return rc;
     // 2. sub-elements, numbered by (parent, local sub index)

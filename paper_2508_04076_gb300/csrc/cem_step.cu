@@ -1,12 +1,17 @@
 // Explicit ES-T-FEM step kernels (Sec. 2.2).
 //
-// One step is five launches over the device mesh:
+// One step is five launches over the device mesh (four in mixed precision,
+// where the predictor is part of the node update):
 //   predict      u <- u + dt v + dt^2/2 a                          (Eq. 15)
 //   strain       h_j = V_j * Voigt(sym grad u) of every element    (Eq. 6 per element)
 //   edge_stress  sigma_k = Dbar_k (sum_{j in fan(k)} h_j) / sumV_k  (Eqs. 4-6, Sec. 2.1)
 //   force        fp_{j,a} = (sum_{k in edges(j)} sigma_k) . (V_j grad N_a)
 //   node_update  f_i = (1/6) sum over node incidence of fp; a = M^-1 (f_ext - f);
 //                v <- v + dt/2 (a_old + a)                         (Eqs. 13-14)
+// Mixed precision: the node update of step n also advances u to u_n (from
+// u_{n-1}, v_{n-1}, a_{n-1}, before overwriting them) and writes the FP32
+// hi/lo record of the next predictor u_n + dt v_n + dt^2/2 a_n for the next
+// strain kernel, so no separate predictor pass reads and writes the node state.
 // The force kernel uses the identity
 //   sum_k Vs_k Bbar_k^T sigma_k = sum_j V_j B_j^T ((1/6) sum_{k in edges(j)} sigma_k)
 // (Vs_k = sumV_k / 6, Bbar_k = sum_j V_j B_j / sumV_k, each element lies in the
@@ -123,8 +128,7 @@ __global__ void __launch_bounds__(BS) k_geometry(const double* __restrict__ X, i
 // dtn (ensembles): per-node time step of the node's specimen; NULL: dt for all.
 __global__ void __launch_bounds__(BS) k_predict(double* __restrict__ u, const double* __restrict__ v,
                                                 const double* __restrict__ a, int64_t Nc, int64_t N,
-                                                double dt, double hdt2, float* __restrict__ uhl,
-                                                const double* __restrict__ dtn) {
+                                                double dt, double hdt2, const double* __restrict__ dtn) {
     CEM_PDL_ENTRY();
     int64_t i = (int64_t)blockIdx.x * BS + threadIdx.x;
     if (i >= N) return;
@@ -132,27 +136,14 @@ __global__ void __launch_bounds__(BS) k_predict(double* __restrict__ u, const do
         dt = dtn[i];
         hdt2 = 0.5 * dt * dt;
     }
-    double un[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         int64_t k = c * Nc + i;
-        un[c] = u[k] + dt * v[k] + hdt2 * a[k];
-        u[k] = un[c];
-    }
-    if (uhl) {
-        float hi[3], lo[3];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            hi[c] = (float)un[c];
-            lo[c] = (float)(un[c] - (double)hi[c]);
-        }
-        float4* p = reinterpret_cast<float4*>(uhl + 8 * i);
-        p[0] = make_float4(hi[0], hi[1], hi[2], lo[0]);
-        p[1] = make_float4(lo[1], lo[2], 0.f, 0.f);
+        u[k] = cem_pred(u[k], v[k], a[k], dt, hdt2);
     }
 }
 
-// Split u into FP32 hi/lo records (mixed mode, after set-up or a split).
+// FP32 hi/lo records of the current u (mixed mode: strain of the current state for an energy evaluation).
 __global__ void __launch_bounds__(BS) k_split_u(const double* __restrict__ u, int64_t Nc, int64_t N,
                                                 float* __restrict__ uhl) {
     CEM_PDL_ENTRY();
@@ -322,22 +313,33 @@ __global__ void __launch_bounds__(TB) k_force(const R* __restrict__ sig, const i
 
 // Prescribed velocity ramp v(t) = min(t / t0, 1) v0 (Sec. 4.1-4.3, 4.5): the
 // velocity and the ramp's acceleration overwrite the corrector's values.
+// Mixed precision also rewrites that component of the next predictor's FP32
+// hi/lo record (the node update wrote it from the corrector's values).
 __global__ void __launch_bounds__(BS) k_prescribe(int64_t n, const int* __restrict__ key,
                                                   const double* __restrict__ v0, double t0, int64_t step, double dt,
                                                   const double* __restrict__ dtn, double* __restrict__ v,
-                                                  double* __restrict__ a, int64_t Nc) {
+                                                  double* __restrict__ a, int64_t Nc, const double* __restrict__ u,
+                                                  float* __restrict__ uhl) {
     CEM_PDL_ENTRY();
     const int64_t q = (int64_t)blockIdx.x * BS + threadIdx.x;
     if (q >= n) return;
     const int i = key[q] >> 2, comp = key[q] & 3;
-    const double t = (double)step * (dtn ? dtn[i] : dt);
+    if (dtn) dt = dtn[i];
+    const double t = (double)step * dt;
     double fv = 1.0, fa = 0.0;
     if (t0 > 0.0 && t < t0) {
         fv = t / t0;
         fa = 1.0 / t0;
     }
-    v[comp * Nc + i] = fv * v0[q];
-    a[comp * Nc + i] = fa * v0[q];
+    const double vv = fv * v0[q], aa = fa * v0[q];
+    v[comp * Nc + i] = vv;
+    a[comp * Nc + i] = aa;
+    if (uhl) {
+        const double x = cem_pred(u[comp * Nc + i], vv, aa, dt, 0.5 * dt * dt);
+        const float hi = (float)x, lo = (float)(x - (double)hi);
+        uhl[8 * (int64_t)i + comp] = hi;
+        uhl[8 * (int64_t)i + 3 + comp] = lo;
+    }
 }
 
 template <class R, int TB, int NB>
@@ -345,7 +347,8 @@ __global__ void __launch_bounds__(TB) k_node_update(const R* __restrict__ fp, co
                                                     const int* __restrict__ inc_cnt, const int* __restrict__ inc_pool,
                                                     const double* __restrict__ fext, const double* __restrict__ minv,
                                                     double* __restrict__ v, double* __restrict__ a, int64_t Nc,
-                                                    int64_t N, double hdt, int first, const double* __restrict__ dtn) {
+                                                    int64_t N, double hdt, int first, const double* __restrict__ dtn,
+                                                    double* __restrict__ u, float* __restrict__ uhl) {
     CEM_PDL_ENTRY();
     int64_t i = (int64_t)blockIdx.x * TB + threadIdx.x;
     if (i >= N) return;
@@ -408,13 +411,45 @@ __global__ void __launch_bounds__(TB) k_node_update(const R* __restrict__ fp, co
     // launch variants; fixing the roundings keeps every variant bit-identical.
     const double mi = minv[i];
     const double sixth = 1.0 / 6.0;
+    const double dt = hdt + hdt, hdt2 = hdt * dt;
+    double un[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         const int64_t k = c * Nc + i;
         const double an = (mi == 0.0) ? 0.0 : __dmul_rn(__fma_rn(-f[c], sixth, fext[k]), mi);
-        if (!first) v[k] = __fma_rn(hdt, __dadd_rn(a[k], an), v[k]);
+        const double ao = a[k], vo = v[k];
+        double vn = vo;
+        if (uhl) {   // fused predictor: u_n from the old state, then the next predictor
+            double uc = u[k];
+            if (!first) {
+                uc = cem_pred(uc, vo, ao, dt, hdt2);
+                u[k] = uc;
+            }
+            if (!first) vn = __fma_rn(hdt, __dadd_rn(ao, an), vo);
+            un[c] = cem_pred(uc, vn, an, dt, hdt2);
+        } else if (!first) {
+            vn = __fma_rn(hdt, __dadd_rn(ao, an), vo);
+        }
+        if (!first) v[k] = vn;
         a[k] = an;
     }
+    if (uhl) cem_store_hl(uhl, i, un);
+}
+
+// Mixed precision: FP32 hi/lo record of the next predictor u + dt v + dt^2/2 a
+// (after set-up, a split or an energy evaluation changed uhl or the state).
+__global__ void __launch_bounds__(BS) k_pred_u(const double* __restrict__ u, const double* __restrict__ v,
+                                               const double* __restrict__ a, int64_t Nc, int64_t N, double dt,
+                                               const double* __restrict__ dtn, float* __restrict__ uhl) {
+    CEM_PDL_ENTRY();
+    int64_t i = (int64_t)blockIdx.x * BS + threadIdx.x;
+    if (i >= N) return;
+    if (dtn) dt = dtn[i];
+    const double hdt2 = 0.5 * dt * dt;
+    double x[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) x[c] = cem_pred(u[c * Nc + i], v[c * Nc + i], a[c * Nc + i], dt, hdt2);
+    cem_store_hl(uhl, i, x);
 }
 
 __global__ void __launch_bounds__(BS) k_edge_coeffs(const int* __restrict__ list, int64_t n,
@@ -694,7 +729,8 @@ void launch_force(cem_ctx* c, int v, const R* sig, const R* Vg, R* fp) {
 template <class R, int TB, int NB>
 void go_node(cem_ctx* c, const R* fp, int first) {
     cem_pdl(c->stream, k_node_update<R, TB, NB>, cem_grid(c->N, TB), TB, fp, c->inc_off, c->inc_cnt, c->inc_pool,
-            c->fext, c->minv, c->v, c->a, c->Nc, c->N, 0.5 * c->dt, first, c->dtn);
+            c->fext, c->minv, c->v, c->a, c->Nc, c->N, 0.5 * c->dt, first, c->dtn, c->u,
+            sizeof(R) == 4 ? c->uhl : nullptr);
 }
 template <class R, int NB>
 void go_node_tb(cem_ctx* c, int v, const R* fp, int first) {
@@ -957,8 +993,17 @@ int cem_launch_geometry(cem_ctx* c, int64_t t0, int64_t t1, double* hbuf) {
 
 int cem_launch_predict(cem_ctx* c) {
     if (c->N == 0) return CEM_OK;
+    if (mixed(c)) return CEM_OK;   // part of the node update
     cem_pdl(c->stream, k_predict, cem_grid(c->N, BS), BS, c->u, c->v, c->a, c->Nc, c->N, c->dt, 0.5 * c->dt * c->dt,
-                                                        mixed(c) ? c->uhl : nullptr, c->dtn);
+                                                        c->dtn);
+    cem_launched(c);
+    CEM_CK(c, cudaGetLastError());
+    return CEM_OK;
+}
+
+int cem_launch_pred_u(cem_ctx* c) {
+    if (!mixed(c) || c->N == 0) return CEM_OK;
+    cem_pdl(c->stream, k_pred_u, cem_grid(c->N, BS), BS, c->u, c->v, c->a, c->Nc, c->N, c->dt, c->dtn, c->uhl);
     cem_launched(c);
     CEM_CK(c, cudaGetLastError());
     return CEM_OK;
@@ -1060,7 +1105,7 @@ int cem_launch_tune_variant(cem_ctx* c, int k, int v) {
 int cem_launch_prescribe(cem_ctx* c, int64_t step) {
     if (c->n_dir == 0) return CEM_OK;
     cem_pdl(c->stream, k_prescribe, cem_grid(c->n_dir, BS), BS, c->n_dir, c->dir_key, c->dir_v0, c->dir_t0, step, c->dt,
-            c->dtn, c->v, c->a, c->Nc);
+            c->dtn, c->v, c->a, c->Nc, c->u, mixed(c) ? c->uhl : nullptr);
     cem_launched(c);
     CEM_CK(c, cudaGetLastError());
     return CEM_OK;

@@ -20,8 +20,9 @@
 //
 // The strain, edge-stress and force kernels are pure functions of their inputs
 // and are simply re-run; the node update is timed in its first-step form,
-// which overwrites the accelerations only, and they are restored afterwards
-// from a copy (tune_save, allocated by cem_autotune).
+// which overwrites the accelerations (and, in mixed precision, the records of
+// the next predictor) only; the accelerations are restored afterwards from a
+// copy (tune_save, allocated by cem_autotune) and the records rebuilt.
 #include "cem_common.cuh"
 
 #include <cmath>
@@ -150,7 +151,10 @@ int tune_kernel(cem_ctx* c, int k, const std::string& gpu) {
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    if (k == TUNE_NODE) CEM_CK(c, cudaMemcpyAsync(c->a, c->tune_save, abytes, cudaMemcpyDeviceToDevice, c->stream));
+    if (k == TUNE_NODE) {   // restore a, then the mixed path's next-predictor records built from it
+        CEM_CK(c, cudaMemcpyAsync(c->a, c->tune_save, abytes, cudaMemcpyDeviceToDevice, c->stream));
+        if (!rc) rc = cem_launch_pred_u(c);
+    }
     if (rc) return rc;
     CEM_CK(c, cudaStreamSynchronize(c->stream));
     c->tune[k] = best;
