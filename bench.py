@@ -51,6 +51,13 @@ def _workload(name="block"):
 
 KERNEL_UNITS = {"predict": "nodes", "strain": "tets", "edge_stress": "edges", "force": "tets", "node_update": "nodes"}
 
+# DRAM bytes (read + write) per unit measured by ncu for the mixed-precision kernels on the
+# 960,000-element block (profiles/mixed_kernels_notched_block_200x80x10.md); scaled by the
+# units of an average launch for the roofline's "traffic".  None: no capture of the current
+# kernel (FP64 path).
+DRAM_BYTES_PER_UNIT = {"mixed": {"strain": 61.1, "edge_stress": 68.0, "force": 124.6, "node_update": 554.0},
+                       "fp64": {}}
+
 
 def kernel_costs(T, E, N, precision):
     """Algorithmic FP64 flops (FMA = 2; FP64 path) and bytes per unit of each hot kernel.
@@ -262,7 +269,7 @@ def run_cem(a):
         sim.step(a.warmup)
         barrier()
         clocks = ClockSampler(_bus_id(dev)) if (clocks_on and rank == 0) else None
-        sim.profile(PROFILE_EVERY)
+        sim.profile(max(1, min(PROFILE_EVERY, steps // 4)))   # at least a few sampled steps
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         sim.step(steps)
@@ -290,6 +297,8 @@ def run_cem(a):
         fp64_peak = 152 * 4 * sm_clock * 1e6      # 152 SMs x 2 FP64 FMA/clk x 2 FLOP
         # timed launches are a sample (every PROFILE_EVERY-th step): scale sums to the whole region
         n_sampled = max(prof["strain"][1], 1)
+        if prof["strain"][1] == 0:
+            raise RuntimeError("no sampled step in the timed region")
         scale = steps / n_sampled
         kernels = {}
         for k, (ms_tot, nl) in prof.items():
@@ -313,8 +322,12 @@ def run_cem(a):
         else:
             achieved, peak, unit = bytes_ / per_launch_s / 1e9, hbm, "GB/s"
             src = "MEASURED_PEAKS.json hbm_gbs (measured copy bandwidth)"
+        per_unit = DRAM_BYTES_PER_UNIT.get(precision, {}).get(dom)
+        traffic = per_unit * units if per_unit is not None else None
         roofline = {"bound": "alu" if alu_bound else "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
-                    "unit": unit, "frac": achieved / peak, "traffic": None, "peak_source": src,
+                    "unit": unit, "frac": achieved / peak, "traffic": traffic, "peak_source": src,
+                    "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum per unit on the 960,000-"
+                                       "element block, scaled to this launch's units" if traffic else None),
                     "per_launch_us": per_launch_s * 1e6, "algorithmic_bytes_per_launch": bytes_,
                     "hbm_gbs_achieved": bytes_ / per_launch_s / 1e9, "hbm_peak_gbs": hbm,
                     "units_per_launch": units}
