@@ -183,6 +183,75 @@ def kuhn_block(nx: int, ny: int, nz: int, Lx: float, Ly: float, Lz: float, *,
 
 
 # ---------------------------------------------------------------------------
+# Trilinear hexahedra (the ES-H-FEM form of Sec. 2.2)
+# ---------------------------------------------------------------------------
+
+@dataclass
+class HexWorkload:
+    """A block of 8-node hexahedra (host numpy).  Local node order: (i,j,k),
+    (i+1,j,k), (i+1,j+1,k), (i,j+1,k), then the same four at k+1, so natural
+    coordinates (xi, eta, zeta) run along x, y, z and the volume is positive."""
+    name: str
+    X: np.ndarray            # (N, 3) float64
+    hexes: np.ndarray        # (T, 8) int32 node ids
+    tquads: np.ndarray       # (F, 4) int32 traction quadrilaterals
+    tvec: np.ndarray         # (F, 3) float64 traction vector on each face [Pa]
+    E: np.ndarray            # (T,) float64
+    nu: float
+    rho: float
+    shape: tuple = ()
+    params: dict = field(default_factory=dict)
+
+    @property
+    def n_nodes(self) -> int:
+        return int(self.X.shape[0])
+
+    @property
+    def n_elems(self) -> int:
+        return int(self.hexes.shape[0])
+
+
+def hex_block(nx: int, ny: int, nz: int, Lx: float, Ly: float, Lz: float, *,
+              E: float = 32e9, nu: float = 0.2, rho: float = 2450.0, traction: float = 1e6,
+              jitter: float = 0.0, E_cov: float = 0.0, seed: int = 0, name: str | None = None) -> HexWorkload:
+    """Structured block of nx*ny*nz hexahedral cells (node and cell numbering as in
+    kuhn_block).  Traction +traction (y) on the quadrilaterals of y = Ly and
+    -traction on those of y = 0; interior nodes jittered as in kuhn_block."""
+    hx, hy, hz = Lx / nx, Ly / ny, Lz / nz
+    NX, NY, NZ = nx + 1, ny + 1, nz + 1
+    n_nodes = NX * NY * NZ
+    ii, jj, kk = np.meshgrid(np.arange(NX), np.arange(NY), np.arange(NZ), indexing="ij")
+    ii, jj, kk = (a.transpose(2, 1, 0).ravel() for a in (ii, jj, kk))
+    X = np.stack([ii * hx, jj * hy, kk * hz], axis=1).astype(np.float64)
+    if jitter > 0.0:
+        interior = ((ii > 0) & (ii < nx) & (jj > 0) & (jj < ny) & (kk > 0) & (kk < nz))
+        r = uniform01(seed, 3 * n_nodes, stream=1).reshape(n_nodes, 3)
+        d = (2.0 * r - 1.0) * jitter * np.array([hx, hy, hz])
+        X[interior] += d[interior]
+    ci, cj, ck = np.meshgrid(np.arange(nx), np.arange(ny), np.arange(nz), indexing="ij")
+    ci, cj, ck = (a.transpose(2, 1, 0).ravel() for a in (ci, cj, ck))
+
+    def nid(i, j, k):
+        return i + NX * (j + NY * k)
+
+    corner = [(0, 0, 0), (1, 0, 0), (1, 1, 0), (0, 1, 0), (0, 0, 1), (1, 0, 1), (1, 1, 1), (0, 1, 1)]
+    hexes = np.stack([nid(ci + a, cj + b, ck + c) for a, b, c in corner], axis=1)
+    quads, qvec = [], []
+    for j, sgn in ((ny, 1.0), (0, -1.0)):
+        fi, fk = np.meshgrid(np.arange(nx), np.arange(nz), indexing="ij")
+        fi, fk = fi.ravel(), fk.ravel()
+        quads.append(np.stack([nid(fi, j, fk), nid(fi + 1, j, fk), nid(fi + 1, j, fk + 1), nid(fi, j, fk + 1)], axis=1))
+        qvec.append(np.tile([0.0, sgn * traction, 0.0], (fi.size, 1)))
+    T = hexes.shape[0]
+    Ev = lognormal(seed, T, E, E_cov, stream=2) if E_cov > 0 else np.full(T, float(E))
+    return HexWorkload(name=name or f"hex_block_{nx}x{ny}x{nz}", X=X, hexes=hexes.astype(np.int32),
+                       tquads=np.concatenate(quads).astype(np.int32), tvec=np.concatenate(qvec), E=Ev,
+                       nu=float(nu), rho=float(rho), shape=(nx, ny, nz),
+                       params=dict(Lx=Lx, Ly=Ly, Lz=Lz, traction=traction, jitter=jitter, E_mean=E, E_cov=E_cov,
+                                   seed=seed))
+
+
+# ---------------------------------------------------------------------------
 # Named workloads: the pre-notched block at three resolutions.
 # ---------------------------------------------------------------------------
 
