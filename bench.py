@@ -104,6 +104,8 @@ def _args():
                    help="steps of the gradient (adjoint) sub-run on the 102,000-element block; 0 skips it")
     p.add_argument("--ensemble-steps", type=int, default=200,
                    help="steps of the ensemble sub-run in the default (block) mode; 0 skips it")
+    p.add_argument("--hex-steps", type=int, default=1000,
+                   help="steps of the hexahedral (ES-H-FEM) sub-run on 200x80x10 hexahedra; 0 skips it")
     p.add_argument("--no-compare", action="store_true", help="skip the second-precision run and agreement check")
     p.add_argument("--no-autotune", action="store_true", help="keep the default launch variants")
     p.add_argument("--split-capacity", type=int, default=0,
@@ -404,6 +406,30 @@ def run_cem(a):
                "note": "wall time of one cem_adjoint call: forward, segment recompute and reverse sweep"}
         del wa
 
+    # the ES-H-FEM step on the same block as 160,000 trilinear hexahedra (fixed topology)
+    hexres = None
+    if a.workload == "block" and a.hex_steps > 0:
+        from cem_inputs import hex_block
+        wh = hex_block(200, 80, 10, 0.1, 0.04, 0.01, traction=1e6, name="hex_block_200x80x10")
+        hexres = {"workload": wh.name, "elements": wh.n_elems, "steps": a.hex_steps, "warmup": a.warmup}
+        for prec in ("mixed", "fp64"):
+            sh = CEM.from_hex_workload(wh, device=dev, precision=prec)
+            sh.step(a.warmup)
+            barrier()
+            sh.profile(max(1, min(PROFILE_EVERY, a.hex_steps // 4)))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            sh.step(a.hex_steps)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            t_ms = e0.elapsed_time(e1)
+            prof, _ = sh.profile_read()
+            hexres[prec] = {"value": wh.n_elems * a.hex_steps / (t_ms * 1e-3), "unit": "hex-steps/s",
+                            "ms_per_step": t_ms / a.hex_steps,
+                            "per_launch_us": {k: 1e3 * v[0] / v[1] for k, v in prof.items() if v[1]}}
+            sh.close()
+        del wh
+
     # end to end through the public API with host buffers: create + material + K steps + read back
     barrier()
     t0 = time.perf_counter()
@@ -465,6 +491,8 @@ def run_cem(a):
         line["ensemble"] = ens
     if adj is not None:
         line["adjoint"] = adj
+    if hexres is not None:
+        line["hexahedra"] = hexres
     if a.workload == "ensemble":
         line["config"]["workload"] = w.name
         line["config"]["instances"] = w.params["n_instances"]

@@ -67,6 +67,12 @@ extern "C" {
 #define CEM_PATTERN_I  1    /* quadrilateral G1 G2 G4 G3: two nodes on each side      */
 #define CEM_PATTERN_II 2    /* triangle G1 G2 G6: one node cut off                    */
 
+/* element type (cem_mesh_desc.elem_type) */
+#define CEM_ELEM_TET4 0         /* linear tetrahedra, ES-T-FEM (Sec. 2.2); the crack path */
+#define CEM_ELEM_HEX8 1         /* trilinear hexahedra, ES-H-FEM (Sec. 2.2), fixed       */
+                                /* topology (no crack patterns: those of Sec. 3 for      */
+                                /* hexahedra are defined only by figures)                */
+
 /* split rule (cem_mesh_desc.split_mode) */
 #define CEM_SPLIT_SUBDIVIDE  0  /* the split element is replaced by sub-tetrahedra on    */
                                 /* both sides of its crack (its remainder keeps working) */
@@ -90,8 +96,8 @@ typedef struct cem_mesh_desc {
     int64_t        n_tets;       /* T > 0                                              */
     const double*  X;            /* N x 3 row-major reference coordinates [m]          */
     const int32_t* tets;         /* T x 4 node ids of linear tetrahedra                */
-    int64_t        n_tfaces;     /* F >= 0 traction triangles                          */
-    const int32_t* tfaces;       /* F x 3 node ids                                     */
+    int64_t        n_tfaces;     /* F >= 0 traction faces                              */
+    const int32_t* tfaces;       /* F x tface_nodes node ids                           */
     const double*  tvec;         /* F x 3 traction vector of each face [Pa]; the load  */
                                  /* t*A/3 goes to each face node (Sec. 2.2, Eq. 12)    */
     int64_t        n_notch;      /* K >= 0 pre-split (notch) elements                  */
@@ -129,6 +135,17 @@ typedef struct cem_mesh_desc {
     const uint8_t* dir_comp;     /* D components in {0, 1, 2}                          */
     const double*  dir_v0;       /* D final velocities [m/s]                           */
     double         dir_t0;       /* ramp time t0 [s]; <= 0: v = v0 from t = 0          */
+    int32_t        elem_type;    /* CEM_ELEM_TET4 (0) or CEM_ELEM_HEX8.  HEX8: `tets`   */
+                                 /* holds n_tets x 8 node ids (local order: the face   */
+                                 /* z- counter-clockwise seen from z+, then the face   */
+                                 /* z+ in the same order; positive volume required),   */
+                                 /* split_enabled and n_notch must be 0, one specimen. */
+                                 /* Smoothing domains take 1/12 of each hexahedron of  */
+                                 /* an edge's fan; element strains are sampled at the  */
+                                 /* edge midpoints with mean-corrected gradients.      */
+    int32_t        tface_nodes;  /* nodes per traction face: 3 (or 0: triangles, load  */
+                                 /* t A / 3 per node) or 4 (bilinear quadrilaterals,   */
+                                 /* load t * integral of N_a dA)                       */
 } cem_mesh_desc;
 
 typedef struct cem_ctx cem_ctx;

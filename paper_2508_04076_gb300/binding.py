@@ -46,6 +46,7 @@ class MeshDesc(C.Structure):
         ("split_mode", C.c_int32), ("g_variant", C.c_int32),
         ("n_dirichlet", C.c_int64), ("dir_node", C.POINTER(C.c_int32)), ("dir_comp", C.POINTER(C.c_uint8)),
         ("dir_v0", C.POINTER(C.c_double)), ("dir_t0", C.c_double),
+        ("elem_type", C.c_int32), ("tface_nodes", C.c_int32),
     ]
 
 
@@ -131,9 +132,11 @@ class CEM:
     def __init__(self, X, tets, tfaces=None, tvec=None, notch_tet=None, notch_side=None, *,
                  dt=0.0, cfl_factor=0.5, split_enabled=True, split_capacity=0, device=0,
                  stream=None, torch_allocator=True, precision="fp64", tet_instance=None,
-                 split_mode="subdivide", g_variant="principal", dirichlet=None):
+                 split_mode="subdivide", g_variant="principal", dirichlet=None, elem="tet"):
         """dirichlet: None or (nodes, comps, v0, t0), prescribed velocity components
-        v(t) = min(t / t0, 1) v0 (see cem_mesh_desc)."""
+        v(t) = min(t / t0, 1) v0 (see cem_mesh_desc).  elem: "tet" (linear tetrahedra,
+        traction triangles) or "hex" (trilinear hexahedra passed as `tets` with 8 nodes
+        each, traction quadrilaterals; fixed topology)."""
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("the CEM library needs a CUDA GPU; no CPU fallback exists")
@@ -143,9 +146,12 @@ class CEM:
         if stream is None:
             stream = torch.cuda.current_stream(self.device).cuda_stream
         self.stream = int(stream)
+        if elem not in ("tet", "hex"):
+            raise ValueError("elem must be 'tet' or 'hex'")
+        npe, nf = (4, 3) if elem == "tet" else (8, 4)
         X = np.ascontiguousarray(X, dtype=np.float64).reshape(-1, 3)
-        tets = np.ascontiguousarray(tets, dtype=np.int32).reshape(-1, 4)
-        tfaces = np.ascontiguousarray(np.zeros((0, 3)) if tfaces is None else tfaces, dtype=np.int32).reshape(-1, 3)
+        tets = np.ascontiguousarray(tets, dtype=np.int32).reshape(-1, npe)
+        tfaces = np.ascontiguousarray(np.zeros((0, nf)) if tfaces is None else tfaces, dtype=np.int32).reshape(-1, nf)
         tvec = np.ascontiguousarray(np.zeros((0, 3)) if tvec is None else tvec, dtype=np.float64).reshape(-1, 3)
         notch_tet = np.ascontiguousarray([] if notch_tet is None else notch_tet, dtype=np.int32).ravel()
         notch_side = np.ascontiguousarray([] if notch_side is None else notch_side, dtype=np.uint8).ravel()
@@ -166,6 +172,8 @@ class CEM:
         d.n_nodes, d.n_tets = X.shape[0], tets.shape[0]
         d.X, d.tets = _ptr(X, C.c_double), _ptr(tets, C.c_int32)
         d.n_tfaces, d.tfaces, d.tvec = tfaces.shape[0], _ptr(tfaces, C.c_int32), _ptr(tvec, C.c_double)
+        d.elem_type, d.tface_nodes = (0, 3) if elem == "tet" else (1, 4)
+        self.elem = elem
         d.n_notch, d.notch_tet, d.notch_side = notch_tet.size, _ptr(notch_tet, C.c_int32), _ptr(notch_side, C.c_uint8)
         if precision not in ("fp64", "mixed"):
             raise ValueError("precision must be 'fp64' or 'mixed'")
@@ -205,6 +213,14 @@ class CEM:
         if rc != CEM_OK:
             raise CEMError(rc, self._lib.cem_last_error(None).decode())
         self._ctx = ctx
+
+    @classmethod
+    def from_hex_workload(cls, w, **kw):
+        """Context for a cem_inputs.HexWorkload (fixed topology) with its material set."""
+        kw.setdefault("split_enabled", False)
+        sim = cls(w.X, w.hexes, w.tquads, w.tvec, None, None, elem="hex", **kw)
+        sim.set_material(w.rho, w.nu, w.E, np.array([1.0]))
+        return sim
 
     @classmethod
     def from_workload(cls, w, **kw):

@@ -60,6 +60,7 @@ extern "C" int cem_adjoint(cem_ctx* c, int64_t n_steps, int64_t checkpoint_every
     if (c->split_enabled) return cem_fail(c, CEM_ESTATE, "the adjoint needs a fixed topology (split_enabled = 0)");
     if (c->n_inst > 1) return cem_fail(c, CEM_ESTATE, "the adjoint takes one specimen, not an ensemble");
     if (c->n_dir > 0) return cem_fail(c, CEM_ESTATE, "the adjoint does not take prescribed velocities");
+    if (c->elem_type != CEM_ELEM_TET4) return cem_fail(c, CEM_ESTATE, "the adjoint covers tetrahedral meshes");
     CEM_CK(c, cudaSetDevice(c->device));
     const int64_t C = checkpoint_every > 0 ? checkpoint_every
                                            : std::max<int64_t>(1, (int64_t)std::ceil(std::sqrt((double)n_steps)));

@@ -166,6 +166,240 @@ int sync_counts(cem_ctx* c) {
     return CEM_OK;
 }
 
+// Traction load on the host: triangles give t A / 3 to each node (Eq. 12);
+// bilinear quadrilaterals give t * int N_a dA (2x2 Gauss).  Faces in order.
+int traction_loads(cem_ctx* c, const cem_mesh_desc* d, int64_t N0, std::vector<double>& f) {
+    const int nf = d->tface_nodes == 4 ? 4 : 3;
+    f.assign(3 * N0, 0.0);
+    const double g = 1.0 / std::sqrt(3.0);
+    for (int64_t q = 0; q < d->n_tfaces; ++q) {
+        const int* fn = d->tfaces + (int64_t)nf * q;
+        for (int k = 0; k < nf; ++k)
+            if (fn[k] < 0 || fn[k] >= N0) return cem_fail(c, CEM_EINVAL, "traction face node id out of range");
+        const double* t = d->tvec + 3 * q;
+        if (nf == 3) {
+            const double* P = d->X + 3 * fn[0];
+            const double* Q = d->X + 3 * fn[1];
+            const double* R = d->X + 3 * fn[2];
+            const double a[3] = {Q[0] - P[0], Q[1] - P[1], Q[2] - P[2]};
+            const double b[3] = {R[0] - P[0], R[1] - P[1], R[2] - P[2]};
+            const double cr[3] = {a[1] * b[2] - a[2] * b[1], a[2] * b[0] - a[0] * b[2], a[0] * b[1] - a[1] * b[0]};
+            const double A = 0.5 * std::sqrt(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]);
+            for (int k = 0; k < 3; ++k)
+                for (int r = 0; r < 3; ++r) f[k * N0 + fn[r]] += t[k] * A / 3.0;
+        } else {
+            const double sa[4] = {-1, 1, 1, -1}, ea[4] = {-1, -1, 1, 1};
+            double w[4] = {0, 0, 0, 0};   // int N_a dA
+            for (int gp = 0; gp < 4; ++gp) {
+                const double s_ = (gp & 1) ? g : -g, r_ = (gp & 2) ? g : -g;
+                double xs[3] = {0, 0, 0}, xr[3] = {0, 0, 0};
+                for (int a = 0; a < 4; ++a)
+                    for (int k = 0; k < 3; ++k) {
+                        xs[k] += sa[a] * (1 + ea[a] * r_) / 4.0 * d->X[3 * fn[a] + k];
+                        xr[k] += ea[a] * (1 + sa[a] * s_) / 4.0 * d->X[3 * fn[a] + k];
+                    }
+                const double cx = xs[1] * xr[2] - xs[2] * xr[1], cy = xs[2] * xr[0] - xs[0] * xr[2],
+                             cz = xs[0] * xr[1] - xs[1] * xr[0];
+                const double dA = std::sqrt(cx * cx + cy * cy + cz * cz);
+                for (int a = 0; a < 4; ++a) w[a] += (1 + sa[a] * s_) * (1 + ea[a] * r_) / 4.0 * dA;
+            }
+            for (int k = 0; k < 3; ++k)
+                for (int a = 0; a < 4; ++a) f[k * N0 + fn[a]] += t[k] * w[a];
+        }
+    }
+    return CEM_OK;
+}
+
+// Hexahedral mesh (fixed topology): host topology from the 12 local edges,
+// device arrays, geometry, load.  No notch, no splitting, one specimen.
+const int HEX_LE[12][2] = {{0, 1}, {1, 2}, {2, 3}, {3, 0}, {4, 5}, {5, 6}, {6, 7}, {7, 4}, {0, 4}, {1, 5}, {2, 6}, {3, 7}};
+
+int create_hex_impl(const cem_mesh_desc* d, cem_ctx* c) {
+    if (d->split_enabled || d->n_notch > 0)
+        return cem_fail(c, CEM_EINVAL, "hexahedral meshes run with a fixed topology: split_enabled and n_notch must be 0");
+    if (d->n_instances > 1) return cem_fail(c, CEM_EINVAL, "hexahedral meshes take one specimen");
+    const int64_t N0 = d->n_nodes, T0 = d->n_tets;
+    if (T0 >= (1ll << 26)) return cem_fail(c, CEM_EINVAL, "too many hexahedra for 32-bit entry ids");
+    c->N0 = N0;
+    c->T0 = T0;
+    c->elem_type = CEM_ELEM_HEX8;
+    c->npe = 8;
+    c->epe = 12;
+    c->split_enabled = 0;
+    std::vector<int> conn(d->tets, d->tets + 8 * T0);
+    const double g = 1.0 / std::sqrt(3.0);
+    const double XI[8][3] = {{-1, -1, -1}, {1, -1, -1}, {1, 1, -1}, {-1, 1, -1},
+                             {-1, -1, 1},  {1, -1, 1},  {1, 1, 1},  {-1, 1, 1}};
+    for (int64_t t = 0; t < T0; ++t) {
+        const int* n = &conn[t * 8];
+        for (int a = 0; a < 8; ++a) {
+            if (n[a] < 0 || n[a] >= N0) return cem_fail(c, CEM_EINVAL, "element node id out of range");
+            for (int b = a + 1; b < 8; ++b)
+                if (n[a] == n[b]) return cem_fail(c, CEM_EINVAL, "element with a repeated node");
+        }
+        double V = 0.0;   // 2x2x2 Gauss of det J
+        for (int q = 0; q < 8; ++q) {
+            const double x = (q & 1) ? g : -g, y = (q & 2) ? g : -g, z = (q & 4) ? g : -g;
+            double J[3][3] = {};
+            for (int i = 0; i < 8; ++i) {
+                const double a = XI[i][0], b = XI[i][1], cc = XI[i][2];
+                const double gr[3] = {a * (1 + b * y) * (1 + cc * z) / 8, b * (1 + a * x) * (1 + cc * z) / 8,
+                                      cc * (1 + a * x) * (1 + b * y) / 8};
+                for (int r = 0; r < 3; ++r)
+                    for (int k = 0; k < 3; ++k) J[r][k] += d->X[3 * n[i] + r] * gr[k];
+            }
+            V += J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) - J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+                 J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+        }
+        if (!(V > 0.0) || !std::isfinite(V)) return cem_fail(c, CEM_EINVAL, "hexahedron without positive volume");
+    }
+    // topology: incidence (entries 8 t + l), edges from the 12 local edges, fans (entries 12 t + l)
+    std::vector<int> inc_off(N0 + 1, 0), inc(8 * T0);
+    for (int64_t t = 0; t < T0; ++t)
+        for (int l = 0; l < 8; ++l) inc_off[conn[t * 8 + l] + 1]++;
+    for (int64_t i = 0; i < N0; ++i) inc_off[i + 1] += inc_off[i];
+    {
+        std::vector<int> cur(inc_off.begin(), inc_off.end() - 1);
+        for (int64_t t = 0; t < T0; ++t)
+            for (int l = 0; l < 8; ++l) inc[cur[conn[t * 8 + l]]++] = (int)(t * 8 + l);
+    }
+    std::vector<std::pair<long long, int>> pk(12 * T0);   // (edge key, fan entry)
+    for (int64_t t = 0; t < T0; ++t)
+        for (int l = 0; l < 12; ++l) {
+            long long x = conn[t * 8 + HEX_LE[l][0]], y = conn[t * 8 + HEX_LE[l][1]];
+            if (x > y) std::swap(x, y);
+            pk[t * 12 + l] = {x * N0 + y, (int)(t * 12 + l)};
+        }
+    std::sort(pk.begin(), pk.end());
+    std::vector<int> t2e(12 * T0), fan(12 * T0), fan_off;
+    int64_t E0 = 0;
+    for (size_t q = 0; q < pk.size(); ++q) {
+        if (q == 0 || pk[q].first != pk[q - 1].first) {
+            fan_off.push_back((int)q);
+            ++E0;
+        }
+        const int ent = pk[q].second;
+        t2e[(ent % 12) * T0 + ent / 12] = (int)(E0 - 1);
+        fan[q] = ent;
+    }
+    fan_off.push_back((int)pk.size());
+    c->E0 = E0;
+    c->max_inc0 = 0;
+    for (int64_t i = 0; i < N0; ++i) c->max_inc0 = std::max<int64_t>(c->max_inc0, inc_off[i + 1] - inc_off[i]);
+    c->max_fan0 = 0;
+    for (int64_t e = 0; e < E0; ++e) c->max_fan0 = std::max<int64_t>(c->max_fan0, fan_off[e + 1] - fan_off[e]);
+    std::vector<double> fload;
+    if (int rc = traction_loads(c, d, N0, fload)) return rc;
+
+    c->S_cap = 0;
+    c->Tc = T0;
+    c->Nc = N0;
+    c->Ec = E0;
+    c->fan_cap = 12 * T0;
+    c->inc_cap = 8 * T0;
+    if (int rc = select_device(c)) return rc;
+    const int64_t Nc = c->Nc, Tc = c->Tc, Ec = c->Ec, HGV = cem_hex_geometry_values();
+    const bool mixed = c->precision == CEM_MIXED;
+    bool ok = true;
+    ok = ok && dalloc(c, c->X, 3 * Nc) && dalloc(c, c->u, 3 * Nc) && dalloc(c, c->v, 3 * Nc) && dalloc(c, c->a, 3 * Nc);
+    ok = ok && dalloc(c, c->fext, 3 * Nc) && dalloc(c, c->mass, Nc) && dalloc(c, c->minv, Nc);
+    ok = ok && dalloc(c, c->inc_off, Nc) && dalloc(c, c->inc_cnt, Nc) && dalloc(c, c->inc_pool, c->inc_cap);
+    ok = ok && dalloc(c, c->conn, 8 * Tc) && dalloc(c, c->t2e, 12 * Tc) && dalloc(c, c->anc, Tc);
+    ok = ok && dalloc(c, c->active, Tc) && dalloc(c, c->Vg, HGV * Tc) && dalloc(c, c->vol, Tc);
+    ok = ok && dalloc(c, c->lam, Tc) && dalloc(c, c->mu, Tc) && dalloc(c, c->Gc, Tc);
+    if (mixed)
+        ok = ok && dalloc(c, c->Vg32, HGV * Tc) && dalloc(c, c->h32, 8 * 12 * Tc) && dalloc(c, c->fp32, 32 * Tc) &&
+             dalloc(c, c->uhl, 8 * Nc) && dalloc(c, c->cl32, Ec) && dalloc(c, c->cm32, Ec) && dalloc(c, c->sig32, 8 * Ec);
+    else
+        ok = ok && dalloc(c, c->h, 6 * 12 * Tc) && dalloc(c, c->fp, 24 * Tc) && dalloc(c, c->sig, 6 * Ec);
+    ok = ok && dalloc(c, c->fan_off, Ec) && dalloc(c, c->fan_cnt, Ec) && dalloc(c, c->fan_pool, c->fan_cap);
+    ok = ok && dalloc(c, c->cl, Ec) && dalloc(c, c->cm, Ec) && dalloc(c, c->sumV, Ec);
+    ok = ok && dalloc(c, c->Ud, 1) && dalloc(c, c->dec_G, T0) && dalloc(c, c->ud_part, T0);
+    ok = ok && dalloc(c, c->red_part, cem_reduction_doubles()) && dalloc(c, c->red_out, 8);
+    ok = ok && dalloc(c, c->dcount, CNT_COUNT);
+    if (c->n_dir > 0) ok = ok && dalloc(c, c->dir_key, c->n_dir) && dalloc(c, c->dir_v0, c->n_dir);
+    if (!ok) return cem_fail(c, CEM_ENOMEM, "device allocation failed");
+    CEM_CK(c, cudaMallocHost((void**)&c->hcount, CNT_COUNT * sizeof(long long)));
+    CEM_CK(c, cudaMallocHost((void**)&c->hred, 8 * sizeof(double)));
+    cudaStream_t s = c->stream;
+    for (double* p : {c->u, c->v, c->a}) CEM_CK(c, cudaMemsetAsync(p, 0, 3 * Nc * sizeof(double), s));
+    CEM_CK(c, cudaMemsetAsync(c->Ud, 0, sizeof(double), s));
+    CEM_CK(c, cudaMemsetAsync(c->dcount, 0, CNT_COUNT * sizeof(long long), s));
+    CEM_CK(c, cudaMemsetAsync(c->active, 1, Tc, s));
+    if (mixed) CEM_CK(c, cudaMemsetAsync(c->uhl, 0, 8 * Nc * sizeof(float), s));
+    {
+        std::vector<double> Xs(3 * N0);
+        for (int64_t i = 0; i < N0; ++i)
+            for (int k = 0; k < 3; ++k) Xs[k * N0 + i] = d->X[3 * i + k];
+        for (int k = 0; k < 3; ++k)
+            if (int rc = upload(c, c->X + k * Nc, Xs.data() + k * N0, N0)) return rc;
+        std::vector<int> cs(8 * T0);
+        for (int64_t t = 0; t < T0; ++t)
+            for (int l = 0; l < 8; ++l) cs[l * T0 + t] = conn[t * 8 + l];
+        if (int rc = upload(c, c->conn, cs.data(), 8 * T0)) return rc;
+        if (int rc = upload(c, c->t2e, t2e.data(), 12 * T0)) return rc;
+        std::vector<int> anc(T0);
+        std::iota(anc.begin(), anc.end(), 0);
+        if (int rc = upload(c, c->anc, anc.data(), T0)) return rc;
+        std::vector<int> fo(E0), fc(E0), io(N0), ic(N0);
+        for (int64_t e = 0; e < E0; ++e) {
+            fo[e] = fan_off[e];
+            fc[e] = fan_off[e + 1] - fan_off[e];
+        }
+        for (int64_t i = 0; i < N0; ++i) {
+            io[i] = inc_off[i];
+            ic[i] = inc_off[i + 1] - inc_off[i];
+        }
+        if (int rc = upload(c, c->fan_off, fo.data(), E0)) return rc;
+        if (int rc = upload(c, c->fan_cnt, fc.data(), E0)) return rc;
+        if (int rc = upload(c, c->fan_pool, fan.data(), 12 * T0)) return rc;
+        if (int rc = upload(c, c->inc_off, io.data(), N0)) return rc;
+        if (int rc = upload(c, c->inc_cnt, ic.data(), N0)) return rc;
+        if (int rc = upload(c, c->inc_pool, inc.data(), 8 * T0)) return rc;
+        for (int k = 0; k < 3; ++k)
+            if (int rc = upload(c, c->fext + k * Nc, fload.data() + k * N0, N0)) return rc;
+        CEM_CK(c, cudaStreamSynchronize(s));
+    }
+    c->fan_top = 12 * T0;
+    c->inc_top = 8 * T0;
+    c->N = N0;
+    c->T = T0;
+    c->E = E0;
+    c->n_active = T0;
+    if (c->n_dir > 0) {
+        if (int rc = upload(c, c->dir_key, c->h_dir_key.data(), c->n_dir)) return rc;
+        if (int rc = upload(c, c->dir_v0, c->h_dir_v0.data(), c->n_dir)) return rc;
+    }
+    if (int rc = cem_hex_geometry(c, c->dec_G)) return rc;
+    std::vector<double> hm(T0);
+    CEM_CK(c, cudaMemcpyAsync(hm.data(), c->dec_G, T0 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CEM_CK(c, cudaStreamSynchronize(s));
+    c->h_min = *std::min_element(hm.begin(), hm.end());
+    c->inst_hmin.assign(1, c->h_min);
+    return CEM_OK;
+}
+
+// Prescribed velocity components, keyed 4 * node + component (distinct), kept on the host until upload.
+int parse_dirichlet(cem_ctx* c, const cem_mesh_desc* d) {
+    const int64_t N0 = d->n_nodes;
+    c->h_dir_key.assign(d->n_dirichlet, 0);
+    c->h_dir_v0.assign(d->n_dirichlet, 0.0);
+    for (int64_t q = 0; q < d->n_dirichlet; ++q) {
+        const int i = d->dir_node[q], k = d->dir_comp[q];
+        if (i < 0 || i >= N0 || k > 2) return cem_fail(c, CEM_EINVAL, "prescribed node or component out of range");
+        if (!std::isfinite(d->dir_v0[q])) return cem_fail(c, CEM_EINVAL, "prescribed velocity must be finite");
+        c->h_dir_key[q] = 4 * i + k;
+        c->h_dir_v0[q] = d->dir_v0[q];
+    }
+    std::vector<int> sorted_keys(c->h_dir_key);
+    std::sort(sorted_keys.begin(), sorted_keys.end());
+    if (std::adjacent_find(sorted_keys.begin(), sorted_keys.end()) != sorted_keys.end())
+        return cem_fail(c, CEM_EINVAL, "a node component is prescribed twice");
+    c->n_dir = d->n_dirichlet;
+    c->dir_t0 = d->dir_t0;
+    return CEM_OK;
+}
+
 int create_impl(const cem_mesh_desc* d, cem_ctx* c) {
     if (!d || d->n_nodes <= 0 || d->n_tets <= 0 || !d->X || !d->tets)
         return cem_fail(c, CEM_EINVAL, "n_nodes, n_tets, X and tets are required");
@@ -196,6 +430,11 @@ int create_impl(const cem_mesh_desc* d, cem_ctx* c) {
     c->g_variant = d->g_variant;
     c->precision = d->precision;
     for (int k = 0; k < TUNE_COUNT; ++k) c->tune[k] = cem_tune_default(k, c->precision);
+    if (d->tface_nodes != 0 && d->tface_nodes != 3 && d->tface_nodes != 4)
+        return cem_fail(c, CEM_EINVAL, "tface_nodes must be 3 or 4");
+    if (int rc = parse_dirichlet(c, d)) return rc;
+    if (d->elem_type == CEM_ELEM_HEX8) return create_hex_impl(d, c);
+    if (d->elem_type != CEM_ELEM_TET4) return cem_fail(c, CEM_EINVAL, "elem_type must be CEM_ELEM_TET4 or CEM_ELEM_HEX8");
 
     const int64_t N0 = d->n_nodes, T0 = d->n_tets;
     c->N0 = N0;
@@ -246,25 +485,6 @@ int create_impl(const cem_mesh_desc* d, cem_ctx* c) {
     HostTopo H;
     if (int rc = build_topology(c, conn, H)) return rc;
     const int64_t E0 = c->E0;
-
-    // prescribed velocity components, keyed 4 * node + component (distinct)
-    std::vector<int> dir_key(d->n_dirichlet);
-    std::vector<double> dir_v0(d->n_dirichlet);
-    for (int64_t q = 0; q < d->n_dirichlet; ++q) {
-        const int i = d->dir_node[q], k = d->dir_comp[q];
-        if (i < 0 || i >= N0 || k > 2) return cem_fail(c, CEM_EINVAL, "prescribed node or component out of range");
-        if (!std::isfinite(d->dir_v0[q])) return cem_fail(c, CEM_EINVAL, "prescribed velocity must be finite");
-        dir_key[q] = 4 * i + k;
-        dir_v0[q] = d->dir_v0[q];
-    }
-    {
-        std::vector<int> sorted_keys(dir_key);
-        std::sort(sorted_keys.begin(), sorted_keys.end());
-        if (std::adjacent_find(sorted_keys.begin(), sorted_keys.end()) != sorted_keys.end())
-            return cem_fail(c, CEM_EINVAL, "a node component is prescribed twice");
-    }
-    c->n_dir = d->n_dirichlet;
-    c->dir_t0 = d->dir_t0;
 
     // notch list: validated, oriented, side masks normalised (local node 0 on side 0), ascending
     std::vector<std::pair<int, int>> notch;
@@ -453,29 +673,16 @@ int create_impl(const cem_mesh_desc* d, cem_ctx* c) {
         c->inc_top = (int64_t)H.inc.size();
         CEM_CK(c, cudaStreamSynchronize(s));
     }
-    {   // traction load, Eq. 12: t * A / 3 to each face node, in face order
-        std::vector<double> f(3 * N0, 0.0);
-        for (int64_t q = 0; q < d->n_tfaces; ++q) {
-            const int* fn = d->tfaces + 3 * q;
-            for (int k = 0; k < 3; ++k)
-                if (fn[k] < 0 || fn[k] >= N0) return cem_fail(c, CEM_EINVAL, "traction face node id out of range");
-            const double* P = d->X + 3 * fn[0];
-            const double* Q = d->X + 3 * fn[1];
-            const double* R = d->X + 3 * fn[2];
-            const double a[3] = {Q[0] - P[0], Q[1] - P[1], Q[2] - P[2]};
-            const double b[3] = {R[0] - P[0], R[1] - P[1], R[2] - P[2]};
-            const double cr[3] = {a[1] * b[2] - a[2] * b[1], a[2] * b[0] - a[0] * b[2], a[0] * b[1] - a[1] * b[0]};
-            const double A = 0.5 * std::sqrt(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]);
-            for (int k = 0; k < 3; ++k)
-                for (int r = 0; r < 3; ++r) f[k * N0 + fn[r]] += d->tvec[3 * q + k] * A / 3.0;
-        }
+    {   // traction load (Eq. 12)
+        std::vector<double> f;
+        if (int rc = traction_loads(c, d, N0, f)) return rc;
         for (int k = 0; k < 3; ++k)
             if (int rc = upload(c, c->fext + k * Nc, f.data() + k * N0, N0)) return rc;
         CEM_CK(c, cudaStreamSynchronize(s));
     }
     if (c->n_dir > 0) {
-        if (int rc = upload(c, c->dir_key, dir_key.data(), c->n_dir)) return rc;
-        if (int rc = upload(c, c->dir_v0, dir_v0.data(), c->n_dir)) return rc;
+        if (int rc = upload(c, c->dir_key, c->h_dir_key.data(), c->n_dir)) return rc;
+        if (int rc = upload(c, c->dir_v0, c->h_dir_v0.data(), c->n_dir)) return rc;
         CEM_CK(c, cudaStreamSynchronize(s));
     }
     c->N = N0;
@@ -763,6 +970,10 @@ int cem_energy_instance(cem_ctx* c, int64_t instance, cem_energy_t* out) {
 int cem_crack_state(cem_ctx* c, int64_t* n_split, int32_t* tet, int8_t* pattern, uint8_t* side, int64_t* step,
                     double* G, int64_t cap) {
     if (!c || !n_split) return CEM_EINVAL;
+    if (c->elem_type != CEM_ELEM_TET4) {   // hexahedral meshes never split
+        *n_split = 0;
+        return CEM_OK;
+    }
     if (int rc = select_device(c)) return rc;
     const int64_t T0 = c->T0;
     std::vector<uint8_t> sd(T0);

@@ -98,6 +98,9 @@ struct cem_ctx {
     bool material = false;
     int64_t step = 0;
     int split_enabled = 1;
+    int elem_type = CEM_ELEM_TET4;
+    int npe = 4;                // nodes per element
+    int epe = 6;                // edges per element (smoothing-volume share 1 / epe, Eq. 9)
     int split_mode = CEM_SPLIT_SUBDIVIDE;
     int g_variant = CEM_G_PRINCIPAL;
     int precision = CEM_FP64;
@@ -133,6 +136,8 @@ struct cem_ctx {
     int* dir_key = nullptr;
     double* dir_v0 = nullptr;
     double dir_t0 = 0.0;
+    std::vector<int> h_dir_key;         // host copies until upload
+    std::vector<double> h_dir_v0;
     // cracks
     int* face_nbr = nullptr;
     uint8_t* side = nullptr;
@@ -266,6 +271,14 @@ void cem_tune_describe(int kernel, int v, int* block, int* batch);
 int cem_tune_default(int kernel, int precision);
 int cem_launch_tune_variant(cem_ctx* c, int kernel, int v);
 int cem_tune_maybe(cem_ctx* c);   // re-tune kernels whose size bucket changed (automatic mode)
+
+// ---------------------------------------------------------------- hexahedra (cem_hex.cu)
+// conn [8][Tc], t2e [12][Tc], Vg / Vg32 hold 132 geometry values per element,
+// h records per (element, local edge) at index 12 j + l, fp 8 nodal shares per element.
+int cem_hex_geometry(cem_ctx* c, double* hbuf);
+int cem_hex_strain(cem_ctx* c, const double* u, const float* uhl, void* hout);
+int cem_hex_force(cem_ctx* c);
+int64_t cem_hex_geometry_values();
 
 // ---------------------------------------------------------------- crack path (cem_crack.cu)
 int cem_launch_front_G(cem_ctx* c);

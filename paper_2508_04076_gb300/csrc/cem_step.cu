@@ -348,7 +348,7 @@ __global__ void __launch_bounds__(TB) k_node_update(const R* __restrict__ fp, co
                                                     const double* __restrict__ fext, const double* __restrict__ minv,
                                                     double* __restrict__ v, double* __restrict__ a, int64_t Nc,
                                                     int64_t N, double hdt, int first, const double* __restrict__ dtn,
-                                                    double* __restrict__ u, float* __restrict__ uhl) {
+                                                    double* __restrict__ u, float* __restrict__ uhl, double coef) {
     CEM_PDL_ENTRY();
     int64_t i = (int64_t)blockIdx.x * TB + threadIdx.x;
     if (i >= N) return;
@@ -366,7 +366,7 @@ __global__ void __launch_bounds__(TB) k_node_update(const R* __restrict__ fp, co
 #pragma unroll
             for (int b = 0; b < B; ++b)
                 if (ee[b] >= 0) {
-                    const double* p = fp + 12 * (int64_t)(ee[b] >> 2) + 3 * (ee[b] & 3);
+                    const double* p = fp + 3 * (int64_t)ee[b];   // entry = element * npe + local node
                     x[b][0] = p[0];
                     x[b][1] = p[1];
                     x[b][2] = p[2];
@@ -389,7 +389,7 @@ __global__ void __launch_bounds__(TB) k_node_update(const R* __restrict__ fp, co
             float4 x[B];
 #pragma unroll
             for (int b = 0; b < B; ++b)
-                if (ee[b] >= 0) x[b] = reinterpret_cast<const float4*>(fp)[4 * (int64_t)(ee[b] >> 2) + (ee[b] & 3)];
+                if (ee[b] >= 0) x[b] = reinterpret_cast<const float4*>(fp)[ee[b]];
 #pragma unroll
             for (int b = 0; b < B; ++b)
                 if (ee[b] >= 0) {
@@ -410,7 +410,7 @@ __global__ void __launch_bounds__(TB) k_node_update(const R* __restrict__ fp, co
     // and an add here depends on the code around it, which differs between the
     // launch variants; fixing the roundings keeps every variant bit-identical.
     const double mi = minv[i];
-    const double sixth = 1.0 / 6.0;
+    const double sixth = coef;   // 1 / (edges per element): the smoothing-volume share of Eq. 9
     const double dt = hdt + hdt, hdt2 = hdt * dt;
     double un[3];
 #pragma unroll
@@ -458,7 +458,7 @@ __global__ void __launch_bounds__(BS) k_edge_coeffs(const int* __restrict__ list
                                                     const double* __restrict__ lam, const double* __restrict__ mu,
                                                     double* __restrict__ cl, double* __restrict__ cm,
                                                     double* __restrict__ sumV, float* __restrict__ cl32,
-                                                    float* __restrict__ cm32) {
+                                                    float* __restrict__ cm32, int fan_div) {
     CEM_PDL_ENTRY();
     int64_t i = (int64_t)blockIdx.x * BS + threadIdx.x;
     if (i >= n) return;
@@ -466,7 +466,7 @@ __global__ void __launch_bounds__(BS) k_edge_coeffs(const int* __restrict__ list
     const int off = fan_off[k], cnt = fan_cnt[k];
     double sv = 0.0, sl = 0.0, sm = 0.0;
     for (int q = 0; q < cnt; ++q) {
-        const int j = fan_pool[off + q];
+        const int j = fan_pool[off + q] / fan_div;   // fan entry -> element
         const double V = vol[j];
         sv += V;
         sl += V * lam[j];
@@ -485,14 +485,16 @@ __global__ void __launch_bounds__(BS) k_edge_coeffs(const int* __restrict__ list
 __global__ void __launch_bounds__(BS) k_node_mass(const int* __restrict__ list, int64_t n,
                                                   const int* __restrict__ inc_off, const int* __restrict__ inc_cnt,
                                                   const int* __restrict__ inc_pool, const double* __restrict__ vol,
-                                                  double rho, double* __restrict__ mass, double* __restrict__ minv) {
+                                                  double rho, double* __restrict__ mass, double* __restrict__ minv,
+                                                  int npe) {
     CEM_PDL_ENTRY();
     int64_t i0 = (int64_t)blockIdx.x * BS + threadIdx.x;
     if (i0 >= n) return;
     const int i = list ? list[i0] : (int)i0;
     const int off = inc_off[i], cnt = inc_cnt[i];
+    const double share = 1.0 / npe;   // lumped mass: rho V / (nodes per element)
     double m = 0.0;
-    for (int q = 0; q < cnt; ++q) m += rho * vol[inc_pool[off + q] >> 2] * 0.25;
+    for (int q = 0; q < cnt; ++q) m += rho * vol[inc_pool[off + q] / npe] * share;
     mass[i] = m;
     minv[i] = m > 0.0 ? 1.0 / m : 0.0;
 }
@@ -554,7 +556,8 @@ __global__ void __launch_bounds__(RB) k_energy_nodes(const double* __restrict__ 
 template <class R>
 __global__ void __launch_bounds__(RB) k_energy_edges(const R* __restrict__ h, const int* __restrict__ fan_off,
                                                      const int* __restrict__ fan_cnt, const int* __restrict__ fan_pool,
-                                                     const R* __restrict__ sig, int64_t E, double* __restrict__ part) {
+                                                     const R* __restrict__ sig, int64_t E, double ecoef,
+                                                     double* __restrict__ part) {
     CEM_PDL_ENTRY();
     double x[1] = {0};
     for (int64_t k = (int64_t)blockIdx.x * RB + threadIdx.x; k < E; k += (int64_t)RG * RB) {
@@ -569,7 +572,7 @@ __global__ void __launch_bounds__(RB) k_energy_edges(const R* __restrict__ h, co
         Rec<R>::load6(sig + Rec<R>::S6 * k, s);
         double e = 0;
         for (int q = 0; q < 6; ++q) e += H[q] * (double)s[q];
-        x[0] += e * (1.0 / 12.0);   // 1/2 Vs eps.sigma = 1/2 (sumV/6) (H/sumV).sigma
+        x[0] += e * ecoef;   // 1/2 Vs eps.sigma = 1/2 (sumV/ne) (H/sumV).sigma, ecoef = 1 / (2 ne)
     }
     block_sum_store<1>(x, part + 3 * RG);
 }
@@ -608,7 +611,7 @@ __global__ void __launch_bounds__(RB) k_energy_edges_inst(const R* __restrict__ 
                                                           const int* __restrict__ fan_pool, const R* __restrict__ sig,
                                                           const int* __restrict__ anc,
                                                           const int* __restrict__ tet_inst, int inst, int64_t E,
-                                                          double* __restrict__ part) {
+                                                          double ecoef, double* __restrict__ part) {
     CEM_PDL_ENTRY();
     double x[1] = {0};
     for (int64_t k = (int64_t)blockIdx.x * RB + threadIdx.x; k < E; k += (int64_t)RG * RB) {
@@ -625,7 +628,7 @@ __global__ void __launch_bounds__(RB) k_energy_edges_inst(const R* __restrict__ 
         Rec<R>::load6(sig + Rec<R>::S6 * k, s);
         double e = 0;
         for (int q = 0; q < 6; ++q) e += H[q] * (double)s[q];
-        x[0] += e * (1.0 / 12.0);
+        x[0] += e * ecoef;
     }
     block_sum_store<1>(x, part + 3 * RG);
 }
@@ -730,7 +733,7 @@ template <class R, int TB, int NB>
 void go_node(cem_ctx* c, const R* fp, int first) {
     cem_pdl(c->stream, k_node_update<R, TB, NB>, cem_grid(c->N, TB), TB, fp, c->inc_off, c->inc_cnt, c->inc_pool,
             c->fext, c->minv, c->v, c->a, c->Nc, c->N, 0.5 * c->dt, first, c->dtn, c->u,
-            sizeof(R) == 4 ? c->uhl : nullptr);
+            sizeof(R) == 4 ? c->uhl : nullptr, 1.0 / c->epe);
 }
 template <class R, int NB>
 void go_node_tb(cem_ctx* c, int v, const R* fp, int first) {
@@ -1018,6 +1021,7 @@ int cem_launch_split_u(cem_ctx* c) {
 }
 
 int cem_launch_strain(cem_ctx* c) {
+    if (c->elem_type == CEM_ELEM_HEX8) return cem_hex_strain(c, c->u, c->uhl, mixed(c) ? (void*)c->h32 : (void*)c->h);
     if (mixed(c))
         launch_strain<float>(c, c->tune[TUNE_STRAIN], c->u, c->uhl, c->Vg32, c->h32);
     else
@@ -1038,6 +1042,7 @@ int cem_launch_edge_stress(cem_ctx* c) {
 }
 
 int cem_launch_force(cem_ctx* c) {
+    if (c->elem_type == CEM_ELEM_HEX8) return cem_hex_force(c);
     if (mixed(c))
         launch_force<float>(c, c->tune[TUNE_FORCE], c->sig32, c->Vg32, c->fp32);
     else
@@ -1115,7 +1120,8 @@ int cem_launch_edge_coeffs(cem_ctx* c, const int* list, int64_t n) {
     if (!list) n = c->E;
     if (n <= 0) return CEM_OK;
     cem_pdl(c->stream, k_edge_coeffs, cem_grid(n, BS), BS, list, n, c->fan_off, c->fan_cnt, c->fan_pool, c->vol, c->lam,
-                                                         c->mu, c->cl, c->cm, c->sumV, c->cl32, c->cm32);
+                                                         c->mu, c->cl, c->cm, c->sumV, c->cl32, c->cm32,
+                                                         c->elem_type == CEM_ELEM_HEX8 ? c->epe : 1);
     cem_launched(c);
     CEM_CK(c, cudaGetLastError());
     return CEM_OK;
@@ -1125,7 +1131,7 @@ int cem_launch_node_mass(cem_ctx* c, const int* list, int64_t n) {
     if (!list) n = c->N;
     if (n <= 0) return CEM_OK;
     cem_pdl(c->stream, k_node_mass, cem_grid(n, BS), BS, list, n, c->inc_off, c->inc_cnt, c->inc_pool, c->vol, c->rho,
-                                                       c->mass, c->minv);
+                                                       c->mass, c->minv, c->npe);
     cem_launched(c);
     CEM_CK(c, cudaGetLastError());
     return CEM_OK;
@@ -1144,10 +1150,10 @@ int cem_energy_reduce(cem_ctx* c, double out[4]) {
     cem_pdl(c->stream, k_energy_nodes, RG, RB, c->u, c->v, c->a, c->mass, c->fext, c->Nc, c->N, c->red_part);
     if (mixed(c))
         cem_pdl(c->stream, k_energy_edges<float>, RG, RB, c->h32, c->fan_off, c->fan_cnt, c->fan_pool, c->sig32, c->E,
-                                                        c->red_part);
+                                                        0.5 / c->epe, c->red_part);
     else
         cem_pdl(c->stream, k_energy_edges<double>, RG, RB, c->h, c->fan_off, c->fan_cnt, c->fan_pool, c->sig, c->E,
-                                                         c->red_part);
+                                                         0.5 / c->epe, c->red_part);
     cem_pdl(c->stream, k_reduce_final, 1, RB, c->red_part, 4, c->red_out);
     cem_launched(c, 3);
     CEM_CK(c, cudaGetLastError());
@@ -1163,10 +1169,12 @@ int cem_energy_reduce_instance(cem_ctx* c, int inst, double out[5]) {
                                                   c->red_part);
     if (mixed(c))
         cem_pdl(c->stream, k_energy_edges_inst<float>, RG, RB, c->h32, c->fan_off, c->fan_cnt, c->fan_pool, c->sig32,
-                                                             c->anc, c->tet_inst, inst, c->E, c->red_part);
+                                                             c->anc, c->tet_inst, inst, c->E, 0.5 / c->epe,
+                                                             c->red_part);
     else
         cem_pdl(c->stream, k_energy_edges_inst<double>, RG, RB, c->h, c->fan_off, c->fan_cnt, c->fan_pool, c->sig,
-                                                              c->anc, c->tet_inst, inst, c->E, c->red_part);
+                                                              c->anc, c->tet_inst, inst, c->E, 0.5 / c->epe,
+                                                              c->red_part);
     cem_pdl(c->stream, k_ud_inst, RG, RB, c->ud_tet, c->tet_inst, inst, c->T0, c->red_part);
     cem_pdl(c->stream, k_reduce_final, 1, RB, c->red_part, 5, c->red_out);
     cem_launched(c, 4);

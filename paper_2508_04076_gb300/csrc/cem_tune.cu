@@ -183,6 +183,7 @@ extern "C" int cem_autotune(cem_ctx* c, const char* cache_path, int reps, int au
     if (!c) return CEM_EINVAL;
     if (!c->material) return cem_fail(c, CEM_ESTATE, "cem_set_material must be called before cem_autotune");
     if (reps < 0 || reps > 1000) return cem_fail(c, CEM_EINVAL, "reps must be in [0, 1000]");
+    if (c->elem_type != CEM_ELEM_TET4) return cem_fail(c, CEM_ESTATE, "the autotuner covers the tetrahedral kernels");
     CEM_CK(c, cudaSetDevice(c->device));
     if (!c->tune_save) {
         void* p = nullptr;
@@ -216,6 +217,8 @@ extern "C" int cem_tune_get(cem_ctx* c, int kernel, int* block, int* batch, doub
 
 extern "C" int cem_tune_set(cem_ctx* c, int kernel, int block, int batch) {
     if (!c || kernel < 0 || kernel >= TUNE_COUNT) return CEM_EINVAL;
+    if (c->elem_type != CEM_ELEM_TET4 && (kernel == TUNE_STRAIN || kernel == TUNE_FORCE))
+        return cem_fail(c, CEM_ESTATE, "hexahedral strain and force kernels have no variants");
     const int v = variant_of(kernel, block, batch);
     if (v < 0) return cem_fail(c, CEM_EINVAL, "no such launch variant");
     c->tune[kernel] = v;

@@ -63,6 +63,10 @@ UNIT = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1.0]])
     ("dir_component", "out of range"),
     ("dir_node", "out of range"),
     ("dir_missing", "dir_node"),
+    ("bad_elem_type", "elem_type"),
+    ("bad_tface_nodes", "tface_nodes"),
+    ("hex_with_splitting", "fixed topology"),
+    ("hex_zero_volume", "positive volume"),
 ])
 def test_host_validation_rejects(lib, case, expect):
     X, tets, nt, ns, prec = UNIT, [[0, 1, 2, 3]], [], [], 0
@@ -85,7 +89,19 @@ def test_host_validation_rejects(lib, case, expect):
         dirichlet = ([1], [3], [0.0])
     elif case == "dir_node":
         dirichlet = ([4], [0], [0.0])
+    hexX = np.array([[0, 0, 0], [1, 0, 0], [1, 1, 0], [0, 1, 0], [0, 0, 1], [1, 0, 1], [1, 1, 1], [0, 1, 1.0]])
+    if case == "hex_with_splitting":
+        X, tets = hexX, [list(range(8))]
+    elif case == "hex_zero_volume":
+        X, tets = hexX, [[0, 3, 2, 1, 4, 7, 6, 5]]   # mirrored: negative volume
     d, keep = _desc(X, tets, nt, ns, prec)
+    if case in ("hex_with_splitting", "hex_zero_volume"):
+        d.elem_type = 1
+        d.split_enabled = 1 if case == "hex_with_splitting" else 0
+    if case == "bad_elem_type":
+        d.elem_type = 5
+    elif case == "bad_tface_nodes":
+        d.tface_nodes = 5
     if case == "bad_split_mode":
         d.split_mode = 2
     elif case == "bad_g_variant":
