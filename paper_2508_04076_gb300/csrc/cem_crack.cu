@@ -345,9 +345,13 @@ struct EdgeStore {
 // Per split: flag the (cut edge, side) keys that have no node yet, and count
 // its sub-elements (6 for pattern I, 4 for pattern II; none when splits only
 // deactivate).
+// The first to flag a key also appends it to new_keys (count in *nk), so a
+// step with few splits can number its new nodes by sorting that short list
+// instead of scanning every key.
 __global__ void k_split_prep(int S, const int* __restrict__ split_list, const uint8_t* __restrict__ split_mask,
                              const int* __restrict__ t2e, int64_t Tc, const int* __restrict__ node_of_key,
-                             uint8_t* __restrict__ key_flag, int* __restrict__ cnt, int deact) {
+                             uint8_t* __restrict__ key_flag, int* __restrict__ cnt, int deact,
+                             int* __restrict__ new_keys, long long* __restrict__ nk) {
     CEM_PDL_ENTRY();
     const int i = blockIdx.x * BS + threadIdx.x;
     if (i >= S) return;
@@ -360,11 +364,51 @@ __global__ void k_split_prep(int S, const int* __restrict__ split_list, const ui
         const int x = CEM_LE0(l), y = CEM_LE1(l);
         if (((m >> x) ^ (m >> y)) & 1) {
             const int e = t2e[l * Tc + p];
-            for (int s = 0; s < 2; ++s)
-                if (node_of_key[2 * e + s] < 0) key_flag[2 * e + s] = 1;
+            for (int s = 0; s < 2; ++s) {
+                const int key = 2 * e + s;
+                if (node_of_key[key] >= 0) continue;
+                // byte test-and-set through its aligned 32-bit word
+                unsigned* w = reinterpret_cast<unsigned*>(key_flag + (key & ~3));
+                const unsigned bit = 1u << (8 * (key & 3));
+                if (!(atomicOr(w, bit) & bit)) new_keys[atomicAdd((unsigned long long*)nk, 1ull)] = key;
+            }
         }
     }
     cnt[i] = (__popc((unsigned)m) == 2) ? 6 : 4;
+}
+
+// New nodes of a step with at most NK_SORT keys: sort the appended keys in
+// shared memory (bitonic) and create node N + rank for each, in ascending key
+// order, exactly as the ordered scan over all keys would.
+constexpr int NK_SORT = 4096;
+
+template <class Store>
+__global__ void __launch_bounds__(1024) k_node_sorted(const long long* __restrict__ nk, const int* __restrict__ new_keys,
+                                                      Store st, long long* __restrict__ count) {
+    CEM_PDL_ENTRY();
+    __shared__ int sk[NK_SORT];
+    const int n = (int)min(*nk, (long long)NK_SORT);
+    int size = 2;
+    while (size < n) size <<= 1;
+    for (int i = threadIdx.x; i < size; i += blockDim.x) sk[i] = i < n ? new_keys[i] : INT_MAX;
+    __syncthreads();
+    for (int k = 2; k <= size; k <<= 1)
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < size; i += blockDim.x) {
+                const int ij = i ^ j;
+                if (ij > i) {
+                    const bool up = (i & k) == 0;
+                    const int a = sk[i], b = sk[ij];
+                    if ((a > b) == up) {
+                        sk[i] = b;
+                        sk[ij] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    for (int i = threadIdx.x; i < n; i += blockDim.x) st((int64_t)sk[i], i, 1);
+    if (threadIdx.x == 0) *count = n;
 }
 
 
@@ -406,7 +450,10 @@ __global__ void k_create_subs(int S, int64_t T, const int* __restrict__ split_li
                               const double* __restrict__ Gc, uint8_t* __restrict__ cand_flag,
                               double* __restrict__ ud_part, double* __restrict__ ud_tet, int deact) {
     CEM_PDL_ENTRY();
-    const int i = blockIdx.x * BS + threadIdx.x;
+    // six threads per split: thread qs builds sub-element qs (the sub-element list is
+    // rebuilt by each, it is cheap integer work); thread 0 also closes the parent
+    const int tid = blockIdx.x * BS + threadIdx.x;
+    const int i = tid / 6, qs = tid % 6;
     if (i >= S) return;
     const int p = split_list[i];
     const int m = split_mask[i];
@@ -470,7 +517,7 @@ __global__ void k_create_subs(int S, int64_t T, const int* __restrict__ split_li
     if (deact) ns = 0;   // the element only leaves the computation
     const int64_t base = T + sub_off[i];
     const double lp = lam[p], mp = mu[p];
-    for (int q = 0; q < ns; ++q) {
+    for (int q = qs; q < ns && q == qs; ++q) {
         int* s = subs[q];
         // orientation and geometry (V * grad N for local nodes 1..3)
         double x0[3], e[3][3];
@@ -518,6 +565,7 @@ __global__ void k_create_subs(int S, int64_t T, const int* __restrict__ split_li
         lam[j] = lp;
         mu[j] = mp;
     }
+    if (qs != 0) return;
     active[p] = 0;
     side[p] = (uint8_t)m;
     split_step[p] = (int)step;
@@ -637,27 +685,47 @@ __global__ void k_mark_affected(int kind, int S, const int* __restrict__ split_l
     atomicAdd(&add_cnt[x], 1);
 }
 
+// The list kernels give each affected list a group of LG = 8 lanes: the lanes
+// load LG entries (and what they point to) at once, so a list costs a few
+// dependent loads rather than one chain per entry.  Kept entries keep their
+// order (positions from ballots), and every sum runs over the list in order
+// (lane 0 adds the group's values in lane order), as a single thread would.
+constexpr int LG = 8;
+
+__device__ __forceinline__ unsigned group_bits(unsigned ballot) {
+    return (ballot >> (threadIdx.x & 24)) & 0xFFu;   // this group's 8 lanes
+}
+
 __global__ void k_list_count(int kind, const long long* __restrict__ count, const int* __restrict__ aff,
                              const int* __restrict__ off, const int* __restrict__ cnt, const int* __restrict__ pool,
                              const uint8_t* __restrict__ active, const int* __restrict__ add_cnt,
                              int* __restrict__ keep, int* __restrict__ need, int bound) {
     CEM_PDL_ENTRY();
-    const int i = blockIdx.x * BS + threadIdx.x;
-    if (i >= bound) return;
-    if (i >= *count) {   // slots past the affected count take no pool space
-        keep[i] = 0;
-        need[i] = 0;
-        return;
+    const int tid = blockIdx.x * BS + threadIdx.x;
+    const int i = tid / LG, g = tid % LG;
+    const long long na = *count;
+    const bool live = i < na;
+    int x = 0, o = 0, n = 0;
+    if (live) {
+        x = aff[i];
+        o = off[x];
+        n = cnt[x];
     }
-    const int x = aff[i];
-    const int o = off[x], n = cnt[x];
     int k = 0;
-    for (int q = 0; q < n; ++q) {
-        const int e = pool[o + q];
-        k += active[kind == 0 ? e : (e >> 2)] ? 1 : 0;
+    for (int base = 0;; base += LG) {
+        const bool more = live && base < n;
+        if (!__any_sync(0xffffffffu, more)) break;
+        bool act = false;
+        if (more && base + g < n) {
+            const int e = pool[o + base + g];
+            act = active[kind == 0 ? e : (e >> 2)] != 0;
+        }
+        k += __popc(group_bits(__ballot_sync(0xffffffffu, act)));
     }
-    keep[i] = k;
-    need[i] = k + add_cnt[x];
+    if (g == 0 && i < bound) {
+        keep[i] = live ? k : 0;            // slots past the affected count take no pool space
+        need[i] = live ? k + add_cnt[x] : 0;
+    }
 }
 
 __global__ void k_list_write(int kind, const long long* __restrict__ count, const int* __restrict__ aff,
@@ -665,19 +733,36 @@ __global__ void k_list_write(int kind, const long long* __restrict__ count, cons
                              const int* __restrict__ need, int* __restrict__ off, int* __restrict__ cnt,
                              int* __restrict__ pool, const uint8_t* __restrict__ active, int* __restrict__ cursor) {
     CEM_PDL_ENTRY();
-    const int i = blockIdx.x * BS + threadIdx.x;
-    if (i >= *count) return;
-    const int x = aff[i];
-    const int o = off[x], n = cnt[x];
-    const int64_t no = top + aoff[i];
-    int w = 0;
-    for (int q = 0; q < n; ++q) {
-        const int e = pool[o + q];
-        if (active[kind == 0 ? e : (e >> 2)]) pool[no + w++] = e;
+    const int tid = blockIdx.x * BS + threadIdx.x;
+    const int i = tid / LG, g = tid % LG;
+    const bool live = i < *count;
+    int x = 0, o = 0, n = 0;
+    int64_t no = 0;
+    if (live) {
+        x = aff[i];
+        o = off[x];
+        n = cnt[x];
+        no = top + aoff[i];
     }
-    off[x] = (int)no;
-    cnt[x] = need[i];
-    cursor[x] = keep[i];
+    int w = 0;
+    for (int base = 0;; base += LG) {
+        const bool more = live && base < n;
+        if (!__any_sync(0xffffffffu, more)) break;
+        bool act = false;
+        int e = 0;
+        if (more && base + g < n) {
+            e = pool[o + base + g];
+            act = active[kind == 0 ? e : (e >> 2)] != 0;
+        }
+        const unsigned b = group_bits(__ballot_sync(0xffffffffu, act));
+        if (act) pool[no + w + __popc(b & ((1u << g) - 1u))] = e;
+        w += __popc(b);
+    }
+    if (live && g == 0) {
+        off[x] = (int)no;
+        cnt[x] = need[i];
+        cursor[x] = keep[i];
+    }
 }
 
 __global__ void k_list_append(int kind, const long long* __restrict__ nsub, int64_t T, const int* __restrict__ t2e,
@@ -702,31 +787,76 @@ __global__ void k_list_finish(int kind, const long long* __restrict__ count, con
                               double* __restrict__ sumV, float* __restrict__ cl32, float* __restrict__ cm32,
                               double rho, double* __restrict__ mass, double* __restrict__ minv) {
     CEM_PDL_ENTRY();
-    const int i = blockIdx.x * BS + threadIdx.x;
-    if (i >= *count) return;
-    const int x = aff[i];
-    const int o = off[x], n = cnt[x], k0 = keep[i];
-    // appended entries arrive in any order: sort them (ascending) after the kept ones
-    for (int q = k0 + 1; q < n; ++q) {
-        const int e = pool[o + q];
-        int r = q - 1;
-        while (r >= k0 && pool[o + r] > e) {
-            pool[o + r + 1] = pool[o + r];
-            --r;
-        }
-        pool[o + r + 1] = e;
+    const int tid = blockIdx.x * BS + threadIdx.x;
+    const int i = tid / LG, g = tid % LG;
+    const bool live = i < *count;
+    int x = 0, o = 0, n = 0, k0 = 0;
+    if (live) {
+        x = aff[i];
+        o = off[x];
+        n = cnt[x];
+        k0 = keep[i];
     }
+    // the appended tail [k0, n) arrives in any order and holds only new (larger) ids:
+    // sort it ascending.  Up to LG entries: each lane places one by its rank.
+    const int m = n - k0;
+    const bool small = m <= LG;
+    int e = 0;
+    if (live && small && g < m) e = pool[o + k0 + g];
+    int rank = 0;
+#pragma unroll
+    for (int r = 0; r < LG; ++r) {
+        const int er = __shfl_sync(0xffffffffu, e, (threadIdx.x & ~(LG - 1)) + r);
+        if (r < m && (er < e || (er == e && r < g))) ++rank;
+    }
+    __syncwarp();
+    if (live && small && g < m) pool[o + k0 + rank] = e;
+    if (live && !small && g == 0) {
+        for (int q = k0 + 1; q < n; ++q) {
+            const int v = pool[o + q];
+            int r = q - 1;
+            while (r >= k0 && pool[o + r] > v) {
+                pool[o + r + 1] = pool[o + r];
+                --r;
+            }
+            pool[o + r + 1] = v;
+        }
+    }
+    __syncwarp();
+    // sums over the list in order: the lanes load, lane 0 adds in lane order
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+    for (int base = 0;; base += LG) {
+        const bool more = live && base < n;
+        if (!__any_sync(0xffffffffu, more)) break;
+        double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+        if (more && base + g < n) {
+            const int v = pool[o + base + g];
+            if (kind == 0) {
+                const double V = vol[v];
+                a0 = V;
+                a1 = V * lam[v];
+                a2 = V * mu[v];
+            } else {
+                a0 = rho * vol[v >> 2] * 0.25;
+            }
+        }
+        for (int r = 0; r < LG; ++r) {
+            const int src = (threadIdx.x & ~(LG - 1)) + r;
+            const double b0 = __shfl_sync(0xffffffffu, a0, src);
+            const double b1 = __shfl_sync(0xffffffffu, a1, src);
+            const double b2 = __shfl_sync(0xffffffffu, a2, src);
+            if (base + r < n) {
+                s0 += b0;
+                s1 += b1;
+                s2 += b2;
+            }
+        }
+    }
+    if (!live || g != 0) return;
     flag[x] = 0;
     add_cnt[x] = 0;
     if (kind == 0) {
-        double sv = 0.0, sl = 0.0, sm = 0.0;
-        for (int q = 0; q < n; ++q) {
-            const int j = pool[o + q];
-            const double V = vol[j];
-            sv += V;
-            sl += V * lam[j];
-            sm += V * mu[j];
-        }
+        const double sv = s0, sl = s1, sm = s2;
         const double inv2 = sv > 0.0 ? 1.0 / (sv * sv) : 0.0;
         cl[x] = sl * inv2;
         cm[x] = sm * inv2;
@@ -736,10 +866,9 @@ __global__ void k_list_finish(int kind, const long long* __restrict__ count, con
             cm32[x] = (float)(sm * inv2);
         }
     } else {
-        double m = 0.0;
-        for (int q = 0; q < n; ++q) m += rho * vol[pool[o + q] >> 2] * 0.25;
-        mass[x] = m;
-        minv[x] = m > 0.0 ? 1.0 / m : 0.0;
+        const double mm = s0;
+        mass[x] = mm;
+        minv[x] = mm > 0.0 ? 1.0 / mm : 0.0;
     }
 }
 
@@ -818,7 +947,7 @@ int update_lists(cem_ctx* c, int kind, int S, int64_t n_items) {
     int rc = cem_compact_u8(c, flag, n_items, c->aff, CNT_AFFECTED);
     if (rc) return rc;
     int* pool = kind == 0 ? c->fan_pool : c->inc_pool;
-    cem_pdl(c->stream, k_list_count, cem_grid(bound, BS), BS, kind, c->dcount + CNT_AFFECTED, c->aff, off, cnt, pool,
+    cem_pdl(c->stream, k_list_count, cem_grid((int64_t)LG * bound, BS), BS, kind, c->dcount + CNT_AFFECTED, c->aff, off, cnt, pool,
                                                            c->active, c->add_cnt, c->aff_keep, c->aff_new, bound);
     cem_launched(c, 1);
     CEM_CK(c, cudaGetLastError());
@@ -840,12 +969,12 @@ int update_lists(cem_ctx* c, int kind, int S, int64_t n_items) {
         }
     }
     pool = kind == 0 ? c->fan_pool : c->inc_pool;
-    cem_pdl(c->stream, k_list_write, cem_grid(bound, BS), BS, kind, c->dcount + CNT_AFFECTED, c->aff, top, c->aff_off,
+    cem_pdl(c->stream, k_list_write, cem_grid((int64_t)LG * bound, BS), BS, kind, c->dcount + CNT_AFFECTED, c->aff, top, c->aff_off,
                                                            c->aff_keep, c->aff_new, off, cnt, pool, c->active,
                                                            c->cursor);
     cem_pdl(c->stream, k_list_append, cem_grid(6 * S * per, BS), BS, kind, nsub, c->T, c->t2e, c->conn, c->Tc, off,
                                                                   pool, c->cursor);
-    cem_pdl(c->stream, k_list_finish, cem_grid(bound, BS), BS, kind, c->dcount + CNT_AFFECTED, c->aff, c->aff_keep, off,
+    cem_pdl(c->stream, k_list_finish, cem_grid((int64_t)LG * bound, BS), BS, kind, c->dcount + CNT_AFFECTED, c->aff, c->aff_keep, off,
                                                             cnt, pool, flag, c->add_cnt, c->vol, c->lam, c->mu, c->cl,
                                                             c->cm, c->sumV, c->cl32, c->cm32, c->rho, c->mass,
                                                             c->minv);
@@ -881,19 +1010,26 @@ int cem_apply_splits(cem_ctx* c, int64_t S64, int64_t step, int book_energy) {
     if (c->n_split_all + S > c->S_cap) return cem_fail(c, CEM_ECAPACITY, "split capacity exhausted");
     int rc;
     // 1. new nodes: one per (cut original edge, side) not yet present; sub-element counts
+    CEM_CK(c, cudaMemsetAsync(c->dcount + CNT_SCRATCH0, 0, sizeof(long long), c->stream));
     cem_pdl(c->stream, k_split_prep, cem_grid(S, BS), BS, S, c->split_list, c->split_mask, c->t2e, c->Tc,
-            c->node_of_key, c->key_flag, c->aff_new, (int)(c->split_mode == CEM_SPLIT_DEACTIVATE));
+            c->node_of_key, c->key_flag, c->aff_new, (int)(c->split_mode == CEM_SPLIT_DEACTIVATE), c->new_keys,
+            c->dcount + CNT_SCRATCH0);
     cem_launched(c, 1);
     CEM_CK(c, cudaGetLastError());
-    if ((rc = run_scan(c, U8Load{c->key_flag},
-                       NodeStore{c->N, c->Nc, c->node_of_key, c->key_flag, c->oe_n0, c->oe_n1, c->X, c->u, c->v, c->a,
-                                 c->fext, c->mass, c->minv, c->dtn, c->inc_off, c->inc_cnt, c->node_inst,
-                                 c->precision == CEM_MIXED ? c->uhl : nullptr, c->dt},
-                       2 * c->E0, CNT_NEWNODE)))
+    const NodeStore ns{c->N, c->Nc, c->node_of_key, c->key_flag, c->oe_n0, c->oe_n1, c->X, c->u, c->v, c->a,
+                       c->fext, c->mass, c->minv, c->dtn, c->inc_off, c->inc_cnt, c->node_inst,
+                       c->precision == CEM_MIXED ? c->uhl : nullptr, c->dt};
+    if (8 * (int64_t)S <= NK_SORT) {   // at most 8 keys per split: sort the short list
+        cem_pdl(c->stream, k_node_sorted<NodeStore>, 1, 1024, c->dcount + CNT_SCRATCH0, c->new_keys, ns,
+                c->dcount + CNT_NEWNODE);
+        cem_launched(c, 1);
+        CEM_CK(c, cudaGetLastError());
+    } else if ((rc = run_scan(c, U8Load{c->key_flag}, ns, 2 * c->E0, CNT_NEWNODE))) {
         return rc;
+    }
     // 2. sub-elements, numbered by (parent, local sub index)
     if ((rc = cem_scan_i32(c, c->aff_new, S, c->sub_off, CNT_NEWSUB))) return rc;
-    cem_pdl(c->stream, k_create_subs, cem_grid(S, BS), BS,
+    cem_pdl(c->stream, k_create_subs, cem_grid(6 * (int64_t)S, BS), BS,
             S, c->T, c->split_list, c->split_mask, c->split_Gv, c->sub_off, step, book_energy, c->conn, c->t2e, c->anc,
             c->active, c->Vg, c->Vg32, c->vol, c->lam, c->mu, c->Tc, c->node_of_key, c->X, c->Nc, c->side,
             c->split_step, c->split_G, c->Gc, c->cand_flag, c->ud_part, c->ud_tet,
