@@ -558,6 +558,10 @@ int create_impl(const cem_mesh_desc* d, cem_ctx* c) {
     ok = ok && dalloc(c, c->aff, aff_cap) && dalloc(c, c->aff_keep, aff_cap) && dalloc(c, c->aff_new, aff_cap) &&
          dalloc(c, c->aff_off, aff_cap);
     ok = ok && dalloc(c, c->add_cnt, big) && dalloc(c, c->cursor, big) && dalloc(c, c->scan_tmp, scan_max);
+    const int64_t aff_cap_n = std::max(Nc, 28 * S_cap);   // node marks of one split step: 7 S x 4
+    ok = ok && dalloc(c, c->aff_n, aff_cap_n) && dalloc(c, c->aff_keep_n, aff_cap_n) &&
+         dalloc(c, c->aff_new_n, aff_cap_n) && dalloc(c, c->aff_off_n, aff_cap_n);
+    ok = ok && dalloc(c, c->add_cnt_n, Nc) && dalloc(c, c->cursor_n, Nc);
     ok = ok && dalloc(c, c->scan_status, c->scan_blocks_cap) && dalloc(c, c->scan_ticket, 1);
     ok = ok && dalloc(c, c->red_part, cem_reduction_doubles()) && dalloc(c, c->red_out, 8);
     ok = ok && dalloc(c, c->dcount, CNT_COUNT);
@@ -613,6 +617,8 @@ int create_impl(const cem_mesh_desc* d, cem_ctx* c) {
     CEM_CK(c, cudaMemsetAsync(c->code_flag, 0, n_codes_cap, s));
     CEM_CK(c, cudaMemsetAsync(c->add_cnt, 0, big * sizeof(int), s));
     CEM_CK(c, cudaMemsetAsync(c->cursor, 0, big * sizeof(int), s));
+    CEM_CK(c, cudaMemsetAsync(c->add_cnt_n, 0, Nc * sizeof(int), s));
+    CEM_CK(c, cudaMemsetAsync(c->cursor_n, 0, Nc * sizeof(int), s));
     CEM_CK(c, cudaMemsetAsync(c->fan_cnt, 0, Ec * sizeof(int), s));
     CEM_CK(c, cudaMemsetAsync(c->fan_off, 0, Ec * sizeof(int), s));
     CEM_CK(c, cudaMemsetAsync(c->inc_cnt, 0, Nc * sizeof(int), s));

@@ -59,8 +59,8 @@ enum {
     CNT_NEWNODE,       // new nodes in this split step
     CNT_NEWSUB,        // new sub-elements in this split step
     CNT_NEWEDGE,       // new edges in this split step
-    CNT_AFFECTED,      // affected edges / nodes (reused)
-    CNT_POOLNEED,      // pool entries needed by this update (exact path)
+    CNT_AFFECTED,      // affected edges of a split step
+    CNT_AFFECTED_N,    // affected nodes of a split step
     CNT_NEED_FAN,      // pool entries taken by this step's fan update
     CNT_NEED_INC,      // pool entries taken by this step's incidence update
     CNT_CAND,          // crack-front elements
@@ -161,7 +161,9 @@ struct cem_ctx {
     uint8_t *key_flag = nullptr, *edge_flag = nullptr, *node_flag = nullptr, *code_flag = nullptr;
     int *new_keys = nullptr, *sub_off = nullptr, *slot_of = nullptr, *code_rank = nullptr;
     int *aff = nullptr, *aff_keep = nullptr, *aff_new = nullptr, *aff_off = nullptr;
-    int *add_cnt = nullptr, *cursor = nullptr;           // [max(Ec, Nc)]
+    int *add_cnt = nullptr, *cursor = nullptr;           // [max(Ec, Nc)]  (edge fans)
+    int *aff_n = nullptr, *aff_keep_n = nullptr, *aff_new_n = nullptr, *aff_off_n = nullptr;   // node lists
+    int *add_cnt_n = nullptr, *cursor_n = nullptr;       // [Nc]
     int* scan_tmp = nullptr;                            // positions, [max scan length]
     int* scan_blocks = nullptr;                         // (unused by the single-pass scan)
     unsigned long long* scan_status = nullptr;          // look-back status words, one per block

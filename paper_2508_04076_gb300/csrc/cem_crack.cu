@@ -165,8 +165,10 @@ __global__ void __launch_bounds__(BS) k_front_G(const int* __restrict__ cand_lis
                                                 int64_t Nc, const double* __restrict__ sig,
                                                 const float* __restrict__ sig32,
                                                 const double* __restrict__ Gc, int gvar,
-                                                uint8_t* __restrict__ dec_mask, double* __restrict__ dec_G) {
+                                                uint8_t* __restrict__ dec_mask, double* __restrict__ dec_G,
+                                                long long* __restrict__ nk) {
     CEM_PDL_ENTRY();
+    if (blockIdx.x == 0 && threadIdx.x == 0) *nk = 0;   // new-key counter of this step's splits
     const int tid = blockIdx.x * BS + threadIdx.x;
     const int ci = tid >> 2, f = tid & 3;
     double G = -1.0 / 0.0;
@@ -575,19 +577,6 @@ __global__ void k_create_subs(int S, int64_t T, const int* __restrict__ split_li
     ud_tet[p] = ud_part[i];
 }
 
-__global__ void k_ud_sum(int S, const double* __restrict__ part, double* __restrict__ Ud) {
-    CEM_PDL_ENTRY();
-    __shared__ double sh[BS];
-    double s = 0.0;
-    for (int i = threadIdx.x; i < S; i += BS) s += part[i];
-    sh[threadIdx.x] = s;
-    __syncthreads();
-    for (int w = BS / 2; w > 0; w >>= 1) {
-        if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) *Ud += sh[0];
-}
 
 // ------------------------------------------------------------------ new edges
 __device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
@@ -661,28 +650,43 @@ __global__ void k_edge_resolve(const long long* __restrict__ nsub, int64_t T, co
 }
 
 // ------------------------------------------------------------------ fans / incidence
-// kind 0: edge fans (entries: element id; 6 per element via t2e)
-// kind 1: node incidence (entries: element*4 + local; 4 per element via conn)
-__global__ void k_mark_affected(int kind, int S, const int* __restrict__ split_list,
-                                const long long* __restrict__ nsub, int64_t T,
-                                const int* __restrict__ t2e, const int* __restrict__ conn, int64_t Tc,
-                                uint8_t* __restrict__ flag, int* __restrict__ add_cnt) {
+// Both kinds of list are updated by the same launches: kind 0, the edge fans
+// (entries: element ids; 6 per element via t2e), and kind 1, the node
+// incidence (entries: element * 4 + local; 4 per element via conn).  A
+// thread's kind follows from its index: the kind-0 range first.
+struct ListKind {
+    int kind, per, bound;                 // bound: marks of this step, S parents + 6 S sub-elements
+    uint8_t* flag;
+    int *off, *cnt, *pool;
+    int *aff, *keep, *need, *aoff, *add_cnt, *cursor;
+    const long long* count;               // affected items (device)
+    int64_t top;                          // first free pool entry
+};
+
+__device__ __forceinline__ int list_item(const ListKind& L, const int* t2e, const int* conn, int64_t Tc,
+                                         int64_t elem, int l) {
+    return L.kind == 0 ? t2e[l * Tc + elem] : conn[l * Tc + elem];
+}
+
+__global__ void k_mark_affected(ListKind L0, ListKind L1, int S, const int* __restrict__ split_list,
+                                const long long* __restrict__ nsub, int64_t T, const int* __restrict__ t2e,
+                                const int* __restrict__ conn, int64_t Tc) {
     CEM_PDL_ENTRY();
-    const int per = kind == 0 ? 6 : 4;
-    const int i = blockIdx.x * BS + threadIdx.x;
+    int i = blockIdx.x * BS + threadIdx.x;
+    const bool k1 = i >= L0.bound;
+    const ListKind& L = k1 ? L1 : L0;
+    if (k1) i -= L0.bound;
+    if (i >= L.bound) return;
+    const int per = L.per;
     if (i < S * per) {
-        const int p = split_list[i / per], l = i % per;
-        const int x = kind == 0 ? t2e[l * Tc + p] : conn[l * Tc + p];
-        flag[x] = 1;
+        L.flag[list_item(L, t2e, conn, Tc, split_list[i / per], i % per)] = 1;
         return;
     }
     const int c = i - S * per;
     if (c >= *nsub * per) return;
-    const int64_t s = T + c / per;
-    const int l = c % per;
-    const int x = kind == 0 ? t2e[l * Tc + s] : conn[l * Tc + s];
-    flag[x] = 1;
-    atomicAdd(&add_cnt[x], 1);
+    const int x = list_item(L, t2e, conn, Tc, T + c / per, c % per);
+    L.flag[x] = 1;
+    atomicAdd(&L.add_cnt[x], 1);
 }
 
 // The list kernels give each affected list a group of LG = 8 lanes: the lanes
@@ -690,26 +694,29 @@ __global__ void k_mark_affected(int kind, int S, const int* __restrict__ split_l
 // dependent loads rather than one chain per entry.  Kept entries keep their
 // order (positions from ballots), and every sum runs over the list in order
 // (lane 0 adds the group's values in lane order), as a single thread would.
+// A whole warp always has one kind: both kinds' ranges are multiples of 32.
 constexpr int LG = 8;
 
 __device__ __forceinline__ unsigned group_bits(unsigned ballot) {
     return (ballot >> (threadIdx.x & 24)) & 0xFFu;   // this group's 8 lanes
 }
 
-__global__ void k_list_count(int kind, const long long* __restrict__ count, const int* __restrict__ aff,
-                             const int* __restrict__ off, const int* __restrict__ cnt, const int* __restrict__ pool,
-                             const uint8_t* __restrict__ active, const int* __restrict__ add_cnt,
-                             int* __restrict__ keep, int* __restrict__ need, int bound) {
+__device__ __forceinline__ int group_range(int bound) { return ((LG * bound + 31) / 32) * 32; }
+
+__global__ void k_list_count(ListKind L0, ListKind L1, const uint8_t* __restrict__ active) {
     CEM_PDL_ENTRY();
-    const int tid = blockIdx.x * BS + threadIdx.x;
+    int tid = blockIdx.x * BS + threadIdx.x;
+    const int r0 = group_range(L0.bound);
+    const bool k1 = tid >= r0;
+    const ListKind& L = k1 ? L1 : L0;
+    if (k1) tid -= r0;
     const int i = tid / LG, g = tid % LG;
-    const long long na = *count;
-    const bool live = i < na;
+    const bool live = i < *L.count;
     int x = 0, o = 0, n = 0;
     if (live) {
-        x = aff[i];
-        o = off[x];
-        n = cnt[x];
+        x = L.aff[i];
+        o = L.off[x];
+        n = L.cnt[x];
     }
     int k = 0;
     for (int base = 0;; base += LG) {
@@ -717,32 +724,33 @@ __global__ void k_list_count(int kind, const long long* __restrict__ count, cons
         if (!__any_sync(0xffffffffu, more)) break;
         bool act = false;
         if (more && base + g < n) {
-            const int e = pool[o + base + g];
-            act = active[kind == 0 ? e : (e >> 2)] != 0;
+            const int e = L.pool[o + base + g];
+            act = active[L.kind == 0 ? e : (e >> 2)] != 0;
         }
         k += __popc(group_bits(__ballot_sync(0xffffffffu, act)));
     }
-    if (g == 0 && i < bound) {
-        keep[i] = live ? k : 0;            // slots past the affected count take no pool space
-        need[i] = live ? k + add_cnt[x] : 0;
+    if (g == 0 && i < L.bound) {
+        L.keep[i] = live ? k : 0;            // slots past the affected count take no pool space
+        L.need[i] = live ? k + L.add_cnt[x] : 0;
     }
 }
 
-__global__ void k_list_write(int kind, const long long* __restrict__ count, const int* __restrict__ aff,
-                             int64_t top, const int* __restrict__ aoff, const int* __restrict__ keep,
-                             const int* __restrict__ need, int* __restrict__ off, int* __restrict__ cnt,
-                             int* __restrict__ pool, const uint8_t* __restrict__ active, int* __restrict__ cursor) {
+__global__ void k_list_write(ListKind L0, ListKind L1, const uint8_t* __restrict__ active) {
     CEM_PDL_ENTRY();
-    const int tid = blockIdx.x * BS + threadIdx.x;
+    int tid = blockIdx.x * BS + threadIdx.x;
+    const int r0 = group_range(L0.bound);
+    const bool k1 = tid >= r0;
+    const ListKind& L = k1 ? L1 : L0;
+    if (k1) tid -= r0;
     const int i = tid / LG, g = tid % LG;
-    const bool live = i < *count;
+    const bool live = i < *L.count;
     int x = 0, o = 0, n = 0;
     int64_t no = 0;
     if (live) {
-        x = aff[i];
-        o = off[x];
-        n = cnt[x];
-        no = top + aoff[i];
+        x = L.aff[i];
+        o = L.off[x];
+        n = L.cnt[x];
+        no = L.top + L.aoff[i];
     }
     int w = 0;
     for (int base = 0;; base += LG) {
@@ -751,51 +759,58 @@ __global__ void k_list_write(int kind, const long long* __restrict__ count, cons
         bool act = false;
         int e = 0;
         if (more && base + g < n) {
-            e = pool[o + base + g];
-            act = active[kind == 0 ? e : (e >> 2)] != 0;
+            e = L.pool[o + base + g];
+            act = active[L.kind == 0 ? e : (e >> 2)] != 0;
         }
         const unsigned b = group_bits(__ballot_sync(0xffffffffu, act));
-        if (act) pool[no + w + __popc(b & ((1u << g) - 1u))] = e;
+        if (act) L.pool[no + w + __popc(b & ((1u << g) - 1u))] = e;
         w += __popc(b);
     }
     if (live && g == 0) {
-        off[x] = (int)no;
-        cnt[x] = need[i];
-        cursor[x] = keep[i];
+        L.off[x] = (int)no;
+        L.cnt[x] = L.need[i];
+        L.cursor[x] = L.keep[i];
     }
 }
 
-__global__ void k_list_append(int kind, const long long* __restrict__ nsub, int64_t T, const int* __restrict__ t2e,
-                              const int* __restrict__ conn, int64_t Tc, const int* __restrict__ off,
-                              int* __restrict__ pool, int* __restrict__ cursor) {
+__global__ void k_list_append(ListKind L0, ListKind L1, const long long* __restrict__ nsub, int64_t T,
+                              const int* __restrict__ t2e, const int* __restrict__ conn, int64_t Tc, int S) {
     CEM_PDL_ENTRY();
-    const int per = kind == 0 ? 6 : 4;
-    const int c = blockIdx.x * BS + threadIdx.x;
+    int c = blockIdx.x * BS + threadIdx.x;
+    const int r0 = 6 * S * L0.per;
+    const bool k1 = c >= r0;
+    const ListKind& L = k1 ? L1 : L0;
+    if (k1) c -= r0;
+    const int per = L.per;
     if (c >= *nsub * per) return;
     const int64_t s = T + c / per;
     const int l = c % per;
-    const int x = kind == 0 ? t2e[l * Tc + s] : conn[l * Tc + s];
-    const int pos = atomicAdd(&cursor[x], 1);
-    pool[off[x] + pos] = kind == 0 ? (int)s : (int)(s * 4 + l);
+    const int x = list_item(L, t2e, conn, Tc, s, l);
+    const int pos = atomicAdd(&L.cursor[x], 1);
+    L.pool[L.off[x] + pos] = L.kind == 0 ? (int)s : (int)(s * 4 + l);
 }
 
-__global__ void k_list_finish(int kind, const long long* __restrict__ count, const int* __restrict__ aff,
-                              const int* __restrict__ keep, const int* __restrict__ off, const int* __restrict__ cnt,
-                              int* __restrict__ pool, uint8_t* __restrict__ flag, int* __restrict__ add_cnt,
-                              const double* __restrict__ vol, const double* __restrict__ lam,
-                              const double* __restrict__ mu, double* __restrict__ cl, double* __restrict__ cm,
-                              double* __restrict__ sumV, float* __restrict__ cl32, float* __restrict__ cm32,
-                              double rho, double* __restrict__ mass, double* __restrict__ minv) {
+__global__ void k_list_finish(ListKind L0, ListKind L1, const double* __restrict__ vol,
+                              const double* __restrict__ lam, const double* __restrict__ mu, double* __restrict__ cl,
+                              double* __restrict__ cm, double* __restrict__ sumV, float* __restrict__ cl32,
+                              float* __restrict__ cm32, double rho, double* __restrict__ mass,
+                              double* __restrict__ minv) {
     CEM_PDL_ENTRY();
-    const int tid = blockIdx.x * BS + threadIdx.x;
+    int tid = blockIdx.x * BS + threadIdx.x;
+    const int r0 = group_range(L0.bound);
+    const bool k1 = tid >= r0;
+    const ListKind& L = k1 ? L1 : L0;
+    if (k1) tid -= r0;
+    const int kind = L.kind;
+    int* pool = L.pool;
     const int i = tid / LG, g = tid % LG;
-    const bool live = i < *count;
+    const bool live = i < *L.count;
     int x = 0, o = 0, n = 0, k0 = 0;
     if (live) {
-        x = aff[i];
-        o = off[x];
-        n = cnt[x];
-        k0 = keep[i];
+        x = L.aff[i];
+        o = L.off[x];
+        n = L.cnt[x];
+        k0 = L.keep[i];
     }
     // the appended tail [k0, n) arrives in any order and holds only new (larger) ids:
     // sort it ascending.  Up to LG entries: each lane places one by its rank.
@@ -853,8 +868,8 @@ __global__ void k_list_finish(int kind, const long long* __restrict__ count, con
         }
     }
     if (!live || g != 0) return;
-    flag[x] = 0;
-    add_cnt[x] = 0;
+    L.flag[x] = 0;
+    L.add_cnt[x] = 0;
     if (kind == 0) {
         const double sv = s0, sl = s1, sm = s2;
         const double inv2 = sv > 0.0 ? 1.0 / (sv * sv) : 0.0;
@@ -884,21 +899,36 @@ __global__ void k_defrag(int64_t n, const int* __restrict__ newoff, int* __restr
 }
 
 // ------------------------------------------------------------------ candidates
+// Flag the unsplit face neighbours the new cracks reach.  Block 0 also adds
+// this step's dissipated energy to U_d (a fixed-order block reduction).
 __global__ void k_cand_mark(int S, const int* __restrict__ split_list, const uint8_t* __restrict__ split_mask,
                             const int* __restrict__ face_nbr, int64_t T0, const uint8_t* __restrict__ side,
-                            uint8_t* __restrict__ cand_flag) {
+                            uint8_t* __restrict__ cand_flag, const double* __restrict__ ud_part,
+                            double* __restrict__ Ud) {
     CEM_PDL_ENTRY();
     const int i = blockIdx.x * BS + threadIdx.x;
-    if (i >= S) return;
-    const int p = split_list[i], m = split_mask[i];
-    for (int f = 0; f < 4; ++f) {
-        int b[3], k = 0;
-        for (int l = 0; l < 4; ++l)
-            if (l != f) b[k++] = (m >> l) & 1;
-        if (b[0] == b[1] && b[1] == b[2]) continue;
-        const int nb = face_nbr[f * T0 + p];
-        if (nb >= 0 && side[nb] == 0) cand_flag[nb] = 1;
+    if (i < S) {
+        const int p = split_list[i], m = split_mask[i];
+        for (int f = 0; f < 4; ++f) {
+            int b[3], k = 0;
+            for (int l = 0; l < 4; ++l)
+                if (l != f) b[k++] = (m >> l) & 1;
+            if (b[0] == b[1] && b[1] == b[2]) continue;
+            const int nb = face_nbr[f * T0 + p];
+            if (nb >= 0 && side[nb] == 0) cand_flag[nb] = 1;
+        }
     }
+    if (blockIdx.x != 0) return;
+    __shared__ double sh[BS];
+    double s = 0.0;
+    for (int q = threadIdx.x; q < S; q += BS) s += ud_part[q];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = BS / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *Ud += sh[0];
 }
 
 int sync_counts(cem_ctx* c) {
@@ -929,58 +959,76 @@ int defrag(cem_ctx* c, int kind) {
     return CEM_OK;
 }
 
-// Update the fan (kind 0) or incidence (kind 1) lists of every affected edge /
-// node.  S splits of this step; the number of new sub-elements is read on the
-// device (at most 6 S), n_items bounds the flag range.  The host does not wait
-// unless the pool may be too short for the worst case this step can need.
-int update_lists(cem_ctx* c, int kind, int S, int64_t n_items) {
-    const int per = kind == 0 ? 6 : 4;
-    uint8_t* flag = kind == 0 ? c->edge_flag : c->node_flag;
-    int* off = kind == 0 ? c->fan_off : c->inc_off;
-    int* cnt = kind == 0 ? c->fan_cnt : c->inc_cnt;
+// Update the fan and incidence lists of every affected edge and node.  S
+// splits of this step; the number of new sub-elements is read on the device
+// (at most 6 S).  The host does not wait unless a pool may be too short for
+// the worst case this step can need.
+ListKind list_kind(cem_ctx* c, int kind, int S) {
+    ListKind L;
+    L.kind = kind;
+    L.per = kind == 0 ? 6 : 4;
+    L.bound = 7 * S * L.per;   // marks: S parents + at most 6 S sub-elements
+    L.flag = kind == 0 ? c->edge_flag : c->node_flag;
+    L.off = kind == 0 ? c->fan_off : c->inc_off;
+    L.cnt = kind == 0 ? c->fan_cnt : c->inc_cnt;
+    L.pool = kind == 0 ? c->fan_pool : c->inc_pool;
+    L.aff = kind == 0 ? c->aff : c->aff_n;
+    L.keep = kind == 0 ? c->aff_keep : c->aff_keep_n;
+    L.need = kind == 0 ? c->aff_new : c->aff_new_n;
+    L.aoff = kind == 0 ? c->aff_off : c->aff_off_n;
+    L.add_cnt = kind == 0 ? c->add_cnt : c->add_cnt_n;
+    L.cursor = kind == 0 ? c->cursor : c->cursor_n;
+    L.count = c->dcount + (kind == 0 ? CNT_AFFECTED : CNT_AFFECTED_N);
+    L.top = kind == 0 ? c->fan_top : c->inc_top;
+    return L;
+}
+
+int64_t group_threads(int bound) { return ((LG * (int64_t)bound + 31) / 32) * 32; }
+
+int update_lists(cem_ctx* c, int S) {
     const long long* nsub = c->dcount + CNT_NEWSUB;
-    const int bound = 7 * S * per;   // marks: S parents + at most 6 S sub-elements
-    cem_pdl(c->stream, k_mark_affected, cem_grid(bound, BS), BS, kind, S, c->split_list, nsub, c->T, c->t2e, c->conn,
-                                                              c->Tc, flag, c->add_cnt);
+    ListKind L0 = list_kind(c, 0, S), L1 = list_kind(c, 1, S);
+    cem_pdl(c->stream, k_mark_affected, cem_grid(L0.bound + L1.bound, BS), BS, L0, L1, S, c->split_list, nsub, c->T,
+            c->t2e, c->conn, c->Tc);
     cem_launched(c, 1);
     CEM_CK(c, cudaGetLastError());
-    int rc = cem_compact_u8(c, flag, n_items, c->aff, CNT_AFFECTED);
-    if (rc) return rc;
-    int* pool = kind == 0 ? c->fan_pool : c->inc_pool;
-    cem_pdl(c->stream, k_list_count, cem_grid((int64_t)LG * bound, BS), BS, kind, c->dcount + CNT_AFFECTED, c->aff, off, cnt, pool,
-                                                           c->active, c->add_cnt, c->aff_keep, c->aff_new, bound);
+    int rc;
+    if ((rc = cem_compact_u8(c, L0.flag, c->E + 22 * (int64_t)S, L0.aff, CNT_AFFECTED)) ||
+        (rc = cem_compact_u8(c, L1.flag, c->N + 8 * (int64_t)S, L1.aff, CNT_AFFECTED_N)))
+        return rc;
+    const int64_t gthreads = group_threads(L0.bound) + group_threads(L1.bound);
+    cem_pdl(c->stream, k_list_count, cem_grid(gthreads, BS), BS, L0, L1, (const uint8_t*)c->active);
     cem_launched(c, 1);
     CEM_CK(c, cudaGetLastError());
-    const int need_slot = kind == 0 ? CNT_NEED_FAN : CNT_NEED_INC;
-    rc = cem_scan_i32(c, c->aff_new, bound, c->aff_off, need_slot);
-    if (rc) return rc;
-    int64_t& top = kind == 0 ? c->fan_top : c->inc_top;
-    const int64_t cap = kind == 0 ? c->fan_cap : c->inc_cap;
+    if ((rc = cem_scan_i32(c, L0.need, L0.bound, L0.aoff, CNT_NEED_FAN)) ||
+        (rc = cem_scan_i32(c, L1.need, L1.bound, L1.aoff, CNT_NEED_INC)))
+        return rc;
     // every affected list holds at most 3 times the largest input fan / incidence
-    const int64_t per_list = 3 * (kind == 0 ? c->max_fan0 : std::max(c->max_inc0, c->max_fan0));
-    if (top + (int64_t)bound * per_list > cap) {
-        rc = sync_counts(c);
-        if (rc) return rc;
-        const int64_t need = c->hcount[need_slot];
+    bool synced = false;
+    for (int kind = 0; kind < 2; ++kind) {
+        int64_t& top = kind == 0 ? c->fan_top : c->inc_top;
+        const int64_t cap = kind == 0 ? c->fan_cap : c->inc_cap;
+        const int bound = kind == 0 ? L0.bound : L1.bound;
+        const int64_t per_list = 3 * (kind == 0 ? c->max_fan0 : std::max(c->max_inc0, c->max_fan0));
+        if (top + (int64_t)bound * per_list <= cap) continue;
+        if (!synced && (rc = sync_counts(c))) return rc;
+        synced = true;
+        const int64_t need = c->hcount[kind == 0 ? CNT_NEED_FAN : CNT_NEED_INC];
         if (top + need > cap) {
-            rc = defrag(c, kind);
-            if (rc) return rc;
+            if ((rc = defrag(c, kind))) return rc;
             if (top + need > cap) return cem_fail(c, CEM_ECAPACITY, "fan/incidence pool exhausted");
         }
     }
-    pool = kind == 0 ? c->fan_pool : c->inc_pool;
-    cem_pdl(c->stream, k_list_write, cem_grid((int64_t)LG * bound, BS), BS, kind, c->dcount + CNT_AFFECTED, c->aff, top, c->aff_off,
-                                                           c->aff_keep, c->aff_new, off, cnt, pool, c->active,
-                                                           c->cursor);
-    cem_pdl(c->stream, k_list_append, cem_grid(6 * S * per, BS), BS, kind, nsub, c->T, c->t2e, c->conn, c->Tc, off,
-                                                                  pool, c->cursor);
-    cem_pdl(c->stream, k_list_finish, cem_grid((int64_t)LG * bound, BS), BS, kind, c->dcount + CNT_AFFECTED, c->aff, c->aff_keep, off,
-                                                            cnt, pool, flag, c->add_cnt, c->vol, c->lam, c->mu, c->cl,
-                                                            c->cm, c->sumV, c->cl32, c->cm32, c->rho, c->mass,
-                                                            c->minv);
+    L0 = list_kind(c, 0, S);   // pools may have moved (defragmentation)
+    L1 = list_kind(c, 1, S);
+    cem_pdl(c->stream, k_list_write, cem_grid(gthreads, BS), BS, L0, L1, (const uint8_t*)c->active);
+    cem_pdl(c->stream, k_list_append, cem_grid(6 * (int64_t)S * (L0.per + L1.per), BS), BS, L0, L1, nsub, c->T,
+            c->t2e, c->conn, c->Tc, S);
+    cem_pdl(c->stream, k_list_finish, cem_grid(gthreads, BS), BS, L0, L1, c->vol, c->lam, c->mu, c->cl, c->cm,
+            c->sumV, c->cl32, c->cm32, c->rho, c->mass, c->minv);
     cem_launched(c, 3);
     CEM_CK(c, cudaGetLastError());
-    return CEM_OK;   // the host advances `top` by the need once it next reads the counters
+    return CEM_OK;   // the host advances the pool tops by the needs once it next reads the counters
 }
 
 }  // namespace
@@ -990,7 +1038,7 @@ int cem_launch_front_G(cem_ctx* c) {
         cem_pdl(c->stream, k_front_G, cem_grid(4 * c->n_cand, BS), BS, c->cand_list, (int)c->n_cand, c->conn, c->t2e, c->Tc,
                                                                  c->face_nbr, c->side, c->T0, c->X, c->u, c->Nc, c->sig,
                                                                  c->sig32, c->Gc, c->g_variant, c->dec_mask,
-                                                                 c->dec_G);
+                                                                 c->dec_G, c->dcount + CNT_SCRATCH0);
         cem_launched(c, 1);
         CEM_CK(c, cudaGetLastError());
     }
@@ -1010,7 +1058,8 @@ int cem_apply_splits(cem_ctx* c, int64_t S64, int64_t step, int book_energy) {
     if (c->n_split_all + S > c->S_cap) return cem_fail(c, CEM_ECAPACITY, "split capacity exhausted");
     int rc;
     // 1. new nodes: one per (cut original edge, side) not yet present; sub-element counts
-    CEM_CK(c, cudaMemsetAsync(c->dcount + CNT_SCRATCH0, 0, sizeof(long long), c->stream));
+    // the new-key counter starts at 0: reset by the front evaluation of this step, or here for the notch
+    if (step < 0) CEM_CK(c, cudaMemsetAsync(c->dcount + CNT_SCRATCH0, 0, sizeof(long long), c->stream));
     cem_pdl(c->stream, k_split_prep, cem_grid(S, BS), BS, S, c->split_list, c->split_mask, c->t2e, c->Tc,
             c->node_of_key, c->key_flag, c->aff_new, (int)(c->split_mode == CEM_SPLIT_DEACTIVATE), c->new_keys,
             c->dcount + CNT_SCRATCH0);
@@ -1034,14 +1083,13 @@ int cem_apply_splits(cem_ctx* c, int64_t S64, int64_t step, int book_energy) {
             c->active, c->Vg, c->Vg32, c->vol, c->lam, c->mu, c->Tc, c->node_of_key, c->X, c->Nc, c->side,
             c->split_step, c->split_G, c->Gc, c->cand_flag, c->ud_part, c->ud_tet,
             (int)(c->split_mode == CEM_SPLIT_DEACTIVATE));
-    cem_pdl(c->stream, k_ud_sum, 1, BS, S, c->ud_part, c->Ud);
     // 3. edges of the sub-elements: parent edges or (new) hashed node pairs
     const long long* nsub = c->dcount + CNT_NEWSUB;
     const int codes = 36 * S;
     cem_pdl(c->stream, k_sub_edges, cem_grid(codes, BS), BS, nsub, c->T, c->N0, c->conn, c->t2e, c->anc, c->Tc,
             c->hkeys, c->hvals, c->hfirst, c->hash_cap - 1, c->slot_of, c->dcount + CNT_ERR);
     cem_pdl(c->stream, k_edge_owner, cem_grid(codes, BS), BS, nsub, c->slot_of, c->hvals, c->hfirst, c->code_flag);
-    cem_launched(c, 4);
+    cem_launched(c, 3);
     CEM_CK(c, cudaGetLastError());
     if ((rc = run_scan(c, U8Load{c->code_flag},
                        EdgeStore{c->E, c->slot_of, c->hvals, c->hfirst, c->code_flag, c->fan_off, c->fan_cnt, c->cl,
@@ -1052,11 +1100,10 @@ int cem_apply_splits(cem_ctx* c, int64_t S64, int64_t step, int book_energy) {
     cem_launched(c, 1);
     CEM_CK(c, cudaGetLastError());
     // 4. fans of affected edges, incidence (and mass) of affected nodes
-    if ((rc = update_lists(c, 0, S, c->E + 22 * (int64_t)S))) return rc;
-    if ((rc = update_lists(c, 1, S, c->N + 8 * (int64_t)S))) return rc;
+    if ((rc = update_lists(c, S))) return rc;
     // 5. crack-front candidates
     cem_pdl(c->stream, k_cand_mark, cem_grid(S, BS), BS, S, c->split_list, c->split_mask, c->face_nbr, c->T0, c->side,
-                                                       c->cand_flag);
+                                                       c->cand_flag, c->ud_part, c->Ud);
     cem_launched(c, 1);
     CEM_CK(c, cudaGetLastError());
     if ((rc = cem_compact_u8(c, c->cand_flag, c->T0, c->cand_list, CNT_CAND))) return rc;
