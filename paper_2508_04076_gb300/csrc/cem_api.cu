@@ -554,7 +554,7 @@ int create_impl(const cem_mesh_desc* d, cem_ctx* c) {
     ok = ok && dalloc(c, c->hkeys, c->hash_cap) && dalloc(c, c->hvals, c->hash_cap) && dalloc(c, c->hfirst, c->hash_cap);
     ok = ok && dalloc(c, c->key_flag, 2 * E0) && dalloc(c, c->edge_flag, Ec) && dalloc(c, c->node_flag, Nc);
     ok = ok && dalloc(c, c->code_flag, n_codes_cap) && dalloc(c, c->new_keys, 2 * E0) && dalloc(c, c->sub_off, T0);
-    ok = ok && dalloc(c, c->slot_of, n_codes_cap) && dalloc(c, c->code_rank, n_codes_cap);
+    ok = ok && dalloc(c, c->slot_of, n_codes_cap);
     ok = ok && dalloc(c, c->aff, aff_cap) && dalloc(c, c->aff_keep, aff_cap) && dalloc(c, c->aff_new, aff_cap) &&
          dalloc(c, c->aff_off, aff_cap);
     ok = ok && dalloc(c, c->add_cnt, big) && dalloc(c, c->cursor, big) && dalloc(c, c->scan_tmp, scan_max);

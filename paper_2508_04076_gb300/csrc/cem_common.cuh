@@ -70,7 +70,7 @@ enum {
     CNT_COUNT
 };
 
-enum { DERR_HASH_FULL = 1, DERR_CAPACITY = 2, DERR_SCAN_WAIT = 4 };
+enum { DERR_HASH_FULL = 1, DERR_SCAN_WAIT = 4 };
 
 // kernels with tuned launch variants (block size, gather batch)
 enum { TUNE_STRAIN = 0, TUNE_EDGE, TUNE_FORCE, TUNE_NODE, TUNE_COUNT };
@@ -159,13 +159,12 @@ struct cem_ctx {
     int *hvals = nullptr, *hfirst = nullptr;
     // split-step scratch
     uint8_t *key_flag = nullptr, *edge_flag = nullptr, *node_flag = nullptr, *code_flag = nullptr;
-    int *new_keys = nullptr, *sub_off = nullptr, *slot_of = nullptr, *code_rank = nullptr;
+    int *new_keys = nullptr, *sub_off = nullptr, *slot_of = nullptr;
     int *aff = nullptr, *aff_keep = nullptr, *aff_new = nullptr, *aff_off = nullptr;
     int *add_cnt = nullptr, *cursor = nullptr;           // [max(Ec, Nc)]  (edge fans)
     int *aff_n = nullptr, *aff_keep_n = nullptr, *aff_new_n = nullptr, *aff_off_n = nullptr;   // node lists
     int *add_cnt_n = nullptr, *cursor_n = nullptr;       // [Nc]
     int* scan_tmp = nullptr;                            // positions, [max scan length]
-    int* scan_blocks = nullptr;                         // (unused by the single-pass scan)
     unsigned long long* scan_status = nullptr;          // look-back status words, one per block
     unsigned int* scan_ticket = nullptr;                // block tickets of the running scan
     unsigned long long scan_epoch = 0;
