@@ -330,6 +330,22 @@ int cem_probe_fp64_fma(int device, void* stream, double* flops_per_s);
 int cem_node_energies_noalloc(const double* u, const double* v, const double* a, const double* mass,
                               const double* fext, int64_t n_nodes, int64_t ld, double* out, void* stream);
 
+/* Checkpoint and resume.  cem_save writes the context's dynamic state to the
+ * file `path`: node, element and edge arrays up to their current counts, the
+ * fan and incidence lists, the crack records, the candidate list, the
+ * new-node and new-edge maps, U_d and the step counter (not the step's
+ * scratch, which every step rewrites before reading).  cem_load reads such a
+ * file into a context created from the same mesh description with the same
+ * material; stepping it then continues bit for bit as the saved context
+ * would have.  Both synchronise the context's stream and return after the
+ * file is written / the state is on the device.  Errors: CEM_ESTATE (no
+ * material), CEM_EINVAL (cannot open or write the file; not a checkpoint; a
+ * different mesh, element type, precision, capacity or time step; a
+ * truncated file, after which the context's state is undefined), CEM_ECUDA.
+ * The file is in host byte order. */
+int cem_save(cem_ctx* ctx, const char* path);
+int cem_load(cem_ctx* ctx, const char* path);
+
 /* Release every device allocation and the context (NULL is accepted). */
 int cem_destroy(cem_ctx* ctx);
 

@@ -27,7 +27,7 @@ FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_void_p)
 
 EXPORTED = ["cem_mesh_create", "cem_set_material", "cem_step", "cem_energy", "cem_crack_state",
             "cem_get_field", "cem_info", "cem_energy_instance", "cem_adjoint", "cem_profile", "cem_profile_read",
-            "cem_autotune", "cem_tune_get", "cem_tune_set", "cem_probe_fp64_fma", "cem_destroy", "cem_last_error"]
+            "cem_autotune", "cem_tune_get", "cem_tune_set", "cem_save", "cem_load", "cem_probe_fp64_fma", "cem_destroy", "cem_last_error"]
 TUNED = ["strain", "edge_stress", "force", "node_update"]
 KERNELS = ["predict", "strain", "edge_stress", "force", "node_update", "front_G", "split"]
 
@@ -94,6 +94,8 @@ def load_library(build: bool = True):
     lib.cem_probe_fp64_fma.argtypes = [C.c_int, C.c_void_p, C.POINTER(C.c_double)]
     lib.cem_autotune.argtypes = [P, C.c_char_p, C.c_int, C.c_int]
     lib.cem_tune_set.argtypes = [P, C.c_int, C.c_int, C.c_int]
+    lib.cem_save.argtypes = [P, C.c_char_p]
+    lib.cem_load.argtypes = [P, C.c_char_p]
     lib.cem_tune_get.argtypes = [P, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_double),
                                  C.POINTER(C.c_double)]
     lib.cem_destroy.argtypes = [P]
@@ -287,6 +289,14 @@ class CEM:
             self._check(self._lib.cem_tune_get(self._ctx, k, C.byref(b), C.byref(q), C.byref(us), C.byref(du)))
             out[name] = (b.value, q.value, us.value, du.value)
         return out
+
+    def save(self, path):
+        """Write the dynamic state to a checkpoint file (cem_save)."""
+        self._check(self._lib.cem_save(self._ctx, os.fsencode(path)))
+
+    def load(self, path):
+        """Resume from a checkpoint written by a context of the same mesh and material (cem_load)."""
+        self._check(self._lib.cem_load(self._ctx, os.fsencode(path)))
 
     def info(self) -> dict:
         i = Info()

@@ -1,0 +1,212 @@
+// Checkpoint and resume: the dynamic state of a context to a file and back.
+//
+// A checkpoint holds everything a step reads that is not fixed by the mesh
+// description and the material: node, element and edge arrays up to their
+// current counts, the fan and incidence pools up to their tops, the crack
+// records of the input elements, the candidate list, the new-node and
+// new-edge maps, U_d and the counters.  The step's scratch (element strains,
+// edge stresses, element forces, flags) is rewritten before it is read and is
+// not saved.  A context built from the same description and material and then
+// loaded continues bit for bit as the saved one would have.
+//
+// File layout (host byte order): the 8-byte tag "CEMCKPT1", a header of int64
+// fields (HDR_* below), then every array as raw bytes in a fixed order, each
+// preceded by its byte count.
+#include "cem_common.cuh"
+
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+namespace {
+
+enum {
+    HDR_ELEM, HDR_PREC, HDR_N0, HDR_T0, HDR_E0, HDR_NC, HDR_TC, HDR_EC, HDR_FANCAP, HDR_INCCAP, HDR_HASHCAP,
+    HDR_NINST, HDR_SPLITMODE, HDR_N, HDR_T, HDR_E, HDR_NCAND, HDR_NSPLITALL, HDR_NSPLITRUN, HDR_NACTIVE,
+    HDR_FANTOP, HDR_INCTOP, HDR_STEP, HDR_DT_BITS, HDR_COUNT
+};
+const char TAG[8] = {'C', 'E', 'M', 'C', 'K', 'P', 'T', '1'};
+
+struct Field {   // one array slice: device pointer, bytes
+    void* p;
+    size_t bytes;
+};
+
+// The saved arrays, in file order (null pointers are skipped consistently on both sides).
+std::vector<Field> fields(cem_ctx* c) {
+    std::vector<Field> f;
+    auto add = [&](void* p, int64_t n, size_t esz) {
+        if (p && n > 0) f.push_back({p, (size_t)n * esz});
+    };
+    auto rows = [&](void* p, int nrow, int64_t ld, int64_t n, size_t esz) {
+        for (int r = 0; r < nrow && p; ++r) add((char*)p + (size_t)r * ld * esz, n, esz);
+    };
+    const int64_t N = c->N, T = c->T, E = c->E;
+    const bool hex = c->elem_type == CEM_ELEM_HEX8;
+    rows(c->X, 3, c->Nc, N, 8);
+    rows(c->u, 3, c->Nc, N, 8);
+    rows(c->v, 3, c->Nc, N, 8);
+    rows(c->a, 3, c->Nc, N, 8);
+    rows(c->fext, 3, c->Nc, N, 8);
+    add(c->mass, N, 8);
+    add(c->minv, N, 8);
+    add(c->inc_off, N, 4);
+    add(c->inc_cnt, N, 4);
+    add(c->dtn, N, 8);
+    add(c->node_inst, N, 4);
+    add(c->uhl, 8 * N, 4);
+    rows(c->conn, c->npe, c->Tc, T, 4);
+    rows(c->t2e, c->epe, c->Tc, T, 4);
+    add(c->anc, T, 4);
+    add(c->active, T, 1);
+    const int ng = hex ? (int)cem_hex_geometry_values() : 9;
+    rows(c->Vg, ng, c->Tc, T, 8);
+    rows(c->Vg32, ng, c->Tc, T, 4);
+    add(c->vol, T, 8);
+    add(c->lam, T, 8);
+    add(c->mu, T, 8);
+    add(c->fan_off, E, 4);
+    add(c->fan_cnt, E, 4);
+    add(c->cl, E, 8);
+    add(c->cm, E, 8);
+    add(c->sumV, E, 8);
+    add(c->cl32, E, 4);
+    add(c->cm32, E, 4);
+    add(c->fan_pool, c->fan_top, 4);
+    add(c->inc_pool, c->inc_top, 4);
+    add(c->Gc, c->T0, 8);
+    add(c->side, c->T0, 1);
+    add(c->split_step, c->T0, 4);
+    add(c->split_G, c->T0, 8);
+    add(c->ud_tet, c->T0, 8);
+    add(c->cand_flag, c->T0, 1);
+    add(c->cand_list, c->n_cand, 4);
+    add(c->node_of_key, 2 * c->E0, 4);
+    add(c->hkeys, c->hash_cap, 8);
+    add(c->hvals, c->hash_cap, 4);
+    add(c->hfirst, c->hash_cap, 4);
+    add(c->Ud, 1, 8);
+    return f;
+}
+
+void header(const cem_ctx* c, int64_t h[HDR_COUNT]) {
+    h[HDR_ELEM] = c->elem_type;
+    h[HDR_PREC] = c->precision;
+    h[HDR_N0] = c->N0;
+    h[HDR_T0] = c->T0;
+    h[HDR_E0] = c->E0;
+    h[HDR_NC] = c->Nc;
+    h[HDR_TC] = c->Tc;
+    h[HDR_EC] = c->Ec;
+    h[HDR_FANCAP] = c->fan_cap;
+    h[HDR_INCCAP] = c->inc_cap;
+    h[HDR_HASHCAP] = c->hash_cap;
+    h[HDR_NINST] = c->n_inst;
+    h[HDR_SPLITMODE] = c->split_mode;
+    h[HDR_N] = c->N;
+    h[HDR_T] = c->T;
+    h[HDR_E] = c->E;
+    h[HDR_NCAND] = c->n_cand;
+    h[HDR_NSPLITALL] = c->n_split_all;
+    h[HDR_NSPLITRUN] = c->n_split_run;
+    h[HDR_NACTIVE] = c->n_active;
+    h[HDR_FANTOP] = c->fan_top;
+    h[HDR_INCTOP] = c->inc_top;
+    h[HDR_STEP] = c->step;
+    std::memcpy(&h[HDR_DT_BITS], &c->dt, sizeof(double));
+}
+
+}  // namespace
+
+extern "C" int cem_save(cem_ctx* c, const char* path) {
+    if (!c || !path) return CEM_EINVAL;
+    if (!c->material) return cem_fail(c, CEM_ESTATE, "cem_set_material must be called before cem_save");
+    CEM_CK(c, cudaSetDevice(c->device));
+    CEM_CK(c, cudaStreamSynchronize(c->stream));
+    FILE* fp = std::fopen(path, "wb");
+    if (!fp) return cem_fail(c, CEM_EINVAL, "cannot open the checkpoint file for writing");
+    int64_t h[HDR_COUNT];
+    header(c, h);
+    bool ok = std::fwrite(TAG, 1, 8, fp) == 8 && std::fwrite(h, sizeof(int64_t), HDR_COUNT, fp) == HDR_COUNT;
+    std::vector<char> buf;
+    for (const Field& f : fields(c)) {
+        if (!ok) break;
+        buf.resize(f.bytes);
+        if (cudaMemcpy(buf.data(), f.p, f.bytes, cudaMemcpyDeviceToHost) != cudaSuccess) {
+            std::fclose(fp);
+            return cem_fail(c, CEM_ECUDA, "device to host copy of the checkpoint");
+        }
+        const int64_t nb = (int64_t)f.bytes;
+        ok = std::fwrite(&nb, sizeof nb, 1, fp) == 1 && std::fwrite(buf.data(), 1, f.bytes, fp) == f.bytes;
+    }
+    ok = (std::fclose(fp) == 0) && ok;
+    return ok ? CEM_OK : cem_fail(c, CEM_EINVAL, "writing the checkpoint file failed");
+}
+
+extern "C" int cem_load(cem_ctx* c, const char* path) {
+    if (!c || !path) return CEM_EINVAL;
+    if (!c->material) return cem_fail(c, CEM_ESTATE, "cem_set_material must be called before cem_load");
+    CEM_CK(c, cudaSetDevice(c->device));
+    CEM_CK(c, cudaStreamSynchronize(c->stream));
+    FILE* fp = std::fopen(path, "rb");
+    if (!fp) return cem_fail(c, CEM_EINVAL, "cannot open the checkpoint file");
+    char tag[8];
+    int64_t h[HDR_COUNT], mine[HDR_COUNT];
+    if (std::fread(tag, 1, 8, fp) != 8 || std::memcmp(tag, TAG, 8) != 0 ||
+        std::fread(h, sizeof(int64_t), HDR_COUNT, fp) != HDR_COUNT) {
+        std::fclose(fp);
+        return cem_fail(c, CEM_EINVAL, "not a checkpoint file");
+    }
+    header(c, mine);
+    for (int q = HDR_ELEM; q <= HDR_SPLITMODE; ++q)
+        if (h[q] != mine[q]) {
+            std::fclose(fp);
+            return cem_fail(c, CEM_EINVAL, "checkpoint of a different mesh, precision or capacity");
+        }
+    if (h[HDR_DT_BITS] != mine[HDR_DT_BITS]) {
+        std::fclose(fp);
+        return cem_fail(c, CEM_EINVAL, "checkpoint with a different time step (material)");
+    }
+    // counts within the context's capacities (the file is not trusted)
+    const bool sizes_ok = h[HDR_N] >= c->N0 && h[HDR_N] <= c->Nc && h[HDR_T] >= c->T0 && h[HDR_T] <= c->Tc &&
+                          h[HDR_E] >= c->E0 && h[HDR_E] <= c->Ec && h[HDR_NCAND] >= 0 && h[HDR_NCAND] <= c->T0 &&
+                          h[HDR_FANTOP] >= 0 && h[HDR_FANTOP] <= c->fan_cap && h[HDR_INCTOP] >= 0 &&
+                          h[HDR_INCTOP] <= c->inc_cap && h[HDR_NSPLITALL] >= 0 && h[HDR_NSPLITALL] <= c->S_cap &&
+                          h[HDR_NSPLITRUN] >= 0 && h[HDR_NACTIVE] >= 0 && h[HDR_NACTIVE] <= h[HDR_T] &&
+                          h[HDR_STEP] >= 0;
+    if (!sizes_ok) {
+        std::fclose(fp);
+        return cem_fail(c, CEM_EINVAL, "checkpoint counts exceed the context's capacities");
+    }
+    // adopt the saved counts, then read the arrays they size
+    c->N = h[HDR_N];
+    c->T = h[HDR_T];
+    c->E = h[HDR_E];
+    c->n_cand = h[HDR_NCAND];
+    c->n_split_all = h[HDR_NSPLITALL];
+    c->n_split_run = h[HDR_NSPLITRUN];
+    c->n_active = h[HDR_NACTIVE];
+    c->fan_top = h[HDR_FANTOP];
+    c->inc_top = h[HDR_INCTOP];
+    c->step = h[HDR_STEP];
+    std::vector<char> buf;
+    for (const Field& f : fields(c)) {
+        int64_t nb = 0;
+        if (std::fread(&nb, sizeof nb, 1, fp) != 1 || nb != (int64_t)f.bytes) {
+            std::fclose(fp);
+            return cem_fail(c, CEM_EINVAL, "checkpoint file truncated or inconsistent; context state undefined");
+        }
+        buf.resize(f.bytes);
+        if (std::fread(buf.data(), 1, f.bytes, fp) != f.bytes) {
+            std::fclose(fp);
+            return cem_fail(c, CEM_EINVAL, "checkpoint file truncated; context state undefined");
+        }
+        if (cudaMemcpy(f.p, buf.data(), f.bytes, cudaMemcpyHostToDevice) != cudaSuccess) {
+            std::fclose(fp);
+            return cem_fail(c, CEM_ECUDA, "host to device copy of the checkpoint");
+        }
+    }
+    std::fclose(fp);
+    CEM_CK(c, cudaDeviceSynchronize());
+    return CEM_OK;
+}
