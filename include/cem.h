@@ -47,9 +47,9 @@ extern "C" {
 #define CEM_EINVAL     -1   /* bad argument or malformed mesh                        */
 #define CEM_ENOMEM     -2   /* the allocator returned NULL                           */
 #define CEM_ECUDA      -3   /* a CUDA runtime call failed                            */
-#define CEM_ECAPACITY  -4   /* split capacity exhausted; state left at step start   */
+#define CEM_ECAPACITY  -4   /* split or storage capacity exhausted (see cem_step)    */
 #define CEM_ENONFINITE -5   /* a non-finite displacement was produced               */
-#define CEM_ETIMEOUT   -6   /* reserved: a bounded device wait gave up              */
+#define CEM_ETIMEOUT   -6   /* a bounded device wait gave up (see cem_set_wait_limit)*/
 #define CEM_ESTATE     -7   /* call not valid in the context's current state        */
 
 /* precision of the force evaluation */
@@ -199,9 +199,26 @@ int cem_set_material(cem_ctx* ctx, double rho, double nu,
  * each step the energy release rates G_I, G_II (Eqs. 16-18) of every
  * crack-front element are evaluated on the end-of-step state, and every
  * element with max(G_I, G_II) > Gc is split (Sec. 3).  Errors: CEM_ESTATE
- * (no material), CEM_ECAPACITY (state left at the last completed step),
+ * (no material); CEM_ECAPACITY: when the split capacity would be exceeded the
+ * splits of that step are not applied and the state is the step's
+ * end-of-step kinematics (the context stays usable); when a storage
+ * capacity (new edges, nodes, fan or incidence pool) runs out while splits
+ * are applied, the step's topology is partly updated and the context should
+ * be destroyed; CEM_ETIMEOUT (a bounded device wait gave up; as the second
+ * ECAPACITY case); CEM_ENONFINITE (a displacement became non-finite);
  * CEM_ECUDA. */
 int cem_step(cem_ctx* ctx, int64_t n);
+
+/* Bounded device waits.  Every spin-wait in the library's kernels (the
+ * look-back of the ordered scans) gives up after a number of polls, records
+ * an error flag and returns; the host then reports CEM_ETIMEOUT instead of
+ * hanging.  cem_set_wait_limit sets that number (spins > 0; 0 restores the
+ * default of 4,194,304 polls, about a second).  cem_wait_probe runs one
+ * bounded wait on a device flag that nothing sets, as a check of this path:
+ * it returns CEM_ETIMEOUT after the limit and leaves the context usable.
+ * Neither has a counterpart in the paper. */
+int cem_set_wait_limit(cem_ctx* ctx, int64_t spins);
+int cem_wait_probe(cem_ctx* ctx);
 
 /* Discrete adjoint of n_steps explicit steps from the current state, with the
  * topology fixed (requires split_enabled = 0; one specimen).  Objective

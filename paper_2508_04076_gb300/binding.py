@@ -27,7 +27,8 @@ FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_void_p)
 
 EXPORTED = ["cem_mesh_create", "cem_set_material", "cem_step", "cem_energy", "cem_crack_state",
             "cem_get_field", "cem_info", "cem_energy_instance", "cem_adjoint", "cem_profile", "cem_profile_read",
-            "cem_autotune", "cem_tune_get", "cem_tune_set", "cem_save", "cem_load", "cem_probe_fp64_fma", "cem_destroy", "cem_last_error"]
+            "cem_autotune", "cem_tune_get", "cem_tune_set", "cem_save", "cem_load", "cem_set_wait_limit",
+            "cem_wait_probe", "cem_probe_fp64_fma", "cem_destroy", "cem_last_error"]
 TUNED = ["strain", "edge_stress", "force", "node_update"]
 KERNELS = ["predict", "strain", "edge_stress", "force", "node_update", "front_G", "split"]
 
@@ -95,6 +96,8 @@ def load_library(build: bool = True):
     lib.cem_autotune.argtypes = [P, C.c_char_p, C.c_int, C.c_int]
     lib.cem_tune_set.argtypes = [P, C.c_int, C.c_int, C.c_int]
     lib.cem_save.argtypes = [P, C.c_char_p]
+    lib.cem_set_wait_limit.argtypes = [P, C.c_int64]
+    lib.cem_wait_probe.argtypes = [P]
     lib.cem_load.argtypes = [P, C.c_char_p]
     lib.cem_tune_get.argtypes = [P, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_double),
                                  C.POINTER(C.c_double)]
@@ -297,6 +300,14 @@ class CEM:
     def load(self, path):
         """Resume from a checkpoint written by a context of the same mesh and material (cem_load)."""
         self._check(self._lib.cem_load(self._ctx, os.fsencode(path)))
+
+    def set_wait_limit(self, spins=0):
+        """Polls before a bounded device wait gives up (0: the default)."""
+        self._check(self._lib.cem_set_wait_limit(self._ctx, int(spins)))
+
+    def wait_probe(self):
+        """Run one bounded wait on a flag nothing sets; raises CEMError(CEM_ETIMEOUT)."""
+        self._check(self._lib.cem_wait_probe(self._ctx))
 
     def info(self) -> dict:
         i = Info()

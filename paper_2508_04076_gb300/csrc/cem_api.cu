@@ -9,6 +9,8 @@
 // the split sequence.
 #include "cem_common.cuh"
 
+#include <nvtx3/nvToolsExt.h>   // header-only; ranges cost nothing unless a profiler is attached
+
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -778,7 +780,14 @@ int prof_resolve(cem_ctx* c) {
         if (rc_) return rc_;               \
     } while (0)
 
+// NVTX range for the duration of a scope (seen by nsys / ncu timelines)
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+};
+
 int run_step(cem_ctx* c) {
+    NvtxRange range("cem.step");
     if (c->tune_auto)
         if (int rc = cem_tune_maybe(c)) return rc;
     c->prof_now = c->prof && (c->step % c->prof_every == 0);
@@ -791,7 +800,10 @@ int run_step(cem_ctx* c) {
     if (int rc = cem_launch_prescribe(c, c->step + 1)) return rc;
     c->step += 1;
     if (c->split_enabled && c->n_cand > 0) {
-        TIMED(c, CEM_KERNEL_FRONT_G, cem_launch_front_G(c));
+        {
+            NvtxRange front("cem.front_G");
+            TIMED(c, CEM_KERNEL_FRONT_G, cem_launch_front_G(c));
+        }
         int rc;
         if ((rc = sync_counts(c))) return rc;
         if (c->hcount[CNT_ERR] & DERR_SCAN_WAIT)
@@ -800,6 +812,7 @@ int run_step(cem_ctx* c) {
         if (S > 0) {
             if (c->n_split_all + S > c->S_cap)
                 return cem_fail(c, CEM_ECAPACITY, "split capacity exhausted; splits of this step not applied");
+            NvtxRange split("cem.split");
             TIMED(c, CEM_KERNEL_SPLIT, cem_apply_splits(c, S, c->step, 1));
         }
     }

@@ -168,6 +168,7 @@ struct cem_ctx {
     unsigned long long* scan_status = nullptr;          // look-back status words, one per block
     unsigned int* scan_ticket = nullptr;                // block tickets of the running scan
     unsigned long long scan_epoch = 0;
+    long long wait_limit = 1ll << 22;   // polls of a bounded device wait before it gives up
     // reductions
     double* red_part = nullptr;   // block partials
     double* red_out = nullptr;    // final values

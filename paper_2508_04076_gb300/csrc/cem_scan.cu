@@ -37,6 +37,45 @@ struct PosStore {     // scan: index -> position
 
 int64_t cem_scan_blocks_needed(int64_t n) { return (n + SCHUNK - 1) / SCHUNK + 2; }
 
+namespace {
+// One bounded wait on a flag that nothing sets, polled like the scans' look-back:
+// after `limit` polls it records the timeout flag and returns.
+__global__ void k_wait_probe(const unsigned long long* flag, long long limit, long long* err) {
+    long long spins = 0;
+    while (*((volatile const unsigned long long*)flag) == 0ull) {
+        if (++spins > limit) {
+            atomicOr((unsigned long long*)err, (unsigned long long)DERR_SCAN_WAIT);
+            return;
+        }
+    }
+}
+}  // namespace
+
+extern "C" int cem_set_wait_limit(cem_ctx* c, int64_t spins) {
+    if (!c || spins < 0) return CEM_EINVAL;
+    c->wait_limit = spins > 0 ? spins : (1ll << 22);
+    return CEM_OK;
+}
+
+extern "C" int cem_wait_probe(cem_ctx* c) {
+    if (!c) return CEM_EINVAL;
+    CEM_CK(c, cudaSetDevice(c->device));
+    // the flag: a zeroed counter slot that no kernel writes
+    CEM_CK(c, cudaMemsetAsync(c->dcount + CNT_SCRATCH1, 0, sizeof(long long), c->stream));
+    CEM_CK(c, cudaMemsetAsync(c->dcount + CNT_ERR, 0, sizeof(long long), c->stream));
+    k_wait_probe<<<1, 1, 0, c->stream>>>((const unsigned long long*)(c->dcount + CNT_SCRATCH1), c->wait_limit,
+                                         c->dcount + CNT_ERR);
+    cem_launched(c);
+    CEM_CK(c, cudaGetLastError());
+    long long e = 0;
+    CEM_CK(c, cudaMemcpyAsync(&e, c->dcount + CNT_ERR, sizeof e, cudaMemcpyDeviceToHost, c->stream));
+    CEM_CK(c, cudaStreamSynchronize(c->stream));
+    CEM_CK(c, cudaMemsetAsync(c->dcount + CNT_ERR, 0, sizeof(long long), c->stream));
+    CEM_CK(c, cudaStreamSynchronize(c->stream));
+    if (e & DERR_SCAN_WAIT) return cem_fail(c, CEM_ETIMEOUT, "the probe's bounded wait gave up, as it should");
+    return CEM_OK;
+}
+
 int cem_compact_u8(cem_ctx* c, const uint8_t* flags, int64_t n, int* idx, int slot) {
     return run_scan(c, FlagLoad{flags}, IndexStore{idx}, n, slot);
 }

@@ -43,12 +43,12 @@ __device__ int block_excl_scan(int x, int* total) {
 }
 
 constexpr unsigned long long FLAG_AGG = 1ull << 32, FLAG_INC = 2ull << 32, FLAG_MASK = 3ull << 32;
-constexpr long long SPIN_LIMIT = 1ll << 22;   // about a second of polling
 
 template <class Load, class Store>
 __global__ void __launch_bounds__(SB) k_scan_single(Load ld, Store st, int64_t n, int nb,
                                                     unsigned long long* status, unsigned int* ticket,
-                                                    unsigned long long epoch, long long* count, long long* err) {
+                                                    unsigned long long epoch, long long* count, long long* err,
+                                                    long long spin_limit) {
     CEM_PDL_ENTRY();
     __shared__ int s_bid, s_prefix;
     if (threadIdx.x == 0) s_bid = (int)atomicAdd(ticket, 1u);
@@ -80,7 +80,7 @@ __global__ void __launch_bounds__(SB) k_scan_single(Load ld, Store st, int64_t n
             if (idx >= 0) w = *((volatile unsigned long long*)&status[idx]);
             const bool ready = ((w >> 34) == epoch) && (w & FLAG_MASK);
             if (!__all_sync(0xffffffffu, ready)) {
-                if (++spins > SPIN_LIMIT) {
+                if (++spins > spin_limit) {
                     if (lane == 0) atomicOr((unsigned long long*)err, 4ull);
                     break;
                 }
@@ -132,7 +132,7 @@ int run_scan(cem_ctx* c, Load ld, Store st, int64_t n, int slot) {
         return cem_fail(c, CEM_EINVAL, "internal: scan longer than its status buffer");
     const unsigned long long epoch = ++c->scan_epoch & ((1ull << 30) - 1);
     cem_pdl(c->stream, (k_scan_single<Load, Store>), (unsigned)nb, SB, ld, st, n, (int)nb, c->scan_status,
-            c->scan_ticket, epoch, c->dcount + slot, c->dcount + CNT_ERR);
+            c->scan_ticket, epoch, c->dcount + slot, c->dcount + CNT_ERR, c->wait_limit);
     cem_launched(c, 1);
     CEM_CK(c, cudaGetLastError());
     return CEM_OK;

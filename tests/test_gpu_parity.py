@@ -183,3 +183,60 @@ def test_full_size_workload_first_steps(CEM):
     o.step(4)
     sim.step(4)
     _compare(sim, o)
+
+
+def test_bounded_wait_times_out_and_context_survives(CEM):
+    """A bounded device wait on a flag nothing sets gives up, the call reports
+    CEM_ETIMEOUT, and the context keeps working."""
+    from paper_2508_04076_gb300 import CEMError
+    from paper_2508_04076_gb300.binding import CEM_ETIMEOUT
+    w = plate_small()
+    sim = CEM.from_workload(w)
+    o = CEMOracle.from_workload(w)
+    sim.set_wait_limit(20000)
+    with pytest.raises(CEMError) as ex:
+        sim.wait_probe()
+    assert ex.value.code == CEM_ETIMEOUT
+    sim.set_wait_limit(0)
+    sim.step(200)
+    o.step(200)
+    _compare(sim, o)
+
+
+def test_allocation_failure_reports_enomem_without_leaks(CEM):
+    """An allocator hook that fails partway makes cem_mesh_create return CEM_ENOMEM and
+    release what it had taken."""
+    import ctypes as C
+    import torch
+    from paper_2508_04076_gb300 import load_library
+    from paper_2508_04076_gb300.binding import ALLOC_FN, FREE_FN, MeshDesc, _ptr
+    lib = load_library()
+    w = plate_small()
+    X = np.ascontiguousarray(w.X, np.float64)
+    tets = np.ascontiguousarray(w.tets, np.int32)
+    live = {}
+    budget = [12]
+
+    def alloc(nbytes, stream, user):
+        if budget[0] <= 0:
+            return None
+        budget[0] -= 1
+        p = torch.cuda.caching_allocator_alloc(int(nbytes), 0, int(stream or 0))
+        live[p] = nbytes
+        return p
+
+    def free(ptr, stream, user):
+        live.pop(int(ptr))
+        torch.cuda.caching_allocator_delete(int(ptr))
+
+    a_cb, f_cb = ALLOC_FN(alloc), FREE_FN(free)
+    d = MeshDesc()
+    d.n_nodes, d.n_tets = X.shape[0], tets.shape[0]
+    d.X, d.tets = _ptr(X, C.c_double), _ptr(tets, C.c_int32)
+    d.precision, d.split_enabled = 0, 1
+    d.stream = torch.cuda.current_stream().cuda_stream
+    d.alloc, d.free = a_cb, f_cb
+    ctx = C.c_void_p()
+    rc = lib.cem_mesh_create(C.byref(d), C.byref(ctx))
+    assert rc == -2 and not ctx.value
+    assert live == {}
