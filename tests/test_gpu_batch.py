@@ -91,3 +91,34 @@ def test_union_rejects_shared_nodes(CEM):
     with pytest.raises(CEMError) as e:
         CEM(w.X, w.tets, w.tfaces, w.tvec, tet_instance=inst)
     assert e.value.code == -1
+
+
+def test_full_ensemble_sampled_members(CEM):
+    """The 256-specimen ensemble (about 2.6e7 elements, mixed precision, split capacity
+    a quarter of the elements, as the benchmark runs it) for 200 steps: its three
+    smallest specimens match separate oracle runs (1e-4, split-set agreement >= 0.99),
+    and every specimen's energies are finite."""
+    from cem_inputs import ensemble, ensemble_members
+    members = ensemble_members()
+    w = ensemble()
+    assert w.params["n_instances"] == 256 and w.n_tets > 2.5e7
+    sim = CEM.from_workload(w, precision="mixed", split_capacity=w.n_tets // 4)
+    steps = 200
+    sim.step(steps)
+    u_all = sim.field("u")
+    crack = sim.crack_state()
+    toff = w.params["tet_offsets"]
+    for i in np.argsort([m.n_tets for m in members])[:3]:
+        o = CEMOracle.from_workload(members[i])
+        o.step(steps)
+        u_i = _instance_view(sim, u_all, w, i)
+        assert u_i.shape == o.u.shape, (i, u_i.shape, o.u.shape)
+        assert np.linalg.norm(u_i - o.u) <= 1e-4 * np.linalg.norm(o.u), i
+        recs = {(r[0] - toff[i], r[3]) for r in crack if toff[i] <= r[0] < toff[i + 1]}
+        ref = {(r[0], r[3]) for r in o.crack_state()}
+        assert len(recs & ref) / max(len(recs | ref), 1) >= 0.99, i
+        e, eo = sim.energy_instance(int(i)), o.energy()
+        assert abs(e["kinetic"] - eo["kinetic"]) <= 1e-4 * max(eo["kinetic"], eo["strain"])
+    for i in range(0, 256, 51):
+        e = sim.energy_instance(i)
+        assert all(np.isfinite(e[k]) for k in ("kinetic", "strain", "ext_work"))
