@@ -110,6 +110,12 @@ def _args():
     p.add_argument("--no-autotune", action="store_true", help="keep the default launch variants")
     p.add_argument("--split-capacity", type=int, default=0,
                    help="max elements that may split (0: all); lower it to shrink device memory for profiling")
+    p.add_argument("--state", help="checkpoint file for --save-at / --resume")
+    p.add_argument("--save-at", type=int, default=0,
+                   help="run the benchmark workload this many steps, write its state to --state and exit "
+                        "(to profile a late window of the job without replaying it)")
+    p.add_argument("--resume", action="store_true",
+                   help="load --state into a fresh context and time --steps steps from there, then exit")
     p.add_argument("--cpu-baseline-worker", action="store_true", help=argparse.SUPPRESS)
     p.add_argument("--cpu-steps", type=int, default=12, help=argparse.SUPPRESS)
     return p.parse_args()
@@ -256,6 +262,33 @@ def run_cem(a):
     if a.workload == "ensemble" and a.split_capacity == 0:
         a.split_capacity = w.n_tets // 4
     stream = torch.cuda.current_stream(dev)
+    if a.save_at > 0 or a.resume:   # checkpointed windows of the job (profiling aid)
+        if not a.state:
+            raise SystemExit("--save-at and --resume need --state PATH")
+        sim = CEM.from_workload(w, device=dev, split_capacity=a.split_capacity, precision=a.precision)
+        if not a.no_autotune:
+            sim.autotune(reps=10, automatic=True)
+        if a.save_at > 0:
+            sim.step(a.save_at)
+            sim.save(a.state)
+            info = sim.info()
+            print(json.dumps({"saved": a.state, "step": a.save_at, "elements": info["n_active_tets"],
+                              "nodes": info["n_nodes"], "edges": info["n_edges"]}), flush=True)
+        else:
+            sim.load(a.state)
+            step0 = sim.energy()["step"]
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            sim.step(a.steps)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            info = sim.info()
+            print(json.dumps({"resumed": a.state, "from_step": step0, "steps": a.steps,
+                              "ms_per_step": e0.elapsed_time(e1) / max(a.steps, 1),
+                              "elements": info["n_active_tets"], "nodes": info["n_nodes"],
+                              "edges": info["n_edges"]}), flush=True)
+        sim.close()
+        return
     peaks = _peaks()
     hbm = peaks.get("hbm_gbs")
     fp64_peak_meas = probe_fp64_fma(dev, stream.cuda_stream)
