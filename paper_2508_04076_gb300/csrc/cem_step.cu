@@ -233,6 +233,9 @@ __global__ void __launch_bounds__(TB) k_edge_stress(const R* __restrict__ h, con
     int64_t k = (int64_t)blockIdx.x * TB + threadIdx.x;
     if (k >= E) return;
     const int off = fan_off[k], cnt = fan_cnt[k];
+    // An edge whose fan emptied (every element around it split) is read by no
+    // active element: its stress is left as it was (finite; its energy term has H = 0).
+    if (cnt == 0) return;
     R H[6] = {0, 0, 0, 0, 0, 0};
     int i = 0;
     if constexpr (FB > 1) {
@@ -562,6 +565,7 @@ __global__ void __launch_bounds__(RB) k_energy_edges(const R* __restrict__ h, co
     double x[1] = {0};
     for (int64_t k = (int64_t)blockIdx.x * RB + threadIdx.x; k < E; k += (int64_t)RG * RB) {
         const int off = fan_off[k], cnt = fan_cnt[k];
+        if (cnt == 0) continue;   // an emptied fan holds no energy
         double H[6] = {0, 0, 0, 0, 0, 0};
         for (int i = 0; i < cnt; ++i) {
             R y[6];
