@@ -37,6 +37,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "tet-steps/s"
+CHUNK_STEPS = 500    # steps between host reads of the mesh counts in the timed region
 PROFILE_EVERY = 16   # kernel timing sampled on every 16th step (events between kernels block launch overlap)
 WORKLOAD = "notched_block_200x80x10"
 
@@ -306,8 +307,23 @@ def run_cem(a):
         clocks = ClockSampler(_bus_id(dev)) if (clocks_on and rank == 0) else None
         sim.profile(max(1, min(PROFILE_EVERY, steps // 4)))   # at least a few sampled steps
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        # The mesh grows during the run, so the sampled launches' units (elements, edges, nodes)
+        # are integrated chunk by chunk: each chunk's sampled kernel time is paired with the mean
+        # of its first and last counts.  The counts and timing sums are read on the host between
+        # chunks; every step already ends with a host read of its split count.
+        chunks = []
+        c_prev, p_prev = sim.info(), {k: (0.0, 0) for k in KERNEL_UNITS}
         e0.record(stream)
-        sim.step(steps)
+        done = 0
+        while done < steps:
+            n = min(CHUNK_STEPS, steps - done)
+            sim.step(n)
+            done += n
+            c_now = sim.info()
+            p_now = sim.profile_read()[0]
+            chunks.append(({u: (c_prev[u] + c_now[u]) / 2.0 for u in ("n_active_tets", "n_edges", "n_nodes")},
+                           {k: (p_now[k][0] - p_prev[k][0], p_now[k][1] - p_prev[k][1]) for k in KERNEL_UNITS}))
+            c_prev, p_prev = c_now, {k: p_now[k] for k in KERNEL_UNITS}
         e1.record(stream)
         torch.cuda.synchronize()
         t_ms = e0.elapsed_time(e1)
@@ -323,11 +339,6 @@ def run_cem(a):
         energy = sim.energy()
         tuning = {k: {"block": v[0], "batch": v[1]} for k, v in sim.tuning().items()}
         sim.close()
-        Tm = (info0["n_tets"] + info["n_tets"]) / 2.0
-        Ta = (info0["n_active_tets"] + info["n_active_tets"]) / 2.0
-        Em = (info0["n_edges"] + info["n_edges"]) / 2.0
-        Nm = (info0["n_nodes"] + info["n_nodes"]) / 2.0
-        fl, by = kernel_costs(Ta, Em, Nm, precision)
         sm_clock = (clk or {}).get("sm_max_mhz") or peaks.get("sm_max_mhz") or 2070.0
         fp64_peak = 152 * 4 * sm_clock * 1e6      # 152 SMs x 2 FP64 FMA/clk x 2 FLOP
         # timed launches are a sample (every PROFILE_EVERY-th step): scale sums to the whole region
@@ -335,21 +346,33 @@ def run_cem(a):
         if prof["strain"][1] == 0:
             raise RuntimeError("no sampled step in the timed region")
         scale = steps / n_sampled
+        # algorithmic bytes, flops, units and DRAM traffic of the sampled launches, summed over chunks
+        acc = {k: dict(bytes=0.0, flops=0.0, units=0.0, traffic=0.0) for k in KERNEL_UNITS}
+        for cnt, dp in chunks:
+            fl, by = kernel_costs(cnt["n_active_tets"], cnt["n_edges"], cnt["n_nodes"], precision)
+            per_unit = DRAM_BYTES_PER_UNIT.get(precision, {})
+            for k, (_, nl) in dp.items():
+                units = {"tets": cnt["n_active_tets"], "edges": cnt["n_edges"], "nodes": cnt["n_nodes"]}[
+                    KERNEL_UNITS[k]]
+                acc[k]["bytes"] += nl * by[k] * units
+                acc[k]["flops"] += nl * fl[k] * units
+                acc[k]["units"] += nl * units
+                acc[k]["traffic"] += nl * per_unit.get(k, 0.0) * units
         kernels = {}
         for k, (ms_tot, nl) in prof.items():
             kernels[k] = {"ms": ms_tot * scale, "launches_timed": nl, "share": ms_tot * scale / max(t_ms, 1e-9)}
             if k in KERNEL_UNITS and nl:
-                units = {"tets": Tm, "edges": Em, "nodes": Nm}[KERNEL_UNITS[k]]
-                sec = ms_tot * 1e-3 / nl
-                kernels[k].update(per_launch_us=sec * 1e6, gbs=by[k] * units / sec / 1e9)
+                sec = ms_tot * 1e-3
+                kernels[k].update(per_launch_us=sec / nl * 1e6, gbs=acc[k]["bytes"] / sec / 1e9)
                 if precision == "fp64":
-                    kernels[k]["fp64_tflops"] = fl[k] * units / sec / 1e12
+                    kernels[k]["fp64_tflops"] = acc[k]["flops"] / sec / 1e12
         hot = {k: prof[k] for k in KERNEL_UNITS}
         dom = max(hot, key=lambda k: hot[k][0])
         ms_tot, nl = hot[dom]
-        per_launch_s = ms_tot * 1e-3 / max(nl, 1)
-        units = {"tets": Tm, "edges": Em, "nodes": Nm}[KERNEL_UNITS[dom]]
-        flops, bytes_ = fl[dom] * units, by[dom] * units
+        nl = max(nl, 1)
+        per_launch_s = ms_tot * 1e-3 / nl
+        units = acc[dom]["units"] / nl
+        flops, bytes_ = acc[dom]["flops"] / nl, acc[dom]["bytes"] / nl
         alu_bound = precision == "fp64" and flops / fp64_peak > bytes_ / ((hbm or 6651.4) * 1e9)
         if alu_bound:
             achieved, peak, unit = flops / per_launch_s / 1e12, fp64_peak / 1e12, "TFLOP/s"
@@ -357,15 +380,16 @@ def run_cem(a):
         else:
             achieved, peak, unit = bytes_ / per_launch_s / 1e9, hbm, "GB/s"
             src = "MEASURED_PEAKS.json hbm_gbs (measured copy bandwidth)"
-        per_unit = DRAM_BYTES_PER_UNIT.get(precision, {}).get(dom)
-        traffic = per_unit * units if per_unit is not None else None
+        traffic = acc[dom]["traffic"] / nl if dom in DRAM_BYTES_PER_UNIT.get(precision, {}) else None
         roofline = {"bound": "alu" if alu_bound else "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
                     "unit": unit, "frac": achieved / peak, "traffic": traffic, "peak_source": src,
                     "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum per unit on the 960,000-"
-                                       "element block, scaled to this launch's units" if traffic else None),
+                                       "element block, scaled to the units of each sampled launch" if traffic
+                                       else None),
                     "per_launch_us": per_launch_s * 1e6, "algorithmic_bytes_per_launch": bytes_,
                     "hbm_gbs_achieved": bytes_ / per_launch_s / 1e9, "hbm_peak_gbs": hbm,
-                    "units_per_launch": units}
+                    "units_per_launch": units, "units_integrated_over": "%d chunks of <= %d steps" % (
+                        len(chunks), CHUNK_STEPS)}
         if precision == "fp64":
             roofline.update(algorithmic_flops_per_launch=flops, fp64_tflops_achieved=flops / per_launch_s / 1e12,
                             fp64_peak_tflops=fp64_peak / 1e12, fp64_fma_measured_tflops=fp64_peak_meas / 1e12)

@@ -548,6 +548,10 @@ int create_impl(const cem_mesh_desc* d, cem_ctx* c) {
     ok = ok && dalloc(c, c->split_G, T0) && dalloc(c, c->Gc, T0) && dalloc(c, c->oe_n0, E0) && dalloc(c, c->oe_n1, E0);
     ok = ok && dalloc(c, c->node_of_key, 2 * E0) && dalloc(c, c->cand_flag, T0) && dalloc(c, c->cand_list, T0);
     ok = ok && dalloc(c, c->dec_mask, T0) && dalloc(c, c->dec_G, T0) && dalloc(c, c->split_list, T0);
+    c->front_cap = std::min<int64_t>(T0, 1 << 16);
+    const int64_t ff = 4 * c->front_cap;
+    ok = ok && dalloc(c, c->ff_mask, ff) && dalloc(c, c->ff_prod, 4 * ff) && dalloc(c, c->ff_nrm, 6 * ff) &&
+         dalloc(c, c->ff_edge, 3 * ff) && dalloc(c, c->ff_item, 3 * ff) && dalloc(c, c->ff_s, 3 * ff);
     ok = ok && dalloc(c, c->split_mask, T0) && dalloc(c, c->split_Gv, T0) && dalloc(c, c->ud_part, T0);
     ok = ok && dalloc(c, c->Ud, 1) && dalloc(c, c->ud_tet, T0);
     if (c->n_inst > 1)

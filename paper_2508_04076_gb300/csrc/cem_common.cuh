@@ -67,6 +67,7 @@ enum {
     CNT_ERR,           // device-side error flags (bit mask)
     CNT_SCRATCH0,
     CNT_SCRATCH1,
+    CNT_FRONT_Q,       // queued edge projections of a front evaluation (0 between evaluations)
     CNT_COUNT
 };
 
@@ -149,6 +150,15 @@ struct cem_ctx {
     int* cand_list = nullptr;
     uint8_t* dec_mask = nullptr;
     double* dec_G = nullptr;
+    // front evaluation, in chunks of front_cap candidates: per (candidate, face) records
+    // and a dense queue of the faces' edge projections
+    int64_t front_cap = 0;
+    int* ff_mask = nullptr;            // [4 cap] 0: face not cut twice, else mask_I | mask_II << 4
+    double* ff_prod = nullptr;         // [4][4 cap] |d1.n_I|, |d2.n_I|, |d1.n_II|, |d2.n_II|
+    double* ff_nrm = nullptr;          // [6][4 cap] n_I, n_II
+    int* ff_edge = nullptr;            // [3][4 cap] edges ad, bd, cd
+    int* ff_item = nullptr;            // [12 cap] queued projections: 3 face + q
+    double* ff_s = nullptr;            // [12 cap] s of projection 3 face + q
     int* split_list = nullptr;         // [T0] this step's split parents (ascending)
     uint8_t* split_mask = nullptr;     // [T0]
     double* split_Gv = nullptr;        // [T0]

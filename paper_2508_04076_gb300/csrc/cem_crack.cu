@@ -29,6 +29,7 @@
 // scans, so the topology is identical on every run.
 #include "cem_scan.cuh"
 
+#include <algorithm>
 #include <climits>
 
 namespace {
@@ -155,29 +156,35 @@ __device__ __forceinline__ double edge_projection(const double* sig64, const flo
 
 __device__ __forceinline__ int normalize_side(int m) { return (m & 1) ? ((~m) & 15) : m; }
 
-// One thread per (candidate, local face f); the four faces of a candidate are
-// neighbouring lanes of one warp and are reduced with shuffles: largest G,
-// ties to the lowest face.
-__global__ void __launch_bounds__(BS) k_front_G(const int* __restrict__ cand_list, int n_cand,
-                                                const int* __restrict__ conn, const int* __restrict__ t2e, int64_t Tc,
-                                                const int* __restrict__ face_nbr, const uint8_t* __restrict__ side,
-                                                int64_t T0, const double* __restrict__ X, const double* __restrict__ u,
-                                                int64_t Nc, const double* __restrict__ sig,
-                                                const float* __restrict__ sig32,
-                                                const double* __restrict__ Gc, int gvar,
-                                                uint8_t* __restrict__ dec_mask, double* __restrict__ dec_G,
-                                                long long* __restrict__ nk) {
+// The front evaluation runs as three kernels so that the FP64 work, which
+// GB300 issues at a small fraction of its FP32 rate, fills whole warps and
+// spreads over every SM:
+//   k_front_faces  one thread per (candidate, local face f): the face test,
+//                  stretches and normals; a face cut twice queues its three
+//                  edge projections;
+//   k_front_proj   one thread per queued projection s(k, n);
+//   k_front_pick   one thread per candidate: G_I, G_II of its faces and the
+//                  largest, ties to the lowest face.
+constexpr int FB = 64;   // threads per block of the front kernels (small blocks reach every SM)
+
+__global__ void __launch_bounds__(FB) k_front_faces(const int* __restrict__ cand, int nc,
+                                                    const int* __restrict__ conn, const int* __restrict__ t2e,
+                                                    int64_t Tc, const int* __restrict__ face_nbr,
+                                                    const uint8_t* __restrict__ side, int64_t T0,
+                                                    const double* __restrict__ X, const double* __restrict__ u,
+                                                    int64_t Nc, int* __restrict__ ff_mask,
+                                                    double* __restrict__ ff_prod, double* __restrict__ ff_nrm,
+                                                    int* __restrict__ ff_edge, int64_t cap4,
+                                                    int* __restrict__ items, long long* __restrict__ qn) {
     CEM_PDL_ENTRY();
-    if (blockIdx.x == 0 && threadIdx.x == 0) *nk = 0;   // new-key counter of this step's splits
-    const int tid = blockIdx.x * BS + threadIdx.x;
+    const int tid = blockIdx.x * FB + threadIdx.x;   // face record 4 ci + f of this chunk
     const int ci = tid >> 2, f = tid & 3;
-    double G = -1.0 / 0.0;
-    int mask = 0;
-    int t = -1;
-    if (ci < n_cand) {
-        t = cand_list[ci];
+    bool cut = false;
+    if (ci < nc) {
+        const int t = cand[ci];
         const int s = face_nbr[f * T0 + t];
         const int ms = (s >= 0) ? side[s] : 0;
+        int mk = 0;
         if (ms) {
             int tn[4], sn[4];
             for (int l = 0; l < 4; ++l) {
@@ -194,6 +201,7 @@ __global__ void __launch_bounds__(BS) k_front_G(const int* __restrict__ cand_lis
                     if (sn[r] == tn[fl[q]]) bit[q] = (ms >> r) & 1;
             }
             if (!(bit[0] == bit[1] && bit[1] == bit[2])) {   // two cut edges on this face
+                cut = true;
                 const int apex = (bit[0] == bit[1]) ? 2 : ((bit[0] == bit[2]) ? 1 : 0);
                 const int cl_ = fl[apex];
                 const int al = fl[apex == 0 ? 1 : 0];
@@ -218,38 +226,86 @@ __global__ void __launch_bounds__(BS) k_front_G(const int* __restrict__ cand_lis
                 for (int q = 0; q < 3; ++q) {
                     nI[q] *= iI;
                     nII[q] *= iII;
+                    ff_nrm[q * cap4 + tid] = nI[q];
+                    ff_nrm[(3 + q) * cap4 + tid] = nII[q];
                 }
-                const double s_ad = edge_projection(sig, sig32, t2e[local_edge(al, dl) * Tc + t], nI, gvar);
-                const double s_bd = edge_projection(sig, sig32, t2e[local_edge(bl, dl) * Tc + t], nI, gvar);
-                const double s_cd = edge_projection(sig, sig32, t2e[local_edge(cl_, dl) * Tc + t], nII, gvar);
-                const double GI = 0.5 * (s_ad * fabs(dot3(d1, nI)) + s_bd * fabs(dot3(d2, nI)));
-                const double GII = 0.5 * (s_cd * fabs(dot3(d1, nII)) + s_cd * fabs(dot3(d2, nII)));
-                if (GI >= GII) {
-                    G = GI;
-                    mask = normalize_side((1 << cl_) | (1 << dl));
-                } else {
-                    G = GII;
-                    mask = normalize_side(1 << cl_);
-                }
+                ff_prod[tid] = fabs(dot3(d1, nI));
+                ff_prod[cap4 + tid] = fabs(dot3(d2, nI));
+                ff_prod[2 * cap4 + tid] = fabs(dot3(d1, nII));
+                ff_prod[3 * cap4 + tid] = fabs(dot3(d2, nII));
+                ff_edge[tid] = t2e[local_edge(al, dl) * Tc + t];
+                ff_edge[cap4 + tid] = t2e[local_edge(bl, dl) * Tc + t];
+                ff_edge[2 * cap4 + tid] = t2e[local_edge(cl_, dl) * Tc + t];
+                mk = normalize_side((1 << cl_) | (1 << dl)) | (normalize_side(1 << cl_) << 4);
             }
         }
+        ff_mask[tid] = mk;
     }
-    int fb = f;
-#pragma unroll
-    for (int o = 1; o < 4; o <<= 1) {
-        const double G2 = __shfl_xor_sync(0xffffffffu, G, o);
-        const int m2 = __shfl_xor_sync(0xffffffffu, mask, o);
-        const int f2 = __shfl_xor_sync(0xffffffffu, fb, o);
-        if (G2 > G || (G2 == G && f2 < fb)) {
-            G = G2;
-            mask = m2;
-            fb = f2;
+    // queue the three projections of every face cut twice (one atomic per warp)
+    const unsigned ball = __ballot_sync(0xffffffffu, cut);
+    if (ball) {
+        const int lane = threadIdx.x & 31, leader = __ffs(ball) - 1;
+        long long base = 0;
+        if (lane == leader) base = (long long)atomicAdd((unsigned long long*)qn, 3ull * (unsigned)__popc(ball));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        if (cut) {
+            const long long r = base + 3 * __popc(ball & ((1u << lane) - 1u));
+            for (int q = 0; q < 3; ++q) items[r + q] = 3 * tid + q;
         }
     }
-    if (f == 0 && ci < n_cand) {
-        dec_G[ci] = G;
-        dec_mask[ci] = (mask != 0 && G > Gc[t]) ? (uint8_t)mask : (uint8_t)0;
+}
+
+// s(k, n) of the queued projections: edges ad, bd with n_I, edge cd with n_II.
+__global__ void __launch_bounds__(FB) k_front_proj(const int* __restrict__ items, const long long* __restrict__ qn,
+                                                   const int* __restrict__ ff_edge, const double* __restrict__ ff_nrm,
+                                                   int64_t cap4, const double* __restrict__ sig,
+                                                   const float* __restrict__ sig32, int gvar,
+                                                   double* __restrict__ ff_s) {
+    CEM_PDL_ENTRY();
+    const int64_t i = (int64_t)blockIdx.x * FB + threadIdx.x;
+    if (i >= *qn) return;
+    const int it = items[i];
+    const int face = it / 3, q = it - 3 * face;
+    const int r = (q < 2) ? 0 : 3;
+    const double n[3] = {ff_nrm[r * cap4 + face], ff_nrm[(r + 1) * cap4 + face], ff_nrm[(r + 2) * cap4 + face]};
+    ff_s[it] = edge_projection(sig, sig32, ff_edge[q * cap4 + face], n, gvar);
+}
+
+// G = max over the candidate's faces cut twice of max(G_I, G_II) (Eqs. 17-18),
+// ties to the lowest face; the split decision G > Gc.  Thread 0 empties the
+// projection queue and the step's new-key counter for what follows.
+__global__ void __launch_bounds__(FB) k_front_pick(const int* __restrict__ cand, int nc,
+                                                   const int* __restrict__ ff_mask, const double* __restrict__ ff_prod,
+                                                   const double* __restrict__ ff_s, int64_t cap4,
+                                                   const double* __restrict__ Gc, uint8_t* __restrict__ dec_mask,
+                                                   double* __restrict__ dec_G, long long* __restrict__ qn,
+                                                   long long* __restrict__ nk) {
+    CEM_PDL_ENTRY();
+    const int ci = blockIdx.x * FB + threadIdx.x;
+    if (ci == 0) {
+        *qn = 0;
+        if (nk) *nk = 0;
     }
+    if (ci >= nc) return;
+    double G = -1.0 / 0.0;
+    int mask = 0;
+    for (int f = 0; f < 4; ++f) {
+        const int face = 4 * ci + f;
+        const int mk = ff_mask[face];
+        if (!mk) continue;
+        const double* s = ff_s + 3 * (int64_t)face;
+        const double GI = 0.5 * __dadd_rn(__dmul_rn(s[0], ff_prod[face]), __dmul_rn(s[1], ff_prod[cap4 + face]));
+        const double GII =
+            0.5 * __dadd_rn(__dmul_rn(s[2], ff_prod[2 * cap4 + face]), __dmul_rn(s[2], ff_prod[3 * cap4 + face]));
+        const bool modeI = GI >= GII;
+        const double Gf = modeI ? GI : GII;
+        if (Gf > G) {
+            G = Gf;
+            mask = modeI ? (mk & 15) : (mk >> 4);
+        }
+    }
+    dec_G[ci] = G;
+    dec_mask[ci] = (mask != 0 && G > Gc[cand[ci]]) ? (uint8_t)mask : (uint8_t)0;
 }
 
 // ------------------------------------------------------------------ scan functors
@@ -521,6 +577,18 @@ __global__ void k_create_subs(int S, int64_t T, const int* __restrict__ split_li
     const double lp = lam[p], mp = mu[p];
     for (int q = qs; q < ns && q == qs; ++q) {
         int* s = subs[q];
+        // Local nodes in ascending id order (then at most the last two swapped for a
+        // positive volume).  The element-force record keeps local nodes 0,1 and 2,3 in
+        // one 32-byte sector each; pairing the two oldest and the two newest nodes lets
+        // the node update find the other half of a sector in L2.
+#define CEM_CSWAP(a_, b_)              \
+    if (s[a_] > s[b_]) {               \
+        const int w_ = s[a_];          \
+        s[a_] = s[b_];                 \
+        s[b_] = w_;                    \
+    }
+        CEM_CSWAP(0, 1) CEM_CSWAP(2, 3) CEM_CSWAP(0, 2) CEM_CSWAP(1, 3) CEM_CSWAP(1, 2)
+#undef CEM_CSWAP
         // orientation and geometry (V * grad N for local nodes 1..3)
         double x0[3], e[3][3];
         load3(X, Nc, s[0], x0);
@@ -1034,12 +1102,18 @@ int update_lists(cem_ctx* c, int S) {
 }  // namespace
 
 int cem_launch_front_G(cem_ctx* c) {
-    if (c->n_cand > 0) {
-        cem_pdl(c->stream, k_front_G, cem_grid(4 * c->n_cand, BS), BS, c->cand_list, (int)c->n_cand, c->conn, c->t2e, c->Tc,
-                                                                 c->face_nbr, c->side, c->T0, c->X, c->u, c->Nc, c->sig,
-                                                                 c->sig32, c->Gc, c->g_variant, c->dec_mask,
-                                                                 c->dec_G, c->dcount + CNT_SCRATCH0);
-        cem_launched(c, 1);
+    const int64_t cap = c->front_cap, cap4 = 4 * cap;
+    for (int64_t c0 = 0; c0 < c->n_cand; c0 += cap) {
+        const int nc = (int)std::min<int64_t>(cap, c->n_cand - c0);
+        long long* qn = c->dcount + CNT_FRONT_Q;
+        cem_pdl(c->stream, k_front_faces, cem_grid(4 * (int64_t)nc, FB), FB, c->cand_list + c0, nc, c->conn, c->t2e,
+                c->Tc, c->face_nbr, c->side, c->T0, c->X, c->u, c->Nc, c->ff_mask, c->ff_prod, c->ff_nrm, c->ff_edge,
+                cap4, c->ff_item, qn);
+        cem_pdl(c->stream, k_front_proj, cem_grid(12 * (int64_t)nc, FB), FB, c->ff_item, qn, c->ff_edge, c->ff_nrm,
+                cap4, c->sig, c->sig32, c->g_variant, c->ff_s);
+        cem_pdl(c->stream, k_front_pick, cem_grid(nc, FB), FB, c->cand_list + c0, nc, c->ff_mask, c->ff_prod, c->ff_s,
+                cap4, c->Gc, c->dec_mask + c0, c->dec_G + c0, qn, c0 == 0 ? c->dcount + CNT_SCRATCH0 : nullptr);
+        cem_launched(c, 3);
         CEM_CK(c, cudaGetLastError());
     }
     return run_scan(c, U8Load{c->dec_mask},
