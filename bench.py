@@ -109,6 +109,9 @@ def _args():
                    help="steps of the hexahedral (ES-H-FEM) sub-run on 200x80x10 hexahedra; 0 skips it")
     p.add_argument("--no-compare", action="store_true", help="skip the second-precision run and agreement check")
     p.add_argument("--no-autotune", action="store_true", help="keep the default launch variants")
+    p.add_argument("--reorder-growth", type=float, default=None,
+                   help="renumber node storage after this fractional node growth (0: never; default: the "
+                        "library's)")
     p.add_argument("--split-capacity", type=int, default=0,
                    help="max elements that may split (0: all); lower it to shrink device memory for profiling")
     p.add_argument("--state", help="checkpoint file for --save-at / --resume")
@@ -239,6 +242,11 @@ def run_reference(a):
     print(json.dumps(line), flush=True)
 
 
+def _reorder(sim, a):
+    if a.reorder_growth is not None:
+        sim.set_reorder(a.reorder_growth)
+
+
 def run_cem(a):
     import numpy as np
     import torch
@@ -267,6 +275,7 @@ def run_cem(a):
         if not a.state:
             raise SystemExit("--save-at and --resume need --state PATH")
         sim = CEM.from_workload(w, device=dev, split_capacity=a.split_capacity, precision=a.precision)
+        _reorder(sim, a)
         if not a.no_autotune:
             sim.autotune(reps=10, automatic=True)
         if a.save_at > 0:
@@ -299,6 +308,7 @@ def run_cem(a):
         steps = a.steps if steps is None else steps
         cap = a.split_capacity if split_capacity is None else split_capacity
         sim = CEM.from_workload(w, device=dev, split_capacity=cap, precision=precision)
+        _reorder(sim, a)
         info0 = sim.info()
         if not a.no_autotune:   # launch variants for the current sizes; re-tuned in the run as the mesh grows
             sim.autotune(reps=10, automatic=True)
@@ -491,6 +501,7 @@ def run_cem(a):
     barrier()
     t0 = time.perf_counter()
     sim2 = CEM.from_workload(w, device=dev, split_capacity=a.split_capacity, precision=a.precision)
+    _reorder(sim2, a)
     if not a.no_autotune:
         sim2.autotune(reps=10, automatic=True)
     sim2.step(a.steps)

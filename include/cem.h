@@ -174,6 +174,7 @@ typedef struct cem_info_t {
     double  dt;              /* time step [s]                                           */
     double  h_min;           /* min over input elements of 3V / max face area [m]       */
     int64_t device_bytes;    /* device memory held by the context                       */
+    int64_t n_reorder;       /* node renumberings so far (cem_set_reorder)              */
 } cem_info_t;
 
 /* Build the device mesh: edges and their element fans (Sec. 2.2, Fig. 4),
@@ -346,6 +347,26 @@ int cem_probe_fp64_fma(int device, void* stream, double* flops_per_s);
  * library routine. */
 int cem_node_energies_noalloc(const double* u, const double* v, const double* a, const double* mass,
                               const double* fext, int64_t n_nodes, int64_t ld, double* out, void* stream);
+
+/* Node renumbering for memory locality (no counterpart in the paper).  Split
+ * nodes are appended to the node arrays, so an element made by a split pairs
+ * nodes whose storage lies far apart, and the node update gathers its force
+ * record from DRAM once per such node.  A renumbering puts the nodes in
+ * Morton order of their reference coordinates (ties by id) and rewrites the
+ * incidence lists in that order.  It changes only where nodes are stored:
+ * every function of this header keeps taking and returning nodes by their
+ * creation ids (input nodes first, then split nodes in the order they were
+ * made), and every result is bit-identical to a run without renumbering
+ * except for the last bits of energy sums, which add nodes in storage order.
+ * cem_set_reorder sets the trigger: after a split step, renumber when the
+ * node count has grown by the fraction `growth` since the last renumbering
+ * (or since the input mesh); growth = 0 never renumbers.  Default 0.25 for
+ * tetrahedral meshes with splitting; CEM_EINVAL for growth < 0.
+ * cem_reorder_nodes renumbers now.  Both return CEM_ESTATE for contexts
+ * without splitting (hexahedral or split_enabled = 0), whose node order is
+ * the input's. */
+int cem_set_reorder(cem_ctx* ctx, double growth);
+int cem_reorder_nodes(cem_ctx* ctx);
 
 /* Checkpoint and resume.  cem_save writes the context's dynamic state to the
  * file `path`: node, element and edge arrays up to their current counts, the

@@ -28,7 +28,8 @@ FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_void_p)
 EXPORTED = ["cem_mesh_create", "cem_set_material", "cem_step", "cem_energy", "cem_crack_state",
             "cem_get_field", "cem_info", "cem_energy_instance", "cem_adjoint", "cem_profile", "cem_profile_read",
             "cem_autotune", "cem_tune_get", "cem_tune_set", "cem_save", "cem_load", "cem_set_wait_limit",
-            "cem_wait_probe", "cem_probe_fp64_fma", "cem_destroy", "cem_last_error"]
+            "cem_wait_probe", "cem_set_reorder", "cem_reorder_nodes", "cem_probe_fp64_fma", "cem_destroy",
+            "cem_last_error"]
 TUNED = ["strain", "edge_stress", "force", "node_update"]
 KERNELS = ["predict", "strain", "edge_stress", "force", "node_update", "front_G", "split"]
 
@@ -60,7 +61,8 @@ class Energy(C.Structure):
 class Info(C.Structure):
     _fields_ = [("n_nodes", C.c_int64), ("n_tets", C.c_int64), ("n_active_tets", C.c_int64),
                 ("n_edges", C.c_int64), ("n_candidates", C.c_int64), ("n_orig_edges", C.c_int64),
-                ("dt", C.c_double), ("h_min", C.c_double), ("device_bytes", C.c_int64)]
+                ("dt", C.c_double), ("h_min", C.c_double), ("device_bytes", C.c_int64),
+                ("n_reorder", C.c_int64)]
 
 
 _LIB = None
@@ -98,6 +100,8 @@ def load_library(build: bool = True):
     lib.cem_save.argtypes = [P, C.c_char_p]
     lib.cem_set_wait_limit.argtypes = [P, C.c_int64]
     lib.cem_wait_probe.argtypes = [P]
+    lib.cem_set_reorder.argtypes = [P, C.c_double]
+    lib.cem_reorder_nodes.argtypes = [P]
     lib.cem_load.argtypes = [P, C.c_char_p]
     lib.cem_tune_get.argtypes = [P, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_double),
                                  C.POINTER(C.c_double)]
@@ -308,6 +312,14 @@ class CEM:
     def wait_probe(self):
         """Run one bounded wait on a flag nothing sets; raises CEMError(CEM_ETIMEOUT)."""
         self._check(self._lib.cem_wait_probe(self._ctx))
+
+    def set_reorder(self, growth=0.25):
+        """Renumber node storage once the node count grew by this fraction (0: never)."""
+        self._check(self._lib.cem_set_reorder(self._ctx, float(growth)))
+
+    def reorder_nodes(self):
+        """Renumber node storage now (results are unchanged; node ids stay creation ids)."""
+        self._check(self._lib.cem_reorder_nodes(self._ctx))
 
     def info(self) -> dict:
         i = Info()

@@ -31,13 +31,7 @@ int cem_cuda_fail(cem_ctx* c, cudaError_t e, const char* what) {
 
 int64_t cem_reduction_doubles();
 
-namespace {
-
-const int LE[6][2] = {{0, 1}, {0, 2}, {0, 3}, {1, 2}, {1, 3}, {2, 3}};
-
-template <class T>
-bool dalloc(cem_ctx* c, T*& p, int64_t n) {
-    size_t bytes = (size_t)std::max<int64_t>(n, 1) * sizeof(T);
+void* cem_dalloc_bytes(cem_ctx* c, size_t bytes) {
     bytes = (bytes + 255) & ~(size_t)255;
     void* q = nullptr;
     if (c->alloc) {
@@ -45,11 +39,20 @@ bool dalloc(cem_ctx* c, T*& p, int64_t n) {
     } else if (cudaMalloc(&q, bytes) != cudaSuccess) {
         q = nullptr;
     }
-    if (!q) return false;
+    if (!q) return nullptr;
     c->allocs.push_back(q);
     c->bytes += (int64_t)bytes;
-    p = (T*)q;
-    return true;
+    return q;
+}
+
+namespace {
+
+const int LE[6][2] = {{0, 1}, {0, 2}, {0, 3}, {1, 2}, {1, 3}, {2, 3}};
+
+template <class T>
+bool dalloc(cem_ctx* c, T*& p, int64_t n) {
+    p = (T*)cem_dalloc_bytes(c, (size_t)std::max<int64_t>(n, 1) * sizeof(T));
+    return p != nullptr;
 }
 
 int select_device(cem_ctx* c) {
@@ -548,6 +551,17 @@ int create_impl(const cem_mesh_desc* d, cem_ctx* c) {
     ok = ok && dalloc(c, c->split_G, T0) && dalloc(c, c->Gc, T0) && dalloc(c, c->oe_n0, E0) && dalloc(c, c->oe_n1, E0);
     ok = ok && dalloc(c, c->node_of_key, 2 * E0) && dalloc(c, c->cand_flag, T0) && dalloc(c, c->cand_list, T0);
     ok = ok && dalloc(c, c->dec_mask, T0) && dalloc(c, c->dec_G, T0) && dalloc(c, c->split_list, T0);
+    ok = ok && dalloc(c, c->ext_of_int, Nc) && dalloc(c, c->int_of_ext, Nc) && dalloc(c, c->rn_map, Nc);
+    if (ok) {   // renumbering scratch: the step's element-force and strain records are dead between steps
+        int64_t kcap = 2048;
+        while (kcap < Nc) kcap <<= 1;
+        c->rn_keys_cap = kcap;
+        const int64_t fp_bytes = (mixed ? 64 : 96) * Tc, h_bytes = (mixed ? 32 : 48) * Tc;
+        if (fp_bytes >= 32 * Nc) c->rn_tmp = mixed ? (double*)c->fp32 : c->fp;
+        else ok = dalloc(c, c->rn_tmp, 4 * Nc);
+        if (h_bytes >= 8 * kcap) c->rn_keys = mixed ? (unsigned long long*)c->h32 : (unsigned long long*)c->h;
+        else ok = ok && dalloc(c, c->rn_keys, kcap);
+    }
     c->front_cap = std::min<int64_t>(T0, 1 << 16);
     const int64_t ff = 4 * c->front_cap;
     ok = ok && dalloc(c, c->ff_mask, ff) && dalloc(c, c->ff_prod, 4 * ff) && dalloc(c, c->ff_nrm, 6 * ff) &&
@@ -640,6 +654,7 @@ int create_impl(const cem_mesh_desc* d, cem_ctx* c) {
             for (int k = 0; k < 3; ++k) Xs[k * N0 + i] = d->X[3 * i + k];
         for (int k = 0; k < 3; ++k)
             if (int rc = upload(c, c->X + k * Nc, Xs.data() + k * N0, N0)) return rc;
+        if (int rc = cem_reorder_init(c, d->X, N0)) return rc;
         CEM_CK(c, cudaStreamSynchronize(s));
     }
     {
@@ -817,7 +832,8 @@ int run_step(cem_ctx* c) {
             if (c->n_split_all + S > c->S_cap)
                 return cem_fail(c, CEM_ECAPACITY, "split capacity exhausted; splits of this step not applied");
             NvtxRange split("cem.split");
-            TIMED(c, CEM_KERNEL_SPLIT, cem_apply_splits(c, S, c->step, 1));
+            // the splits, then a renumbering of node storage when the node count has grown enough
+            TIMED(c, CEM_KERNEL_SPLIT, (rc = cem_apply_splits(c, S, c->step, 1)) ? rc : cem_reorder_maybe(c));
         }
     }
     if (c->ev_pending.size() > 4096) return prof_resolve(c);
@@ -1036,9 +1052,16 @@ int cem_get_field(cem_ctx* c, int which, double* out, int64_t cap, int64_t* n_no
     for (int k = 0; k < 3; ++k)
         CEM_CK(c, cudaMemcpyAsync(tmp.data() + k * c->N, src + k * c->Nc, c->N * sizeof(double),
                                   cudaMemcpyDeviceToHost, c->stream));
+    std::vector<int> at;   // storage index of every creation id (renumbered nodes)
+    if (c->renumbered) {
+        at.resize(c->N);
+        CEM_CK(c, cudaMemcpyAsync(at.data(), c->int_of_ext, c->N * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    }
     CEM_CK(c, cudaStreamSynchronize(c->stream));
-    for (int64_t i = 0; i < c->N; ++i)
-        for (int k = 0; k < 3; ++k) out[3 * i + k] = tmp[k * c->N + i];
+    for (int64_t i = 0; i < c->N; ++i) {
+        const int64_t j = c->renumbered ? at[i] : i;
+        for (int k = 0; k < 3; ++k) out[3 * i + k] = tmp[k * c->N + j];
+    }
     return CEM_OK;
 }
 
@@ -1053,6 +1076,7 @@ int cem_info(cem_ctx* c, cem_info_t* out) {
     out->dt = c->dt;
     out->h_min = c->h_min;
     out->device_bytes = c->bytes;
+    out->n_reorder = c->n_reorder;
     return CEM_OK;
 }
 

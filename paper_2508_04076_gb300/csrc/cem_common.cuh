@@ -113,6 +113,21 @@ struct cem_ctx {
     std::vector<void*> allocs;
     std::string err;
 
+    // node storage order (renumbering for locality): the API's creation ids <-> storage ids
+    int* ext_of_int = nullptr;          // [Nc] creation id of the node stored at i
+    int* int_of_ext = nullptr;          // [Nc] storage index of creation id j
+    bool renumbered = false;            // the maps are not the identity
+    double reorder_growth = 0.25;       // renumber after N grew by this fraction (0: never)
+    int64_t reorder_n = 0;              // N at the last renumbering (N0 before the first)
+    int64_t n_reorder = 0;              // renumberings so far
+    double bb_lo[3] = {0, 0, 0};        // bounding box of the input nodes (Morton keys)
+    double bb_inv = 0.0;                // 1023 / largest extent
+    // renumbering scratch; keys and tmp alias the step's strain and element-force
+    // records (dead between steps) when those are large enough
+    unsigned long long* rn_keys = nullptr;   // [rn_keys_cap = 2^p >= Nc] sort keys
+    int64_t rn_keys_cap = 0;
+    int* rn_map = nullptr;              // [Nc] new storage index of old index
+    double* rn_tmp = nullptr;           // [4 Nc] permutation scratch (32 bytes per node)
     // nodes
     double *X = nullptr, *u = nullptr, *v = nullptr, *a = nullptr, *fext = nullptr;
     double *mass = nullptr, *minv = nullptr;
@@ -294,4 +309,11 @@ int64_t cem_hex_geometry_values();
 
 // ---------------------------------------------------------------- crack path (cem_crack.cu)
 int cem_launch_front_G(cem_ctx* c);
+int cem_defrag_lists(cem_ctx* c, int kind);   // rewrite fan (0) or incidence (1) lists in index order
+int cem_renumber_nodes(cem_ctx* c);           // Morton-order node storage (cem_reorder.cu)
+int cem_reorder_maybe(cem_ctx* c);            // renumber when the growth trigger is reached
+int cem_reorder_init(cem_ctx* c, const double* X, int64_t n);   // identity maps, Morton box of the input nodes
+int cem_reorder_identity(cem_ctx* c);         // identity maps on [0, Nc)
+int cem_reorder_inverse(cem_ctx* c);          // int_of_ext from ext_of_int on [0, N)
+void* cem_dalloc_bytes(cem_ctx* c, size_t bytes);   // device allocation owned by the context
 int cem_apply_splits(cem_ctx* c, int64_t S, int64_t step, int book_energy);

@@ -471,15 +471,17 @@ __global__ void __launch_bounds__(1024) k_node_sorted(const long long* __restric
 
 
 struct SubCtx {
-    const int* pn;        // parent's 4 node ids
+    const int* pn;        // parent's 4 node ids (storage indices)
+    const int* pe;        // their creation ids
     int p;
     const int* t2e;
     int64_t Tc;
     const int* node_of_key;
     // new node on the parent's edge between local nodes x and y, attached to x
+    // (side 0: x is the end with the smaller creation id)
     __device__ int M(int x, int y) const {
         const int e = t2e[local_edge(x, y) * Tc + p];
-        const int s = (pn[x] < pn[y]) ? 0 : 1;
+        const int s = (pe[x] < pe[y]) ? 0 : 1;
         return node_of_key[2 * e + s];
     }
 };
@@ -506,7 +508,8 @@ __global__ void k_create_subs(int S, int64_t T, const int* __restrict__ split_li
                               const double* __restrict__ X, int64_t Nc, uint8_t* __restrict__ side,
                               int* __restrict__ split_step, double* __restrict__ split_G,
                               const double* __restrict__ Gc, uint8_t* __restrict__ cand_flag,
-                              double* __restrict__ ud_part, double* __restrict__ ud_tet, int deact) {
+                              double* __restrict__ ud_part, double* __restrict__ ud_tet, int deact,
+                              const int* __restrict__ ext) {
     CEM_PDL_ENTRY();
     // six threads per split: thread qs builds sub-element qs (the sub-element list is
     // rebuilt by each, it is cheap integer work); thread 0 also closes the parent
@@ -515,9 +518,12 @@ __global__ void k_create_subs(int S, int64_t T, const int* __restrict__ split_li
     if (i >= S) return;
     const int p = split_list[i];
     const int m = split_mask[i];
-    int pn[4];
-    for (int l = 0; l < 4; ++l) pn[l] = conn[l * Tc + p];
-    SubCtx sc{pn, p, t2e, Tc, node_of_key};
+    int pn[4], pe[4];
+    for (int l = 0; l < 4; ++l) {
+        pn[l] = conn[l * Tc + p];
+        pe[l] = ext[pn[l]];
+    }
+    SubCtx sc{pn, pe, p, t2e, Tc, node_of_key};
     int subs[6][4];
     int ns = 0;
     double area;
@@ -577,15 +583,21 @@ __global__ void k_create_subs(int S, int64_t T, const int* __restrict__ split_li
     const double lp = lam[p], mp = mu[p];
     for (int q = qs; q < ns && q == qs; ++q) {
         int* s = subs[q];
-        // Local nodes in ascending id order (then at most the last two swapped for a
-        // positive volume).  The element-force record keeps local nodes 0,1 and 2,3 in
-        // one 32-byte sector each; pairing the two oldest and the two newest nodes lets
-        // the node update find the other half of a sector in L2.
+        // Local nodes in ascending creation-id order (then at most the last two
+        // swapped for a positive volume): the element-force record keeps local
+        // nodes 0,1 and 2,3 in one 32-byte sector each, and pairing the two oldest
+        // and the two newest nodes lets the node update find the other half of a
+        // sector in L2.  Creation ids keep the order independent of node storage.
+        int se[4];
+        for (int l = 0; l < 4; ++l) se[l] = ext[s[l]];
 #define CEM_CSWAP(a_, b_)              \
-    if (s[a_] > s[b_]) {               \
-        const int w_ = s[a_];          \
+    if (se[a_] > se[b_]) {             \
+        int w_ = s[a_];                \
         s[a_] = s[b_];                 \
         s[b_] = w_;                    \
+        w_ = se[a_];                   \
+        se[a_] = se[b_];               \
+        se[b_] = w_;                   \
     }
         CEM_CSWAP(0, 1) CEM_CSWAP(2, 3) CEM_CSWAP(0, 2) CEM_CSWAP(1, 3) CEM_CSWAP(1, 2)
 #undef CEM_CSWAP
@@ -657,14 +669,15 @@ __global__ void k_sub_edges(const long long* __restrict__ nsub, int64_t T, int64
                             int* __restrict__ t2e, const int* __restrict__ anc, int64_t Tc,
                             unsigned long long* __restrict__ hkeys, const int* __restrict__ hvals,
                             int* __restrict__ hfirst, int64_t hmask, int* __restrict__ slot_of,
-                            long long* __restrict__ err) {
+                            long long* __restrict__ err, const int* __restrict__ ext) {
     CEM_PDL_ENTRY();
     const int cidx = blockIdx.x * BS + threadIdx.x;
     if (cidx >= 6 * *nsub) return;
     const int q = cidx / 6, l = cidx % 6;
     const int64_t s = T + q;
     const int x = conn[CEM_LE0(l) * Tc + s], y = conn[CEM_LE1(l) * Tc + s];
-    if (x < N0 && y < N0) {   // both original nodes: an edge of the parent
+    const int xe = ext[x], ye = ext[y];   // creation ids: input nodes are those below N0
+    if (xe < N0 && ye < N0) {   // both original nodes: an edge of the parent
         const int p = anc[s];
         int e = -1;
         for (int l2 = 0; l2 < 6; ++l2) {
@@ -675,7 +688,7 @@ __global__ void k_sub_edges(const long long* __restrict__ nsub, int64_t T, int64
         slot_of[cidx] = -1;
         return;
     }
-    const unsigned long long lo = (unsigned)min(x, y), hi = (unsigned)max(x, y);
+    const unsigned long long lo = (unsigned)min(xe, ye), hi = (unsigned)max(xe, ye);
     const unsigned long long key = (lo << 32) | hi;
     int64_t slot = (int64_t)(mix64(key) & (unsigned long long)hmask);
     for (int64_t probe = 0;; ++probe) {
@@ -1027,6 +1040,12 @@ int defrag(cem_ctx* c, int kind) {
     return CEM_OK;
 }
 
+}  // namespace
+
+int cem_defrag_lists(cem_ctx* c, int kind) { return defrag(c, kind); }
+
+namespace {
+
 // Update the fan and incidence lists of every affected edge and node.  S
 // splits of this step; the number of new sub-elements is read on the device
 // (at most 6 S).  The host does not wait unless a pool may be too short for
@@ -1156,12 +1175,13 @@ int cem_apply_splits(cem_ctx* c, int64_t S64, int64_t step, int book_energy) {
             S, c->T, c->split_list, c->split_mask, c->split_Gv, c->sub_off, step, book_energy, c->conn, c->t2e, c->anc,
             c->active, c->Vg, c->Vg32, c->vol, c->lam, c->mu, c->Tc, c->node_of_key, c->X, c->Nc, c->side,
             c->split_step, c->split_G, c->Gc, c->cand_flag, c->ud_part, c->ud_tet,
-            (int)(c->split_mode == CEM_SPLIT_DEACTIVATE));
+            (int)(c->split_mode == CEM_SPLIT_DEACTIVATE), (const int*)c->ext_of_int);
     // 3. edges of the sub-elements: parent edges or (new) hashed node pairs
     const long long* nsub = c->dcount + CNT_NEWSUB;
     const int codes = 36 * S;
     cem_pdl(c->stream, k_sub_edges, cem_grid(codes, BS), BS, nsub, c->T, c->N0, c->conn, c->t2e, c->anc, c->Tc,
-            c->hkeys, c->hvals, c->hfirst, c->hash_cap - 1, c->slot_of, c->dcount + CNT_ERR);
+            c->hkeys, c->hvals, c->hfirst, c->hash_cap - 1, c->slot_of, c->dcount + CNT_ERR,
+            (const int*)c->ext_of_int);
     cem_pdl(c->stream, k_edge_owner, cem_grid(codes, BS), BS, nsub, c->slot_of, c->hvals, c->hfirst, c->code_flag);
     cem_launched(c, 3);
     CEM_CK(c, cudaGetLastError());

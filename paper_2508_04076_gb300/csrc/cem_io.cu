@@ -4,12 +4,13 @@
 // description and the material: node, element and edge arrays up to their
 // current counts, the fan and incidence pools up to their tops, the crack
 // records of the input elements, the candidate list, the new-node and
-// new-edge maps, U_d and the counters.  The step's scratch (element strains,
+// new-edge maps, U_d, the counters, and the node storage order with the node
+// references a renumbering rewrites.  The step's scratch (element strains,
 // edge stresses, element forces, flags) is rewritten before it is read and is
 // not saved.  A context built from the same description and material and then
 // loaded continues bit for bit as the saved one would have.
 //
-// File layout (host byte order): the 8-byte tag "CEMCKPT1", a header of int64
+// File layout (host byte order): the 8-byte tag "CEMCKPT2", a header of int64
 // fields (HDR_* below), then every array as raw bytes in a fixed order, each
 // preceded by its byte count.
 #include "cem_common.cuh"
@@ -23,9 +24,9 @@ namespace {
 enum {
     HDR_ELEM, HDR_PREC, HDR_N0, HDR_T0, HDR_E0, HDR_NC, HDR_TC, HDR_EC, HDR_FANCAP, HDR_INCCAP, HDR_HASHCAP,
     HDR_NINST, HDR_SPLITMODE, HDR_N, HDR_T, HDR_E, HDR_NCAND, HDR_NSPLITALL, HDR_NSPLITRUN, HDR_NACTIVE,
-    HDR_FANTOP, HDR_INCTOP, HDR_STEP, HDR_DT_BITS, HDR_COUNT
+    HDR_FANTOP, HDR_INCTOP, HDR_STEP, HDR_DT_BITS, HDR_RENUMBERED, HDR_REORDER_N, HDR_NREORDER, HDR_COUNT
 };
-const char TAG[8] = {'C', 'E', 'M', 'C', 'K', 'P', 'T', '1'};
+const char TAG[8] = {'C', 'E', 'M', 'C', 'K', 'P', 'T', '2'};
 
 struct Field {   // one array slice: device pointer, bytes
     void* p;
@@ -86,6 +87,12 @@ std::vector<Field> fields(cem_ctx* c) {
     add(c->hvals, c->hash_cap, 4);
     add(c->hfirst, c->hash_cap, 4);
     add(c->Ud, 1, 8);
+    // node storage order (creation id of each stored node) and the node references a
+    // renumbering rewrites besides conn and node_of_key
+    add(c->ext_of_int, N, 4);
+    add(c->oe_n0, c->E0, 4);
+    add(c->oe_n1, c->E0, 4);
+    add(c->dir_key, c->n_dir, 4);
     return f;
 }
 
@@ -114,6 +121,9 @@ void header(const cem_ctx* c, int64_t h[HDR_COUNT]) {
     h[HDR_INCTOP] = c->inc_top;
     h[HDR_STEP] = c->step;
     std::memcpy(&h[HDR_DT_BITS], &c->dt, sizeof(double));
+    h[HDR_RENUMBERED] = c->renumbered ? 1 : 0;
+    h[HDR_REORDER_N] = c->reorder_n;
+    h[HDR_NREORDER] = c->n_reorder;
 }
 
 }  // namespace
@@ -173,7 +183,8 @@ extern "C" int cem_load(cem_ctx* c, const char* path) {
                           h[HDR_FANTOP] >= 0 && h[HDR_FANTOP] <= c->fan_cap && h[HDR_INCTOP] >= 0 &&
                           h[HDR_INCTOP] <= c->inc_cap && h[HDR_NSPLITALL] >= 0 && h[HDR_NSPLITALL] <= c->S_cap &&
                           h[HDR_NSPLITRUN] >= 0 && h[HDR_NACTIVE] >= 0 && h[HDR_NACTIVE] <= h[HDR_T] &&
-                          h[HDR_STEP] >= 0;
+                          h[HDR_STEP] >= 0 && h[HDR_REORDER_N] >= 0 && h[HDR_REORDER_N] <= h[HDR_N] &&
+                          h[HDR_NREORDER] >= 0 && (h[HDR_RENUMBERED] == 0 || h[HDR_RENUMBERED] == 1);
     if (!sizes_ok) {
         std::fclose(fp);
         return cem_fail(c, CEM_EINVAL, "checkpoint counts exceed the context's capacities");
@@ -189,6 +200,15 @@ extern "C" int cem_load(cem_ctx* c, const char* path) {
     c->fan_top = h[HDR_FANTOP];
     c->inc_top = h[HDR_INCTOP];
     c->step = h[HDR_STEP];
+    c->renumbered = h[HDR_RENUMBERED] != 0;
+    c->reorder_n = h[HDR_REORDER_N];
+    c->n_reorder = h[HDR_NREORDER];
+    // node maps: identity, then the saved storage order of the first N nodes and its inverse
+    if (int rc = cem_reorder_identity(c)) {
+        std::fclose(fp);
+        return rc;
+    }
+    CEM_CK(c, cudaStreamSynchronize(c->stream));
     std::vector<char> buf;
     for (const Field& f : fields(c)) {
         int64_t nb = 0;
@@ -208,5 +228,7 @@ extern "C" int cem_load(cem_ctx* c, const char* path) {
     }
     std::fclose(fp);
     CEM_CK(c, cudaDeviceSynchronize());
+    if (int rc = cem_reorder_inverse(c)) return rc;
+    CEM_CK(c, cudaStreamSynchronize(c->stream));
     return CEM_OK;
 }
