@@ -326,6 +326,14 @@ int cem_tune_set(cem_ctx* ctx, int kernel, int block, int batch);
  * Allocates and frees a small device buffer itself. */
 int cem_probe_fp64_fma(int device, void* stream, double* flops_per_s);
 
+/* Diagnostics (no counterpart in the paper): the integer-only conversions of
+ * the mixed-precision node update on the current device, for n host values:
+ * (hi[i], lo[i]) = the FP32 pair of x[i] (x truncated to 24 significant bits,
+ * then the remainder truncated to 24 bits; for |x| outside [2^-74, 2^128)
+ * other than zero, the rounded pair RN(x), RN(x - RN(x))) and fd[i] = f[i] as
+ * a double.  Synchronous; allocates and frees its own device buffers. */
+int cem_probe_split(const double* x, const float* f, int64_t n, float* hi, float* lo, double* fd);
+
 /* Nodal energy sums of caller-owned device arrays, with no allocation.  The
  * paper has no counterpart: this is a library facility for callers that
  * cannot call cudaMalloc, for example code whose device memory is entirely

@@ -28,7 +28,7 @@ FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_void_p)
 EXPORTED = ["cem_mesh_create", "cem_set_material", "cem_step", "cem_energy", "cem_crack_state",
             "cem_get_field", "cem_info", "cem_energy_instance", "cem_adjoint", "cem_profile", "cem_profile_read",
             "cem_autotune", "cem_tune_get", "cem_tune_set", "cem_save", "cem_load", "cem_set_wait_limit",
-            "cem_wait_probe", "cem_set_reorder", "cem_reorder_nodes", "cem_probe_fp64_fma", "cem_destroy",
+            "cem_wait_probe", "cem_set_reorder", "cem_reorder_nodes", "cem_probe_fp64_fma", "cem_probe_split", "cem_destroy",
             "cem_last_error"]
 TUNED = ["strain", "edge_stress", "force", "node_update"]
 KERNELS = ["predict", "strain", "edge_stress", "force", "node_update", "front_G", "split"]
@@ -95,6 +95,8 @@ def load_library(build: bool = True):
     lib.cem_profile.argtypes = [P, C.c_int]
     lib.cem_profile_read.argtypes = [P, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.c_int, C.POINTER(C.c_int64)]
     lib.cem_probe_fp64_fma.argtypes = [C.c_int, C.c_void_p, C.POINTER(C.c_double)]
+    lib.cem_probe_split.argtypes = [C.POINTER(C.c_double), C.POINTER(C.c_float), C.c_int64,
+                                    C.POINTER(C.c_float), C.POINTER(C.c_float), C.POINTER(C.c_double)]
     lib.cem_autotune.argtypes = [P, C.c_char_p, C.c_int, C.c_int]
     lib.cem_tune_set.argtypes = [P, C.c_int, C.c_int, C.c_int]
     lib.cem_save.argtypes = [P, C.c_char_p]
@@ -123,6 +125,22 @@ def probe_fp64_fma(device=0, stream=0) -> float:
     if rc != CEM_OK:
         raise CEMError(rc, "FP64 probe failed")
     return out.value
+
+
+def probe_split(x, f):
+    """(hi, lo, fd): the mixed node update's integer-only FP32 pair of each double x
+    and float-to-double conversion of each float f, run on the current GPU."""
+    lib = load_library()
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    f = np.ascontiguousarray(f, dtype=np.float32)
+    if x.shape != f.shape:
+        raise ValueError("x and f must have the same shape")
+    hi, lo, fd = np.empty(x.shape, np.float32), np.empty(x.shape, np.float32), np.empty(x.shape, np.float64)
+    rc = lib.cem_probe_split(_ptr(x, C.c_double), _ptr(f, C.c_float), x.size, _ptr(hi, C.c_float),
+                             _ptr(lo, C.c_float), _ptr(fd, C.c_double))
+    if rc != CEM_OK:
+        raise CEMError(rc, "split probe failed")
+    return hi, lo, fd
 
 
 class CEMError(RuntimeError):

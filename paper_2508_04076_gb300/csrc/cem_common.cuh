@@ -36,15 +36,53 @@ __device__ __forceinline__ double cem_pred(double u, double v, double a, double 
     return __fma_rn(hdt2, a, __fma_rn(dt, v, u));
 }
 
+// FP32 pair (hi, lo) of a double x, from its bit pattern with integer
+// operations only: GB300 issues FP64 conversions at its FP64 rate, a small
+// fraction of its integer rate.  hi is x truncated to 24 significant bits and
+// lo the remainder truncated to 24 bits, so |x - hi - lo| <= 2^-47 |x|.  For
+// 2^-74 <= |x| < 2^128 both are normal floats, and +-0 gives +-0 twice; other
+// x (tiny, huge, non-finite) take the conversion instructions: hi = RN(x),
+// lo = RN(x - hi).
+__device__ __forceinline__ void cem_split_hl(double x, float& hi, float& lo) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+    if ((b << 1) == 0ull) {   // +-0 (nodes the load has not reached yet)
+        hi = lo = __uint_as_float(sign);
+        return;
+    }
+    const int E = (int)((b >> 52) & 0x7ffull) - 1023;
+    if (E < -74 || E > 127) {
+        hi = (float)x;
+        lo = (float)(x - (double)hi);
+        return;
+    }
+    const unsigned long long m = b & 0xfffffffffffffull;                 // 52 fraction bits
+    hi = __uint_as_float(sign | ((unsigned)(E + 127) << 23) | (unsigned)(m >> 29));
+    const unsigned r = (unsigned)(m & 0x1fffffffull);                    // remainder r 2^(E-52)
+    const int p = 31 - __clz((int)r);                                     // leading bit of r (r > 0)
+    const unsigned frac = (p >= 23 ? (r >> (p - 23)) : (r << (23 - p))) & 0x7fffffu;
+    lo = r ? __uint_as_float(sign | ((unsigned)(E - 52 + p + 127) << 23) | frac) : 0.f;
+}
+
+// Exact float -> double from the bit pattern (integer operations; zero
+// included); subnormal and non-finite floats take the conversion instruction.
+__device__ __forceinline__ double cem_f2d(float f) {
+    const unsigned u = __float_as_uint(f);
+    const unsigned e = (u >> 23) & 0xffu;
+    if (e == 0xffu || (e == 0u && (u & 0x7fffffu))) return (double)f;
+    const unsigned long long sgn = (unsigned long long)(u & 0x80000000u) << 32;
+    const unsigned long long bits = e ? (sgn | ((unsigned long long)(e + 896u) << 52) |
+                                         ((unsigned long long)(u & 0x7fffffu) << 29))
+                                      : sgn;
+    return __longlong_as_double((long long)bits);
+}
+
 // Mixed precision: FP32 hi/lo record of a node's predicted displacement
 // (hi.xyz, lo.x | lo.y, lo.z, pad, pad), read by the strain kernel.
 __device__ __forceinline__ void cem_store_hl(float* uhl, int64_t i, const double x[3]) {
     float hi[3], lo[3];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        hi[c] = (float)x[c];
-        lo[c] = (float)(x[c] - (double)hi[c]);
-    }
+    for (int c = 0; c < 3; ++c) cem_split_hl(x[c], hi[c], lo[c]);
     float4* p = reinterpret_cast<float4*>(uhl + 8 * i);
     p[0] = make_float4(hi[0], hi[1], hi[2], lo[0]);
     p[1] = make_float4(lo[1], lo[2], 0.f, 0.f);

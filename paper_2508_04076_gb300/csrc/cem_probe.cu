@@ -60,3 +60,42 @@ extern "C" int cem_probe_fp64_fma(int device, void* stream_, double* flops_per_s
     *flops_per_s = flops / (best * 1e-3);
     return CEM_OK;
 }
+
+namespace {
+__global__ void k_probe_split(const double* __restrict__ x, const float* __restrict__ f, int64_t n,
+                              float* __restrict__ hi, float* __restrict__ lo, double* __restrict__ fd) {
+    const int64_t i = (int64_t)blockIdx.x * PB + threadIdx.x;
+    if (i >= n) return;
+    cem_split_hl(x[i], hi[i], lo[i]);
+    fd[i] = cem_f2d(f[i]);
+}
+}  // namespace
+
+extern "C" int cem_probe_split(const double* x, const float* f, int64_t n, float* hi, float* lo, double* fd) {
+    if (n < 0 || (n > 0 && (!x || !f || !hi || !lo || !fd))) return CEM_EINVAL;
+    if (n == 0) return CEM_OK;
+    double *dx = nullptr, *dfd = nullptr;
+    float *dff = nullptr, *dhi = nullptr, *dlo = nullptr;
+    int rc = CEM_OK;
+    if (cudaMalloc(&dx, n * sizeof(double)) != cudaSuccess || cudaMalloc(&dfd, n * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&dff, n * sizeof(float)) != cudaSuccess || cudaMalloc(&dhi, n * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&dlo, n * sizeof(float)) != cudaSuccess) {
+        rc = CEM_ENOMEM;
+    } else if (cudaMemcpy(dx, x, n * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
+               cudaMemcpy(dff, f, n * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess) {
+        rc = CEM_ECUDA;
+    } else {
+        k_probe_split<<<(unsigned)((n + PB - 1) / PB), PB>>>(dx, dff, n, dhi, dlo, dfd);
+        if (cudaGetLastError() != cudaSuccess ||
+            cudaMemcpy(hi, dhi, n * sizeof(float), cudaMemcpyDeviceToHost) != cudaSuccess ||
+            cudaMemcpy(lo, dlo, n * sizeof(float), cudaMemcpyDeviceToHost) != cudaSuccess ||
+            cudaMemcpy(fd, dfd, n * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
+            rc = CEM_ECUDA;
+    }
+    cudaFree(dx);
+    cudaFree(dfd);
+    cudaFree(dff);
+    cudaFree(dhi);
+    cudaFree(dlo);
+    return rc;
+}

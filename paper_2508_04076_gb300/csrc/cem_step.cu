@@ -339,7 +339,8 @@ __global__ void __launch_bounds__(BS) k_prescribe(int64_t n, const int* __restri
     a[comp * Nc + i] = aa;
     if (uhl) {
         const double x = cem_pred(u[comp * Nc + i], vv, aa, dt, 0.5 * dt * dt);
-        const float hi = (float)x, lo = (float)(x - (double)hi);
+        float hi, lo;
+        cem_split_hl(x, hi, lo);
         uhl[8 * (int64_t)i + comp] = hi;
         uhl[8 * (int64_t)i + 3 + comp] = lo;
     }
@@ -351,11 +352,16 @@ __global__ void __launch_bounds__(TB) k_node_update(const R* __restrict__ fp, co
                                                     const double* __restrict__ fext, const double* __restrict__ minv,
                                                     double* __restrict__ v, double* __restrict__ a, int64_t Nc,
                                                     int64_t N, double hdt, int first, const double* __restrict__ dtn,
-                                                    double* __restrict__ u, float* __restrict__ uhl, double coef) {
+                                                    double* __restrict__ u, float* __restrict__ uhl, double coef,
+                                                    double dt, double hdt2) {
     CEM_PDL_ENTRY();
     int64_t i = (int64_t)blockIdx.x * TB + threadIdx.x;
     if (i >= N) return;
-    if (dtn) hdt = 0.5 * dtn[i];
+    if (dtn) {   // the node's own specimen step; otherwise dt = 2 hdt and hdt2 = hdt dt come from the host
+        hdt = 0.5 * dtn[i];
+        dt = hdt + hdt;
+        hdt2 = hdt * dt;
+    }
     const int off = inc_off[i], cnt = inc_cnt[i];
     double f[3];
     constexpr int B = NB;
@@ -407,19 +413,19 @@ __global__ void __launch_bounds__(TB) k_node_update(const R* __restrict__ fp, co
                 }
         }
 #pragma unroll
-        for (int c = 0; c < 3; ++c) f[c] = (double)s[c] - (double)cmp[c];
+        for (int c = 0; c < 3; ++c) f[c] = cem_f2d(s[c]) - cem_f2d(cmp[c]);
     }
     // Explicitly rounded operations: whether the compiler would fuse a multiply
     // and an add here depends on the code around it, which differs between the
     // launch variants; fixing the roundings keeps every variant bit-identical.
     const double mi = minv[i];
+    const bool massless = __double_as_longlong(mi) == 0;   // a node no active element holds
     const double sixth = coef;   // 1 / (edges per element): the smoothing-volume share of Eq. 9
-    const double dt = hdt + hdt, hdt2 = hdt * dt;
     double un[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         const int64_t k = c * Nc + i;
-        const double an = (mi == 0.0) ? 0.0 : __dmul_rn(__fma_rn(-f[c], sixth, fext[k]), mi);
+        const double an = massless ? 0.0 : __dmul_rn(__fma_rn(-f[c], sixth, fext[k]), mi);
         const double ao = a[k], vo = v[k];
         double vn = vo;
         if (uhl) {   // fused predictor: u_n from the old state, then the next predictor
@@ -735,9 +741,10 @@ void launch_force(cem_ctx* c, int v, const R* sig, const R* Vg, R* fp) {
 
 template <class R, int TB, int NB>
 void go_node(cem_ctx* c, const R* fp, int first) {
+    const double hdt = 0.5 * c->dt, dt = hdt + hdt;   // as the kernel forms them from a per-node step
     cem_pdl(c->stream, k_node_update<R, TB, NB>, cem_grid(c->N, TB), TB, fp, c->inc_off, c->inc_cnt, c->inc_pool,
-            c->fext, c->minv, c->v, c->a, c->Nc, c->N, 0.5 * c->dt, first, c->dtn, c->u,
-            sizeof(R) == 4 ? c->uhl : nullptr, 1.0 / c->epe);
+            c->fext, c->minv, c->v, c->a, c->Nc, c->N, hdt, first, c->dtn, c->u,
+            sizeof(R) == 4 ? c->uhl : nullptr, 1.0 / c->epe, dt, hdt * dt);
 }
 template <class R, int NB>
 void go_node_tb(cem_ctx* c, int v, const R* fp, int first) {
