@@ -276,9 +276,9 @@ def run_cem(a):
             raise SystemExit("--save-at and --resume need --state PATH")
         sim = CEM.from_workload(w, device=dev, split_capacity=a.split_capacity, precision=a.precision)
         _reorder(sim, a)
-        if not a.no_autotune:
-            sim.autotune(reps=10, automatic=True)
         if a.save_at > 0:
+            if not a.no_autotune:
+                sim.autotune(reps=10, automatic=True)
             sim.step(a.save_at)
             sim.save(a.state)
             info = sim.info()
@@ -286,6 +286,8 @@ def run_cem(a):
                               "nodes": info["n_nodes"], "edges": info["n_edges"]}), flush=True)
         else:
             sim.load(a.state)
+            if not a.no_autotune:   # variants for the loaded mesh, tuned before the timed window
+                sim.autotune(reps=10, automatic=True)
             step0 = sim.energy()["step"]
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
@@ -295,6 +297,7 @@ def run_cem(a):
             info = sim.info()
             print(json.dumps({"resumed": a.state, "from_step": step0, "steps": a.steps,
                               "ms_per_step": e0.elapsed_time(e1) / max(a.steps, 1),
+                              "launch_variants": None if a.no_autotune else sim.tuning(),
                               "elements": info["n_active_tets"], "nodes": info["n_nodes"],
                               "edges": info["n_edges"]}), flush=True)
         sim.close()

@@ -315,7 +315,8 @@ int cem_profile_read(cem_ctx* ctx, double* ms, int64_t* launches, int n, int64_t
 int cem_autotune(cem_ctx* ctx, const char* cache_path, int reps, int automatic);
 int cem_tune_get(cem_ctx* ctx, int kernel, int* block, int* batch, double* us, double* default_us);
 /* Pin kernel k's variant (block in {128, 256, 512}; batch 1 for strain and
- * force, {1, 2, 4} for the edge stress, {2, 4, 8} for the node update).  An
+ * force, {2, 4, 8} for the edge stress, {2, 4, 8, 128} for the node update,
+ * where 128 selects warp-balanced gathers in rounds of 128 entries).  An
  * automatic autotuner may replace it when the kernel's bucket changes.
  * CEM_EINVAL for an unknown kernel or variant. */
 int cem_tune_set(cem_ctx* ctx, int kernel, int block, int batch);

@@ -224,6 +224,22 @@ __global__ void __launch_bounds__(TB) k_strain(const double* __restrict__ u, con
 // all indices, then all records, so several records are in flight per thread.
 // Sums keep the list's ascending order whatever the batch, so every variant
 // gives bit-identical results; the autotuner picks the fastest.
+__device__ __forceinline__ float fma_r(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_r(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+// Smoothed stress of edge k from H = sum over its fan of the element strain
+// records (Eqs. 5-6 with the fan-averaged elasticity folded into cl, cm):
+// sigma = cl tr(H) I + cm (2 H_normal, H_shear).  Explicit FMAs keep every
+// launch variant bit-identical.
+template <class R>
+__device__ __forceinline__ void edge_sigma(int64_t k, const R H[6], const R* __restrict__ cl,
+                                           const R* __restrict__ cm, R* __restrict__ sig) {
+    const R tr = H[0] + H[1] + H[2];
+    const R l = cl[k] * tr, m = cm[k], m2 = m + m;
+    const R s[6] = {fma_r(m2, H[0], l), fma_r(m2, H[1], l), fma_r(m2, H[2], l), m * H[3], m * H[4], m * H[5]};
+    Rec<R>::store6(sig + Rec<R>::S6 * k, s);
+}
+
 template <class R, int TB, int FB>
 __global__ void __launch_bounds__(TB) k_edge_stress(const R* __restrict__ h, const int* __restrict__ fan_off,
                                                     const int* __restrict__ fan_cnt, const int* __restrict__ fan_pool,
@@ -236,34 +252,26 @@ __global__ void __launch_bounds__(TB) k_edge_stress(const R* __restrict__ h, con
     // An edge whose fan emptied (every element around it split) is read by no
     // active element: its stress is left as it was (finite; its energy term has H = 0).
     if (cnt == 0) return;
+    // FB fan entries per round, then their FB records: a round costs two dependent
+    // loads whatever the fan size; sums stay in fan order (every FB gives the same bits)
     R H[6] = {0, 0, 0, 0, 0, 0};
-    int i = 0;
-    if constexpr (FB > 1) {
-        for (; i + FB <= cnt; i += FB) {
-            int jj[FB];
+    for (int i = 0; i < cnt; i += FB) {
+        int jj[FB];
 #pragma unroll
-            for (int b = 0; b < FB; ++b) jj[b] = fan_pool[off + i + b];
-            R x[FB][6];
+        for (int b = 0; b < FB; ++b) jj[b] = (i + b < cnt) ? fan_pool[off + i + b] : -1;
+        R x[FB][6];
 #pragma unroll
-            for (int b = 0; b < FB; ++b) Rec<R>::load6(h + Rec<R>::S6 * (int64_t)jj[b], x[b]);
+        for (int b = 0; b < FB; ++b)
+            if (jj[b] >= 0) Rec<R>::load6(h + Rec<R>::S6 * (int64_t)jj[b], x[b]);
 #pragma unroll
-            for (int b = 0; b < FB; ++b)
+        for (int b = 0; b < FB; ++b)
+            if (jj[b] >= 0)
 #pragma unroll
                 for (int q = 0; q < 6; ++q) H[q] += x[b][q];
-        }
     }
-    for (; i < cnt; ++i) {
-        const int j = fan_pool[off + i];
-        R x[6];
-        Rec<R>::load6(h + Rec<R>::S6 * (int64_t)j, x);
-#pragma unroll
-        for (int q = 0; q < 6; ++q) H[q] += x[q];
-    }
-    const R tr = H[0] + H[1] + H[2];
-    const R l = cl[k] * tr, m = cm[k], m2 = m + m;
-    const R s[6] = {m2 * H[0] + l, m2 * H[1] + l, m2 * H[2] + l, m * H[3], m * H[4], m * H[5]};
-    Rec<R>::store6(sig + Rec<R>::S6 * k, s);
+    edge_sigma(k, H, cl, cm, sig);
 }
+
 
 template <class R, int TB>
 __global__ void __launch_bounds__(TB) k_force(const R* __restrict__ sig, const int* __restrict__ t2e,
@@ -346,103 +354,174 @@ __global__ void __launch_bounds__(BS) k_prescribe(int64_t n, const int* __restri
     }
 }
 
-template <class R, int TB, int NB>
-__global__ void __launch_bounds__(TB) k_node_update(const R* __restrict__ fp, const int* __restrict__ inc_off,
-                                                    const int* __restrict__ inc_cnt, const int* __restrict__ inc_pool,
-                                                    const double* __restrict__ fext, const double* __restrict__ minv,
-                                                    double* __restrict__ v, double* __restrict__ a, int64_t Nc,
-                                                    int64_t N, double hdt, int first, const double* __restrict__ dtn,
-                                                    double* __restrict__ u, float* __restrict__ uhl, double coef,
-                                                    double dt, double hdt2) {
-    CEM_PDL_ENTRY();
-    int64_t i = (int64_t)blockIdx.x * TB + threadIdx.x;
-    if (i >= N) return;
-    if (dtn) {   // the node's own specimen step; otherwise dt = 2 hdt and hdt2 = hdt dt come from the host
-        hdt = 0.5 * dtn[i];
+// Sum of a node's element-force shares, in incidence-list order: FP64 adds, or
+// a compensated FP32 sum (Kahan) of the FP32 records in mixed precision.
+template <class R> struct NodeSum;
+template <> struct NodeSum<double> {
+    struct Slot { double x, y, z; };
+    double f[3] = {0.0, 0.0, 0.0};
+    __device__ static Slot load(const double* fp, int e) {   // entry = element * npe + local node
+        const double* p = fp + 3 * (int64_t)e;
+        return {p[0], p[1], p[2]};
+    }
+    __device__ void add(const Slot& x) {
+        f[0] += x.x;
+        f[1] += x.y;
+        f[2] += x.z;
+    }
+    __device__ void finish(double out[3]) const {
+        out[0] = f[0];
+        out[1] = f[1];
+        out[2] = f[2];
+    }
+};
+template <> struct NodeSum<float> {
+    using Slot = float4;
+    float s[3] = {0.f, 0.f, 0.f}, cmp[3] = {0.f, 0.f, 0.f};
+    __device__ static Slot load(const float* fp, int e) { return reinterpret_cast<const float4*>(fp)[e]; }
+    __device__ void add(const Slot& x) {
+        const float xv[3] = {x.x, x.y, x.z};
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float y = xv[c] - cmp[c];
+            const float t = s[c] + y;
+            cmp[c] = (t - s[c]) - y;
+            s[c] = t;
+        }
+    }
+    __device__ void finish(double out[3]) const {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) out[c] = cem_f2d(s[c]) - cem_f2d(cmp[c]);
+    }
+};
+
+struct NodeArgs {
+    const double *fext, *minv, *dtn;
+    double *v, *a, *u;
+    float* uhl;            // mixed precision: next-predictor records (fused predictor)
+    int64_t Nc, N;
+    double hdt, dt, hdt2;  // dt = 2 hdt and hdt2 = hdt dt, formed on the host
+    double coef;           // 1 / (edges per element): the smoothing-volume share of Eq. 9
+    int first;
+};
+
+// Eqs. 13-15 for node i from its summed element force f.  Explicitly rounded
+// operations: whether the compiler would fuse a multiply and an add here depends
+// on the code around it, which differs between the launch variants; fixing the
+// roundings keeps every variant bit-identical.
+__device__ __forceinline__ void node_integrate(const NodeArgs& A, int64_t i, const double f[3]) {
+    double hdt = A.hdt, dt = A.dt, hdt2 = A.hdt2;
+    if (A.dtn) {   // the node's own specimen step
+        hdt = 0.5 * A.dtn[i];
         dt = hdt + hdt;
         hdt2 = hdt * dt;
     }
-    const int off = inc_off[i], cnt = inc_cnt[i];
-    double f[3];
-    constexpr int B = NB;
-    if constexpr (sizeof(R) == 8) {
-        f[0] = f[1] = f[2] = 0.0;
-        for (int base = 0; base < cnt; base += B) {
-            int ee[B];
-#pragma unroll
-            for (int b = 0; b < B; ++b) ee[b] = (base + b < cnt) ? inc_pool[off + base + b] : -1;
-            double x[B][3];
-#pragma unroll
-            for (int b = 0; b < B; ++b)
-                if (ee[b] >= 0) {
-                    const double* p = fp + 3 * (int64_t)ee[b];   // entry = element * npe + local node
-                    x[b][0] = p[0];
-                    x[b][1] = p[1];
-                    x[b][2] = p[2];
-                }
-#pragma unroll
-            for (int b = 0; b < B; ++b)
-                if (ee[b] >= 0) {
-                    f[0] += x[b][0];
-                    f[1] += x[b][1];
-                    f[2] += x[b][2];
-                }
-        }
-    } else {
-        // compensated FP32 sum (Kahan) of the FP32 element forces
-        float s[3] = {0.f, 0.f, 0.f}, cmp[3] = {0.f, 0.f, 0.f};
-        for (int base = 0; base < cnt; base += B) {
-            int ee[B];
-#pragma unroll
-            for (int b = 0; b < B; ++b) ee[b] = (base + b < cnt) ? inc_pool[off + base + b] : -1;
-            float4 x[B];
-#pragma unroll
-            for (int b = 0; b < B; ++b)
-                if (ee[b] >= 0) x[b] = reinterpret_cast<const float4*>(fp)[ee[b]];
-#pragma unroll
-            for (int b = 0; b < B; ++b)
-                if (ee[b] >= 0) {
-                    const float xv[3] = {x[b].x, x[b].y, x[b].z};
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) {
-                        const float y = xv[c] - cmp[c];
-                        const float t = s[c] + y;
-                        cmp[c] = (t - s[c]) - y;
-                        s[c] = t;
-                    }
-                }
-        }
-#pragma unroll
-        for (int c = 0; c < 3; ++c) f[c] = cem_f2d(s[c]) - cem_f2d(cmp[c]);
-    }
-    // Explicitly rounded operations: whether the compiler would fuse a multiply
-    // and an add here depends on the code around it, which differs between the
-    // launch variants; fixing the roundings keeps every variant bit-identical.
-    const double mi = minv[i];
+    const double mi = A.minv[i];
     const bool massless = __double_as_longlong(mi) == 0;   // a node no active element holds
-    const double sixth = coef;   // 1 / (edges per element): the smoothing-volume share of Eq. 9
     double un[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        const int64_t k = c * Nc + i;
-        const double an = massless ? 0.0 : __dmul_rn(__fma_rn(-f[c], sixth, fext[k]), mi);
-        const double ao = a[k], vo = v[k];
+        const int64_t k = c * A.Nc + i;
+        const double an = massless ? 0.0 : __dmul_rn(__fma_rn(-f[c], A.coef, A.fext[k]), mi);
+        const double ao = A.a[k], vo = A.v[k];
         double vn = vo;
-        if (uhl) {   // fused predictor: u_n from the old state, then the next predictor
-            double uc = u[k];
-            if (!first) {
+        if (A.uhl) {   // fused predictor: u_n from the old state, then the next predictor
+            double uc = A.u[k];
+            if (!A.first) {
                 uc = cem_pred(uc, vo, ao, dt, hdt2);
-                u[k] = uc;
+                A.u[k] = uc;
             }
-            if (!first) vn = __fma_rn(hdt, __dadd_rn(ao, an), vo);
+            if (!A.first) vn = __fma_rn(hdt, __dadd_rn(ao, an), vo);
             un[c] = cem_pred(uc, vn, an, dt, hdt2);
-        } else if (!first) {
+        } else if (!A.first) {
             vn = __fma_rn(hdt, __dadd_rn(ao, an), vo);
         }
-        if (!first) v[k] = vn;
-        a[k] = an;
+        if (!A.first) A.v[k] = vn;
+        A.a[k] = an;
     }
-    if (uhl) cem_store_hl(uhl, i, un);
+    if (A.uhl) cem_store_hl(A.uhl, i, un);
+}
+
+// One thread per node: NB incidence entries, then their NB records, per round.
+template <class R, int TB, int NB>
+__global__ void __launch_bounds__(TB) k_node_update(const R* __restrict__ fp, const int* __restrict__ inc_off,
+                                                    const int* __restrict__ inc_cnt, const int* __restrict__ inc_pool,
+                                                    NodeArgs A) {
+    CEM_PDL_ENTRY();
+    const int64_t i = (int64_t)blockIdx.x * TB + threadIdx.x;
+    if (i >= A.N) return;
+    const int off = inc_off[i], cnt = inc_cnt[i];
+    NodeSum<R> acc;
+    for (int base = 0; base < cnt; base += NB) {
+        int ee[NB];
+#pragma unroll
+        for (int b = 0; b < NB; ++b) ee[b] = (base + b < cnt) ? inc_pool[off + base + b] : -1;
+        typename NodeSum<R>::Slot x[NB];
+#pragma unroll
+        for (int b = 0; b < NB; ++b)
+            if (ee[b] >= 0) x[b] = NodeSum<R>::load(fp, ee[b]);
+#pragma unroll
+        for (int b = 0; b < NB; ++b)
+            if (ee[b] >= 0) acc.add(x[b]);
+    }
+    double f[3];
+    acc.finish(f);
+    node_integrate(A, i, f);
+}
+
+// Warp-balanced gathers: a node with a long incidence list (an input node next
+// to many split elements: up to 3 sub-elements replace each parent) holds its
+// whole warp in the per-thread form.  Here a warp takes its 32 nodes' lists
+// as one sequence and gathers it in rounds of 128 entries, 4 per lane, into
+// shared memory; each lane then adds its own node's entries of the round in
+// list order, so the sums are those of the per-thread form, bit for bit.
+constexpr int NODE_ROUND = 128;
+
+template <class R, int TB>
+__global__ void __launch_bounds__(TB) k_node_update_bal(const R* __restrict__ fp, const int* __restrict__ inc_off,
+                                                        const int* __restrict__ inc_cnt,
+                                                        const int* __restrict__ inc_pool, NodeArgs A) {
+    CEM_PDL_ENTRY();
+    using Slot = typename NodeSum<R>::Slot;
+    __shared__ Slot buf[TB / 32][NODE_ROUND];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t i = (int64_t)blockIdx.x * TB + threadIdx.x;
+    const bool valid = i < A.N;
+    const int off = valid ? inc_off[i] : 0, cnt = valid ? inc_cnt[i] : 0;
+    int incl = cnt;   // inclusive scan of the warp's list lengths
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    const int excl = incl - cnt;
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    NodeSum<R> acc;
+    for (int r = 0; r < total; r += NODE_ROUND) {
+        int ee[NODE_ROUND / 32];
+#pragma unroll
+        for (int b = 0; b < NODE_ROUND / 32; ++b) {
+            const int q = r + 32 * b + lane;               // position in the warp's sequence
+            const int qc = min(q, total - 1);
+            int o = 0;                                      // owner: the first lane with incl > qc
+#pragma unroll
+            for (int step = 16; step > 0; step >>= 1)
+                if (__shfl_sync(0xffffffffu, incl, o + step - 1) <= qc) o += step;
+            const int o_off = __shfl_sync(0xffffffffu, off, o), o_excl = __shfl_sync(0xffffffffu, excl, o);
+            ee[b] = (q < total) ? inc_pool[o_off + (qc - o_excl)] : -1;
+        }
+#pragma unroll
+        for (int b = 0; b < NODE_ROUND / 32; ++b)
+            if (ee[b] >= 0) buf[w][32 * b + lane] = NodeSum<R>::load(fp, ee[b]);
+        __syncwarp();
+        const int q1 = min(incl, r + NODE_ROUND);
+        for (int q = max(excl, r); q < q1; ++q) acc.add(buf[w][q - r]);
+        __syncwarp();
+    }
+    if (!valid) return;
+    double f[3];
+    acc.finish(f);
+    node_integrate(A, i, f);
 }
 
 // Mixed precision: FP32 hi/lo record of the next predictor u + dt v + dt^2/2 a
@@ -720,9 +799,9 @@ void go_edge_tb(cem_ctx* c, int v, const R* h, const R* cl, const R* cm, R* sig)
 template <class R>
 void launch_edge(cem_ctx* c, int v, const R* h, const R* cl, const R* cm, R* sig) {
     switch (v / 3) {
-        case 0: go_edge_tb<R, 1>(c, v, h, cl, cm, sig); break;
-        case 1: go_edge_tb<R, 2>(c, v, h, cl, cm, sig); break;
-        default: go_edge_tb<R, 4>(c, v, h, cl, cm, sig);
+        case 0: go_edge_tb<R, 2>(c, v, h, cl, cm, sig); break;
+        case 1: go_edge_tb<R, 4>(c, v, h, cl, cm, sig); break;
+        default: go_edge_tb<R, 8>(c, v, h, cl, cm, sig);
     }
 }
 
@@ -739,12 +818,34 @@ void launch_force(cem_ctx* c, int v, const R* sig, const R* Vg, R* fp) {
     }
 }
 
+NodeArgs node_args(cem_ctx* c, bool mixed_records, int first) {
+    NodeArgs A;
+    A.fext = c->fext;
+    A.minv = c->minv;
+    A.dtn = c->dtn;
+    A.v = c->v;
+    A.a = c->a;
+    A.u = c->u;
+    A.uhl = mixed_records ? c->uhl : nullptr;
+    A.Nc = c->Nc;
+    A.N = c->N;
+    A.hdt = 0.5 * c->dt;   // as the kernels form them from a per-node step
+    A.dt = A.hdt + A.hdt;
+    A.hdt2 = A.hdt * A.dt;
+    A.coef = 1.0 / c->epe;
+    A.first = first;
+    return A;
+}
+
 template <class R, int TB, int NB>
 void go_node(cem_ctx* c, const R* fp, int first) {
-    const double hdt = 0.5 * c->dt, dt = hdt + hdt;   // as the kernel forms them from a per-node step
-    cem_pdl(c->stream, k_node_update<R, TB, NB>, cem_grid(c->N, TB), TB, fp, c->inc_off, c->inc_cnt, c->inc_pool,
-            c->fext, c->minv, c->v, c->a, c->Nc, c->N, hdt, first, c->dtn, c->u,
-            sizeof(R) == 4 ? c->uhl : nullptr, 1.0 / c->epe, dt, hdt * dt);
+    const NodeArgs A = node_args(c, sizeof(R) == 4, first);
+    if constexpr (NB == NODE_ROUND)
+        cem_pdl(c->stream, k_node_update_bal<R, TB>, cem_grid(c->N, TB), TB, fp, c->inc_off, c->inc_cnt,
+                c->inc_pool, A);
+    else
+        cem_pdl(c->stream, k_node_update<R, TB, NB>, cem_grid(c->N, TB), TB, fp, c->inc_off, c->inc_cnt,
+                c->inc_pool, A);
 }
 template <class R, int NB>
 void go_node_tb(cem_ctx* c, int v, const R* fp, int first) {
@@ -759,7 +860,8 @@ void launch_node(cem_ctx* c, int v, const R* fp, int first) {
     switch (v / 3) {
         case 0: go_node_tb<R, 2>(c, v, fp, first); break;
         case 1: go_node_tb<R, 4>(c, v, fp, first); break;
-        default: go_node_tb<R, 8>(c, v, fp, first);
+        case 2: go_node_tb<R, 8>(c, v, fp, first); break;
+        default: go_node_tb<R, NODE_ROUND>(c, v, fp, first);
     }
 }
 
@@ -1076,17 +1178,18 @@ int cem_launch_node_update(cem_ctx* c, int first) {
 // ---- tuning variants: variant v of a kernel runs TB = 128 << (v % 3) threads per
 // block and the kernel's batch parameter BATCH[kernel][v / 3]
 namespace {
-constexpr int TUNE_BATCH[TUNE_COUNT][3] = {{1, 1, 1}, {1, 2, 4}, {1, 1, 1}, {2, 4, 8}};
+// (the node update's fourth batch value selects the warp-balanced kernel)
+constexpr int TUNE_BATCH[TUNE_COUNT][4] = {{1, 1, 1, 1}, {2, 4, 8, 8}, {1, 1, 1, 1}, {2, 4, 8, NODE_ROUND}};
 }  // namespace
 
-int cem_tune_variants(int k) { return (k == TUNE_EDGE || k == TUNE_NODE) ? 9 : 3; }
+int cem_tune_variants(int k) { return k == TUNE_NODE ? 12 : k == TUNE_EDGE ? 9 : 3; }
 
 void cem_tune_describe(int k, int v, int* block, int* batch) {
     *block = 128 << (v % 3);
     *batch = TUNE_BATCH[k][v / 3];
 }
 
-// The variants used before any tuning: 256 threads, plain fans, node batches of 8 (FP32) or 4 (FP64).
+// The variants used before any tuning: 256 threads, fan rounds of 2, node batches of 8 (FP32) or 4 (FP64).
 int cem_tune_default(int k, int precision) {
     if (k == TUNE_NODE) return 1 + 3 * (precision == CEM_MIXED ? 2 : 1);
     return 1;
