@@ -77,15 +77,28 @@ __device__ __forceinline__ double cem_f2d(float f) {
     return __longlong_as_double((long long)bits);
 }
 
+// 32-byte records (8 floats, 32-byte aligned) in one memory request each:
+// the 256-bit vector load and store of sm_100 and later.  The load takes the
+// read-only path: no kernel reads a record it writes.
+__device__ __forceinline__ void cem_ld8(const float* p, float v[8]) {
+    asm volatile("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7])
+                 : "l"(p));
+}
+__device__ __forceinline__ void cem_st8(float* p, const float v[8]) {
+    asm volatile("st.global.v8.f32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p), "f"(v[0]), "f"(v[1]),
+                 "f"(v[2]), "f"(v[3]), "f"(v[4]), "f"(v[5]), "f"(v[6]), "f"(v[7])
+                 : "memory");
+}
+
 // Mixed precision: FP32 hi/lo record of a node's predicted displacement
 // (hi.xyz, lo.x | lo.y, lo.z, pad, pad), read by the strain kernel.
 __device__ __forceinline__ void cem_store_hl(float* uhl, int64_t i, const double x[3]) {
-    float hi[3], lo[3];
+    float r[8];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) cem_split_hl(x[c], hi[c], lo[c]);
-    float4* p = reinterpret_cast<float4*>(uhl + 8 * i);
-    p[0] = make_float4(hi[0], hi[1], hi[2], lo[0]);
-    p[1] = make_float4(lo[1], lo[2], 0.f, 0.f);
+    for (int c = 0; c < 3; ++c) cem_split_hl(x[c], r[c], r[3 + c]);
+    r[6] = r[7] = 0.f;
+    cem_st8(uhl + 8 * i, r);
 }
 
 #define CEM_LE0(l) (((l) < 3) ? 0 : (((l) < 5) ? 1 : 2))

@@ -61,13 +61,14 @@ template <> struct Rec<float> {
     static constexpr int S6 = 8;
     static constexpr int SF = 16;    // 4 values (3 + pad) per local node
     __device__ static void load6(const float* p, float v[6]) {
-        const float4 a = reinterpret_cast<const float4*>(p)[0];
-        const float2 b = reinterpret_cast<const float2*>(p)[2];
-        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y;
+        float r[8];
+        cem_ld8(p, r);
+#pragma unroll
+        for (int q = 0; q < 6; ++q) v[q] = r[q];
     }
     __device__ static void store6(float* p, const float v[6]) {
-        reinterpret_cast<float4*>(p)[0] = make_float4(v[0], v[1], v[2], v[3]);
-        reinterpret_cast<float4*>(p)[1] = make_float4(v[4], v[5], 0.f, 0.f);
+        const float r[8] = {v[0], v[1], v[2], v[3], v[4], v[5], 0.f, 0.f};
+        cem_st8(p, r);
     }
 };
 
@@ -149,15 +150,9 @@ __global__ void __launch_bounds__(BS) k_split_u(const double* __restrict__ u, in
     CEM_PDL_ENTRY();
     int64_t i = (int64_t)blockIdx.x * BS + threadIdx.x;
     if (i >= N) return;
-    float hi[3], lo[3];
-    for (int c = 0; c < 3; ++c) {
-        const double x = u[c * Nc + i];
-        hi[c] = (float)x;
-        lo[c] = (float)(x - (double)hi[c]);
-    }
-    float4* p = reinterpret_cast<float4*>(uhl + 8 * i);
-    p[0] = make_float4(hi[0], hi[1], hi[2], lo[0]);
-    p[1] = make_float4(lo[1], lo[2], 0.f, 0.f);
+    double x[3];
+    for (int c = 0; c < 3; ++c) x[c] = u[c * Nc + i];
+    cem_store_hl(uhl, i, x);
 }
 
 template <class R>
@@ -183,11 +178,10 @@ __device__ __forceinline__ void node_disp_diff<float>(const double*, const float
     float hi[4][3], lo[4][3];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-        const float4* p = reinterpret_cast<const float4*>(uhl + 8 * (int64_t)n[q]);
-        const float4 a = p[0];
-        const float2 b = reinterpret_cast<const float2*>(p + 1)[0];
-        hi[q][0] = a.x; hi[q][1] = a.y; hi[q][2] = a.z;
-        lo[q][0] = a.w; lo[q][1] = b.x; lo[q][2] = b.y;
+        float r[8];
+        cem_ld8(uhl + 8 * (int64_t)n[q], r);
+        hi[q][0] = r[0]; hi[q][1] = r[1]; hi[q][2] = r[2];
+        lo[q][0] = r[3]; lo[q][1] = r[4]; lo[q][2] = r[5];
     }
 #pragma unroll
     for (int a = 0; a < 3; ++a)
@@ -316,9 +310,10 @@ __global__ void __launch_bounds__(TB) k_force(const R* __restrict__ sig, const i
         p[4] = make_double2(f[2][2], f[3][0]);
         p[5] = make_double2(f[3][1], f[3][2]);
     } else {
-        float4* p = reinterpret_cast<float4*>(o);
-#pragma unroll
-        for (int a = 0; a < 4; ++a) p[a] = make_float4(f[a][0], f[a][1], f[a][2], 0.f);
+        const float r0[8] = {f[0][0], f[0][1], f[0][2], 0.f, f[1][0], f[1][1], f[1][2], 0.f};
+        const float r1[8] = {f[2][0], f[2][1], f[2][2], 0.f, f[3][0], f[3][1], f[3][2], 0.f};
+        cem_st8(o, r0);
+        cem_st8(o + 8, r1);
     }
 }
 
