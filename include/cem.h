@@ -287,18 +287,20 @@ int cem_profile_read(cem_ctx* ctx, double* ms, int64_t* launches, int n, int64_t
  * CEM_TUNE_FORCE (per-element forces) and CEM_TUNE_NODE (node update, a
  * gather over each node's element incidence).  A variant is a block size
  * (128, 256 or 512 threads) and, for the two gathers, how many list entries
- * have their loads issued together (fan: 1, 2 or 4; incidence: 2, 4 or 8).
+ * have their loads issued together (fan: 2, 4 or 8; incidence: 2, 4 or 8, or
+ * 128 for warp-balanced rounds of up to 128 entries).
  * All variants of a kernel compute the same values in the same order: the
  * choice never changes results, only speed.
  *
  * cem_autotune times every variant on the context's current mesh and state
  * (CUDA events, one warm-up launch then `reps` launches; reps <= 0 means 5),
  * keeps the fastest, and records it under (GPU name, kernel, precision,
- * floor(log2(item count))).  cache_path (may be NULL) names a text file that
- * is read first (entries found there are used without timing) and appended
- * with new results.  automatic != 0 makes cem_step re-tune a kernel (from the
- * cache when possible) whenever its item count (elements, edges or nodes)
- * enters a new power-of-two bucket.  The state of the simulation is
+ * size bucket): floor(log2(item count)), floor(2 log2(node count)) for the
+ * node update.  cache_path (may be NULL) names a text file that is read first
+ * (entries found there are used without timing) and appended with new
+ * results.  automatic != 0 makes cem_step re-tune a kernel (from the cache
+ * when possible) whenever its item count (elements, edges or nodes) enters a
+ * new bucket.  The state of the simulation is
  * unchanged.  The first call allocates one 3 x (node capacity) double buffer
  * through the context's allocator, held until cem_destroy.  Errors:
  * CEM_ESTATE (no material), CEM_EINVAL, CEM_ENOMEM, CEM_ECUDA.

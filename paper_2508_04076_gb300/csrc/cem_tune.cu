@@ -4,15 +4,16 @@
 // Four kernels have variants: the element strain, the edge stress (fan
 // gather), the element force and the node update (incidence gather).  A
 // variant is a block size (128, 256 or 512 threads) and, for the two gather
-// kernels, the number of list entries whose loads are issued together (1/2/4
-// fan entries, 2/4/8 incidence entries).  Every variant of a kernel performs
-// the same arithmetic in the same order, so the choice never changes results.
+// kernels, the number of list entries whose loads are issued together (2/4/8
+// fan entries, 2/4/8 incidence entries or the node update's warp-balanced
+// form).  Every variant of a kernel performs the same arithmetic in the same
+// order, so the choice never changes results.
 //
 // Tuning times each variant on the context's current mesh and state with CUDA
 // events (one warm-up launch, then `reps` launches) and keeps the fastest.
 // Results are keyed by (GPU name, kernel, precision, size bucket), where the
 // bucket is floor(log2(items)) of the kernel's item count (elements, edges or
-// nodes).  They are kept in memory and, when a cache path is given, in a text
+// nodes), floor(2 log2(items)) for the node update.  They are kept in memory and, when a cache path is given, in a text
 // file with one "gpu<TAB>kernel<TAB>precision<TAB>bucket<TAB>block<TAB>batch<TAB>us"
 // line per entry, read before tuning and appended after it.  In automatic mode
 // cem_step re-tunes a kernel (from the cache when it can) whenever its item
@@ -45,7 +46,14 @@ int items(const cem_ctx* c, int k) {
     return (int)std::max<int64_t>(1, (k == TUNE_EDGE) ? c->E : (k == TUNE_NODE ? c->N : c->T));
 }
 
-int bucket_of(int64_t n) { return n <= 1 ? 0 : (int)std::floor(std::log2((double)n)); }
+// The node update's best variant also moves with the shape of its lists: after the
+// specimen breaks, incidence lists grow a long tail that favours the warp-balanced
+// form.  It is re-tuned at every half octave of its node count, the others at octaves.
+int bucket_of(int k, int64_t n) {
+    if (n <= 1) return 0;
+    const double l = std::log2((double)n);
+    return (int)std::floor(k == TUNE_NODE ? 2.0 * l : l);
+}
 
 std::string gpu_name(cem_ctx* c) {
     cudaDeviceProp p;
@@ -115,7 +123,7 @@ int time_variant(cem_ctx* c, int k, int v, int reps, cudaEvent_t e0, cudaEvent_t
 
 // Tune kernel k for the current sizes (cache first), set c->tune[k].
 int tune_kernel(cem_ctx* c, int k, const std::string& gpu) {
-    const int b = bucket_of(items(c, k));
+    const int b = bucket_of(k, items(c, k));
     const Key key(gpu, k, c->precision, b);
     c->tune_bucket[k] = b;
     {
@@ -172,7 +180,7 @@ int cem_tune_maybe(cem_ctx* c) {
     if (!c->tune_auto) return CEM_OK;
     std::string gpu;
     for (int k = 0; k < TUNE_COUNT; ++k)
-        if (bucket_of(items(c, k)) != c->tune_bucket[k]) {
+        if (bucket_of(k, items(c, k)) != c->tune_bucket[k]) {
             if (gpu.empty()) gpu = gpu_name(c);
             if (int rc = tune_kernel(c, k, gpu)) return rc;
         }
