@@ -167,6 +167,90 @@ __device__ __forceinline__ int normalize_side(int m) { return (m & 1) ? ((~m) & 
 //                  largest, ties to the lowest face.
 constexpr int FB = 64;   // threads per block of the front kernels (small blocks reach every SM)
 
+// One front face: whether the split neighbour across local face f of candidate t
+// cuts two of its edges, and if so the face's stretch products |d.n| (Eq. 16),
+// normals n_I, n_II (Appendix I), its three edges ad, bd, cd and the side masks
+// of modes I and II (packed mask_I | mask_II << 4; 0 for a face not cut twice).
+struct FrontFace {
+    int mask;
+    double prod[4], nrm[6];
+    int edge[3];
+};
+
+__device__ __forceinline__ FrontFace front_face(int t, int f, const int* __restrict__ conn,
+                                                const int* __restrict__ t2e, int64_t Tc,
+                                                const int* __restrict__ face_nbr, const uint8_t* __restrict__ side,
+                                                int64_t T0, const double* __restrict__ X,
+                                                const double* __restrict__ u, int64_t Nc) {
+    FrontFace F;
+    F.mask = 0;
+    const int s = face_nbr[f * T0 + t];
+    const int ms = (s >= 0) ? side[s] : 0;
+    if (!ms) return F;
+    int tn[4], sn[4];
+    for (int l = 0; l < 4; ++l) {
+        tn[l] = conn[l * Tc + t];
+        sn[l] = conn[l * Tc + s];
+    }
+    int fl[3], k = 0;
+    for (int l = 0; l < 4; ++l)
+        if (l != f) fl[k++] = l;
+    int bit[3];
+    for (int q = 0; q < 3; ++q) {
+        bit[q] = 0;
+        for (int r = 0; r < 4; ++r)
+            if (sn[r] == tn[fl[q]]) bit[q] = (ms >> r) & 1;
+    }
+    if (bit[0] == bit[1] && bit[1] == bit[2]) return F;   // not two cut edges on this face
+    const int apex = (bit[0] == bit[1]) ? 2 : ((bit[0] == bit[2]) ? 1 : 0);
+    const int cl_ = fl[apex];
+    const int al = fl[apex == 0 ? 1 : 0];
+    const int bl = fl[apex == 2 ? 1 : 2];
+    const int dl = f;
+    const int a = tn[al], c = tn[cl_], b = tn[bl], d = tn[dl];
+    double d1[3], d2[3];
+    stretch(X, u, Nc, a, c, d1);
+    stretch(X, u, Nc, c, b, d2);
+    double Xa[3], Xb[3], Xc[3], Xd[3];
+    load3(X, Nc, a, Xa);
+    load3(X, Nc, b, Xb);
+    load3(X, Nc, c, Xc);
+    load3(X, Nc, d, Xd);
+    double ba[3] = {Xb[0] - Xa[0], Xb[1] - Xa[1], Xb[2] - Xa[2]};
+    double dc[3] = {Xd[0] - Xc[0], Xd[1] - Xc[1], Xd[2] - Xc[2]};
+    double da[3] = {Xd[0] - Xa[0], Xd[1] - Xa[1], Xd[2] - Xa[2]};
+    double nI[3], nII[3];
+    cross3(ba, dc, nI);
+    cross3(ba, da, nII);
+    const double iI = 1.0 / sqrt(dot3(nI, nI)), iII = 1.0 / sqrt(dot3(nII, nII));
+    for (int q = 0; q < 3; ++q) {
+        nI[q] *= iI;
+        nII[q] *= iII;
+        F.nrm[q] = nI[q];
+        F.nrm[3 + q] = nII[q];
+    }
+    F.prod[0] = fabs(dot3(d1, nI));
+    F.prod[1] = fabs(dot3(d2, nI));
+    F.prod[2] = fabs(dot3(d1, nII));
+    F.prod[3] = fabs(dot3(d2, nII));
+    F.edge[0] = t2e[local_edge(al, dl) * Tc + t];
+    F.edge[1] = t2e[local_edge(bl, dl) * Tc + t];
+    F.edge[2] = t2e[local_edge(cl_, dl) * Tc + t];
+    F.mask = normalize_side((1 << cl_) | (1 << dl)) | (normalize_side(1 << cl_) << 4);
+    return F;
+}
+
+// G of one face from its projections s_ad, s_bd, s_cd and stretch products
+// (Eqs. 17-18, explicit roundings); *mode_mask is the side mask of the larger mode.
+__device__ __forceinline__ double face_G(int mk, const double s[3], double p0, double p1, double p2, double p3,
+                                         int* mode_mask) {
+    const double GI = 0.5 * __dadd_rn(__dmul_rn(s[0], p0), __dmul_rn(s[1], p1));
+    const double GII = 0.5 * __dadd_rn(__dmul_rn(s[2], p2), __dmul_rn(s[2], p3));
+    const bool modeI = GI >= GII;
+    *mode_mask = modeI ? (mk & 15) : (mk >> 4);
+    return modeI ? GI : GII;
+}
+
 __global__ void __launch_bounds__(FB) k_front_faces(const int* __restrict__ cand, int nc,
                                                     const int* __restrict__ conn, const int* __restrict__ t2e,
                                                     int64_t Tc, const int* __restrict__ face_nbr,
@@ -181,65 +265,14 @@ __global__ void __launch_bounds__(FB) k_front_faces(const int* __restrict__ cand
     const int ci = tid >> 2, f = tid & 3;
     bool cut = false;
     if (ci < nc) {
-        const int t = cand[ci];
-        const int s = face_nbr[f * T0 + t];
-        const int ms = (s >= 0) ? side[s] : 0;
-        int mk = 0;
-        if (ms) {
-            int tn[4], sn[4];
-            for (int l = 0; l < 4; ++l) {
-                tn[l] = conn[l * Tc + t];
-                sn[l] = conn[l * Tc + s];
-            }
-            int fl[3], k = 0;
-            for (int l = 0; l < 4; ++l)
-                if (l != f) fl[k++] = l;
-            int bit[3];
-            for (int q = 0; q < 3; ++q) {
-                bit[q] = 0;
-                for (int r = 0; r < 4; ++r)
-                    if (sn[r] == tn[fl[q]]) bit[q] = (ms >> r) & 1;
-            }
-            if (!(bit[0] == bit[1] && bit[1] == bit[2])) {   // two cut edges on this face
-                cut = true;
-                const int apex = (bit[0] == bit[1]) ? 2 : ((bit[0] == bit[2]) ? 1 : 0);
-                const int cl_ = fl[apex];
-                const int al = fl[apex == 0 ? 1 : 0];
-                const int bl = fl[apex == 2 ? 1 : 2];
-                const int dl = f;
-                const int a = tn[al], c = tn[cl_], b = tn[bl], d = tn[dl];
-                double d1[3], d2[3];
-                stretch(X, u, Nc, a, c, d1);
-                stretch(X, u, Nc, c, b, d2);
-                double Xa[3], Xb[3], Xc[3], Xd[3];
-                load3(X, Nc, a, Xa);
-                load3(X, Nc, b, Xb);
-                load3(X, Nc, c, Xc);
-                load3(X, Nc, d, Xd);
-                double ba[3] = {Xb[0] - Xa[0], Xb[1] - Xa[1], Xb[2] - Xa[2]};
-                double dc[3] = {Xd[0] - Xc[0], Xd[1] - Xc[1], Xd[2] - Xc[2]};
-                double da[3] = {Xd[0] - Xa[0], Xd[1] - Xa[1], Xd[2] - Xa[2]};
-                double nI[3], nII[3];
-                cross3(ba, dc, nI);
-                cross3(ba, da, nII);
-                const double iI = 1.0 / sqrt(dot3(nI, nI)), iII = 1.0 / sqrt(dot3(nII, nII));
-                for (int q = 0; q < 3; ++q) {
-                    nI[q] *= iI;
-                    nII[q] *= iII;
-                    ff_nrm[q * cap4 + tid] = nI[q];
-                    ff_nrm[(3 + q) * cap4 + tid] = nII[q];
-                }
-                ff_prod[tid] = fabs(dot3(d1, nI));
-                ff_prod[cap4 + tid] = fabs(dot3(d2, nI));
-                ff_prod[2 * cap4 + tid] = fabs(dot3(d1, nII));
-                ff_prod[3 * cap4 + tid] = fabs(dot3(d2, nII));
-                ff_edge[tid] = t2e[local_edge(al, dl) * Tc + t];
-                ff_edge[cap4 + tid] = t2e[local_edge(bl, dl) * Tc + t];
-                ff_edge[2 * cap4 + tid] = t2e[local_edge(cl_, dl) * Tc + t];
-                mk = normalize_side((1 << cl_) | (1 << dl)) | (normalize_side(1 << cl_) << 4);
-            }
+        const FrontFace F = front_face(cand[ci], f, conn, t2e, Tc, face_nbr, side, T0, X, u, Nc);
+        if (F.mask) {
+            cut = true;
+            for (int q = 0; q < 6; ++q) ff_nrm[q * cap4 + tid] = F.nrm[q];
+            for (int q = 0; q < 4; ++q) ff_prod[q * cap4 + tid] = F.prod[q];
+            for (int q = 0; q < 3; ++q) ff_edge[q * cap4 + tid] = F.edge[q];
         }
-        ff_mask[tid] = mk;
+        ff_mask[tid] = F.mask;
     }
     // queue the three projections of every face cut twice (one atomic per warp)
     const unsigned ball = __ballot_sync(0xffffffffu, cut);
@@ -293,19 +326,92 @@ __global__ void __launch_bounds__(FB) k_front_pick(const int* __restrict__ cand,
         const int face = 4 * ci + f;
         const int mk = ff_mask[face];
         if (!mk) continue;
-        const double* s = ff_s + 3 * (int64_t)face;
-        const double GI = 0.5 * __dadd_rn(__dmul_rn(s[0], ff_prod[face]), __dmul_rn(s[1], ff_prod[cap4 + face]));
-        const double GII =
-            0.5 * __dadd_rn(__dmul_rn(s[2], ff_prod[2 * cap4 + face]), __dmul_rn(s[2], ff_prod[3 * cap4 + face]));
-        const bool modeI = GI >= GII;
-        const double Gf = modeI ? GI : GII;
+        int mf;
+        const double Gf = face_G(mk, ff_s + 3 * (int64_t)face, ff_prod[face], ff_prod[cap4 + face],
+                                 ff_prod[2 * cap4 + face], ff_prod[3 * cap4 + face], &mf);
         if (Gf > G) {
             G = Gf;
-            mask = modeI ? (mk & 15) : (mk >> 4);
+            mask = mf;
         }
     }
     dec_G[ci] = G;
     dec_mask[ci] = (mask != 0 && G > Gc[cand[ci]]) ? (uint8_t)mask : (uint8_t)0;
+}
+
+// The whole front evaluation of a short candidate list (after the specimen has
+// broken, a handful of elements) in one block: faces, queued projections, the
+// pick and the ordered compaction of the decisions, in shared memory.  The
+// values are those of the three-kernel form (same functions, same roundings),
+// and the splits come out in candidate order, as the ordered scan gives them.
+constexpr int FRONT_SMALL = 16;   // candidates
+constexpr int FS_T = 128;         // threads
+
+__global__ void __launch_bounds__(FS_T) k_front_small(const int* __restrict__ cand, int nc,
+                                                      const int* __restrict__ conn, const int* __restrict__ t2e,
+                                                      int64_t Tc, const int* __restrict__ face_nbr,
+                                                      const uint8_t* __restrict__ side, int64_t T0,
+                                                      const double* __restrict__ X, const double* __restrict__ u,
+                                                      int64_t Nc, const double* __restrict__ sig,
+                                                      const float* __restrict__ sig32, const double* __restrict__ Gc,
+                                                      int gvar, int* __restrict__ split_list,
+                                                      uint8_t* __restrict__ split_mask, double* __restrict__ split_G,
+                                                      long long* __restrict__ count, long long* __restrict__ nk) {
+    CEM_PDL_ENTRY();
+    __shared__ FrontFace face[4 * FRONT_SMALL];
+    __shared__ int items[12 * FRONT_SMALL];
+    __shared__ double sval[12 * FRONT_SMALL];
+    __shared__ int n_items;
+    __shared__ int d_mask[FRONT_SMALL];
+    __shared__ double d_G[FRONT_SMALL];
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        n_items = 0;
+        *nk = 0;   // new-key counter of this step's splits
+    }
+    __syncthreads();
+    for (int it = tid; it < 4 * nc; it += FS_T) {
+        face[it] = front_face(cand[it >> 2], it & 3, conn, t2e, Tc, face_nbr, side, T0, X, u, Nc);
+        if (face[it].mask) {
+            const int r = atomicAdd(&n_items, 3);
+            for (int q = 0; q < 3; ++q) items[r + q] = 3 * it + q;
+        }
+    }
+    __syncthreads();
+    for (int i = tid; i < n_items; i += FS_T) {
+        const int it = items[i], fc = it / 3, q = it - 3 * fc;
+        const double* nr = face[fc].nrm + (q < 2 ? 0 : 3);
+        const double n[3] = {nr[0], nr[1], nr[2]};
+        sval[it] = edge_projection(sig, sig32, face[fc].edge[q], n, gvar);
+    }
+    __syncthreads();
+    for (int ci = tid; ci < nc; ci += FS_T) {
+        double G = -1.0 / 0.0;
+        int mask = 0;
+        for (int f = 0; f < 4; ++f) {
+            const FrontFace& F = face[4 * ci + f];
+            if (!F.mask) continue;
+            int mf;
+            const double Gf = face_G(F.mask, sval + 3 * (4 * ci + f), F.prod[0], F.prod[1], F.prod[2], F.prod[3], &mf);
+            if (Gf > G) {
+                G = Gf;
+                mask = mf;
+            }
+        }
+        d_G[ci] = G;
+        d_mask[ci] = (mask != 0 && G > Gc[cand[ci]]) ? mask : 0;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        long long S = 0;
+        for (int ci = 0; ci < nc; ++ci)
+            if (d_mask[ci]) {
+                split_list[S] = cand[ci];
+                split_mask[S] = (uint8_t)d_mask[ci];
+                split_G[S] = d_G[ci];
+                ++S;
+            }
+        *count = S;
+    }
 }
 
 // ------------------------------------------------------------------ scan functors
@@ -1121,6 +1227,16 @@ int update_lists(cem_ctx* c, int S) {
 }  // namespace
 
 int cem_launch_front_G(cem_ctx* c) {
+    if (c->n_cand > 0 && c->n_cand <= FRONT_SMALL) {
+        cem_pdl(c->stream, k_front_small, 1, FS_T, (const int*)c->cand_list, (int)c->n_cand, (const int*)c->conn,
+                (const int*)c->t2e, c->Tc, (const int*)c->face_nbr, (const uint8_t*)c->side, c->T0,
+                (const double*)c->X, (const double*)c->u, c->Nc, (const double*)c->sig, (const float*)c->sig32,
+                (const double*)c->Gc, c->g_variant, c->split_list, c->split_mask, c->split_Gv,
+                c->dcount + CNT_SPLIT, c->dcount + CNT_SCRATCH0);
+        cem_launched(c, 1);
+        CEM_CK(c, cudaGetLastError());
+        return CEM_OK;
+    }
     const int64_t cap = c->front_cap, cap4 = 4 * cap;
     for (int64_t c0 = 0; c0 < c->n_cand; c0 += cap) {
         const int nc = (int)std::min<int64_t>(cap, c->n_cand - c0);
