@@ -515,30 +515,26 @@ struct EdgeStore {
 __global__ void k_split_prep(int S, const int* __restrict__ split_list, const uint8_t* __restrict__ split_mask,
                              const int* __restrict__ t2e, int64_t Tc, const int* __restrict__ node_of_key,
                              uint8_t* __restrict__ key_flag, int* __restrict__ cnt, int deact,
-                             int* __restrict__ new_keys, long long* __restrict__ nk) {
+                             int* __restrict__ new_keys, long long* __restrict__ nk,
+                             long long* __restrict__ affected) {
     CEM_PDL_ENTRY();
-    const int i = blockIdx.x * BS + threadIdx.x;
+    // one thread per (split, local edge, side): the keys' dependent loads and atomics
+    // run side by side instead of one after another per split
+    const int tid = blockIdx.x * BS + threadIdx.x;
+    if (tid == 0) affected[0] = affected[1] = 0;   // the affected-item counters of this step's list update
+    const int i = tid / 12, r = tid - 12 * i, l = r >> 1, s = r & 1;
     if (i >= S) return;
-    if (deact) {
-        cnt[i] = 0;
-        return;
-    }
-    const int p = split_list[i], m = split_mask[i];
-    for (int l = 0; l < 6; ++l) {
-        const int x = CEM_LE0(l), y = CEM_LE1(l);
-        if (((m >> x) ^ (m >> y)) & 1) {
-            const int e = t2e[l * Tc + p];
-            for (int s = 0; s < 2; ++s) {
-                const int key = 2 * e + s;
-                if (node_of_key[key] >= 0) continue;
-                // byte test-and-set through its aligned 32-bit word
-                unsigned* w = reinterpret_cast<unsigned*>(key_flag + (key & ~3));
-                const unsigned bit = 1u << (8 * (key & 3));
-                if (!(atomicOr(w, bit) & bit)) new_keys[atomicAdd((unsigned long long*)nk, 1ull)] = key;
-            }
-        }
-    }
-    cnt[i] = (__popc((unsigned)m) == 2) ? 6 : 4;
+    const int m = split_mask[i];
+    if (r == 0) cnt[i] = deact ? 0 : ((__popc((unsigned)m) == 2) ? 6 : 4);
+    if (deact) return;
+    const int x = CEM_LE0(l), y = CEM_LE1(l);
+    if (!(((m >> x) ^ (m >> y)) & 1)) return;
+    const int key = 2 * t2e[l * Tc + split_list[i]] + s;
+    if (node_of_key[key] >= 0) return;
+    // byte test-and-set through its aligned 32-bit word
+    unsigned* w = reinterpret_cast<unsigned*>(key_flag + (key & ~3));
+    const unsigned bit = 1u << (8 * (key & 3));
+    if (!(atomicOr(w, bit) & bit)) new_keys[atomicAdd((unsigned long long*)nk, 1ull)] = key;
 }
 
 // New nodes of a step with at most NK_SORT keys: sort the appended keys in
@@ -546,15 +542,11 @@ __global__ void k_split_prep(int S, const int* __restrict__ split_list, const ui
 // order, exactly as the ordered scan over all keys would.
 constexpr int NK_SORT = 4096;
 
-template <class Store>
-__global__ void __launch_bounds__(1024) k_node_sorted(const long long* __restrict__ nk, const int* __restrict__ new_keys,
-                                                      Store st, long long* __restrict__ count) {
-    CEM_PDL_ENTRY();
-    __shared__ int sk[NK_SORT];
-    const int n = (int)min(*nk, (long long)NK_SORT);
+// Bitonic sort, ascending, of src[0..n) (n <= NK_SORT) into the block's shared sk.
+__device__ void block_sort(int* sk, const int* __restrict__ src, int n) {
     int size = 2;
     while (size < n) size <<= 1;
-    for (int i = threadIdx.x; i < size; i += blockDim.x) sk[i] = i < n ? new_keys[i] : INT_MAX;
+    for (int i = threadIdx.x; i < size; i += blockDim.x) sk[i] = i < n ? src[i] : INT_MAX;
     __syncthreads();
     for (int k = 2; k <= size; k <<= 1)
         for (int j = k >> 1; j > 0; j >>= 1) {
@@ -571,6 +563,15 @@ __global__ void __launch_bounds__(1024) k_node_sorted(const long long* __restric
             }
             __syncthreads();
         }
+}
+
+template <class Store>
+__global__ void __launch_bounds__(1024) k_node_sorted(const long long* __restrict__ nk, const int* __restrict__ new_keys,
+                                                      Store st, long long* __restrict__ count) {
+    CEM_PDL_ENTRY();
+    __shared__ int sk[NK_SORT];
+    const int n = (int)min(*nk, (long long)NK_SORT);
+    block_sort(sk, new_keys, n);
     for (int i = threadIdx.x; i < n; i += blockDim.x) st((int64_t)sk[i], i, 1);
     if (threadIdx.x == 0) *count = n;
 }
@@ -855,9 +856,22 @@ __device__ __forceinline__ int list_item(const ListKind& L, const int* t2e, cons
     return L.kind == 0 ? t2e[l * Tc + elem] : conn[l * Tc + elem];
 }
 
+// Flag item x as affected.  With `append` (a step with few splits) the first
+// to flag it also appends it to L.aff, which is sorted afterwards (k_sort_affected)
+// instead of compacting the flags of every edge and node.
+__device__ __forceinline__ void mark_item(const ListKind& L, int x, int append) {
+    if (!append) {
+        L.flag[x] = 1;
+        return;
+    }
+    unsigned* w = reinterpret_cast<unsigned*>(L.flag + (x & ~3));   // byte test-and-set
+    const unsigned bit = 1u << (8 * (x & 3));
+    if (!(atomicOr(w, bit) & bit)) L.aff[atomicAdd((unsigned long long*)L.count, 1ull)] = x;
+}
+
 __global__ void k_mark_affected(ListKind L0, ListKind L1, int S, const int* __restrict__ split_list,
                                 const long long* __restrict__ nsub, int64_t T, const int* __restrict__ t2e,
-                                const int* __restrict__ conn, int64_t Tc) {
+                                const int* __restrict__ conn, int64_t Tc, int append) {
     CEM_PDL_ENTRY();
     int i = blockIdx.x * BS + threadIdx.x;
     const bool k1 = i >= L0.bound;
@@ -866,14 +880,25 @@ __global__ void k_mark_affected(ListKind L0, ListKind L1, int S, const int* __re
     if (i >= L.bound) return;
     const int per = L.per;
     if (i < S * per) {
-        L.flag[list_item(L, t2e, conn, Tc, split_list[i / per], i % per)] = 1;
+        mark_item(L, list_item(L, t2e, conn, Tc, split_list[i / per], i % per), append);
         return;
     }
     const int c = i - S * per;
     if (c >= *nsub * per) return;
     const int x = list_item(L, t2e, conn, Tc, T + c / per, c % per);
-    L.flag[x] = 1;
+    mark_item(L, x, append);
     atomicAdd(&L.add_cnt[x], 1);
+}
+
+// The appended affected items of each kind in ascending order (block b sorts kind b),
+// as the ordered compaction of the flags would list them.
+__global__ void __launch_bounds__(1024) k_sort_affected(ListKind L0, ListKind L1) {
+    CEM_PDL_ENTRY();
+    __shared__ int sk[NK_SORT];
+    const ListKind& L = blockIdx.x ? L1 : L0;
+    const int n = (int)min(*L.count, (long long)NK_SORT);
+    block_sort(sk, L.aff, n);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) L.aff[i] = sk[i];
 }
 
 // The list kernels give each affected list a group of LG = 8 lanes: the lanes
@@ -1181,14 +1206,23 @@ int64_t group_threads(int bound) { return ((LG * (int64_t)bound + 31) / 32) * 32
 int update_lists(cem_ctx* c, int S) {
     const long long* nsub = c->dcount + CNT_NEWSUB;
     ListKind L0 = list_kind(c, 0, S), L1 = list_kind(c, 1, S);
+    // few splits: append the affected items as they are flagged and sort the short
+    // lists; otherwise compact the flags of every edge and node (the counters were
+    // zeroed by this step's k_split_prep)
+    const int append = L0.bound <= NK_SORT && L1.bound <= NK_SORT;
     cem_pdl(c->stream, k_mark_affected, cem_grid(L0.bound + L1.bound, BS), BS, L0, L1, S, c->split_list, nsub, c->T,
-            c->t2e, c->conn, c->Tc);
+            c->t2e, c->conn, c->Tc, append);
     cem_launched(c, 1);
     CEM_CK(c, cudaGetLastError());
     int rc;
-    if ((rc = cem_compact_u8(c, L0.flag, c->E + 22 * (int64_t)S, L0.aff, CNT_AFFECTED)) ||
-        (rc = cem_compact_u8(c, L1.flag, c->N + 8 * (int64_t)S, L1.aff, CNT_AFFECTED_N)))
+    if (append) {
+        cem_pdl(c->stream, k_sort_affected, 2, 1024, L0, L1);
+        cem_launched(c, 1);
+        CEM_CK(c, cudaGetLastError());
+    } else if ((rc = cem_compact_u8(c, L0.flag, c->E + 22 * (int64_t)S, L0.aff, CNT_AFFECTED)) ||
+               (rc = cem_compact_u8(c, L1.flag, c->N + 8 * (int64_t)S, L1.aff, CNT_AFFECTED_N))) {
         return rc;
+    }
     const int64_t gthreads = group_threads(L0.bound) + group_threads(L1.bound);
     cem_pdl(c->stream, k_list_count, cem_grid(gthreads, BS), BS, L0, L1, (const uint8_t*)c->active);
     cem_launched(c, 1);
@@ -1269,9 +1303,9 @@ int cem_apply_splits(cem_ctx* c, int64_t S64, int64_t step, int book_energy) {
     // 1. new nodes: one per (cut original edge, side) not yet present; sub-element counts
     // the new-key counter starts at 0: reset by the front evaluation of this step, or here for the notch
     if (step < 0) CEM_CK(c, cudaMemsetAsync(c->dcount + CNT_SCRATCH0, 0, sizeof(long long), c->stream));
-    cem_pdl(c->stream, k_split_prep, cem_grid(S, BS), BS, S, c->split_list, c->split_mask, c->t2e, c->Tc,
+    cem_pdl(c->stream, k_split_prep, cem_grid(12 * (int64_t)S, BS), BS, S, c->split_list, c->split_mask, c->t2e, c->Tc,
             c->node_of_key, c->key_flag, c->aff_new, (int)(c->split_mode == CEM_SPLIT_DEACTIVATE), c->new_keys,
-            c->dcount + CNT_SCRATCH0);
+            c->dcount + CNT_SCRATCH0, c->dcount + CNT_AFFECTED);
     cem_launched(c, 1);
     CEM_CK(c, cudaGetLastError());
     const NodeStore ns{c->N, c->Nc, c->node_of_key, c->key_flag, c->oe_n0, c->oe_n1, c->X, c->u, c->v, c->a,
