@@ -772,14 +772,14 @@ __device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
     return z ^ (z >> 31);
 }
 
-__global__ void k_sub_edges(const long long* __restrict__ nsub, int64_t T, int64_t N0, const int* __restrict__ conn,
-                            int* __restrict__ t2e, const int* __restrict__ anc, int64_t Tc,
-                            unsigned long long* __restrict__ hkeys, const int* __restrict__ hvals,
-                            int* __restrict__ hfirst, int64_t hmask, int* __restrict__ slot_of,
-                            long long* __restrict__ err, const int* __restrict__ ext) {
-    CEM_PDL_ENTRY();
-    const int cidx = blockIdx.x * BS + threadIdx.x;
-    if (cidx >= 6 * *nsub) return;
+// Edge l of sub-element q (code 6 q + l): a parent edge when both ends are input
+// nodes, else the hash slot of its node pair (inserted if new) and, for a pair with
+// no edge yet, a bid for the lowest code referencing it (hfirst).
+__device__ __forceinline__ void sub_edge(int cidx, int64_t T, int64_t N0, const int* __restrict__ conn,
+                                         int* __restrict__ t2e, const int* __restrict__ anc, int64_t Tc,
+                                         unsigned long long* __restrict__ hkeys, const int* hvals,
+                                         int* __restrict__ hfirst, int64_t hmask, int* __restrict__ slot_of,
+                                         long long* __restrict__ err, const int* __restrict__ ext) {
     const int q = cidx / 6, l = cidx % 6;
     const int64_t s = T + q;
     const int x = conn[CEM_LE0(l) * Tc + s], y = conn[CEM_LE1(l) * Tc + s];
@@ -814,6 +814,81 @@ __global__ void k_sub_edges(const long long* __restrict__ nsub, int64_t T, int64
     }
     slot_of[cidx] = (int)slot;
     if (hvals[slot] < 0) atomicMin(&hfirst[slot], cidx);
+}
+
+__global__ void k_sub_edges(const long long* __restrict__ nsub, int64_t T, int64_t N0, const int* __restrict__ conn,
+                            int* __restrict__ t2e, const int* __restrict__ anc, int64_t Tc,
+                            unsigned long long* __restrict__ hkeys, const int* __restrict__ hvals,
+                            int* __restrict__ hfirst, int64_t hmask, int* __restrict__ slot_of,
+                            long long* __restrict__ err, const int* __restrict__ ext) {
+    CEM_PDL_ENTRY();
+    const int cidx = blockIdx.x * BS + threadIdx.x;
+    if (cidx >= 6 * *nsub) return;
+    sub_edge(cidx, T, N0, conn, t2e, anc, Tc, hkeys, hvals, hfirst, hmask, slot_of, err, ext);
+}
+// The new edges of a step with at most EDGE_SMALL codes in one block: the codes'
+// slots and bids (sub_edge), then the owners numbered in code order, as the
+// ordered scan over the owner flags numbers them, then every code's edge id.
+constexpr int EDGE_SMALL = 4096;
+constexpr int ES_T = 1024;
+
+__global__ void __launch_bounds__(ES_T) k_sub_edges_small(const long long* __restrict__ nsub, int64_t T, int64_t N0,
+                                                          const int* __restrict__ conn, int* __restrict__ t2e,
+                                                          const int* __restrict__ anc, int64_t Tc,
+                                                          unsigned long long* __restrict__ hkeys,
+                                                          int* __restrict__ hfirst, int64_t hmask,
+                                                          int* __restrict__ slot_of, long long* __restrict__ err,
+                                                          const int* __restrict__ ext, EdgeStore st,
+                                                          long long* __restrict__ count) {
+    CEM_PDL_ENTRY();
+    constexpr int PER = EDGE_SMALL / ES_T;   // codes per thread in the numbering
+    __shared__ int wsum[ES_T / 32];
+    const int n = (int)min(6 * *nsub, (long long)EDGE_SMALL);
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    for (int c = tid; c < n; c += ES_T)
+        sub_edge(c, T, N0, conn, t2e, anc, Tc, hkeys, st.hvals, hfirst, hmask, slot_of, err, ext);
+    __syncthreads();
+    int own[PER], cnt = 0;
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+        const int c = PER * tid + j;
+        own[j] = 0;
+        if (c < n) {
+            const int sl = slot_of[c];
+            own[j] = (sl >= 0 && st.hvals[sl] < 0 && hfirst[sl] == c) ? 1 : 0;
+        }
+        cnt += own[j];
+    }
+    // exclusive block scan of the owner counts, in code order
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) wsum[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+        const int v = lane < ES_T / 32 ? wsum[lane] : 0;
+        int vi = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, vi, o);
+            if (lane >= o) vi += y;
+        }
+        if (lane < ES_T / 32) wsum[lane] = vi - v;   // exclusive prefix of warp w
+        if (lane == ES_T / 32 - 1) *count = vi;
+    }
+    __syncthreads();
+    int pos = wsum[w] + incl - cnt;
+#pragma unroll
+    for (int j = 0; j < PER; ++j)
+        if (own[j]) st(PER * tid + j, pos++, 1);
+    __syncthreads();
+    for (int c = tid; c < n; c += ES_T) {
+        const int sl = slot_of[c];
+        if (sl >= 0) t2e[(c % 6) * Tc + T + c / 6] = st.hvals[sl];
+    }
 }
 
 __global__ void k_edge_owner(const long long* __restrict__ nsub, const int* __restrict__ slot_of,
@@ -1329,20 +1404,27 @@ int cem_apply_splits(cem_ctx* c, int64_t S64, int64_t step, int book_energy) {
     // 3. edges of the sub-elements: parent edges or (new) hashed node pairs
     const long long* nsub = c->dcount + CNT_NEWSUB;
     const int codes = 36 * S;
-    cem_pdl(c->stream, k_sub_edges, cem_grid(codes, BS), BS, nsub, c->T, c->N0, c->conn, c->t2e, c->anc, c->Tc,
-            c->hkeys, c->hvals, c->hfirst, c->hash_cap - 1, c->slot_of, c->dcount + CNT_ERR,
-            (const int*)c->ext_of_int);
-    cem_pdl(c->stream, k_edge_owner, cem_grid(codes, BS), BS, nsub, c->slot_of, c->hvals, c->hfirst, c->code_flag);
-    cem_launched(c, 3);
-    CEM_CK(c, cudaGetLastError());
-    if ((rc = run_scan(c, U8Load{c->code_flag},
-                       EdgeStore{c->E, c->slot_of, c->hvals, c->hfirst, c->code_flag, c->fan_off, c->fan_cnt, c->cl,
-                                 c->cm, c->sumV, c->cl32, c->cm32},
-                       codes, CNT_NEWEDGE)))
-        return rc;
-    cem_pdl(c->stream, k_edge_resolve, cem_grid(codes, BS), BS, nsub, c->T, c->slot_of, c->hvals, c->t2e, c->Tc);
-    cem_launched(c, 1);
-    CEM_CK(c, cudaGetLastError());
+    const EdgeStore es{c->E,       c->slot_of, c->hvals, c->hfirst, c->code_flag, c->fan_off,
+                       c->fan_cnt, c->cl,      c->cm,    c->sumV,   c->cl32,      c->cm32};
+    if (codes <= EDGE_SMALL) {   // one block: slots, owners numbered in code order, edge ids
+        cem_pdl(c->stream, k_sub_edges_small, 1, ES_T, nsub, c->T, c->N0, (const int*)c->conn, c->t2e,
+                (const int*)c->anc, c->Tc, c->hkeys, c->hfirst, c->hash_cap - 1, c->slot_of, c->dcount + CNT_ERR,
+                (const int*)c->ext_of_int, es, c->dcount + CNT_NEWEDGE);
+        cem_launched(c, 2);   // with k_create_subs
+        CEM_CK(c, cudaGetLastError());
+    } else {
+        cem_pdl(c->stream, k_sub_edges, cem_grid(codes, BS), BS, nsub, c->T, c->N0, c->conn, c->t2e, c->anc, c->Tc,
+                c->hkeys, c->hvals, c->hfirst, c->hash_cap - 1, c->slot_of, c->dcount + CNT_ERR,
+                (const int*)c->ext_of_int);
+        cem_pdl(c->stream, k_edge_owner, cem_grid(codes, BS), BS, nsub, c->slot_of, c->hvals, c->hfirst,
+                c->code_flag);
+        cem_launched(c, 3);   // with k_create_subs
+        CEM_CK(c, cudaGetLastError());
+        if ((rc = run_scan(c, U8Load{c->code_flag}, es, codes, CNT_NEWEDGE))) return rc;
+        cem_pdl(c->stream, k_edge_resolve, cem_grid(codes, BS), BS, nsub, c->T, c->slot_of, c->hvals, c->t2e, c->Tc);
+        cem_launched(c, 1);
+        CEM_CK(c, cudaGetLastError());
+    }
     // 4. fans of affected edges, incidence (and mass) of affected nodes
     if ((rc = update_lists(c, S))) return rc;
     // 5. crack-front candidates
