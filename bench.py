@@ -56,7 +56,7 @@ KERNEL_UNITS = {"predict": "nodes", "strain": "tets", "edge_stress": "edges", "f
 # 960,000-element block (profiles/mixed_kernels_notched_block_200x80x10.md); scaled by the
 # units of an average launch for the roofline's "traffic".  None: no capture of the current
 # kernel (FP64 path).
-DRAM_BYTES_PER_UNIT = {"mixed": {"strain": 61.1, "edge_stress": 68.0, "force": 124.6, "node_update": 554.0},
+DRAM_BYTES_PER_UNIT = {"mixed": {"strain": 62.6, "edge_stress": 68.0, "force": 126.3, "node_update": 564.5},
                        "fp64": {}}
 
 
