@@ -565,15 +565,44 @@ __device__ void block_sort(int* sk, const int* __restrict__ src, int n) {
         }
 }
 
+// Also numbers the step's sub-elements (at most 1,024 splits here): sub_off =
+// exclusive prefix sums of the per-split counts sub_cnt, *sub_total their sum,
+// as the ordered scan would give them.
 template <class Store>
 __global__ void __launch_bounds__(1024) k_node_sorted(const long long* __restrict__ nk, const int* __restrict__ new_keys,
-                                                      Store st, long long* __restrict__ count) {
+                                                      Store st, long long* __restrict__ count,
+                                                      const int* __restrict__ sub_cnt, int S, int* __restrict__ sub_off,
+                                                      long long* __restrict__ sub_total) {
     CEM_PDL_ENTRY();
     __shared__ int sk[NK_SORT];
+    __shared__ int wsum[32];
     const int n = (int)min(*nk, (long long)NK_SORT);
     block_sort(sk, new_keys, n);
     for (int i = threadIdx.x; i < n; i += blockDim.x) st((int64_t)sk[i], i, 1);
     if (threadIdx.x == 0) *count = n;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int v = (int)threadIdx.x < S ? sub_cnt[threadIdx.x] : 0;
+    int incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) wsum[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+        const int x = wsum[lane];
+        int xi = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, xi, o);
+            if (lane >= o) xi += y;
+        }
+        wsum[lane] = xi - x;
+        if (lane == 31) *sub_total = xi;
+    }
+    __syncthreads();
+    if ((int)threadIdx.x < S) sub_off[threadIdx.x] = wsum[w] + incl - v;
 }
 
 
@@ -1386,16 +1415,16 @@ int cem_apply_splits(cem_ctx* c, int64_t S64, int64_t step, int book_energy) {
     const NodeStore ns{c->N, c->Nc, c->node_of_key, c->key_flag, c->oe_n0, c->oe_n1, c->X, c->u, c->v, c->a,
                        c->fext, c->mass, c->minv, c->dtn, c->inc_off, c->inc_cnt, c->node_inst,
                        c->precision == CEM_MIXED ? c->uhl : nullptr, c->dt};
-    if (8 * (int64_t)S <= NK_SORT) {   // at most 8 keys per split: sort the short list
+    // 2. sub-elements, numbered by (parent, local sub index)
+    if (8 * (int64_t)S <= NK_SORT) {   // at most 8 keys per split: sort the short list (S <= 512)
         cem_pdl(c->stream, k_node_sorted<NodeStore>, 1, 1024, c->dcount + CNT_SCRATCH0, c->new_keys, ns,
-                c->dcount + CNT_NEWNODE);
+                c->dcount + CNT_NEWNODE, (const int*)c->aff_new, S, c->sub_off, c->dcount + CNT_NEWSUB);
         cem_launched(c, 1);
         CEM_CK(c, cudaGetLastError());
-    } else if ((rc = run_scan(c, U8Load{c->key_flag}, ns, 2 * c->E0, CNT_NEWNODE))) {
+    } else if ((rc = run_scan(c, U8Load{c->key_flag}, ns, 2 * c->E0, CNT_NEWNODE)) ||
+               (rc = cem_scan_i32(c, c->aff_new, S, c->sub_off, CNT_NEWSUB))) {
         return rc;
     }
-    // 2. sub-elements, numbered by (parent, local sub index)
-    if ((rc = cem_scan_i32(c, c->aff_new, S, c->sub_off, CNT_NEWSUB))) return rc;
     cem_pdl(c->stream, k_create_subs, cem_grid(6 * (int64_t)S, BS), BS,
             S, c->T, c->split_list, c->split_mask, c->split_Gv, c->sub_off, step, book_energy, c->conn, c->t2e, c->anc,
             c->active, c->Vg, c->Vg32, c->vol, c->lam, c->mu, c->Tc, c->node_of_key, c->X, c->Nc, c->side,
