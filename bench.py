@@ -89,6 +89,66 @@ def kernel_costs(T, E, N, precision):
     return flops, byts
 
 
+def roofline_accounting(chunks, prof, precision, scale, t_ms, hbm, sm_clock):
+    """Per-kernel shares and the dominant step kernel's roofline from sampled kernel times.
+
+    chunks: [(counts, {kernel: (ms, launches)})] for consecutive windows of the timed
+    region; counts holds the window's mean n_active_tets, n_edges and n_nodes, and the
+    dict the sampled launches' time and number in that window.  prof: {kernel:
+    (total ms, launches)} over the whole region; scale = timed steps / sampled steps;
+    t_ms the region's time.  The algorithmic bytes (flops) of a sampled launch are the
+    per-unit figures of kernel_costs for its window's sizes times its units, so a mesh
+    that grows during the run is accounted window by window.  Achieved = the dominant
+    kernel's bytes (flops) per launch / its mean launch time; it is FP64-ALU-bound when
+    its flops take longer at the FP64 peak than its bytes at the HBM peak (FP64 path only).
+    """
+    acc = {k: dict(bytes=0.0, flops=0.0, units=0.0, traffic=0.0) for k in KERNEL_UNITS}
+    per_unit = DRAM_BYTES_PER_UNIT.get(precision, {})
+    for cnt, dp in chunks:
+        fl, by = kernel_costs(cnt["n_active_tets"], cnt["n_edges"], cnt["n_nodes"], precision)
+        for k, (_, nl) in dp.items():
+            units = {"tets": cnt["n_active_tets"], "edges": cnt["n_edges"], "nodes": cnt["n_nodes"]}[KERNEL_UNITS[k]]
+            acc[k]["bytes"] += nl * by[k] * units
+            acc[k]["flops"] += nl * fl[k] * units
+            acc[k]["units"] += nl * units
+            acc[k]["traffic"] += nl * per_unit.get(k, 0.0) * units
+    kernels = {}
+    for k, (ms_tot, nl) in prof.items():
+        kernels[k] = {"ms": ms_tot * scale, "launches_timed": nl, "share": ms_tot * scale / max(t_ms, 1e-9)}
+        if k in KERNEL_UNITS and nl:
+            sec = ms_tot * 1e-3
+            kernels[k].update(per_launch_us=sec / nl * 1e6, gbs=acc[k]["bytes"] / sec / 1e9)
+            if precision == "fp64":
+                kernels[k]["fp64_tflops"] = acc[k]["flops"] / sec / 1e12
+    fp64_peak = 152 * 4 * sm_clock * 1e6      # 152 SMs x 2 FP64 FMA/clk x 2 FLOP
+    hot = {k: prof[k] for k in KERNEL_UNITS}
+    dom = max(hot, key=lambda k: hot[k][0])
+    ms_tot, nl = hot[dom]
+    nl = max(nl, 1)
+    per_launch_s = ms_tot * 1e-3 / nl
+    units = acc[dom]["units"] / nl
+    flops, bytes_ = acc[dom]["flops"] / nl, acc[dom]["bytes"] / nl
+    alu_bound = precision == "fp64" and flops / fp64_peak > bytes_ / ((hbm or 6651.4) * 1e9)
+    if alu_bound:
+        achieved, peak, unit = flops / per_launch_s / 1e12, fp64_peak / 1e12, "TFLOP/s"
+        src = "derived: 152 SMs x 4 FP64 FLOP/clk x %.0f MHz (nominal 1.25 TFLOP/s at 2070 MHz)" % sm_clock
+    else:
+        achieved, peak, unit = bytes_ / per_launch_s / 1e9, hbm, "GB/s"
+        src = "MEASURED_PEAKS.json hbm_gbs (measured copy bandwidth)"
+    traffic = acc[dom]["traffic"] / nl if dom in per_unit else None
+    roofline = {"bound": "alu" if alu_bound else "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
+                "unit": unit, "frac": achieved / peak if peak else None, "traffic": traffic, "peak_source": src,
+                "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum per unit on the 960,000-"
+                                   "element block, scaled to the units of each sampled launch" if traffic
+                                   else None),
+                "per_launch_us": per_launch_s * 1e6, "algorithmic_bytes_per_launch": bytes_,
+                "algorithmic_flops_per_launch": flops,
+                "hbm_gbs_achieved": bytes_ / per_launch_s / 1e9, "hbm_peak_gbs": hbm,
+                "units_per_launch": units, "units_integrated_over": "%d chunks of <= %d steps" % (
+                    len(chunks), CHUNK_STEPS)}
+    return kernels, roofline
+
+
 # --------------------------------------------------------------------------- helpers
 def _args():
     p = argparse.ArgumentParser()
@@ -359,53 +419,13 @@ def run_cem(a):
         if prof["strain"][1] == 0:
             raise RuntimeError("no sampled step in the timed region")
         scale = steps / n_sampled
-        # algorithmic bytes, flops, units and DRAM traffic of the sampled launches, summed over chunks
-        acc = {k: dict(bytes=0.0, flops=0.0, units=0.0, traffic=0.0) for k in KERNEL_UNITS}
-        for cnt, dp in chunks:
-            fl, by = kernel_costs(cnt["n_active_tets"], cnt["n_edges"], cnt["n_nodes"], precision)
-            per_unit = DRAM_BYTES_PER_UNIT.get(precision, {})
-            for k, (_, nl) in dp.items():
-                units = {"tets": cnt["n_active_tets"], "edges": cnt["n_edges"], "nodes": cnt["n_nodes"]}[
-                    KERNEL_UNITS[k]]
-                acc[k]["bytes"] += nl * by[k] * units
-                acc[k]["flops"] += nl * fl[k] * units
-                acc[k]["units"] += nl * units
-                acc[k]["traffic"] += nl * per_unit.get(k, 0.0) * units
-        kernels = {}
-        for k, (ms_tot, nl) in prof.items():
-            kernels[k] = {"ms": ms_tot * scale, "launches_timed": nl, "share": ms_tot * scale / max(t_ms, 1e-9)}
-            if k in KERNEL_UNITS and nl:
-                sec = ms_tot * 1e-3
-                kernels[k].update(per_launch_us=sec / nl * 1e6, gbs=acc[k]["bytes"] / sec / 1e9)
-                if precision == "fp64":
-                    kernels[k]["fp64_tflops"] = acc[k]["flops"] / sec / 1e12
-        hot = {k: prof[k] for k in KERNEL_UNITS}
-        dom = max(hot, key=lambda k: hot[k][0])
-        ms_tot, nl = hot[dom]
-        nl = max(nl, 1)
-        per_launch_s = ms_tot * 1e-3 / nl
-        units = acc[dom]["units"] / nl
-        flops, bytes_ = acc[dom]["flops"] / nl, acc[dom]["bytes"] / nl
-        alu_bound = precision == "fp64" and flops / fp64_peak > bytes_ / ((hbm or 6651.4) * 1e9)
-        if alu_bound:
-            achieved, peak, unit = flops / per_launch_s / 1e12, fp64_peak / 1e12, "TFLOP/s"
-            src = "derived: 152 SMs x 4 FP64 FLOP/clk x %.0f MHz (nominal 1.25 TFLOP/s at 2070 MHz)" % sm_clock
-        else:
-            achieved, peak, unit = bytes_ / per_launch_s / 1e9, hbm, "GB/s"
-            src = "MEASURED_PEAKS.json hbm_gbs (measured copy bandwidth)"
-        traffic = acc[dom]["traffic"] / nl if dom in DRAM_BYTES_PER_UNIT.get(precision, {}) else None
-        roofline = {"bound": "alu" if alu_bound else "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
-                    "unit": unit, "frac": achieved / peak, "traffic": traffic, "peak_source": src,
-                    "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum per unit on the 960,000-"
-                                       "element block, scaled to the units of each sampled launch" if traffic
-                                       else None),
-                    "per_launch_us": per_launch_s * 1e6, "algorithmic_bytes_per_launch": bytes_,
-                    "hbm_gbs_achieved": bytes_ / per_launch_s / 1e9, "hbm_peak_gbs": hbm,
-                    "units_per_launch": units, "units_integrated_over": "%d chunks of <= %d steps" % (
-                        len(chunks), CHUNK_STEPS)}
+        kernels, roofline = roofline_accounting(chunks, prof, precision, scale, t_ms, hbm, sm_clock)
+        flops, per_launch_s = roofline["algorithmic_flops_per_launch"], roofline["per_launch_us"] * 1e-6
         if precision == "fp64":
-            roofline.update(algorithmic_flops_per_launch=flops, fp64_tflops_achieved=flops / per_launch_s / 1e12,
-                            fp64_peak_tflops=fp64_peak / 1e12, fp64_fma_measured_tflops=fp64_peak_meas / 1e12)
+            roofline.update(fp64_tflops_achieved=flops / per_launch_s / 1e12, fp64_peak_tflops=fp64_peak / 1e12,
+                            fp64_fma_measured_tflops=fp64_peak_meas / 1e12)
+        else:
+            del roofline["algorithmic_flops_per_launch"]
         return dict(t_ms=t_ms, value=w.n_tets * steps * world / (t_ms * 1e-3), roofline=roofline, kernels=kernels,
                     clocks=clk, launches=launches, info0=info0, info=info, energy=energy, steps=steps,
                     tuning=tuning)
