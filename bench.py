@@ -302,6 +302,22 @@ def run_reference(a):
     print(json.dumps(line), flush=True)
 
 
+def max_over_ranks(x, world, device):
+    """x's maximum over the ranks of the default process group (x itself for one rank)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(n_tets, steps, world, t_ms):
+    """Whole-job tet-steps/s of `world` independent replicas, timed by the slowest rank."""
+    return n_tets * steps * world / (t_ms * 1e-3)
+
+
 def _reorder(sim, a):
     if a.reorder_growth is not None:
         sim.set_reorder(a.reorder_growth)
@@ -404,10 +420,7 @@ def run_cem(a):
         prof, launches = sim.profile_read()
         sim.profile(0)
         barrier()
-        tmax = torch.tensor([t_ms], device="cuda", dtype=torch.float64)
-        if world > 1:
-            dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        t_ms = float(tmax.item())
+        t_ms = max_over_ranks(t_ms, world, "cuda")
         info = sim.info()
         energy = sim.energy()
         tuning = {k: {"block": v[0], "batch": v[1]} for k, v in sim.tuning().items()}
@@ -426,7 +439,8 @@ def run_cem(a):
                             fp64_fma_measured_tflops=fp64_peak_meas / 1e12)
         else:
             del roofline["algorithmic_flops_per_launch"]
-        return dict(t_ms=t_ms, value=w.n_tets * steps * world / (t_ms * 1e-3), roofline=roofline, kernels=kernels,
+        return dict(t_ms=t_ms, value=replica_throughput(w.n_tets, steps, world, t_ms), roofline=roofline,
+                    kernels=kernels,
                     clocks=clk, launches=launches, info0=info0, info=info, energy=energy, steps=steps,
                     tuning=tuning)
 
@@ -533,10 +547,7 @@ def run_cem(a):
     torch.cuda.synchronize()
     t_e2e = time.perf_counter() - t0
     sim2.close()
-    te = torch.tensor([t_e2e], device="cuda", dtype=torch.float64)
-    if world > 1:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    t_e2e = float(te.item())
+    t_e2e = max_over_ranks(t_e2e, world, "cuda")
     h2d = (w.X.nbytes + w.tets.nbytes + w.tfaces.nbytes + w.tvec.nbytes + w.notch_tet.nbytes
            + w.notch_side.nbytes + 16)
     d2h = u.nbytes + 64
@@ -563,7 +574,7 @@ def run_cem(a):
         "roofline": main["roofline"],
         "kernels": main["kernels"],
         "clocks": main["clocks"],
-        "e2e": {"value": w.n_tets * a.steps * world / t_e2e, "unit": METRIC,
+        "e2e": {"value": replica_throughput(w.n_tets, a.steps, world, t_e2e * 1e3), "unit": METRIC,
                 "h2d_bytes_per_step": h2d / a.steps, "d2h_bytes_per_step": d2h / a.steps,
                 "includes": "mesh upload and topology build, material, K steps, u and energy read-back"},
         "gpu_launches": main["launches"],
