@@ -180,6 +180,27 @@ def pattern_of_side(mask):
     raise ValueError("side mask %d does not cut the element" % mask)
 
 
+def prism_tets(A, B):
+    """The three tetrahedra of the triangular prism A0 A1 A2 / B0 B1 B2 (rails Ai-Bi)
+    that cut every quadrilateral face along the diagonal through its smallest id.
+
+    Turn the prism so that its smallest vertex is v1, with v1 v2 v3 one triangle
+    and v4 v5 v6 the other (rails v1-v4, v2-v5, v3-v6).  The two faces through v1
+    take the diagonals v1-v5 and v1-v6; the face v2 v3 v6 v5 takes v2-v6 when
+    min(v2, v6) < min(v3, v5), else v3-v5; each case leaves one division into
+    three tetrahedra.
+    """
+    V = list(A) + list(B)
+    i = min(range(6), key=lambda q: V[q])
+    j = i % 3
+    lo, hi = (A, B) if i < 3 else (B, A)
+    v1, v2, v3 = lo[j], lo[(j + 1) % 3], lo[(j + 2) % 3]
+    v4, v5, v6 = hi[j], hi[(j + 1) % 3], hi[(j + 2) % 3]
+    if min(v2, v6) < min(v3, v5):
+        return [(v1, v2, v3, v6), (v1, v2, v6, v5), (v1, v5, v6, v4)]
+    return [(v1, v2, v3, v5), (v1, v5, v3, v6), (v1, v5, v6, v4)]
+
+
 def sub_tet_nodes(conn, mask, M):
     """Sub-tetrahedra replacing a split element (canonical order).
 
@@ -190,14 +211,16 @@ def sub_tet_nodes(conn, mask, M):
     holding local node 0 first.  Pattern II (lone node c, others o0<o1<o2):
     the corner tetrahedron (c, M(c,o0), M(c,o1), M(c,o2)) then the prism
     A = (M(o0,c), M(o1,c), M(o2,c)) over B = (o0, o1, o2).
-    A prism (A0 A1 A2 / B0 B1 B2) becomes (A0,A1,A2,B2), (A0,A1,B1,B2),
-    (A0,B0,B1,B2).  Orientation is fixed by the caller.
+    A prism (A0 A1 A2 / B0 B1 B2, rails Ai-Bi) becomes three tetrahedra whose
+    quadrilateral faces are cut along the diagonal through each face's
+    smallest node id, so that split neighbours sharing a quadrilateral cut it
+    alike (prism_tets).  Orientation is fixed by the caller.
     """
     bits = _bits(mask)
     n = [int(c) for c in conn]
 
     def prism(A, B):
-        return [(A[0], A[1], A[2], B[2]), (A[0], A[1], B[1], B[2]), (A[0], B[0], B[1], B[2])]
+        return prism_tets(A, B)
 
     if pattern_of_side(mask) == PATTERN_I:
         P = [l for l in range(4) if bits[l] == 0]

@@ -28,6 +28,7 @@
 // canonical order (ascending key / parent / first reference) with ordered
 // scans, so the topology is identical on every run.
 #include "cem_scan.cuh"
+#include "cem_prism.cuh"
 
 #include <algorithm>
 #include <climits>
@@ -622,15 +623,13 @@ struct SubCtx {
     }
 };
 
-__device__ __forceinline__ void prism(int out[][4], int& k, const int A[3], const int B[3]) {
-    int t0[4] = {A[0], A[1], A[2], B[2]};
-    int t1[4] = {A[0], A[1], B[1], B[2]};
-    int t2[4] = {A[0], B[0], B[1], B[2]};
-    for (int q = 0; q < 4; ++q) {
-        out[k][q] = t0[q];
-        out[k + 1][q] = t1[q];
-        out[k + 2][q] = t2[q];
-    }
+// the prism A / B as three sub-elements out[k..k+2] (diagonals from creation ids)
+__device__ __forceinline__ void prism(int out[][4], int& k, const int A[3], const int B[3], const int* ext) {
+    const int Ae[3] = {ext[A[0]], ext[A[1]], ext[A[2]]}, Be[3] = {ext[B[0]], ext[B[1]], ext[B[2]]};
+    int t[3][4];
+    cem_prism_division(A, B, Ae, Be, t);
+    for (int r = 0; r < 3; ++r)
+        for (int q = 0; q < 4; ++q) out[k + r][q] = t[r][q];
     k += 3;
 }
 
@@ -674,7 +673,7 @@ __global__ void k_create_subs(int S, int64_t T, const int* __restrict__ split_li
             const int* H = side_ ? P : Q;
             int A[3] = {pn[G[0]], sc.M(G[0], H[0]), sc.M(G[0], H[1])};
             int B[3] = {pn[G[1]], sc.M(G[1], H[0]), sc.M(G[1], H[1])};
-            prism(subs, ns, A, B);
+            prism(subs, ns, A, B, ext);
         }
         double xp0[3], xp1[3], xq0[3], xq1[3];
         load3(X, Nc, pn[P[0]], xp0);
@@ -703,7 +702,7 @@ __global__ void k_create_subs(int S, int64_t T, const int* __restrict__ split_li
         ns = 1;
         int A[3] = {sc.M(o[0], lone), sc.M(o[1], lone), sc.M(o[2], lone)};
         int B[3] = {pn[o[0]], pn[o[1]], pn[o[2]]};
-        prism(subs, ns, A, B);
+        prism(subs, ns, A, B, ext);
         double x0[3], x1[3], x2[3];
         load3(X, Nc, pn[o[0]], x0);
         load3(X, Nc, pn[o[1]], x1);

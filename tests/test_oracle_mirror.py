@@ -12,12 +12,10 @@ labelled by local index) breaks this; so does anything that treats the two
 halves' nodes or elements differently.
 
 The splits only deactivate elements here (the variant of Sec. 1).  The
-subdividing rule divides each remaining prism into three tetrahedra along
-diagonals fixed by the element's local node order, and the mirror image of an
-element has its local nodes in another order: its sub-elements are not the
-mirror images of the original's, so that rule is not mirror-symmetric (the
-node masses of mirror pairs differ by up to 1.6% of the largest mass after the
-notch alone).
+subdividing rule cuts each remaining prism along diagonals fixed by node ids,
+and the ids of mirror images are not mirror-symmetric, so the sub-elements of a
+mirror pair are not mirror images (the node masses of mirror pairs differ by up
+to 4% of the largest mass after the notch alone).
 """
 import numpy as np
 
