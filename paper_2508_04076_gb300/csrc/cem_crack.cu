@@ -673,7 +673,7 @@ __global__ void k_create_subs(int S, int64_t T, const int* __restrict__ split_li
             const int* H = side_ ? P : Q;
             int A[3] = {pn[G[0]], sc.M(G[0], H[0]), sc.M(G[0], H[1])};
             int B[3] = {pn[G[1]], sc.M(G[1], H[0]), sc.M(G[1], H[1])};
-            prism(subs, ns, A, B, ext);
+            if (!deact) prism(subs, ns, A, B, ext);   // (no new nodes exist when splits only deactivate)
         }
         double xp0[3], xp1[3], xq0[3], xq1[3];
         load3(X, Nc, pn[P[0]], xp0);
@@ -702,7 +702,7 @@ __global__ void k_create_subs(int S, int64_t T, const int* __restrict__ split_li
         ns = 1;
         int A[3] = {sc.M(o[0], lone), sc.M(o[1], lone), sc.M(o[2], lone)};
         int B[3] = {pn[o[0]], pn[o[1]], pn[o[2]]};
-        prism(subs, ns, A, B, ext);
+        if (!deact) prism(subs, ns, A, B, ext);
         double x0[3], x1[3], x2[3];
         load3(X, Nc, pn[o[0]], x0);
         load3(X, Nc, pn[o[1]], x1);
