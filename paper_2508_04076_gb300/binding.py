@@ -28,8 +28,8 @@ FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_void_p)
 EXPORTED = ["cem_mesh_create", "cem_set_material", "cem_step", "cem_energy", "cem_crack_state",
             "cem_get_field", "cem_info", "cem_energy_instance", "cem_adjoint", "cem_profile", "cem_profile_read",
             "cem_autotune", "cem_tune_get", "cem_tune_set", "cem_save", "cem_load", "cem_set_wait_limit",
-            "cem_wait_probe", "cem_set_reorder", "cem_reorder_nodes", "cem_probe_fp64_fma", "cem_probe_split", "cem_destroy",
-            "cem_last_error"]
+            "cem_wait_probe", "cem_set_reorder", "cem_reorder_nodes", "cem_probe_fp64_fma", "cem_probe_split",
+            "cem_node_energies_noalloc", "cem_destroy", "cem_last_error"]
 TUNED = ["strain", "edge_stress", "force", "node_update"]
 KERNELS = ["predict", "strain", "edge_stress", "force", "node_update", "front_G", "split"]
 
@@ -107,6 +107,7 @@ def load_library(build: bool = True):
     lib.cem_load.argtypes = [P, C.c_char_p]
     lib.cem_tune_get.argtypes = [P, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_double),
                                  C.POINTER(C.c_double)]
+    lib.cem_node_energies_noalloc.argtypes = [P] * 5 + [C.c_int64, C.c_int64, P, P]
     lib.cem_destroy.argtypes = [P]
     lib.cem_last_error.argtypes = [P]
     lib.cem_last_error.restype = C.c_char_p

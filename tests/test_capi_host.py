@@ -28,6 +28,14 @@ def test_exports_every_declared_symbol(lib):
         assert hasattr(lib, n), n
 
 
+def test_binding_binds_every_declared_symbol(lib):
+    # the Python binding sets return and argument types for exactly the header's entry points
+    from paper_2508_04076_gb300.binding import EXPORTED
+    assert sorted(EXPORTED) == _declared()
+    for n in EXPORTED:
+        assert getattr(lib, n).argtypes is not None, n
+
+
 def _desc(X, tets, notch_tet=(), notch_side=(), precision=0):
     from paper_2508_04076_gb300.binding import MeshDesc, ALLOC_FN, FREE_FN
     X = np.ascontiguousarray(X, np.float64)
