@@ -387,11 +387,15 @@ int cem_reorder_nodes(cem_ctx* ctx);
  * file into a context created from the same mesh description with the same
  * material; stepping it then continues bit for bit as the saved context
  * would have.  Both synchronise the context's stream and return after the
- * file is written / the state is on the device.  Errors: CEM_ESTATE (no
- * material), CEM_EINVAL (cannot open or write the file; not a checkpoint; a
- * different mesh, element type, precision, capacity or time step; a
- * truncated file, after which the context's state is undefined), CEM_ECUDA.
- * The file is in host byte order. */
+ * file is written / the state is on the device.  The file ends with a
+ * 64-bit FNV-1a hash of its bytes; cem_load reads and checks the whole file
+ * before it changes the context.  Errors: CEM_ESTATE (no material),
+ * CEM_EINVAL (cannot open or write the file; not a checkpoint; a different
+ * mesh, element type, precision, capacity or time step; a truncated or
+ * corrupted file: in all of these the context is left as it was; a file
+ * that changes while it is being loaded, after which the context's state is
+ * undefined), CEM_ECUDA.  Array contents are not validated beyond the hash:
+ * load only files that cem_save wrote.  The file is in host byte order. */
 int cem_save(cem_ctx* ctx, const char* path);
 int cem_load(cem_ctx* ctx, const char* path);
 

@@ -10,11 +10,17 @@
 // not saved.  A context built from the same description and material and then
 // loaded continues bit for bit as the saved one would have.
 //
-// File layout (host byte order): the 8-byte tag "CEMCKPT2", a header of int64
+// File layout (host byte order): the 8-byte tag "CEMCKPT3", a header of int64
 // fields (HDR_* below), then every array as raw bytes in a fixed order, each
-// preceded by its byte count.
+// preceded by its byte count, and last a 64-bit FNV-1a hash of every byte
+// before it.  Loading reads and hashes the whole file before it changes the
+// context, so a truncated or corrupted file leaves the context as it was
+// (array contents are not otherwise validated: indices out of range would
+// be read by the kernels as they stand).
 #include "cem_common.cuh"
 
+#include <algorithm>
+#include <cstdint>
 #include <cstdio>
 #include <cstring>
 #include <vector>
@@ -26,7 +32,15 @@ enum {
     HDR_NINST, HDR_SPLITMODE, HDR_N, HDR_T, HDR_E, HDR_NCAND, HDR_NSPLITALL, HDR_NSPLITRUN, HDR_NACTIVE,
     HDR_FANTOP, HDR_INCTOP, HDR_STEP, HDR_DT_BITS, HDR_RENUMBERED, HDR_REORDER_N, HDR_NREORDER, HDR_COUNT
 };
-const char TAG[8] = {'C', 'E', 'M', 'C', 'K', 'P', 'T', '2'};
+const char TAG[8] = {'C', 'E', 'M', 'C', 'K', 'P', 'T', '3'};
+
+// 64-bit FNV-1a (Fowler, Noll, Vo): offset basis and prime as published.
+const uint64_t FNV_BASIS = 0xcbf29ce484222325ull, FNV_PRIME = 0x100000001b3ull;
+uint64_t fnv1a(uint64_t h, const void* p, size_t n) {
+    const unsigned char* b = (const unsigned char*)p;
+    for (size_t i = 0; i < n; ++i) h = (h ^ b[i]) * FNV_PRIME;
+    return h;
+}
 
 struct Field {   // one array slice: device pointer, bytes
     void* p;
@@ -126,6 +140,33 @@ void header(const cem_ctx* c, int64_t h[HDR_COUNT]) {
     h[HDR_NREORDER] = c->n_reorder;
 }
 
+// The context's counts that a checkpoint sets (kept to restore them when a load fails).
+struct Counts {
+    int64_t N, T, E, n_cand, n_split_all, n_split_run, n_active, fan_top, inc_top, step, reorder_n, n_reorder;
+    bool renumbered;
+};
+
+Counts counts_of(const cem_ctx* c) {
+    return {c->N, c->T, c->E, c->n_cand, c->n_split_all, c->n_split_run, c->n_active, c->fan_top, c->inc_top,
+            c->step, c->reorder_n, c->n_reorder, c->renumbered};
+}
+
+void set_counts(cem_ctx* c, const Counts& k) {
+    c->N = k.N;
+    c->T = k.T;
+    c->E = k.E;
+    c->n_cand = k.n_cand;
+    c->n_split_all = k.n_split_all;
+    c->n_split_run = k.n_split_run;
+    c->n_active = k.n_active;
+    c->fan_top = k.fan_top;
+    c->inc_top = k.inc_top;
+    c->step = k.step;
+    c->reorder_n = k.reorder_n;
+    c->n_reorder = k.n_reorder;
+    c->renumbered = k.renumbered;
+}
+
 }  // namespace
 
 extern "C" int cem_save(cem_ctx* c, const char* path) {
@@ -138,6 +179,7 @@ extern "C" int cem_save(cem_ctx* c, const char* path) {
     int64_t h[HDR_COUNT];
     header(c, h);
     bool ok = std::fwrite(TAG, 1, 8, fp) == 8 && std::fwrite(h, sizeof(int64_t), HDR_COUNT, fp) == HDR_COUNT;
+    uint64_t hash = fnv1a(fnv1a(FNV_BASIS, TAG, 8), h, sizeof h);
     std::vector<char> buf;
     for (const Field& f : fields(c)) {
         if (!ok) break;
@@ -148,7 +190,9 @@ extern "C" int cem_save(cem_ctx* c, const char* path) {
         }
         const int64_t nb = (int64_t)f.bytes;
         ok = std::fwrite(&nb, sizeof nb, 1, fp) == 1 && std::fwrite(buf.data(), 1, f.bytes, fp) == f.bytes;
+        hash = fnv1a(fnv1a(hash, &nb, sizeof nb), buf.data(), f.bytes);
     }
+    ok = ok && std::fwrite(&hash, sizeof hash, 1, fp) == 1;
     ok = (std::fclose(fp) == 0) && ok;
     return ok ? CEM_OK : cem_fail(c, CEM_EINVAL, "writing the checkpoint file failed");
 }
@@ -189,37 +233,54 @@ extern "C" int cem_load(cem_ctx* c, const char* path) {
         std::fclose(fp);
         return cem_fail(c, CEM_EINVAL, "checkpoint counts exceed the context's capacities");
     }
-    // adopt the saved counts, then read the arrays they size
-    c->N = h[HDR_N];
-    c->T = h[HDR_T];
-    c->E = h[HDR_E];
-    c->n_cand = h[HDR_NCAND];
-    c->n_split_all = h[HDR_NSPLITALL];
-    c->n_split_run = h[HDR_NSPLITRUN];
-    c->n_active = h[HDR_NACTIVE];
-    c->fan_top = h[HDR_FANTOP];
-    c->inc_top = h[HDR_INCTOP];
-    c->step = h[HDR_STEP];
-    c->renumbered = h[HDR_RENUMBERED] != 0;
-    c->reorder_n = h[HDR_REORDER_N];
-    c->n_reorder = h[HDR_NREORDER];
+    // adopt the saved counts (they size the arrays), then read and hash the whole
+    // file once before anything on the device changes
+    const Counts old = counts_of(c);
+    set_counts(c, {h[HDR_N], h[HDR_T], h[HDR_E], h[HDR_NCAND], h[HDR_NSPLITALL], h[HDR_NSPLITRUN], h[HDR_NACTIVE],
+                   h[HDR_FANTOP], h[HDR_INCTOP], h[HDR_STEP], h[HDR_REORDER_N], h[HDR_NREORDER],
+                   h[HDR_RENUMBERED] != 0});
+    const std::vector<Field> fl = fields(c);
+    const long data_at = std::ftell(fp);
+    uint64_t hash = fnv1a(fnv1a(FNV_BASIS, tag, 8), h, sizeof h);
+    bool ok = data_at >= 0;
+    std::vector<char> buf;
+    for (size_t q = 0; q < fl.size() && ok; ++q) {
+        int64_t nb = 0;
+        ok = std::fread(&nb, sizeof nb, 1, fp) == 1 && nb == (int64_t)fl[q].bytes;
+        if (!ok) break;
+        hash = fnv1a(hash, &nb, sizeof nb);
+        for (size_t done = 0; done < fl[q].bytes && ok;) {   // in pieces of at most 64 MiB
+            const size_t n = std::min(fl[q].bytes - done, (size_t)1 << 26);
+            buf.resize(n);
+            ok = std::fread(buf.data(), 1, n, fp) == n;
+            if (ok) hash = fnv1a(hash, buf.data(), n);
+            done += n;
+        }
+    }
+    uint64_t want = 0;
+    ok = ok && std::fread(&want, sizeof want, 1, fp) == 1 && want == hash;
+    if (!ok) {
+        set_counts(c, old);
+        std::fclose(fp);
+        return cem_fail(c, CEM_EINVAL, "checkpoint file truncated, inconsistent or corrupt; context unchanged");
+    }
     // node maps: identity, then the saved storage order of the first N nodes and its inverse
     if (int rc = cem_reorder_identity(c)) {
         std::fclose(fp);
         return rc;
     }
     CEM_CK(c, cudaStreamSynchronize(c->stream));
-    std::vector<char> buf;
-    for (const Field& f : fields(c)) {
+    if (std::fseek(fp, data_at, SEEK_SET) != 0) {
+        std::fclose(fp);
+        return cem_fail(c, CEM_EINVAL, "checkpoint file cannot be re-read; context state undefined");
+    }
+    for (const Field& f : fl) {
         int64_t nb = 0;
-        if (std::fread(&nb, sizeof nb, 1, fp) != 1 || nb != (int64_t)f.bytes) {
-            std::fclose(fp);
-            return cem_fail(c, CEM_EINVAL, "checkpoint file truncated or inconsistent; context state undefined");
-        }
         buf.resize(f.bytes);
-        if (std::fread(buf.data(), 1, f.bytes, fp) != f.bytes) {
+        if (std::fread(&nb, sizeof nb, 1, fp) != 1 || nb != (int64_t)f.bytes ||
+            std::fread(buf.data(), 1, f.bytes, fp) != f.bytes) {
             std::fclose(fp);
-            return cem_fail(c, CEM_EINVAL, "checkpoint file truncated; context state undefined");
+            return cem_fail(c, CEM_EINVAL, "checkpoint file changed while loading; context state undefined");
         }
         if (cudaMemcpy(f.p, buf.data(), f.bytes, cudaMemcpyHostToDevice) != cudaSuccess) {
             std::fclose(fp);

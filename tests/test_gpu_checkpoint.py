@@ -1,5 +1,6 @@
 """Checkpoint and resume (cem_save / cem_load): a context loaded from a
-checkpoint continues bit for bit as the saved one does."""
+checkpoint continues bit for bit as the saved one does; files of another mesh,
+truncated or corrupted files are rejected and leave the context as it was."""
 import numpy as np
 import pytest
 
@@ -74,3 +75,16 @@ def test_load_rejects_other_meshes_and_bad_files(CEM, tmp_path):
     b = CEM.from_workload(plate_small())
     with pytest.raises(CEMError):
         b.load(str(trunc))
+    # a flipped bit inside an array: rejected by the file hash, the context left as it was
+    raw = bytearray(open(path, "rb").read())
+    raw[len(raw) // 2] ^= 0x40
+    flip = tmp_path / "flip.bin"
+    flip.write_bytes(bytes(raw))
+    c = CEM.from_workload(plate_small())
+    c.step(5)
+    u5 = c.field("u")
+    with pytest.raises(CEMError):
+        c.load(str(flip))
+    assert np.array_equal(c.field("u"), u5) and c.energy()["step"] == 5
+    c.step(5)
+    assert np.array_equal(c.field("u"), a.field("u")) and c.energy() == a.energy()
