@@ -41,6 +41,9 @@ What it computes, in the paper's order and notation (arxiv 2508.04076):
   three tetrahedra as for the parallelepiped remainder in Sec. 3).
 * Appendix I: the quadrilateral crack surface is planar.
 
+Diagnostic: decision_margins(t) (and margin_log, when set to a list) gives how
+far each discrete decision of the split test lies from its switch point.
+
 Paper variants (constructor switches):
 * split_mode="deactivate": the literal wording of Sec. 1 and the conclusion,
   where an element whose rate exceeds Gc is only deactivated (no
@@ -332,6 +335,7 @@ class CEMOracle:
         self.side = np.zeros(T0, dtype=np.int64)
         self.node_of_key = {}
         self.crack_log = []       # (tet, step, pattern, side mask, G)
+        self.margin_log = None    # a list: (step, tet, decision_margins) of every candidate evaluated
 
         # external load, Eq. 12
         self.f_ext = np.zeros_like(self.X)
@@ -588,10 +592,67 @@ class CEMOracle:
                 best = (G, pat, normalize_side(mask), f)
         return best
 
+    def decision_margins(self, t):
+        """How far each discrete decision of the split test of candidate t lies from
+        its switch point, on the current state (Sec. 3, Eqs. 16-18).
+
+        Returns a dict of relative distances, each the smallest over the element's
+        front faces:
+        "G": |G - Gc| / Gc, the split test itself;
+        "pattern": |G_I - G_II| / max(G_I, G_II), the pattern choice (inf unless the
+        element splits: otherwise the pattern is never used);
+        "face": the relative gap between the element's G and the best G of a face
+        that would split it otherwise (another pattern or side mask), the face
+        choice (inf when no face differs, or unless the element splits);
+        "stretch": |l / L - 1| of the front edges, the Heaviside of Eq. 16, over
+        edges whose end displacements differ (equal displacements give exactly
+        l = L on any implementation);
+        "eigen": (sigma_1 - sigma_2) / max|sigma| of the nonzero edge stresses
+        that enter (how well sigma_1's eigenvector is defined; inf for
+        g_variant "normal").
+        A decision within rounding of its switch point can differ between two
+        correct implementations; these margins show whether a run has one.
+        """
+        X, u = self.X, self.u
+        loc = list(self.conn[t])
+        rows = []
+        stretch = eig = np.inf
+        for f in range(4):
+            fr = self.front_face(t, f)
+            if fr is None:
+                continue
+            a, c, b, d = fr
+            GI, GII = self.energy_release_rates(a, c, b, d)
+            for i, j in ((a, c), (c, b)):
+                if np.any(u[i] != u[j]):
+                    r = np.linalg.norm(X[j] + u[j] - X[i] - u[i]) / np.linalg.norm(X[j] - X[i])
+                    stretch = min(stretch, abs(r - 1.0))
+            if self.g_variant != "normal":
+                for i, j in ((a, d), (b, d), (c, d)):
+                    w = np.linalg.eigvalsh(voigt_to_tensor(self.sigma[self._edge_index(i, j)]))
+                    if np.abs(w).max() > 0.0:
+                        eig = min(eig, (w[-1] - w[-2]) / np.abs(w).max())
+            G = max(GI, GII)
+            outcome = (PATTERN_I, normalize_side(sum(1 << loc.index(x) for x in (c, d)))) if GI >= GII else \
+                (PATTERN_II, normalize_side(1 << loc.index(c)))
+            rows.append((G, abs(GI - GII) / G if G > 0.0 else np.inf, outcome))
+        if not rows:
+            return None
+        best = max(rows, key=lambda r: r[0])
+        Gc = float(self.Gc_t[t])
+        splits = best[0] > Gc
+        other = [best[0] - r[0] for r in rows if r[2] != best[2]]
+        return {"G": abs(best[0] - Gc) / Gc,
+                "pattern": min(r[1] for r in rows) if splits else np.inf,
+                "face": min(other) / best[0] if splits and other else np.inf,
+                "stretch": stretch, "eigen": eig}
+
     def _crack_step(self):
         splits = []
         for t in self.candidates():
             best = self.evaluate_candidate(t)
+            if self.margin_log is not None and best is not None:
+                self.margin_log.append((self.n_step, t, self.decision_margins(t)))
             if best is not None and best[0] > self.Gc_t[t]:
                 splits.append((t, best[2], best[0]))
         if splits:
