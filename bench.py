@@ -260,6 +260,20 @@ def _oracle_rate(steps):
     return w.n_tets * steps / dt, steps, dt
 
 
+def _host_cpu():
+    """The host's logical CPU count and model name (lscpu), for the baseline record."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.startswith("Model name:"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    return {"nproc": os.cpu_count(), "model": model}
+
+
 def _cpu_baseline(steps):
     """Run the oracle in a single-threaded subprocess; returns the cpu_baseline object."""
     cmd = [sys.executable, os.path.abspath(__file__), "--cpu-baseline-worker", "--cpu-steps", str(steps)]
@@ -270,7 +284,8 @@ def _cpu_baseline(steps):
     res = json.loads(r.stdout.strip().splitlines()[-1])
     return {"value": res["value"], "unit": METRIC, "cores": 1, "kind": "oracle",
             "sample": "%s, steps 2-%d of the run (%.1f s of CPU time; setup untimed), "
-                      "single-threaded numpy/scipy FP64 oracle" % (WORKLOAD, res["steps"] + 1, res["seconds"])}
+                      "single-threaded numpy/scipy FP64 oracle" % (WORKLOAD, res["steps"] + 1, res["seconds"]),
+            "host": _host_cpu()}
 
 
 # --------------------------------------------------------------------------- arms
@@ -297,7 +312,8 @@ def run_reference(a):
                        "split": True},
             "cpu_baseline": {"value": value, "unit": METRIC, "cores": 1, "kind": "oracle",
                              "sample": "%s, %d steps after %d warm-up steps (capped at %.0f s), single-threaded"
-                                       % (WORKLOAD, done, max(1, min(a.warmup, 3)), budget_s)},
+                                       % (WORKLOAD, done, max(1, min(a.warmup, 3)), budget_s),
+                             "host": _host_cpu()},
             "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
