@@ -117,6 +117,41 @@ def test_internal_force_is_energy_gradient():
         assert abs(fd - f[i, c]) <= 1e-6 * np.abs(f).max()
 
 
+def test_heterogeneous_modulus_enters_by_fan_volume_weights():
+    """Element moduli enter the edge stress as Dbar_k = sum_j (V_j / sum V) D(E_j) (the
+    paper is silent; Sec. 2.2 reading): then dU/dE_j = sum over the element's six edges of
+    (V_j / 6) 1/2 eps_k . Dhat eps_k, Dhat the elasticity at E = 1 (central differences of
+    the oracle's strain energy at a fixed displacement).  An unweighted fan mean, or a
+    weight by the smoothing volume alone, fails this."""
+    w = kuhn_block(3, 2, 2, 0.03, 0.02, 0.02, jitter=0.1, seed=4, E_cov=0.3)
+    rng = np.random.default_rng(5)
+    u0 = rng.normal(size=w.X.shape) * 1e-5
+
+    def U(E):
+        o = CEMOracle(w.X, w.tets, w.tfaces, w.tvec, E, w.Gc, w.nu, w.rho, split_enabled=False)
+        _, eps, sig = o._internal_force(u0)
+        return 0.5 * np.sum(o.Vs[:, None] * eps * sig), o, eps
+
+    _, o, eps = U(w.E)
+    nu = w.nu
+    lam1, mu1 = nu / ((1 + nu) * (1 - 2 * nu)), 1.0 / (2 * (1 + nu))
+    tets = np.asarray(w.tets, dtype=np.int64)
+    h = 1e-6
+    for j in (0, 7, 23, len(tets) - 1):
+        n = tets[j]
+        Vj = abs(np.linalg.det(w.X[n[1:]] - w.X[n[0]])) / 6.0
+        want = 0.0
+        for a, b in itertools.combinations(n, 2):
+            e = eps[o._edge_index(int(a), int(b))]
+            tr = e[0] + e[1] + e[2]
+            want += Vj / 6.0 * 0.5 * (lam1 * tr * tr + 2 * mu1 * (e[:3] @ e[:3]) + mu1 * (e[3:] @ e[3:]))
+        Ep, Em = w.E.copy(), w.E.copy()
+        Ep[j] *= 1 + h
+        Em[j] *= 1 - h
+        fd = (U(Ep)[0] - U(Em)[0]) / (2 * h * w.E[j])
+        assert abs(fd - want) <= 1e-7 * abs(want), (j, fd, want)
+
+
 def test_smoothing_volumes_partition_domain():
     """Every element is shared by its 6 edges: sum_k Vs_k = sum_e V_e (Sec. 2.2 partition)."""
     w = kuhn_block(4, 4, 2, 0.04, 0.04, 0.02, notch_length=0.02, jitter=0.12, seed=6)
