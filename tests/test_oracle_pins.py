@@ -117,6 +117,33 @@ def test_internal_force_is_energy_gradient():
         assert abs(fd - f[i, c]) <= 1e-6 * np.abs(f).max()
 
 
+def test_assembled_force_equals_the_element_factored_form():
+    """Eq. 9 assembled (f = Bbar^T (Vs sigma), the oracle) equals the element form the CUDA
+    path computes: f_a = sum over active j containing node a of V_j sigma~_j grad N_{j,a},
+    sigma~_j = (1/6) sum over the six edges of j of sigma_k (Vs_k = sum_fan V / 6 and
+    w_j = V_j / sum_fan V cancel).  Checked on a split, jittered, heterogeneous mesh."""
+    w = kuhn_block(8, 6, 2, 0.04, 0.03, 0.01, notch_length=0.02, jitter=0.12, E_cov=0.3, seed=6, traction=2e6)
+    o = CEMOracle.from_workload(w)
+    o.step(60)
+    assert o.energy()["n_split"] > 0
+    rng = np.random.default_rng(8)
+    u = rng.normal(size=o.X.shape) * 1e-5
+    f_ref, _, sig = o._internal_force(u)
+    f = np.zeros_like(f_ref)
+    for j in np.nonzero(o.active)[0]:
+        n = [int(x) for x in o.conn[j]]
+        Xe = o.X[n]
+        Jm = (Xe[1:] - Xe[0]).T                      # columns X_a - X_0, a = 1..3
+        G = np.linalg.inv(Jm)                        # rows: grad N_1..N_3
+        grads = np.vstack([-G.sum(axis=0), G])
+        V = abs(np.linalg.det(Jm)) / 6.0
+        s = sum(sig[o._edge_index(a, b)] for a, b in itertools.combinations(n, 2)) / 6.0
+        S = np.array([[s[0], s[3], s[5]], [s[3], s[1], s[4]], [s[5], s[4], s[2]]])
+        for a in range(4):
+            f[n[a]] += V * S @ grads[a]
+    assert np.abs(f - f_ref).max() <= 1e-12 * np.abs(f_ref).max()
+
+
 def test_heterogeneous_modulus_enters_by_fan_volume_weights():
     """Element moduli enter the edge stress as Dbar_k = sum_j (V_j / sum V) D(E_j) (the
     paper is silent; Sec. 2.2 reading): then dU/dE_j = sum over the element's six edges of
