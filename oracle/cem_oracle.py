@@ -60,15 +60,20 @@ face's edges; sigma_G is the principal-stress vector sigma_1 p_1 of the edge
 stress; projections are taken in absolute value; the normal uses reference
 coordinates; a split element is replaced by sub-tetrahedra whose cut edges
 carry one new node per side (shared with every other element cut through
-the same edge on the same side); ties break towards pattern I and the lowest
-local face; the test is G > Gc.
+the same edge on the same side), each remaining prism divided into three
+tetrahedra by cutting every quadrilateral face through its smallest node id
+(so split neighbours triangulate a shared face alike); ties break towards
+pattern I and the lowest local face; the test is G > Gc.
 
-Parity pins (tests/test_oracle_*.py): ES-FEM constant-strain patch test,
-momentum balance of f_int, the 1D bar wave speed sqrt(E/rho), the exactly
-conserved modified energy of the central-difference scheme, the printed
-Rayleigh speeds of Sec. 4.1 / 4.3, closed-form G under an affine field,
-Appendix I planarity, sub-element volume and mass closure, and a brute-force
-geometric check of the crack patterns.
+Parity pins (tests/test_oracle_*.py, tests/test_prism_rule.py): ES-FEM
+constant-strain patch test, momentum balance of f_int, f_int as the energy
+gradient and as the element-factored form, the fan-volume weighting of
+element moduli, the 1D bar wave speed sqrt(E/rho), the exactly conserved
+modified energy of the central-difference scheme, the printed Rayleigh
+speeds of Sec. 4.1 / 4.3, closed-form G under an affine field, Appendix I
+planarity, sub-element volume and mass closure, conforming prism division,
+mirror symmetry of the deactivating split, and a brute-force geometric
+check of the crack patterns.
 """
 from __future__ import annotations
 
