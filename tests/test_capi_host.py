@@ -75,6 +75,8 @@ UNIT = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1.0]])
     ("bad_tface_nodes", "tface_nodes"),
     ("hex_with_splitting", "fixed topology"),
     ("hex_zero_volume", "positive volume"),
+    ("empty_mesh", "required"),
+    ("no_nodes", "required"),
 ])
 def test_host_validation_rejects(lib, case, expect):
     X, tets, nt, ns, prec = UNIT, [[0, 1, 2, 3]], [], [], 0
@@ -91,6 +93,10 @@ def test_host_validation_rejects(lib, case, expect):
         nt, ns = [3], [1]
     elif case == "bad_precision":
         prec = 7
+    elif case == "empty_mesh":
+        tets = np.zeros((0, 4), np.int32)
+    elif case == "no_nodes":
+        X = np.zeros((0, 3))
     elif case == "dir_twice":
         dirichlet = ([1, 2, 1], [0, 0, 0], [0.0, 0.0, 1.0])
     elif case == "dir_component":
