@@ -181,7 +181,7 @@ def _args():
     p.add_argument("--resume", action="store_true",
                    help="load --state into a fresh context and time --steps steps from there, then exit")
     p.add_argument("--cpu-baseline-worker", action="store_true", help=argparse.SUPPRESS)
-    p.add_argument("--cpu-steps", type=int, default=12, help=argparse.SUPPRESS)
+    p.add_argument("--cpu-steps", type=int, default=80, help=argparse.SUPPRESS)
     return p.parse_args()
 
 
