@@ -337,6 +337,20 @@ int cem_probe_fp64_fma(int device, void* stream, double* flops_per_s);
  * a double.  Synchronous; allocates and frees its own device buffers. */
 int cem_probe_split(const double* x, const float* f, int64_t n, float* hi, float* lo, double* fd);
 
+/* Diagnostics: the split rule of Sec. 3 (the sub-elements that replace a
+ * split element, each remaining prism divided into three tetrahedra) run on
+ * the current device with the device code cem_step uses, for n host cases.
+ * Case q: nodes[4q..4q+3] the element's node indices, ids[4q..] their
+ * creation ids, mask[q] its side mask (1..14: bit l = side of local node l),
+ * mnode[16q + 4x + y] / mid[16q + 4x + y] the new node on local edge x-y that
+ * stays attached to x, and its creation id.  Writes subs[24q + 4r + c] = node
+ * c of sub-element r (r < count[q]; later rows -1) and count[q] (6 for
+ * pattern I, 4 for pattern II), before orientation.  CEM_EINVAL for a null
+ * pointer or a mask outside 1..14; synchronous; allocates and frees its own
+ * device buffers. */
+int cem_probe_split_rule(int64_t n, const int32_t* nodes, const int32_t* ids, const int32_t* mask,
+                         const int32_t* mnode, const int32_t* mid, int32_t* subs, int32_t* count);
+
 /* Nodal energy sums of caller-owned device arrays, with no allocation.  The
  * paper has no counterpart: this is a library facility for callers that
  * cannot call cudaMalloc, for example code whose device memory is entirely
@@ -355,7 +369,9 @@ int cem_probe_split(const double* x, const float* f, int64_t n, float* hi, float
  * with the device current; make that first call before any stream capture
  * begins.  All calls on a device share the array: calls that overlap on the
  * GPU race and give wrong sums.  Calls no cudaMalloc, cudaFree or allocating
- * library routine. */
+ * library routine.  An error already pending on the calling thread (from
+ * earlier work) is reported as CEM_ECUDA and left pending, with nothing
+ * launched. */
 int cem_node_energies_noalloc(const double* u, const double* v, const double* a, const double* mass,
                               const double* fext, int64_t n_nodes, int64_t ld, double* out, void* stream);
 

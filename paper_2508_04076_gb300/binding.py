@@ -29,7 +29,7 @@ EXPORTED = ["cem_mesh_create", "cem_set_material", "cem_step", "cem_energy", "ce
             "cem_get_field", "cem_info", "cem_energy_instance", "cem_adjoint", "cem_profile", "cem_profile_read",
             "cem_autotune", "cem_tune_get", "cem_tune_set", "cem_save", "cem_load", "cem_set_wait_limit",
             "cem_wait_probe", "cem_set_reorder", "cem_reorder_nodes", "cem_probe_fp64_fma", "cem_probe_split",
-            "cem_node_energies_noalloc", "cem_destroy", "cem_last_error"]
+            "cem_probe_split_rule", "cem_node_energies_noalloc", "cem_destroy", "cem_last_error"]
 TUNED = ["strain", "edge_stress", "force", "node_update"]
 KERNELS = ["predict", "strain", "edge_stress", "force", "node_update", "front_G", "split"]
 
@@ -97,6 +97,8 @@ def load_library(build: bool = True):
     lib.cem_probe_fp64_fma.argtypes = [C.c_int, C.c_void_p, C.POINTER(C.c_double)]
     lib.cem_probe_split.argtypes = [C.POINTER(C.c_double), C.POINTER(C.c_float), C.c_int64,
                                     C.POINTER(C.c_float), C.POINTER(C.c_float), C.POINTER(C.c_double)]
+    I32 = C.POINTER(C.c_int32)
+    lib.cem_probe_split_rule.argtypes = [C.c_int64, I32, I32, I32, I32, I32, I32, I32]
     lib.cem_autotune.argtypes = [P, C.c_char_p, C.c_int, C.c_int]
     lib.cem_tune_set.argtypes = [P, C.c_int, C.c_int, C.c_int]
     lib.cem_save.argtypes = [P, C.c_char_p]
@@ -142,6 +144,29 @@ def probe_split(x, f):
     if rc != CEM_OK:
         raise CEMError(rc, "split probe failed")
     return hi, lo, fd
+
+
+def probe_split_rule(nodes, ids, mask, mnode, mid):
+    """The split rule (sub-elements of a split element) run on the current GPU.
+
+    nodes, ids: (n, 4) node indices of each element and their creation ids;
+    mask: (n,) side masks; mnode, mid: (n, 4, 4), [q, x, y] = the new node on
+    local edge x-y attached to x and its creation id.  Returns (subs, count):
+    (n, 6, 4) sub-element nodes (rows past count[q] are -1) and (n,) counts."""
+    lib = load_library()
+    nodes = np.ascontiguousarray(nodes, dtype=np.int32).reshape(-1, 4)
+    n = nodes.shape[0]
+    ids = np.ascontiguousarray(ids, dtype=np.int32).reshape(n, 4)
+    mask = np.ascontiguousarray(mask, dtype=np.int32).reshape(n)
+    mnode = np.ascontiguousarray(mnode, dtype=np.int32).reshape(n, 4, 4)
+    mid = np.ascontiguousarray(mid, dtype=np.int32).reshape(n, 4, 4)
+    subs, count = np.empty((n, 6, 4), np.int32), np.empty(n, np.int32)
+    rc = lib.cem_probe_split_rule(n, _ptr(nodes, C.c_int32), _ptr(ids, C.c_int32), _ptr(mask, C.c_int32),
+                                  _ptr(mnode, C.c_int32), _ptr(mid, C.c_int32), _ptr(subs, C.c_int32),
+                                  _ptr(count, C.c_int32))
+    if rc != CEM_OK:
+        raise CEMError(rc, "split-rule probe failed")
+    return subs, count
 
 
 class CEMError(RuntimeError):

@@ -607,30 +607,71 @@ __global__ void __launch_bounds__(1024) k_node_sorted(const long long* __restric
 }
 
 
-struct SubCtx {
-    const int* pn;        // parent's 4 node ids (storage indices)
-    const int* pe;        // their creation ids
+// New node on the parent's edge between local nodes x and y, attached to x
+// (side 0: x is the end with the smaller creation id), and its creation id.
+struct SubNode {
     int p;
     const int* t2e;
     int64_t Tc;
     const int* node_of_key;
-    // new node on the parent's edge between local nodes x and y, attached to x
-    // (side 0: x is the end with the smaller creation id)
-    __device__ int M(int x, int y) const {
+    const int* ext;
+    int x0, x1, x2, x3;   // creation ids of the parent's nodes
+    __device__ void operator()(int x, int y, int* node, int* id) const {
         const int e = t2e[local_edge(x, y) * Tc + p];
-        const int s = (pe[x] < pe[y]) ? 0 : 1;
-        return node_of_key[2 * e + s];
+        const int s = (cem_pick4(x0, x1, x2, x3, x) < cem_pick4(x0, x1, x2, x3, y)) ? 0 : 1;
+        const int nd = node_of_key[2 * e + s];
+        *node = nd;
+        *id = ext[nd];
     }
 };
 
-// the prism A / B as three sub-elements out[k..k+2] (diagonals from creation ids)
-__device__ __forceinline__ void prism(int out[][4], int& k, const int A[3], const int B[3], const int* ext) {
-    const int Ae[3] = {ext[A[0]], ext[A[1]], ext[A[2]]}, Be[3] = {ext[B[0]], ext[B[1]], ext[B[2]]};
-    int t[3][4];
-    cem_prism_division(A, B, Ae, Be, t);
-    for (int r = 0; r < 3; ++r)
-        for (int q = 0; q < 4; ++q) out[k + r][q] = t[r][q];
-    k += 3;
+// Crack area of a split (Appendix I): pattern I, the parallelogram with sides
+// (X_p1 - X_p0)/2 and (X_q1 - X_q0)/2; pattern II, the triangle with sides
+// (X_o1 - X_o0)/2 and (X_o2 - X_o0)/2 of the three nodes other than the lone one.
+__device__ double split_area(const double* __restrict__ X, int64_t Nc, int n0, int n1, int n2, int n3, int m) {
+    const int ones = __popc((unsigned)m & 15u);
+    int a0, a1, b0, b1;
+    double f;
+    if (ones == 2) {   // a: the nodes of side 0 (ascending), b: side 1
+        int pa = -1, pb = -1, qa = -1, qb = -1;
+        for (int l = 0; l < 4; ++l) {
+            if ((m >> l) & 1) {
+                if (qa < 0) qa = l;
+                else qb = l;
+            } else {
+                if (pa < 0) pa = l;
+                else pb = l;
+            }
+        }
+        a0 = cem_pick4(n0, n1, n2, n3, pa);
+        a1 = cem_pick4(n0, n1, n2, n3, pb);
+        b0 = cem_pick4(n0, n1, n2, n3, qa);
+        b1 = cem_pick4(n0, n1, n2, n3, qb);
+        f = 0.25;
+    } else {           // the lone node c; the others o0 < o1 < o2
+        int c = -1, first0 = -1;
+        for (int l = 0; l < 4; ++l) {
+            if ((m >> l) & 1) c = l;
+            else if (first0 < 0) first0 = l;
+        }
+        if (ones != 1) c = first0;
+        const int o0 = c == 0 ? 1 : 0, o1 = c <= 1 ? 2 : 1, o2 = c <= 2 ? 3 : 2;
+        a0 = cem_pick4(n0, n1, n2, n3, o0);
+        a1 = cem_pick4(n0, n1, n2, n3, o1);
+        b0 = a0;
+        b1 = cem_pick4(n0, n1, n2, n3, o2);
+        f = 0.125;
+    }
+    double xa0[3], xa1[3], xb0[3], xb1[3];
+    load3(X, Nc, a0, xa0);
+    load3(X, Nc, a1, xa1);
+    load3(X, Nc, b0, xb0);
+    load3(X, Nc, b1, xb1);
+    const double e1[3] = {xa1[0] - xa0[0], xa1[1] - xa0[1], xa1[2] - xa0[2]};
+    const double e2[3] = {xb1[0] - xb0[0], xb1[1] - xb0[1], xb1[2] - xb0[2]};
+    double cr[3];
+    cross3(e1, e2, cr);
+    return f * sqrt(dot3(cr, cr));
 }
 
 __global__ void k_create_subs(int S, int64_t T, const int* __restrict__ split_list,
@@ -646,78 +687,31 @@ __global__ void k_create_subs(int S, int64_t T, const int* __restrict__ split_li
                               double* __restrict__ ud_part, double* __restrict__ ud_tet, int deact,
                               const int* __restrict__ ext) {
     CEM_PDL_ENTRY();
-    // six threads per split: thread qs builds sub-element qs (the sub-element list is
-    // rebuilt by each, it is cheap integer work); thread 0 also closes the parent
+    // six threads per split: thread qs builds sub-element qs (each thread evaluates the
+    // split rule, which is cheap integer work); thread 0 also closes the parent
     const int tid = blockIdx.x * BS + threadIdx.x;
     const int i = tid / 6, qs = tid % 6;
     if (i >= S) return;
     const int p = split_list[i];
     const int m = split_mask[i];
-    int pn[4], pe[4];
-    for (int l = 0; l < 4; ++l) {
-        pn[l] = conn[l * Tc + p];
-        pe[l] = ext[pn[l]];
-    }
-    SubCtx sc{pn, pe, p, t2e, Tc, node_of_key};
+    const int n0 = conn[p], n1 = conn[Tc + p], n2 = conn[2 * Tc + p], n3 = conn[3 * Tc + p];
+    const SubNode mf{p, t2e, Tc, node_of_key, ext, ext[n0], ext[n1], ext[n2], ext[n3]};
     int subs[6][4];
-    int ns = 0;
-    double area;
-    if (__popc((unsigned)m) == 2) {
-        int P[2], Q[2], kp = 0, kq = 0;
-        for (int l = 0; l < 4; ++l) {
-            if ((m >> l) & 1) Q[kq++] = l;
-            else P[kp++] = l;
-        }
-        for (int side_ = 0; side_ < 2; ++side_) {
-            const int* G = side_ ? Q : P;
-            const int* H = side_ ? P : Q;
-            int A[3] = {pn[G[0]], sc.M(G[0], H[0]), sc.M(G[0], H[1])};
-            int B[3] = {pn[G[1]], sc.M(G[1], H[0]), sc.M(G[1], H[1])};
-            if (!deact) prism(subs, ns, A, B, ext);   // (no new nodes exist when splits only deactivate)
-        }
-        double xp0[3], xp1[3], xq0[3], xq1[3];
-        load3(X, Nc, pn[P[0]], xp0);
-        load3(X, Nc, pn[P[1]], xp1);
-        load3(X, Nc, pn[Q[0]], xq0);
-        load3(X, Nc, pn[Q[1]], xq1);
-        double e1[3] = {xp1[0] - xp0[0], xp1[1] - xp0[1], xp1[2] - xp0[2]};
-        double e2[3] = {xq1[0] - xq0[0], xq1[1] - xq0[1], xq1[2] - xq0[2]};
-        double cr[3];
-        cross3(e1, e2, cr);
-        area = 0.25 * sqrt(dot3(cr, cr));
-    } else {
-        int ones = 0, lone1 = -1, lone0 = -1;
-        for (int l = 0; l < 4; ++l) {
-            if ((m >> l) & 1) { ++ones; lone1 = l; }
-            else if (lone0 < 0) lone0 = l;
-        }
-        const int lone = (ones == 1) ? lone1 : lone0;
-        int o[3], k = 0;
-        for (int l = 0; l < 4; ++l)
-            if (l != lone) o[k++] = l;
-        subs[0][0] = pn[lone];
-        subs[0][1] = sc.M(lone, o[0]);
-        subs[0][2] = sc.M(lone, o[1]);
-        subs[0][3] = sc.M(lone, o[2]);
-        ns = 1;
-        int A[3] = {sc.M(o[0], lone), sc.M(o[1], lone), sc.M(o[2], lone)};
-        int B[3] = {pn[o[0]], pn[o[1]], pn[o[2]]};
-        if (!deact) prism(subs, ns, A, B, ext);
-        double x0[3], x1[3], x2[3];
-        load3(X, Nc, pn[o[0]], x0);
-        load3(X, Nc, pn[o[1]], x1);
-        load3(X, Nc, pn[o[2]], x2);
-        double e1[3] = {x1[0] - x0[0], x1[1] - x0[1], x1[2] - x0[2]};
-        double e2[3] = {x2[0] - x0[0], x2[1] - x0[1], x2[2] - x0[2]};
-        double cr[3];
-        cross3(e1, e2, cr);
-        area = 0.125 * sqrt(dot3(cr, cr));
-    }
-    if (deact) ns = 0;   // the element only leaves the computation
+    // (no new nodes exist when splits only deactivate: the element only leaves the computation)
+    const int ns = deact ? 0 : cem_split_subs(n0, n1, n2, n3, mf.x0, mf.x1, mf.x2, mf.x3, m, mf, subs);
+    const double area = split_area(X, Nc, n0, n1, n2, n3, m);
     const int64_t base = T + sub_off[i];
     const double lp = lam[p], mp = mu[p];
-    for (int q = qs; q < ns && q == qs; ++q) {
-        int* s = subs[q];
+    if (qs < ns) {
+        const int q = qs;
+        int s[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            int v = subs[0][c];
+#pragma unroll
+            for (int r = 1; r < 6; ++r) v = (r == q) ? subs[r][c] : v;
+            s[c] = v;
+        }
         // Local nodes in ascending creation-id order (then at most the last two
         // swapped for a positive volume): the element-force record keeps local
         // nodes 0,1 and 2,3 in one 32-byte sector each, and pairing the two oldest

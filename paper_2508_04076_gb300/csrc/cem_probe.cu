@@ -99,3 +99,74 @@ extern "C" int cem_probe_split(const double* x, const float* f, int64_t n, float
     cudaFree(dlo);
     return rc;
 }
+
+// ---------------------------------------------------------------- split rule on the device
+#include "cem_prism.cuh"
+
+namespace {
+// new-node lookup of one probe case: mnode / mid[4 x + y] = the node on local edge x-y attached to x
+struct TableNode {
+    const int* mn;
+    const int* mi;
+    __device__ void operator()(int x, int y, int* node, int* id) const {
+        *node = mn[4 * x + y];
+        *id = mi[4 * x + y];
+    }
+};
+
+__global__ void k_probe_split_rule(int64_t n, const int* __restrict__ nodes, const int* __restrict__ ids,
+                                   const int* __restrict__ mask, const int* __restrict__ mnode,
+                                   const int* __restrict__ mid, int* __restrict__ subs, int* __restrict__ count) {
+    const int64_t q = (int64_t)blockIdx.x * PB + threadIdx.x;
+    if (q >= n) return;
+    const int* nd = nodes + 4 * q;
+    const int* id = ids + 4 * q;
+    int out[6][4];
+    const TableNode mf{mnode + 16 * q, mid + 16 * q};
+    const int k = cem_split_subs(nd[0], nd[1], nd[2], nd[3], id[0], id[1], id[2], id[3], mask[q], mf, out);
+    count[q] = k;
+    for (int r = 0; r < 6; ++r)
+        for (int c = 0; c < 4; ++c) subs[24 * q + 4 * r + c] = r < k ? out[r][c] : -1;
+}
+}  // namespace
+
+extern "C" int cem_probe_split_rule(int64_t n, const int* nodes, const int* ids, const int* mask, const int* mnode,
+                                    const int* mid, int* subs, int* count) {
+    if (n < 0 || (n > 0 && (!nodes || !ids || !mask || !mnode || !mid || !subs || !count))) return CEM_EINVAL;
+    for (int64_t q = 0; q < n; ++q) {   // a cut element: side mask of 4 bits with 1, 2 or 3 set
+        const int m = mask[q];
+        if (m <= 0 || m >= 15) return CEM_EINVAL;
+    }
+    if (n == 0) return CEM_OK;
+    int *d_nodes = nullptr, *d_ids = nullptr, *d_mask = nullptr, *d_mn = nullptr, *d_mi = nullptr, *d_subs = nullptr,
+        *d_cnt = nullptr;
+    int rc = CEM_OK;
+    const size_t b4 = 4 * n * sizeof(int), b16 = 16 * n * sizeof(int), b1 = n * sizeof(int);
+    if (cudaMalloc(&d_nodes, b4) != cudaSuccess || cudaMalloc(&d_ids, b4) != cudaSuccess ||
+        cudaMalloc(&d_mask, b1) != cudaSuccess || cudaMalloc(&d_mn, b16) != cudaSuccess ||
+        cudaMalloc(&d_mi, b16) != cudaSuccess || cudaMalloc(&d_subs, 24 * n * sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&d_cnt, b1) != cudaSuccess) {
+        rc = CEM_ENOMEM;
+    } else if (cudaMemcpy(d_nodes, nodes, b4, cudaMemcpyHostToDevice) != cudaSuccess ||
+               cudaMemcpy(d_ids, ids, b4, cudaMemcpyHostToDevice) != cudaSuccess ||
+               cudaMemcpy(d_mask, mask, b1, cudaMemcpyHostToDevice) != cudaSuccess ||
+               cudaMemcpy(d_mn, mnode, b16, cudaMemcpyHostToDevice) != cudaSuccess ||
+               cudaMemcpy(d_mi, mid, b16, cudaMemcpyHostToDevice) != cudaSuccess) {
+        rc = CEM_ECUDA;
+    } else {
+        k_probe_split_rule<<<(unsigned)((n + PB - 1) / PB), PB>>>(n, d_nodes, d_ids, d_mask, d_mn, d_mi, d_subs,
+                                                                   d_cnt);
+        if (cudaGetLastError() != cudaSuccess ||
+            cudaMemcpy(subs, d_subs, 24 * n * sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess ||
+            cudaMemcpy(count, d_cnt, b1, cudaMemcpyDeviceToHost) != cudaSuccess)
+            rc = CEM_ECUDA;
+    }
+    cudaFree(d_nodes);
+    cudaFree(d_ids);
+    cudaFree(d_mask);
+    cudaFree(d_mn);
+    cudaFree(d_mi);
+    cudaFree(d_subs);
+    cudaFree(d_cnt);
+    return rc;
+}

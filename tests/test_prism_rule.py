@@ -140,3 +140,65 @@ def test_cuda_division_matches_the_oracle(tmp_path):
         want = [[to_sto[v] for v in t] for t in prism_tets(tuple(int(x) for x in ext[:3]),
                                                            tuple(int(x) for x in ext[3:]))]
         assert got.tolist() == want
+
+
+RULE_DRIVER = r"""
+#include <cstdio>
+#include "%s"
+struct Table {
+    const int* mn;
+    const int* mi;
+    void operator()(int x, int y, int* node, int* id) const {
+        *node = mn[4 * x + y];
+        *id = mi[4 * x + y];
+    }
+};
+int main() {
+    int nd[4], id[4], m, mn[16], mi[16], out[6][4];
+    while (std::scanf("%%d %%d %%d %%d %%d %%d %%d %%d %%d", &nd[0], &nd[1], &nd[2], &nd[3], &id[0], &id[1], &id[2],
+                      &id[3], &m) == 9) {
+        for (int q = 0; q < 16; ++q) std::scanf("%%d", &mn[q]);
+        for (int q = 0; q < 16; ++q) std::scanf("%%d", &mi[q]);
+        const int k = cem_split_subs(nd[0], nd[1], nd[2], nd[3], id[0], id[1], id[2], id[3], m, Table{mn, mi}, out);
+        std::printf("%%d", k);
+        for (int r = 0; r < k; ++r) std::printf(" %%d %%d %%d %%d", out[r][0], out[r][1], out[r][2], out[r][3]);
+        std::printf("\n");
+    }
+    return 0;
+}
+"""
+
+
+def _run_rule_driver(tmp_path, nodes, ids, mask, mn, mi):
+    src = tmp_path / "rule.cpp"
+    src.write_text(RULE_DRIVER % HEADER)
+    exe = tmp_path / "rule"
+    subprocess.run(["g++", "-O2", "-std=c++17", "-o", str(exe), str(src)], check=True, capture_output=True)
+    lines = []
+    for q in range(nodes.shape[0]):
+        vals = list(nodes[q]) + list(ids[q]) + [mask[q]] + list(mn[q].ravel()) + list(mi[q].ravel())
+        lines.append(" ".join(str(int(v)) for v in vals))
+    r = subprocess.run([str(exe)], input="\n".join(lines) + "\n", capture_output=True, text=True, check=True)
+    out = []
+    for row in r.stdout.strip().split("\n"):
+        v = [int(x) for x in row.split()]
+        out.append(np.array(v[1:], dtype=np.int64).reshape(v[0], 4).tolist())
+    return out
+
+
+@pytest.mark.skipif(shutil.which("g++") is None, reason="needs a host C++ compiler")
+def test_cuda_split_rule_matches_the_oracle(tmp_path):
+    """The CUDA path's whole split rule (cem_split_subs, compiled here for the host)
+    gives the oracle's sub-elements, in the oracle's order: for random elements with
+    every side mask, and for the notch splits of three notched blocks."""
+    from cem_inputs import kuhn_block
+    from oracle import CEMOracle
+    from split_cases import notch_cases, random_cases
+    sets = [random_cases(2000, 21)]
+    for k, w in enumerate([kuhn_block(10, 4, 1, 0.05, 0.02, 0.005, notch_length=0.025, traction=1.5e6),
+                           kuhn_block(5, 4, 1, 0.025, 0.02, 0.005, notch_length=0.012, E_cov=0.2, seed=8),
+                           kuhn_block(16, 8, 3, 0.08, 0.04, 0.015, notch_length=0.04)]):
+        sets.append(notch_cases(CEMOracle.from_workload(w, split_enabled=False), 30 + k))
+    for nodes, ids, mask, mn, mi, want in sets:
+        got = _run_rule_driver(tmp_path, nodes, ids, mask, mn, mi)
+        assert got == want
