@@ -512,3 +512,24 @@ def test_adjoint_matches_central_differences():
         assert abs(fd - dE[j]) <= 1e-6 * np.abs(dE).max(), (j, fd, dE[j])
     fd = (_J(w, w.E, 1 + h, n, c, wu_fn) - _J(w, w.E, 1 - h, n, c, wu_fn)) / (2 * h)
     assert abs(fd - da) <= 1e-6 * abs(da), (fd, da)
+
+
+def test_time_step_hand_value_on_the_small_block():
+    """The fixed step of the 20x8x2 block (5 mm cubes, E = 32 GPa, nu = 0.2,
+    rho = 2450) against its value by hand: each cube splits into six Kuhn
+    tetrahedra of volume h^3/6 whose largest face is the right triangle with legs
+    h and h sqrt(2) (area h^2/sqrt(2)), so 3V / (largest face area) = h/sqrt(2);
+    the dilatational wave speed is sqrt((lambda + 2 mu)/rho) = 3,809.5 m/s; and the
+    step is 0.5 (h/sqrt(2)) / (2 c_d) = 2.320e-7 s (the factor 2 of the reading of
+    the CFL step: the split rule's sub-elements have half the parent's edges)."""
+    w = plate_small()
+    o = CEMOracle.from_workload(w)
+    h = 0.1 / 20
+    E, nu, rho = 32e9, 0.2, 2450.0
+    # lambda + 2 mu = E (1 - nu) / ((1 + nu)(1 - 2 nu)), the P-wave modulus
+    c_d = np.sqrt(E * (1 - nu) / ((1 + nu) * (1 - 2 * nu)) / rho)
+    assert abs(c_d - 3809.5) < 0.05
+    dt_hand = 0.5 * (h / np.sqrt(2.0)) / (2.0 * c_d)
+    assert abs(dt_hand - 2.3202e-7) < 1e-11
+    assert abs(o.dt - dt_hand) <= 1e-12 * dt_hand, (o.dt, dt_hand)
+    assert abs(o.h_min - h / np.sqrt(2.0)) <= 1e-12 * h
