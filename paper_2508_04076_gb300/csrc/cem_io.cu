@@ -15,8 +15,10 @@
 // preceded by its byte count, and last a 64-bit FNV-1a hash of every byte
 // before it.  Loading reads and hashes the whole file before it changes the
 // context, so a truncated or corrupted file leaves the context as it was
-// (array contents are not otherwise validated: indices out of range would
-// be read by the kernels as they stand).
+// Every index array is also range-checked on the host in that first pass
+// (node, element, edge and pool indices, the storage order a permutation,
+// every list inside its pool's used part), so a file that cem_save did not
+// write cannot put an out-of-range index on the device.
 #include "cem_common.cuh"
 
 #include <algorithm>
@@ -42,9 +44,14 @@ uint64_t fnv1a(uint64_t h, const void* p, size_t n) {
     return h;
 }
 
-struct Field {   // one array slice: device pointer, bytes
+// One array slice: device pointer, bytes; for int32 index arrays the range
+// [lo, hi) every entry must lie in (hi = 0: not an index array), with -1 also
+// allowed where `unset` says so.
+struct Field {
     void* p;
     size_t bytes;
+    int64_t lo = 0, hi = 0;
+    bool unset = false;
 };
 
 // The saved arrays, in file order (null pointers are skipped consistently on both sides).
@@ -53,8 +60,15 @@ std::vector<Field> fields(cem_ctx* c) {
     auto add = [&](void* p, int64_t n, size_t esz) {
         if (p && n > 0) f.push_back({p, (size_t)n * esz});
     };
+    // an int32 index array with entries in [lo, hi) (or -1 if unset)
+    auto idx = [&](void* p, int64_t n, int64_t lo, int64_t hi, bool unset = false) {
+        if (p && n > 0) f.push_back({p, (size_t)n * 4, lo, hi, unset});
+    };
     auto rows = [&](void* p, int nrow, int64_t ld, int64_t n, size_t esz) {
         for (int r = 0; r < nrow && p; ++r) add((char*)p + (size_t)r * ld * esz, n, esz);
+    };
+    auto idx_rows = [&](int* p, int nrow, int64_t ld, int64_t n, int64_t lo, int64_t hi) {
+        for (int r = 0; r < nrow && p; ++r) idx(p + (size_t)r * ld, n, lo, hi);
     };
     const int64_t N = c->N, T = c->T, E = c->E;
     const bool hex = c->elem_type == CEM_ELEM_HEX8;
@@ -65,14 +79,14 @@ std::vector<Field> fields(cem_ctx* c) {
     rows(c->fext, 3, c->Nc, N, 8);
     add(c->mass, N, 8);
     add(c->minv, N, 8);
-    add(c->inc_off, N, 4);
-    add(c->inc_cnt, N, 4);
+    idx(c->inc_off, N, 0, std::max<int64_t>(c->inc_top, 1));
+    idx(c->inc_cnt, N, 0, c->inc_top + 1);
     add(c->dtn, N, 8);
     add(c->node_inst, N, 4);
     add(c->uhl, 8 * N, 4);
-    rows(c->conn, c->npe, c->Tc, T, 4);
-    rows(c->t2e, c->epe, c->Tc, T, 4);
-    add(c->anc, T, 4);
+    idx_rows(c->conn, c->npe, c->Tc, T, 0, N);
+    idx_rows(c->t2e, c->epe, c->Tc, T, 0, E);
+    idx(c->anc, T, 0, c->T0);
     add(c->active, T, 1);
     const int ng = hex ? (int)cem_hex_geometry_values() : 9;
     rows(c->Vg, ng, c->Tc, T, 8);
@@ -80,33 +94,33 @@ std::vector<Field> fields(cem_ctx* c) {
     add(c->vol, T, 8);
     add(c->lam, T, 8);
     add(c->mu, T, 8);
-    add(c->fan_off, E, 4);
-    add(c->fan_cnt, E, 4);
+    idx(c->fan_off, E, 0, std::max<int64_t>(c->fan_top, 1));
+    idx(c->fan_cnt, E, 0, c->fan_top + 1);
     add(c->cl, E, 8);
     add(c->cm, E, 8);
     add(c->sumV, E, 8);
     add(c->cl32, E, 4);
     add(c->cm32, E, 4);
-    add(c->fan_pool, c->fan_top, 4);
-    add(c->inc_pool, c->inc_top, 4);
+    idx(c->fan_pool, c->fan_top, 0, hex ? T * c->epe : T);   // fan entries: elements (hexahedra: element * 12 + edge)
+    idx(c->inc_pool, c->inc_top, 0, T * c->npe);               // incidence entries: element * nodes + local
     add(c->Gc, c->T0, 8);
     add(c->side, c->T0, 1);
     add(c->split_step, c->T0, 4);
     add(c->split_G, c->T0, 8);
     add(c->ud_tet, c->T0, 8);
     add(c->cand_flag, c->T0, 1);
-    add(c->cand_list, c->n_cand, 4);
-    add(c->node_of_key, 2 * c->E0, 4);
+    idx(c->cand_list, c->n_cand, 0, c->T0);
+    idx(c->node_of_key, 2 * c->E0, 0, N, true);
     add(c->hkeys, c->hash_cap, 8);
-    add(c->hvals, c->hash_cap, 4);
+    idx(c->hvals, c->hash_cap, 0, E, true);
     add(c->hfirst, c->hash_cap, 4);
     add(c->Ud, 1, 8);
     // node storage order (creation id of each stored node) and the node references a
     // renumbering rewrites besides conn and node_of_key
-    add(c->ext_of_int, N, 4);
-    add(c->oe_n0, c->E0, 4);
-    add(c->oe_n1, c->E0, 4);
-    add(c->dir_key, c->n_dir, 4);
+    idx(c->ext_of_int, N, 0, N);
+    idx(c->oe_n0, c->E0, 0, N);
+    idx(c->oe_n1, c->E0, 0, N);
+    idx(c->dir_key, c->n_dir, 0, 4 * N);
     return f;
 }
 
@@ -244,16 +258,28 @@ extern "C" int cem_load(cem_ctx* c, const char* path) {
     uint64_t hash = fnv1a(fnv1a(FNV_BASIS, tag, 8), h, sizeof h);
     bool ok = data_at >= 0;
     std::vector<char> buf;
+    bool in_range = true;
+    // the list offsets and counts and the storage order, kept for the cross checks below
+    std::vector<int> keep_off[2], keep_cnt[2], keep_ext;
     for (size_t q = 0; q < fl.size() && ok; ++q) {
         int64_t nb = 0;
         ok = std::fread(&nb, sizeof nb, 1, fp) == 1 && nb == (int64_t)fl[q].bytes;
         if (!ok) break;
         hash = fnv1a(hash, &nb, sizeof nb);
-        for (size_t done = 0; done < fl[q].bytes && ok;) {   // in pieces of at most 64 MiB
+        std::vector<int>* keep = fl[q].p == c->fan_off ? &keep_off[0] : fl[q].p == c->fan_cnt ? &keep_cnt[0]
+                               : fl[q].p == c->inc_off ? &keep_off[1] : fl[q].p == c->inc_cnt ? &keep_cnt[1]
+                               : fl[q].p == c->ext_of_int ? &keep_ext : nullptr;
+        for (size_t done = 0; done < fl[q].bytes && ok;) {   // in pieces of at most 64 MiB (whole int32 entries)
             const size_t n = std::min(fl[q].bytes - done, (size_t)1 << 26);
             buf.resize(n);
             ok = std::fread(buf.data(), 1, n, fp) == n;
             if (ok) hash = fnv1a(hash, buf.data(), n);
+            if (ok && fl[q].hi > 0) {
+                const int* v = (const int*)buf.data();
+                for (size_t k = 0; k < n / 4; ++k)
+                    in_range = in_range && ((v[k] >= fl[q].lo && v[k] < fl[q].hi) || (fl[q].unset && v[k] == -1));
+                if (keep) keep->insert(keep->end(), v, v + n / 4);
+            }
             done += n;
         }
     }
@@ -263,6 +289,23 @@ extern "C" int cem_load(cem_ctx* c, const char* path) {
         set_counts(c, old);
         std::fclose(fp);
         return cem_fail(c, CEM_EINVAL, "checkpoint file truncated, inconsistent or corrupt; context unchanged");
+    }
+    // every list inside its pool's used part; the storage order a permutation of [0, N)
+    const int64_t tops[2] = {c->fan_top, c->inc_top};
+    for (int k = 0; k < 2 && in_range; ++k)
+        for (size_t x = 0; x < keep_off[k].size() && x < keep_cnt[k].size(); ++x)
+            in_range = in_range && (int64_t)keep_off[k][x] + keep_cnt[k][x] <= tops[k];
+    if (in_range && !keep_ext.empty()) {
+        std::vector<char> seen(keep_ext.size(), 0);
+        for (int v : keep_ext) {
+            in_range = in_range && !seen[v];
+            seen[v] = 1;
+        }
+    }
+    if (!in_range) {
+        set_counts(c, old);
+        std::fclose(fp);
+        return cem_fail(c, CEM_EINVAL, "checkpoint holds an index out of range; context unchanged");
     }
     // node maps: identity, then the saved storage order of the first N nodes and its inverse
     if (int rc = cem_reorder_identity(c)) {

@@ -88,3 +88,38 @@ def test_load_rejects_other_meshes_and_bad_files(CEM, tmp_path):
     assert np.array_equal(c.field("u"), u5) and c.energy()["step"] == 5
     c.step(5)
     assert np.array_equal(c.field("u"), a.field("u")) and c.energy() == a.energy()
+
+
+def test_load_rejects_indices_out_of_range(CEM, tmp_path):
+    """A file with a valid hash whose element holds a node index past the node
+    count (a file cem_save did not write) is rejected before anything reaches the
+    device, and the context continues as it was."""
+    from ckpt_reader import chunks, read, rehash
+    from paper_2508_04076_gb300 import CEMError
+    path = str(tmp_path / "ck.bin")
+    a = CEM.from_workload(plate_small())
+    a.step(10)
+    a.save(path)
+    H, _ = read(path)
+    raw = bytearray(open(path, "rb").read())
+    conn0 = chunks(raw)[19]            # X, u, v, a, f_ext (3 rows each), mass, 1/m, incidence offset and count
+    assert conn0[1] == 4 * H["T"]
+    for bad_value in (H["N"] + 5, -1):
+        mod = bytearray(raw)
+        mod[conn0[0]:conn0[0] + 4] = int(bad_value).to_bytes(4, "little", signed=True)
+        bad = tmp_path / "bad.bin"
+        bad.write_bytes(bytes(rehash(mod)))
+        c = CEM.from_workload(plate_small())
+        c.step(5)
+        u5 = c.field("u")
+        with pytest.raises(CEMError):
+            c.load(str(bad))
+        assert np.array_equal(c.field("u"), u5) and c.energy()["step"] == 5
+        c.step(5)
+        assert np.array_equal(c.field("u"), a.field("u")) and c.energy() == a.energy()
+    # the same file with its hash recomputed but no index changed loads
+    ok = tmp_path / "ok.bin"
+    ok.write_bytes(bytes(rehash(raw)))
+    d = CEM.from_workload(plate_small())
+    d.load(str(ok))
+    assert np.array_equal(d.field("u"), a.field("u"))
