@@ -113,11 +113,14 @@ extern "C" int cem_node_energies_noalloc(const double* u, const double* v, const
     if (!out || n_nodes < 0 || ld < n_nodes) return CEM_EINVAL;
     if (n_nodes > NA_MAX_NODES) return CEM_ECAPACITY;
     if (n_nodes > 0 && (!u || !v || !a || !mass || !fext)) return CEM_EINVAL;
+    // an error left pending by earlier work on this thread is reported, not cleared: it is
+    // the caller's to read (a sticky error from a fault means the context is lost anyway)
+    if (cudaPeekAtLastError() != cudaSuccess) return CEM_ECUDA;
     double* part = nullptr;
     if (int rc = scratch_address(&part)) return rc;
     const int nb = n_nodes > 0 ? (int)((n_nodes + (int64_t)NA_BS * NA_IPT - 1) / ((int64_t)NA_BS * NA_IPT)) : 1;
     cudaStream_t s = (cudaStream_t)stream;
     k_node_energy_partials<<<nb, NA_BS, 0, s>>>(u, v, a, mass, fext, n_nodes, ld, part);
     k_node_energy_final<<<1, NA_BS, 0, s>>>(part, nb, out);
-    return cudaGetLastError() == cudaSuccess ? CEM_OK : CEM_ECUDA;
+    return cudaGetLastError() == cudaSuccess ? CEM_OK : CEM_ECUDA;   // only these launches' errors are pending here
 }
