@@ -29,7 +29,7 @@ import tempfile
 import threading
 import time
 
-if "reference" in sys.argv or "--cpu-baseline-worker" in sys.argv:
+if "reference" in sys.argv or "--cpu-baseline-worker" in sys.argv or "--cpu-allcore-worker" in sys.argv:
     for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "NUMEXPR_NUM_THREADS"):
         os.environ[_v] = "1"
 
@@ -52,100 +52,153 @@ def _workload(name="block"):
 
 KERNEL_UNITS = {"predict": "nodes", "strain": "tets", "edge_stress": "edges", "force": "tets", "node_update": "nodes"}
 
-# DRAM bytes (read + write) per unit measured by ncu for the mixed-precision kernels on the
-# 960,000-element block (profiles/mixed_kernels_notched_block_200x80x10.md); scaled by the
-# units of an average launch for the roofline's "traffic".  None: no capture of the current
-# kernel (FP64 path).
-DRAM_BYTES_PER_UNIT = {"mixed": {"strain": 62.6, "edge_stress": 68.0, "force": 126.3, "node_update": 564.5},
-                       "fp64": {}}
+# DRAM bytes (read + write) per unit measured by ncu (dram__bytes_read.sum + dram__bytes_write.sum of one
+# launch, divided by the launch's units: 982,000 elements, 1,219,792 edges, 187,533 nodes after the notch)
+# on the intact 960,000-element block, for the kernels as they are now.  Source:
+# profiles/step_kernels_fp64_notched_block_200x80x10.md and profiles/step_kernels_mixed_notched_block_200x80x10.md.
+DRAM_BYTES_PER_UNIT = {"fp64": {"strain": 108.7, "edge_stress": 103.6, "force": 216.2, "node_update": 847.3},
+                       "mixed": {"strain": 63.0, "edge_stress": 70.9, "force": 129.7, "node_update": 557.3}}
+
+
+def b_alg_per_tet_step(T, E, N, precision):
+    """Algorithmic bytes per element-step of the whole step (the survey's model, section 8(d)).
+
+    Each algorithmic array is streamed once per step; gathers hit in L2; the
+    intermediates h (element strains), sigma (edge stresses) and the element forces
+    are not algorithmic (a perfectly fused step keeps them on chip).  FP64:
+      node state u r/w, v r/w, 1/m, f_ext   128 B per node
+      connectivity (4 x i32)                 16 B per element
+      geometry V grad N (9 x f64)            72 B per element
+      edge fan CSR (6 i32 per element, one i32 offset per edge)  24 + 4 E/T
+      edge 1/sum V (f64)                      8 B per edge
+      node CSR (4 i32 per element, one i32 offset per node)       16 + 4 N/T
+    Mixed: geometry (36 B) and 1/sum V (4 B) in FP32, and a Kahan compensation of u
+    (80 B per node: the survey's +14 B per element-step at N/T = 0.1738).
+    """
+    n, e = N / T, E / T
+    b = 128.0 * n + 16 + 72 + 24 + 4.0 * e + 8.0 * e + 16 + 4.0 * n
+    if precision == "mixed":
+        b += -36.0 - 4.0 * e + 80.0 * n
+    return b
+
+
+def flops_per_tet_step(T, E, N):
+    """Algorithmic FP64 flops per element-step of the whole step (FMA = 2): the sum of
+    kernel_costs' per-unit counts weighted by units per element."""
+    fl, _, _ = kernel_costs(T, E, N, "fp64")
+    return fl["predict"] * N / T + fl["strain"] + fl["edge_stress"] * E / T + fl["force"] + fl["node_update"] * N / T
 
 
 def kernel_costs(T, E, N, precision):
-    """Algorithmic FP64 flops (FMA = 2; FP64 path) and bytes per unit of each hot kernel.
+    """Per unit of each hot kernel: (FP64 flops, algorithmic bytes, moved bytes).
 
-    Bytes are the arrays the kernel reads or writes, each once (gathered
-    operands counted once per producer: u per node, h per element, sigma per
-    edge, element forces per element).  f = mean fan size 6T/E, g = mean node
-    incidence 4T/N.  Mixed precision: FP32 geometry, coefficients and
-    intermediate records (h, sigma: 32 B; element forces: 64 B), an FP32
-    hi/lo copy of the predicted u (32 B per node), FP64 node state; the node
-    update also reads and writes u and writes that copy (the fused predictor).
+    Flops (FMA = 2) are counted from the kernels' arithmetic.  Algorithmic bytes
+    charge each array of b_alg_per_tet_step to the first kernel of the step that
+    reads it (so they sum to the whole step's figure): the predictor the u read and
+    write (the node update in mixed precision, which carries the predictor),
+    strain the connectivity and geometry, edge stress the fan lists and 1/sum V,
+    the node update v, 1/m, f_ext, the incidence lists and (mixed) the Kahan term;
+    the force kernel reads only intermediates and the element-edge map.  Moved
+    bytes are what the kernel as written reads and writes, each array once,
+    intermediates included (gathered operands counted once per producer).
+    f = mean fan size 6T/E, g = mean node incidence 4T/N.
     """
     f, g = 6.0 * T / E, 4.0 * T / N
     flops = {"predict": 12.0, "strain": 57.0, "edge_stress": 6.0 * f + 13.0, "force": 90.0,
              "node_update": 3.0 * g + 18.0}
     if precision == "fp64":
-        byts = {"predict": 96.0,
-                "strain": 16 + 72 + 48 + 24.0 * N / T,
-                "edge_stress": 8 + 4.0 * f + 16 + 48 + 48.0 * T / E,
-                "force": 24 + 72 + 96 + 48.0 * E / T,
-                "node_update": 8 + 4.0 * g + 24 + 8 + 96 + 96.0 * T / N}
+        alg = {"predict": 48.0, "strain": 16.0 + 72.0, "edge_stress": 4.0 * f + 4.0 + 8.0, "force": 0.0,
+               "node_update": 48.0 + 8.0 + 24.0 + 4.0 * g + 4.0}
+        moved = {"predict": 96.0,
+                 "strain": 16 + 72 + 48 + 24.0 * N / T,
+                 "edge_stress": 8 + 4.0 * f + 16 + 48 + 48.0 * T / E,
+                 "force": 24 + 72 + 96 + 48.0 * E / T,
+                 "node_update": 8 + 4.0 * g + 24 + 8 + 96 + 96.0 * T / N}
     else:
-        byts = {"predict": 0.0,   # carried by the node update
-                "strain": 16 + 36 + 32 + 32.0 * N / T,
-                "edge_stress": 8 + 4.0 * f + 8 + 32 + 32.0 * T / E,
-                "force": 24 + 36 + 64 + 32.0 * E / T,
-                "node_update": 8 + 4.0 * g + 24 + 8 + 96 + 80 + 64.0 * T / N}
-    return flops, byts
+        alg = {"predict": 0.0, "strain": 16.0 + 36.0, "edge_stress": 4.0 * f + 4.0 + 4.0, "force": 0.0,
+               "node_update": 48.0 + 48.0 + 8.0 + 24.0 + 4.0 * g + 4.0 + 80.0}
+        moved = {"predict": 0.0,   # carried by the node update
+                 "strain": 16 + 36 + 32 + 32.0 * N / T,
+                 "edge_stress": 8 + 4.0 * f + 8 + 32 + 32.0 * T / E,
+                 "force": 24 + 36 + 64 + 32.0 * E / T,
+                 "node_update": 8 + 4.0 * g + 24 + 8 + 96 + 80 + 64.0 * T / N}
+    return flops, alg, moved
 
 
-def roofline_accounting(chunks, prof, precision, scale, t_ms, hbm, sm_clock):
-    """Per-kernel shares and the dominant step kernel's roofline from sampled kernel times.
+def roofline_accounting(chunks, prof, precision, scale, t_ms, hbm, fp64_peak):
+    """Per-kernel figures, the dominant step kernel's roofline and the whole step's.
 
-    chunks: [(counts, {kernel: (ms, launches)})] for consecutive windows of the timed
-    region; counts holds the window's mean n_active_tets, n_edges and n_nodes, and the
-    dict the sampled launches' time and number in that window.  prof: {kernel:
-    (total ms, launches)} over the whole region; scale = timed steps / sampled steps;
-    t_ms the region's time.  The algorithmic bytes (flops) of a sampled launch are the
-    per-unit figures of kernel_costs for its window's sizes times its units, so a mesh
-    that grows during the run is accounted window by window.  Achieved = the dominant
-    kernel's bytes (flops) per launch / its mean launch time; it is FP64-ALU-bound when
-    its flops take longer at the FP64 peak than its bytes at the HBM peak (FP64 path only).
+    chunks: [(counts, steps, {kernel: (ms, launches)})] for consecutive windows of the
+    timed region; counts holds the window's mean n_active_tets, n_edges and n_nodes,
+    steps the window's step count and the dict the sampled launches' time and number in
+    that window.  prof: {kernel: (total ms, launches)} over the whole region; scale =
+    timed steps / sampled steps; t_ms the region's time; hbm the HBM peak in GB/s;
+    fp64_peak the FP64 FMA rate in FLOP/s.  The flops and bytes of a sampled launch are
+    the per-unit figures of kernel_costs for its window's sizes times its units, so a
+    mesh that grows during the run is accounted window by window.
+
+    The dominant kernel's roofline: FP64 path, bound "alu": its FP64 flops per launch /
+    its mean launch time against fp64_peak (the FP64 step kernels do several FP64
+    operations per algorithmic byte, far above GB300's FP64-to-HBM balance of about 0.19
+    flop/B).  Mixed path, bound "hbm": its algorithmic bytes per launch / its mean launch
+    time against hbm.  The whole step: algorithmic bytes (flops) of every element-step of
+    the region / the region's time, against the same peaks.
     """
-    acc = {k: dict(bytes=0.0, flops=0.0, units=0.0, traffic=0.0) for k in KERNEL_UNITS}
+    acc = {k: dict(bytes=0.0, moved=0.0, flops=0.0, units=0.0, traffic=0.0) for k in KERNEL_UNITS}
     per_unit = DRAM_BYTES_PER_UNIT.get(precision, {})
-    for cnt, dp in chunks:
-        fl, by = kernel_costs(cnt["n_active_tets"], cnt["n_edges"], cnt["n_nodes"], precision)
+    whole_bytes = whole_flops = elem_steps = 0.0
+    for cnt, nsteps, dp in chunks:
+        T, E, N = cnt["n_active_tets"], cnt["n_edges"], cnt["n_nodes"]
+        fl, alg, mv = kernel_costs(T, E, N, precision)
+        whole_bytes += b_alg_per_tet_step(T, E, N, precision) * T * nsteps
+        whole_flops += flops_per_tet_step(T, E, N) * T * nsteps
+        elem_steps += T * nsteps
         for k, (_, nl) in dp.items():
-            units = {"tets": cnt["n_active_tets"], "edges": cnt["n_edges"], "nodes": cnt["n_nodes"]}[KERNEL_UNITS[k]]
-            acc[k]["bytes"] += nl * by[k] * units
+            units = {"tets": T, "edges": E, "nodes": N}[KERNEL_UNITS[k]]
+            acc[k]["bytes"] += nl * alg[k] * units
+            acc[k]["moved"] += nl * mv[k] * units
             acc[k]["flops"] += nl * fl[k] * units
             acc[k]["units"] += nl * units
-            acc[k]["traffic"] += nl * per_unit.get(k, 0.0) * units
+            acc[k]["traffic"] += nl * (per_unit.get(k) or 0.0) * units
     kernels = {}
     for k, (ms_tot, nl) in prof.items():
         kernels[k] = {"ms": ms_tot * scale, "launches_timed": nl, "share": ms_tot * scale / max(t_ms, 1e-9)}
         if k in KERNEL_UNITS and nl:
             sec = ms_tot * 1e-3
-            kernels[k].update(per_launch_us=sec / nl * 1e6, gbs=acc[k]["bytes"] / sec / 1e9)
-            if precision == "fp64":
-                kernels[k]["fp64_tflops"] = acc[k]["flops"] / sec / 1e12
-    fp64_peak = 152 * 4 * sm_clock * 1e6      # 152 SMs x 2 FP64 FMA/clk x 2 FLOP
+            kernels[k].update(per_launch_us=sec / nl * 1e6, alg_gbs=acc[k]["bytes"] / sec / 1e9,
+                              moved_gbs=acc[k]["moved"] / sec / 1e9, fp64_tflops=acc[k]["flops"] / sec / 1e12)
     hot = {k: prof[k] for k in KERNEL_UNITS}
     dom = max(hot, key=lambda k: hot[k][0])
     ms_tot, nl = hot[dom]
     nl = max(nl, 1)
     per_launch_s = ms_tot * 1e-3 / nl
     units = acc[dom]["units"] / nl
-    flops, bytes_ = acc[dom]["flops"] / nl, acc[dom]["bytes"] / nl
-    alu_bound = precision == "fp64" and flops / fp64_peak > bytes_ / ((hbm or 6651.4) * 1e9)
-    if alu_bound:
-        achieved, peak, unit = flops / per_launch_s / 1e12, fp64_peak / 1e12, "TFLOP/s"
-        src = "derived: 152 SMs x 4 FP64 FLOP/clk x %.0f MHz (nominal 1.25 TFLOP/s at 2070 MHz)" % sm_clock
+    flops, bytes_, moved = acc[dom]["flops"] / nl, acc[dom]["bytes"] / nl, acc[dom]["moved"] / nl
+    if precision == "fp64":
+        achieved, peak, unit, bound = flops / per_launch_s / 1e12, fp64_peak / 1e12, "TFLOP/s", "alu"
+        src = "FP64 FMA rate measured live on this GPU (cem_probe_fp64_fma, FMA = 2 FLOP)"
     else:
-        achieved, peak, unit = bytes_ / per_launch_s / 1e9, hbm, "GB/s"
-        src = "MEASURED_PEAKS.json hbm_gbs (measured copy bandwidth)"
-    traffic = acc[dom]["traffic"] / nl if dom in per_unit else None
-    roofline = {"bound": "alu" if alu_bound else "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
-                "unit": unit, "frac": achieved / peak if peak else None, "traffic": traffic, "peak_source": src,
-                "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum per unit on the 960,000-"
-                                   "element block, scaled to the units of each sampled launch" if traffic
-                                   else None),
-                "per_launch_us": per_launch_s * 1e6, "algorithmic_bytes_per_launch": bytes_,
-                "algorithmic_flops_per_launch": flops,
-                "hbm_gbs_achieved": bytes_ / per_launch_s / 1e9, "hbm_peak_gbs": hbm,
-                "units_per_launch": units, "units_integrated_over": "%d chunks of <= %d steps" % (
-                    len(chunks), CHUNK_STEPS)}
+        achieved, peak, unit, bound = bytes_ / per_launch_s / 1e9, hbm, "GB/s", "hbm"
+        src = "HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"
+    traffic = acc[dom]["traffic"] / nl if per_unit.get(dom) else None
+    t_s = t_ms * 1e-3
+    roofline = {"bound": bound, "kernel": dom, "achieved": achieved, "peak": peak, "unit": unit,
+                "frac": achieved / peak if peak else None, "traffic": traffic, "peak_source": src,
+                "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum per unit of the current "
+                                   "kernel on the intact 960,000-element block, times the units per launch"
+                                   if traffic else None),
+                "per_launch_us": per_launch_s * 1e6, "algorithmic_flops_per_launch": flops,
+                "algorithmic_bytes_per_launch": bytes_, "moved_bytes_per_launch": moved,
+                "units_per_launch": units,
+                "units_integrated_over": "%d windows of <= %d steps" % (len(chunks), CHUNK_STEPS),
+                "whole_step": {
+                    "b_alg_per_element_step": whole_bytes / max(elem_steps, 1.0),
+                    "flops_per_element_step": whole_flops / max(elem_steps, 1.0),
+                    "alg_gbs": whole_bytes / t_s / 1e9, "hbm_peak_gbs": hbm,
+                    "hbm_frac": whole_bytes / t_s / 1e9 / hbm if hbm else None,
+                    "fp64_tflops": whole_flops / t_s / 1e12, "fp64_peak_tflops": fp64_peak / 1e12,
+                    "fp64_frac": whole_flops / t_s / fp64_peak if fp64_peak else None,
+                    "active_element_steps_per_s": elem_steps / t_s}}
     return kernels, roofline
 
 
@@ -157,7 +210,8 @@ def _args():
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", choices=["cem", "reference"], default="cem")
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--precision", choices=["fp64", "mixed"], default="mixed")
+    p.add_argument("--precision", choices=["fp64", "mixed"], default="fp64",
+                   help="precision of the headline run (default: plain FP64); the other runs as a sub-object")
     p.add_argument("--workload", choices=["block", "ensemble"], default="block",
                    help="block: the 960,000-element notched block; ensemble: 256 notched blocks of "
                         "5k-200k elements (about 2.6e7) advanced as one union mesh")
@@ -181,6 +235,7 @@ def _args():
     p.add_argument("--resume", action="store_true",
                    help="load --state into a fresh context and time --steps steps from there, then exit")
     p.add_argument("--cpu-baseline-worker", action="store_true", help=argparse.SUPPRESS)
+    p.add_argument("--cpu-allcore-worker", action="store_true", help=argparse.SUPPRESS)
     p.add_argument("--cpu-steps", type=int, default=80, help=argparse.SUPPRESS)
     return p.parse_args()
 
@@ -190,6 +245,24 @@ def _peaks():
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except Exception:
         return {}
+
+
+HBM_FALLBACK_GBS = 6800.0   # the profiling recipe's fallback copy bandwidth, used only without MEASURED_PEAKS.json
+
+
+def _hbm_peak(peaks):
+    """(HBM GB/s, source): the measured copy bandwidth, else the recipe's fallback."""
+    if peaks.get("hbm_gbs"):
+        return float(peaks["hbm_gbs"]), "of measured (MEASURED_PEAKS.json hbm_gbs)"
+    return HBM_FALLBACK_GBS, "of fallback (no MEASURED_PEAKS.json: the recipe's 6.8 TB/s)"
+
+
+def _leg(name, fn):
+    """Run a secondary leg; a failure is recorded in the line instead of losing it."""
+    try:
+        return fn()
+    except Exception as ex:   # reported, not hidden
+        return {"error": "%s: %r" % (name, ex)}
 
 
 class ClockSampler:
@@ -208,6 +281,16 @@ class ClockSampler:
             self.p = subprocess.Popen(cmd, stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.p = None
+
+    def wait_first(self, timeout=5.0):
+        """Block until nvidia-smi has written its first sample (or timeout)."""
+        t0 = time.time()
+        while self.p is not None and time.time() - t0 < timeout:
+            self.f.flush()
+            if os.path.getsize(self.f.name) > 0:
+                return True
+            time.sleep(0.05)
+        return False
 
     def stop(self):
         if self.p is not None:
@@ -274,18 +357,77 @@ def _host_cpu():
     return {"nproc": os.cpu_count(), "model": model}
 
 
-def _cpu_baseline(steps):
-    """Run the oracle in a single-threaded subprocess; returns the cpu_baseline object."""
-    cmd = [sys.executable, os.path.abspath(__file__), "--cpu-baseline-worker", "--cpu-steps", str(steps)]
+def _single_thread_env():
     env = dict(os.environ)
     for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "NUMEXPR_NUM_THREADS"):
         env[v] = "1"
-    r = subprocess.run(cmd, capture_output=True, text=True, env=env, timeout=1800)
+    return env
+
+
+ALLCORE_BLOCK = (100, 40, 10, 0.05, 0.02, 0.01, 0.025)   # the benchmark's cell shape on a quarter of its block
+
+
+def _allcore_workload():
+    from cem_inputs import kuhn_block
+    nx, ny, nz, lx, ly, lz, notch = ALLCORE_BLOCK
+    return kuhn_block(nx, ny, nz, lx, ly, lz, notch_length=notch, traction=1e6)
+
+
+def _allcore_worker(steps):
+    """One single-threaded oracle process of the all-core baseline: set up, report ready,
+    wait for the go line on stdin, time `steps` steps, report."""
+    from oracle import CEMOracle
+    w = _allcore_workload()
+    o = CEMOracle.from_workload(w)
+    o.step(1)
+    print("ready", flush=True)
+    sys.stdin.readline()
+    t0 = time.time()
+    o.step(steps)
+    t1 = time.time()
+    print(json.dumps({"tets": w.n_tets, "steps": steps, "t0": t0, "t1": t1}), flush=True)
+
+
+def _cpu_baseline(steps, allcore_steps=20):
+    """The oracle on the host cores; returns the cpu_baseline object.
+
+    value: one single-threaded process on the benchmark workload (steps 2..steps+1).
+    all_cores: one single-threaded process per logical CPU at once, each on a quarter-size
+    block of the same cell shape (one benchmark-size oracle per core would not fit in host
+    memory): every process sets up untimed, then all start together; the figure is the
+    elements x steps of all processes over the span from the first start to the last end.
+    """
+    cmd = [sys.executable, os.path.abspath(__file__), "--cpu-baseline-worker", "--cpu-steps", str(steps)]
+    r = subprocess.run(cmd, capture_output=True, text=True, env=_single_thread_env(), timeout=1800)
     res = json.loads(r.stdout.strip().splitlines()[-1])
-    return {"value": res["value"], "unit": METRIC, "cores": 1, "kind": "oracle",
-            "sample": "%s, steps 2-%d of the run (%.1f s of CPU time; setup untimed), "
-                      "single-threaded numpy/scipy FP64 oracle" % (WORKLOAD, res["steps"] + 1, res["seconds"]),
-            "host": _host_cpu()}
+    out = {"value": res["value"], "unit": METRIC, "cores": 1, "kind": "oracle",
+           "sample": "%s, steps 2-%d of the run (%.1f s of CPU time; setup untimed), "
+                     "single-threaded numpy/scipy FP64 oracle" % (WORKLOAD, res["steps"] + 1, res["seconds"]),
+           "host": _host_cpu()}
+    try:
+        n = os.cpu_count() or 1
+        wcmd = [sys.executable, os.path.abspath(__file__), "--cpu-allcore-worker", "--cpu-steps", str(allcore_steps)]
+        procs = [subprocess.Popen(wcmd, stdin=subprocess.PIPE, stdout=subprocess.PIPE, text=True,
+                                  env=_single_thread_env()) for _ in range(n)]
+        for p in procs:
+            if p.stdout.readline().strip() != "ready":
+                raise RuntimeError("an all-core worker failed to set up")
+        for p in procs:
+            p.stdin.write("go\n")
+            p.stdin.flush()
+        rows = [json.loads(p.stdout.readline()) for p in procs]
+        for p in procs:
+            p.wait(timeout=600)
+        span = max(r_["t1"] for r_ in rows) - min(r_["t0"] for r_ in rows)
+        work = sum(r_["tets"] * r_["steps"] for r_ in rows)
+        nx, ny, nz = ALLCORE_BLOCK[:3]
+        out["all_cores"] = {"value": work / span, "unit": METRIC, "cores": n, "kind": "oracle",
+                            "sample": "%d single-threaded oracle processes at once, each %d steps of a %dx%dx%d "
+                                      "notched block (%d elements, the benchmark's cell shape); %.1f s span"
+                                      % (n, allcore_steps, nx, ny, nz, rows[0]["tets"], span)}
+    except Exception as ex:   # reported, not hidden
+        out["all_cores"] = {"error": repr(ex)}
+    return out
 
 
 # --------------------------------------------------------------------------- arms
@@ -395,10 +537,10 @@ def run_cem(a):
         sim.close()
         return
     peaks = _peaks()
-    hbm = peaks.get("hbm_gbs")
-    fp64_peak_meas = probe_fp64_fma(dev, stream.cuda_stream)
+    hbm, hbm_src = _hbm_peak(peaks)
+    fp64_peak = probe_fp64_fma(dev, stream.cuda_stream)
 
-    def timed(precision, clocks_on, w=w, steps=None, split_capacity=None):
+    def timed(precision, clocks_on, w=w, steps=None, split_capacity=None, keep_u=False):
         """W untimed then K timed steps of a fresh context: metrics of the timed region."""
         steps = a.steps if steps is None else steps
         cap = a.split_capacity if split_capacity is None else split_capacity
@@ -407,15 +549,19 @@ def run_cem(a):
         info0 = sim.info()
         if not a.no_autotune:   # launch variants for the current sizes; re-tuned in the run as the mesh grows
             sim.autotune(reps=10, automatic=True)
+        # clocks: the sampler runs from before the warm-up steps to after the timed region (a
+        # short timed region may see no sample of its own at nvidia-smi's 100 ms period)
+        clocks = ClockSampler(_bus_id(dev)) if (clocks_on and rank == 0) else None
+        if clocks:
+            clocks.wait_first()
         sim.step(a.warmup)
         barrier()
-        clocks = ClockSampler(_bus_id(dev)) if (clocks_on and rank == 0) else None
         sim.profile(max(1, min(PROFILE_EVERY, steps // 4)))   # at least a few sampled steps
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         # The mesh grows during the run, so the sampled launches' units (elements, edges, nodes)
-        # are integrated chunk by chunk: each chunk's sampled kernel time is paired with the mean
-        # of its first and last counts.  The counts and timing sums are read on the host between
-        # chunks; every step already ends with a host read of its split count.
+        # are integrated window by window: each window's sampled kernel time is paired with the
+        # mean of its first and last counts.  The counts and timing sums are read on the host
+        # between windows; every step already ends with a host read of its split count.
         chunks = []
         c_prev, p_prev = sim.info(), {k: (0.0, 0) for k in KERNEL_UNITS}
         e0.record(stream)
@@ -426,48 +572,61 @@ def run_cem(a):
             done += n
             c_now = sim.info()
             p_now = sim.profile_read()[0]
-            chunks.append(({u: (c_prev[u] + c_now[u]) / 2.0 for u in ("n_active_tets", "n_edges", "n_nodes")},
+            chunks.append(({u: (c_prev[u] + c_now[u]) / 2.0 for u in ("n_active_tets", "n_edges", "n_nodes")}, n,
                            {k: (p_now[k][0] - p_prev[k][0], p_now[k][1] - p_prev[k][1]) for k in KERNEL_UNITS}))
             c_prev, p_prev = c_now, {k: p_now[k] for k in KERNEL_UNITS}
         e1.record(stream)
         torch.cuda.synchronize()
         t_ms = e0.elapsed_time(e1)
+        if clocks:
+            time.sleep(0.25)   # one more sample after the region
         clk = clocks.stop() if clocks else None
+        if clk is not None:
+            clk["window"] = "from before the warm-up steps to 0.25 s after the timed region"
         prof, launches = sim.profile_read()
         sim.profile(0)
         barrier()
         t_ms = max_over_ranks(t_ms, world, "cuda")
         info = sim.info()
         energy = sim.energy()
+        u = sim.field("u") if keep_u else None
+        cracks = {(r[0], r[3]) for r in sim.crack_state()}
         tuning = {k: {"block": v[0], "batch": v[1]} for k, v in sim.tuning().items()}
         sim.close()
-        sm_clock = (clk or {}).get("sm_max_mhz") or peaks.get("sm_max_mhz") or 2070.0
-        fp64_peak = 152 * 4 * sm_clock * 1e6      # 152 SMs x 2 FP64 FMA/clk x 2 FLOP
         # timed launches are a sample (every PROFILE_EVERY-th step): scale sums to the whole region
         n_sampled = max(prof["strain"][1], 1)
         if prof["strain"][1] == 0:
             raise RuntimeError("no sampled step in the timed region")
         scale = steps / n_sampled
-        kernels, roofline = roofline_accounting(chunks, prof, precision, scale, t_ms, hbm, sm_clock)
-        flops, per_launch_s = roofline["algorithmic_flops_per_launch"], roofline["per_launch_us"] * 1e-6
-        if precision == "fp64":
-            roofline.update(fp64_tflops_achieved=flops / per_launch_s / 1e12, fp64_peak_tflops=fp64_peak / 1e12,
-                            fp64_fma_measured_tflops=fp64_peak_meas / 1e12)
-        else:
-            del roofline["algorithmic_flops_per_launch"]
+        kernels, roofline = roofline_accounting(chunks, prof, precision, scale, t_ms, hbm, fp64_peak)
+        roofline["whole_step"]["hbm_peak_source"] = hbm_src
         return dict(t_ms=t_ms, value=replica_throughput(w.n_tets, steps, world, t_ms), roofline=roofline,
-                    kernels=kernels,
-                    clocks=clk, launches=launches, info0=info0, info=info, energy=energy, steps=steps,
-                    tuning=tuning)
+                    kernels=kernels, clocks=clk, launches=launches, info0=info0, info=info, energy=energy,
+                    steps=steps, tuning=tuning, u=u, cracks=cracks)
 
-    main = timed(a.precision, True)
-    other = None
-    if not a.no_compare:
-        other = timed("fp64" if a.precision == "mixed" else "mixed", False)
+    main = timed(a.precision, True, keep_u=a.workload == "block")
+    other_prec = "mixed" if a.precision == "fp64" else "fp64"
 
-    # agreement of the two precisions on a short window (both paths from the same start)
-    agree = None
-    if not a.no_compare and a.workload == "block":
+    def other_leg():
+        o = timed(other_prec, False, keep_u=a.workload == "block")
+        f64, mx = (main, o) if a.precision == "fp64" else (o, main)
+        out = {"value": o["value"], "ms_per_step": o["t_ms"] / a.steps, "roofline": o["roofline"],
+               "kernels": {k: {kk: v[kk] for kk in ("ms", "share", "per_launch_us", "alg_gbs", "moved_gbs")
+                               if kk in v} for k, v in o["kernels"].items()},
+               "gpu_launches": o["launches"],
+               "speedup_mixed_over_fp64": mx["value"] / f64["value"],
+               "after_timed_region": {"steps": a.warmup + a.steps}}
+        if f64["u"] is not None and mx["u"] is not None and f64["u"].shape == mx["u"].shape:
+            out["after_timed_region"]["rel_l2_u_mixed_vs_fp64"] = float(
+                np.linalg.norm(mx["u"] - f64["u"]) / max(np.linalg.norm(f64["u"]), 1e-300))
+        out["after_timed_region"]["split_jaccard"] = (len(f64["cracks"] & mx["cracks"]) /
+                                                      max(len(f64["cracks"] | mx["cracks"]), 1))
+        return out
+
+    other = None if a.no_compare else _leg(other_prec, other_leg)
+
+    # agreement of the two precisions through crack growth (both paths from the same start)
+    def agree_leg():
         n_cmp = 500
         s64 = CEM.from_workload(w, device=dev, split_capacity=a.split_capacity, precision="fp64")
         s32 = CEM.from_workload(w, device=dev, split_capacity=a.split_capacity, precision="mixed")
@@ -477,31 +636,34 @@ def run_cem(a):
         c64 = {(r[0], r[3]) for r in s64.crack_state()}
         c32 = {(r[0], r[3]) for r in s32.crack_state()}
         rel = (float(np.linalg.norm(u32 - u64) / np.linalg.norm(u64)) if u32.shape == u64.shape else None)
-        agree = {"steps": n_cmp, "rel_l2_u_mixed_vs_fp64": rel,
-                 "split_jaccard": len(c64 & c32) / max(len(c64 | c32), 1), "splits_fp64": len(c64)}
         s64.close()
         s32.close()
+        return {"steps": n_cmp, "rel_l2_u_mixed_vs_fp64": rel,
+                "split_jaccard": len(c64 & c32) / max(len(c64 | c32), 1), "splits_fp64": len(c64)}
+
+    agree = _leg("precision_agreement", agree_leg) if (not a.no_compare and a.workload == "block") else None
 
     # the 256-specimen ensemble as one union mesh, mixed against FP64 (default block mode only)
-    ens = None
-    if a.workload == "block" and a.ensemble_steps > 0:
+    def ens_leg():
         we = _workload("ensemble")
         em = timed("mixed", False, w=we, steps=a.ensemble_steps, split_capacity=we.n_tets // 4)
         ef = timed("fp64", False, w=we, steps=a.ensemble_steps, split_capacity=we.n_tets // 4)
-        ens = {"workload": we.name, "instances": we.params["n_instances"], "tets": we.n_tets,
-               "steps": a.ensemble_steps, "warmup": a.warmup,
-               "mixed": {"value": em["value"], "ms_per_step": em["t_ms"] / a.ensemble_steps,
-                         "roofline": {k: em["roofline"][k] for k in ("bound", "kernel", "achieved", "peak", "unit",
-                                                                     "frac")}},
-               "fp64": {"value": ef["value"], "ms_per_step": ef["t_ms"] / a.ensemble_steps},
-               "mixed_speedup_over_fp64": em["value"] / ef["value"],
-               "split_elements_at_end_mixed": em["energy"]["n_split"]}
-        del we
+        return {"workload": we.name, "instances": we.params["n_instances"], "tets": we.n_tets,
+                "steps": a.ensemble_steps, "warmup": a.warmup,
+                "mixed": {"value": em["value"], "ms_per_step": em["t_ms"] / a.ensemble_steps,
+                          "roofline": {k: em["roofline"][k] for k in ("bound", "kernel", "achieved", "peak", "unit",
+                                                                      "frac", "whole_step")}},
+                "fp64": {"value": ef["value"], "ms_per_step": ef["t_ms"] / a.ensemble_steps,
+                         "roofline": {k: ef["roofline"][k] for k in ("bound", "kernel", "achieved", "peak", "unit",
+                                                                     "frac", "whole_step")}},
+                "mixed_speedup_over_fp64": em["value"] / ef["value"],
+                "split_elements_at_end_mixed": em["energy"]["n_split"]}
+
+    ens = _leg("ensemble", ens_leg) if (a.workload == "block" and a.ensemble_steps > 0) else None
 
     # gradients: FP32 forward + adjoint with sqrt(N) checkpoints on the 102,000-element block,
     # J = final strain energy + mean top-face y displacement, topology frozen after the notch
-    adj = None
-    if a.workload == "block" and a.adjoint_steps > 0:
+    def adj_leg():
         from cem_inputs import adjoint_block, top_face_weights
         wa = adjoint_block()
         res = {}
@@ -516,22 +678,22 @@ def run_cem(a):
             sa.close()
         tm, Jm, dEm, dam = res["mixed"]
         tf, Jf, dEf, daf = res["fp64"]
-        adj = {"workload": wa.name, "tets": wa.n_tets, "steps": a.adjoint_steps,
-               "checkpoint_every": int(np.ceil(np.sqrt(a.adjoint_steps))),
-               "mixed": {"seconds": tm, "tet_steps_per_s": wa.n_tets * a.adjoint_steps / tm},
-               "fp64": {"seconds": tf, "tet_steps_per_s": wa.n_tets * a.adjoint_steps / tf},
-               "rel_err_J_mixed": abs(Jm - Jf) / abs(Jf),
-               "rel_err_dJdE_mixed": float(np.abs(dEm - dEf).max() / np.abs(dEf).max()),
-               "rel_err_dJdalpha_mixed": abs(dam - daf) / abs(daf),
-               "note": "wall time of one cem_adjoint call: forward, segment recompute and reverse sweep"}
-        del wa
+        return {"workload": wa.name, "tets": wa.n_tets, "steps": a.adjoint_steps,
+                "checkpoint_every": int(np.ceil(np.sqrt(a.adjoint_steps))),
+                "mixed": {"seconds": tm, "tet_steps_per_s": wa.n_tets * a.adjoint_steps / tm},
+                "fp64": {"seconds": tf, "tet_steps_per_s": wa.n_tets * a.adjoint_steps / tf},
+                "rel_err_J_mixed": abs(Jm - Jf) / abs(Jf),
+                "rel_err_dJdE_mixed": float(np.abs(dEm - dEf).max() / np.abs(dEf).max()),
+                "rel_err_dJdalpha_mixed": abs(dam - daf) / abs(daf),
+                "note": "wall time of one cem_adjoint call: forward, segment recompute and reverse sweep"}
+
+    adj = _leg("adjoint", adj_leg) if (a.workload == "block" and a.adjoint_steps > 0) else None
 
     # the ES-H-FEM step on the same block as 160,000 trilinear hexahedra (fixed topology)
-    hexres = None
-    if a.workload == "block" and a.hex_steps > 0:
+    def hex_leg():
         from cem_inputs import hex_block
         wh = hex_block(200, 80, 10, 0.1, 0.04, 0.01, traction=1e6, name="hex_block_200x80x10")
-        hexres = {"workload": wh.name, "elements": wh.n_elems, "steps": a.hex_steps, "warmup": a.warmup}
+        out = {"workload": wh.name, "elements": wh.n_elems, "steps": a.hex_steps, "warmup": a.warmup}
         for prec in ("mixed", "fp64"):
             sh = CEM.from_hex_workload(wh, device=dev, precision=prec)
             sh.step(a.warmup)
@@ -544,20 +706,20 @@ def run_cem(a):
             torch.cuda.synchronize()
             t_ms = e0.elapsed_time(e1)
             prof, _ = sh.profile_read()
-            hexres[prec] = {"value": wh.n_elems * a.hex_steps / (t_ms * 1e-3), "unit": "hex-steps/s",
-                            "ms_per_step": t_ms / a.hex_steps,
-                            "per_launch_us": {k: 1e3 * v[0] / v[1] for k, v in prof.items() if v[1]}}
+            out[prec] = {"value": wh.n_elems * a.hex_steps / (t_ms * 1e-3), "unit": "hex-steps/s",
+                         "ms_per_step": t_ms / a.hex_steps,
+                         "per_launch_us": {k: 1e3 * v[0] / v[1] for k, v in prof.items() if v[1]}}
             sh.close()
-        del wh
+        return out
+
+    hexres = _leg("hexahedra", hex_leg) if (a.workload == "block" and a.hex_steps > 0) else None
 
     # end to end through the public API with host buffers: create + material + K steps + read back
     barrier()
     t0 = time.perf_counter()
     sim2 = CEM.from_workload(w, device=dev, split_capacity=a.split_capacity, precision=a.precision)
     _reorder(sim2, a)
-    if not a.no_autotune:
-        sim2.autotune(reps=10, automatic=True)
-    sim2.step(a.steps)
+    sim2.step(a.steps)   # default launch variants: the autotuner is not part of a plain run
     u = sim2.field("u")
     sim2.energy()
     torch.cuda.synchronize()
@@ -572,37 +734,36 @@ def run_cem(a):
         return
     cpu = None
     if world == 1 and not a.no_cpu_baseline and a.workload == "block":
-        try:
-            cpu = _cpu_baseline(a.cpu_steps)
-        except Exception as ex:  # reported, not hidden
-            cpu = {"value": None, "unit": METRIC, "cores": 1, "kind": "oracle", "sample": "failed: %r" % (ex,)}
+        cpu = _leg("cpu_baseline", lambda: _cpu_baseline(a.cpu_steps))
     info0, info, energy = main["info0"], main["info"], main["energy"]
+    dt = info0["dt"]
     line = {
         "metric": METRIC, "value": main["value"], "unit": METRIC, "n_gpus": world, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": main["t_ms"] / a.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32/f64 mixed" if a.precision == "mixed" else "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "tets": w.n_tets, "nodes": w.n_nodes, "edges": info0["n_edges"],
-                   "precision": a.precision, "split": True,
+        "vs_baseline": None, "dtype": "f64" if a.precision == "fp64" else "f32/f64 mixed", "data": "synthetic",
+        "config": {"workload": WORKLOAD if a.workload == "block" else w.name, "tets": w.n_tets, "nodes": w.n_nodes,
+                   "edges": info0["n_edges"], "precision": a.precision, "split": True,
                    "parallelism": "replicas" if world > 1 else "single",
-                   "l2": "working set %.2f GB > 129 MB L2 (no flush needed)" % (info["device_bytes"] / 1e9),
+                   "l2": "inputs larger than L2: working set %.2f GB > 129 MB L2 (no flush)"
+                         % (info["device_bytes"] / 1e9),
+                   "dt_s": dt, "simulated_time_s": {"timed_region": a.steps * dt,
+                                                    "end_of_timed_region": (a.warmup + a.steps) * dt},
                    "split_elements_at_end": energy["n_split"], "elements_at_end": info["n_active_tets"],
                    "steps_before_timing": a.warmup},
         "roofline": main["roofline"],
+        "active_element_steps_per_s": main["roofline"]["whole_step"]["active_element_steps_per_s"],
         "kernels": main["kernels"],
         "clocks": main["clocks"],
         "e2e": {"value": replica_throughput(w.n_tets, a.steps, world, t_e2e * 1e3), "unit": METRIC,
                 "h2d_bytes_per_step": h2d / a.steps, "d2h_bytes_per_step": d2h / a.steps,
-                "includes": "mesh upload and topology build, material, K steps, u and energy read-back"},
+                "includes": "mesh upload from host arrays and topology build, material and a_0, K steps "
+                            "(default launch variants), u and energy read-back"},
         "gpu_launches": main["launches"],
         "cpu_baseline": cpu,
         "launch_variants": main["tuning"] if not a.no_autotune else "defaults (autotuner off)",
     }
     if other is not None:
-        line["fp64" if a.precision == "mixed" else "mixed"] = {
-            "value": other["value"], "ms_per_step": other["t_ms"] / a.steps, "roofline": other["roofline"],
-            "kernels": {k: {kk: v[kk] for kk in ("ms", "share", "per_launch_us") if kk in v}
-                        for k, v in other["kernels"].items()},
-            "gpu_launches": other["launches"], "speedup_of_main": main["value"] / other["value"]}
+        line[other_prec] = other
     if agree is not None:
         line["precision_agreement"] = agree
     if ens is not None:
@@ -612,7 +773,6 @@ def run_cem(a):
     if hexres is not None:
         line["hexahedra"] = hexres
     if a.workload == "ensemble":
-        line["config"]["workload"] = w.name
         line["config"]["instances"] = w.params["n_instances"]
         line["config"]["split_capacity"] = a.split_capacity
     print(json.dumps(line), flush=True)
@@ -625,6 +785,9 @@ def main():
     if a.cpu_baseline_worker:
         v, s, t = _oracle_rate(a.cpu_steps)
         print(json.dumps({"value": v, "steps": s, "seconds": t}))
+        return
+    if a.cpu_allcore_worker:
+        _allcore_worker(a.cpu_steps)
         return
     if a.impl == "reference":
         run_reference(a)
