@@ -189,6 +189,11 @@ __device__ __forceinline__ void node_disp_diff<float>(const double*, const float
         for (int c = 0; c < 3; ++c) d[a][c] = (hi[a + 1][c] - hi[0][c]) + (lo[a + 1][c] - lo[0][c]);
 }
 
+// Explicitly rounded FMA: the same operations in every launch variant, whatever the compiler
+// would contract.
+__device__ __forceinline__ float fma_r(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_r(double a, double b, double c) { return __fma_rn(a, b, c); }
+
 // Inactive (split) element slots are skipped: no fan or incidence list refers to them.
 // TB (threads per block) is a tuning parameter (see cem_tune.cu).
 template <class R, int TB>
@@ -205,12 +210,19 @@ __global__ void __launch_bounds__(TB) k_strain(const double* __restrict__ u, con
     R g[3][3];
 #pragma unroll
     for (int q = 0; q < 9; ++q) g[q / 3][q % 3] = Vg[q * Tc + j];
-    R F[3][3];   // F[c][e] = sum_a d[a][c] * g[a][e]  (V * du_c/dx_e)
-#pragma unroll
-    for (int c = 0; c < 3; ++c)
-#pragma unroll
-        for (int e = 0; e < 3; ++e) F[c][e] = d[0][c] * g[0][e] + d[1][c] * g[1][e] + d[2][c] * g[2][e];
-    const R out[6] = {F[0][0], F[1][1], F[2][2], F[0][1] + F[1][0], F[1][2] + F[2][1], F[0][2] + F[2][0]};
+    // V * (du_c/dx_c) and V * (du_c/dx_e + du_e/dx_c) = sum_a (d[a][c] g[a][e] + d[a][e] g[a][c]):
+    // each engineering shear strain is one chain of six products (a multiply and five FMAs)
+    // rather than two chains of three and an add
+    auto diag = [&](int c) { return fma_r(d[2][c], g[2][c], fma_r(d[1][c], g[1][c], d[0][c] * g[0][c])); };
+    auto shear = [&](int c, int e) {
+        R x = d[0][c] * g[0][e];
+        x = fma_r(d[0][e], g[0][c], x);
+        x = fma_r(d[1][c], g[1][e], x);
+        x = fma_r(d[1][e], g[1][c], x);
+        x = fma_r(d[2][c], g[2][e], x);
+        return fma_r(d[2][e], g[2][c], x);
+    };
+    const R out[6] = {diag(0), diag(1), diag(2), shear(0, 1), shear(1, 2), shear(0, 2)};
     Rec<R>::store6(h + Rec<R>::S6 * j, out);
 }
 
@@ -218,8 +230,6 @@ __global__ void __launch_bounds__(TB) k_strain(const double* __restrict__ u, con
 // all indices, then all records, so several records are in flight per thread.
 // Sums keep the list's ascending order whatever the batch, so every variant
 // gives bit-identical results; the autotuner picks the fastest.
-__device__ __forceinline__ float fma_r(float a, float b, float c) { return __fmaf_rn(a, b, c); }
-__device__ __forceinline__ double fma_r(double a, double b, double c) { return __fma_rn(a, b, c); }
 
 // Smoothed stress of edge k from H = sum over its fan of the element strain
 // records (Eqs. 5-6 with the fan-averaged elasticity folded into cl, cm):
@@ -234,21 +244,12 @@ __device__ __forceinline__ void edge_sigma(int64_t k, const R H[6], const R* __r
     Rec<R>::store6(sig + Rec<R>::S6 * k, s);
 }
 
-template <class R, int TB, int FB>
-__global__ void __launch_bounds__(TB) k_edge_stress(const R* __restrict__ h, const int* __restrict__ fan_off,
-                                                    const int* __restrict__ fan_cnt, const int* __restrict__ fan_pool,
-                                                    const R* __restrict__ cl, const R* __restrict__ cm, int64_t E,
-                                                    R* __restrict__ sig) {
-    CEM_PDL_ENTRY();
-    int64_t k = (int64_t)blockIdx.x * TB + threadIdx.x;
-    if (k >= E) return;
-    const int off = fan_off[k], cnt = fan_cnt[k];
-    // An edge whose fan emptied (every element around it split) is read by no
-    // active element: its stress is left as it was (finite; its energy term has H = 0).
-    if (cnt == 0) return;
-    // FB fan entries per round, then their FB records: a round costs two dependent
-    // loads whatever the fan size; sums stay in fan order (every FB gives the same bits)
-    R H[6] = {0, 0, 0, 0, 0, 0};
+// Sum of the fan's strain records of one edge, in fan order, starting from the first
+// record (cnt >= 1).  FB fan entries per round, then their FB records: a round costs two
+// dependent loads whatever the fan size; every FB gives the same bits.
+template <class R, int FB>
+__device__ __forceinline__ void fan_sum(const R* __restrict__ h, const int* __restrict__ fan_pool, int off, int cnt,
+                                        R H[6]) {
     for (int i = 0; i < cnt; i += FB) {
         int jj[FB];
 #pragma unroll
@@ -258,11 +259,75 @@ __global__ void __launch_bounds__(TB) k_edge_stress(const R* __restrict__ h, con
         for (int b = 0; b < FB; ++b)
             if (jj[b] >= 0) Rec<R>::load6(h + Rec<R>::S6 * (int64_t)jj[b], x[b]);
 #pragma unroll
-        for (int b = 0; b < FB; ++b)
-            if (jj[b] >= 0)
+        for (int b = 0; b < FB; ++b) {
+            if (i == 0 && b == 0) {
+#pragma unroll
+                for (int q = 0; q < 6; ++q) H[q] = x[0][q];
+            } else if (jj[b] >= 0) {
 #pragma unroll
                 for (int q = 0; q < 6; ++q) H[q] += x[b][q];
+            }
+        }
     }
+}
+
+// SORT: the block's edges are handed to its threads in order of fan size (a counting
+// sort in shared memory), so the 32 edges of a warp have nearly equal fans.  A warp
+// runs as many rounds as its longest fan needs, and on GB300 an FP64 warp instruction
+// takes the FP64 pipe for the same time whatever the number of active lanes; edges of
+// different fan sizes alternate in edge order (axis edges, face and body diagonals of
+// each node), so without the sort about a fifth of the FP64 issue is spent on idle lanes.
+// Each edge's sum is the same whichever thread takes it.
+constexpr int FAN_KEYS = 32;   // fans longer than 31 share the last key
+
+template <class R, int TB, int FB, bool SORT>
+__global__ void __launch_bounds__(TB) k_edge_stress(const R* __restrict__ h, const int* __restrict__ fan_off,
+                                                    const int* __restrict__ fan_cnt, const int* __restrict__ fan_pool,
+                                                    const R* __restrict__ cl, const R* __restrict__ cm, int64_t E,
+                                                    R* __restrict__ sig) {
+    CEM_PDL_ENTRY();
+    const int64_t k0 = (int64_t)blockIdx.x * TB;
+    int64_t k = k0 + threadIdx.x;
+    int off = 0, cnt = 0;
+    if (k < E) {
+        off = fan_off[k];
+        cnt = fan_cnt[k];
+    }
+    if constexpr (SORT) {
+        __shared__ int s_hist[FAN_KEYS], s_base[FAN_KEYS];
+        __shared__ int s_off[TB], s_cnt[TB];
+        __shared__ short s_slot[TB];
+        if (threadIdx.x < FAN_KEYS) s_hist[threadIdx.x] = 0;
+        __syncthreads();
+        const int key = cnt < FAN_KEYS - 1 ? cnt : FAN_KEYS - 1;
+        const int rank = atomicAdd(&s_hist[key], 1);
+        __syncthreads();
+        if (threadIdx.x < 32) {   // exclusive prefix of the key counts, by one warp
+            const int v = s_hist[threadIdx.x];
+            int incl = v;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                if ((int)threadIdx.x >= o) incl += y;
+            }
+            s_base[threadIdx.x] = incl - v;
+        }
+        __syncthreads();
+        const int pos = s_base[key] + rank;
+        s_off[pos] = off;
+        s_cnt[pos] = cnt;
+        s_slot[pos] = (short)threadIdx.x;
+        __syncthreads();
+        off = s_off[threadIdx.x];
+        cnt = s_cnt[threadIdx.x];
+        k = k0 + s_slot[threadIdx.x];
+    }
+    // An edge whose fan emptied (every element around it split), or a slot past the
+    // last edge, is read by no active element: its stress is left as it was (finite;
+    // its energy term has H = 0).
+    if (k >= E || cnt == 0) return;
+    R H[6];
+    fan_sum<R, FB>(h, fan_pool, off, cnt, H);
     edge_sigma(k, H, cl, cm, sig);
 }
 
@@ -274,32 +339,32 @@ __global__ void __launch_bounds__(TB) k_force(const R* __restrict__ sig, const i
     CEM_PDL_ENTRY();
     int64_t j = (int64_t)blockIdx.x * TB + threadIdx.x;
     if (j >= T || !active[j]) return;
-    R S[6] = {0, 0, 0, 0, 0, 0};
     int kk[6];
 #pragma unroll
     for (int l = 0; l < 6; ++l) kk[l] = t2e[l * Tc + j];
     R x[6][6];
 #pragma unroll
     for (int l = 0; l < 6; ++l) Rec<R>::load6(sig + Rec<R>::S6 * (int64_t)kk[l], x[l]);
+    // the sum of the six edge stresses, in local edge order, starting from the first
+    // (FP64 issue is the scarce resource here: no add of a zero, no separate negation)
+    R S[6];
 #pragma unroll
-    for (int l = 0; l < 6; ++l)
+    for (int q = 0; q < 6; ++q) S[q] = x[0][q];
+#pragma unroll
+    for (int l = 1; l < 6; ++l)
 #pragma unroll
         for (int q = 0; q < 6; ++q) S[q] += x[l][q];
     R f[4][3];
-    f[0][0] = f[0][1] = f[0][2] = 0;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         const R gx = Vg[(3 * a) * Tc + j], gy = Vg[(3 * a + 1) * Tc + j], gz = Vg[(3 * a + 2) * Tc + j];
-        f[a + 1][0] = S[0] * gx + S[3] * gy + S[5] * gz;
-        f[a + 1][1] = S[3] * gx + S[1] * gy + S[4] * gz;
-        f[a + 1][2] = S[5] * gx + S[4] * gy + S[2] * gz;
-        f[0][0] += f[a + 1][0];
-        f[0][1] += f[a + 1][1];
-        f[0][2] += f[a + 1][2];
+        f[a + 1][0] = fma_r(S[5], gz, fma_r(S[3], gy, S[0] * gx));
+        f[a + 1][1] = fma_r(S[4], gz, fma_r(S[1], gy, S[3] * gx));
+        f[a + 1][2] = fma_r(S[2], gz, fma_r(S[4], gy, S[5] * gx));
     }
-    f[0][0] = -f[0][0];
-    f[0][1] = -f[0][1];
-    f[0][2] = -f[0][2];
+    // grad N_0 = -(grad N_1 + grad N_2 + grad N_3): f_0 = -f_1 - f_2 - f_3
+#pragma unroll
+    for (int c = 0; c < 3; ++c) f[0][c] = (-f[1][c] - f[2][c]) - f[3][c];
     R* o = fp + Rec<R>::SF * j;
     if constexpr (sizeof(R) == 8) {
         double2* p = reinterpret_cast<double2*>(o);
@@ -778,25 +843,29 @@ void launch_strain(cem_ctx* c, int v, const double* u, const float* uhl, const R
     }
 }
 
-template <class R, int TB, int FB>
+template <class R, int TB, int FB, bool SORT>
 void go_edge(cem_ctx* c, const R* h, const R* cl, const R* cm, R* sig) {
-    cem_pdl(c->stream, k_edge_stress<R, TB, FB>, cem_grid(c->E, TB), TB, h, c->fan_off, c->fan_cnt, c->fan_pool, cl, cm,
-            c->E, sig);
+    cem_pdl(c->stream, k_edge_stress<R, TB, FB, SORT>, cem_grid(c->E, TB), TB, h, c->fan_off, c->fan_cnt, c->fan_pool,
+            cl, cm, c->E, sig);
 }
-template <class R, int FB>
+template <class R, int FB, bool SORT>
 void go_edge_tb(cem_ctx* c, int v, const R* h, const R* cl, const R* cm, R* sig) {
     switch (v % 3) {
-        case 0: go_edge<R, 128, FB>(c, h, cl, cm, sig); break;
-        case 1: go_edge<R, 256, FB>(c, h, cl, cm, sig); break;
-        default: go_edge<R, 512, FB>(c, h, cl, cm, sig);
+        case 0: go_edge<R, 128, FB, SORT>(c, h, cl, cm, sig); break;
+        case 1: go_edge<R, 256, FB, SORT>(c, h, cl, cm, sig); break;
+        default: go_edge<R, 512, FB, SORT>(c, h, cl, cm, sig);
     }
 }
+// v / 3: fan rounds of 2, 4, 8 in edge order (0-2) or with the block's edges sorted by fan size (3-5)
 template <class R>
 void launch_edge(cem_ctx* c, int v, const R* h, const R* cl, const R* cm, R* sig) {
     switch (v / 3) {
-        case 0: go_edge_tb<R, 2>(c, v, h, cl, cm, sig); break;
-        case 1: go_edge_tb<R, 4>(c, v, h, cl, cm, sig); break;
-        default: go_edge_tb<R, 8>(c, v, h, cl, cm, sig);
+        case 0: go_edge_tb<R, 2, false>(c, v, h, cl, cm, sig); break;
+        case 1: go_edge_tb<R, 4, false>(c, v, h, cl, cm, sig); break;
+        case 2: go_edge_tb<R, 8, false>(c, v, h, cl, cm, sig); break;
+        case 3: go_edge_tb<R, 2, true>(c, v, h, cl, cm, sig); break;
+        case 4: go_edge_tb<R, 4, true>(c, v, h, cl, cm, sig); break;
+        default: go_edge_tb<R, 8, true>(c, v, h, cl, cm, sig);
     }
 }
 
@@ -1174,19 +1243,25 @@ int cem_launch_node_update(cem_ctx* c, int first) {
 // block and the kernel's batch parameter BATCH[kernel][v / 3]
 namespace {
 // (the node update's fourth batch value selects the warp-balanced kernel)
-constexpr int TUNE_BATCH[TUNE_COUNT][4] = {{1, 1, 1, 1}, {2, 4, 8, 8}, {1, 1, 1, 1}, {2, 4, 8, NODE_ROUND}};
+// batch of variant v / 3; for the edge stress, 100 + rounds marks the fan-sorted form
+constexpr int TUNE_BATCH[TUNE_COUNT][6] = {{1, 1, 1, 1, 1, 1},
+                                           {2, 4, 8, 102, 104, 108},
+                                           {1, 1, 1, 1, 1, 1},
+                                           {2, 4, 8, NODE_ROUND, NODE_ROUND, NODE_ROUND}};
 }  // namespace
 
-int cem_tune_variants(int k) { return k == TUNE_NODE ? 12 : k == TUNE_EDGE ? 9 : 3; }
+int cem_tune_variants(int k) { return k == TUNE_NODE ? 12 : k == TUNE_EDGE ? 18 : 3; }
 
 void cem_tune_describe(int k, int v, int* block, int* batch) {
     *block = 128 << (v % 3);
     *batch = TUNE_BATCH[k][v / 3];
 }
 
-// The variants used before any tuning: 256 threads, fan rounds of 2, node batches of 8 (FP32) or 4 (FP64).
+// The variants used before any tuning: 256 threads, fan rounds of 2 over fan-sorted edges,
+// node batches of 8 (FP32) or 4 (FP64).
 int cem_tune_default(int k, int precision) {
     if (k == TUNE_NODE) return 1 + 3 * (precision == CEM_MIXED ? 2 : 1);
+    if (k == TUNE_EDGE) return 1 + 3 * 3;
     return 1;
 }
 
