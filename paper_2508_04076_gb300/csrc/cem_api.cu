@@ -12,10 +12,12 @@
 #include <nvtx3/nvToolsExt.h>   // header-only; ranges cost nothing unless a profiler is attached
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <numeric>
 #include <string>
+#include <thread>
 #include <vector>
 
 static thread_local std::string g_create_error;
@@ -73,6 +75,24 @@ int64_t next_pow2(int64_t x) {
     return p;
 }
 
+// f(begin, end) over [0, n) split into contiguous chunks on the host's cores.  Every
+// caller writes disjoint output slots, so the result does not depend on the split.
+template <class F>
+void parallel_for(int64_t n, F f) {
+    const int64_t nt = std::max<int64_t>(1, std::min<int64_t>(std::thread::hardware_concurrency(), 64));
+    if (n < 16384 || nt == 1) {
+        f((int64_t)0, n);
+        return;
+    }
+    const int64_t chunk = (n + nt - 1) / nt;
+    std::vector<std::thread> th;
+    for (int64_t k = 0; k < nt; ++k) {
+        const int64_t a = k * chunk, b = std::min(n, a + chunk);
+        if (a < b) th.emplace_back(f, a, b);
+    }
+    for (auto& t : th) t.join();
+}
+
 struct HostTopo {
     std::vector<int> inc_off, inc;          // node -> element*4+local, ascending
     std::vector<int> e_off, e_nbr;          // node i -> sorted neighbours j > i (edge ids e_off[i] + r)
@@ -93,12 +113,9 @@ int build_topology(cem_ctx* c, const std::vector<int>& conn, HostTopo& H) {
         for (int64_t t = 0; t < T; ++t)
             for (int l = 0; l < 4; ++l) H.inc[cur[conn[t * 4 + l]]++] = (int)(t * 4 + l);
     }
-    // edges: for each node the sorted distinct neighbours with larger id
-    H.e_off.assign(N + 1, 0);
-    H.e_nbr.clear();
-    H.e_nbr.reserve(T * 2);
-    std::vector<int> buf;
-    for (int64_t i = 0; i < N; ++i) {
+    // edges: for each node the sorted distinct neighbours with larger id (counted, then
+    // written, node by node on all host cores)
+    auto neighbours = [&](int64_t i, std::vector<int>& buf) {
         buf.clear();
         for (int q = H.inc_off[i]; q < H.inc_off[i + 1]; ++q) {
             const int t = H.inc[q] >> 2;
@@ -109,21 +126,38 @@ int build_topology(cem_ctx* c, const std::vector<int>& conn, HostTopo& H) {
         }
         std::sort(buf.begin(), buf.end());
         buf.erase(std::unique(buf.begin(), buf.end()), buf.end());
-        H.e_nbr.insert(H.e_nbr.end(), buf.begin(), buf.end());
-        H.e_off[i + 1] = (int)H.e_nbr.size();
-    }
+    };
+    H.e_off.assign(N + 1, 0);
+    parallel_for(N, [&](int64_t a, int64_t b) {
+        std::vector<int> buf;
+        for (int64_t i = a; i < b; ++i) {
+            neighbours(i, buf);
+            H.e_off[i + 1] = (int)buf.size();
+        }
+    });
+    for (int64_t i = 0; i < N; ++i) H.e_off[i + 1] += H.e_off[i];
+    H.e_nbr.assign(H.e_off[N], 0);
+    parallel_for(N, [&](int64_t a, int64_t b) {
+        std::vector<int> buf;
+        for (int64_t i = a; i < b; ++i) {
+            neighbours(i, buf);
+            std::copy(buf.begin(), buf.end(), H.e_nbr.begin() + H.e_off[i]);
+        }
+    });
     c->E0 = (int64_t)H.e_nbr.size();
     c->max_inc0 = 0;
     for (int64_t i = 0; i < N; ++i) c->max_inc0 = std::max<int64_t>(c->max_inc0, H.inc_off[i + 1] - H.inc_off[i]);
     H.t2e.assign(6 * T, 0);
-    for (int64_t t = 0; t < T; ++t)
-        for (int l = 0; l < 6; ++l) {
-            int x = conn[t * 4 + LE[l][0]], y = conn[t * 4 + LE[l][1]];
-            if (x > y) std::swap(x, y);
-            auto b = H.e_nbr.begin() + H.e_off[x], e = H.e_nbr.begin() + H.e_off[x + 1];
-            auto it = std::lower_bound(b, e, y);
-            H.t2e[l * T + t] = H.e_off[x] + (int)(it - b);
-        }
+    parallel_for(T, [&](int64_t a, int64_t b) {
+        for (int64_t t = a; t < b; ++t)
+            for (int l = 0; l < 6; ++l) {
+                int x = conn[t * 4 + LE[l][0]], y = conn[t * 4 + LE[l][1]];
+                if (x > y) std::swap(x, y);
+                auto lo = H.e_nbr.begin() + H.e_off[x], hi = H.e_nbr.begin() + H.e_off[x + 1];
+                auto it = std::lower_bound(lo, hi, y);
+                H.t2e[l * T + t] = H.e_off[x] + (int)(it - lo);
+            }
+    });
     // fans: elements of each edge in ascending element order
     H.fan_off.assign(c->E0 + 1, 0);
     for (int64_t t = 0; t < T; ++t)
@@ -139,28 +173,33 @@ int build_topology(cem_ctx* c, const std::vector<int>& conn, HostTopo& H) {
     }
     // face adjacency (local face f is opposite local node f)
     H.face_nbr.assign(4 * T, -1);
-    for (int64_t t = 0; t < T; ++t)
-        for (int f = 0; f < 4; ++f) {
-            int fn[3], k = 0;
-            for (int l = 0; l < 4; ++l)
-                if (l != f) fn[k++] = conn[t * 4 + l];
-            int found = -1, nfound = 0;
-            for (int q = H.inc_off[fn[0]]; q < H.inc_off[fn[0] + 1]; ++q) {
-                const int s = H.inc[q] >> 2;
-                if (s == t) continue;
-                int hits = 0;
-                for (int l = 0; l < 4; ++l) {
-                    const int x = conn[(int64_t)s * 4 + l];
-                    hits += (x == fn[1]) + (x == fn[2]);
+    std::atomic<bool> non_manifold{false};
+    parallel_for(T, [&](int64_t a, int64_t b) {
+        for (int64_t t = a; t < b; ++t)
+            for (int f = 0; f < 4; ++f) {
+                int fn[3], k = 0;
+                for (int l = 0; l < 4; ++l)
+                    if (l != f) fn[k++] = conn[t * 4 + l];
+                int found = -1, nfound = 0;
+                for (int q = H.inc_off[fn[0]]; q < H.inc_off[fn[0] + 1]; ++q) {
+                    const int s = H.inc[q] >> 2;
+                    if (s == t) continue;
+                    int hits = 0;
+                    for (int l = 0; l < 4; ++l) {
+                        const int x = conn[(int64_t)s * 4 + l];
+                        hits += (x == fn[1]) + (x == fn[2]);
+                    }
+                    if (hits == 2) {
+                        found = s;
+                        ++nfound;
+                    }
                 }
-                if (hits == 2) {
-                    found = s;
-                    ++nfound;
-                }
+                if (nfound > 1) non_manifold.store(true);
+                H.face_nbr[f * T + t] = found;
             }
-            if (nfound > 1) return cem_fail(c, CEM_EINVAL, "non-manifold mesh: a face is shared by more than two elements");
-            H.face_nbr[f * T + t] = found;
-        }
+    });
+    if (non_manifold.load())
+        return cem_fail(c, CEM_EINVAL, "non-manifold mesh: a face is shared by more than two elements");
     return CEM_OK;
 }
 
@@ -805,21 +844,56 @@ struct NvtxRange {
     ~NvtxRange() { nvtxRangePop(); }
 };
 
+// The front evaluation (Eqs. 16-18) on the side stream, forked from the context's
+// stream after the edge stresses: it reads u, the edge stresses and the crack
+// topology, none of which the force and node-update kernels of an FP64 step
+// write (the FP64 node update writes v and a; u changes only in the next
+// predictor), so it runs beside them and joins before the split decision is read.
+int launch_front_side(cem_ctx* c) {
+    if (!c->side_stream) {
+        CEM_CK(c, cudaStreamCreateWithFlags(&c->side_stream, cudaStreamNonBlocking));
+        CEM_CK(c, cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
+        CEM_CK(c, cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
+    }
+    CEM_CK(c, cudaEventRecord(c->ev_fork, c->stream));
+    CEM_CK(c, cudaStreamWaitEvent(c->side_stream, c->ev_fork, 0));
+    cudaStream_t main = c->stream;
+    c->stream = c->side_stream;   // the front's launches and its timing events go to the side stream
+    cudaEvent_t ev = prof_begin(c);
+    int rc;
+    {
+        NvtxRange front("cem.front_G");
+        rc = cem_launch_front_G(c);
+    }
+    prof_end(c, CEM_KERNEL_FRONT_G, ev);
+    c->stream = main;
+    if (rc) return rc;
+    CEM_CK(c, cudaEventRecord(c->ev_join, c->side_stream));
+    return CEM_OK;
+}
+
 int run_step(cem_ctx* c) {
     NvtxRange range("cem.step");
     if (c->tune_auto)
         if (int rc = cem_tune_maybe(c)) return rc;
     c->prof_now = c->prof && (c->step % c->prof_every == 0);
+    // mixed precision: the node update advances u, so the front evaluation follows it
+    const bool fronts = c->split_enabled && c->n_cand > 0;
+    const bool beside = fronts && c->precision != CEM_MIXED;
     if (c->precision != CEM_MIXED)   // mixed precision: the node update carries the predictor
         TIMED(c, CEM_KERNEL_PREDICT, cem_launch_predict(c));
     TIMED(c, CEM_KERNEL_STRAIN, cem_launch_strain(c));
     TIMED(c, CEM_KERNEL_EDGE_STRESS, cem_launch_edge_stress(c));
+    if (beside)
+        if (int rc = launch_front_side(c)) return rc;
     TIMED(c, CEM_KERNEL_FORCE, cem_launch_force(c));
     TIMED(c, CEM_KERNEL_NODE_UPDATE, cem_launch_node_update(c, 0));
     if (int rc = cem_launch_prescribe(c, c->step + 1)) return rc;
     c->step += 1;
-    if (c->split_enabled && c->n_cand > 0) {
-        {
+    if (fronts) {
+        if (beside) {
+            CEM_CK(c, cudaStreamWaitEvent(c->stream, c->ev_join, 0));
+        } else {
             NvtxRange front("cem.front_G");
             TIMED(c, CEM_KERNEL_FRONT_G, cem_launch_front_G(c));
         }
@@ -921,6 +995,67 @@ int cem_step(cem_ctx* c, int64_t n) {
     if (int rc = sync_counts(c)) return rc;
     if (c->hcount[CNT_SCRATCH1]) return cem_fail(c, CEM_ENONFINITE, "non-finite displacement");
     return prof_resolve(c);
+}
+
+// n steps of a context whose topology cannot change over them (splitting off, or
+// no crack-front element), launched as one CUDA graph.  The graph is captured
+// on a private stream the first time (or when the sizes, the launch variants or
+// n change) and replayed on the context's stream afterwards; the kernels and
+// their arguments are those cem_step launches, so the results are bit-identical.
+int cem_step_graph(cem_ctx* c, int64_t n) {
+    if (!c || n < 0) return CEM_EINVAL;
+    if (!c->material) return cem_fail(c, CEM_ESTATE, "cem_set_material must be called before cem_step_graph");
+    if (c->split_enabled && c->n_cand > 0)
+        return cem_fail(c, CEM_ESTATE, "crack-front elements need a host decision every step: use cem_step");
+    if (c->n_dir > 0)
+        return cem_fail(c, CEM_ESTATE, "prescribed velocities depend on the step number: use cem_step");
+    if (c->prof) return cem_fail(c, CEM_ESTATE, "kernel timing is on (cem_profile): use cem_step");
+    if (int rc = select_device(c)) return rc;
+    if (n == 0) return CEM_OK;
+    if (c->tune_auto)   // settle the launch variants for the current sizes before capturing them
+        if (int rc = cem_tune_maybe(c)) return rc;
+    const int64_t key[8] = {n, c->T, c->E, c->N, c->tune[0], c->tune[1], c->tune[2], c->tune[3]};
+    if (!c->graph_exec || !std::equal(key, key + 8, c->graph_key)) {
+        if (c->graph_exec) {
+            CEM_CK(c, cudaGraphExecDestroy(c->graph_exec));
+            c->graph_exec = nullptr;
+        }
+        if (!c->cap_stream) CEM_CK(c, cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+        CEM_CK(c, cudaStreamSynchronize(c->stream));   // the state the graph starts from is in place
+        const cudaStream_t main = c->stream;
+        const int64_t step0 = c->step, launch0 = c->n_launch;
+        c->stream = c->cap_stream;
+        int rc = CEM_OK;
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            for (int64_t q = 0; q < n && rc == CEM_OK; ++q) rc = run_step(c);
+            e = cudaStreamEndCapture(c->cap_stream, &g);
+        }
+        c->stream = main;
+        c->step = step0;   // capture launched nothing: the steps run at replay
+        c->n_graph_launch = c->n_launch - launch0;
+        c->n_launch = launch0;
+        if (rc) {
+            if (g) cudaGraphDestroy(g);
+            return rc;
+        }
+        if (e != cudaSuccess) return cem_cuda_fail(c, e, "stream capture of the step graph");
+        e = cudaGraphInstantiate(&c->graph_exec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            c->graph_exec = nullptr;
+            return cem_cuda_fail(c, e, "cudaGraphInstantiate");
+        }
+        std::copy(key, key + 8, c->graph_key);
+    }
+    CEM_CK(c, cudaGraphLaunch(c->graph_exec, c->stream));
+    c->step += n;
+    cem_launched(c, (int)c->n_graph_launch);
+    if (int rc = cem_launch_check_finite(c)) return rc;
+    if (int rc = sync_counts(c)) return rc;
+    if (c->hcount[CNT_SCRATCH1]) return cem_fail(c, CEM_ENONFINITE, "non-finite displacement");
+    return CEM_OK;
 }
 
 int cem_profile(cem_ctx* c, int enable) {
@@ -1084,6 +1219,17 @@ int cem_destroy(cem_ctx* c) {
     if (!c) return CEM_OK;
     cudaSetDevice(c->device);
     cudaStreamSynchronize(c->stream);
+    if (c->side_stream) {
+        cudaStreamSynchronize(c->side_stream);
+        cudaStreamDestroy(c->side_stream);
+    }
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
+    if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+    if (c->cap_stream) {
+        cudaStreamSynchronize(c->cap_stream);
+        cudaStreamDestroy(c->cap_stream);
+    }
     for (void* p : c->allocs) {
         if (c->free_fn) c->free_fn(p, (void*)c->stream, c->alloc_user);
         else cudaFree(p);

@@ -157,6 +157,14 @@ struct cem_ctx {
     int g_variant = CEM_G_PRINCIPAL;
     int precision = CEM_FP64;
     cudaStream_t stream = 0;
+    // FP64 front evaluation beside the force and node-update kernels (created on first use)
+    cudaStream_t side_stream = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    // cem_step_graph: a captured n-step graph of a fixed-topology context and what it was captured for
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+    int64_t graph_key[8] = {-1, -1, -1, -1, -1, -1, -1, -1};
+    int64_t n_graph_launch = 0;   // kernels in one replay of the captured graph
     int device = 0;
     cem_alloc_fn alloc = nullptr;
     cem_free_fn free_fn = nullptr;
