@@ -661,6 +661,37 @@ def run_cem(a):
 
     ens = _leg("ensemble", ens_leg) if (a.workload == "block" and a.ensemble_steps > 0) else None
 
+    # steps launched as one captured CUDA graph (cem_step_graph) against eager launches, on
+    # fixed topology (splitting off after the notch): a small specimen, where launches
+    # dominate, and the 256-specimen ensemble
+    def graph_leg():
+        from cem_inputs import plate_small
+        out = {"note": "fixed topology (split_enabled = 0 after the notch); graph: one capture, then the "
+                       "timed replay; the same kernels and arguments as eager stepping (bit-identical)"}
+        cases = [("notched_block_20x8x2", plate_small(), 2000, "fp64")]
+        if a.ensemble_steps > 0:
+            cases.append(("ensemble_256_seed4", _workload("ensemble"), a.ensemble_steps, "mixed"))
+        for name, wk, steps, prec in cases:
+            res = {"tets": wk.n_tets, "steps": steps, "precision": prec}
+            for mode in ("eager", "graph"):
+                sg = CEM.from_workload(wk, device=dev, split_enabled=False, precision=prec)
+                run = sg.step if mode == "eager" else sg.step_graph
+                run(steps)   # warm-up (and the capture)
+                barrier()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                run(steps)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                t_ms = e0.elapsed_time(e1)
+                res[mode] = {"value": wk.n_tets * steps / (t_ms * 1e-3), "ms_per_step": t_ms / steps}
+                sg.close()
+            res["graph_speedup"] = res["graph"]["value"] / res["eager"]["value"]
+            out[name] = res
+        return out
+
+    graph = _leg("graph", graph_leg) if a.workload == "block" else None
+
     # gradients: FP32 forward + adjoint with sqrt(N) checkpoints on the 102,000-element block,
     # J = final strain energy + mean top-face y displacement, topology frozen after the notch
     def adj_leg():
@@ -717,13 +748,20 @@ def run_cem(a):
     # end to end through the public API with host buffers: create + material + K steps + read back
     barrier()
     t0 = time.perf_counter()
-    sim2 = CEM.from_workload(w, device=dev, split_capacity=a.split_capacity, precision=a.precision)
+    sim2 = CEM(w.X, w.tets, w.tfaces, w.tvec, w.notch_tet, w.notch_side, device=dev,
+               split_capacity=a.split_capacity, precision=a.precision)
+    t1 = time.perf_counter()
+    sim2.set_material(w.rho, w.nu, w.E, w.Gc)
     _reorder(sim2, a)
+    t2 = time.perf_counter()
     sim2.step(a.steps)   # default launch variants: the autotuner is not part of a plain run
+    torch.cuda.synchronize()
+    t3 = time.perf_counter()
     u = sim2.field("u")
     sim2.energy()
     torch.cuda.synchronize()
     t_e2e = time.perf_counter() - t0
+    e2e_parts = {"create_s": t1 - t0, "material_s": t2 - t1, "steps_s": t3 - t2, "readback_s": t_e2e - (t3 - t0)}
     sim2.close()
     t_e2e = max_over_ranks(t_e2e, world, "cuda")
     h2d = (w.X.nbytes + w.tets.nbytes + w.tfaces.nbytes + w.tvec.nbytes + w.notch_tet.nbytes
@@ -757,7 +795,7 @@ def run_cem(a):
         "e2e": {"value": replica_throughput(w.n_tets, a.steps, world, t_e2e * 1e3), "unit": METRIC,
                 "h2d_bytes_per_step": h2d / a.steps, "d2h_bytes_per_step": d2h / a.steps,
                 "includes": "mesh upload from host arrays and topology build, material and a_0, K steps "
-                            "(default launch variants), u and energy read-back"},
+                            "(default launch variants), u and energy read-back", "parts": e2e_parts},
         "gpu_launches": main["launches"],
         "cpu_baseline": cpu,
         "launch_variants": main["tuning"] if not a.no_autotune else "defaults (autotuner off)",
@@ -768,6 +806,8 @@ def run_cem(a):
         line["precision_agreement"] = agree
     if ens is not None:
         line["ensemble"] = ens
+    if graph is not None:
+        line["graph"] = graph
     if adj is not None:
         line["adjoint"] = adj
     if hexres is not None:

@@ -210,6 +210,21 @@ int cem_set_material(cem_ctx* ctx, double rho, double nu,
  * CEM_ECUDA. */
 int cem_step(cem_ctx* ctx, int64_t n);
 
+/* The same n steps as cem_step, launched as one CUDA graph (no counterpart in
+ * the paper; the batched-ensemble pattern of SURVEY NEXT-2 for a topology that
+ * does not change).  Valid only while no step can split: splitting disabled
+ * (split_enabled = 0; the notch still applies at creation) or no crack-front
+ * element; the split path sizes its launches from counts the host reads every
+ * step and cannot run inside a graph.  The graph is captured on a private
+ * stream on the first call and re-captured when n, the mesh sizes or the
+ * launch variants change; later calls replay it on the context's stream.
+ * Results are bit-identical to cem_step.  Synchronises once at the end (to
+ * check for non-finite displacements).  Errors: CEM_ESTATE (no material; a
+ * context with crack-front elements and splitting on; prescribed velocities,
+ * whose values depend on the step number; kernel timing on), CEM_ENONFINITE,
+ * CEM_ECUDA. */
+int cem_step_graph(cem_ctx* ctx, int64_t n);
+
 /* Bounded device waits.  Every spin-wait in the library's kernels (the
  * look-back of the ordered scans) gives up after a number of polls, records
  * an error flag and returns; the host then reports CEM_ETIMEOUT instead of

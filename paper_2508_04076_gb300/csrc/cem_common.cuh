@@ -367,7 +367,7 @@ int cem_hex_force(cem_ctx* c);
 int64_t cem_hex_geometry_values();
 
 // ---------------------------------------------------------------- crack path (cem_crack.cu)
-int cem_launch_front_G(cem_ctx* c);
+int cem_launch_front_G(cem_ctx* c, int predict_u);   // predict_u: read u + dt v + dt^2/2 a (see FrontU)
 int cem_defrag_lists(cem_ctx* c, int kind);   // rewrite fan (0) or incidence (1) lists in index order
 int cem_renumber_nodes(cem_ctx* c);           // Morton-order node storage (cem_reorder.cu)
 int cem_reorder_maybe(cem_ctx* c);            // renumber when the growth trigger is reached

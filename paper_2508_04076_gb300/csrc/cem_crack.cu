@@ -59,13 +59,37 @@ __device__ __forceinline__ double dot3(const double a[3], const double b[3]) {
     return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
 }
 
+// The end-of-step displacement the front evaluation reads: u as stored, or, in
+// mixed precision when the evaluation runs before the node update has advanced u
+// (beside the force kernel), the predictor of the stored state u + dt v + dt^2/2 a,
+// formed exactly as the node update forms it (cem_pred with the same step values),
+// so both give the same bits.
+struct FrontU {
+    const double *u, *v, *a, *dtn;
+    double dt, hdt2;   // dt = hdt + hdt and hdt2 = hdt dt, hdt = dt / 2 (per node from dtn)
+    int pred;
+    __device__ void load(int64_t Nc, int i, double r[3]) const {
+        if (!pred) {
+            load3(u, Nc, i, r);
+            return;
+        }
+        double d = dt, h2 = hdt2;
+        if (dtn) {
+            const double hd = 0.5 * dtn[i];
+            d = hd + hd;
+            h2 = hd * d;
+        }
+        for (int c = 0; c < 3; ++c) r[c] = cem_pred(u[c * Nc + i], v[c * Nc + i], a[c * Nc + i], d, h2);
+    }
+};
+
 // Eq. 16: (u_i - u_j) if the edge is longer than in the reference, else 0.
-__device__ void stretch(const double* X, const double* u, int64_t Nc, int i, int j, double d[3]) {
+__device__ void stretch(const double* X, const FrontU& U, int64_t Nc, int i, int j, double d[3]) {
     double Xi[3], Xj[3], ui[3], uj[3];
     load3(X, Nc, i, Xi);
     load3(X, Nc, j, Xj);
-    load3(u, Nc, i, ui);
-    load3(u, Nc, j, uj);
+    U.load(Nc, i, ui);
+    U.load(Nc, j, uj);
     double L2 = 0, l2 = 0;
     for (int c = 0; c < 3; ++c) {
         double dX = Xj[c] - Xi[c];
@@ -182,7 +206,7 @@ __device__ __forceinline__ FrontFace front_face(int t, int f, const int* __restr
                                                 const int* __restrict__ t2e, int64_t Tc,
                                                 const int* __restrict__ face_nbr, const uint8_t* __restrict__ side,
                                                 int64_t T0, const double* __restrict__ X,
-                                                const double* __restrict__ u, int64_t Nc) {
+                                                const FrontU& U, int64_t Nc) {
     FrontFace F;
     F.mask = 0;
     const int s = face_nbr[f * T0 + t];
@@ -210,8 +234,8 @@ __device__ __forceinline__ FrontFace front_face(int t, int f, const int* __restr
     const int dl = f;
     const int a = tn[al], c = tn[cl_], b = tn[bl], d = tn[dl];
     double d1[3], d2[3];
-    stretch(X, u, Nc, a, c, d1);
-    stretch(X, u, Nc, c, b, d2);
+    stretch(X, U, Nc, a, c, d1);
+    stretch(X, U, Nc, c, b, d2);
     double Xa[3], Xb[3], Xc[3], Xd[3];
     load3(X, Nc, a, Xa);
     load3(X, Nc, b, Xb);
@@ -256,7 +280,7 @@ __global__ void __launch_bounds__(FB) k_front_faces(const int* __restrict__ cand
                                                     const int* __restrict__ conn, const int* __restrict__ t2e,
                                                     int64_t Tc, const int* __restrict__ face_nbr,
                                                     const uint8_t* __restrict__ side, int64_t T0,
-                                                    const double* __restrict__ X, const double* __restrict__ u,
+                                                    const double* __restrict__ X, FrontU U,
                                                     int64_t Nc, int* __restrict__ ff_mask,
                                                     double* __restrict__ ff_prod, double* __restrict__ ff_nrm,
                                                     int* __restrict__ ff_edge, int64_t cap4,
@@ -266,7 +290,7 @@ __global__ void __launch_bounds__(FB) k_front_faces(const int* __restrict__ cand
     const int ci = tid >> 2, f = tid & 3;
     bool cut = false;
     if (ci < nc) {
-        const FrontFace F = front_face(cand[ci], f, conn, t2e, Tc, face_nbr, side, T0, X, u, Nc);
+        const FrontFace F = front_face(cand[ci], f, conn, t2e, Tc, face_nbr, side, T0, X, U, Nc);
         if (F.mask) {
             cut = true;
             for (int q = 0; q < 6; ++q) ff_nrm[q * cap4 + tid] = F.nrm[q];
@@ -351,7 +375,7 @@ __global__ void __launch_bounds__(FS_T) k_front_small(const int* __restrict__ ca
                                                       const int* __restrict__ conn, const int* __restrict__ t2e,
                                                       int64_t Tc, const int* __restrict__ face_nbr,
                                                       const uint8_t* __restrict__ side, int64_t T0,
-                                                      const double* __restrict__ X, const double* __restrict__ u,
+                                                      const double* __restrict__ X, FrontU U,
                                                       int64_t Nc, const double* __restrict__ sig,
                                                       const float* __restrict__ sig32, const double* __restrict__ Gc,
                                                       int gvar, int* __restrict__ split_list,
@@ -371,7 +395,7 @@ __global__ void __launch_bounds__(FS_T) k_front_small(const int* __restrict__ ca
     }
     __syncthreads();
     for (int it = tid; it < 4 * nc; it += FS_T) {
-        face[it] = front_face(cand[it >> 2], it & 3, conn, t2e, Tc, face_nbr, side, T0, X, u, Nc);
+        face[it] = front_face(cand[it >> 2], it & 3, conn, t2e, Tc, face_nbr, side, T0, X, U, Nc);
         if (face[it].mask) {
             const int r = atomicAdd(&n_items, 3);
             for (int q = 0; q < 3; ++q) items[r + q] = 3 * it + q;
@@ -1357,11 +1381,13 @@ int update_lists(cem_ctx* c, int S) {
 
 }  // namespace
 
-int cem_launch_front_G(cem_ctx* c) {
+int cem_launch_front_G(cem_ctx* c, int predict_u) {
+    const double hdt = 0.5 * c->dt, dts = hdt + hdt;
+    const FrontU U{c->u, c->v, c->a, c->dtn, dts, hdt * dts, predict_u};
     if (c->n_cand > 0 && c->n_cand <= FRONT_SMALL) {
         cem_pdl(c->stream, k_front_small, 1, FS_T, (const int*)c->cand_list, (int)c->n_cand, (const int*)c->conn,
                 (const int*)c->t2e, c->Tc, (const int*)c->face_nbr, (const uint8_t*)c->side, c->T0,
-                (const double*)c->X, (const double*)c->u, c->Nc, (const double*)c->sig, (const float*)c->sig32,
+                (const double*)c->X, U, c->Nc, (const double*)c->sig, (const float*)c->sig32,
                 (const double*)c->Gc, c->g_variant, c->split_list, c->split_mask, c->split_Gv,
                 c->dcount + CNT_SPLIT, c->dcount + CNT_SCRATCH0);
         cem_launched(c, 1);
@@ -1373,7 +1399,7 @@ int cem_launch_front_G(cem_ctx* c) {
         const int nc = (int)std::min<int64_t>(cap, c->n_cand - c0);
         long long* qn = c->dcount + CNT_FRONT_Q;
         cem_pdl(c->stream, k_front_faces, cem_grid(4 * (int64_t)nc, FB), FB, c->cand_list + c0, nc, c->conn, c->t2e,
-                c->Tc, c->face_nbr, c->side, c->T0, c->X, c->u, c->Nc, c->ff_mask, c->ff_prod, c->ff_nrm, c->ff_edge,
+                c->Tc, c->face_nbr, c->side, c->T0, c->X, U, c->Nc, c->ff_mask, c->ff_prod, c->ff_nrm, c->ff_edge,
                 cap4, c->ff_item, qn);
         cem_pdl(c->stream, k_front_proj, cem_grid(12 * (int64_t)nc, FB), FB, c->ff_item, qn, c->ff_edge, c->ff_nrm,
                 cap4, c->sig, c->sig32, c->g_variant, c->ff_s);

@@ -420,11 +420,19 @@ template <class R> struct NodeSum;
 template <> struct NodeSum<double> {
     struct Slot { double x, y, z; };
     double f[3] = {0.0, 0.0, 0.0};
+    bool first = true;   // the sum starts from its first term (no FP64 add of a zero)
     __device__ static Slot load(const double* fp, int e) {   // entry = element * npe + local node
         const double* p = fp + 3 * (int64_t)e;
         return {p[0], p[1], p[2]};
     }
     __device__ void add(const Slot& x) {
+        if (first) {
+            f[0] = x.x;
+            f[1] = x.y;
+            f[2] = x.z;
+            first = false;
+            return;
+        }
         f[0] += x.x;
         f[1] += x.y;
         f[2] += x.z;
