@@ -845,13 +845,20 @@ struct NvtxRange {
 };
 
 // The front evaluation (Eqs. 16-18) on the side stream, forked from the context's
-// stream after the edge stresses: it reads u, the edge stresses and the crack
-// topology, none of which the force and node-update kernels of an FP64 step
-// write (the FP64 node update writes v and a; u changes only in the next
-// predictor), so it runs beside them and joins before the split decision is read.
+// stream after the edge stresses.  It reads the end-of-step displacement, the edge
+// stresses and the crack topology.  FP64: u is already the end-of-step displacement
+// and neither the force nor the node-update kernel writes u, the edge stresses or
+// the topology (the FP64 node update writes v and a), so the evaluation runs beside
+// both and joins before the split decision is read.  Mixed precision: the node update
+// advances u, so the evaluation forms the end-of-step displacement from the stored
+// u, v, a as the node update does (FrontU) and joins before the node update.
 int launch_front_side(cem_ctx* c) {
     if (!c->side_stream) {
-        CEM_CK(c, cudaStreamCreateWithFlags(&c->side_stream, cudaStreamNonBlocking));
+        // the highest priority: the block scheduler then starts the front's few blocks as
+        // soon as an SM has room, ahead of the force kernel's blocks still waiting
+        int lo = 0, hi = 0;
+        CEM_CK(c, cudaDeviceGetStreamPriorityRange(&lo, &hi));
+        CEM_CK(c, cudaStreamCreateWithPriority(&c->side_stream, cudaStreamNonBlocking, hi));
         CEM_CK(c, cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
         CEM_CK(c, cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
     }
@@ -863,7 +870,7 @@ int launch_front_side(cem_ctx* c) {
     int rc;
     {
         NvtxRange front("cem.front_G");
-        rc = cem_launch_front_G(c);
+        rc = cem_launch_front_G(c, c->precision == CEM_MIXED ? 1 : 0);
     }
     prof_end(c, CEM_KERNEL_FRONT_G, ev);
     c->stream = main;
@@ -877,26 +884,22 @@ int run_step(cem_ctx* c) {
     if (c->tune_auto)
         if (int rc = cem_tune_maybe(c)) return rc;
     c->prof_now = c->prof && (c->step % c->prof_every == 0);
-    // mixed precision: the node update advances u, so the front evaluation follows it
+    // the front evaluation runs beside the force kernel (and, FP64, the node update)
     const bool fronts = c->split_enabled && c->n_cand > 0;
-    const bool beside = fronts && c->precision != CEM_MIXED;
-    if (c->precision != CEM_MIXED)   // mixed precision: the node update carries the predictor
+    const bool mix = c->precision == CEM_MIXED;
+    if (!mix)   // mixed precision: the node update carries the predictor
         TIMED(c, CEM_KERNEL_PREDICT, cem_launch_predict(c));
     TIMED(c, CEM_KERNEL_STRAIN, cem_launch_strain(c));
     TIMED(c, CEM_KERNEL_EDGE_STRESS, cem_launch_edge_stress(c));
-    if (beside)
+    if (fronts)
         if (int rc = launch_front_side(c)) return rc;
     TIMED(c, CEM_KERNEL_FORCE, cem_launch_force(c));
+    if (fronts && mix) CEM_CK(c, cudaStreamWaitEvent(c->stream, c->ev_join, 0));
     TIMED(c, CEM_KERNEL_NODE_UPDATE, cem_launch_node_update(c, 0));
     if (int rc = cem_launch_prescribe(c, c->step + 1)) return rc;
     c->step += 1;
     if (fronts) {
-        if (beside) {
-            CEM_CK(c, cudaStreamWaitEvent(c->stream, c->ev_join, 0));
-        } else {
-            NvtxRange front("cem.front_G");
-            TIMED(c, CEM_KERNEL_FRONT_G, cem_launch_front_G(c));
-        }
+        if (!mix) CEM_CK(c, cudaStreamWaitEvent(c->stream, c->ev_join, 0));
         int rc;
         if ((rc = sync_counts(c))) return rc;
         if (c->hcount[CNT_ERR] & DERR_SCAN_WAIT)
