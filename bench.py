@@ -56,8 +56,8 @@ KERNEL_UNITS = {"predict": "nodes", "strain": "tets", "edge_stress": "edges", "f
 # launch, divided by the launch's units: 982,000 elements, 1,219,792 edges, 187,533 nodes after the notch)
 # on the intact 960,000-element block, for the kernels as they are now.  Source:
 # profiles/step_kernels_fp64_notched_block_200x80x10.md and profiles/step_kernels_mixed_notched_block_200x80x10.md.
-DRAM_BYTES_PER_UNIT = {"fp64": {"strain": 108.7, "edge_stress": 103.6, "force": 216.2, "node_update": 847.3},
-                       "mixed": {"strain": 63.0, "edge_stress": 70.9, "force": 129.7, "node_update": 557.3}}
+DRAM_BYTES_PER_UNIT = {"fp64": {"strain": 107.5, "edge_stress": 104.0, "force": 215.6, "node_update": 834.4},
+                       "mixed": {"strain": 63.3, "edge_stress": 71.8, "force": 129.2, "node_update": 559.9}}
 
 
 def b_alg_per_tet_step(T, E, N, precision):
@@ -196,8 +196,11 @@ def roofline_accounting(chunks, prof, precision, scale, t_ms, hbm, fp64_peak):
                     "flops_per_element_step": whole_flops / max(elem_steps, 1.0),
                     "alg_gbs": whole_bytes / t_s / 1e9, "hbm_peak_gbs": hbm,
                     "hbm_frac": whole_bytes / t_s / 1e9 / hbm if hbm else None,
-                    "fp64_tflops": whole_flops / t_s / 1e12, "fp64_peak_tflops": fp64_peak / 1e12,
-                    "fp64_frac": whole_flops / t_s / fp64_peak if fp64_peak else None,
+                    # the FP64 figures only for the FP64 path (mixed precision does its element and
+                    # edge arithmetic in FP32)
+                    "fp64_tflops": whole_flops / t_s / 1e12 if precision == "fp64" else None,
+                    "fp64_peak_tflops": fp64_peak / 1e12,
+                    "fp64_frac": whole_flops / t_s / fp64_peak if (fp64_peak and precision == "fp64") else None,
                     "active_element_steps_per_s": elem_steps / t_s}}
     return kernels, roofline
 

@@ -1265,11 +1265,11 @@ void cem_tune_describe(int k, int v, int* block, int* batch) {
     *batch = TUNE_BATCH[k][v / 3];
 }
 
-// The variants used before any tuning: 256 threads, fan rounds of 2 over fan-sorted edges,
-// node batches of 8 (FP32) or 4 (FP64).
+// The variants used before any tuning: 256 threads, fan rounds of 2 (over fan-sorted edges in
+// FP64, where idle lanes cost FP64 issue; in edge order in FP32), node batches of 8 (FP32) or 4 (FP64).
 int cem_tune_default(int k, int precision) {
     if (k == TUNE_NODE) return 1 + 3 * (precision == CEM_MIXED ? 2 : 1);
-    if (k == TUNE_EDGE) return 1 + 3 * 3;
+    if (k == TUNE_EDGE) return precision == CEM_MIXED ? 1 : 1 + 3 * 3;
     return 1;
 }
 
