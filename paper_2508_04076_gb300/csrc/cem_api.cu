@@ -15,6 +15,7 @@
 #include <atomic>
 #include <cmath>
 #include <cstring>
+#include <memory>
 #include <numeric>
 #include <string>
 #include <thread>
@@ -103,15 +104,24 @@ struct HostTopo {
 
 int build_topology(cem_ctx* c, const std::vector<int>& conn, HostTopo& H) {
     const int64_t N = c->N0, T = c->T0;
+    // node -> element * 4 + local, ascending: counted and placed with atomic counters on
+    // all host cores, then each node's list sorted (the result does not depend on the order)
     H.inc_off.assign(N + 1, 0);
-    for (int64_t t = 0; t < T; ++t)
-        for (int l = 0; l < 4; ++l) H.inc_off[conn[t * 4 + l] + 1]++;
-    for (int64_t i = 0; i < N; ++i) H.inc_off[i + 1] += H.inc_off[i];
-    H.inc.assign(4 * T, 0);
     {
-        std::vector<int> cur(H.inc_off.begin(), H.inc_off.end() - 1);
-        for (int64_t t = 0; t < T; ++t)
-            for (int l = 0; l < 4; ++l) H.inc[cur[conn[t * 4 + l]]++] = (int)(t * 4 + l);
+        std::unique_ptr<std::atomic<int>[]> cnt(new std::atomic<int>[N + 1]);
+        for (int64_t i = 0; i <= N; ++i) cnt[i].store(0, std::memory_order_relaxed);
+        parallel_for(4 * T, [&](int64_t a, int64_t b) {
+            for (int64_t q = a; q < b; ++q) cnt[conn[q]].fetch_add(1, std::memory_order_relaxed);
+        });
+        for (int64_t i = 0; i < N; ++i) H.inc_off[i + 1] = H.inc_off[i] + cnt[i].load(std::memory_order_relaxed);
+        for (int64_t i = 0; i < N; ++i) cnt[i].store(H.inc_off[i], std::memory_order_relaxed);
+        H.inc.assign(4 * T, 0);
+        parallel_for(4 * T, [&](int64_t a, int64_t b) {
+            for (int64_t q = a; q < b; ++q) H.inc[cnt[conn[q]].fetch_add(1, std::memory_order_relaxed)] = (int)q;
+        });
+        parallel_for(N, [&](int64_t a, int64_t b) {
+            for (int64_t i = a; i < b; ++i) std::sort(H.inc.begin() + H.inc_off[i], H.inc.begin() + H.inc_off[i + 1]);
+        });
     }
     // edges: for each node the sorted distinct neighbours with larger id (counted, then
     // written, node by node on all host cores)
@@ -158,38 +168,58 @@ int build_topology(cem_ctx* c, const std::vector<int>& conn, HostTopo& H) {
                 H.t2e[l * T + t] = H.e_off[x] + (int)(it - lo);
             }
     });
-    // fans: elements of each edge in ascending element order
+    // fans: elements of each edge in ascending element order, the intersection of its
+    // end nodes' (ascending) incidence lists; counted, then written, node by node
+    auto fan_of = [&](int64_t x, int y, int* out) {   // writes when out != nullptr; returns the size
+        int p = H.inc_off[x], pe = H.inc_off[x + 1], q = H.inc_off[y], qe = H.inc_off[y + 1], k = 0;
+        while (p < pe && q < qe) {
+            const int ta = H.inc[p] >> 2, tb = H.inc[q] >> 2;
+            if (ta < tb) ++p;
+            else if (tb < ta) ++q;
+            else {
+                if (out) out[k] = ta;
+                ++k, ++p, ++q;
+            }
+        }
+        return k;
+    };
     H.fan_off.assign(c->E0 + 1, 0);
-    for (int64_t t = 0; t < T; ++t)
-        for (int l = 0; l < 6; ++l) H.fan_off[H.t2e[l * T + t] + 1]++;
+    parallel_for(N, [&](int64_t a, int64_t b) {
+        for (int64_t x = a; x < b; ++x)
+            for (int e = H.e_off[x]; e < H.e_off[x + 1]; ++e) H.fan_off[e + 1] = fan_of(x, H.e_nbr[e], nullptr);
+    });
     c->max_fan0 = 0;
     for (int64_t e = 0; e < c->E0; ++e) c->max_fan0 = std::max<int64_t>(c->max_fan0, H.fan_off[e + 1]);
     for (int64_t e = 0; e < c->E0; ++e) H.fan_off[e + 1] += H.fan_off[e];
-    H.fan.assign(6 * T, 0);
-    {
-        std::vector<int> cur(H.fan_off.begin(), H.fan_off.end() - 1);
-        for (int64_t t = 0; t < T; ++t)
-            for (int l = 0; l < 6; ++l) H.fan[cur[H.t2e[l * T + t]]++] = (int)t;
-    }
+    H.fan.assign(H.fan_off[c->E0], 0);
+    parallel_for(N, [&](int64_t a, int64_t b) {
+        for (int64_t x = a; x < b; ++x)
+            for (int e = H.e_off[x]; e < H.e_off[x + 1]; ++e) fan_of(x, H.e_nbr[e], H.fan.data() + H.fan_off[e]);
+    });
     // face adjacency (local face f is opposite local node f)
     H.face_nbr.assign(4 * T, -1);
     std::atomic<bool> non_manifold{false};
+    // the element across face f (opposite local node f) shares the face's edge between its
+    // first two nodes, so it is in that edge's fan: look for the fan element that also holds
+    // the face's third node
     parallel_for(T, [&](int64_t a, int64_t b) {
         for (int64_t t = a; t < b; ++t)
             for (int f = 0; f < 4; ++f) {
-                int fn[3], k = 0;
+                int fl[3], k = 0;
                 for (int l = 0; l < 4; ++l)
-                    if (l != f) fn[k++] = conn[t * 4 + l];
+                    if (l != f) fl[k++] = l;
+                int le = 0;
+                for (int l = 0; l < 6; ++l)
+                    if ((LE[l][0] == fl[0] && LE[l][1] == fl[1]) || (LE[l][0] == fl[1] && LE[l][1] == fl[0])) le = l;
+                const int e = H.t2e[le * T + t];
+                const int third = conn[t * 4 + fl[2]];
                 int found = -1, nfound = 0;
-                for (int q = H.inc_off[fn[0]]; q < H.inc_off[fn[0] + 1]; ++q) {
-                    const int s = H.inc[q] >> 2;
+                for (int q = H.fan_off[e]; q < H.fan_off[e + 1]; ++q) {
+                    const int s = H.fan[q];
                     if (s == t) continue;
-                    int hits = 0;
-                    for (int l = 0; l < 4; ++l) {
-                        const int x = conn[(int64_t)s * 4 + l];
-                        hits += (x == fn[1]) + (x == fn[2]);
-                    }
-                    if (hits == 2) {
+                    bool has = false;
+                    for (int l = 0; l < 4; ++l) has = has || conn[(int64_t)s * 4 + l] == third;
+                    if (has) {
                         found = s;
                         ++nfound;
                     }
@@ -484,28 +514,48 @@ int create_impl(const cem_mesh_desc* d, cem_ctx* c) {
     c->N0 = N0;
     c->T0 = T0;
     std::vector<int> conn(d->tets, d->tets + 4 * T0);
-    for (int64_t q = 0; q < 4 * T0; ++q)
-        if (conn[q] < 0 || conn[q] >= N0) return cem_fail(c, CEM_EINVAL, "element node id out of range");
-    // orientation: negative signed volume swaps local nodes 2 and 3
+    // node ids in range, no repeated node, non-zero finite volume; a negative signed
+    // volume swaps local nodes 2 and 3 (element by element on all host cores)
     std::vector<char> swapped(T0, 0);
-    for (int64_t t = 0; t < T0; ++t) {
+    std::atomic<int> bad{0};   // 1 id out of range, 2 repeated node, 3 zero volume
+    parallel_for(T0, [&](int64_t a0, int64_t b0) {
         const double* X = d->X;
-        const int* n = &conn[t * 4];
-        for (int a = 0; a < 4; ++a)
-            for (int b = a + 1; b < 4; ++b)
-                if (n[a] == n[b]) return cem_fail(c, CEM_EINVAL, "element with a repeated node");
-        double e[3][3];
-        for (int r = 0; r < 3; ++r)
-            for (int k = 0; k < 3; ++k) e[r][k] = X[3 * n[r + 1] + k] - X[3 * n[0] + k];
-        const double V6 = e[0][0] * (e[1][1] * e[2][2] - e[1][2] * e[2][1]) -
-                          e[0][1] * (e[1][0] * e[2][2] - e[1][2] * e[2][0]) +
-                          e[0][2] * (e[1][0] * e[2][1] - e[1][1] * e[2][0]);
-        if (!(V6 != 0.0) || !std::isfinite(V6)) return cem_fail(c, CEM_EINVAL, "zero-volume element");
-        if (V6 < 0) {
-            std::swap(conn[t * 4 + 2], conn[t * 4 + 3]);
-            swapped[t] = 1;
+        for (int64_t t = a0; t < b0; ++t) {
+            int* n = &conn[t * 4];
+            bool ok = true;
+            for (int a = 0; a < 4; ++a) ok = ok && n[a] >= 0 && n[a] < N0;
+            if (!ok) {
+                bad.store(1);
+                continue;
+            }
+            for (int a = 0; a < 4; ++a)
+                for (int b = a + 1; b < 4; ++b)
+                    if (n[a] == n[b]) ok = false;
+            if (!ok) {
+                int z = 0;
+                bad.compare_exchange_strong(z, 2);
+                continue;
+            }
+            double e[3][3];
+            for (int r = 0; r < 3; ++r)
+                for (int k = 0; k < 3; ++k) e[r][k] = X[3 * n[r + 1] + k] - X[3 * n[0] + k];
+            const double V6 = e[0][0] * (e[1][1] * e[2][2] - e[1][2] * e[2][1]) -
+                              e[0][1] * (e[1][0] * e[2][2] - e[1][2] * e[2][0]) +
+                              e[0][2] * (e[1][0] * e[2][1] - e[1][1] * e[2][0]);
+            if (!(V6 != 0.0) || !std::isfinite(V6)) {
+                int z = 0;
+                bad.compare_exchange_strong(z, 3);
+                continue;
+            }
+            if (V6 < 0) {
+                std::swap(n[2], n[3]);
+                swapped[t] = 1;
+            }
         }
-    }
+    });
+    if (bad.load() == 1) return cem_fail(c, CEM_EINVAL, "element node id out of range");
+    if (bad.load() == 2) return cem_fail(c, CEM_EINVAL, "element with a repeated node");
+    if (bad.load() == 3) return cem_fail(c, CEM_EINVAL, "zero-volume element");
     // ensembles: element -> specimen map; every node must belong to one specimen
     std::vector<int> node_inst;
     c->n_inst = d->n_instances > 1 ? d->n_instances : 1;
@@ -590,6 +640,7 @@ int create_impl(const cem_mesh_desc* d, cem_ctx* c) {
     ok = ok && dalloc(c, c->split_G, T0) && dalloc(c, c->Gc, T0) && dalloc(c, c->oe_n0, E0) && dalloc(c, c->oe_n1, E0);
     ok = ok && dalloc(c, c->node_of_key, 2 * E0) && dalloc(c, c->cand_flag, T0) && dalloc(c, c->cand_list, T0);
     ok = ok && dalloc(c, c->dec_mask, T0) && dalloc(c, c->dec_G, T0) && dalloc(c, c->split_list, T0);
+    ok = ok && dalloc(c, c->act_orig, T0);
     ok = ok && dalloc(c, c->ext_of_int, Nc) && dalloc(c, c->int_of_ext, Nc) && dalloc(c, c->rn_map, Nc);
     if (ok) {   // renumbering scratch: the step's element-force and strain records are dead between steps
         int64_t kcap = 2048;
@@ -758,14 +809,17 @@ int create_impl(const cem_mesh_desc* d, cem_ctx* c) {
 
     // geometry of the input elements; h_min = min 3V / max face area
     if (int rc = cem_launch_geometry(c, 0, T0, c->dec_G)) return rc;
-    {
+    if (c->n_inst == 1) {   // one specimen: the minimum on the device
+        if (int rc = cem_device_min(c, c->dec_G, T0, &c->h_min)) return rc;
+        c->inst_hmin.assign(1, c->h_min);
+    } else {                // an ensemble: each specimen's minimum on the host
         std::vector<double> hm(T0);
         CEM_CK(c, cudaMemcpyAsync(hm.data(), c->dec_G, T0 * sizeof(double), cudaMemcpyDeviceToHost, s));
         CEM_CK(c, cudaStreamSynchronize(s));
         c->h_min = *std::min_element(hm.begin(), hm.end());
         c->inst_hmin.assign(c->n_inst, 1e300);
         for (int64_t t = 0; t < T0; ++t) {
-            const int i = c->n_inst > 1 ? c->h_tet_inst[t] : 0;
+            const int i = c->h_tet_inst[t];
             c->inst_hmin[i] = std::min(c->inst_hmin[i], hm[t]);
         }
     }

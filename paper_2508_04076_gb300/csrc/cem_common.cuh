@@ -119,6 +119,7 @@ enum {
     CNT_SCRATCH0,
     CNT_SCRATCH1,
     CNT_FRONT_Q,       // queued edge projections of a front evaluation (0 between evaluations)
+    CNT_ACT_ORIG,      // active original elements listed in act_orig
     CNT_COUNT
 };
 
@@ -160,6 +161,10 @@ struct cem_ctx {
     // FP64 front evaluation beside the force and node-update kernels (created on first use)
     cudaStream_t side_stream = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    // the active original elements in ascending order, used by the strain and force launches
+    // once many originals have split (n_act_orig < 0: no list, every slot is visited)
+    int* act_orig = nullptr;
+    int64_t n_act_orig = -1;
     // cem_step_graph: a captured n-step graph of a fixed-topology context and what it was captured for
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
@@ -367,7 +372,9 @@ int cem_hex_force(cem_ctx* c);
 int64_t cem_hex_geometry_values();
 
 // ---------------------------------------------------------------- crack path (cem_crack.cu)
-int cem_launch_front_G(cem_ctx* c, int predict_u);   // predict_u: read u + dt v + dt^2/2 a (see FrontU)
+int cem_launch_front_G(cem_ctx* c, int predict_u);
+int cem_refresh_act_orig(cem_ctx* c);
+int cem_device_min(cem_ctx* c, const double* x, int64_t n, double* out);   // min of n device doubles   // rebuild the active-original list (after a checkpoint load)   // predict_u: read u + dt v + dt^2/2 a (see FrontU)
 int cem_defrag_lists(cem_ctx* c, int kind);   // rewrite fan (0) or incidence (1) lists in index order
 int cem_renumber_nodes(cem_ctx* c);           // Morton-order node storage (cem_reorder.cu)
 int cem_reorder_maybe(cem_ctx* c);            // renumber when the growth trigger is reached

@@ -633,19 +633,40 @@ __global__ void __launch_bounds__(1024) k_node_sorted(const long long* __restric
 
 // New node on the parent's edge between local nodes x and y, attached to x
 // (side 0: x is the end with the smaller creation id), and its creation id.
+// The new nodes on a split element's cut edges and their creation ids, loaded up front:
+// index 2 l + s for local edge l and side s (0: the node attached to the edge end with the
+// smaller creation id).  Three rounds of independent loads (edge ids, nodes, creation ids)
+// take the place of one chain of three dependent loads per lookup.  A lookup of the new
+// node on local edge x-y attached to x selects from registers.
 struct SubNode {
-    int p;
-    const int* t2e;
-    int64_t Tc;
-    const int* node_of_key;
-    const int* ext;
+    int nd[12], id[12];
     int x0, x1, x2, x3;   // creation ids of the parent's nodes
-    __device__ void operator()(int x, int y, int* node, int* id) const {
-        const int e = t2e[local_edge(x, y) * Tc + p];
+    __device__ void load(int p, int m, const int* __restrict__ t2e, int64_t Tc, const int* __restrict__ node_of_key,
+                         const int* __restrict__ ext) {
+        int e[6];
+#pragma unroll
+        for (int l = 0; l < 6; ++l) e[l] = t2e[l * Tc + p];
+#pragma unroll
+        for (int l = 0; l < 6; ++l) {
+            const bool cut = ((m >> CEM_LE0(l)) ^ (m >> CEM_LE1(l))) & 1;
+            nd[2 * l] = cut ? node_of_key[2 * e[l]] : -1;
+            nd[2 * l + 1] = cut ? node_of_key[2 * e[l] + 1] : -1;
+        }
+#pragma unroll
+        for (int q = 0; q < 12; ++q) id[q] = nd[q] >= 0 ? ext[nd[q]] : -1;
+    }
+    __device__ void operator()(int x, int y, int* node, int* cid) const {
         const int s = (cem_pick4(x0, x1, x2, x3, x) < cem_pick4(x0, x1, x2, x3, y)) ? 0 : 1;
-        const int nd = node_of_key[2 * e + s];
-        *node = nd;
-        *id = ext[nd];
+        const int k = 2 * local_edge(x, y) + s;
+        int a = nd[0], b = id[0];
+#pragma unroll
+        for (int q = 1; q < 12; ++q)
+            if (q == k) {
+                a = nd[q];
+                b = id[q];
+            }
+        *node = a;
+        *cid = b;
     }
 };
 
@@ -719,9 +740,14 @@ __global__ void k_create_subs(int S, int64_t T, const int* __restrict__ split_li
     const int p = split_list[i];
     const int m = split_mask[i];
     const int n0 = conn[p], n1 = conn[Tc + p], n2 = conn[2 * Tc + p], n3 = conn[3 * Tc + p];
-    const SubNode mf{p, t2e, Tc, node_of_key, ext, ext[n0], ext[n1], ext[n2], ext[n3]};
+    SubNode mf;
+    mf.x0 = ext[n0];
+    mf.x1 = ext[n1];
+    mf.x2 = ext[n2];
+    mf.x3 = ext[n3];
     int subs[6][4];
     // (no new nodes exist when splits only deactivate: the element only leaves the computation)
+    if (!deact) mf.load(p, m, t2e, Tc, node_of_key, ext);
     const int ns = deact ? 0 : cem_split_subs(n0, n1, n2, n3, mf.x0, mf.x1, mf.x2, mf.x3, m, mf, subs);
     const double area = split_area(X, Nc, n0, n1, n2, n3, m);
     const int64_t base = T + sub_off[i];
@@ -1413,6 +1439,15 @@ int cem_launch_front_G(cem_ctx* c, int predict_u) {
                     c->n_cand, CNT_SPLIT);
 }
 
+// The strain and force launches visit the listed active originals and then every
+// sub-element once a sixteenth of the original elements has split; before that they
+// visit every slot (an inactive slot returns at once, and few warps hold one).  On
+// GB300 a warp with a few active lanes costs as much FP64 issue as a full one, and
+// late in a run most original slots are inactive and scattered.
+static bool act_list_wanted(const cem_ctx* c, int64_t n_split) {
+    return c->act_orig != nullptr && c->elem_type == CEM_ELEM_TET4 && n_split * 16 >= c->T0;
+}
+
 // Apply the S splits held in split_list / split_mask / split_Gv (ascending
 // element ids).  step is recorded with each split; book_energy adds Gc * area
 // to the dissipated energy.  Grid sizes come from per-split bounds (at most 8
@@ -1481,6 +1516,9 @@ int cem_apply_splits(cem_ctx* c, int64_t S64, int64_t step, int book_energy) {
     cem_launched(c, 1);
     CEM_CK(c, cudaGetLastError());
     if ((rc = cem_compact_u8(c, c->cand_flag, c->T0, c->cand_list, CNT_CAND))) return rc;
+    // 6. the active originals for the strain and force launches (once many have split)
+    const bool act_list = act_list_wanted(c, c->n_split_all + S);
+    if (act_list && (rc = cem_compact_u8(c, c->active, c->T0, c->act_orig, CNT_ACT_ORIG))) return rc;
     if ((rc = sync_counts(c))) return rc;
     if (c->hcount[CNT_ERR] & DERR_SCAN_WAIT) return cem_fail(c, CEM_ETIMEOUT, "a scan's bounded look-back wait gave up");
     if (c->hcount[CNT_ERR] & DERR_HASH_FULL) return cem_fail(c, CEM_ECAPACITY, "edge hash table full");
@@ -1496,5 +1534,16 @@ int cem_apply_splits(cem_ctx* c, int64_t S64, int64_t step, int book_energy) {
     c->n_active += NS - S;
     c->n_split_all += S;
     if (book_energy) c->n_split_run += S;
+    c->n_act_orig = act_list ? c->hcount[CNT_ACT_ORIG] : -1;
+    return CEM_OK;
+}
+
+// After a checkpoint load: the active-original list of the loaded state.
+int cem_refresh_act_orig(cem_ctx* c) {
+    c->n_act_orig = -1;
+    if (!act_list_wanted(c, c->n_split_all)) return CEM_OK;
+    int rc;
+    if ((rc = cem_compact_u8(c, c->active, c->T0, c->act_orig, CNT_ACT_ORIG)) || (rc = sync_counts(c))) return rc;
+    c->n_act_orig = c->hcount[CNT_ACT_ORIG];
     return CEM_OK;
 }

@@ -334,5 +334,5 @@ extern "C" int cem_load(cem_ctx* c, const char* path) {
     CEM_CK(c, cudaDeviceSynchronize());
     if (int rc = cem_reorder_inverse(c)) return rc;
     CEM_CK(c, cudaStreamSynchronize(c->stream));
-    return CEM_OK;
+    return cem_refresh_act_orig(c);
 }

@@ -196,14 +196,27 @@ __device__ __forceinline__ double fma_r(double a, double b, double c) { return _
 
 // Inactive (split) element slots are skipped: no fan or incidence list refers to them.
 // TB (threads per block) is a tuning parameter (see cem_tune.cu).
+// The element slots a strain or force launch visits (ElemRange): every slot below T, or,
+// once many original elements have split, the listed active originals (ascending) and
+// then every sub-element slot from T0 on.
+struct ElemRange {
+    const int* act;   // active originals, or nullptr: slot i is element i
+    int64_t n_act, T0, n;
+    __device__ __forceinline__ int64_t elem(int64_t i) const {
+        return act ? (i < n_act ? (int64_t)act[i] : T0 + (i - n_act)) : i;
+    }
+};
+
 template <class R, int TB>
 __global__ void __launch_bounds__(TB) k_strain(const double* __restrict__ u, const float* __restrict__ uhl,
                                                int64_t Nc, const int* __restrict__ conn, const R* __restrict__ Vg,
-                                               const uint8_t* __restrict__ active, int64_t Tc, int64_t T,
+                                               const uint8_t* __restrict__ active, int64_t Tc, ElemRange rg,
                                                R* __restrict__ h) {
     CEM_PDL_ENTRY();
-    int64_t j = (int64_t)blockIdx.x * TB + threadIdx.x;
-    if (j >= T || !active[j]) return;
+    const int64_t i = (int64_t)blockIdx.x * TB + threadIdx.x;
+    if (i >= rg.n) return;
+    const int64_t j = rg.elem(i);
+    if (!active[j]) return;
     const int n[4] = {conn[j], conn[Tc + j], conn[2 * Tc + j], conn[3 * Tc + j]};
     R d[3][3];   // d[a][c] = u_{a+1,c} - u_{0,c}
     node_disp_diff<R>(u, uhl, Nc, n, d);
@@ -335,10 +348,12 @@ __global__ void __launch_bounds__(TB) k_edge_stress(const R* __restrict__ h, con
 template <class R, int TB>
 __global__ void __launch_bounds__(TB) k_force(const R* __restrict__ sig, const int* __restrict__ t2e,
                                               const R* __restrict__ Vg, const uint8_t* __restrict__ active,
-                                              int64_t Tc, int64_t T, R* __restrict__ fp) {
+                                              int64_t Tc, ElemRange rg, R* __restrict__ fp) {
     CEM_PDL_ENTRY();
-    int64_t j = (int64_t)blockIdx.x * TB + threadIdx.x;
-    if (j >= T || !active[j]) return;
+    const int64_t i = (int64_t)blockIdx.x * TB + threadIdx.x;
+    if (i >= rg.n) return;
+    const int64_t j = rg.elem(i);
+    if (!active[j]) return;
     int kk[6];
 #pragma unroll
     for (int l = 0; l < 6; ++l) kk[l] = t2e[l * Tc + j];
@@ -838,9 +853,15 @@ inline bool mixed(const cem_ctx* c) { return c->precision == CEM_MIXED; }
 
 // ---------------------------------------------------------------- variant dispatch
 // Variant v: TB = 128 << (v % 3) threads per block; v / 3 selects the batch.
+inline ElemRange elem_range(const cem_ctx* c) {
+    if (c->n_act_orig >= 0) return {c->act_orig, c->n_act_orig, c->T0, c->n_act_orig + (c->T - c->T0)};
+    return {nullptr, 0, c->T0, c->T};
+}
+
 template <class R, int TB>
 void go_strain(cem_ctx* c, const double* u, const float* uhl, const R* Vg, R* h) {
-    cem_pdl(c->stream, k_strain<R, TB>, cem_grid(c->T, TB), TB, u, uhl, c->Nc, c->conn, Vg, c->active, c->Tc, c->T, h);
+    const ElemRange rg = elem_range(c);
+    cem_pdl(c->stream, k_strain<R, TB>, cem_grid(rg.n, TB), TB, u, uhl, c->Nc, c->conn, Vg, c->active, c->Tc, rg, h);
 }
 template <class R>
 void launch_strain(cem_ctx* c, int v, const double* u, const float* uhl, const R* Vg, R* h) {
@@ -879,7 +900,8 @@ void launch_edge(cem_ctx* c, int v, const R* h, const R* cl, const R* cm, R* sig
 
 template <class R, int TB>
 void go_force(cem_ctx* c, const R* sig, const R* Vg, R* fp) {
-    cem_pdl(c->stream, k_force<R, TB>, cem_grid(c->T, TB), TB, sig, c->t2e, Vg, c->active, c->Tc, c->T, fp);
+    const ElemRange rg = elem_range(c);
+    cem_pdl(c->stream, k_force<R, TB>, cem_grid(rg.n, TB), TB, sig, c->t2e, Vg, c->active, c->Tc, rg, fp);
 }
 template <class R>
 void launch_force(cem_ctx* c, int v, const R* sig, const R* Vg, R* fp) {
@@ -1305,6 +1327,34 @@ int cem_launch_prescribe(cem_ctx* c, int64_t step) {
             c->dtn, c->v, c->a, c->Nc, c->u, mixed(c) ? c->uhl : nullptr);
     cem_launched(c);
     CEM_CK(c, cudaGetLastError());
+    return CEM_OK;
+}
+
+// The smallest of n device doubles to the host (min is exact, so the order of the tree
+// does not matter): per-block minima, then one block over them.
+__global__ void __launch_bounds__(RB) k_min_partial(const double* __restrict__ x, int64_t n, double* __restrict__ part) {
+    CEM_PDL_ENTRY();
+    __shared__ double sh[RB];
+    double m = 1.0 / 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * RB + threadIdx.x; i < n; i += (int64_t)gridDim.x * RB) m = fmin(m, x[i]);
+    sh[threadIdx.x] = m;
+    __syncthreads();
+    for (int w = RB / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) sh[threadIdx.x] = fmin(sh[threadIdx.x], sh[threadIdx.x + w]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+
+int cem_device_min(cem_ctx* c, const double* x, int64_t n, double* out) {
+    const int nb = (int)std::min<int64_t>(RG, std::max<int64_t>(1, (n + RB - 1) / RB));
+    cem_pdl(c->stream, k_min_partial, nb, RB, x, n, c->red_part);
+    cem_pdl(c->stream, k_min_partial, 1, RB, (const double*)c->red_part, (int64_t)nb, c->red_out);
+    cem_launched(c, 2);
+    CEM_CK(c, cudaGetLastError());
+    CEM_CK(c, cudaMemcpyAsync(c->hred, c->red_out, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CEM_CK(c, cudaStreamSynchronize(c->stream));
+    *out = c->hred[0];
     return CEM_OK;
 }
 
