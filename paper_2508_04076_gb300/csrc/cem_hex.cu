@@ -31,6 +31,36 @@ __device__ __constant__ signed char HEX_XI_C[8][3] = {{-1, -1, -1}, {1, -1, -1},
 __device__ __constant__ signed char HEX_EDGE_C[12][2] = {{0, 1}, {1, 2}, {2, 3}, {3, 0}, {4, 5}, {5, 6},
                                                          {6, 7}, {7, 4}, {0, 4}, {1, 5}, {2, 6}, {3, 7}};
 
+// The same tables as compile-time functions, and dN_i/dxi_c at the midpoint of edge l
+// (natural coordinates in {-1, 0, 1}, so every value is 0, +-1/8, +-1/4 or +-1/2).  The
+// strain and force kernels unroll their loops over edge points and nodes, so these fold to
+// constants and the zero terms drop out.
+// natural coordinate c of node i, and the two nodes of edge l (the tables above, as functions)
+__host__ __device__ constexpr int hex_xi(int i, int c) {
+    return c == 0 ? ((i == 1 || i == 2 || i == 5 || i == 6) ? 1 : -1)
+                  : (c == 1 ? ((i == 2 || i == 3 || i == 6 || i == 7) ? 1 : -1) : (i >= 4 ? 1 : -1));
+}
+__host__ __device__ constexpr int hex_edge(int l, int e) {
+    return l < 4 ? (e == 0 ? l : (l + 1) % 4) : (l < 8 ? (e == 0 ? l : 4 + (l - 3) % 4) : (e == 0 ? l - 8 : l - 4));
+}
+__host__ __device__ constexpr double hex_ref_grad(int l, int i, int c) {
+    const int p = hex_edge(l, 0), q = hex_edge(l, 1);
+    const double x = 0.5 * (hex_xi(p, 0) + hex_xi(q, 0));
+    const double y = 0.5 * (hex_xi(p, 1) + hex_xi(q, 1));
+    const double z = 0.5 * (hex_xi(p, 2) + hex_xi(q, 2));
+    const double a = hex_xi(i, 0), b = hex_xi(i, 1), cc = hex_xi(i, 2);
+    return c == 0 ? 0.125 * a * (1.0 + b * y) * (1.0 + cc * z)
+                  : (c == 1 ? 0.125 * b * (1.0 + a * x) * (1.0 + cc * z) : 0.125 * cc * (1.0 + a * x) * (1.0 + b * y));
+}
+// the functions reproduce the tables
+static_assert(hex_xi(0, 0) == -1 && hex_xi(2, 1) == 1 && hex_xi(5, 0) == 1 && hex_xi(7, 1) == 1 && hex_xi(3, 2) == -1 &&
+                  hex_xi(4, 2) == 1 && hex_xi(6, 0) == 1 && hex_xi(3, 0) == -1,
+              "hex node coordinates");
+static_assert(hex_edge(3, 0) == 3 && hex_edge(3, 1) == 0 && hex_edge(7, 0) == 7 && hex_edge(7, 1) == 4 &&
+                  hex_edge(4, 1) == 5 && hex_edge(8, 0) == 0 && hex_edge(8, 1) == 4 && hex_edge(11, 0) == 3 &&
+                  hex_edge(11, 1) == 7 && hex_edge(1, 1) == 2,
+              "hex edges");
+
 // dN_i/dxi at the natural point (x, y, z)
 __device__ __forceinline__ void grad_nat(int i, double x, double y, double z, double g[3]) {
     const double a = HEX_XI_C[i][0], b = HEX_XI_C[i][1], c = HEX_XI_C[i][2];
@@ -184,24 +214,18 @@ __global__ void __launch_bounds__(BS) k_hex_strain(const double* __restrict__ u,
             const R ci = hg[(108 + 3 * i + r) * Tc + j];
             for (int a = 0; a < 3; ++a) C[a][r] += d[i][a] * ci;
         }
-#pragma unroll 1
+#pragma unroll
     for (int l = 0; l < 12; ++l) {
-        const int p = HEX_EDGE_C[l][0], q = HEX_EDGE_C[l][1];
-        const R x = R(0.5) * (HEX_XI_C[p][0] + HEX_XI_C[q][0]);
-        const R y = R(0.5) * (HEX_XI_C[p][1] + HEX_XI_C[q][1]);
-        const R z = R(0.5) * (HEX_XI_C[p][2] + HEX_XI_C[q][2]);
-        R D[3][3] = {};   // D[a][c] = sum_i d_i[a] dN_i/dxi_c(G_l)
-        for (int i = 1; i < 8; ++i) {
-            const R a = HEX_XI_C[i][0], b = HEX_XI_C[i][1], c = HEX_XI_C[i][2];
-            const R g0 = R(0.125) * a * (R(1) + b * y) * (R(1) + c * z);
-            const R g1 = R(0.125) * b * (R(1) + a * x) * (R(1) + c * z);
-            const R g2 = R(0.125) * c * (R(1) + a * x) * (R(1) + b * y);
-            for (int aa = 0; aa < 3; ++aa) {
-                D[aa][0] += d[i][aa] * g0;
-                D[aa][1] += d[i][aa] * g1;
-                D[aa][2] += d[i][aa] * g2;
+        R D[3][3] = {};   // D[a][c] = sum_i d_i[a] dN_i/dxi_c(G_l), constant gradients, zero terms skipped
+#pragma unroll
+        for (int i = 1; i < 8; ++i)
+#pragma unroll
+            for (int cc = 0; cc < 3; ++cc) {
+                const R g = (R)hex_ref_grad(l, i, cc);
+                if (g != R(0))
+#pragma unroll
+                    for (int aa = 0; aa < 3; ++aa) D[aa][cc] += d[i][aa] * g;
             }
-        }
         R M[3][3];
         for (int c = 0; c < 3; ++c)
             for (int r = 0; r < 3; ++r) M[c][r] = hg[(9 * l + 3 * c + r) * Tc + j];
@@ -234,7 +258,7 @@ __global__ void __launch_bounds__(BS) k_hex_force(const R* __restrict__ sig, con
     if (j >= T) return;
     R f[8][3] = {};
     R Ssum[6] = {};
-#pragma unroll 1
+#pragma unroll
     for (int l = 0; l < 12; ++l) {
         const int64_t k = t2e[l * Tc + j];
         R s[6];
@@ -256,17 +280,16 @@ __global__ void __launch_bounds__(BS) k_hex_force(const R* __restrict__ sig, con
         R Pm[3][3];   // P[a][c] = sum_r S[a][r] M[c][r]
         for (int a = 0; a < 3; ++a)
             for (int c = 0; c < 3; ++c) Pm[a][c] = S[a][0] * M[c][0] + S[a][1] * M[c][1] + S[a][2] * M[c][2];
-        const int p = HEX_EDGE_C[l][0], q2 = HEX_EDGE_C[l][1];
-        const R x = R(0.5) * (HEX_XI_C[p][0] + HEX_XI_C[q2][0]);
-        const R y = R(0.5) * (HEX_XI_C[p][1] + HEX_XI_C[q2][1]);
-        const R z = R(0.5) * (HEX_XI_C[p][2] + HEX_XI_C[q2][2]);
-        for (int i = 0; i < 8; ++i) {
-            const R a = HEX_XI_C[i][0], b = HEX_XI_C[i][1], c = HEX_XI_C[i][2];
-            const R g0 = R(0.125) * a * (R(1) + b * y) * (R(1) + c * z);
-            const R g1 = R(0.125) * b * (R(1) + a * x) * (R(1) + c * z);
-            const R g2 = R(0.125) * c * (R(1) + a * x) * (R(1) + b * y);
-            for (int aa = 0; aa < 3; ++aa) f[i][aa] += Pm[aa][0] * g0 + Pm[aa][1] * g1 + Pm[aa][2] * g2;
-        }
+        // f_i += P g_i(G_l) with the constant gradients, zero terms skipped
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+            for (int cc = 0; cc < 3; ++cc) {
+                const R g = (R)hex_ref_grad(l, i, cc);
+                if (g != R(0))
+#pragma unroll
+                    for (int aa = 0; aa < 3; ++aa) f[i][aa] += Pm[aa][cc] * g;
+            }
     }
     // correction: f_i += (sum_l sigma_l) . c_i
     const R S[3][3] = {{Ssum[0], Ssum[3], Ssum[5]}, {Ssum[3], Ssum[1], Ssum[4]}, {Ssum[5], Ssum[4], Ssum[2]}};
