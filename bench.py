@@ -664,21 +664,29 @@ def run_cem(a):
 
     ens = _leg("ensemble", ens_leg) if (a.workload == "block" and a.ensemble_steps > 0) else None
 
-    # steps launched as one captured CUDA graph (cem_step_graph) against eager launches, on
-    # fixed topology (splitting off after the notch): a small specimen, where launches
-    # dominate, and the 256-specimen ensemble
+    # steps launched as one captured CUDA graph (cem_step_graph) against eager launches: on
+    # fixed topology (splitting off after the notch) for a small specimen, where launches
+    # dominate, and the 256-specimen ensemble; and with splitting on for the benchmark block,
+    # whose notch leaves crack-front elements, against eager steps that read the split
+    # decision after every step (step batch 1) and in batches (the default)
     def graph_leg():
         from cem_inputs import plate_small
-        out = {"note": "fixed topology (split_enabled = 0 after the notch); graph: one capture, then the "
-                       "timed replay; the same kernels and arguments as eager stepping (bit-identical)"}
-        cases = [("notched_block_20x8x2", plate_small(), 2000, "fp64")]
+        out = {"note": "graph: one capture, then the timed replay; the same kernels and arguments as eager "
+                       "stepping (bit-identical).  split_enabled = 0 after the notch, except for the "
+                       "block with crack fronts, where a split would end the replay (none occurs in the "
+                       "timed steps)"}
+        cases = [("notched_block_20x8x2", plate_small(), 2000, "fp64", False)]
         if a.ensemble_steps > 0:
-            cases.append(("ensemble_256_seed4", _workload("ensemble"), a.ensemble_steps, "mixed"))
-        for name, wk, steps, prec in cases:
+            cases.append(("ensemble_256_seed4", _workload("ensemble"), a.ensemble_steps, "mixed", False))
+        cases.append((w.name + "_crack_fronts", w, 100, "fp64", True))
+        for name, wk, steps, prec, fronts in cases:
             res = {"tets": wk.n_tets, "steps": steps, "precision": prec}
-            for mode in ("eager", "graph"):
-                sg = CEM.from_workload(wk, device=dev, split_enabled=False, precision=prec)
-                run = sg.step if mode == "eager" else sg.step_graph
+            for mode in (("eager_per_step", "eager", "graph") if fronts else ("eager", "graph")):
+                sg = CEM.from_workload(wk, device=dev, split_enabled=fronts, precision=prec,
+                                       split_capacity=a.split_capacity if fronts else 0)
+                if mode == "eager_per_step":
+                    sg.set_step_batch(1)
+                run = sg.step_graph if mode == "graph" else sg.step
                 run(steps)   # warm-up (and the capture)
                 barrier()
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -688,8 +696,12 @@ def run_cem(a):
                 torch.cuda.synchronize()
                 t_ms = e0.elapsed_time(e1)
                 res[mode] = {"value": wk.n_tets * steps / (t_ms * 1e-3), "ms_per_step": t_ms / steps}
+                if fronts:
+                    res[mode]["splits"] = sg.energy()["n_split"]
                 sg.close()
             res["graph_speedup"] = res["graph"]["value"] / res["eager"]["value"]
+            if fronts:
+                res["batch_speedup"] = res["eager"]["value"] / res["eager_per_step"]["value"]
             out[name] = res
         return out
 

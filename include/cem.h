@@ -199,8 +199,11 @@ int cem_set_material(cem_ctx* ctx, double rho, double nu,
 /* Advance n >= 0 explicit steps (Eqs. 13-15, beta = 0, gamma = 1/2).  After
  * each step the energy release rates G_I, G_II (Eqs. 16-18) of every
  * crack-front element are evaluated on the end-of-step state, and every
- * element with max(G_I, G_II) > Gc is split (Sec. 3).  Errors: CEM_ESTATE
- * (no material); CEM_ECAPACITY: when the split capacity would be exceeded the
+ * element with max(G_I, G_II) > Gc is split (Sec. 3).  While crack-front
+ * elements exist, the steps are launched in batches and the host reads the
+ * split decision once per batch (see cem_set_step_batch); the results are
+ * those of one step at a time, bit for bit.  Errors: CEM_ESTATE (no
+ * material); CEM_ECAPACITY: when the split capacity would be exceeded the
  * splits of that step are not applied and the state is the step's
  * end-of-step kinematics (the context stays usable); when a storage
  * capacity (new edges, nodes, fan or incidence pool) runs out while splits
@@ -210,18 +213,32 @@ int cem_set_material(cem_ctx* ctx, double rho, double nu,
  * CEM_ECUDA. */
 int cem_step(cem_ctx* ctx, int64_t n);
 
+/* Longest step batch of cem_step (no counterpart in the paper).  While
+ * crack-front elements exist, cem_step launches up to max_steps steps back to
+ * back.  The front evaluation of each step leaves its split decision on the
+ * device; when one decides splits, the kernels of the batch's later steps
+ * return at once without touching the state, the host applies the splits
+ * after that step and continues from there.  A batch's length doubles after
+ * every batch without a split, up to max_steps, and restarts at 1 after a
+ * split.  max_steps = 1 reads the decision after every step.  Default 32.
+ * Errors: CEM_EINVAL (max_steps < 1). */
+int cem_set_step_batch(cem_ctx* ctx, int64_t max_steps);
+
 /* The same n steps as cem_step, launched as one CUDA graph (no counterpart in
- * the paper; the batched-ensemble pattern of SURVEY NEXT-2 for a topology that
- * does not change).  Valid only while no step can split: splitting disabled
- * (split_enabled = 0; the notch still applies at creation) or no crack-front
- * element; the split path sizes its launches from counts the host reads every
- * step and cannot run inside a graph.  The graph is captured on a private
- * stream on the first call and re-captured when n, the mesh sizes or the
- * launch variants change; later calls replay it on the context's stream.
- * Results are bit-identical to cem_step.  Synchronises once at the end (to
- * check for non-finite displacements).  Errors: CEM_ESTATE (no material; a
- * context with crack-front elements and splitting on; prescribed velocities,
- * whose values depend on the step number; kernel timing on), CEM_ENONFINITE,
+ * the paper).  Without crack-front elements (splitting disabled with
+ * split_enabled = 0, the notch still applied at creation, or none left) the
+ * graph holds the n steps.  With them it holds one batch of n steps as
+ * cem_set_step_batch describes: when a step's front evaluation decides
+ * splits, the graph's later steps return at once, the host applies the
+ * splits, and the rest of the n steps run as cem_step runs them (the
+ * topology changed, so that part is not replayed).  The graph is captured on
+ * a private stream on the first call and re-captured when n, the mesh sizes,
+ * the crack-front count, the topology or the launch variants change; later
+ * calls replay it on the context's stream.  Results are bit-identical to
+ * cem_step.  Synchronises once at the end (to read the split decision and
+ * check for non-finite displacements).  Errors: CEM_ESTATE (no material;
+ * prescribed velocities, whose values depend on the step number; kernel
+ * timing on), CEM_ENONFINITE, CEM_ETIMEOUT, CEM_ECAPACITY (as cem_step),
  * CEM_ECUDA. */
 int cem_step_graph(cem_ctx* ctx, int64_t n);
 

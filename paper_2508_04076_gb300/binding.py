@@ -25,7 +25,7 @@ FIELD = {"u": 0, "v": 1, "a": 2, "X": 3}
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_void_p)
 
-EXPORTED = ["cem_mesh_create", "cem_set_material", "cem_step", "cem_step_graph", "cem_energy", "cem_crack_state",
+EXPORTED = ["cem_mesh_create", "cem_set_material", "cem_step", "cem_set_step_batch", "cem_step_graph", "cem_energy", "cem_crack_state",
             "cem_get_field", "cem_info", "cem_energy_instance", "cem_adjoint", "cem_profile", "cem_profile_read",
             "cem_autotune", "cem_tune_get", "cem_tune_set", "cem_save", "cem_load", "cem_set_wait_limit",
             "cem_wait_probe", "cem_set_reorder", "cem_reorder_nodes", "cem_probe_fp64_fma", "cem_probe_split",
@@ -85,6 +85,7 @@ def load_library(build: bool = True):
                                      C.POINTER(C.c_double), C.c_int64]
     lib.cem_step.argtypes = [P, C.c_int64]
     lib.cem_step_graph.argtypes = [P, C.c_int64]
+    lib.cem_set_step_batch.argtypes = [P, C.c_int64]
     lib.cem_energy.argtypes = [P, C.POINTER(Energy)]
     lib.cem_energy_instance.argtypes = [P, C.c_int64, C.POINTER(Energy)]
     lib.cem_adjoint.argtypes = [P, C.c_int64, C.c_int64, C.c_double, C.POINTER(C.c_double),
@@ -301,9 +302,15 @@ class CEM:
     def step(self, n=1):
         self._check(self._lib.cem_step(self._ctx, int(n)))
 
+    def set_step_batch(self, max_steps=32):
+        """Longest batch of steps launched before the host reads the split decision
+        (cem_set_step_batch); 1 reads it after every step."""
+        self._check(self._lib.cem_set_step_batch(self._ctx, int(max_steps)))
+
     def step_graph(self, n=1):
-        """n steps as one captured CUDA graph (fixed topology only: splitting off or no
-        crack-front element); bit-identical to step(n)."""
+        """n steps as one captured CUDA graph (cem_step_graph): with crack-front elements
+        the graph ends at the first step that splits and the rest runs as step() runs it;
+        bit-identical to step(n)."""
         self._check(self._lib.cem_step_graph(self._ctx, int(n)))
 
     def energy(self) -> dict:

@@ -867,7 +867,21 @@ void prof_end(cem_ctx* c, int id, cudaEvent_t a) {
     cudaEvent_t b = ev_get(c);
     if (!b) return;
     cudaEventRecord(b, c->stream);
-    c->ev_pending.push_back({id, a, b});
+    c->ev_pending.push_back({id, a, b, c->step});
+}
+
+// Timing events of batch steps from `from` on (they returned at once) go back to the pool.
+void prof_drop_from(cem_ctx* c, int64_t from) {
+    size_t k = 0;
+    for (auto& r : c->ev_pending) {
+        if (r.step >= from) {
+            c->ev_pool.push_back(r.a);
+            c->ev_pool.push_back(r.b);
+        } else {
+            c->ev_pending[k++] = r;
+        }
+    }
+    c->ev_pending.resize(k);
 }
 
 int prof_resolve(cem_ctx* c) {
@@ -906,16 +920,20 @@ struct NvtxRange {
 // both and joins before the split decision is read.  Mixed precision: the node update
 // advances u, so the evaluation forms the end-of-step displacement from the stored
 // u, v, a as the node update does (FrontU) and joins before the node update.
+int make_side_stream(cem_ctx* c) {
+    if (c->side_stream) return CEM_OK;
+    // the highest priority: the block scheduler then starts the front's few blocks as
+    // soon as an SM has room, ahead of the force kernel's blocks still waiting
+    int lo = 0, hi = 0;
+    CEM_CK(c, cudaDeviceGetStreamPriorityRange(&lo, &hi));
+    CEM_CK(c, cudaStreamCreateWithPriority(&c->side_stream, cudaStreamNonBlocking, hi));
+    CEM_CK(c, cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
+    CEM_CK(c, cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
+    return CEM_OK;
+}
+
 int launch_front_side(cem_ctx* c) {
-    if (!c->side_stream) {
-        // the highest priority: the block scheduler then starts the front's few blocks as
-        // soon as an SM has room, ahead of the force kernel's blocks still waiting
-        int lo = 0, hi = 0;
-        CEM_CK(c, cudaDeviceGetStreamPriorityRange(&lo, &hi));
-        CEM_CK(c, cudaStreamCreateWithPriority(&c->side_stream, cudaStreamNonBlocking, hi));
-        CEM_CK(c, cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
-        CEM_CK(c, cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
-    }
+    if (int rc = make_side_stream(c)) return rc;
     CEM_CK(c, cudaEventRecord(c->ev_fork, c->stream));
     CEM_CK(c, cudaStreamWaitEvent(c->side_stream, c->ev_fork, 0));
     cudaStream_t main = c->stream;
@@ -933,7 +951,9 @@ int launch_front_side(cem_ctx* c) {
     return CEM_OK;
 }
 
-int run_step(cem_ctx* c) {
+// Launches one step; with crack-front elements the split decision is left on the
+// device (CNT_SPLIT) for run_step or the end of a batch.
+int launch_step(cem_ctx* c) {
     NvtxRange range("cem.step");
     if (c->tune_auto)
         if (int rc = cem_tune_maybe(c)) return rc;
@@ -952,22 +972,85 @@ int run_step(cem_ctx* c) {
     TIMED(c, CEM_KERNEL_NODE_UPDATE, cem_launch_node_update(c, 0));
     if (int rc = cem_launch_prescribe(c, c->step + 1)) return rc;
     c->step += 1;
+    if (fronts && !mix) CEM_CK(c, cudaStreamWaitEvent(c->stream, c->ev_join, 0));
+    return CEM_OK;
+}
+
+// Applies the splits the front evaluation of the step just run decided (counters read).
+int apply_step_splits(cem_ctx* c) {
+    if (c->hcount[CNT_ERR] & DERR_SCAN_WAIT) return cem_fail(c, CEM_ETIMEOUT, "a scan's bounded look-back wait gave up");
+    const int64_t S = c->hcount[CNT_SPLIT];
+    if (S <= 0) return CEM_OK;
+    if (c->n_split_all + S > c->S_cap)
+        return cem_fail(c, CEM_ECAPACITY, "split capacity exhausted; splits of this step not applied");
+    NvtxRange split("cem.split");
+    int rc;
+    // the splits, then a renumbering of node storage when the node count has grown enough
+    TIMED(c, CEM_KERNEL_SPLIT, (rc = cem_apply_splits(c, S, c->step, 1)) ? rc : cem_reorder_maybe(c));
+    return CEM_OK;
+}
+
+int run_step(cem_ctx* c, bool* split = nullptr) {
+    const bool fronts = c->split_enabled && c->n_cand > 0;
+    if (int rc = launch_step(c)) return rc;
     if (fronts) {
-        if (!mix) CEM_CK(c, cudaStreamWaitEvent(c->stream, c->ev_join, 0));
-        int rc;
-        if ((rc = sync_counts(c))) return rc;
-        if (c->hcount[CNT_ERR] & DERR_SCAN_WAIT)
-            return cem_fail(c, CEM_ETIMEOUT, "a scan's bounded look-back wait gave up");
-        const int64_t S = c->hcount[CNT_SPLIT];
-        if (S > 0) {
-            if (c->n_split_all + S > c->S_cap)
-                return cem_fail(c, CEM_ECAPACITY, "split capacity exhausted; splits of this step not applied");
-            NvtxRange split("cem.split");
-            // the splits, then a renumbering of node storage when the node count has grown enough
-            TIMED(c, CEM_KERNEL_SPLIT, (rc = cem_apply_splits(c, S, c->step, 1)) ? rc : cem_reorder_maybe(c));
-        }
+        if (int rc = sync_counts(c)) return rc;
+        if (split) *split = c->hcount[CNT_SPLIT] > 0;
+        if (int rc = apply_step_splits(c)) return rc;
     }
     if (c->ev_pending.size() > 4096) return prof_resolve(c);
+    return CEM_OK;
+}
+
+// A batch: B steps launched back to back with crack-front elements, the split decision
+// read once at the end.  Step r of the batch is gated (StepGate): when the front
+// evaluation of step r decides splits, the kernels of steps r+1 .. B-1 return at once,
+// and the host applies the splits after step r, as run_step would.  *ran = steps run.
+int run_batch(cem_ctx* c, int64_t B, int64_t* ran, bool* split) {
+    const int64_t step0 = c->step;
+    CEM_CK(c, cudaMemsetAsync(c->dcount + CNT_HALT, 0, sizeof(long long), c->stream));
+    int rc = CEM_OK;
+    for (int64_t r = 0; r < B && rc == CEM_OK; ++r) {
+        c->spec_r = r;
+        rc = launch_step(c);
+    }
+    c->spec_r = -1;
+    if (rc) return rc;
+    if ((rc = sync_counts(c))) return rc;
+    const int64_t h = c->hcount[CNT_HALT];
+    *ran = h > 0 ? h : B;
+    *split = h > 0;
+    c->step = step0 + *ran;
+    prof_drop_from(c, c->step);
+    if (h > 0) {
+        if ((rc = apply_step_splits(c))) return rc;
+    } else if (c->hcount[CNT_ERR] & DERR_SCAN_WAIT) {
+        return cem_fail(c, CEM_ETIMEOUT, "a scan's bounded look-back wait gave up");
+    }
+    if (c->ev_pending.size() > 4096) return prof_resolve(c);
+    return CEM_OK;
+}
+
+// n steps: one at a time without crack-front elements (no host read between steps);
+// with them, in batches whose length doubles after every batch without a split (up to
+// spec_max) and falls back to 1 after a split.
+int run_steps(cem_ctx* c, int64_t n) {
+    for (int64_t q = 0; q < n;) {
+        const bool fronts = c->split_enabled && c->n_cand > 0;
+        const int64_t B = std::min(c->spec_len, n - q);
+        int64_t ran = 1;
+        bool split = false;
+        if (fronts && B > 1) {
+            if (int rc = run_batch(c, B, &ran, &split)) return rc;
+        } else if (int rc = run_step(c, &split)) {
+            return rc;
+        }
+        q += ran;
+        if (fronts) {
+            if (split) c->spec_len = 1;
+            else if (B == c->spec_len) c->spec_len = std::min(2 * c->spec_len, c->spec_max);
+        }
+    }
     return CEM_OK;
 }
 
@@ -1046,24 +1129,32 @@ int cem_step(cem_ctx* c, int64_t n) {
     if (!c || n < 0) return CEM_EINVAL;
     if (!c->material) return cem_fail(c, CEM_ESTATE, "cem_set_material must be called before cem_step");
     if (int rc = select_device(c)) return rc;
-    for (int64_t q = 0; q < n; ++q)
-        if (int rc = run_step(c)) return rc;
+    if (int rc = run_steps(c, n)) return rc;
     if (int rc = cem_launch_check_finite(c)) return rc;
     if (int rc = sync_counts(c)) return rc;
     if (c->hcount[CNT_SCRATCH1]) return cem_fail(c, CEM_ENONFINITE, "non-finite displacement");
     return prof_resolve(c);
 }
 
-// n steps of a context whose topology cannot change over them (splitting off, or
-// no crack-front element), launched as one CUDA graph.  The graph is captured
-// on a private stream the first time (or when the sizes, the launch variants or
-// n change) and replayed on the context's stream afterwards; the kernels and
-// their arguments are those cem_step launches, so the results are bit-identical.
+int cem_set_step_batch(cem_ctx* c, int64_t max_steps) {
+    if (!c) return CEM_EINVAL;
+    if (max_steps < 1) return cem_fail(c, CEM_EINVAL, "max_steps must be at least 1");
+    c->spec_max = max_steps;
+    c->spec_len = std::min(c->spec_len, max_steps);
+    return CEM_OK;
+}
+
+// n steps launched as one CUDA graph.  Without crack-front elements (splitting off, or
+// none left) the topology cannot change over the steps.  With them the graph holds one
+// batch of n gated steps (see run_batch): when the front evaluation of a step decides
+// splits, the later steps of the graph return at once, the host applies the splits, and
+// the rest of the call runs as cem_step runs it.  The graph is captured on a private
+// stream the first time (or when n, the sizes, the topology or the launch variants
+// change) and replayed on the context's stream; its kernels and arguments are those
+// cem_step launches, so the results are bit-identical.
 int cem_step_graph(cem_ctx* c, int64_t n) {
     if (!c || n < 0) return CEM_EINVAL;
     if (!c->material) return cem_fail(c, CEM_ESTATE, "cem_set_material must be called before cem_step_graph");
-    if (c->split_enabled && c->n_cand > 0)
-        return cem_fail(c, CEM_ESTATE, "crack-front elements need a host decision every step: use cem_step");
     if (c->n_dir > 0)
         return cem_fail(c, CEM_ESTATE, "prescribed velocities depend on the step number: use cem_step");
     if (c->prof) return cem_fail(c, CEM_ESTATE, "kernel timing is on (cem_profile): use cem_step");
@@ -1071,25 +1162,38 @@ int cem_step_graph(cem_ctx* c, int64_t n) {
     if (n == 0) return CEM_OK;
     if (c->tune_auto)   // settle the launch variants for the current sizes before capturing them
         if (int rc = cem_tune_maybe(c)) return rc;
-    const int64_t key[8] = {n, c->T, c->E, c->N, c->tune[0], c->tune[1], c->tune[2], c->tune[3]};
-    if (!c->graph_exec || !std::equal(key, key + 8, c->graph_key)) {
+    const bool fronts = c->split_enabled && c->n_cand > 0;
+    constexpr int K = cem_ctx::GRAPH_KEY;
+    const int64_t key[K] = {n,      c->T,           c->E,       c->N,       c->n_cand,  c->n_act_orig,
+                            fronts, c->topo_version, c->tune[0], c->tune[1], c->tune[2], c->tune[3]};
+    if (!c->graph_exec || !std::equal(key, key + K, c->graph_key)) {
         if (c->graph_exec) {
             CEM_CK(c, cudaGraphExecDestroy(c->graph_exec));
             c->graph_exec = nullptr;
         }
         if (!c->cap_stream) CEM_CK(c, cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+        if (fronts)
+            if (int rc = make_side_stream(c)) return rc;
         CEM_CK(c, cudaStreamSynchronize(c->stream));   // the state the graph starts from is in place
         const cudaStream_t main = c->stream;
         const int64_t step0 = c->step, launch0 = c->n_launch;
         c->stream = c->cap_stream;
+        c->capturing = true;
         int rc = CEM_OK;
         cudaGraph_t g = nullptr;
         cudaError_t e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
-            for (int64_t q = 0; q < n && rc == CEM_OK; ++q) rc = run_step(c);
-            e = cudaStreamEndCapture(c->cap_stream, &g);
+            if (fronts) e = cudaMemsetAsync(c->dcount + CNT_HALT, 0, sizeof(long long), c->cap_stream);
+            for (int64_t q = 0; q < n && rc == CEM_OK && e == cudaSuccess; ++q) {
+                c->spec_r = fronts ? q : -1;
+                rc = launch_step(c);
+            }
+            c->spec_r = -1;
+            const cudaError_t e2 = cudaStreamEndCapture(c->cap_stream, &g);
+            if (e == cudaSuccess) e = e2;
         }
         c->stream = main;
+        c->capturing = false;
         c->step = step0;   // capture launched nothing: the steps run at replay
         c->n_graph_launch = c->n_launch - launch0;
         c->n_launch = launch0;
@@ -1097,18 +1201,35 @@ int cem_step_graph(cem_ctx* c, int64_t n) {
             if (g) cudaGraphDestroy(g);
             return rc;
         }
-        if (e != cudaSuccess) return cem_cuda_fail(c, e, "stream capture of the step graph");
+        if (e != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            return cem_cuda_fail(c, e, "stream capture of the step graph");
+        }
         e = cudaGraphInstantiate(&c->graph_exec, g, 0);
         cudaGraphDestroy(g);
         if (e != cudaSuccess) {
             c->graph_exec = nullptr;
             return cem_cuda_fail(c, e, "cudaGraphInstantiate");
         }
-        std::copy(key, key + 8, c->graph_key);
+        std::copy(key, key + K, c->graph_key);
     }
     CEM_CK(c, cudaGraphLaunch(c->graph_exec, c->stream));
-    c->step += n;
     cem_launched(c, (int)c->n_graph_launch);
+    if (!fronts) {
+        c->step += n;
+    } else {
+        if (int rc = sync_counts(c)) return rc;
+        const int64_t h = c->hcount[CNT_HALT];
+        const int64_t ran = h > 0 ? h : n;
+        c->step += ran;
+        if (h > 0) {
+            if (int rc = apply_step_splits(c)) return rc;
+            c->spec_len = 1;
+            if (int rc = run_steps(c, n - ran)) return rc;   // the topology changed: no replay
+        } else if (c->hcount[CNT_ERR] & DERR_SCAN_WAIT) {
+            return cem_fail(c, CEM_ETIMEOUT, "a scan's bounded look-back wait gave up");
+        }
+    }
     if (int rc = cem_launch_check_finite(c)) return rc;
     if (int rc = sync_counts(c)) return rc;
     if (c->hcount[CNT_SCRATCH1]) return cem_fail(c, CEM_ENONFINITE, "non-finite displacement");

@@ -120,6 +120,7 @@ enum {
     CNT_SCRATCH1,
     CNT_FRONT_Q,       // queued edge projections of a front evaluation (0 between evaluations)
     CNT_ACT_ORIG,      // active original elements listed in act_orig
+    CNT_HALT,          // step batches: 1 + the batch step whose front evaluation decided splits (0: none)
     CNT_COUNT
 };
 
@@ -165,10 +166,12 @@ struct cem_ctx {
     // once many originals have split (n_act_orig < 0: no list, every slot is visited)
     int* act_orig = nullptr;
     int64_t n_act_orig = -1;
-    // cem_step_graph: a captured n-step graph of a fixed-topology context and what it was captured for
+    // cem_step_graph: a captured n-step graph and what it was captured for (n, sizes,
+    // front count, active-original count, fronts, topology version, launch variants)
+    static constexpr int GRAPH_KEY = 12;
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
-    int64_t graph_key[8] = {-1, -1, -1, -1, -1, -1, -1, -1};
+    int64_t graph_key[GRAPH_KEY] = {-1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1};
     int64_t n_graph_launch = 0;   // kernels in one replay of the captured graph
     int device = 0;
     cem_alloc_fn alloc = nullptr;
@@ -281,9 +284,33 @@ struct cem_ctx {
     double prof_ms[CEM_KERNEL_COUNT] = {};
     int64_t prof_n[CEM_KERNEL_COUNT] = {};
     std::vector<cudaEvent_t> ev_pool;
-    struct EvRec { int id; cudaEvent_t a, b; };
+    struct EvRec { int id; cudaEvent_t a, b; int64_t step; };
     std::vector<EvRec> ev_pending;
+    // step batches (cem_step while crack-front elements exist): the steps of a batch are
+    // launched back to back and the host reads the split decision once, after the batch
+    int64_t spec_r = -1;      // step of the batch being launched (-1: not in a batch)
+    int64_t spec_max = 32;    // longest batch (1: the host reads the decision after every step)
+    int64_t spec_len = 1;     // length of the next batch: doubles after a batch without split
+    bool capturing = false;   // launches go into a CUDA graph (cem_step_graph)
+    int64_t topo_version = 0; // changes with the topology or the buffers the step kernels read
 };
+
+// Gate of a batch step (see cem_ctx::spec_r): a kernel of batch step s returns at once
+// when an earlier step of the batch decided splits.  *halt is 1 + that step (0: none);
+// it is written by the front evaluation of that step, whose kernels finish before any
+// kernel of a later step starts, so every block of a kernel reads the same value.
+struct StepGate {
+    long long* halt;   // nullptr: not in a batch
+    long long s;
+    __device__ __forceinline__ bool stop() const {
+        if (!halt) return false;
+        const long long h = __ldcg(halt);
+        return h != 0 && h <= s;
+    }
+};
+static inline StepGate cem_gate(const cem_ctx* c) {
+    return c->spec_r >= 0 ? StepGate{c->dcount + CNT_HALT, c->spec_r} : StepGate{nullptr, 0};
+}
 
 static inline void cem_launched(cem_ctx* c, int k = 1) { c->n_launch += k; }
 
@@ -372,9 +399,9 @@ int cem_hex_force(cem_ctx* c);
 int64_t cem_hex_geometry_values();
 
 // ---------------------------------------------------------------- crack path (cem_crack.cu)
-int cem_launch_front_G(cem_ctx* c, int predict_u);
-int cem_refresh_act_orig(cem_ctx* c);
-int cem_device_min(cem_ctx* c, const double* x, int64_t n, double* out);   // min of n device doubles   // rebuild the active-original list (after a checkpoint load)   // predict_u: read u + dt v + dt^2/2 a (see FrontU)
+int cem_launch_front_G(cem_ctx* c, int predict_u);   // predict_u: read u + dt v + dt^2/2 a (see FrontU)
+int cem_refresh_act_orig(cem_ctx* c);   // rebuild the active-original list (after a checkpoint load)
+int cem_device_min(cem_ctx* c, const double* x, int64_t n, double* out);   // min of n device doubles
 int cem_defrag_lists(cem_ctx* c, int kind);   // rewrite fan (0) or incidence (1) lists in index order
 int cem_renumber_nodes(cem_ctx* c);           // Morton-order node storage (cem_reorder.cu)
 int cem_reorder_maybe(cem_ctx* c);            // renumber when the growth trigger is reached

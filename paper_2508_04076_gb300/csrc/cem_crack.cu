@@ -284,8 +284,9 @@ __global__ void __launch_bounds__(FB) k_front_faces(const int* __restrict__ cand
                                                     int64_t Nc, int* __restrict__ ff_mask,
                                                     double* __restrict__ ff_prod, double* __restrict__ ff_nrm,
                                                     int* __restrict__ ff_edge, int64_t cap4,
-                                                    int* __restrict__ items, long long* __restrict__ qn) {
+                                                    int* __restrict__ items, long long* __restrict__ qn, StepGate g) {
     CEM_PDL_ENTRY();
+    if (g.stop()) return;   // a later step of a batch that splits: the queue stays empty
     const int tid = blockIdx.x * FB + threadIdx.x;   // face record 4 ci + f of this chunk
     const int ci = tid >> 2, f = tid & 3;
     bool cut = false;
@@ -380,8 +381,10 @@ __global__ void __launch_bounds__(FS_T) k_front_small(const int* __restrict__ ca
                                                       const float* __restrict__ sig32, const double* __restrict__ Gc,
                                                       int gvar, int* __restrict__ split_list,
                                                       uint8_t* __restrict__ split_mask, double* __restrict__ split_G,
-                                                      long long* __restrict__ count, long long* __restrict__ nk) {
+                                                      long long* __restrict__ count, long long* __restrict__ nk,
+                                                      StepGate g) {
     CEM_PDL_ENTRY();
+    if (g.stop()) return;
     __shared__ FrontFace face[4 * FRONT_SMALL];
     __shared__ int items[12 * FRONT_SMALL];
     __shared__ double sval[12 * FRONT_SMALL];
@@ -436,6 +439,7 @@ __global__ void __launch_bounds__(FS_T) k_front_small(const int* __restrict__ ca
                 ++S;
             }
         *count = S;
+        if (S > 0 && g.halt) *g.halt = g.s + 1;   // later steps of the batch wait for the split
     }
 }
 
@@ -1299,6 +1303,7 @@ int sync_counts(cem_ctx* c) {
 
 // Rebuild every list of `kind` into the spare pool, compactly.
 int defrag(cem_ctx* c, int kind) {
+    ++c->topo_version;   // the pools change places
     const int64_t n = kind == 0 ? c->E : c->N;
     int* off = kind == 0 ? c->fan_off : c->inc_off;
     int* cnt = kind == 0 ? c->fan_cnt : c->inc_cnt;
@@ -1415,7 +1420,7 @@ int cem_launch_front_G(cem_ctx* c, int predict_u) {
                 (const int*)c->t2e, c->Tc, (const int*)c->face_nbr, (const uint8_t*)c->side, c->T0,
                 (const double*)c->X, U, c->Nc, (const double*)c->sig, (const float*)c->sig32,
                 (const double*)c->Gc, c->g_variant, c->split_list, c->split_mask, c->split_Gv,
-                c->dcount + CNT_SPLIT, c->dcount + CNT_SCRATCH0);
+                c->dcount + CNT_SPLIT, c->dcount + CNT_SCRATCH0, cem_gate(c));
         cem_launched(c, 1);
         CEM_CK(c, cudaGetLastError());
         return CEM_OK;
@@ -1426,7 +1431,7 @@ int cem_launch_front_G(cem_ctx* c, int predict_u) {
         long long* qn = c->dcount + CNT_FRONT_Q;
         cem_pdl(c->stream, k_front_faces, cem_grid(4 * (int64_t)nc, FB), FB, c->cand_list + c0, nc, c->conn, c->t2e,
                 c->Tc, c->face_nbr, c->side, c->T0, c->X, U, c->Nc, c->ff_mask, c->ff_prod, c->ff_nrm, c->ff_edge,
-                cap4, c->ff_item, qn);
+                cap4, c->ff_item, qn, cem_gate(c));
         cem_pdl(c->stream, k_front_proj, cem_grid(12 * (int64_t)nc, FB), FB, c->ff_item, qn, c->ff_edge, c->ff_nrm,
                 cap4, c->sig, c->sig32, c->g_variant, c->ff_s);
         cem_pdl(c->stream, k_front_pick, cem_grid(nc, FB), FB, c->cand_list + c0, nc, c->ff_mask, c->ff_prod, c->ff_s,
@@ -1436,7 +1441,7 @@ int cem_launch_front_G(cem_ctx* c, int predict_u) {
     }
     return run_scan(c, U8Load{c->dec_mask},
                     SplitStore{c->cand_list, c->dec_mask, c->dec_G, c->split_list, c->split_mask, c->split_Gv},
-                    c->n_cand, CNT_SPLIT);
+                    c->n_cand, CNT_SPLIT, cem_gate(c));
 }
 
 // The strain and force launches visit the listed active originals and then every
@@ -1535,6 +1540,7 @@ int cem_apply_splits(cem_ctx* c, int64_t S64, int64_t step, int book_energy) {
     c->n_split_all += S;
     if (book_energy) c->n_split_run += S;
     c->n_act_orig = act_list ? c->hcount[CNT_ACT_ORIG] : -1;
+    ++c->topo_version;
     return CEM_OK;
 }
 

@@ -216,6 +216,7 @@ extern "C" int cem_load(cem_ctx* c, const char* path) {
     if (!c->material) return cem_fail(c, CEM_ESTATE, "cem_set_material must be called before cem_load");
     CEM_CK(c, cudaSetDevice(c->device));
     CEM_CK(c, cudaStreamSynchronize(c->stream));
+    ++c->topo_version;
     FILE* fp = std::fopen(path, "rb");
     if (!fp) return cem_fail(c, CEM_EINVAL, "cannot open the checkpoint file");
     char tag[8];

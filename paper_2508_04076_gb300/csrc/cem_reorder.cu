@@ -224,6 +224,7 @@ int cem_renumber_nodes(cem_ctx* c) {
     if (!reorderable(c)) return cem_fail(c, CEM_ESTATE, "node renumbering needs a tetrahedral mesh with splitting");
     const int64_t N = c->N;
     if (N < 2) return CEM_OK;
+    ++c->topo_version;
     int64_t npad = 2 * RB;
     while (npad < N) npad <<= 1;
     if (!c->rn_map || !c->rn_tmp || !c->rn_keys || npad > c->rn_keys_cap)

@@ -48,8 +48,9 @@ template <class Load, class Store>
 __global__ void __launch_bounds__(SB) k_scan_single(Load ld, Store st, int64_t n, int nb,
                                                     unsigned long long* status, unsigned int* ticket,
                                                     unsigned long long epoch, long long* count, long long* err,
-                                                    long long spin_limit) {
+                                                    long long spin_limit, StepGate g) {
     CEM_PDL_ENTRY();
+    if (g.stop()) return;   // before any ticket is taken: every block returns
     __shared__ int s_bid, s_prefix;
     if (threadIdx.x == 0) s_bid = (int)atomicAdd(ticket, 1u);
     __syncthreads();
@@ -101,6 +102,8 @@ __global__ void __launch_bounds__(SB) k_scan_single(Load ld, Store st, int64_t n
             if (bid == nb - 1) {
                 *count = prefix + tot;
                 *ticket = 0u;   // every block has its ticket by now; the next call starts from 0
+                // a batch step whose scan selects items (the split decisions): later steps wait
+                if (g.halt && prefix + tot > 0) *g.halt = g.s + 1;
             }
         }
     }
@@ -119,8 +122,9 @@ __global__ void k_set_count(long long* count, long long v) {
     *count = v;
 }
 
+// gate: the scan of a batch step (see StepGate); a non-zero total then ends the batch.
 template <class Load, class Store>
-int run_scan(cem_ctx* c, Load ld, Store st, int64_t n, int slot) {
+int run_scan(cem_ctx* c, Load ld, Store st, int64_t n, int slot, StepGate gate = StepGate{nullptr, 0}) {
     if (n <= 0) {
         cem_pdl(c->stream, k_set_count, 1, 1, c->dcount + slot, 0);
         cem_launched(c);
@@ -131,8 +135,12 @@ int run_scan(cem_ctx* c, Load ld, Store st, int64_t n, int slot) {
     if (nb + 1 > c->scan_blocks_cap)
         return cem_fail(c, CEM_EINVAL, "internal: scan longer than its status buffer");
     const unsigned long long epoch = ++c->scan_epoch & ((1ull << 30) - 1);
+    // A captured graph replays its scans with the epochs of the capture: the status words
+    // of the previous replay would carry the same epoch, so they are cleared first.
+    if (c->capturing && nb > 1)
+        CEM_CK(c, cudaMemsetAsync(c->scan_status, 0, (size_t)nb * sizeof(unsigned long long), c->stream));
     cem_pdl(c->stream, (k_scan_single<Load, Store>), (unsigned)nb, SB, ld, st, n, (int)nb, c->scan_status,
-            c->scan_ticket, epoch, c->dcount + slot, c->dcount + CNT_ERR, c->wait_limit);
+            c->scan_ticket, epoch, c->dcount + slot, c->dcount + CNT_ERR, c->wait_limit, gate);
     cem_launched(c, 1);
     CEM_CK(c, cudaGetLastError());
     return CEM_OK;

@@ -129,8 +129,9 @@ __global__ void __launch_bounds__(BS) k_geometry(const double* __restrict__ X, i
 // dtn (ensembles): per-node time step of the node's specimen; NULL: dt for all.
 __global__ void __launch_bounds__(BS) k_predict(double* __restrict__ u, const double* __restrict__ v,
                                                 const double* __restrict__ a, int64_t Nc, int64_t N,
-                                                double dt, double hdt2, const double* __restrict__ dtn) {
+                                                double dt, double hdt2, const double* __restrict__ dtn, StepGate g) {
     CEM_PDL_ENTRY();
+    if (g.stop()) return;
     int64_t i = (int64_t)blockIdx.x * BS + threadIdx.x;
     if (i >= N) return;
     if (dtn) {
@@ -202,6 +203,7 @@ __device__ __forceinline__ double fma_r(double a, double b, double c) { return _
 struct ElemRange {
     const int* act;   // active originals, or nullptr: slot i is element i
     int64_t n_act, T0, n;
+    StepGate g;
     __device__ __forceinline__ int64_t elem(int64_t i) const {
         return act ? (i < n_act ? (int64_t)act[i] : T0 + (i - n_act)) : i;
     }
@@ -213,6 +215,7 @@ __global__ void __launch_bounds__(TB) k_strain(const double* __restrict__ u, con
                                                const uint8_t* __restrict__ active, int64_t Tc, ElemRange rg,
                                                R* __restrict__ h) {
     CEM_PDL_ENTRY();
+    if (rg.g.stop()) return;
     const int64_t i = (int64_t)blockIdx.x * TB + threadIdx.x;
     if (i >= rg.n) return;
     const int64_t j = rg.elem(i);
@@ -297,8 +300,9 @@ template <class R, int TB, int FB, bool SORT>
 __global__ void __launch_bounds__(TB) k_edge_stress(const R* __restrict__ h, const int* __restrict__ fan_off,
                                                     const int* __restrict__ fan_cnt, const int* __restrict__ fan_pool,
                                                     const R* __restrict__ cl, const R* __restrict__ cm, int64_t E,
-                                                    R* __restrict__ sig) {
+                                                    R* __restrict__ sig, StepGate g) {
     CEM_PDL_ENTRY();
+    if (g.stop()) return;
     const int64_t k0 = (int64_t)blockIdx.x * TB;
     int64_t k = k0 + threadIdx.x;
     int off = 0, cnt = 0;
@@ -350,6 +354,7 @@ __global__ void __launch_bounds__(TB) k_force(const R* __restrict__ sig, const i
                                               const R* __restrict__ Vg, const uint8_t* __restrict__ active,
                                               int64_t Tc, ElemRange rg, R* __restrict__ fp) {
     CEM_PDL_ENTRY();
+    if (rg.g.stop()) return;
     const int64_t i = (int64_t)blockIdx.x * TB + threadIdx.x;
     if (i >= rg.n) return;
     const int64_t j = rg.elem(i);
@@ -405,8 +410,9 @@ __global__ void __launch_bounds__(BS) k_prescribe(int64_t n, const int* __restri
                                                   const double* __restrict__ v0, double t0, int64_t step, double dt,
                                                   const double* __restrict__ dtn, double* __restrict__ v,
                                                   double* __restrict__ a, int64_t Nc, const double* __restrict__ u,
-                                                  float* __restrict__ uhl) {
+                                                  float* __restrict__ uhl, StepGate g) {
     CEM_PDL_ENTRY();
+    if (g.stop()) return;
     const int64_t q = (int64_t)blockIdx.x * BS + threadIdx.x;
     if (q >= n) return;
     const int i = key[q] >> 2, comp = key[q] & 3;
@@ -486,6 +492,7 @@ struct NodeArgs {
     double hdt, dt, hdt2;  // dt = 2 hdt and hdt2 = hdt dt, formed on the host
     double coef;           // 1 / (edges per element): the smoothing-volume share of Eq. 9
     int first;
+    StepGate g;
 };
 
 // Eqs. 13-15 for node i from its summed element force f.  Explicitly rounded
@@ -531,6 +538,7 @@ __global__ void __launch_bounds__(TB) k_node_update(const R* __restrict__ fp, co
                                                     const int* __restrict__ inc_cnt, const int* __restrict__ inc_pool,
                                                     NodeArgs A) {
     CEM_PDL_ENTRY();
+    if (A.g.stop()) return;
     const int64_t i = (int64_t)blockIdx.x * TB + threadIdx.x;
     if (i >= A.N) return;
     const int off = inc_off[i], cnt = inc_cnt[i];
@@ -565,6 +573,7 @@ __global__ void __launch_bounds__(TB) k_node_update_bal(const R* __restrict__ fp
                                                         const int* __restrict__ inc_cnt,
                                                         const int* __restrict__ inc_pool, NodeArgs A) {
     CEM_PDL_ENTRY();
+    if (A.g.stop()) return;
     using Slot = typename NodeSum<R>::Slot;
     __shared__ Slot buf[TB / 32][NODE_ROUND];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -854,8 +863,8 @@ inline bool mixed(const cem_ctx* c) { return c->precision == CEM_MIXED; }
 // ---------------------------------------------------------------- variant dispatch
 // Variant v: TB = 128 << (v % 3) threads per block; v / 3 selects the batch.
 inline ElemRange elem_range(const cem_ctx* c) {
-    if (c->n_act_orig >= 0) return {c->act_orig, c->n_act_orig, c->T0, c->n_act_orig + (c->T - c->T0)};
-    return {nullptr, 0, c->T0, c->T};
+    if (c->n_act_orig >= 0) return {c->act_orig, c->n_act_orig, c->T0, c->n_act_orig + (c->T - c->T0), cem_gate(c)};
+    return {nullptr, 0, c->T0, c->T, cem_gate(c)};
 }
 
 template <class R, int TB>
@@ -875,7 +884,7 @@ void launch_strain(cem_ctx* c, int v, const double* u, const float* uhl, const R
 template <class R, int TB, int FB, bool SORT>
 void go_edge(cem_ctx* c, const R* h, const R* cl, const R* cm, R* sig) {
     cem_pdl(c->stream, k_edge_stress<R, TB, FB, SORT>, cem_grid(c->E, TB), TB, h, c->fan_off, c->fan_cnt, c->fan_pool,
-            cl, cm, c->E, sig);
+            cl, cm, c->E, sig, cem_gate(c));
 }
 template <class R, int FB, bool SORT>
 void go_edge_tb(cem_ctx* c, int v, const R* h, const R* cl, const R* cm, R* sig) {
@@ -928,6 +937,7 @@ NodeArgs node_args(cem_ctx* c, bool mixed_records, int first) {
     A.hdt2 = A.hdt * A.dt;
     A.coef = 1.0 / c->epe;
     A.first = first;
+    A.g = cem_gate(c);
     return A;
 }
 
@@ -1205,7 +1215,7 @@ int cem_launch_predict(cem_ctx* c) {
     if (c->N == 0) return CEM_OK;
     if (mixed(c)) return CEM_OK;   // part of the node update
     cem_pdl(c->stream, k_predict, cem_grid(c->N, BS), BS, c->u, c->v, c->a, c->Nc, c->N, c->dt, 0.5 * c->dt * c->dt,
-                                                        c->dtn);
+            c->dtn, cem_gate(c));
     cem_launched(c);
     CEM_CK(c, cudaGetLastError());
     return CEM_OK;
@@ -1324,7 +1334,7 @@ int cem_launch_tune_variant(cem_ctx* c, int k, int v) {
 int cem_launch_prescribe(cem_ctx* c, int64_t step) {
     if (c->n_dir == 0) return CEM_OK;
     cem_pdl(c->stream, k_prescribe, cem_grid(c->n_dir, BS), BS, c->n_dir, c->dir_key, c->dir_v0, c->dir_t0, step, c->dt,
-            c->dtn, c->v, c->a, c->Nc, c->u, mixed(c) ? c->uhl : nullptr);
+            c->dtn, c->v, c->a, c->Nc, c->u, mixed(c) ? c->uhl : nullptr, cem_gate(c));
     cem_launched(c);
     CEM_CK(c, cudaGetLastError());
     return CEM_OK;

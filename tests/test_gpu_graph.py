@@ -1,8 +1,9 @@
 """Steps launched as one captured CUDA graph (cem_step_graph) against eager
 stepping (cem_step) and the oracle: bit-identical fields and energies for one
 specimen and for a three-specimen ensemble (fixed topology after the notch),
-re-capture when the step count changes, each ensemble member within 1e-11 of
-its own oracle run in FP64, and refusal while crack-front elements exist."""
+re-capture when the step count changes, and each ensemble member within 1e-11
+of its own oracle run in FP64.  Graphs with crack-front elements are tested in
+test_gpu_step_batch.py."""
 import numpy as np
 import pytest
 
@@ -70,14 +71,3 @@ def test_graph_ensemble_matches_eager_and_oracle(CEM):
         assert u_i.shape == o.u.shape
         rel = np.linalg.norm(u_i - o.u) / np.linalg.norm(o.u)
         assert rel <= 1e-11, (i, rel)
-
-
-def test_graph_refuses_crack_fronts(CEM):
-    from paper_2508_04076_gb300 import CEMError
-    sim = CEM.from_workload(plate_small())      # splitting on: the notch leaves crack-front elements
-    assert sim.info()["n_candidates"] > 0
-    with pytest.raises(CEMError) as ex:
-        sim.step_graph(10)
-    assert ex.value.code == -7
-    sim.step(10)                                 # the context is unchanged and still steps
-    assert sim.energy()["step"] == 10
