@@ -225,6 +225,7 @@ def _args():
     p.add_argument("--hex-steps", type=int, default=1000,
                    help="steps of the hexahedral (ES-H-FEM) sub-run on 200x80x10 hexahedra; 0 skips it")
     p.add_argument("--no-compare", action="store_true", help="skip the second-precision run and agreement check")
+    p.add_argument("--no-graph", action="store_true", help="skip the graph-replay comparison")
     p.add_argument("--no-autotune", action="store_true", help="keep the default launch variants")
     p.add_argument("--reorder-growth", type=float, default=None,
                    help="renumber node storage after this fractional node growth (0: never; default: the "
@@ -672,7 +673,8 @@ def run_cem(a):
     def graph_leg():
         from cem_inputs import plate_small
         out = {"note": "graph: one capture, then the timed replay; the same kernels and arguments as eager "
-                       "stepping (bit-identical).  split_enabled = 0 after the notch, except for the "
+                       "stepping (bit-identical).  persistent: one cooperative launch per call, grid barriers "
+                       "between the phases (bit-identical).  split_enabled = 0 after the notch, except for the "
                        "block with crack fronts, where a split would end the replay (none occurs in the "
                        "timed steps)"}
         cases = [("notched_block_20x8x2", plate_small(), 2000, "fp64", False)]
@@ -681,12 +683,12 @@ def run_cem(a):
         cases.append((w.name + "_crack_fronts", w, 100, "fp64", True))
         for name, wk, steps, prec, fronts in cases:
             res = {"tets": wk.n_tets, "steps": steps, "precision": prec}
-            for mode in (("eager_per_step", "eager", "graph") if fronts else ("eager", "graph")):
+            for mode in (("eager_per_step", "eager", "graph") if fronts else ("eager", "graph", "persistent")):
                 sg = CEM.from_workload(wk, device=dev, split_enabled=fronts, precision=prec,
                                        split_capacity=a.split_capacity if fronts else 0)
                 if mode == "eager_per_step":
                     sg.set_step_batch(1)
-                run = sg.step_graph if mode == "graph" else sg.step
+                run = {"graph": sg.step_graph, "persistent": sg.step_persistent}.get(mode, sg.step)
                 run(steps)   # warm-up (and the capture)
                 barrier()
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -700,12 +702,14 @@ def run_cem(a):
                     res[mode]["splits"] = sg.energy()["n_split"]
                 sg.close()
             res["graph_speedup"] = res["graph"]["value"] / res["eager"]["value"]
+            if not fronts:
+                res["persistent_speedup"] = res["persistent"]["value"] / res["eager"]["value"]
             if fronts:
                 res["batch_speedup"] = res["eager"]["value"] / res["eager_per_step"]["value"]
             out[name] = res
         return out
 
-    graph = _leg("graph", graph_leg) if a.workload == "block" else None
+    graph = _leg("graph", graph_leg) if (a.workload == "block" and not a.no_graph) else None
 
     # gradients: FP32 forward + adjoint with sqrt(N) checkpoints on the 102,000-element block,
     # J = final strain energy + mean top-face y displacement, topology frozen after the notch

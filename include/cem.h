@@ -175,6 +175,7 @@ typedef struct cem_info_t {
     double  h_min;           /* min over input elements of 3V / max face area [m]       */
     int64_t device_bytes;    /* device memory held by the context                       */
     int64_t n_reorder;       /* node renumberings so far (cem_set_reorder)              */
+    int64_t persistent_blocks; /* blocks of the last cem_step_persistent launch (0: none)  */
 } cem_info_t;
 
 /* Build the device mesh: edges and their element fans (Sec. 2.2, Fig. 4),
@@ -241,6 +242,26 @@ int cem_set_step_batch(cem_ctx* ctx, int64_t max_steps);
  * timing on), CEM_ENONFINITE, CEM_ETIMEOUT, CEM_ECAPACITY (as cem_step),
  * CEM_ECUDA. */
 int cem_step_graph(cem_ctx* ctx, int64_t n);
+
+/* The same n steps as cem_step, for a fixed topology, in one persistent
+ * cooperative kernel launch (no counterpart in the paper).  The kernel's
+ * 64-thread blocks are all resident at once (as many as the largest phase has
+ * items for, at most the device's co-resident count); each phase of a step
+ * (strain, edge stress, force, node update with the next step's predictor)
+ * strides over its elements, edges or nodes, and a grid barrier separates the
+ * phases, so a step costs four barriers instead of four or five kernel
+ * launches.  That pays on small and medium meshes; on large ones the tuned
+ * kernels of cem_step are faster.  Results are bit-identical to cem_step.  Valid while no step
+ * can split (splitting disabled, or no crack-front element), tetrahedral
+ * meshes only.  The barrier waits are bounded (cem_set_wait_limit): a wait
+ * that gives up ends the launch and the call returns CEM_ETIMEOUT; the step
+ * counter then stays where it was, but the node state is partly advanced (not
+ * that of any step) and should be restored from a checkpoint.  Synchronises
+ * once at the end.  Errors: CEM_ESTATE (no material; a hexahedral mesh;
+ * crack-front elements with splitting on; prescribed velocities; kernel
+ * timing on; no cooperative launch on the device), CEM_ETIMEOUT,
+ * CEM_ENONFINITE, CEM_ECUDA. */
+int cem_step_persistent(cem_ctx* ctx, int64_t n);
 
 /* Bounded device waits.  Every spin-wait in the library's kernels (the
  * look-back of the ordered scans) gives up after a number of polls, records

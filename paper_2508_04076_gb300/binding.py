@@ -25,8 +25,8 @@ FIELD = {"u": 0, "v": 1, "a": 2, "X": 3}
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_void_p)
 
-EXPORTED = ["cem_mesh_create", "cem_set_material", "cem_step", "cem_set_step_batch", "cem_step_graph", "cem_energy", "cem_crack_state",
-            "cem_get_field", "cem_info", "cem_energy_instance", "cem_adjoint", "cem_profile", "cem_profile_read",
+EXPORTED = ["cem_mesh_create", "cem_set_material", "cem_step", "cem_set_step_batch", "cem_step_graph",
+            "cem_step_persistent", "cem_energy", "cem_crack_state", "cem_get_field", "cem_info", "cem_energy_instance", "cem_adjoint", "cem_profile", "cem_profile_read",
             "cem_autotune", "cem_tune_get", "cem_tune_set", "cem_save", "cem_load", "cem_set_wait_limit",
             "cem_wait_probe", "cem_set_reorder", "cem_reorder_nodes", "cem_probe_fp64_fma", "cem_probe_split",
             "cem_probe_split_rule", "cem_node_energies_noalloc", "cem_destroy", "cem_last_error"]
@@ -62,7 +62,7 @@ class Info(C.Structure):
     _fields_ = [("n_nodes", C.c_int64), ("n_tets", C.c_int64), ("n_active_tets", C.c_int64),
                 ("n_edges", C.c_int64), ("n_candidates", C.c_int64), ("n_orig_edges", C.c_int64),
                 ("dt", C.c_double), ("h_min", C.c_double), ("device_bytes", C.c_int64),
-                ("n_reorder", C.c_int64)]
+                ("n_reorder", C.c_int64), ("persistent_blocks", C.c_int64)]
 
 
 _LIB = None
@@ -85,6 +85,7 @@ def load_library(build: bool = True):
                                      C.POINTER(C.c_double), C.c_int64]
     lib.cem_step.argtypes = [P, C.c_int64]
     lib.cem_step_graph.argtypes = [P, C.c_int64]
+    lib.cem_step_persistent.argtypes = [P, C.c_int64]
     lib.cem_set_step_batch.argtypes = [P, C.c_int64]
     lib.cem_energy.argtypes = [P, C.POINTER(Energy)]
     lib.cem_energy_instance.argtypes = [P, C.c_int64, C.POINTER(Energy)]
@@ -312,6 +313,11 @@ class CEM:
         the graph ends at the first step that splits and the rest runs as step() runs it;
         bit-identical to step(n)."""
         self._check(self._lib.cem_step_graph(self._ctx, int(n)))
+
+    def step_persistent(self, n=1):
+        """n fixed-topology steps in one persistent cooperative launch with bounded grid
+        barriers (cem_step_persistent); bit-identical to step(n)."""
+        self._check(self._lib.cem_step_persistent(self._ctx, int(n)))
 
     def energy(self) -> dict:
         e = Energy()

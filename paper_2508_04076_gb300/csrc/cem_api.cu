@@ -1136,6 +1136,37 @@ int cem_step(cem_ctx* c, int64_t n) {
     return prof_resolve(c);
 }
 
+// n steps of a fixed-topology context in one persistent cooperative launch: the phases
+// of each step are separated by grid barriers whose waits are bounded.
+int cem_step_persistent(cem_ctx* c, int64_t n) {
+    if (!c || n < 0) return CEM_EINVAL;
+    if (!c->material) return cem_fail(c, CEM_ESTATE, "cem_set_material must be called before cem_step_persistent");
+    if (c->elem_type != CEM_ELEM_TET4) return cem_fail(c, CEM_ESTATE, "the persistent step covers tetrahedral meshes");
+    if (c->split_enabled && c->n_cand > 0)
+        return cem_fail(c, CEM_ESTATE, "crack-front elements need the split test after every step: use cem_step");
+    if (c->n_dir > 0)
+        return cem_fail(c, CEM_ESTATE, "prescribed velocities are applied between steps: use cem_step");
+    if (c->prof) return cem_fail(c, CEM_ESTATE, "kernel timing is on (cem_profile): use cem_step");
+    if (int rc = select_device(c)) return rc;
+    if (n == 0) return CEM_OK;
+    if (c->tune_auto)   // the one-phase kernels' variants stay settled for the sizes
+        if (int rc = cem_tune_maybe(c)) return rc;
+    if (int rc = cem_launch_persistent(c, n)) return rc;
+    if (int rc = sync_counts(c)) return rc;
+    if (c->hcount[CNT_ERR] & DERR_BARRIER) {
+        CEM_CK(c, cudaMemsetAsync(c->dcount + CNT_ERR, 0, sizeof(long long), c->stream));
+        CEM_CK(c, cudaStreamSynchronize(c->stream));
+        return cem_fail(c, CEM_ETIMEOUT,
+                        "a grid barrier's bounded wait gave up; the steps of this call did not all run and the "
+                        "state is not that of any step");
+    }
+    c->step += n;
+    if (int rc = cem_launch_check_finite(c)) return rc;
+    if (int rc = sync_counts(c)) return rc;
+    if (c->hcount[CNT_SCRATCH1]) return cem_fail(c, CEM_ENONFINITE, "non-finite displacement");
+    return CEM_OK;
+}
+
 int cem_set_step_batch(cem_ctx* c, int64_t max_steps) {
     if (!c) return CEM_EINVAL;
     if (max_steps < 1) return cem_fail(c, CEM_EINVAL, "max_steps must be at least 1");
@@ -1390,6 +1421,7 @@ int cem_info(cem_ctx* c, cem_info_t* out) {
     out->h_min = c->h_min;
     out->device_bytes = c->bytes;
     out->n_reorder = c->n_reorder;
+    out->persistent_blocks = c->persist_blocks;
     return CEM_OK;
 }
 

@@ -121,10 +121,12 @@ enum {
     CNT_FRONT_Q,       // queued edge projections of a front evaluation (0 between evaluations)
     CNT_ACT_ORIG,      // active original elements listed in act_orig
     CNT_HALT,          // step batches: 1 + the batch step whose front evaluation decided splits (0: none)
+    CNT_BAR_COUNT,     // persistent launch: blocks arrived at the current grid barrier
+    CNT_BAR_GEN,       // persistent launch: grid barrier generation
     CNT_COUNT
 };
 
-enum { DERR_HASH_FULL = 1, DERR_SCAN_WAIT = 4 };
+enum { DERR_HASH_FULL = 1, DERR_SCAN_WAIT = 4, DERR_BARRIER = 8 };
 
 // kernels with tuned launch variants (block size, gather batch)
 enum { TUNE_STRAIN = 0, TUNE_EDGE, TUNE_FORCE, TUNE_NODE, TUNE_COUNT };
@@ -293,6 +295,7 @@ struct cem_ctx {
     int64_t spec_len = 1;     // length of the next batch: doubles after a batch without split
     bool capturing = false;   // launches go into a CUDA graph (cem_step_graph)
     int64_t topo_version = 0; // changes with the topology or the buffers the step kernels read
+    int64_t persist_blocks = 0;   // grid of the last persistent launch (cem_info)
 };
 
 // Gate of a batch step (see cem_ctx::spec_r): a kernel of batch step s returns at once
@@ -365,6 +368,9 @@ int cem_launch_strain(cem_ctx* c);
 int cem_launch_edge_stress(cem_ctx* c);
 int cem_launch_force(cem_ctx* c);
 int cem_launch_node_update(cem_ctx* c, int first);
+// n fixed-topology steps in one cooperative launch (k_persist); the context's
+// barrier words are reset first.  Counts as one launch.
+int cem_launch_persistent(cem_ctx* c, int64_t n);
 int cem_launch_edge_coeffs(cem_ctx* c, const int* list, int64_t n);     // list == NULL: all E
 int cem_launch_node_mass(cem_ctx* c, const int* list, int64_t n);       // list == NULL: all N
 int cem_launch_material(cem_ctx* c, const double* E_dev, int nE, const double* Gc_dev, int nGc);

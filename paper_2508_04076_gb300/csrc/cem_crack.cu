@@ -364,13 +364,16 @@ __global__ void __launch_bounds__(FB) k_front_pick(const int* __restrict__ cand,
     dec_mask[ci] = (mask != 0 && G > Gc[cand[ci]]) ? (uint8_t)mask : (uint8_t)0;
 }
 
-// The whole front evaluation of a short candidate list (after the specimen has
-// broken, a handful of elements) in one block: faces, queued projections, the
-// pick and the ordered compaction of the decisions, in shared memory.  The
+// The whole front evaluation of a short candidate list (a straight notch front
+// through a specimen tens of elements thick, or a specimen that has broken: a
+// few to tens of elements) in one block: faces, queued projections, the pick and
+// the ordered compaction of the decisions, in shared memory (about 37 KB).  The
 // values are those of the three-kernel form (same functions, same roundings),
 // and the splits come out in candidate order, as the ordered scan gives them.
-constexpr int FRONT_SMALL = 16;   // candidates
-constexpr int FS_T = 128;         // threads
+// One launch instead of four matters when the evaluation runs beside a short
+// force kernel and the node update waits for it (mixed precision).
+constexpr int FRONT_SMALL = 64;   // candidates
+constexpr int FS_T = 256;         // threads: one per face of up to 64 candidates
 
 __global__ void __launch_bounds__(FS_T) k_front_small(const int* __restrict__ cand, int nc,
                                                       const int* __restrict__ conn, const int* __restrict__ t2e,

@@ -127,13 +127,11 @@ __global__ void __launch_bounds__(BS) k_geometry(const double* __restrict__ X, i
 
 // uhl (mixed only): per node 8 floats: hi.xyz, lo.xyz, 2 pad; u = hi + lo to ~48 bits.
 // dtn (ensembles): per-node time step of the node's specimen; NULL: dt for all.
-__global__ void __launch_bounds__(BS) k_predict(double* __restrict__ u, const double* __restrict__ v,
-                                                const double* __restrict__ a, int64_t Nc, int64_t N,
-                                                double dt, double hdt2, const double* __restrict__ dtn, StepGate g) {
-    CEM_PDL_ENTRY();
-    if (g.stop()) return;
-    int64_t i = (int64_t)blockIdx.x * BS + threadIdx.x;
-    if (i >= N) return;
+// The per-item bodies (predict_item, strain_item, edge_item, force_item, node_item)
+// are shared by the one-phase kernels and the persistent kernel (k_persist), so
+// both give the same bits.
+__device__ __forceinline__ void predict_item(double* u, const double* v, const double* a, int64_t Nc, int64_t i,
+                                             double dt, double hdt2, const double* dtn) {
     if (dtn) {
         dt = dtn[i];
         hdt2 = 0.5 * dt * dt;
@@ -143,6 +141,16 @@ __global__ void __launch_bounds__(BS) k_predict(double* __restrict__ u, const do
         int64_t k = c * Nc + i;
         u[k] = cem_pred(u[k], v[k], a[k], dt, hdt2);
     }
+}
+
+__global__ void __launch_bounds__(BS) k_predict(double* __restrict__ u, const double* __restrict__ v,
+                                                const double* __restrict__ a, int64_t Nc, int64_t N,
+                                                double dt, double hdt2, const double* __restrict__ dtn, StepGate g) {
+    CEM_PDL_ENTRY();
+    if (g.stop()) return;
+    int64_t i = (int64_t)blockIdx.x * BS + threadIdx.x;
+    if (i >= N) return;
+    predict_item(u, v, a, Nc, i, dt, hdt2, dtn);
 }
 
 // FP32 hi/lo records of the current u (mixed mode: strain of the current state for an energy evaluation).
@@ -209,17 +217,10 @@ struct ElemRange {
     }
 };
 
-template <class R, int TB>
-__global__ void __launch_bounds__(TB) k_strain(const double* __restrict__ u, const float* __restrict__ uhl,
-                                               int64_t Nc, const int* __restrict__ conn, const R* __restrict__ Vg,
-                                               const uint8_t* __restrict__ active, int64_t Tc, ElemRange rg,
-                                               R* __restrict__ h) {
-    CEM_PDL_ENTRY();
-    if (rg.g.stop()) return;
-    const int64_t i = (int64_t)blockIdx.x * TB + threadIdx.x;
-    if (i >= rg.n) return;
-    const int64_t j = rg.elem(i);
-    if (!active[j]) return;
+// Strain record of active element j.
+template <class R>
+__device__ __forceinline__ void strain_item(const double* u, const float* uhl, int64_t Nc, const int* conn,
+                                            const R* Vg, int64_t Tc, int64_t j, R* h) {
     const int n[4] = {conn[j], conn[Tc + j], conn[2 * Tc + j], conn[3 * Tc + j]};
     R d[3][3];   // d[a][c] = u_{a+1,c} - u_{0,c}
     node_disp_diff<R>(u, uhl, Nc, n, d);
@@ -240,6 +241,20 @@ __global__ void __launch_bounds__(TB) k_strain(const double* __restrict__ u, con
     };
     const R out[6] = {diag(0), diag(1), diag(2), shear(0, 1), shear(1, 2), shear(0, 2)};
     Rec<R>::store6(h + Rec<R>::S6 * j, out);
+}
+
+template <class R, int TB>
+__global__ void __launch_bounds__(TB) k_strain(const double* __restrict__ u, const float* __restrict__ uhl,
+                                               int64_t Nc, const int* __restrict__ conn, const R* __restrict__ Vg,
+                                               const uint8_t* __restrict__ active, int64_t Tc, ElemRange rg,
+                                               R* __restrict__ h) {
+    CEM_PDL_ENTRY();
+    if (rg.g.stop()) return;
+    const int64_t i = (int64_t)blockIdx.x * TB + threadIdx.x;
+    if (i >= rg.n) return;
+    const int64_t j = rg.elem(i);
+    if (!active[j]) return;
+    strain_item<R>(u, uhl, Nc, conn, Vg, Tc, j, h);
 }
 
 // Gathers may be issued in batches of FB (fan) or NB (node incidence) entries:
@@ -296,6 +311,18 @@ __device__ __forceinline__ void fan_sum(const R* __restrict__ h, const int* __re
 // Each edge's sum is the same whichever thread takes it.
 constexpr int FAN_KEYS = 32;   // fans longer than 31 share the last key
 
+// Stress of edge k, whose fan is fan_pool[off .. off + cnt).  An edge whose fan emptied
+// (every element around it split) is read by no active element: its stress is left as
+// it was (finite; its energy term has H = 0).
+template <class R, int FB>
+__device__ __forceinline__ void edge_item(const R* h, const int* fan_pool, int off, int cnt, int64_t k, const R* cl,
+                                          const R* cm, R* sig) {
+    if (cnt == 0) return;
+    R H[6];
+    fan_sum<R, FB>(h, fan_pool, off, cnt, H);
+    edge_sigma(k, H, cl, cm, sig);
+}
+
 template <class R, int TB, int FB, bool SORT>
 __global__ void __launch_bounds__(TB) k_edge_stress(const R* __restrict__ h, const int* __restrict__ fan_off,
                                                     const int* __restrict__ fan_cnt, const int* __restrict__ fan_pool,
@@ -339,26 +366,14 @@ __global__ void __launch_bounds__(TB) k_edge_stress(const R* __restrict__ h, con
         cnt = s_cnt[threadIdx.x];
         k = k0 + s_slot[threadIdx.x];
     }
-    // An edge whose fan emptied (every element around it split), or a slot past the
-    // last edge, is read by no active element: its stress is left as it was (finite;
-    // its energy term has H = 0).
-    if (k >= E || cnt == 0) return;
-    R H[6];
-    fan_sum<R, FB>(h, fan_pool, off, cnt, H);
-    edge_sigma(k, H, cl, cm, sig);
+    if (k >= E) return;
+    edge_item<R, FB>(h, fan_pool, off, cnt, k, cl, cm, sig);
 }
 
 
-template <class R, int TB>
-__global__ void __launch_bounds__(TB) k_force(const R* __restrict__ sig, const int* __restrict__ t2e,
-                                              const R* __restrict__ Vg, const uint8_t* __restrict__ active,
-                                              int64_t Tc, ElemRange rg, R* __restrict__ fp) {
-    CEM_PDL_ENTRY();
-    if (rg.g.stop()) return;
-    const int64_t i = (int64_t)blockIdx.x * TB + threadIdx.x;
-    if (i >= rg.n) return;
-    const int64_t j = rg.elem(i);
-    if (!active[j]) return;
+// Nodal force shares of active element j.
+template <class R>
+__device__ __forceinline__ void force_item(const R* sig, const int* t2e, const R* Vg, int64_t Tc, int64_t j, R* fp) {
     int kk[6];
 #pragma unroll
     for (int l = 0; l < 6; ++l) kk[l] = t2e[l * Tc + j];
@@ -400,6 +415,19 @@ __global__ void __launch_bounds__(TB) k_force(const R* __restrict__ sig, const i
         cem_st8(o, r0);
         cem_st8(o + 8, r1);
     }
+}
+
+template <class R, int TB>
+__global__ void __launch_bounds__(TB) k_force(const R* __restrict__ sig, const int* __restrict__ t2e,
+                                              const R* __restrict__ Vg, const uint8_t* __restrict__ active,
+                                              int64_t Tc, ElemRange rg, R* __restrict__ fp) {
+    CEM_PDL_ENTRY();
+    if (rg.g.stop()) return;
+    const int64_t i = (int64_t)blockIdx.x * TB + threadIdx.x;
+    if (i >= rg.n) return;
+    const int64_t j = rg.elem(i);
+    if (!active[j]) return;
+    force_item<R>(sig, t2e, Vg, Tc, j, fp);
 }
 
 // Prescribed velocity ramp v(t) = min(t / t0, 1) v0 (Sec. 4.1-4.3, 4.5): the
@@ -533,14 +561,9 @@ __device__ __forceinline__ void node_integrate(const NodeArgs& A, int64_t i, con
 }
 
 // One thread per node: NB incidence entries, then their NB records, per round.
-template <class R, int TB, int NB>
-__global__ void __launch_bounds__(TB) k_node_update(const R* __restrict__ fp, const int* __restrict__ inc_off,
-                                                    const int* __restrict__ inc_cnt, const int* __restrict__ inc_pool,
-                                                    NodeArgs A) {
-    CEM_PDL_ENTRY();
-    if (A.g.stop()) return;
-    const int64_t i = (int64_t)blockIdx.x * TB + threadIdx.x;
-    if (i >= A.N) return;
+template <class R, int NB>
+__device__ __forceinline__ void node_item(const R* fp, const int* inc_off, const int* inc_cnt, const int* inc_pool,
+                                          const NodeArgs& A, int64_t i) {
     const int off = inc_off[i], cnt = inc_cnt[i];
     NodeSum<R> acc;
     for (int base = 0; base < cnt; base += NB) {
@@ -558,6 +581,17 @@ __global__ void __launch_bounds__(TB) k_node_update(const R* __restrict__ fp, co
     double f[3];
     acc.finish(f);
     node_integrate(A, i, f);
+}
+
+template <class R, int TB, int NB>
+__global__ void __launch_bounds__(TB) k_node_update(const R* __restrict__ fp, const int* __restrict__ inc_off,
+                                                    const int* __restrict__ inc_cnt, const int* __restrict__ inc_pool,
+                                                    NodeArgs A) {
+    CEM_PDL_ENTRY();
+    if (A.g.stop()) return;
+    const int64_t i = (int64_t)blockIdx.x * TB + threadIdx.x;
+    if (i >= A.N) return;
+    node_item<R, NB>(fp, inc_off, inc_cnt, inc_pool, A, i);
 }
 
 // Warp-balanced gathers: a node with a long incidence list (an input node next
@@ -856,6 +890,119 @@ __global__ void __launch_bounds__(RB) k_count_nonfinite(const double* __restrict
         for (int c = 0; c < 3; ++c)
             if (!isfinite(u[c * Nc + i])) bad = 1;
     if (__syncthreads_or(bad) && threadIdx.x == 0) atomicAdd((unsigned long long*)cnt, 1ull);
+}
+
+// ---------------------------------------------------------------- persistent steps
+// n steps of a fixed-topology tetrahedral mesh in one cooperative launch.  Each
+// phase of the step (strain, edge stress, force, node update) strides the grid over
+// its elements, edges or nodes, and a grid barrier separates the phases, so a step
+// costs four barriers instead of four or five launches.  The FP64 predictor of the
+// next step runs in the node phase, on the node the thread has just updated (the
+// strain phase that reads u is two barriers behind).  Every item is computed by the
+// functions the one-phase kernels use, so the results are bit-identical.  The arrays
+// that one phase writes and a later one reads are reached through plain pointers
+// (PersistArgs), never through the read-only data path, which is not kept coherent
+// with writes made during the launch.
+// 64 threads per block: a small mesh's phases then spread over many SMs (FP64 issue
+// is 2 lanes per clock per SM); on the 1,920-element block 64-thread blocks took 25.6
+// us per step, 256-thread blocks 33.4 and one 16-block cluster with the hardware
+// cluster barrier 28.1.
+constexpr int PT = 64;
+
+// Grid barrier of a cooperative launch: block leaders take the generation, arrive on
+// the counter (release: the block's writes, ordered before by the block barrier, go
+// with the arrival); the last to arrive (acquire: it sees every block's writes) resets
+// the counter and advances the generation (release); the others poll the generation
+// (acquire).  The wait is bounded: past `limit` polls the block records DERR_BARRIER and
+// every thread of the block gets false (the blocks still waiting then give up in turn,
+// at this barrier or the next, and the launch ends without completing its steps).
+struct GridBar {
+    unsigned long long* count;
+    unsigned long long* gen;
+    long long* err;
+    long long limit;
+    __device__ bool sync() const {
+        __shared__ int s_ok;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int ok = 1;
+            unsigned long long g, arrived;
+            asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(g) : "l"(gen) : "memory");
+            asm volatile("atom.acq_rel.gpu.global.add.u64 %0, [%1], %2;"
+                         : "=l"(arrived)
+                         : "l"(count), "l"(1ull)
+                         : "memory");
+            if (arrived + 1ull == gridDim.x) {
+                asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(count), "l"(0ull) : "memory");
+                asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(gen), "l"(1ull) : "memory");
+            } else {
+                long long spins = 0;
+                unsigned long long v;
+                for (;;) {
+                    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(gen) : "memory");
+                    if (v != g) break;
+                    if (++spins > limit) {
+                        atomicOr((unsigned long long*)err, (unsigned long long)DERR_BARRIER);
+                        ok = 0;
+                        break;
+                    }
+                }
+            }
+            s_ok = ok;
+        }
+        __syncthreads();
+        return s_ok != 0;
+    }
+};
+
+template <class R>
+struct PersistArgs {
+    // written during the launch
+    double* u;
+    float* uhl;
+    R *h, *sig, *fp;
+    NodeArgs A;
+    // read only
+    const int* conn;
+    const R* Vg;
+    const uint8_t* active;
+    const int *t2e, *fan_off, *fan_cnt, *fan_pool, *inc_off, *inc_cnt, *inc_pool;
+    const R *cl, *cm;
+    const double* dtn;
+    int64_t Tc, Nc, E, N;
+    ElemRange rg;
+    double dt, hdt2;   // the predictor's step values, as the one-phase predictor gets them
+};
+
+template <class R>
+__global__ void __launch_bounds__(PT) k_persist(PersistArgs<R> P, int64_t n_steps, GridBar bar) {
+    constexpr bool FP64 = sizeof(R) == 8;
+    const int64_t t0 = (int64_t)blockIdx.x * PT + threadIdx.x, stride = (int64_t)gridDim.x * PT;
+    if (FP64) {
+        for (int64_t i = t0; i < P.N; i += stride) predict_item(P.u, P.A.v, P.A.a, P.Nc, i, P.dt, P.hdt2, P.dtn);
+        if (!bar.sync()) return;
+    }
+    for (int64_t s = 0; s < n_steps; ++s) {
+        for (int64_t i = t0; i < P.rg.n; i += stride) {
+            const int64_t j = P.rg.elem(i);
+            if (P.active[j]) strain_item<R>(P.u, P.uhl, P.Nc, P.conn, P.Vg, P.Tc, j, P.h);
+        }
+        if (!bar.sync()) return;
+        for (int64_t k = t0; k < P.E; k += stride)
+            edge_item<R, 4>(P.h, P.fan_pool, P.fan_off[k], P.fan_cnt[k], k, P.cl, P.cm, P.sig);
+        if (!bar.sync()) return;
+        for (int64_t i = t0; i < P.rg.n; i += stride) {
+            const int64_t j = P.rg.elem(i);
+            if (P.active[j]) force_item<R>(P.sig, P.t2e, P.Vg, P.Tc, j, P.fp);
+        }
+        if (!bar.sync()) return;
+        const bool next = s + 1 < n_steps;
+        for (int64_t i = t0; i < P.N; i += stride) {
+            node_item<R, 8>(P.fp, P.inc_off, P.inc_cnt, P.inc_pool, P.A, i);
+            if (FP64 && next) predict_item(P.u, P.A.v, P.A.a, P.Nc, i, P.dt, P.hdt2, P.dtn);
+        }
+        if (next && !bar.sync()) return;
+    }
 }
 
 inline bool mixed(const cem_ctx* c) { return c->precision == CEM_MIXED; }
@@ -1455,3 +1602,75 @@ int cem_launch_check_finite(cem_ctx* c) {
 
 // Reduction scratch size (doubles) needed by cem_energy_reduce.
 int64_t cem_reduction_doubles() { return 5 * RG; }
+
+namespace {
+template <class R>
+int launch_persistent(cem_ctx* c, int64_t n, const R* Vg, R* h, R* sig, R* fp, const R* cl, const R* cm) {
+    PersistArgs<R> P;
+    P.u = c->u;
+    P.uhl = sizeof(R) == 4 ? c->uhl : nullptr;
+    P.h = h;
+    P.sig = sig;
+    P.fp = fp;
+    P.A = node_args(c, sizeof(R) == 4, 0);
+    P.A.g = StepGate{nullptr, 0};
+    P.conn = c->conn;
+    P.Vg = Vg;
+    P.active = c->active;
+    P.t2e = c->t2e;
+    P.fan_off = c->fan_off;
+    P.fan_cnt = c->fan_cnt;
+    P.fan_pool = c->fan_pool;
+    P.inc_off = c->inc_off;
+    P.inc_cnt = c->inc_cnt;
+    P.inc_pool = c->inc_pool;
+    P.cl = cl;
+    P.cm = cm;
+    P.dtn = c->dtn;
+    P.Tc = c->Tc;
+    P.Nc = c->Nc;
+    P.E = c->E;
+    P.N = c->N;
+    P.rg = elem_range(c);
+    P.rg.g = StepGate{nullptr, 0};
+    P.dt = c->dt;
+    P.hdt2 = 0.5 * c->dt * c->dt;
+    const int64_t work = std::max<int64_t>(std::max<int64_t>(P.rg.n, c->E), c->N);
+    const int64_t cblocks = cem_grid(work, PT);
+    cudaLaunchConfig_t cfg = {};
+    cfg.blockDim = dim3(PT);
+    cfg.stream = c->stream;
+    cudaLaunchAttribute at[1];
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int sms = 0, coop = 0, per_sm = 0;
+    CEM_CK(c, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
+    CEM_CK(c, cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, c->device));
+    if (!coop) return cem_fail(c, CEM_ESTATE, "the device does not support cooperative launches");
+    auto k = k_persist<R>;
+    CEM_CK(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, PT, 0));
+    if (per_sm < 1) return cem_fail(c, CEM_ESTATE, "the persistent step kernel does not fit on an SM");
+    // every block must be resident at once: at most the co-resident count, and no more
+    // blocks than the largest phase has items for
+    const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * per_sm, cblocks));
+    const GridBar bar{(unsigned long long*)(c->dcount + CNT_BAR_COUNT), (unsigned long long*)(c->dcount + CNT_BAR_GEN),
+                      c->dcount + CNT_ERR, c->wait_limit};
+    CEM_CK(c, cudaMemsetAsync(c->dcount + CNT_BAR_COUNT, 0, sizeof(long long), c->stream));
+    cfg.gridDim = dim3((unsigned)blocks);
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    CEM_CK(c, cudaLaunchKernelEx(&cfg, k, P, n, bar));
+    c->persist_blocks = blocks;
+    return CEM_OK;
+}
+}  // namespace
+
+int cem_launch_persistent(cem_ctx* c, int64_t n) {
+    if (n <= 0 || c->N == 0) return CEM_OK;
+    int rc = mixed(c) ? launch_persistent<float>(c, n, c->Vg32, c->h32, c->sig32, c->fp32, c->cl32, c->cm32)
+                      : launch_persistent<double>(c, n, c->Vg, c->h, c->sig, c->fp, c->cl, c->cm);
+    if (rc) return rc;
+    cem_launched(c);
+    CEM_CK(c, cudaGetLastError());
+    return CEM_OK;
+}

@@ -108,6 +108,24 @@ def test_heterogeneous_jittered_with_splits(CEM):
     assert o.energy()["n_split"] > 0
 
 
+def test_long_front_general_form(CEM):
+    """A notch front across 36 element layers: 72 to 77 crack-front elements over the
+    first 200 steps, more than the one-block form takes (64), so the faces /
+    projections / pick / ordered-compaction launches run; more than 2,000 splits.
+    Against the oracle every 20 steps, with the G of every split.  (Shorter lists, in
+    one block, are covered by the 20x8x2 block and the ensembles.)"""
+    w = kuhn_block(20, 8, 36, 0.1, 0.04, 0.09, notch_length=0.05, traction=2.0e6)
+    o = CEMOracle.from_workload(w)
+    sim = CEM.from_workload(w)
+    assert sim.info()["n_candidates"] == len(o.candidates()) > 64
+    for _ in range(10):
+        o.step(20)
+        sim.step(20)
+        assert sim.info()["n_candidates"] == len(o.candidates()) > 64
+        _compare(sim, o)
+    assert o.energy()["n_split"] > 2000
+
+
 @pytest.mark.parametrize("shape", [(1, 1, 1), (3, 1, 1), (5, 3, 2)])
 def test_tiny_and_ragged_meshes(CEM, shape):
     w = _no_notch(kuhn_block(*shape, 0.01 * shape[0], 0.01 * shape[1], 0.01 * shape[2], jitter=0.1, seed=1))
