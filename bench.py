@@ -56,8 +56,8 @@ KERNEL_UNITS = {"predict": "nodes", "strain": "tets", "edge_stress": "edges", "f
 # launch, divided by the launch's units: 982,000 elements, 1,219,792 edges, 187,533 nodes after the notch)
 # on the intact 960,000-element block, for the kernels as they are now.  Source:
 # profiles/step_kernels_fp64_notched_block_200x80x10.md and profiles/step_kernels_mixed_notched_block_200x80x10.md.
-DRAM_BYTES_PER_UNIT = {"fp64": {"strain": 107.5, "edge_stress": 104.0, "force": 215.6, "node_update": 834.4},
-                       "mixed": {"strain": 63.3, "edge_stress": 71.8, "force": 129.2, "node_update": 559.9}}
+DRAM_BYTES_PER_UNIT = {"fp64": {"strain": 107.1, "edge_stress": 103.8, "force": 216.3, "node_update": 837.3},
+                       "mixed": {"strain": 63.0, "edge_stress": 70.5, "force": 129.1, "node_update": 556.1}}
 
 
 def b_alg_per_tet_step(T, E, N, precision):
