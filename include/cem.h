@@ -342,8 +342,12 @@ int cem_profile_read(cem_ctx* ctx, double* ms, int64_t* launches, int n, int64_t
  * (128, 256 or 512 threads) and, for the two gathers, how many list entries
  * have their loads issued together (fan: 2, 4 or 8, in edge order, or 102,
  * 104, 108 for 2, 4, 8 with each block's edges handed to its threads sorted by
- * fan size, so the edges of a warp have nearly equal fans; incidence: 2, 4 or
- * 8, or 128 for warp-balanced rounds of up to 128 entries).
+ * fan size, so the edges of a warp have nearly equal fans, or 200 for the
+ * block's strain records gathered into shared memory by TMA tile::gather4
+ * copies, four records per copy, before the threads sum them; incidence: 2, 4
+ * or 8, or 128 for warp-balanced rounds of up to 128 entries).  The TMA
+ * variant's wait for its copies is bounded (cem_set_wait_limit): a wait that
+ * gives up makes cem_step return CEM_ETIMEOUT.
  * All variants of a kernel compute the same values in the same order: the
  * choice never changes results, only speed.
  *
@@ -372,7 +376,7 @@ int cem_profile_read(cem_ctx* ctx, double* ms, int64_t* launches, int n, int64_t
 int cem_autotune(cem_ctx* ctx, const char* cache_path, int reps, int automatic);
 int cem_tune_get(cem_ctx* ctx, int kernel, int* block, int* batch, double* us, double* default_us);
 /* Pin kernel k's variant (block in {128, 256, 512}; batch 1 for strain and
- * force, {2, 4, 8, 102, 104, 108} for the edge stress, {2, 4, 8, 128} for
+ * force, {2, 4, 8, 102, 104, 108, 200} for the edge stress, {2, 4, 8, 128} for
  * the node update,
  * where 128 selects warp-balanced gathers in rounds of 128 entries).  An
  * automatic autotuner may replace it when the kernel's bucket changes.

@@ -736,6 +736,7 @@ int create_impl(const cem_mesh_desc* d, cem_ctx* c) {
     CEM_CK(c, cudaMemsetAsync(c->dcount, 0, CNT_COUNT * sizeof(long long), s));
     CEM_CK(c, cudaMemsetAsync(c->scan_status, 0, c->scan_blocks_cap * sizeof(unsigned long long), s));
     CEM_CK(c, cudaMemsetAsync(c->scan_ticket, 0, sizeof(unsigned int), s));
+    if (int rc = cem_tma_init(c)) return rc;
 
     // uploads (structure of arrays)
     {
@@ -1058,6 +1059,14 @@ int run_steps(cem_ctx* c, int64_t n) {
 
 int cem_run_step(cem_ctx* c) { return run_step(c); }
 
+// A TMA-gather wait of the edge stress that gave up (counters read): CEM_ETIMEOUT, flag cleared.
+static int check_tma_wait(cem_ctx* c) {
+    if (!(c->hcount[CNT_ERR] & DERR_TMA_WAIT)) return CEM_OK;
+    CEM_CK(c, cudaMemsetAsync(c->dcount + CNT_ERR, 0, sizeof(long long), c->stream));
+    CEM_CK(c, cudaStreamSynchronize(c->stream));
+    return cem_fail(c, CEM_ETIMEOUT, "a bounded wait for the edge stress's TMA gathers gave up");
+}
+
 extern "C" {
 
 int cem_mesh_create(const cem_mesh_desc* d, cem_ctx** out) {
@@ -1132,6 +1141,7 @@ int cem_step(cem_ctx* c, int64_t n) {
     if (int rc = run_steps(c, n)) return rc;
     if (int rc = cem_launch_check_finite(c)) return rc;
     if (int rc = sync_counts(c)) return rc;
+    if (int rc = check_tma_wait(c)) return rc;
     if (c->hcount[CNT_SCRATCH1]) return cem_fail(c, CEM_ENONFINITE, "non-finite displacement");
     return prof_resolve(c);
 }
@@ -1263,6 +1273,7 @@ int cem_step_graph(cem_ctx* c, int64_t n) {
     }
     if (int rc = cem_launch_check_finite(c)) return rc;
     if (int rc = sync_counts(c)) return rc;
+    if (int rc = check_tma_wait(c)) return rc;
     if (c->hcount[CNT_SCRATCH1]) return cem_fail(c, CEM_ENONFINITE, "non-finite displacement");
     return CEM_OK;
 }

@@ -21,6 +21,7 @@
 //            smaller (side 0) or larger (side 1) endpoint, -1 if none.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -126,7 +127,7 @@ enum {
     CNT_COUNT
 };
 
-enum { DERR_HASH_FULL = 1, DERR_SCAN_WAIT = 4, DERR_BARRIER = 8 };
+enum { DERR_HASH_FULL = 1, DERR_SCAN_WAIT = 4, DERR_BARRIER = 8, DERR_TMA_WAIT = 16 };
 
 // kernels with tuned launch variants (block size, gather batch)
 enum { TUNE_STRAIN = 0, TUNE_EDGE, TUNE_FORCE, TUNE_NODE, TUNE_COUNT };
@@ -296,6 +297,10 @@ struct cem_ctx {
     bool capturing = false;   // launches go into a CUDA graph (cem_step_graph)
     int64_t topo_version = 0; // changes with the topology or the buffers the step kernels read
     int64_t persist_blocks = 0;   // grid of the last persistent launch (cem_info)
+    // tensor map of the strain records (rows of 6 doubles, or 8 floats in mixed precision) for
+    // the edge-stress variants that gather them with TMA; tma_h: the records it describes
+    CUtensorMap hmap;
+    const void* tma_h = nullptr;
 };
 
 // Gate of a batch step (see cem_ctx::spec_r): a kernel of batch step s returns at once
@@ -371,6 +376,9 @@ int cem_launch_node_update(cem_ctx* c, int first);
 // n fixed-topology steps in one cooperative launch (k_persist); the context's
 // barrier words are reset first.  Counts as one launch.
 int cem_launch_persistent(cem_ctx* c, int64_t n);
+// Encode the strain records' tensor map (tetrahedral meshes; without it the TMA variants of
+// the edge stress run the fan-sorted form instead).
+int cem_tma_init(cem_ctx* c);
 int cem_launch_edge_coeffs(cem_ctx* c, const int* list, int64_t n);     // list == NULL: all E
 int cem_launch_node_mass(cem_ctx* c, const int* list, int64_t n);       // list == NULL: all N
 int cem_launch_material(cem_ctx* c, const double* E_dev, int nE, const double* Gc_dev, int nGc);

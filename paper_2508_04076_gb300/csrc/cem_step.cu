@@ -371,6 +371,166 @@ __global__ void __launch_bounds__(TB) k_edge_stress(const R* __restrict__ h, con
 }
 
 
+// ---- edge stress with the strain records gathered by TMA (Blackwell tile::gather4)
+// A block takes TB consecutive edges.  Their fan entries are numbered by a block scan and
+// copied to shared memory; one warp then issues tensor copies of 4 records each (rows of
+// the strain-record array, by element id) into a staging area, all completing on one
+// mbarrier; the threads sum their edge's staged records in fan order (the same operations
+// in the same order as fan_sum) and store the stress.  A block whose fans hold more rows
+// than the staging area runs several rounds; a fan longer than the whole area is summed
+// from global memory.  The wait on the mbarrier is bounded: past the limit the block
+// records DERR_TMA_WAIT, waits once more (bounded) for the copies it issued, and returns.
+constexpr int TMA_STAGE = 36864;   // bytes of staged records per round
+
+template <class R> struct HRow { static constexpr int COLS = sizeof(R) == 8 ? 6 : 8; };
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+template <int TB>
+__device__ __forceinline__ int block_excl_scan_tb(int x, int* total) {
+    __shared__ int ws[TB / 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int inc = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) ws[w] = inc;
+    __syncthreads();
+    if (w == 0) {
+        const int v = lane < TB / 32 ? ws[lane] : 0;
+        int wi = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += y;
+        }
+        if (lane < TB / 32) ws[lane] = wi - v;
+        if (lane == TB / 32 - 1) *total = wi;   // the block's total (a shared variable)
+    }
+    __syncthreads();
+    return inc - x + ws[w];
+}
+
+template <class R, int TB>
+__global__ void __launch_bounds__(TB) k_edge_stress_tma(const __grid_constant__ CUtensorMap hmap,
+                                                        const int* __restrict__ fan_off,
+                                                        const int* __restrict__ fan_cnt,
+                                                        const int* __restrict__ fan_pool, const R* __restrict__ cl,
+                                                        const R* __restrict__ cm, int64_t E, R* __restrict__ sig,
+                                                        StepGate g, const R* __restrict__ h, long long* err,
+                                                        long long limit) {
+    // a copy of four rows lands at a 128-byte boundary of the staging area (the alignment
+    // tensor copies into shared memory need): FP64 groups of 192 bytes take 256-byte slots
+    constexpr int COLS = HRow<R>::COLS, RB = COLS * (int)sizeof(R), GS = (4 * RB + 127) / 128 * 128;
+    constexpr int ROWS = 4 * (TMA_STAGE / GS);
+    static_assert(RB % 16 == 0, "a tensor-map row must be a multiple of 16 bytes");
+    static_assert(GS % 128 == 0 && (TMA_STAGE / GS) * GS <= TMA_STAGE, "group slots inside the staging area");
+    __shared__ alignas(1024) unsigned char stage[TMA_STAGE];
+    __shared__ int idx[ROWS + 4];
+    __shared__ alignas(8) unsigned long long mbar;
+    __shared__ int s_total, s_next, s_end, s_fail;
+    CEM_PDL_ENTRY();
+    if (g.stop()) return;
+    const int64_t k = (int64_t)blockIdx.x * TB + threadIdx.x;
+    int off = 0, cnt = 0;
+    if (k < E) {
+        off = fan_off[k];
+        cnt = fan_cnt[k];
+    }
+    const int ct = cnt <= ROWS ? cnt : 0;   // rows this edge stages
+    const int pos = block_excl_scan_tb<TB>(ct, &s_total);
+    const uint32_t bar = smem_u32(&mbar);
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // the barrier, seen by the copies
+        s_fail = 0;
+    }
+    __syncthreads();
+    const int total = s_total;
+    uint32_t parity = 0;
+    int r0 = 0;
+    while (r0 < total) {   // block-uniform
+        if (threadIdx.x == 0) {
+            s_next = total;
+            s_end = r0;
+        }
+        __syncthreads();
+        const bool in = ct > 0 && pos >= r0 && pos + ct <= r0 + ROWS;
+        if (ct > 0 && pos >= r0 && !in) atomicMin(&s_next, pos);
+        if (in) {
+            atomicMax(&s_end, pos + ct);
+            for (int q = 0; q < ct; ++q) idx[pos - r0 + q] = fan_pool[off + q];
+        }
+        __syncthreads();
+        const int n = s_end - r0, next = s_next, groups = (n + 3) >> 2;
+        if ((int)threadIdx.x < 4 * groups - n) idx[n + threadIdx.x] = idx[n - 1];   // a full last group
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            if (threadIdx.x == 0)
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
+                             "r"((uint32_t)(groups * 4 * RB))
+                             : "memory");
+            __syncwarp();
+            for (int q = threadIdx.x; q < groups; q += 32)
+                asm volatile(
+                    "cp.async.bulk.tensor.2d.shared::cluster.global.tile::gather4.mbarrier::complete_tx::bytes"
+                    " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(smem_u32(stage + q * GS)),
+                    "l"(&hmap), "r"(0), "r"(idx[4 * q]), "r"(idx[4 * q + 1]), "r"(idx[4 * q + 2]),
+                    "r"(idx[4 * q + 3]), "r"(bar)
+                    : "memory");
+        }
+        long long spins = 0;
+        bool ok = true;
+        while (!mbar_try_wait(bar, parity))
+            if (++spins > limit) {
+                ok = false;
+                break;
+            }
+        if (!__syncthreads_and(ok)) {   // give up: record it, let the copies land, leave
+            if (threadIdx.x == 0) atomicOr((unsigned long long*)err, (unsigned long long)DERR_TMA_WAIT);
+            spins = 0;
+            while (!mbar_try_wait(bar, parity) && ++spins <= limit) {
+            }
+            return;
+        }
+        parity ^= 1u;
+        if (in) {   // row r of the round: slot r % 4 of group r / 4
+            auto row = [&](int r) { return reinterpret_cast<const R*>(stage + (r >> 2) * GS + (r & 3) * RB); };
+            const int r = pos - r0;
+            const R* x = row(r);
+            R H[6];
+#pragma unroll
+            for (int q = 0; q < 6; ++q) H[q] = x[q];
+            for (int e = 1; e < ct; ++e) {
+                x = row(r + e);
+#pragma unroll
+                for (int q = 0; q < 6; ++q) H[q] += x[q];
+            }
+            edge_sigma(k, H, cl, cm, sig);
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // these reads before the next copies
+        __syncthreads();
+        r0 = next;
+    }
+    if (cnt > ROWS) {   // longer than the staging area
+        R H[6];
+        fan_sum<R, 4>(h, fan_pool, off, cnt, H);
+        edge_sigma(k, H, cl, cm, sig);
+    }
+}
+
 // Nodal force shares of active element j.
 template <class R>
 __device__ __forceinline__ void force_item(const R* sig, const int* t2e, const R* Vg, int64_t Tc, int64_t j, R* fp) {
@@ -1041,9 +1201,27 @@ void go_edge_tb(cem_ctx* c, int v, const R* h, const R* cl, const R* cm, R* sig)
         default: go_edge<R, 512, FB, SORT>(c, h, cl, cm, sig);
     }
 }
-// v / 3: fan rounds of 2, 4, 8 in edge order (0-2) or with the block's edges sorted by fan size (3-5)
+template <class R, int TB>
+void go_edge_tma(cem_ctx* c, const R* h, const R* cl, const R* cm, R* sig) {
+    if (h != c->tma_h) {   // no tensor map for these records: the fan-sorted form
+        go_edge<R, TB, 4, true>(c, h, cl, cm, sig);
+        return;
+    }
+    cem_pdl(c->stream, k_edge_stress_tma<R, TB>, cem_grid(c->E, TB), TB, c->hmap, c->fan_off, c->fan_cnt,
+            c->fan_pool, cl, cm, c->E, sig, cem_gate(c), h, c->dcount + CNT_ERR, c->wait_limit);
+}
+// v / 3: fan rounds of 2, 4, 8 in edge order (0-2), with the block's edges sorted by fan size
+// (3-5), or the records gathered by TMA into shared memory (6)
 template <class R>
 void launch_edge(cem_ctx* c, int v, const R* h, const R* cl, const R* cm, R* sig) {
+    if (v / 3 == 6) {
+        switch (v % 3) {
+            case 0: go_edge_tma<R, 128>(c, h, cl, cm, sig); break;
+            case 1: go_edge_tma<R, 256>(c, h, cl, cm, sig); break;
+            default: go_edge_tma<R, 512>(c, h, cl, cm, sig);
+        }
+        return;
+    }
     switch (v / 3) {
         case 0: go_edge_tb<R, 2, false>(c, v, h, cl, cm, sig); break;
         case 1: go_edge_tb<R, 4, false>(c, v, h, cl, cm, sig); break;
@@ -1431,13 +1609,13 @@ int cem_launch_node_update(cem_ctx* c, int first) {
 namespace {
 // (the node update's fourth batch value selects the warp-balanced kernel)
 // batch of variant v / 3; for the edge stress, 100 + rounds marks the fan-sorted form
-constexpr int TUNE_BATCH[TUNE_COUNT][6] = {{1, 1, 1, 1, 1, 1},
-                                           {2, 4, 8, 102, 104, 108},
-                                           {1, 1, 1, 1, 1, 1},
-                                           {2, 4, 8, NODE_ROUND, NODE_ROUND, NODE_ROUND}};
+constexpr int TUNE_BATCH[TUNE_COUNT][7] = {{1, 1, 1, 1, 1, 1, 1},
+                                           {2, 4, 8, 102, 104, 108, 200},
+                                           {1, 1, 1, 1, 1, 1, 1},
+                                           {2, 4, 8, NODE_ROUND, NODE_ROUND, NODE_ROUND, NODE_ROUND}};
 }  // namespace
 
-int cem_tune_variants(int k) { return k == TUNE_NODE ? 12 : k == TUNE_EDGE ? 18 : 3; }
+int cem_tune_variants(int k) { return k == TUNE_NODE ? 12 : k == TUNE_EDGE ? 21 : 3; }
 
 void cem_tune_describe(int k, int v, int* block, int* batch) {
     *block = 128 << (v % 3);
@@ -1672,5 +1850,33 @@ int cem_launch_persistent(cem_ctx* c, int64_t n) {
     if (rc) return rc;
     cem_launched(c);
     CEM_CK(c, cudaGetLastError());
+    return CEM_OK;
+}
+
+int cem_tma_init(cem_ctx* c) {
+    c->tma_h = nullptr;
+    if (c->elem_type != CEM_ELEM_TET4) return CEM_OK;
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn) {
+        (void)cudaGetLastError();
+        return CEM_OK;   // no encoder: the TMA variants run the fan-sorted form
+    }
+    using Encode = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+    const bool m = mixed(c);
+    void* base = m ? (void*)c->h32 : (void*)c->h;
+    const cuuint64_t cols = m ? 8 : 6, esize = m ? 4 : 8;
+    const cuuint64_t dims[2] = {cols, (cuuint64_t)c->Tc};
+    const cuuint64_t strides[1] = {cols * esize};   // bytes between rows (a multiple of 16)
+    const cuuint32_t box[2] = {(cuuint32_t)cols, 1};  // one record per gathered row
+    const cuuint32_t estr[2] = {1, 1};
+    const CUresult r = ((Encode)fn)(&c->hmap, m ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64,
+                                    2, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                                    CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r == CUDA_SUCCESS) c->tma_h = base;
     return CEM_OK;
 }

@@ -5,8 +5,9 @@
 // gather), the element force and the node update (incidence gather).  A
 // variant is a block size (128, 256 or 512 threads) and, for the two gather
 // kernels, the number of list entries whose loads are issued together (2/4/8
-// fan entries, 2/4/8 incidence entries or the node update's warp-balanced
-// form).  Every variant of a kernel performs the same arithmetic in the same
+// fan entries in edge order or over fan-sorted edges, or the fans' records staged
+// in shared memory by TMA gathers; 2/4/8 incidence entries or the node update's
+// warp-balanced form).  Every variant of a kernel performs the same arithmetic in the same
 // order, so the choice never changes results.
 //
 // Tuning times each variant on the context's current mesh and state with CUDA

@@ -21,7 +21,7 @@ def CEM():
     return CEM
 
 
-BATCHES = {"strain": [1], "edge_stress": [2, 4, 8, 102, 104, 108], "force": [1], "node_update": [2, 4, 8, 128]}
+BATCHES = {"strain": [1], "edge_stress": [2, 4, 8, 102, 104, 108, 200], "force": [1], "node_update": [2, 4, 8, 128]}
 
 
 def _run(CEM, w, precision, variants=None, tune=None, steps=300):
