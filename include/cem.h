@@ -347,7 +347,9 @@ int cem_profile_read(cem_ctx* ctx, double* ms, int64_t* launches, int n, int64_t
  * copies, four records per copy, before the threads sum them; incidence: 2, 4
  * or 8, or 128 for warp-balanced rounds of up to 128 entries).  The TMA
  * variant's wait for its copies is bounded (cem_set_wait_limit): a wait that
- * gives up makes cem_step return CEM_ETIMEOUT.
+ * gives up makes cem_step return CEM_ETIMEOUT.  cem_autotune does not time the
+ * TMA variant (it measured slower than the others on GB300); cem_tune_set
+ * selects it.
  * All variants of a kernel compute the same values in the same order: the
  * choice never changes results, only speed.
  *

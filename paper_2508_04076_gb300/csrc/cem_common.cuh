@@ -399,6 +399,7 @@ int cem_run_step(cem_ctx* c);
 int cem_launch_check_finite(cem_ctx* c);
 // tuned variants (cem_step.cu) and the autotuner (cem_tune.cu)
 int cem_tune_variants(int kernel);
+int cem_tune_candidates(int kernel);   // the variants the autotuner times
 void cem_tune_describe(int kernel, int v, int* block, int* batch);
 int cem_tune_default(int kernel, int precision);
 int cem_launch_tune_variant(cem_ctx* c, int kernel, int v);

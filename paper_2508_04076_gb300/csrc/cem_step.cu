@@ -1617,6 +1617,12 @@ constexpr int TUNE_BATCH[TUNE_COUNT][7] = {{1, 1, 1, 1, 1, 1, 1},
 
 int cem_tune_variants(int k) { return k == TUNE_NODE ? 12 : k == TUNE_EDGE ? 21 : 3; }
 
+// The autotuner times the first cem_tune_candidates(k) variants.  The edge stress's TMA
+// variants (18-20) are left out: on GB300 they measured 3-5 times slower than the
+// register gathers, and timing them at every re-tune cost 1-3% of a long job; cem_tune_set
+// still selects them.
+int cem_tune_candidates(int k) { return k == TUNE_EDGE ? 18 : cem_tune_variants(k); }
+
 void cem_tune_describe(int k, int v, int* block, int* batch) {
     *block = 128 << (v % 3);
     *batch = TUNE_BATCH[k][v / 3];

@@ -148,7 +148,7 @@ int tune_kernel(cem_ctx* c, int k, const std::string& gpu) {
     int best = -1, rc = CEM_OK;
     double best_us = 0.0, def_us = 0.0;
     const int def = cem_tune_default(k, c->precision);
-    for (int v = 0; v < cem_tune_variants(k) && rc == CEM_OK; ++v) {
+    for (int v = 0; v < cem_tune_candidates(k) && rc == CEM_OK; ++v) {
         double us = 0.0;
         rc = time_variant(c, k, v, c->tune_reps, e0, e1, &us);
         if (rc) break;
