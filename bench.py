@@ -667,25 +667,27 @@ def run_cem(a):
 
     # steps launched as one captured CUDA graph (cem_step_graph) against eager launches: on
     # fixed topology (splitting off after the notch) for a small specimen, where launches
-    # dominate, and the 256-specimen ensemble; and with splitting on for the benchmark block,
-    # whose notch leaves crack-front elements, against eager steps that read the split
-    # decision after every step (step batch 1) and in batches (the default)
+    # dominate, and the 256-specimen ensemble; and with splitting on for the ensemble and the
+    # benchmark block, whose notches leave crack-front elements, against eager steps that read
+    # the split decision after every step (step batch 1) and in batches (the default)
     def graph_leg():
         from cem_inputs import plate_small
         out = {"note": "graph: one capture, then the timed replay; the same kernels and arguments as eager "
                        "stepping (bit-identical).  persistent: one cooperative launch per call, grid barriers "
                        "between the phases (bit-identical).  split_enabled = 0 after the notch, except for the "
-                       "block with crack fronts, where a split would end the replay (none occurs in the "
-                       "timed steps)"}
+                       "cases with crack fronts, where a split ends the replay and the rest of the call runs "
+                       "eagerly; 'splits' counts the run-time splits at the end"}
         cases = [("notched_block_20x8x2", plate_small(), 2000, "fp64", False)]
         if a.ensemble_steps > 0:
-            cases.append(("ensemble_256_seed4", _workload("ensemble"), a.ensemble_steps, "mixed", False))
+            we = _workload("ensemble")
+            cases.append(("ensemble_256_seed4", we, a.ensemble_steps, "mixed", False))
+            cases.append(("ensemble_256_seed4_crack_fronts", we, a.ensemble_steps, "mixed", True))
         cases.append((w.name + "_crack_fronts", w, 100, "fp64", True))
         for name, wk, steps, prec, fronts in cases:
             res = {"tets": wk.n_tets, "steps": steps, "precision": prec}
             for mode in (("eager_per_step", "eager", "graph") if fronts else ("eager", "graph", "persistent")):
-                sg = CEM.from_workload(wk, device=dev, split_enabled=fronts, precision=prec,
-                                       split_capacity=a.split_capacity if fronts else 0)
+                cap = (wk.n_tets // 4 if name.startswith("ensemble") else a.split_capacity) if fronts else 0
+                sg = CEM.from_workload(wk, device=dev, split_enabled=fronts, precision=prec, split_capacity=cap)
                 if mode == "eager_per_step":
                     sg.set_step_batch(1)
                 run = {"graph": sg.step_graph, "persistent": sg.step_persistent}.get(mode, sg.step)

@@ -232,7 +232,10 @@ int cem_set_step_batch(cem_ctx* ctx, int64_t max_steps);
  * cem_set_step_batch describes: when a step's front evaluation decides
  * splits, the graph's later steps return at once, the host applies the
  * splits, and the rest of the n steps run as cem_step runs them (the
- * topology changed, so that part is not replayed).  The graph is captured on
+ * topology changed, so that part is not replayed).  While the crack is
+ * active (a step split and no step since has run without a split) the call
+ * runs as cem_step does, without a capture, since a replay would end at its
+ * first step.  The graph is captured on
  * a private stream on the first call and re-captured when n, the mesh sizes,
  * the crack-front count, the topology or the launch variants change; later
  * calls replay it on the context's stream.  Results are bit-identical to

@@ -1201,9 +1201,20 @@ int cem_step_graph(cem_ctx* c, int64_t n) {
     if (c->prof) return cem_fail(c, CEM_ESTATE, "kernel timing is on (cem_profile): use cem_step");
     if (int rc = select_device(c)) return rc;
     if (n == 0) return CEM_OK;
+    const bool fronts = c->split_enabled && c->n_cand > 0;
+    // While the crack is active (the last step split, and no step since has run without a
+    // split) a replay would end at its first step and the topology would change under every
+    // capture: run as cem_step does until a step passes without a split.
+    if (fronts && c->spec_len == 1 && c->n_split_run > 0) {
+        if (int rc = run_steps(c, n)) return rc;
+        if (int rc = cem_launch_check_finite(c)) return rc;
+        if (int rc = sync_counts(c)) return rc;
+        if (int rc = check_tma_wait(c)) return rc;
+        if (c->hcount[CNT_SCRATCH1]) return cem_fail(c, CEM_ENONFINITE, "non-finite displacement");
+        return CEM_OK;
+    }
     if (c->tune_auto)   // settle the launch variants for the current sizes before capturing them
         if (int rc = cem_tune_maybe(c)) return rc;
-    const bool fronts = c->split_enabled && c->n_cand > 0;
     constexpr int K = cem_ctx::GRAPH_KEY;
     const int64_t key[K] = {n,      c->T,           c->E,       c->N,       c->n_cand,  c->n_act_orig,
                             fronts, c->topo_version, c->tune[0], c->tune[1], c->tune[2], c->tune[3]};

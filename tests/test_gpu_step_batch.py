@@ -100,7 +100,8 @@ def test_batch_length_is_checked(CEM):
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_graph_with_crack_fronts_matches_eager(CEM, precision):
     """Replays from the first step: the early calls run whole (no split yet, the same
-    graph replayed), later ones end at a split and finish eagerly."""
+    graph replayed); later, a replay that a split ends finishes eagerly, calls made
+    while the crack is active run eagerly, and a quiet crack is captured again."""
     w = plate_small()
     eager = CEM.from_workload(w, precision=precision)
     graph = CEM.from_workload(w, precision=precision)
@@ -120,5 +121,22 @@ def test_graph_with_crack_fronts_ensemble(CEM):
     for _ in range(12):
         eager.step(100)
         graph.step_graph(100)
+        _same(eager, graph)
+    assert graph.energy()["n_split"] > 0
+
+
+def test_graph_with_more_front_elements_than_one_scan_block(CEM):
+    """4,320 crack-front elements (60 specimens, 72 each): the ordered compaction of
+    the front's decisions runs in two blocks, whose look-back status words a graph
+    replay clears first.  Two replays of one graph without a split, then calls whose
+    replay a split ends, against eager steps."""
+    w = union([kuhn_block(20, 8, 36, 0.1, 0.04, 0.09, notch_length=0.05, traction=2.0e6, name="s%d" % i)
+               for i in range(60)], spacing=0.1)
+    eager = CEM.from_workload(w)
+    graph = CEM.from_workload(w)
+    assert graph.info()["n_candidates"] == 4320
+    for n in (10, 10, 30, 30):
+        eager.step(n)
+        graph.step_graph(n)
         _same(eager, graph)
     assert graph.energy()["n_split"] > 0
