@@ -76,22 +76,38 @@ int64_t next_pow2(int64_t x) {
     return p;
 }
 
-// f(begin, end) over [0, n) split into contiguous chunks on the host's cores.  Every
-// caller writes disjoint output slots, so the result does not depend on the split.
+// [0, n) split into nt contiguous chunks of `size` items (the last one shorter or empty),
+// one per host core (one chunk below 16,384 items).
+struct Chunks {
+    int64_t nt, size;
+};
+Chunks chunks_of(int64_t n) {
+    int64_t nt = std::max<int64_t>(1, std::min<int64_t>(std::thread::hardware_concurrency(), 64));
+    if (n < 16384) nt = 1;
+    return {nt, std::max<int64_t>(1, (n + nt - 1) / nt)};
+}
+
+// f(k, begin, end) for chunk k of chunks_of(n), the chunks on the host's cores.  Every
+// caller writes disjoint output slots (or per-chunk buffers), so the result does not
+// depend on the split.
 template <class F>
-void parallel_for(int64_t n, F f) {
-    const int64_t nt = std::max<int64_t>(1, std::min<int64_t>(std::thread::hardware_concurrency(), 64));
-    if (n < 16384 || nt == 1) {
-        f((int64_t)0, n);
+void parallel_chunks(int64_t n, F f) {
+    const Chunks ch = chunks_of(n);
+    if (ch.nt == 1) {
+        f((int64_t)0, (int64_t)0, n);
         return;
     }
-    const int64_t chunk = (n + nt - 1) / nt;
     std::vector<std::thread> th;
-    for (int64_t k = 0; k < nt; ++k) {
-        const int64_t a = k * chunk, b = std::min(n, a + chunk);
-        if (a < b) th.emplace_back(f, a, b);
+    for (int64_t k = 0; k < ch.nt; ++k) {
+        const int64_t a = std::min(n, k * ch.size), b = std::min(n, a + ch.size);
+        th.emplace_back(f, k, a, b);
     }
     for (auto& t : th) t.join();
+}
+
+template <class F>
+void parallel_for(int64_t n, F f) {
+    parallel_chunks(n, [&](int64_t, int64_t a, int64_t b) { f(a, b); });
 }
 
 struct HostTopo {
@@ -104,23 +120,42 @@ struct HostTopo {
 
 int build_topology(cem_ctx* c, const std::vector<int>& conn, HostTopo& H) {
     const int64_t N = c->N0, T = c->T0;
-    // node -> element * 4 + local, ascending: counted and placed with atomic counters on
-    // all host cores, then each node's list sorted (the result does not depend on the order)
+    // node -> element * 4 + local, ascending: a counting sort by node.  Each chunk of
+    // consecutive entries q = 4 element + local counts its entries per node; a node's list
+    // then takes chunk 0's entries, chunk 1's, ..., each in ascending q, so the lists come
+    // out ascending without a sort or an atomic.
     H.inc_off.assign(N + 1, 0);
     {
-        std::unique_ptr<std::atomic<int>[]> cnt(new std::atomic<int>[N + 1]);
-        for (int64_t i = 0; i <= N; ++i) cnt[i].store(0, std::memory_order_relaxed);
-        parallel_for(4 * T, [&](int64_t a, int64_t b) {
-            for (int64_t q = a; q < b; ++q) cnt[conn[q]].fetch_add(1, std::memory_order_relaxed);
-        });
-        for (int64_t i = 0; i < N; ++i) H.inc_off[i + 1] = H.inc_off[i] + cnt[i].load(std::memory_order_relaxed);
-        for (int64_t i = 0; i < N; ++i) cnt[i].store(H.inc_off[i], std::memory_order_relaxed);
-        H.inc.assign(4 * T, 0);
-        parallel_for(4 * T, [&](int64_t a, int64_t b) {
-            for (int64_t q = a; q < b; ++q) H.inc[cnt[conn[q]].fetch_add(1, std::memory_order_relaxed)] = (int)q;
+        const Chunks ch = chunks_of(4 * T);
+        // per chunk: count per node, then its first slot (each chunk clears its own row)
+        std::unique_ptr<int[]> pos(new int[(size_t)ch.nt * N]);
+        parallel_chunks(4 * T, [&](int64_t k, int64_t a, int64_t b) {
+            int* p = pos.get() + k * N;
+            std::fill(p, p + N, 0);
+            for (int64_t q = a; q < b; ++q) ++p[conn[q]];
         });
         parallel_for(N, [&](int64_t a, int64_t b) {
-            for (int64_t i = a; i < b; ++i) std::sort(H.inc.begin() + H.inc_off[i], H.inc.begin() + H.inc_off[i + 1]);
+            for (int64_t i = a; i < b; ++i) {
+                int s = 0;
+                for (int64_t k = 0; k < ch.nt; ++k) s += pos[k * N + i];
+                H.inc_off[i + 1] = s;
+            }
+        });
+        for (int64_t i = 0; i < N; ++i) H.inc_off[i + 1] += H.inc_off[i];
+        parallel_for(N, [&](int64_t a, int64_t b) {
+            for (int64_t i = a; i < b; ++i) {
+                int run = H.inc_off[i];
+                for (int64_t k = 0; k < ch.nt; ++k) {
+                    const int cnt = pos[k * N + i];
+                    pos[k * N + i] = run;
+                    run += cnt;
+                }
+            }
+        });
+        H.inc.assign(4 * T, 0);
+        parallel_chunks(4 * T, [&](int64_t k, int64_t a, int64_t b) {
+            int* p = pos.get() + k * N;
+            for (int64_t q = a; q < b; ++q) H.inc[p[conn[q]]++] = (int)q;
         });
     }
     // edges: for each node the sorted distinct neighbours with larger id (counted, then
@@ -137,23 +172,25 @@ int build_topology(cem_ctx* c, const std::vector<int>& conn, HostTopo& H) {
         std::sort(buf.begin(), buf.end());
         buf.erase(std::unique(buf.begin(), buf.end()), buf.end());
     };
+    // each chunk of nodes keeps its lists in a buffer of its own, copied into place once
+    // the offsets are known
     H.e_off.assign(N + 1, 0);
-    parallel_for(N, [&](int64_t a, int64_t b) {
-        std::vector<int> buf;
-        for (int64_t i = a; i < b; ++i) {
-            neighbours(i, buf);
-            H.e_off[i + 1] = (int)buf.size();
-        }
-    });
-    for (int64_t i = 0; i < N; ++i) H.e_off[i + 1] += H.e_off[i];
-    H.e_nbr.assign(H.e_off[N], 0);
-    parallel_for(N, [&](int64_t a, int64_t b) {
-        std::vector<int> buf;
-        for (int64_t i = a; i < b; ++i) {
-            neighbours(i, buf);
-            std::copy(buf.begin(), buf.end(), H.e_nbr.begin() + H.e_off[i]);
-        }
-    });
+    {
+        std::vector<std::vector<int>> part(chunks_of(N).nt);
+        parallel_chunks(N, [&](int64_t k, int64_t a, int64_t b) {
+            std::vector<int> buf;
+            for (int64_t i = a; i < b; ++i) {
+                neighbours(i, buf);
+                H.e_off[i + 1] = (int)buf.size();
+                part[k].insert(part[k].end(), buf.begin(), buf.end());
+            }
+        });
+        for (int64_t i = 0; i < N; ++i) H.e_off[i + 1] += H.e_off[i];
+        H.e_nbr.assign(H.e_off[N], 0);
+        parallel_chunks(N, [&](int64_t k, int64_t a, int64_t b) {
+            if (a < b) std::copy(part[k].begin(), part[k].end(), H.e_nbr.begin() + H.e_off[a]);
+        });
+    }
     c->E0 = (int64_t)H.e_nbr.size();
     c->max_inc0 = 0;
     for (int64_t i = 0; i < N; ++i) c->max_inc0 = std::max<int64_t>(c->max_inc0, H.inc_off[i + 1] - H.inc_off[i]);
@@ -183,19 +220,35 @@ int build_topology(cem_ctx* c, const std::vector<int>& conn, HostTopo& H) {
         }
         return k;
     };
+    // one intersection per edge, into per-chunk buffers copied into place afterwards
     H.fan_off.assign(c->E0 + 1, 0);
-    parallel_for(N, [&](int64_t a, int64_t b) {
-        for (int64_t x = a; x < b; ++x)
-            for (int e = H.e_off[x]; e < H.e_off[x + 1]; ++e) H.fan_off[e + 1] = fan_of(x, H.e_nbr[e], nullptr);
-    });
-    c->max_fan0 = 0;
-    for (int64_t e = 0; e < c->E0; ++e) c->max_fan0 = std::max<int64_t>(c->max_fan0, H.fan_off[e + 1]);
-    for (int64_t e = 0; e < c->E0; ++e) H.fan_off[e + 1] += H.fan_off[e];
-    H.fan.assign(H.fan_off[c->E0], 0);
-    parallel_for(N, [&](int64_t a, int64_t b) {
-        for (int64_t x = a; x < b; ++x)
-            for (int e = H.e_off[x]; e < H.e_off[x + 1]; ++e) fan_of(x, H.e_nbr[e], H.fan.data() + H.fan_off[e]);
-    });
+    {
+        const Chunks ch = chunks_of(N);
+        std::vector<std::vector<int>> part(ch.nt);
+        std::vector<int64_t> pmax(ch.nt, 0);
+        parallel_chunks(N, [&](int64_t k, int64_t a, int64_t b) {
+            std::vector<int>& out = part[k];
+            size_t used = 0;
+            for (int64_t x = a; x < b; ++x)
+                for (int e = H.e_off[x]; e < H.e_off[x + 1]; ++e) {
+                    const int y = H.e_nbr[e];
+                    // room for the shorter of the two lists (the buffer grows geometrically)
+                    const size_t room = used + std::min(H.inc_off[x + 1] - H.inc_off[x], H.inc_off[y + 1] - H.inc_off[y]);
+                    if (out.size() < room) out.resize(std::max(room, 2 * out.size()));
+                    const int f = fan_of(x, y, out.data() + used);
+                    used += f;
+                    H.fan_off[e + 1] = f;
+                    pmax[k] = std::max<int64_t>(pmax[k], f);
+                }
+            out.resize(used);
+        });
+        c->max_fan0 = *std::max_element(pmax.begin(), pmax.end());
+        for (int64_t e = 0; e < c->E0; ++e) H.fan_off[e + 1] += H.fan_off[e];
+        H.fan.assign(H.fan_off[c->E0], 0);
+        parallel_chunks(N, [&](int64_t k, int64_t a, int64_t b) {
+            if (a < b) std::copy(part[k].begin(), part[k].end(), H.fan.begin() + H.fan_off[H.e_off[a]]);
+        });
+    }
     // face adjacency (local face f is opposite local node f)
     H.face_nbr.assign(4 * T, -1);
     std::atomic<bool> non_manifold{false};
