@@ -475,8 +475,12 @@ int cem_reorder_nodes(cem_ctx* ctx);
  * mesh, element type, precision, capacity or time step; a truncated or
  * corrupted file: in all of these the context is left as it was; a file
  * that changes while it is being loaded, after which the context's state is
- * undefined), CEM_ECUDA.  Array contents are not validated beyond the hash:
- * load only files that cem_save wrote.  The file is in host byte order. */
+ * undefined), CEM_ECUDA.  In the same first pass every index array is
+ * range-checked (node, element, edge and pool indices within the file's
+ * counts, every fan and incidence list inside its pool's used part, the node
+ * storage order a permutation): a file with an index out of range returns
+ * CEM_EINVAL and leaves the context as it was.  Floating-point contents are
+ * not checked.  The file is in host byte order. */
 int cem_save(cem_ctx* ctx, const char* path);
 int cem_load(cem_ctx* ctx, const char* path);
 
